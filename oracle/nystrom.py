@@ -1,0 +1,80 @@
+"""Oracle: randomized Nystrom approximation (App. A) and the Nystrom preconditioner (Alg. 4).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+App. A, Alg. randomized_nystrom, in the paper's order:
+    Omega = randn(p, ell);  Omega = qr(Omega, 0);  Y = G Omega;
+    nu = eps(norm(Y, 'fro'));  Y_nu = Y + nu Omega;  C = chol(Omega^T Y_nu);
+    B = Y_nu / C;  [U, Sigma, ~] = svd(B, 0);  Lambda = max(0, Sigma^2 - nu I).
+Readings where the paper is silent (shared with the CUDA side):
+  * qr is the thin QR normalised so that R has a positive diagonal (unique).
+  * eps(x) is MATLAB's spacing of doubles at x.  When Y comes from a sketch whose
+    inputs were rounded to a unit roundoff u_in (TF32, BF16, FP32), the shift is
+    nu = max(eps(||Y||_F), u_in ||Y||_F) so that Omega^T Y_nu stays positive
+    definite despite the rounding of Y; u_in = 0 is the paper's FP64 algorithm.
+  * chol reads the symmetric part (Omega^T Y_nu + Y_nu^T Omega)/2 and returns the
+    upper factor C with C^T C = that matrix (MATLAB's chol reads one triangle; the
+    two agree in exact arithmetic).
+Preconditioner, Alg. 4 (scaled form of Eq. nystrom_inverse):
+    P^{-1} v = (lambda_ell + mu) U (Lambda + mu I)^{-1} U^T v + (I - U U^T) v.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+EPS64 = 2.0 ** -52
+
+
+def thin_qr(Omega):
+    """Thin QR with a positive diagonal in R; returns Q (App. A, second step)."""
+    Q, R = np.linalg.qr(Omega, mode="reduced")
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s[None, :]
+
+
+def shift(normY: float, u_in: float = 0.0) -> float:
+    """nu = eps(||Y||_F), raised to u_in ||Y||_F for a rounded sketch (reading above)."""
+    return max(float(np.spacing(np.float64(normY))), u_in * normY)
+
+
+def nystrom_factor(Omega, Y, u_in: float = 0.0):
+    """Steps 4-9 of App. A given the orthonormal test matrix and Y = G Omega.
+
+    Returns U (p, ell), lambda_hat (ell, descending) and the shift nu.
+    Raises numpy.linalg.LinAlgError if Omega^T Y_nu is not positive definite.
+    """
+    nu = shift(np.linalg.norm(Y, "fro"), u_in)
+    Ynu = Y + nu * Omega
+    M = Omega.T @ Ynu
+    M = 0.5 * (M + M.T)
+    C = np.linalg.cholesky(M).T                      # upper, C^T C = M
+    B = scipy.linalg.solve_triangular(C, Ynu.T, trans="T", lower=False).T   # B C = Y_nu
+    U, S, _ = np.linalg.svd(B, full_matrices=False)
+    lam = np.maximum(0.0, S * S - nu)
+    return U, lam, nu
+
+
+def randomized_nystrom(G_apply, Omega_raw, u_in: float = 0.0):
+    """The whole of App. A: orthonormalise, sketch Y = G Omega, factor."""
+    Omega = thin_qr(Omega_raw)
+    Y = G_apply(Omega)
+    U, lam, nu = nystrom_factor(Omega, Y, u_in)
+    return Omega, Y, U, lam, nu
+
+
+def nystrom_matrix(U, lam):
+    """G_hat = U diag(lambda_hat) U^T (only for small checks)."""
+    return (U * lam[None, :]) @ U.T
+
+
+def precond_apply(U, lam, mu, v):
+    """P^{-1} v in the scaled form of Alg. 4."""
+    Utv = U.T @ v
+    return (lam[-1] + mu) * (U @ (Utv / (lam + mu))) + (v - U @ Utv)
+
+
+def mu_from_lambda1(lam1: float, gamma: float = 10.0, eps: float = EPS64) -> float:
+    """mu = gamma * eps_mach * lambda_hat_1 (Sec. 4.3, Alg. 4 second step)."""
+    return gamma * eps * lam1

@@ -1,0 +1,125 @@
+"""Oracle: preconditioned CG, Armijo backtracking and one Nystrom-preconditioned NGD step.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The paper solves (G + mu I) d = grad L with pCG (Sec. 4, Alg. 3) but prints no
+pCG pseudocode; this is textbook preconditioned CG (Hestenes-Stiefel, Saad
+Alg. 9.1) with x_0 = 0:
+    r_0 = g, z_0 = P^{-1} r_0, p_0 = z_0
+    repeat: q = A p; alpha = r^T z / p^T q; x += alpha p; r -= alpha q;
+            stop when ||r|| <= rtol ||g|| or maxit iterations are done;
+            z = P^{-1} r; beta = r_new^T z_new / r^T z; p = z + beta p.
+The recurrence residual is the one tested (reading: the paper fixes only maxit).
+
+Armijo (Sec. 4.4 "Algorithmic details", Alg. 1): alpha = 1, accept when
+L(theta - alpha d) <= L(theta) - c1 alpha g^T d, else alpha <- rho alpha; the
+constants are not printed (reading: c1 = 1e-4, rho = 1/2, at most 30 trials,
+non-finite losses rejected, alpha = 0 if no trial is accepted).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import gramian as _gram
+from . import mlp as _mlp
+from . import nystrom as _nys
+from . import philox as _philox
+
+
+class Breakdown(RuntimeError):
+    """p^T (G + mu I) p <= 0 inside CG."""
+
+
+def pcg(A, g, Pinv, rtol: float, maxit: int):
+    """Returns (x, iterations, final recurrence relres ||r_k|| / ||g||)."""
+    g = np.asarray(g, dtype=np.float64)
+    x = np.zeros_like(g)
+    gnorm = float(np.linalg.norm(g))
+    if gnorm == 0.0 or maxit <= 0:
+        return x, 0, 0.0 if gnorm == 0.0 else 1.0
+    r = g.copy()
+    z = Pinv(r) if Pinv is not None else r.copy()
+    p = z.copy()
+    rz = float(r @ z)
+    for k in range(1, maxit + 1):
+        q = A(p)
+        pq = float(p @ q)
+        if not pq > 0.0:
+            raise Breakdown(f"p^T A p = {pq} at iteration {k}")
+        alpha = rz / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rn = float(np.linalg.norm(r))
+        if rn <= rtol * gnorm or k == maxit:
+            return x, k, rn / gnorm
+        z = Pinv(r) if Pinv is not None else r.copy()
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    raise AssertionError("unreachable")
+
+
+def armijo(loss_fn, theta, d, g, L0, c1=1e-4, rho=0.5, max_trials=30):
+    """Backtracking along alpha -> theta - alpha d.  Returns (alpha, L(theta - alpha d), trials)."""
+    slope = float(g @ d)
+    alpha = 1.0
+    for i in range(max_trials):
+        L = loss_fn(theta - alpha * d)
+        if np.isfinite(L) and L <= L0 - c1 * alpha * slope:
+            return alpha, float(L), i + 1
+        alpha *= rho
+    return 0.0, float(L0), max_trials
+
+
+@dataclass
+class StepInfo:
+    loss_before: float
+    loss_after: float
+    alpha: float
+    mu: float
+    lam1: float
+    lam_ell: float
+    nu: float
+    pcg_iters: int
+    relres: float
+    armijo_trials: int
+
+
+def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, u_in=0.0, gamma=10.0,
+             c1=1e-4, rho=0.5, max_trials=30, return_parts=False):
+    """One Nystrom-preconditioned matrix-free NGD step (Alg. 1 + Alg. 3 + Alg. 4, fixed ell).
+
+    mu=None selects mu = gamma eps lambda_hat_1 (Alg. 4).  maxit caps pCG; rtol=0
+    runs exactly maxit iterations (for comparisons at a fixed iteration count).
+    """
+    g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1, line 2
+    J = _mlp.jacobian(problem, theta)                              # 'precompute Jacobian only'
+    w = problem.w
+
+    def G_apply(V):
+        return J.T @ (w[:, None] * (J @ V)) if V.ndim == 2 else _gram.gramian_mv(J, w, V)
+
+    Omega_raw = _philox.gaussian_test_matrix(J.shape[1], ell, seed, step)
+    Omega, Y, U, lam, nu = _nys.randomized_nystrom(G_apply, Omega_raw, u_in)   # Alg. 4, line 1
+    mu_eff = float(mu) if mu is not None else _nys.mu_from_lambda1(lam[0], gamma)  # Alg. 4, line 2
+
+    def A(v):
+        return _gram.gramian_mv(J, w, v, mu_eff)
+
+    def Pinv(v):
+        return _nys.precond_apply(U, lam, mu_eff, v)
+
+    d, iters, relres = pcg(A, g, Pinv, rtol, maxit)                # Alg. 3, line 3
+
+    def loss_fn(th):
+        return _mlp.residual(problem, th)[1]
+
+    alpha, L1, trials = armijo(loss_fn, theta, d, g, L0, c1, rho, max_trials)   # Alg. 1, line 4
+    info = StepInfo(L0, L1, alpha, mu_eff, float(lam[0]), float(lam[-1]), nu, iters, relres, trials)
+    theta_new = theta - alpha * d                                   # Alg. 1, line 5
+    if return_parts:
+        return theta_new, info, dict(g=g, r=r, J=J, Omega=Omega, Y=Y, U=U, lam=lam, d=d)
+    return theta_new, info

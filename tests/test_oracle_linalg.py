@@ -1,0 +1,264 @@
+"""Pins for oracle/gramian.py, oracle/nystrom.py, oracle/solve.py and oracle/philox.py (no GPU)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import gramian, mlp, nystrom, philox, solve
+from paper_2505_11638_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small(seed=0, n_int=16, n_bnd=6, widths=None, d=2):
+    pr, theta = inputs.small_problem(d=d, widths=widths, n_int=n_int, n_bnd=n_bnd, seed=seed)
+    J = mlp.jacobian(pr, theta)
+    return pr, theta, J
+
+
+# ----------------------------------------------------------------------------- Gramian
+def test_gramian_brute_force_symmetric_psd_trace():
+    pr, theta, J = _small(seed=1, n_int=8, n_bnd=3, widths=[2, 4, 3, 1])
+    G = gramian.gramian(J, pr.w)
+    # brute force entry by entry (Thm. 1: G_ij = sum_r w_r dr_r/dtheta_i dr_r/dtheta_j)
+    Gb = np.zeros_like(G)
+    for i in range(pr.p):
+        for j in range(pr.p):
+            Gb[i, j] = sum(pr.w[r] * J[r, i] * J[r, j] for r in range(pr.n))
+    np.testing.assert_allclose(G, Gb, rtol=1e-13, atol=1e-16)
+    assert np.abs(G - G.T).max() <= 1e-15 * np.abs(G).max()
+    ev = np.linalg.eigvalsh(G)
+    assert ev[0] >= -1e-12 * ev[-1]
+    # rank <= number of points
+    assert np.sum(ev > 1e-10 * ev[-1]) <= pr.n
+    # trace and diagonal: Eq. gram_diagonal
+    assert np.trace(G) == pytest.approx(sum(pr.w[r] * J[r] @ J[r] for r in range(pr.n)), rel=1e-13)
+    np.testing.assert_allclose(gramian.gramian_diag(J, pr.w), np.diag(G), rtol=1e-13)
+
+
+def test_gramian_mv_matches_explicit_and_blocked():
+    pr, theta, J = _small(seed=2)
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(pr.p)
+    G = gramian.gramian(J, pr.w)
+    y = gramian.gramian_mv(J, pr.w, v, 1e-3)
+    np.testing.assert_allclose(y, G @ v + 1e-3 * v, rtol=1e-12, atol=1e-14)
+    yb = gramian.gramian_mv_blocked(lambda rows: mlp.jacobian(pr, theta, rows), pr.n, pr.w, v, 1e-3, block=5)
+    np.testing.assert_allclose(yb, y, rtol=1e-12, atol=1e-14)
+    # matrix-free form by JVP then VJP (Thm. 1 consequence)
+    ymf = mlp.vjp(pr, theta, pr.w * mlp.jvp(pr, theta, v)) + 1e-3 * v
+    np.testing.assert_allclose(ymf, y, rtol=1e-11, atol=1e-14)
+
+
+def test_direct_direction_residual():
+    pr, theta, J = _small(seed=3)
+    G = gramian.gramian(J, pr.w)
+    g = mlp.gradient(pr, theta)[0]
+    mu = 1e-6
+    d = gramian.direct_direction(G, g, mu)
+    res = (G + mu * np.eye(pr.p)) @ d - g
+    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(g)
+
+
+# ----------------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        out = philox.philox4x32_10(np.array([v[0:4]], dtype=np.uint32), np.array([v[4:6]], dtype=np.uint32))
+        assert out[0].tolist() == v[6:10]
+
+
+def test_uniform52_and_box_muller():
+    u = philox.uniform52(np.array([0, 0xFFFFFFFF], dtype=np.uint32), np.array([0, 0xFFFFFFFF], dtype=np.uint32))
+    assert u[0] == 0.5 * 2.0 ** -52 and u[1] == 1.0 - 0.5 * 2.0 ** -52
+    assert 0.0 < u[0] < u[1] < 1.0
+    # resolution: consecutive codes differ by exactly 2^-52
+    v = philox.uniform52(np.array([7, 7], dtype=np.uint32), np.array([0, 1 << 12], dtype=np.uint32))
+    assert v[1] - v[0] == 2.0 ** -52
+    rng = np.random.default_rng(0)
+    u1, u2 = rng.uniform(1e-12, 1, 1000), rng.uniform(0, 1, 1000)
+    z0, z1 = philox.box_muller(u1, u2)
+    # invert the polar map: u1 = exp(-(z0^2 + z1^2)/2), 2 pi u2 = atan2(z1, z0) mod 2 pi
+    np.testing.assert_allclose(np.exp(-(z0 ** 2 + z1 ** 2) / 2), u1, rtol=1e-10)
+    np.testing.assert_allclose(np.mod(np.arctan2(z1, z0), 2 * np.pi), 2 * np.pi * u2, rtol=1e-9, atol=1e-9)
+
+
+def test_gaussian_test_matrix_distribution_and_layout():
+    Om = philox.gaussian_test_matrix(4001, 50, seed=12345, step=7)
+    assert Om.shape == (4001, 50)
+    x = Om.ravel()
+    assert abs(x.mean()) < 0.01 and abs(x.std() - 1) < 0.01
+    assert scipy.stats.kstest(x, "norm").pvalue > 1e-3
+    # independent streams for other seeds / steps; identical for the same counters
+    assert not np.allclose(Om, philox.gaussian_test_matrix(4001, 50, seed=12345, step=8))
+    assert not np.allclose(Om, philox.gaussian_test_matrix(4001, 50, seed=12346, step=7))
+    np.testing.assert_array_equal(Om[:, :20], philox.gaussian_test_matrix(4001, 20, seed=12345, step=7))
+    np.testing.assert_array_equal(Om[:4000], philox.gaussian_test_matrix(4000, 50, seed=12345, step=7))
+    # rows 2m and 2m+1 come from one block: counter (m, j, step, 0), key (seed, 0)
+    blk = philox.philox4x32_10(np.array([[3, 5, 7, 0]], dtype=np.uint32), np.array([[12345, 0]], dtype=np.uint32))[0]
+    z0, z1 = philox.box_muller(philox.uniform52(blk[0], blk[1]), philox.uniform52(blk[2], blk[3]))
+    assert Om[6, 5] == z0 and Om[7, 5] == z1
+
+
+# ----------------------------------------------------------------------------- Nystrom
+def _psd(p, rank, rng, decay=0.5):
+    Q = np.linalg.qr(rng.standard_normal((p, rank)))[0]
+    lam = decay ** np.arange(rank)
+    return (Q * lam) @ Q.T
+
+
+def test_thin_qr_unique():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((40, 9))
+    Q = nystrom.thin_qr(A)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(9), atol=1e-14)
+    R = Q.T @ A
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(np.tril(R, -1), 0, atol=1e-13)
+    np.testing.assert_allclose(Q @ R, A, atol=1e-13)
+
+
+def test_nystrom_exact_when_rank_below_ell():
+    """With ell >= rank G the Nystrom approximation reproduces G."""
+    pr, theta, J = _small(seed=4, n_int=14, n_bnd=6, widths=[2, 6, 5, 1])   # N=20, p=59
+    G = gramian.gramian(J, pr.w)
+    Om = philox.gaussian_test_matrix(pr.p, 30, seed=1, step=0)
+    _, _, U, lam, nu = nystrom.randomized_nystrom(lambda V: G @ V, Om)
+    Gh = nystrom.nystrom_matrix(U, lam)
+    assert np.linalg.norm(Gh - G, 2) <= 1e-10 * np.linalg.norm(G, 2)
+    np.testing.assert_allclose(U.T @ U, np.eye(30), atol=1e-12)
+    assert np.all(np.diff(lam) <= 0)
+
+
+def test_nystrom_matches_definition_and_bounds():
+    """Eq. nystrom_approx: G_hat = (G Om)(Om^T G Om)^+ (G Om)^T; G - G_hat is PSD; lambda_hat_i <= lambda_i."""
+    rng = np.random.default_rng(5)
+    p, ell = 60, 12
+    G = _psd(p, 40, rng, decay=0.7)
+    Om = rng.standard_normal((p, ell))
+    _, _, U, lam, nu = nystrom.randomized_nystrom(lambda V: G @ V, Om)
+    Gh = nystrom.nystrom_matrix(U, lam)
+    Y = G @ Om
+    Gdef = Y @ np.linalg.pinv(Om.T @ Y) @ Y.T
+    assert np.linalg.norm(Gh - Gdef, 2) <= 1e-10 * np.linalg.norm(G, 2)
+    assert np.linalg.eigvalsh(G - Gh)[0] >= -1e-12 * np.linalg.norm(G, 2)
+    lam_true = np.sort(np.linalg.eigvalsh(G))[::-1][:ell]
+    assert np.all(lam <= lam_true * (1 + 1e-10) + 1e-14)
+
+
+def test_nystrom_invariant_under_right_multiplication():
+    rng = np.random.default_rng(6)
+    p, ell = 50, 10
+    G = _psd(p, 30, rng, decay=0.6)
+    Om = rng.standard_normal((p, ell))
+    R = rng.standard_normal((ell, ell)) + 3 * np.eye(ell)
+    G1 = nystrom.nystrom_matrix(*nystrom.randomized_nystrom(lambda V: G @ V, Om)[2:4])
+    G2 = nystrom.nystrom_matrix(*nystrom.randomized_nystrom(lambda V: G @ V, Om @ R)[2:4])
+    assert np.linalg.norm(G1 - G2, 2) <= 1e-10 * np.linalg.norm(G, 2)
+
+
+def test_shift_is_spacing_of_doubles():
+    for x in [1.0, 3.7, 1e-3, 123456.0]:
+        assert nystrom.shift(x) == np.spacing(x)
+        assert nystrom.shift(x) == 2.0 ** (np.floor(np.log2(x)) - 52)
+    assert nystrom.shift(8.0, 2.0 ** -10) == 8.0 * 2.0 ** -10
+
+
+def test_preconditioner_exact_nystrom_gives_mu_identity():
+    """If G_hat = G (ell > rank) then lambda_ell = 0 and P^{-1}(G + mu I) = mu I."""
+    rng = np.random.default_rng(7)
+    p = 40
+    G = _psd(p, 8, rng, decay=0.5)
+    _, _, U, lam, nu = nystrom.randomized_nystrom(lambda V: G @ V, rng.standard_normal((p, 12)))
+    assert lam[-1] == 0.0
+    mu = 1e-3
+    M = np.column_stack([nystrom.precond_apply(U, lam, mu, e) for e in np.eye(p)])
+    np.testing.assert_allclose(M @ (G + mu * np.eye(p)), mu * np.eye(p), atol=1e-10)
+    # P^{-1} is symmetric positive definite
+    assert np.abs(M - M.T).max() < 1e-12
+    assert np.linalg.eigvalsh(M)[0] > 0
+
+
+# ----------------------------------------------------------------------------- PCG / Armijo / step
+def test_pcg_reaches_direct_solution():
+    pr, theta, J = _small(seed=8, n_int=30, n_bnd=8)
+    G = gramian.gramian(J, pr.w)
+    g = mlp.gradient(pr, theta)[0]
+    mu = 1e-4
+    dstar = gramian.direct_direction(G, g, mu)
+    x, it, rr = solve.pcg(lambda v: G @ v + mu * v, g, None, 1e-13, 2000)
+    assert rr <= 1e-13
+    assert np.linalg.norm(x - dstar) <= 1e-8 * np.linalg.norm(dstar)
+    _, _, U, lam, _ = nystrom.randomized_nystrom(lambda V: G @ V, philox.gaussian_test_matrix(pr.p, 20, 3, 0))
+    x2, it2, rr2 = solve.pcg(lambda v: G @ v + mu * v, g, lambda v: nystrom.precond_apply(U, lam, mu, v), 1e-13, 2000)
+    assert np.linalg.norm(x2 - dstar) <= 1e-8 * np.linalg.norm(dstar)
+    assert it2 < it
+
+
+def test_cg_finite_termination_low_rank():
+    """G + mu I with rank G = r has at most r + 1 distinct eigenvalues: CG ends in <= r + 1 steps."""
+    rng = np.random.default_rng(9)
+    p, r = 30, 4
+    G = _psd(p, r, rng, decay=0.5)
+    g = rng.standard_normal(p)
+    x, it, rr = solve.pcg(lambda v: G @ v + 0.1 * v, g, None, 1e-10, 100)
+    assert it <= r + 1 and rr <= 1e-10
+
+
+def test_cg_energy_error_monotone():
+    rng = np.random.default_rng(10)
+    p = 25
+    A = _psd(p, p, rng, decay=0.8) + 1e-2 * np.eye(p)
+    g = rng.standard_normal(p)
+    xs = np.linalg.solve(A, g)
+    errs = []
+    for k in range(1, 15):
+        x, _, _ = solve.pcg(lambda v: A @ v, g, None, 0.0, k)
+        e = x - xs
+        errs.append(e @ A @ e)
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-12) for i in range(len(errs) - 1))
+
+
+def test_pcg_one_iteration_with_exact_nystrom():
+    rng = np.random.default_rng(11)
+    p = 40
+    G = _psd(p, 6, rng, decay=0.5)
+    _, _, U, lam, _ = nystrom.randomized_nystrom(lambda V: G @ V, rng.standard_normal((p, 10)))
+    g = rng.standard_normal(p)
+    mu = 1e-3
+    x, it, rr = solve.pcg(lambda v: G @ v + mu * v, g, lambda v: nystrom.precond_apply(U, lam, mu, v), 1e-10, 50)
+    assert it == 1
+    np.testing.assert_allclose(x, np.linalg.solve(G + mu * np.eye(p), g), rtol=1e-8)
+
+
+def test_pcg_breakdown_detected():
+    with pytest.raises(solve.Breakdown):
+        solve.pcg(lambda v: -v, np.ones(3), None, 1e-8, 10)
+
+
+def test_armijo_backtracking_exact_alpha():
+    loss = lambda th: 0.5 * float(th @ th)
+    th = np.array([1.0, -2.0, 0.5])
+    g = th.copy()
+    a, L, n = solve.armijo(loss, th, g, g, loss(th))
+    assert a == 1.0 and L == 0.0 and n == 1
+    a, L, n = solve.armijo(loss, th, 3 * g, g, loss(th))       # alpha = 1 overshoots to -2 theta
+    assert a == 0.5 and n == 2 and L == pytest.approx(loss(-0.5 * th))
+    a, L, n = solve.armijo(lambda t: np.nan, th, g, g, 1.0, max_trials=4)
+    assert a == 0.0 and n == 4
+
+
+def test_ngd_step_decreases_loss_and_matches_direct():
+    pr, theta = inputs.small_problem(d=2, n_int=40, n_bnd=12, seed=12)
+    th1, info, parts = solve.ngd_step(pr, theta, ell=30, mu=1e-6, rtol=1e-12, maxit=500, seed=5, step=0,
+                                      return_parts=True)
+    assert info.loss_after < info.loss_before
+    G = gramian.gramian(parts["J"], pr.w)
+    dstar = gramian.direct_direction(G, parts["g"], 1e-6)
+    assert np.linalg.norm(parts["d"] - dstar) <= 1e-6 * np.linalg.norm(dstar)
+    # the heuristic mu of Alg. 4
+    _, info2 = solve.ngd_step(pr, theta, ell=30, mu=None, rtol=1e-8, maxit=100, seed=5, step=0)
+    assert info2.mu == pytest.approx(10 * 2.0 ** -52 * info2.lam1)
