@@ -1,0 +1,319 @@
+"""Benchmark: Nystrom-preconditioned matrix-free NGD steps/s on one GB300 (or N replicas).
+
+Workload: the 5-D Poisson PINN (MLP 5-64-64-64-1, p = 8769, 4000 interior + 1000 boundary
+points, FP32 activations and Jacobian, FP64 CG reductions, ell = 500, mu = 1e-7, PCG rtol 1e-6),
+synthetic Monte-Carlo points drawn from a fixed seed.  One step = one ngd_step: gradient and
+Jacobian, Gaussian test matrix, sketch, Nystrom factor, preconditioned CG, Armijo, update.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sketch f32|tf32|bf16]
+
+N > 1 runs under torchrun: every rank steps an independent replica (its own seed), with no
+data-path collective; the barrier and the max-over-ranks timing use the process group.
+--impl reference times the FP64 CPU oracle on the host cores for the same workload.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "poisson5d"
+METRIC = "NGD steps/s at PCG rtol 1e-6"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read only)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_11638_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it still matches the sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+def make_problem(seed_offset: int = 0):
+    from paper_2505_11638_gb300 import inputs
+    wl, thetas = inputs.make_workload(WORKLOAD, seed=seed_offset)
+    return wl, wl.problems[0], thetas[0]
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_steps(pr, theta, wl, k_max, budget_s):
+    """Time up to k_max oracle NGD steps (stopping once budget_s is spent). Returns (times, infos)."""
+    from oracle import solve
+    times, infos = [], []
+    th = theta.copy()
+    for k in range(k_max):
+        t0 = time.perf_counter()
+        th, info = solve.ngd_step(pr, th, ell=wl.ell, mu=wl.mu, rtol=wl.rtol, maxit=1000, seed=0, step=k,
+                                  u_in=0.0)
+        times.append(time.perf_counter() - t0)
+        infos.append(info)
+        if sum(times) > budget_s:
+            break
+    return times, infos
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl, pr, theta = make_problem()
+    budget = float(os.environ.get("NGD_REF_BUDGET_S", "150"))
+    _, _ = oracle_steps(pr, theta, wl, 0, budget)          # imports outside the timed loop
+    times, infos = oracle_steps(pr, theta, wl, args.steps, budget)
+    t = float(np.mean(times))
+    value = 1.0 / t
+    sample = (f"{len(times)} of the requested {args.steps} FP64 oracle NGD steps on the full workload "
+              f"(time budget {budget:.0f} s); mean PCG iterations {np.mean([i.pcg_iters for i in infos]):.1f}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": pr.n, "p": pr.p, "ell": wl.ell, "mu": wl.mu, "rtol": wl.rtol},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2505_11638_gb300 import build, ngd
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    ngd.lib()
+    wl, pr, theta0 = make_problem(seed_offset=rank * 1000)
+    ctx = ngd.Context(pr, dtype=wl.dtype)
+    opts = dict(ell=wl.ell, mu=wl.mu, rtol=wl.rtol, maxit=1000, sketch=args.sketch, seed=rank)
+    theta = torch.tensor(theta0, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    # warm-up (also builds every lazily sized workspace)
+    for k in range(args.warmup):
+        ctx.step(theta, step=k, **opts)
+    theta.copy_(torch.tensor(theta0, device="cuda"))
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    l0 = ngd.ngd_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for k in range(args.steps):
+        infos.append(ctx.step(theta, step=k, **opts))
+    e1.record(stream)
+    barrier()
+    launches = ngd.ngd_kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * 1e3 / ms_per_step
+
+    # end to end through the public API with host buffers: theta in from pinned host memory,
+    # the step, theta and the loss back to the host, inside the timed region
+    h_theta = torch.tensor(theta0).pin_memory()
+    h_out = torch.empty_like(h_theta).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 10))
+    for k in range(e2e_steps):
+        theta.copy_(h_theta, non_blocking=True)
+        info = ctx.step(theta, step=k, **opts)
+        h_out.copy_(theta, non_blocking=True)
+        torch.cuda.synchronize()
+        _ = info["loss_after"]
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    barrier()
+
+    # Gramian matvecs/s and the roofline of the matvec kernels, timed alone on the context stream
+    v = torch.randn(pr.p, dtype=torch.float64, device="cuda")
+    ctx.gramian_mv(theta, v, wl.mu)
+    y = torch.empty_like(v)
+    reps = 200
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        ngd.ngd_gramian_mv(ctx.handle, None, v, wl.mu, y)
+    ev0.record(stream)
+    for _ in range(reps):
+        ngd.ngd_gramian_mv(ctx.handle, None, v, wl.mu, y)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gv_ms = ev0.elapsed_time(ev1) / reps
+    ldJ = (pr.p + 31) // 32 * 32
+    gv_bytes = 2.0 * pr.n * ldJ * 4 + 6.0 * pr.p * 8 + 3.0 * pr.n * 8
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    achieved = gv_bytes / (gv_ms * 1e-3) / 1e9
+    roofline = {"kernel": "gramian_mv (k_rowdot + k_coldot: J streamed twice, FP32)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "frac": achieved / (hbm if hbm else 6800.0),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if hbm else "fallback 6.8 TB/s",
+                "traffic": profiled_traffic("gramian_mv_poisson5d"), "bytes_per_launch": gv_bytes,
+                "ms_per_launch": gv_ms}
+
+    phases = {k: float(np.mean([i[k] for i in infos])) for k in
+              ["ms_linearize", "ms_sketch", "ms_factor", "ms_pcg", "ms_linesearch"]}
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": pr.n, "p": pr.p, "ell": wl.ell, "mu": wl.mu, "rtol": wl.rtol,
+                       "sketch": args.sketch, "maxit": 1000,
+                       "l2": "inputs larger than L2: the FP32 Jacobian streamed by every matvec is 176 MB"},
+            "gramian_mv_per_s": 1e3 / gv_ms * world,
+            "pcg_iters_mean": float(np.mean([i["pcg_iters"] for i in infos])),
+            "loss_first_last": [infos[0]["loss_before"], infos[-1]["loss_after"]],
+            "phases_ms": phases,
+            "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": pr.p * 8,
+                    "d2h_bytes_per_step": pr.p * 8 + 8},
+            "gpu_launches": int(launches), "roofline": roofline, "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        budget = float(os.environ.get("NGD_CPU_BUDGET_S", "25"))
+        times, cinfos = oracle_steps(pr, theta0, wl, 3, budget)
+        line["cpu_baseline"] = {"value": 1.0 / float(np.mean(times)), "unit": "steps/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": f"{len(times)} FP64 oracle NGD step(s) on the full workload "
+                                          f"(PCG iterations {[i.pcg_iters for i in cinfos]})"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sketch", default="f32", choices=["f32", "tf32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = _env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * ngd.h -- C ABI of libngd, the GB300 (sm_103a) hot path of matrix-free natural
+ * gradient descent for PINNs with a randomized Nystrom preconditioner
+ * (Bioli, Marcati, Sangalli, arXiv 2505.11638).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *     library never frees them and never keeps them beyond the call, except the
+ *     problem arrays X, w, target of ngd_problem_desc, which must stay valid
+ *     until ngd_destroy.  Pointers named "host" are ordinary host memory.
+ *   - All device work is enqueued on the context's stream.  Calls that return a
+ *     host scalar (loss, iteration count, relres, ngd_step_info) synchronise that
+ *     stream before returning; every other call is asynchronous.
+ *   - Every call returns an ngd_status; no C++ exception crosses the ABI.
+ *     ngd_last_error(ctx) gives a one-line message for the last failure.
+ *     Shapes and pointers are validated on the host (NGD_ERR_INVALID_ARG) before
+ *     anything is enqueued.  Device-side failures (non-SPD core, CG breakdown,
+ *     non-finite values) are recorded in a device status word and reported by
+ *     the next call that synchronises.
+ *   - theta, v, y, g, d and every other length-p parameter-space vector are
+ *     float64.  The working precision of activations, of the Jacobian and of
+ *     the p x ell matrices Omega, Y and U is the context dtype (NGD_F64: double,
+ *     NGD_F32: float).  Residual-space vectors (length N) are float64.
+ *   - theta layout (Sec. 2.3): layer by layer, W_l row-major (n_l x n_{l-1})
+ *     followed by b_l; p = sum_l (n_l n_{l-1} + n_l).
+ *   - "Linearization": calls that take theta (re)linearize the context at theta
+ *     (evaluate the residuals and, in stored-Jacobian mode, form J); passing
+ *     theta = NULL reuses the last linearization (for repeated matvecs).
+ */
+#ifndef NGD_H
+#define NGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ngd_ctx ngd_ctx;
+
+typedef enum {
+  NGD_OK = 0,
+  NGD_ERR_INVALID_ARG = 1,  /* bad shape, pointer, enum or option (host check) */
+  NGD_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  NGD_ERR_OOM = 3,          /* workspace allocation failed */
+  NGD_ERR_NOT_SPD = 4,      /* Omega^T Y_nu not positive definite (Nystrom core) */
+  NGD_ERR_BREAKDOWN = 5,    /* p^T (G + mu I) p <= 0 inside CG */
+  NGD_ERR_MAXIT = 6,        /* reserved: CG stopped at maxit (reported via relres, not as an error) */
+  NGD_ERR_NONFINITE = 7,    /* a NaN/Inf reached a reduction */
+  NGD_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+  NGD_ERR_UNSUPPORTED = 9   /* valid request this build cannot serve (e.g. network too wide) */
+} ngd_status;
+
+typedef enum { NGD_F64 = 0, NGD_F32 = 1 } ngd_dtype;
+
+/* Arithmetic of the sketch GEMMs Z = J Omega and Y = J^T (w .* Z):
+ *   F64  FP64 CUDA cores; F32 FP32 CUDA cores with FP64 cross-tile sums;
+ *   TF32 / BF16 tcgen05 tensor cores (operands rounded, FP32 accumulation in TMEM). */
+typedef enum { NGD_SKETCH_F64 = 0, NGD_SKETCH_F32 = 1, NGD_SKETCH_TF32 = 2, NGD_SKETCH_BF16 = 3 } ngd_sketch_prec;
+
+/* Interior residual: Poisson  r = Delta u + f  (Eq. energy_poisson);
+ *                    heat     r = u_t - kappa Delta u - f, coordinate 0 = t.
+ * Boundary / initial rows: r = u - g.                                          */
+typedef enum { NGD_PDE_POISSON = 0, NGD_PDE_HEAT = 1 } ngd_pde;
+
+/* Gramian matvec strategy (Sec. 4.1.2, Table tab:matvec_costs):
+ *   STORED_J     "precompute Jacobian only": J (N x p) is formed once per
+ *                linearization and streamed by every matvec;
+ *   MATRIX_FREE  "recompute batch Jacobian on the fly": JVP kernel, then the
+ *                VJP by point blocks whose Jacobian rows are recomputed;
+ *   AUTO         STORED_J when J fits mem_budget, else MATRIX_FREE.          */
+typedef enum { NGD_GV_AUTO = 0, NGD_GV_STORED_J = 1, NGD_GV_MATRIX_FREE = 2 } ngd_gv_mode;
+
+typedef struct {
+  int pde;                /* ngd_pde */
+  double kappa;           /* heat diffusivity (ignored for Poisson) */
+  int n_layers;           /* number of affine layers L+1 (>= 2), at most 8 */
+  const int* widths;      /* host, n_layers+1 entries: widths[0] = d_in (<= 16), widths[n_layers] = 1,
+                             hidden widths <= 512 */
+  int64_t n_int, n_bnd;   /* interior rows first, then boundary rows; N = n_int + n_bnd >= 1 */
+  const double* X;        /* device, N x d_in row-major collocation points */
+  const double* w;        /* device, N quadrature weights (w_r phi_r of Thm. 1) */
+  const double* target;   /* device, N: source f at interior rows, boundary value g at boundary rows */
+  int dtype;              /* ngd_dtype: working precision */
+  int gv_mode;            /* ngd_gv_mode */
+  size_t mem_budget;      /* bytes the context may use for J and stored Taylor coefficients; 0 = no limit */
+  void* stream;           /* cudaStream_t the context enqueues on (NULL: legacy default stream) */
+} ngd_problem_desc;
+
+typedef struct {
+  int ell;                /* Nystrom rank (sketch size), 1 <= ell <= min(p, 2048) */
+  double mu;              /* damping; mu <= 0 selects mu = gamma eps lambda_hat_1 (Alg. 4) */
+  double gamma;           /* gamma of the mu rule (paper default 10) */
+  double rtol;            /* PCG stop: ||r_k|| <= rtol ||g|| (recurrence residual) */
+  int maxit;              /* PCG iteration cap */
+  int sketch;             /* ngd_sketch_prec */
+  uint64_t seed;          /* Philox key of the Gaussian test matrix */
+  uint64_t step;          /* Philox counter word: fresh Omega per NGD step */
+  double armijo_c1;       /* sufficient-decrease constant (default 1e-4) */
+  double armijo_rho;      /* backtracking factor (default 0.5) */
+  int armijo_max;         /* maximum number of trial steps (default 30) */
+} ngd_step_opts;
+
+typedef struct {
+  double loss_before, loss_after, alpha, mu, lam1, lam_ell, nu, relres;
+  int pcg_iters, armijo_trials, shift_retries, status;
+  double ms_linearize, ms_sketch, ms_factor, ms_pcg, ms_linesearch; /* CUDA-event phase times */
+} ngd_step_info;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context for one PINN problem.  Copies the description (not X/w/target,
+ * which stay caller-owned and must outlive the context), validates it, sizes and
+ * allocates the workspace with cudaMalloc on the current device.
+ * Errors: INVALID_ARG (bad shape/pointer), UNSUPPORTED (too wide/deep), OOM, CUDA. */
+ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out);
+
+/* Free the context and its workspace (synchronises its stream).  NULL is a no-op. */
+void ngd_destroy(ngd_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); the string is owned by ctx. */
+const char* ngd_last_error(const ngd_ctx* ctx);
+
+/* Total number of CUDA kernels this library has launched in the calling process (all
+ * contexts), for instrumentation: a caller brackets a region with two reads. */
+uint64_t ngd_kernel_launches(void);
+
+/* Number of network parameters p. */
+int64_t ngd_num_params(const ngd_ctx* ctx);
+
+/* Number of collocation points N. */
+int64_t ngd_num_points(const ngd_ctx* ctx);
+
+/* Replace the stream the context enqueues on. */
+ngd_status ngd_set_stream(ngd_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------- residual, JVP, VJP */
+
+/* Residual vector and loss (Sec. 2.2.1, Eq. energy_poisson; Sec. 5.1):
+ * r_r as in ngd_pde, L = 1/2 sum_r w_r r_r^2, by the fused forward-Laplacian
+ * (Taylor-mode) kernel.  theta: device p (float64).  r: device N or NULL.
+ * loss: host or NULL; when non-NULL the call synchronises.
+ * If the context may store Taylor coefficients (mem_budget), they are kept for
+ * a following ngd_vjp(ctx, NULL, ...). */
+ngd_status ngd_residual(ngd_ctx* ctx, const double* theta, double* r, double* loss);
+
+/* Jacobian-vector product Jv (forward-mode tangents of the Taylor-mode forward;
+ * Thm. 1 consequence, Sec. 3.2).  v: device p, out: device N. */
+ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* out);
+
+/* Vector-Jacobian product J^T c, the hand-written reverse of the residual kernel
+ * (Thm. 1 consequence).  theta = NULL reuses the Taylor coefficients stored by the
+ * last ngd_residual when they were kept, else recomputes them.
+ * cot: device N, out: device p. */
+ngd_status ngd_vjp(ngd_ctx* ctx, const double* theta, const double* cot, double* out);
+
+/* Gradient g = grad L = J^T (w .* r) (Alg. 1 line 2), residual r (device N or NULL)
+ * and loss (host or NULL, synchronises when non-NULL).  Linearizes at theta. */
+ngd_status ngd_gradient(ngd_ctx* ctx, const double* theta, double* g, double* r, double* loss);
+
+/* ---------------------------------------------------------------- Gramian */
+
+/* y = (G + mu I) v with G = J^T diag(w) J (Thm. 1, Eq. G_matrixfree) by the
+ * context's matvec strategy.  theta NULL reuses the last linearization.
+ * v, y: device p, must not alias.  mu >= 0. */
+ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, double mu, double* y);
+
+/* ---------------------------------------------------------------- Nystrom */
+
+/* Sketch of App. A, Alg. randomized_nystrom, first three steps:
+ * Omega_raw = randn(p, ell) from Philox4x32-10 (key = seed, counter word = step,
+ * layout in the implementation notes), Omega = thin QR factor with positive
+ * diag(R) (CholeskyQR2), Y = G Omega = J^T (w .* (J Omega)) in the arithmetic
+ * 'prec' (the only dense contraction of the path).
+ * Omega, Y: device, p x ell column-major (leading dimension p), context dtype.
+ * ell <= min(p, 2048).  TF32/BF16 need an F32 context and the stored Jacobian. */
+ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step,
+                              int prec, void* Omega, void* Y);
+
+/* Factor of App. A, remaining steps, given an orthonormal Omega and Y = G Omega:
+ * nu = max(eps(||Y||_F), u_in ||Y||_F) with u_in the unit roundoff of 'prec'
+ * (0 for F64), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
+ * B = Y_nu C^{-1}, eigen-decomposition of B^T B in FP64 (cyclic Jacobi) gives
+ * B = U Sigma V^T, lambda = max(0, Sigma^2 - nu), descending.
+ * shift_scale multiplies nu (1 = the rule above; ngd_step retries with 8, 64).
+ * Omega, Y: device p x ell (context dtype), U: device p x ell out, lam: device ell
+ * float64 out, nu_out: host or NULL (synchronises when non-NULL).
+ * NOT_SPD when C does not exist. */
+ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const void* Y, int prec,
+                              double shift_scale, void* U, double* lam, double* nu_out);
+
+/* Nystrom preconditioner, Alg. 4 (scaled form of Eq. nystrom_inverse):
+ * z = (lam_ell + mu) U (Lambda + mu I)^{-1} U^T v + (I - U U^T) v.
+ * U: device p x ell (context dtype), lam: device ell, v, z: device p (no aliasing). */
+ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, const double* lam, double mu,
+                             const double* v, double* z);
+
+/* ---------------------------------------------------------------- solver */
+
+/* Preconditioned CG for (G + mu I) d = g (Alg. 3; textbook pCG, x0 = 0), stopping
+ * when ||r_k||_2 <= rtol ||g||_2 (recurrence residual, FP64) or after maxit
+ * iterations.  ell = 0 or U = NULL runs unpreconditioned CG.  mu > 0.
+ * theta NULL reuses the last linearization.  g, d: device p; iters, relres: host
+ * (the call synchronises).  Returns BREAKDOWN if p^T (G + mu I) p <= 0. */
+ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, double mu,
+                         const void* U, const double* lam, int ell, double rtol, int maxit,
+                         double* d, int* iters, double* relres);
+
+/* One Nystrom-preconditioned matrix-free NGD step (Alg. 1 with Alg. 3 and Alg. 4,
+ * fixed ell): gradient, sketch with a fresh Omega, factor (retrying with an
+ * 8x / 64x shift on NOT_SPD), mu (fixed or the Alg. 4 rule), pCG, Armijo
+ * backtracking along theta - alpha d, update.  theta: device p, updated in place.
+ * info: host or NULL.  Synchronises. */
+ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* opts, ngd_step_info* info);
+
+/* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
+ * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,
+ * c1 1e-4, rho 0.5, 30 trials. */
+void ngd_default_step_opts(ngd_step_opts* opts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NGD_H */

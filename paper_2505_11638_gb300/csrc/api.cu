@@ -1,0 +1,946 @@
+// C ABI of libngd (include/ngd.h): context, workspace and the orchestration of the
+// Nystrom-preconditioned matrix-free NGD step on one GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "linalg.cuh"
+#include "sketch_tc.cuh"
+
+using namespace ngd;
+
+static std::atomic<unsigned long long> g_launches{0};
+void ngd::note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+struct ngd_ctx {
+  NetDesc net{};
+  PointSet ps{};
+  int dtype = NGD_F64;
+  int gv_mode = NGD_GV_AUTO;
+  size_t mem_budget = 0;
+  cudaStream_t stream = nullptr;
+  int64_t N = 0, p = 0, ldJ = 0, ldP = 0;
+  size_t elt = 8;
+  std::string err;
+
+  bool stored_j = false;     // J (N x ldJ) is kept between matvecs
+  bool tape_allowed = false; // Taylor coefficients may be stored by ngd_residual
+  bool lin_valid = false;    // prep (and J when stored) match the last linearized theta
+  bool tape_valid = false;   // tape matches the current prep
+  bool prep_valid = false;   // prep holds the weights of a caller's theta
+
+  void* prep = nullptr;      // prepared weights of theta (working dtype)
+  void* prep_t = nullptr;    // prepared tangent weights (working dtype)
+  void* J = nullptr;         // N x ldJ (stored mode) or block x ldJ (matrix-free block buffer)
+  int64_t jrows = 0;         // rows J can hold
+  void* tape = nullptr;      // N x tape_per_point
+  void* vT = nullptr;        // ldJ working-dtype vector
+  double* r = nullptr;       // N residuals
+  double* svec = nullptr;    // N scratch
+  double* tvec = nullptr;    // N scratch
+  double* part = nullptr;    // kRedBlocks partials
+  double* lpart = nullptr;   // per-block loss partials of the Taylor kernels (N entries)
+  double* colpart = nullptr; // coldot partials
+  int colsplit = 1;
+  double* scal = nullptr;    // device scalars, see kS* below
+  int* status = nullptr;     // device status word
+  PcgScalars* pcg = nullptr;
+  double *x = nullptr, *rr = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;  // PCG vectors (p)
+  double *g = nullptr, *d = nullptr, *theta_trial = nullptr;                     // step vectors (p)
+
+  // sketch / factor workspace, grown on demand
+  int ell_cap = 0;
+  void *Om = nullptr, *Y = nullptr, *B = nullptr, *U = nullptr, *Lr = nullptr, *VsT = nullptr, *Zw = nullptr;
+  double *M = nullptr, *A1 = nullptr, *V = nullptr, *Vs = nullptr, *sig2 = nullptr, *inv_sigma = nullptr;
+  double *lam = nullptr, *dinv = nullptr, *w1 = nullptr, *gpart = nullptr;
+  size_t gpart_elems = 0;
+  int* perm = nullptr;
+  unsigned int* jac_cnt = nullptr;
+  int* jac_info = nullptr;
+  TcSketch* tc = nullptr;
+
+  double* h_scal = nullptr;  // pinned host scalars
+  int* h_int = nullptr;
+  PcgScalars* h_pcg = nullptr;
+  cudaEvent_t ev[6] = {};
+};
+
+enum { kSLoss = 0, kSFrob2 = 1, kSNu = 2, kSMu = 3, kSDot = 4, kSCount = 8 };
+
+namespace {
+
+ngd_status set_err(ngd_ctx* c, ngd_status st, const char* fmt, const char* a = "") {
+  char buf[512];
+  snprintf(buf, sizeof(buf), fmt, a);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return set_err(ctx, NGD_ERR_CUDA, "CUDA: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(call)                        \
+  do {                                   \
+    ngd_status s_ = (call);              \
+    if (s_ != NGD_OK) return s_;         \
+  } while (0)
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+template <typename P>
+ngd_status dalloc(ngd_ctx* ctx, P** ptr, size_t bytes) {
+  if (*ptr) {
+    cudaFree(*ptr);
+    *ptr = nullptr;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return set_err(ctx, NGD_ERR_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
+  }
+  return NGD_OK;
+}
+
+ngd_status check_launch(ngd_ctx* ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(ctx, NGD_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return NGD_OK;
+}
+
+ngd_status sync_status(ngd_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int st = ctx->h_int[0];
+  if (st & kStatNotSpd) return set_err(ctx, NGD_ERR_NOT_SPD, "Nystrom core Omega^T Y_nu is not positive definite%s");
+  if (st & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
+  if (st & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value in a reduction%s");
+  if (st & kStatTimeout) return set_err(ctx, NGD_ERR_TIMEOUT, "device wait timed out%s");
+  return NGD_OK;
+}
+
+ngd_status clear_status(ngd_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  return NGD_OK;
+}
+
+// ------------------------------------------------------------------ small kernels
+__global__ void k_mul(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c, int64_t n) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) c[i] = a[i] * b[i];
+}
+void launch_mul(const double* a, const double* b, double* c, int64_t n, cudaStream_t s) {
+  k_mul<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(a, b, c, n); note_launch();
+}
+
+template <typename T>
+__global__ void k_d2t_mat(const double* __restrict__ src, int64_t lds, T* __restrict__ dst, int64_t ldd, int64_t rows,
+                          int64_t cols) {
+  const int64_t n = rows * cols, st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += st) {
+    const int64_t c = e / rows, r = e - c * rows;
+    dst[r + c * ldd] = (T)src[r + c * lds];
+  }
+}
+
+// ------------------------------------------------------------------ dtype dispatch helpers
+template <typename F>
+ngd_status by_dtype(ngd_ctx* ctx, F&& f) {
+  if (ctx->dtype == NGD_F32) return f(float(0));
+  return f(double(0));
+}
+
+ngd_status ensure_ell(ngd_ctx* ctx, int ell) {
+  if (ell <= ctx->ell_cap) return NGD_OK;
+  const size_t pe = (size_t)ctx->ldP * ell * ctx->elt;
+  const size_t l2 = (size_t)ell * ell;
+  TRY(dalloc(ctx, &ctx->Om, pe));
+  TRY(dalloc(ctx, &ctx->Y, pe));
+  TRY(dalloc(ctx, &ctx->B, pe));
+  TRY(dalloc(ctx, &ctx->U, pe));
+  TRY(dalloc(ctx, &ctx->Lr, l2 * ctx->elt));
+  TRY(dalloc(ctx, &ctx->VsT, l2 * ctx->elt));
+  TRY(dalloc(ctx, &ctx->Zw, (size_t)ctx->N * ell * ctx->elt));
+  TRY(dalloc(ctx, &ctx->M, l2 * 8));
+  TRY(dalloc(ctx, &ctx->A1, l2 * 8));
+  TRY(dalloc(ctx, &ctx->V, l2 * 8));
+  TRY(dalloc(ctx, &ctx->Vs, l2 * 8));
+  TRY(dalloc(ctx, &ctx->sig2, ell * 8));
+  TRY(dalloc(ctx, &ctx->inv_sigma, ell * 8));
+  TRY(dalloc(ctx, &ctx->lam, ell * 8));
+  TRY(dalloc(ctx, &ctx->dinv, ell * 8));
+  TRY(dalloc(ctx, &ctx->w1, ell * 8));
+  TRY(dalloc(ctx, &ctx->perm, ell * sizeof(int)));
+  ctx->ell_cap = ell;
+  CK(cudaMemsetAsync(ctx->Om, 0, pe, ctx->stream));
+  CK(cudaMemsetAsync(ctx->Y, 0, pe, ctx->stream));
+  CK(cudaMemsetAsync(ctx->B, 0, pe, ctx->stream));
+  CK(cudaMemsetAsync(ctx->U, 0, pe, ctx->stream));
+  return NGD_OK;
+}
+
+ngd_status ensure_gpart(ngd_ctx* ctx, size_t elems) {
+  if (elems <= ctx->gpart_elems) return NGD_OK;
+  TRY(dalloc(ctx, &ctx->gpart, elems * 8));
+  ctx->gpart_elems = elems;
+  return NGD_OK;
+}
+
+// K-splits for an M x N output with a long K (tall-skinny products), so that ~1200 tiles run.
+int choose_splits(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  int64_t ns = std::max<int64_t>(1, 1200 / std::max<int64_t>(tiles, 1));
+  ns = std::min<int64_t>(ns, std::max<int64_t>(1, K / 128));
+  return (int)std::min<int64_t>(ns, 64);
+}
+
+// FP64 out = A^T B for column-major p x ell A and B (ld) -> ell x ell (column-major).
+template <typename T>
+ngd_status gram_atb(ngd_ctx* ctx, const T* A, const T* Bm, int64_t p, int64_t ld, int ell, double* out) {
+  GemmArgs<T> g;
+  g.M = ell; g.N = ell; g.K = p;
+  g.A = A; g.sam = ld; g.sak = 1;
+  g.B = Bm; g.sbk = 1; g.sbn = ld;
+  g.nsplit = choose_splits(ell, ell, p);
+  const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : g.K;
+  const int nz = (int)((g.K + kps - 1) / kps);
+  TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));
+  g.out64 = ctx->gpart; g.split_stride = (int64_t)ell * ell;
+  g.scm = 1; g.scn = ell;
+  launch_gemm<T>(g, ctx->stream);
+  launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, out, ctx->stream);
+  return check_launch(ctx);
+}
+
+// ------------------------------------------------------------------ linearization
+template <typename T>
+ngd_status prep_theta(ngd_ctx* ctx, const double* theta) {
+  launch_prep_weights<T>(ctx->net, theta, (T*)ctx->prep, ctx->stream);
+  ctx->tape_valid = false;
+  ctx->prep_valid = true;
+  return check_launch(ctx);
+}
+
+// Residuals, loss (scal[kSLoss]) and, in stored mode, the full Jacobian at theta.
+template <typename T>
+ngd_status linearize(ngd_ctx* ctx, const double* theta) {
+  TRY(prep_theta<T>(ctx, theta));
+  int nb;
+  if (ctx->stored_j) {
+    nb = launch_jacobian<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, (T*)ctx->J, ctx->ldJ, ctx->r,
+                            ctx->lpart, nullptr, 0, ctx->stream);
+    if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
+  } else {
+    T* tape = ctx->tape_allowed ? (T*)ctx->tape : nullptr;
+    nb = launch_forward<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, ctx->r, ctx->lpart, tape, 0,
+                           ctx->stream);
+    if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the forward kernel%s");
+    ctx->tape_valid = tape != nullptr;
+  }
+  launch_sum_partials(ctx->lpart, nb, 0.5, ctx->scal + kSLoss, ctx->stream);
+  ctx->lin_valid = true;
+  return check_launch(ctx);
+}
+
+// y = J^T c for the current prep: stored J (when valid), else by point blocks whose Jacobian
+// rows are recomputed (or rebuilt from the stored tape).
+template <typename T>
+ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_stored) {
+  if (use_stored && ctx->stored_j && ctx->lin_valid) {
+    launch_coldot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, cot, ctx->colpart, ctx->colsplit, nullptr, ctx->stream);
+    launch_coldot_finish(ctx->colpart, ctx->colsplit, ctx->p, ctx->ldJ, nullptr, 0.0, nullptr, out, 0, nullptr,
+                         ctx->stream);
+    return check_launch(ctx);
+  }
+  const int64_t B = ctx->jrows;
+  const T* tape = ctx->tape_valid ? (const T*)ctx->tape : nullptr;
+  for (int64_t r0 = 0; r0 < ctx->N; r0 += B) {
+    const int64_t nr = std::min(B, ctx->N - r0);
+    const int nb = launch_jacobian<T>(ctx->net, ctx->ps, (const T*)ctx->prep, r0, nr, (T*)ctx->J, ctx->ldJ, nullptr,
+                                      nullptr, tape, 0, ctx->stream);
+    if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
+    const int ns = coldot_nsplit(nr, ctx->ldJ, sizeof(T) == 4 ? 4 : 2);
+    launch_coldot<T>((const T*)ctx->J, ctx->ldJ, nr, cot + r0, ctx->colpart, ns, nullptr, ctx->stream);
+    launch_coldot_finish(ctx->colpart, ns, ctx->p, ctx->ldJ, nullptr, 0.0, nullptr, out, r0 > 0 ? 1 : 0, nullptr,
+                         ctx->stream);
+  }
+  return check_launch(ctx);
+}
+
+// y = (G + mu I) v at the current linearization.
+template <typename T>
+ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* mu_d, double* y, const int* done) {
+  if (ctx->stored_j) {
+    launch_d2t<T>(v, (T*)ctx->vT, ctx->p, ctx->ldJ, ctx->stream);
+    launch_rowdot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, (const T*)ctx->vT, ctx->ps.w, nullptr, ctx->svec, done,
+                     ctx->stream);
+    launch_coldot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->svec, ctx->colpart, ctx->colsplit, done, ctx->stream);
+    launch_coldot_finish(ctx->colpart, ctx->colsplit, ctx->p, ctx->ldJ, v, mu_h, mu_d, y, 0, done, ctx->stream);
+    return check_launch(ctx);
+  }
+  // matrix-free: t = J v by forward tangents, then y = J^T (w t) by recomputed Jacobian blocks
+  launch_prep_weights<T>(ctx->net, v, (T*)ctx->prep_t, ctx->stream);
+  if (launch_jvp<T>(ctx->net, ctx->ps, (const T*)ctx->prep, (const T*)ctx->prep_t, ctx->tvec, 0, ctx->stream) <= 0)
+    return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the JVP kernel%s");
+  launch_mul(ctx->ps.w, ctx->tvec, ctx->svec, ctx->N, ctx->stream);
+  TRY(vjp_current<T>(ctx, ctx->svec, y, false));
+  launch_coldot_finish(nullptr, 0, ctx->p, ctx->p, v, mu_h, mu_d, y, 1, nullptr, ctx->stream);  // y += mu v
+  return check_launch(ctx);
+}
+
+// ------------------------------------------------------------------ sketch and factor (internal buffers, ld = ldP)
+double unit_roundoff(int prec) {
+  switch (prec) {
+    case NGD_SKETCH_TF32: return std::ldexp(1.0, -10);   // tensor cores read the top 19 bits (truncation)
+    case NGD_SKETCH_BF16: return std::ldexp(1.0, -8);
+    case NGD_SKETCH_F32: return std::ldexp(1.0, -20);    // FP32 products summed over 128-deep FP32 chunks
+    default: return 0.0;
+  }
+}
+
+template <typename T>
+ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell) {
+  // CholeskyQR2: Om <- Om R^{-1} twice, R = chol(Om^T Om)^T (positive diagonal)
+  for (int pass = 0; pass < 2; ++pass) {
+    TRY(gram_atb<T>(ctx, Om, Om, ctx->p, ctx->ldP, ell, ctx->M));
+    launch_symmetrize(ctx->M, ell, ctx->stream);
+    CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));
+    launch_trsm_lt<T>(Om, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->dinv, ctx->stream);
+  }
+  return check_launch(ctx);
+}
+
+template <typename T>
+ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, int prec) {
+  TRY(ensure_ell(ctx, ell));
+  T* Om = (T*)ctx->Om;
+  T* Y = (T*)ctx->Y;
+  CK(cudaMemsetAsync(Om, 0, (size_t)ctx->ldP * ell * sizeof(T), ctx->stream));
+  launch_philox_omega<T>(Om, ctx->ldP, ctx->p, ell, seed, step, ctx->stream);
+  TRY(clear_status(ctx));
+  TRY(thin_qr_inplace<T>(ctx, Om, ell));
+  if (prec == NGD_SKETCH_TF32 || prec == NGD_SKETCH_BF16) {
+    if (!std::is_same<T, float>::value) return set_err(ctx, NGD_ERR_INVALID_ARG, "TF32/BF16 sketch needs an F32 context%s");
+    if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "TF32/BF16 sketch needs the stored Jacobian%s");
+    if (!ctx->tc) {
+      ctx->tc = tc_create();
+      if (!ctx->tc) return set_err(ctx, NGD_ERR_OOM, "tensor-core sketch state%s");
+    }
+    const char* why = nullptr;
+    cudaError_t e = tc_sketch(ctx->tc, prec == NGD_SKETCH_BF16, (const float*)ctx->J, ctx->ldJ, ctx->N, ctx->p,
+                              (const float*)Om, ctx->ldP, ell, ctx->ps.w, (float*)Y, &why, ctx->stream, ctx->status);
+    if (why) return set_err(ctx, NGD_ERR_UNSUPPORTED, "tensor-core sketch: %s", why);
+    CK(e);
+    return check_launch(ctx);
+  }
+  if (ctx->stored_j) {
+    // Zw = diag(w) J Om  (N x ell, row-major), then Y = J^T Zw  (p x ell, column-major)
+    GemmArgs<T> g1;
+    g1.M = ctx->N; g1.N = ell; g1.K = ctx->p;
+    g1.A = (const T*)ctx->J; g1.sam = ctx->ldJ; g1.sak = 1;
+    g1.B = Om; g1.sbk = 1; g1.sbn = ctx->ldP;
+    g1.outT = (T*)ctx->Zw; g1.scm = ell; g1.scn = 1;
+    g1.rowscale = ctx->ps.w;
+    launch_gemm<T>(g1, ctx->stream);
+    GemmArgs<T> g2;
+    g2.M = ctx->p; g2.N = ell; g2.K = ctx->N;
+    g2.A = (const T*)ctx->J; g2.sam = 1; g2.sak = ctx->ldJ;
+    g2.B = (const T*)ctx->Zw; g2.sbk = ell; g2.sbn = 1;
+    g2.outT = Y; g2.scm = 1; g2.scn = ctx->ldP;
+    launch_gemm<T>(g2, ctx->stream);
+    return check_launch(ctx);
+  }
+  // matrix-free: the same two products by point blocks whose Jacobian rows are recomputed
+  // (Eq. G_matrixfree_batch), Y accumulated in FP64.
+  const int64_t Bsz = ctx->jrows;
+  TRY(ensure_gpart(ctx, (size_t)ctx->ldP * ell));
+  for (int64_t r0 = 0; r0 < ctx->N; r0 += Bsz) {
+    const int64_t nr = std::min(Bsz, ctx->N - r0);
+    if (launch_jacobian<T>(ctx->net, ctx->ps, (const T*)ctx->prep, r0, nr, (T*)ctx->J, ctx->ldJ, nullptr, nullptr,
+                           ctx->tape_valid ? (const T*)ctx->tape : nullptr, 0, ctx->stream) <= 0)
+      return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
+    GemmArgs<T> g1;
+    g1.M = nr; g1.N = ell; g1.K = ctx->p;
+    g1.A = (const T*)ctx->J; g1.sam = ctx->ldJ; g1.sak = 1;
+    g1.B = Om; g1.sbk = 1; g1.sbn = ctx->ldP;
+    g1.outT = (T*)ctx->Zw; g1.scm = ell; g1.scn = 1;
+    g1.rowscale = ctx->ps.w + r0;
+    launch_gemm<T>(g1, ctx->stream);
+    GemmArgs<T> g2;
+    g2.M = ctx->p; g2.N = ell; g2.K = nr;
+    g2.A = (const T*)ctx->J; g2.sam = 1; g2.sak = ctx->ldJ;
+    g2.B = (const T*)ctx->Zw; g2.sbk = ell; g2.sbn = 1;
+    g2.out64 = ctx->gpart; g2.split_stride = 0; g2.scm = 1; g2.scn = ctx->ldP;
+    g2.accumulate = r0 > 0 ? 1 : 0;
+    launch_gemm<T>(g2, ctx->stream);
+  }
+  launch_sum_splits_t<T>(ctx->gpart, 1, 0, ctx->p, ell, ctx->ldP, Y, ctx->ldP, ctx->stream);
+  return check_launch(ctx);
+}
+
+template <typename T>
+ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) {
+  TRY(ensure_ell(ctx, ell));
+  const T* Om = (const T*)ctx->Om;
+  const T* Y = (const T*)ctx->Y;
+  T* Bm = (T*)ctx->B;
+  TRY(clear_status(ctx));
+  launch_frob2<T>(Y, ctx->ldP, ctx->p, ell, ctx->part, ctx->scal + kSFrob2, ctx->stream);
+  launch_compute_nu(ctx->scal + kSFrob2, unit_roundoff(prec), shift_scale, ctx->scal + kSNu, ctx->stream);
+  launch_shift_add<T>(Y, Om, ctx->scal + kSNu, Bm, ctx->ldP, ctx->p, ell, ctx->stream);   // Y_nu
+  TRY(gram_atb<T>(ctx, Om, Bm, ctx->p, ctx->ldP, ell, ctx->M));                          // Omega^T Y_nu
+  launch_symmetrize(ctx->M, ell, ctx->stream);
+  CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));                            // = L L^T, C = L^T
+  launch_trsm_lt<T>(Bm, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->dinv, ctx->stream);  // B = Y_nu C^{-1}
+  TRY(gram_atb<T>(ctx, Bm, Bm, ctx->p, ctx->ldP, ell, ctx->V));                          // S = B^T B
+  launch_symmetrize(ctx->V, ell, ctx->stream);
+  CK(cudaMemcpyAsync(ctx->A1, ctx->V, (size_t)ell * ell * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  // Jacobi works on (A1, Vs as the second buffer) and accumulates rotations in V
+  CK(launch_jacobi(ctx->A1, ctx->Vs, ctx->V, ell, 40, 4.0 * std::ldexp(1.0, -53), ctx->jac_cnt, ctx->jac_info,
+                   ctx->jac_info + 1, ctx->stream));
+  // the final buffer is A1 or Vs; sort the diagonal and gather eigenvectors into M (free now)
+  CK(cudaMemcpyAsync(ctx->h_int + 2, ctx->jac_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double* Afin = ctx->h_int[2] == 0 ? ctx->A1 : ctx->Vs;
+  launch_eig_sort(Afin, ctx->V, ell, ctx->sig2, ctx->M, ctx->perm, ctx->stream);
+  launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
+  // U = B V_sorted diag(1/sigma)
+  {
+    const int64_t n2 = (int64_t)ell * ell;
+    k_d2t_mat<T><<<(int)std::min<int64_t>((n2 + 255) / 256, 4096), 256, 0, ctx->stream>>>(ctx->M, ell, (T*)ctx->VsT,
+                                                                                            ell, ell, ell); note_launch();
+    GemmArgs<T> g;
+    g.M = ctx->p; g.N = ell; g.K = ell;
+    g.A = Bm; g.sam = 1; g.sak = ctx->ldP;
+    g.B = (const T*)ctx->VsT; g.sbk = 1; g.sbn = ell;
+    g.outT = (T*)ctx->U; g.scm = 1; g.scn = ctx->ldP;
+    g.colscale = ctx->inv_sigma;
+    launch_gemm<T>(g, ctx->stream);
+  }
+  TRY(check_launch(ctx));
+  return sync_status(ctx);
+}
+
+// ------------------------------------------------------------------ PCG
+template <typename T>
+ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double* mu_d, const void* U, int64_t ldU,
+                        const double* lam, int ell, double rtol, int maxit, double* dout, int* iters, double* relres) {
+  PcgScalars* h = ctx->h_pcg;
+  memset(h, 0, sizeof(PcgScalars));
+  h->rtol2 = rtol * rtol;
+  h->maxit = maxit;
+  CK(cudaMemcpyAsync(ctx->pcg, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, ctx->stream));
+  TRY(clear_status(ctx));
+  const int64_t p = ctx->p;
+  double* x = dout;
+  double* r = ctx->rr;
+  double* z = ctx->z;
+  double* pv = ctx->pv;
+  double* q = ctx->q;
+  const bool pre = U != nullptr && ell > 0;
+  const int* done = &ctx->pcg->done;
+  launch_pcg_init(g, x, r, p, ctx->part, ctx->pcg, ctx->stream);
+  if (pre)
+    launch_precond<T>((const T*)U, ldU, p, ell, lam, mu_h, mu_d, r, z, ctx->w1, nullptr, ctx->stream);
+  launch_pcg_first_dir(r, pre ? z : r, pv, p, ctx->part, ctx->pcg, ctx->stream);
+  TRY(check_launch(ctx));
+  const int chunk = 2;
+  int launched = 0;
+  while (launched < maxit) {
+    for (int k = 0; k < chunk && launched < maxit; ++k, ++launched) {
+      TRY(gv_current<T>(ctx, pv, mu_h, mu_d, q, done));
+      launch_pcg_alpha(pv, q, p, ctx->part, ctx->pcg, ctx->stream);
+      launch_pcg_update_xr(x, r, pv, q, p, ctx->part, ctx->pcg, ctx->stream);
+      if (pre) launch_precond<T>((const T*)U, ldU, p, ell, lam, mu_h, mu_d, r, z, ctx->w1, done, ctx->stream);
+      launch_pcg_beta(r, pre ? z : r, p, ctx->part, ctx->pcg, ctx->stream);
+      launch_pcg_update_p(pv, pre ? z : r, p, ctx->pcg, ctx->stream);
+    }
+    TRY(check_launch(ctx));
+    CK(cudaMemcpyAsync(h, ctx->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h->done) break;
+  }
+  if (iters) *iters = h->iters;
+  if (relres) *relres = h->gn2 > 0 ? std::sqrt(h->rn2 / h->gn2) : 0.0;
+  if (h->status & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
+  if (h->status & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value inside CG%s");
+  return NGD_OK;
+}
+
+template <typename T>
+ngd_status loss_at(ngd_ctx* ctx, const double* theta, double* loss_host) {
+  TRY(prep_theta<T>(ctx, theta));
+  const int nb = launch_forward<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, nullptr, ctx->lpart, nullptr, 0,
+                                   ctx->stream);
+  if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the forward kernel%s");
+  launch_sum_partials(ctx->lpart, nb, 0.5, ctx->scal + kSLoss, ctx->stream);
+  CK(cudaMemcpyAsync(ctx->h_scal + kSLoss, ctx->scal + kSLoss, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *loss_host = ctx->h_scal[kSLoss];
+  ctx->lin_valid = false;
+  ctx->prep_valid = false;
+  return check_launch(ctx);
+}
+
+float ev_ms(ngd_ctx* ctx, int a, int b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+  return ms;
+}
+
+template <typename T>
+ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_step_info* info) {
+  ngd_step_info inf{};
+  const int64_t p = ctx->p;
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  // Alg. 1 line 2: gradient at theta (and the linearization the matvecs use)
+  TRY(linearize<T>(ctx, theta));
+  launch_mul(ctx->ps.w, ctx->r, ctx->svec, ctx->N, ctx->stream);
+  TRY(vjp_current<T>(ctx, ctx->svec, ctx->g, true));
+  CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  // Alg. 4 line 1: randomized Nystrom (App. A), fresh Omega from (seed, step)
+  TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch));
+  CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+  double scale = 1.0;
+  ngd_status fs = NGD_OK;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    fs = factor_internal<T>(ctx, o->ell, o->sketch, scale);
+    if (fs != NGD_ERR_NOT_SPD) break;
+    inf.shift_retries++;
+    scale *= 8.0;
+  }
+  if (fs != NGD_OK) return fs;
+  CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+  // Alg. 4 line 2: mu (fixed, or gamma eps lambda_1)
+  launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSMu, ctx->stream);
+  // Alg. 3 line 3: pCG on (G + mu I) d = g with the Nystrom preconditioner of Alg. 4
+  int iters = 0;
+  double relres = 0.0;
+  TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, ctx->U, ctx->ldP, ctx->lam, o->ell, o->rtol, o->maxit,
+                      ctx->d, &iters, &relres));
+  CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+  // Alg. 1 line 4: Armijo backtracking along theta - alpha d
+  launch_dot(ctx->g, ctx->d, p, ctx->part, ctx->scal + kSDot, ctx->stream);
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double L0 = ctx->h_scal[kSLoss], slope = ctx->h_scal[kSDot], mu = ctx->h_scal[kSMu], nu = ctx->h_scal[kSNu];
+  double lam_h[2] = {0, 0};
+  CK(cudaMemcpyAsync(ctx->h_scal + 6, ctx->lam, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_scal + 7, ctx->lam + (o->ell - 1), 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  lam_h[0] = ctx->h_scal[6];
+  lam_h[1] = ctx->h_scal[7];
+  double alpha = 1.0, L1 = L0;
+  int trials = 0;
+  bool accepted = false;
+  for (; trials < o->armijo_max;) {
+    ++trials;
+    launch_axpy_to(theta, ctx->d, alpha, ctx->theta_trial, p, ctx->stream);
+    double Lt = 0.0;
+    TRY(loss_at<T>(ctx, ctx->theta_trial, &Lt));
+    if (std::isfinite(Lt) && Lt <= L0 - o->armijo_c1 * alpha * slope) {
+      L1 = Lt;
+      accepted = true;
+      break;
+    }
+    alpha *= o->armijo_rho;
+  }
+  if (!accepted) alpha = 0.0;
+  // Alg. 1 line 5
+  if (alpha != 0.0) launch_axpy_to(theta, ctx->d, alpha, theta, p, ctx->stream);
+  CK(cudaEventRecord(ctx->ev[5], ctx->stream));
+  CK(cudaEventSynchronize(ctx->ev[5]));
+  ctx->lin_valid = false;
+  ctx->tape_valid = false;
+  ctx->prep_valid = false;
+  inf.loss_before = L0;
+  inf.loss_after = L1;
+  inf.alpha = alpha;
+  inf.mu = mu;
+  inf.nu = nu;
+  inf.lam1 = lam_h[0];
+  inf.lam_ell = lam_h[1];
+  inf.relres = relres;
+  inf.pcg_iters = iters;
+  inf.armijo_trials = trials;
+  inf.status = 0;
+  inf.ms_linearize = ev_ms(ctx, 0, 1);
+  inf.ms_sketch = ev_ms(ctx, 1, 2);
+  inf.ms_factor = ev_ms(ctx, 2, 3);
+  inf.ms_pcg = ev_ms(ctx, 3, 4);
+  inf.ms_linesearch = ev_ms(ctx, 4, 5);
+  if (info) *info = inf;
+  return check_launch(ctx);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void ngd_default_step_opts(ngd_step_opts* o) {
+  if (!o) return;
+  o->ell = 100;
+  o->mu = 0.0;
+  o->gamma = 10.0;
+  o->rtol = 1e-6;
+  o->maxit = 500;
+  o->sketch = NGD_SKETCH_TF32;
+  o->seed = 0;
+  o->step = 0;
+  o->armijo_c1 = 1e-4;
+  o->armijo_rho = 0.5;
+  o->armijo_max = 30;
+}
+
+ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
+  ngd_ctx* ctx = nullptr;
+  if (!out) return NGD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || !desc->widths || !desc->X || !desc->w || !desc->target) return NGD_ERR_INVALID_ARG;
+  const int L = desc->n_layers;
+  if (L < 2 || L > kMaxLayers) return NGD_ERR_INVALID_ARG;
+  const int d = desc->widths[0];
+  if (d < 1 || d > kMaxD || desc->widths[L] != 1) return NGD_ERR_INVALID_ARG;
+  for (int l = 1; l < L; ++l)
+    if (desc->widths[l] < 1 || desc->widths[l] > kMaxWidth) return NGD_ERR_INVALID_ARG;
+  if (desc->n_int < 0 || desc->n_bnd < 0 || desc->n_int + desc->n_bnd < 1) return NGD_ERR_INVALID_ARG;
+  if (desc->pde != NGD_PDE_POISSON && desc->pde != NGD_PDE_HEAT) return NGD_ERR_INVALID_ARG;
+  if (desc->pde == NGD_PDE_HEAT && d < 2) return NGD_ERR_INVALID_ARG;
+  if (desc->dtype != NGD_F64 && desc->dtype != NGD_F32) return NGD_ERR_INVALID_ARG;
+  if (desc->gv_mode < NGD_GV_AUTO || desc->gv_mode > NGD_GV_MATRIX_FREE) return NGD_ERR_INVALID_ARG;
+
+  ctx = new (std::nothrow) ngd_ctx();
+  if (!ctx) return NGD_ERR_OOM;
+  NetDesc& net = ctx->net;
+  net.n_layers = L;
+  net.d = d;
+  net.C = d + 2;
+  net.pde = desc->pde;
+  net.kappa = desc->kappa;
+  int64_t off = 0, wsum = 0, bsum = 0, hsum = 0;
+  int maxw = 1;
+  for (int l = 0; l <= L; ++l) net.width[l] = desc->widths[l];
+  for (int l = 0; l < L; ++l) {
+    const int64_t ni = net.width[l], no = net.width[l + 1];
+    net.theta_off[l] = off;
+    off += no * ni + no;
+    wsum += no * ni;
+    bsum += no;
+    if (l >= 1) maxw = std::max(maxw, (int)ni);
+    if (l < L - 1) hsum += no;
+  }
+  net.max_width = maxw;
+  net.p = off;
+  int64_t o1 = 0;
+  for (int l = 0; l < L; ++l) {
+    net.wt_off[l] = o1;
+    o1 += (int64_t)net.width[l + 1] * net.width[l];
+  }
+  for (int l = 0; l < L; ++l) {
+    net.wr_off[l] = o1;
+    o1 += (int64_t)net.width[l + 1] * net.width[l];
+  }
+  for (int l = 0; l < L; ++l) {
+    net.b_off[l] = o1;
+    o1 += net.width[l + 1];
+  }
+  net.prep_size = o1;
+  net.tape_per_point = (int64_t)net.C * hsum;
+  (void)wsum; (void)bsum;
+
+  ctx->ps.X = desc->X;
+  ctx->ps.w = desc->w;
+  ctx->ps.target = desc->target;
+  ctx->ps.n_int = desc->n_int;
+  ctx->ps.N = desc->n_int + desc->n_bnd;
+  ctx->dtype = desc->dtype;
+  ctx->gv_mode = desc->gv_mode;
+  ctx->mem_budget = desc->mem_budget;
+  ctx->stream = (cudaStream_t)desc->stream;
+  ctx->elt = desc->dtype == NGD_F32 ? 4 : 8;
+  ctx->N = ctx->ps.N;
+  ctx->p = net.p;
+  ctx->ldJ = round_up(net.p, 32);
+  ctx->ldP = round_up(net.p, 32);
+
+  auto fail = [&](ngd_status st) {
+    ngd_destroy(ctx);
+    return st;
+  };
+  if (jac_smem_per_point(net, ctx->elt) * 4 > 200 * 1024 || jvp_smem_per_point(net, ctx->elt) * 2 > 200 * 1024)
+    return fail(NGD_ERR_UNSUPPORTED);
+
+  const size_t jbytes = (size_t)ctx->N * ctx->ldJ * ctx->elt;
+  if (ctx->gv_mode == NGD_GV_STORED_J)
+    ctx->stored_j = true;
+  else if (ctx->gv_mode == NGD_GV_MATRIX_FREE)
+    ctx->stored_j = false;
+  else
+    ctx->stored_j = ctx->mem_budget == 0 || jbytes <= ctx->mem_budget;
+  const size_t tbytes = (size_t)ctx->N * net.tape_per_point * ctx->elt;
+  const size_t used = ctx->stored_j ? jbytes : 0;
+  ctx->tape_allowed = ctx->mem_budget == 0 ? !ctx->stored_j : (used + tbytes <= ctx->mem_budget);
+
+  if (ctx->stored_j) {
+    ctx->jrows = ctx->N;
+  } else {
+    const int64_t rows = (int64_t)((64ull << 20) / ((size_t)ctx->ldJ * ctx->elt));
+    ctx->jrows = std::max<int64_t>(32, std::min<int64_t>(rows, ctx->N));
+  }
+  const int vn = ctx->elt == 4 ? 4 : 2;
+  ctx->colsplit = coldot_nsplit(ctx->N, ctx->ldJ, vn);
+  const int64_t N = ctx->N, p = ctx->p;
+  if (dalloc(ctx, &ctx->J, (size_t)ctx->jrows * ctx->ldJ * ctx->elt) != NGD_OK) return fail(NGD_ERR_OOM);
+  if (ctx->tape_allowed && dalloc(ctx, &ctx->tape, tbytes) != NGD_OK) return fail(NGD_ERR_OOM);
+  if (dalloc(ctx, &ctx->prep, net.prep_size * ctx->elt) != NGD_OK || dalloc(ctx, &ctx->prep_t, net.prep_size * ctx->elt) != NGD_OK ||
+      dalloc(ctx, &ctx->vT, ctx->ldJ * ctx->elt) != NGD_OK || dalloc(ctx, &ctx->r, N * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->svec, N * 8) != NGD_OK || dalloc(ctx, &ctx->tvec, N * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->lpart, N * 8) != NGD_OK || dalloc(ctx, &ctx->part, kRedBlocks * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->colpart, (size_t)ctx->colsplit * ctx->ldJ * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->scal, kSCount * 8) != NGD_OK || dalloc(ctx, &ctx->status, 16) != NGD_OK ||
+      dalloc(ctx, &ctx->pcg, sizeof(PcgScalars)) != NGD_OK || dalloc(ctx, &ctx->x, p * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->rr, p * 8) != NGD_OK || dalloc(ctx, &ctx->z, p * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->pv, p * 8) != NGD_OK || dalloc(ctx, &ctx->q, p * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->g, p * 8) != NGD_OK || dalloc(ctx, &ctx->d, p * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->theta_trial, p * 8) != NGD_OK || dalloc(ctx, &ctx->jac_cnt, 16) != NGD_OK ||
+      dalloc(ctx, &ctx->jac_info, 16) != NGD_OK)
+    return fail(NGD_ERR_OOM);
+  if (cudaMallocHost((void**)&ctx->h_scal, kSCount * 8) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_int, 16 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_pcg, sizeof(PcgScalars)) != cudaSuccess)
+    return fail(NGD_ERR_OOM);
+  for (auto& e : ctx->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(NGD_ERR_CUDA);
+  if (cudaMemsetAsync(ctx->J, 0, (size_t)ctx->jrows * ctx->ldJ * ctx->elt, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->status, 0, 16, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->scal, 0, kSCount * 8, ctx->stream) != cudaSuccess)
+    return fail(NGD_ERR_CUDA);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(NGD_ERR_CUDA);
+  *out = ctx;
+  return NGD_OK;
+}
+
+void ngd_destroy(ngd_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  void* dev[] = {ctx->prep, ctx->prep_t, ctx->J, ctx->tape, ctx->vT, ctx->r, ctx->svec, ctx->tvec, ctx->part,
+                 ctx->lpart, ctx->colpart, ctx->scal, ctx->status, ctx->pcg, ctx->x, ctx->rr, ctx->z, ctx->pv, ctx->q,
+                 ctx->g, ctx->d, ctx->theta_trial, ctx->Om, ctx->Y, ctx->B, ctx->U, ctx->Lr, ctx->VsT, ctx->Zw, ctx->M,
+                 ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
+                 ctx->perm, ctx->jac_cnt, ctx->jac_info};
+  for (void* pp : dev)
+    if (pp) cudaFree(pp);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  if (ctx->h_int) cudaFreeHost(ctx->h_int);
+  if (ctx->h_pcg) cudaFreeHost(ctx->h_pcg);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->tc) tc_destroy(ctx->tc);
+  delete ctx;
+}
+
+uint64_t ngd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* ngd_last_error(const ngd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+int64_t ngd_num_params(const ngd_ctx* ctx) { return ctx ? ctx->p : -1; }
+int64_t ngd_num_points(const ngd_ctx* ctx) { return ctx ? ctx->N : -1; }
+
+ngd_status ngd_set_stream(ngd_ctx* ctx, void* stream) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return NGD_OK;
+}
+
+ngd_status ngd_residual(ngd_ctx* ctx, const double* theta, double* r, double* loss) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!theta) return set_err(ctx, NGD_ERR_INVALID_ARG, "theta is NULL%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    TRY(prep_theta<T>(ctx, theta));
+    T* tape = ctx->tape_allowed ? (T*)ctx->tape : nullptr;
+    const int nb = launch_forward<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, r ? r : ctx->r, ctx->lpart,
+                                     tape, 0, ctx->stream);
+    if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the forward kernel%s");
+    launch_sum_partials(ctx->lpart, nb, 0.5, ctx->scal + kSLoss, ctx->stream);
+    ctx->tape_valid = tape != nullptr;
+    ctx->lin_valid = !ctx->stored_j;
+    TRY(check_launch(ctx));
+    if (loss) {
+      CK(cudaMemcpyAsync(ctx->h_scal + kSLoss, ctx->scal + kSLoss, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      *loss = ctx->h_scal[kSLoss];
+    }
+    return NGD_OK;
+  });
+}
+
+ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* out) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!v || !out) return set_err(ctx, NGD_ERR_INVALID_ARG, "v/out is NULL%s");
+  if (!theta && !ctx->prep_valid)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "theta is NULL and the context holds no parameters%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) {
+      TRY(prep_theta<T>(ctx, theta));
+      ctx->lin_valid = !ctx->stored_j;
+    }
+    launch_prep_weights<T>(ctx->net, v, (T*)ctx->prep_t, ctx->stream);
+    if (launch_jvp<T>(ctx->net, ctx->ps, (const T*)ctx->prep, (const T*)ctx->prep_t, out, 0, ctx->stream) <= 0)
+      return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the JVP kernel%s");
+    return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_vjp(ngd_ctx* ctx, const double* theta, const double* cot, double* out) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!cot || !out) return set_err(ctx, NGD_ERR_INVALID_ARG, "cot/out is NULL%s");
+  if (!theta && !ctx->prep_valid)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "theta is NULL and the context holds no parameters%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) {
+      TRY(prep_theta<T>(ctx, theta));
+      ctx->lin_valid = !ctx->stored_j;
+    }
+    // stored J serves only when nothing newer (theta, tape) was prepared since it was formed
+    return vjp_current<T>(ctx, cot, out, theta == nullptr && !ctx->tape_valid);
+  });
+}
+
+ngd_status ngd_gradient(ngd_ctx* ctx, const double* theta, double* g, double* r, double* loss) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!theta || !g) return set_err(ctx, NGD_ERR_INVALID_ARG, "theta/g is NULL%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    TRY(linearize<T>(ctx, theta));
+    launch_mul(ctx->ps.w, ctx->r, ctx->svec, ctx->N, ctx->stream);
+    TRY(vjp_current<T>(ctx, ctx->svec, g, true));
+    if (r) CK(cudaMemcpyAsync(r, ctx->r, ctx->N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (loss) {
+      CK(cudaMemcpyAsync(ctx->h_scal + kSLoss, ctx->scal + kSLoss, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      *loss = ctx->h_scal[kSLoss];
+    }
+    return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, double mu, double* y) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!v || !y || v == y) return set_err(ctx, NGD_ERR_INVALID_ARG, "v/y NULL or aliased%s");
+  if (!(mu >= 0.0)) return set_err(ctx, NGD_ERR_INVALID_ARG, "mu must be >= 0%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    return gv_current<T>(ctx, v, mu, nullptr, y, nullptr);
+  });
+}
+
+static bool valid_prec(int prec) { return prec >= NGD_SKETCH_F64 && prec <= NGD_SKETCH_BF16; }
+
+ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step, int prec,
+                              void* Omega, void* Y) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!Omega || !Y) return set_err(ctx, NGD_ERR_INVALID_ARG, "Omega/Y is NULL%s");
+  if (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048)) return set_err(ctx, NGD_ERR_INVALID_ARG, "ell out of range%s");
+  if (!valid_prec(prec)) return set_err(ctx, NGD_ERR_INVALID_ARG, "bad sketch precision%s");
+  if (ctx->dtype == NGD_F64 && prec != NGD_SKETCH_F64)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
+  if (ctx->dtype == NGD_F32 && prec == NGD_SKETCH_F64)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F32 context has no F64 sketch%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    TRY(sketch_internal<T>(ctx, ell, seed, step, prec));
+    TRY(sync_status(ctx));
+    const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
+    CK(cudaMemcpy2DAsync(Omega, w, ctx->Om, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpy2DAsync(Y, w, ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const void* Y, int prec, double shift_scale,
+                              void* U, double* lam, double* nu_out) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!Omega || !Y || !U || !lam) return set_err(ctx, NGD_ERR_INVALID_ARG, "NULL argument%s");
+  if (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048)) return set_err(ctx, NGD_ERR_INVALID_ARG, "ell out of range%s");
+  if (!valid_prec(prec) || !(shift_scale > 0.0)) return set_err(ctx, NGD_ERR_INVALID_ARG, "bad precision/shift%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    TRY(ensure_ell(ctx, ell));
+    const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
+    CK(cudaMemcpy2DAsync(ctx->Om, sp, Omega, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpy2DAsync(ctx->Y, sp, Y, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    TRY(factor_internal<T>(ctx, ell, prec, shift_scale));
+    CK(cudaMemcpy2DAsync(U, w, ctx->U, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(lam, ctx->lam, ell * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (nu_out) {
+      CK(cudaMemcpyAsync(ctx->h_scal + kSNu, ctx->scal + kSNu, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      *nu_out = ctx->h_scal[kSNu];
+    }
+    return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, const double* lam, double mu, const double* v,
+                             double* zout) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!U || !lam || !v || !zout || v == zout) return set_err(ctx, NGD_ERR_INVALID_ARG, "NULL or aliased argument%s");
+  if (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048) || !(mu >= 0.0))
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "ell/mu out of range%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    TRY(ensure_ell(ctx, ell));
+    launch_precond<T>((const T*)U, ctx->p, ctx->p, ell, lam, mu, nullptr, v, zout, ctx->w1, nullptr, ctx->stream);
+    return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, double mu, const void* U,
+                         const double* lam, int ell, double rtol, int maxit, double* dout, int* iters, double* relres) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!g || !dout || dout == g) return set_err(ctx, NGD_ERR_INVALID_ARG, "g/d NULL or aliased%s");
+  if (!(mu > 0.0) || !(rtol >= 0.0) || maxit < 0) return set_err(ctx, NGD_ERR_INVALID_ARG, "mu/rtol/maxit%s");
+  if (U && (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048) || !lam))
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "ell/lam%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    if (U) TRY(ensure_ell(ctx, ell));
+    return pcg_internal<T>(ctx, g, mu, nullptr, U, ctx->p, lam, U ? ell : 0, rtol, maxit, dout, iters, relres);
+  });
+}
+
+ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_step_info* info) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!theta || !o) return set_err(ctx, NGD_ERR_INVALID_ARG, "theta/opts NULL%s");
+  if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
+      !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
+  if ((ctx->dtype == NGD_F64) != (o->sketch == NGD_SKETCH_F64))
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "sketch precision does not match the context dtype%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    return step_impl<T>(ctx, theta, o, info);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,1164 @@
+// Dense kernels of the NGD hot path: deterministic reductions, the stored-Jacobian
+// Gramian matvec, preconditioned-CG vector updates, the Nystrom preconditioner, the
+// Philox Gaussian test matrix, a tiled SIMT GEMM (FP64 / FP32 with FP64 cross-tile
+// sums), the row-wise triangular solve and the FP64 l x l core (blocked Cholesky,
+// cyclic Jacobi eigen-solver).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "linalg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ngd {
+
+template <typename T> __device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = wsum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  }
+  return s;  // valid in thread 0
+}
+
+// "Last block finishes" reduction: each block stores its partial; the block that
+// arrives last sums all partials in block order (deterministic) and returns true in
+// thread 0 with the total in *total.
+__device__ __forceinline__ bool last_block_total(double mine, double* part, unsigned int* counter, double* total) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = mine;
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    double s = 0.0;
+    volatile double* vp = part;
+    for (unsigned int b = 0; b < gridDim.x; ++b) s += vp[b];
+    *total = s;
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+// ---------------------------------------------------------------------------- reductions
+__global__ void k_sum_partials(const double* __restrict__ part, int n, double scale, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  // fixed assignment of partials to threads, fixed tree: deterministic
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s * scale;
+}
+
+void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 256, 0, s>>>(part, n, scale, out); note_launch();
+}
+
+// ---------------------------------------------------------------------------- conversions
+template <typename T>
+__global__ void k_d2t(const double* __restrict__ x, T* __restrict__ y, int64_t n, int64_t npad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += stride)
+    y[i] = i < n ? (T)x[i] : T(0);
+}
+
+template <typename T>
+void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((npad + 255) / 256, 2048);
+  k_d2t<T><<<blocks, 256, 0, s>>>(x, y, n, npad); note_launch();
+}
+template void launch_d2t<float>(const double*, float*, int64_t, int64_t, cudaStream_t);
+template void launch_d2t<double>(const double*, double*, int64_t, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------- stored-J matvec
+// t[n] = sum_j J[n, j] v[j] (v already in the working dtype, zero-padded to ldJ),
+// s[n] = w[n] t[n].  One warp per row, 16-byte vector loads.
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ T vdot(const typename Vec<T>::type& a, const typename Vec<T>::type& b);
+template <> __device__ __forceinline__ float vdot<float>(const float4& a, const float4& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+template <> __device__ __forceinline__ double vdot<double>(const double2& a, const double2& b) {
+  return a.x * b.x + a.y * b.y;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowdot(const T* __restrict__ J, int64_t ldJ, int64_t nrows,
+                                                const T* __restrict__ v, const double* __restrict__ w,
+                                                double* __restrict__ t_out, double* __restrict__ s_out,
+                                                const int* __restrict__ done) {
+  if (done && *done) return;
+  using V = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nv = ldJ / VN;
+  const V* __restrict__ vv = reinterpret_cast<const V*>(v);
+  for (int64_t row = warp; row < nrows; row += nwarps) {
+    const V* __restrict__ jr = reinterpret_cast<const V*>(J + row * ldJ);
+    T a0 = T(0), a1 = T(0);
+    int64_t k = lane;
+    for (; k + 32 < nv; k += 64) {
+      a0 += vdot<T>(jr[k], vv[k]);
+      a1 += vdot<T>(jr[k + 32], vv[k + 32]);
+    }
+    if (k < nv) a0 += vdot<T>(jr[k], vv[k]);
+    const double tsum = (double)wsum(a0 + a1);
+    if (lane == 0) {
+      if (t_out) t_out[row] = tsum;
+      if (s_out) s_out[row] = w ? w[row] * tsum : tsum;
+    }
+  }
+}
+
+template <typename T>
+void launch_rowdot(const T* J, int64_t ldJ, int64_t nrows, const T* v, const double* w, double* t_out,
+                   double* s_out, const int* done, cudaStream_t s) {
+  const int64_t warps = nrows;
+  const int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 152 * 16);
+  k_rowdot<T><<<blocks, 256, 0, s>>>(J, ldJ, nrows, v, w, t_out, s_out, done); note_launch();
+}
+template void launch_rowdot<float>(const float*, int64_t, int64_t, const float*, const double*, double*, double*,
+                                   const int*, cudaStream_t);
+template void launch_rowdot<double>(const double*, int64_t, int64_t, const double*, const double*, double*,
+                                    double*, const int*, cudaStream_t);
+
+// part[split][j] = sum_{rows of split} J[n, j] s[n]; each thread owns VN consecutive columns.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coldot(const T* __restrict__ J, int64_t ldJ, int64_t nrows,
+                                                const double* __restrict__ s, double* __restrict__ part,
+                                                int64_t rows_per_split, const int* __restrict__ done) {
+  if (done && *done) return;
+  using V = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN;
+  if (col >= ldJ) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r1 = min(nrows, r0 + rows_per_split);
+  T acc[VN];
+#pragma unroll
+  for (int e = 0; e < VN; ++e) acc[e] = T(0);
+  for (int64_t n = r0; n < r1; ++n) {
+    const T sn = (T)s[n];
+    const V jv = *reinterpret_cast<const V*>(J + n * ldJ + col);
+    const T* je = reinterpret_cast<const T*>(&jv);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) acc[e] += je[e] * sn;
+  }
+  double* pp = part + (int64_t)blockIdx.y * ldJ + col;
+#pragma unroll
+  for (int e = 0; e < VN; ++e) pp[e] = (double)acc[e];
+}
+
+int coldot_nsplit(int64_t nrows, int64_t ldJ, int vn) {
+  const int64_t colblocks = (ldJ / vn + 255) / 256;
+  int64_t ns = std::max<int64_t>(1, 1216 / std::max<int64_t>(colblocks, 1));
+  ns = std::min<int64_t>(ns, std::max<int64_t>(1, nrows / 16));
+  return (int)std::min<int64_t>(ns, 1024);
+}
+
+template <typename T>
+void launch_coldot(const T* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
+                   const int* done, cudaStream_t st) {
+  constexpr int VN = Vec<T>::n;
+  const int64_t rps = (nrows + nsplit - 1) / nsplit;
+  dim3 grid((unsigned)((ldJ / VN + 255) / 256), (unsigned)nsplit);
+  k_coldot<T><<<grid, 256, 0, st>>>(J, ldJ, nrows, s_vec, part, rps, done); note_launch();
+}
+template void launch_coldot<float>(const float*, int64_t, int64_t, const double*, double*, int, const int*,
+                                   cudaStream_t);
+template void launch_coldot<double>(const double*, int64_t, int64_t, const double*, double*, int, const int*,
+                                    cudaStream_t);
+
+// y[j] = (accumulate ? y[j] : 0) + sum_split part[split][j] + mu v[j]   (mu from device or host)
+__global__ void k_coldot_finish(const double* __restrict__ part, int nsplit, int64_t p, int64_t ld_part,
+                                const double* __restrict__ v, double mu_h, const double* __restrict__ mu_d,
+                                double* __restrict__ y, int accumulate, const int* __restrict__ done) {
+  if (done && *done) return;
+  const double mu = mu_d ? *mu_d : mu_h;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += stride) {
+    double s = accumulate ? y[j] : 0.0;
+    for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * ld_part + j];
+    if (v) s += mu * v[j];
+    y[j] = s;
+  }
+}
+
+void launch_coldot_finish(const double* part, int nsplit, int64_t p, int64_t ld_part, const double* v, double mu_h,
+                          const double* mu_d, double* y, int accumulate, const int* done, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((p + 255) / 256, 1024);
+  k_coldot_finish<<<blocks, 256, 0, s>>>(part, nsplit, p, ld_part, v, mu_h, mu_d, y, accumulate, done); note_launch();
+}
+
+// ---------------------------------------------------------------------------- vectors / PCG
+__global__ void k_pcg_init(const double* __restrict__ g, double* __restrict__ x, double* __restrict__ r, int64_t n,
+                           double* part, PcgScalars* sc) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double gi = g[i];
+    x[i] = 0.0;
+    r[i] = gi;
+    acc += gi * gi;
+  }
+  acc = block_sum(acc, red);
+  double tot;
+  if (last_block_total(acc, part, &sc->counter, &tot)) {
+    sc->gn2 = tot;
+    sc->cur_iter = 0;
+    sc->iters = 0;
+    sc->rn2 = tot;
+    sc->done = (tot == 0.0 || sc->maxit <= 0) ? 1 : 0;
+    if (!isfinite(tot)) {
+      sc->status |= kStatNonFinite;
+      sc->done = 1;
+    }
+  }
+}
+
+// p = z, rz = r . z
+__global__ void k_pcg_first_dir(const double* __restrict__ r, const double* __restrict__ z, double* __restrict__ pv,
+                                int64_t n, double* part, PcgScalars* sc) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double zi = z[i];
+    pv[i] = zi;
+    acc += r[i] * zi;
+  }
+  acc = block_sum(acc, red);
+  double tot;
+  if (last_block_total(acc, part, &sc->counter, &tot)) sc->rz = tot;
+}
+
+// alpha = rz / (p . q)
+__global__ void k_pcg_alpha(const double* __restrict__ pv, const double* __restrict__ q, int64_t n, double* part,
+                            PcgScalars* sc) {
+  if (sc->done) return;
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc += pv[i] * q[i];
+  acc = block_sum(acc, red);
+  double tot;
+  if (last_block_total(acc, part, &sc->counter, &tot)) {
+    sc->pq = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      sc->status |= isfinite(tot) ? kStatBreakdown : kStatNonFinite;
+      sc->done = 1;
+      sc->iters = sc->cur_iter;
+    } else {
+      sc->alpha = sc->rz / tot;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, ||r||^2, convergence test
+__global__ void k_pcg_update_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ pv,
+                                const double* __restrict__ q, int64_t n, double* part, PcgScalars* sc) {
+  if (sc->done) return;
+  __shared__ double red[32];
+  const double alpha = sc->alpha;
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    x[i] += alpha * pv[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  acc = block_sum(acc, red);
+  double tot;
+  if (last_block_total(acc, part, &sc->counter, &tot)) {
+    const int it = sc->cur_iter + 1;
+    sc->cur_iter = it;
+    sc->iters = it;
+    sc->rn2 = tot;
+    if (!isfinite(tot)) {
+      sc->status |= kStatNonFinite;
+      sc->done = 1;
+    } else if (tot <= sc->rtol2 * sc->gn2 || it >= sc->maxit) {
+      sc->done = 1;
+    }
+  }
+}
+
+// rz_new = r . z, beta = rz_new / rz
+__global__ void k_pcg_beta(const double* __restrict__ r, const double* __restrict__ z, int64_t n, double* part,
+                           PcgScalars* sc) {
+  if (sc->done) return;
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc += r[i] * z[i];
+  acc = block_sum(acc, red);
+  double tot;
+  if (last_block_total(acc, part, &sc->counter, &tot)) {
+    sc->beta = tot / sc->rz;
+    sc->rz = tot;
+  }
+}
+
+// p = z + beta p
+__global__ void k_pcg_update_p(double* __restrict__ pv, const double* __restrict__ z, int64_t n, PcgScalars* sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) pv[i] = z[i] + beta * pv[i];
+}
+
+static int vec_blocks(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, kRedBlocks); }
+
+void launch_pcg_init(const double* g, double* x, double* r, int64_t n, double* part, PcgScalars* sc,
+                     cudaStream_t s) {
+  k_pcg_init<<<vec_blocks(n), 256, 0, s>>>(g, x, r, n, part, sc); note_launch();
+}
+void launch_pcg_first_dir(const double* r, const double* z, double* pv, int64_t n, double* part, PcgScalars* sc,
+                          cudaStream_t s) {
+  k_pcg_first_dir<<<vec_blocks(n), 256, 0, s>>>(r, z, pv, n, part, sc); note_launch();
+}
+void launch_pcg_alpha(const double* pv, const double* q, int64_t n, double* part, PcgScalars* sc, cudaStream_t s) {
+  k_pcg_alpha<<<vec_blocks(n), 256, 0, s>>>(pv, q, n, part, sc); note_launch();
+}
+void launch_pcg_update_xr(double* x, double* r, const double* pv, const double* q, int64_t n, double* part,
+                          PcgScalars* sc, cudaStream_t s) {
+  k_pcg_update_xr<<<vec_blocks(n), 256, 0, s>>>(x, r, pv, q, n, part, sc); note_launch();
+}
+void launch_pcg_beta(const double* r, const double* z, int64_t n, double* part, PcgScalars* sc, cudaStream_t s) {
+  k_pcg_beta<<<vec_blocks(n), 256, 0, s>>>(r, z, n, part, sc); note_launch();
+}
+void launch_pcg_update_p(double* pv, const double* z, int64_t n, PcgScalars* sc, cudaStream_t s) {
+  k_pcg_update_p<<<vec_blocks(n), 256, 0, s>>>(pv, z, n, sc); note_launch();
+}
+
+// y = x - alpha d  (Armijo trial point / final update)
+__global__ void k_axpy_to(const double* __restrict__ x, const double* __restrict__ d, double alpha,
+                          double* __restrict__ y, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = x[i] - alpha * d[i];
+}
+void launch_axpy_to(const double* x, const double* d, double alpha, double* y, int64_t n, cudaStream_t s) {
+  k_axpy_to<<<vec_blocks(n), 256, 0, s>>>(x, d, alpha, y, n); note_launch();
+}
+
+// dot product into *out (deterministic, two kernels: partials then ordered sum)
+__global__ void k_dot_part(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc += a[i] * b[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t s) {
+  const int nb = vec_blocks(n);
+  k_dot_part<<<nb, 256, 0, s>>>(a, b, n, part); note_launch();
+  launch_sum_partials(part, nb, 1.0, out, s);
+}
+
+// ---------------------------------------------------------------------------- Nystrom preconditioner
+// The scaled preconditioner maps the leading eigen-directions to (lam_ell + mu) / (lam_i + mu),
+// which is ~ mu / lam_1 (1e-8 for the 5-D Poisson workload) and far below the FP32 unit
+// roundoff, so its apply must be accurate to well below that: with FP32 arithmetic the computed
+// P^{-1} v carries noise of ~1e-7 |v| and CG stalls.  FP32-stored U (float) is therefore applied
+// with double-float (FP32 pair) accumulation: each FP32 product is split exactly with fmaf and
+// summed by TwoSum (Knuth), which keeps ~2^-44 relative accuracy on the FP32 pipes instead of the
+// scarce FP64 units.  FP64 U (double) uses FP64 arithmetic.
+struct DF {  // unevaluated sum hi + lo
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float pe = fmaf(a, bh, -p);      // exact error of the product
+  const float t = s.hi + p;              // TwoSum(s.hi, p)
+  const float z = t - s.hi;
+  const float e = (s.hi - (t - z)) + (p - z);
+  s.hi = t;
+  s.lo += e + pe + a * bl;
+}
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// w1[j] = sum_i U[i, j] v[i], four columns per block.
+__global__ void __launch_bounds__(256) k_utv_f(const float* __restrict__ U, int64_t ld, int64_t p, int ell,
+                                               const double* __restrict__ v, double* __restrict__ w1,
+                                               const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double red[4][32];
+  const int j0 = blockIdx.x * 4;
+  DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+    float vh, vl;
+    split_df(v[i], vh, vl);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (j0 + c < ell) df_add_prod(acc[c], U[i + (int64_t)(j0 + c) * ld], vh, vl);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double sv = wsum((double)acc[c].hi + (double)acc[c].lo);
+    if (lane == 0) red[c][warp] = sv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && j0 + (int)threadIdx.x < ell) {
+    double sv = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sv += red[threadIdx.x][w];
+    w1[j0 + threadIdx.x] = sv;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_utv_d(const double* __restrict__ U, int64_t ld, int64_t p, int ell,
+                                               const double* __restrict__ v, double* __restrict__ w1,
+                                               const int* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double red[4][32];
+  const int j0 = blockIdx.x * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+    const double vi = v[i];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (j0 + c < ell) acc[c] += U[i + (int64_t)(j0 + c) * ld] * vi;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double sv = wsum(acc[c]);
+    if (lane == 0) red[c][warp] = sv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && j0 + (int)threadIdx.x < ell) {
+    double sv = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sv += red[threadIdx.x][w];
+    w1[j0 + threadIdx.x] = sv;
+  }
+}
+
+// z[i] = v[i] + sum_j U[i, j] w2[j],  w2[j] = ((lam_ell + mu) / (lam_j + mu) - 1) w1[j]
+__global__ void __launch_bounds__(256) k_precond_apply_f(const float* __restrict__ U, int64_t ld, int64_t p, int ell,
+                                                         const double* __restrict__ lam, double mu_h,
+                                                         const double* __restrict__ mu_d,
+                                                         const double* __restrict__ w1, const double* __restrict__ v,
+                                                         double* __restrict__ z, const int* __restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* w2 = reinterpret_cast<float2*>(smem_raw);
+  const double mu = mu_d ? *mu_d : mu_h;
+  const double ln = lam[ell - 1] + mu;
+  for (int j = threadIdx.x; j < ell; j += blockDim.x) {
+    float h, l;
+    split_df((ln / (lam[j] + mu) - 1.0) * w1[j], h, l);
+    w2[j] = make_float2(h, l);
+  }
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += stride) {
+    DF acc = {0.f, 0.f};
+    for (int j = 0; j < ell; ++j) {
+      const float2 ww = w2[j];
+      df_add_prod(acc, U[i + (int64_t)j * ld], ww.x, ww.y);
+    }
+    z[i] = v[i] + ((double)acc.hi + (double)acc.lo);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_precond_apply_d(const double* __restrict__ U, int64_t ld, int64_t p, int ell,
+                                                         const double* __restrict__ lam, double mu_h,
+                                                         const double* __restrict__ mu_d,
+                                                         const double* __restrict__ w1, const double* __restrict__ v,
+                                                         double* __restrict__ z, const int* __restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* w2 = reinterpret_cast<double*>(smem_raw);
+  const double mu = mu_d ? *mu_d : mu_h;
+  const double ln = lam[ell - 1] + mu;
+  for (int j = threadIdx.x; j < ell; j += blockDim.x) w2[j] = (ln / (lam[j] + mu) - 1.0) * w1[j];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += stride) {
+    double a0 = 0.0, a1 = 0.0;
+    int j = 0;
+    for (; j + 1 < ell; j += 2) {
+      a0 += U[i + (int64_t)j * ld] * w2[j];
+      a1 += U[i + (int64_t)(j + 1) * ld] * w2[j + 1];
+    }
+    if (j < ell) a0 += U[i + (int64_t)j * ld] * w2[j];
+    z[i] = v[i] + (a0 + a1);
+  }
+}
+
+template <typename T>
+void launch_precond(const T* U, int64_t ld, int64_t p, int ell, const double* lam, double mu_h, const double* mu_d,
+                    const double* v, double* z, double* w1, const int* done, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((p + 255) / 256, 2048);
+  if (sizeof(T) == 4) {
+    k_utv_f<<<(ell + 3) / 4, 256, 0, s>>>((const float*)U, ld, p, ell, v, w1, done); note_launch();
+    k_precond_apply_f<<<blocks, 256, ell * sizeof(float2), s>>>((const float*)U, ld, p, ell, lam, mu_h, mu_d, w1, v,
+                                                                  z, done); note_launch();
+  } else {
+    k_utv_d<<<(ell + 3) / 4, 256, 0, s>>>((const double*)U, ld, p, ell, v, w1, done); note_launch();
+    k_precond_apply_d<<<blocks, 256, ell * sizeof(double), s>>>((const double*)U, ld, p, ell, lam, mu_h, mu_d, w1, v,
+                                                                   z, done); note_launch();
+  }
+}
+template void launch_precond<float>(const float*, int64_t, int64_t, int, const double*, double, const double*,
+                                    const double*, double*, double*, const int*, cudaStream_t);
+template void launch_precond<double>(const double*, int64_t, int64_t, int, const double*, double, const double*,
+                                     const double*, double*, double*, const int*, cudaStream_t);
+
+// ---------------------------------------------------------------------------- Philox test matrix
+// Philox4x32-10 (Salmon et al., SC'11): round (c0..c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2),
+// hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); key += (W0, W1) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ double uniform52(uint32_t a, uint32_t b) {
+  const uint64_t m = ((((uint64_t)a) << 20) ^ (uint64_t)(b >> 12)) & ((1ull << 52) - 1ull);
+  return ((double)m + 0.5) * 0x1p-52;
+}
+
+// Omega[i + j*ld] for i < p (rows 2m, 2m+1 from counter (m, j, step_lo, step_hi), key (seed_lo, seed_hi)).
+template <typename T>
+__global__ void k_philox_omega(T* __restrict__ Om, int64_t ld, int64_t p, int ell, uint64_t seed, uint64_t step) {
+  const int64_t npairs = (p + 1) / 2;
+  const int64_t total = npairs * ell;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int j = (int)(t / npairs);
+    const int64_t m = t - (int64_t)j * npairs;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)j, (uint32_t)step, (uint32_t)(step >> 32)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u1 = uniform52(x.x, x.y), u2 = uniform52(x.z, x.w);
+    const double rr = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    T* col = Om + (int64_t)j * ld;
+    col[2 * m] = (T)(rr * cs);
+    if (2 * m + 1 < p) col[2 * m + 1] = (T)(rr * sn);
+  }
+}
+
+template <typename T>
+void launch_philox_omega(T* Om, int64_t ld, int64_t p, int ell, uint64_t seed, uint64_t step, cudaStream_t s) {
+  const int64_t total = (p + 1) / 2 * ell;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
+  k_philox_omega<T><<<blocks, 256, 0, s>>>(Om, ld, p, ell, seed, step); note_launch();
+}
+template void launch_philox_omega<float>(float*, int64_t, int64_t, int, uint64_t, uint64_t, cudaStream_t);
+template void launch_philox_omega<double>(double*, int64_t, int64_t, int, uint64_t, uint64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------- SIMT GEMM
+// C(m, n) = sum_k A(m, k) B(k, n) with element strides; A(m,k) = A[m*sam + k*sak],
+// B(k,n) = B[k*sbk + n*sbn].  64x64 tiles, 16-deep K slices, 4x4 per thread.
+// FP32 products are summed in FP32 over 128-deep chunks and then in FP64.
+// Output: out64 (double, partial per blockIdx.z at out64 + z*split_stride) or outT.
+// Epilogue scales: rowscale[m] (double, nullable), colscale[n] (double, nullable).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, const T* __restrict__ A, int64_t sam,
+                                              int64_t sak, const T* __restrict__ B, int64_t sbk, int64_t sbn,
+                                              int64_t k_per_split, double* __restrict__ out64, int64_t split_stride,
+                                              T* __restrict__ outT, int64_t scm, int64_t scn,
+                                              const double* __restrict__ rowscale,
+                                              const double* __restrict__ colscale, int accumulate) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kb = (int64_t)blockIdx.z * k_per_split;
+  const int64_t ke = min(K, kb + k_per_split);
+  T acc[4][4];
+  double acc64[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[a][b] = T(0);
+      acc64[a][b] = 0.0;
+    }
+  int slice = 0;
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    // load A tile (BM x BK) and B tile (BK x BN): unit-stride dimension on consecutive threads
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int mm, kk;
+      if (sak == 1) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < ke) ? A[gm * sam + gk * sak] : T(0);
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      int kk, nn;
+      if (sbk == 1) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gn < N && gk < ke) ? B[gk * sbk + gn * sbn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[kk][ty + 16 * i];
+        b[i] = Bs[kk][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+    if (sizeof(T) == 4 && (++slice & 7) == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc64[i][j] += (double)acc[i][j];
+          acc[i][j] = T(0);
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+    const double rs = rowscale ? rowscale[gm] : 1.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double v = (acc64[i][j] + (double)acc[i][j]) * rs;
+      if (colscale) v *= colscale[gn];
+      if (out64) {
+        double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
+        *o = accumulate ? *o + v : v;
+      } else
+        outT[gm * scm + gn * scn] = (T)v;
+    }
+  }
+}
+
+template <typename T>
+void launch_gemm(const GemmArgs<T>& g, cudaStream_t s) {
+  const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : std::max<int64_t>(g.K, 1);
+  const int nz = (int)((g.K + kps - 1) / kps);
+  dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)std::max(nz, 1));
+  k_gemm<T><<<grid, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.sam, g.sak, g.B, g.sbk, g.sbn, kps, g.out64, g.split_stride,
+                                 g.outT, g.scm, g.scn, g.rowscale, g.colscale, g.accumulate); note_launch();
+}
+template void launch_gemm<float>(const GemmArgs<float>&, cudaStream_t);
+template void launch_gemm<double>(const GemmArgs<double>&, cudaStream_t);
+
+int gemm_splits(const GemmArgs<float>& g) {  // number of z-slices launch_gemm will use
+  const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : std::max<int64_t>(g.K, 1);
+  return (int)std::max<int64_t>(1, (g.K + kps - 1) / kps);
+}
+
+// out[i] = sum_z part[z*stride + i] for i < n  (ordered, deterministic)
+__global__ void k_sum_splits(const double* __restrict__ part, int nz, int64_t stride, int64_t n,
+                             double* __restrict__ out) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) {
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += part[(int64_t)z * stride + i];
+    out[i] = s;
+  }
+}
+template <typename T>
+__global__ void k_sum_splits_t(const double* __restrict__ part, int nz, int64_t stride, int64_t rows, int64_t cols,
+                               int64_t ldp, T* __restrict__ out, int64_t ldo) {
+  const int64_t n = rows * cols;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += st) {
+    const int64_t c = e / rows, r = e - c * rows;
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += part[(int64_t)z * stride + r + c * ldp];
+    out[r + c * ldo] = (T)s;
+  }
+}
+void launch_sum_splits(const double* part, int nz, int64_t stride, int64_t n, double* out, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_sum_splits<<<blocks, 256, 0, s>>>(part, nz, stride, n, out); note_launch();
+}
+template <typename T>
+void launch_sum_splits_t(const double* part, int nz, int64_t stride, int64_t rows, int64_t cols, int64_t ldp, T* out,
+                         int64_t ldo, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((rows * cols + 255) / 256, 8192);
+  k_sum_splits_t<T><<<blocks, 256, 0, s>>>(part, nz, stride, rows, cols, ldp, out, ldo); note_launch();
+}
+template void launch_sum_splits_t<float>(const double*, int, int64_t, int64_t, int64_t, int64_t, float*, int64_t,
+                                         cudaStream_t);
+template void launch_sum_splits_t<double>(const double*, int, int64_t, int64_t, int64_t, int64_t, double*, int64_t,
+                                          cudaStream_t);
+
+// ---------------------------------------------------------------------------- small elementwise helpers
+// Y_nu = Y + nu Omega with nu = scale * max(eps(||Y||_F), u_in ||Y||_F) computed on the device
+// from frob2 = ||Y||_F^2; stores nu in *nu_out.
+__device__ __forceinline__ double spacing_of(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return 0.0;
+  int e;
+  frexp(x, &e);  // x = m 2^e, m in [0.5, 1)
+  return ldexp(1.0, e - 53);
+}
+__global__ void k_compute_nu(const double* frob2, double u_in, double scale, double* nu_out) {
+  const double n = sqrt(*frob2);
+  *nu_out = scale * fmax(spacing_of(n), u_in * n);
+}
+void launch_compute_nu(const double* frob2, double u_in, double scale, double* nu_out, cudaStream_t s) {
+  k_compute_nu<<<1, 1, 0, s>>>(frob2, u_in, scale, nu_out); note_launch();
+}
+
+template <typename T>
+__global__ void k_frob2_part(const T* __restrict__ Y, int64_t ld, int64_t p, int ell, double* part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t n = p * ell;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int64_t j = e / p, i = e - j * p;
+    const double v = (double)Y[i + j * ld];
+    acc += v * v;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+template <typename T>
+void launch_frob2(const T* Y, int64_t ld, int64_t p, int ell, double* part, double* out, cudaStream_t s) {
+  const int nb = (int)std::min<int64_t>((p * ell + 255) / 256, kRedBlocks);
+  k_frob2_part<T><<<nb, 256, 0, s>>>(Y, ld, p, ell, part); note_launch();
+  launch_sum_partials(part, nb, 1.0, out, s);
+}
+template void launch_frob2<float>(const float*, int64_t, int64_t, int, double*, double*, cudaStream_t);
+template void launch_frob2<double>(const double*, int64_t, int64_t, int, double*, double*, cudaStream_t);
+
+// dst = src + nu * Om  (p x ell, column-major, same ld; padding rows zero)
+template <typename T>
+__global__ void k_shift_add(const T* __restrict__ src, const T* __restrict__ Om, const double* __restrict__ nu,
+                            T* __restrict__ dst, int64_t ld, int64_t p, int ell) {
+  const double nv = *nu;
+  const int64_t n = ld * ell;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int64_t i = e % ld;
+    dst[e] = i < p ? (T)((double)src[e] + nv * (double)Om[e]) : T(0);
+  }
+}
+template <typename T>
+void launch_shift_add(const T* src, const T* Om, const double* nu, T* dst, int64_t ld, int64_t p, int ell,
+                      cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((ld * ell + 255) / 256, 8192);
+  k_shift_add<T><<<blocks, 256, 0, s>>>(src, Om, nu, dst, ld, p, ell); note_launch();
+}
+template void launch_shift_add<float>(const float*, const float*, const double*, float*, int64_t, int64_t, int,
+                                      cudaStream_t);
+template void launch_shift_add<double>(const double*, const double*, const double*, double*, int64_t, int64_t, int,
+                                       cudaStream_t);
+
+// M = (M + M^T) / 2 in place (n x n column-major)
+__global__ void k_symmetrize(double* M, int n) {
+  const int64_t total = (int64_t)n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) {
+      const double v = 0.5 * (M[i + (int64_t)j * n] + M[j + (int64_t)i * n]);
+      M[i + (int64_t)j * n] = v;
+      M[j + (int64_t)i * n] = v;
+    }
+  }
+}
+void launch_symmetrize(double* M, int n, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
+  k_symmetrize<<<blocks, 256, 0, s>>>(M, n); note_launch();
+}
+
+// ---------------------------------------------------------------------------- triangular solve
+// X (p x ell, column-major) <- X L^{-T} with L lower (FP64, column-major n x n): row-wise
+// forward substitution x_j = (x_j - sum_{t<j} L[j,t] x_t) / L[j,j].  Lr = L row-major in T,
+// dinv = 1 / diag(L).  RB rows per block, one warp per row, the rows staged in shared memory.
+template <typename T>
+__global__ void k_lower_to_rowmajor(const double* __restrict__ L, int n, T* __restrict__ Lr, double* __restrict__ dinv) {
+  const int64_t total = (int64_t)n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int j = (int)(e / n), t = (int)(e % n);  // Lr[j*n + t] = L[j, t]
+    Lr[e] = t <= j ? (T)L[j + (int64_t)t * n] : T(0);
+    if (t == j) dinv[j] = 1.0 / L[j + (int64_t)j * n];
+  }
+}
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(RB * 32) k_trsm_rows(T* __restrict__ X, int64_t ld, int64_t p, int n,
+                                                      const T* __restrict__ Lr, const double* __restrict__ dinv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);  // [n][RB]
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  const int rows = (int)min((int64_t)RB, p - r0);
+  // coalesced load: for each column t, RB consecutive rows
+  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
+    const int t = e / RB, rr = e - t * RB;
+    xs[e] = rr < rows ? X[r0 + rr + (int64_t)t * ld] : T(0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < rows) {
+    for (int j = 0; j < n; ++j) {
+      const T* lrow = Lr + (int64_t)j * n;
+      T acc = T(0);
+      for (int t = lane; t < j; t += 32) acc += lrow[t] * xs[t * RB + warp];
+      acc = wsum(acc);
+      if (lane == 0) xs[j * RB + warp] = (T)(((double)xs[j * RB + warp] - (double)acc) * dinv[j]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
+    const int t = e / RB, rr = e - t * RB;
+    if (rr < rows) X[r0 + rr + (int64_t)t * ld] = xs[e];
+  }
+}
+
+template <typename T>
+void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* Lr, double* dinv, cudaStream_t s) {
+  const int blocks0 = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
+  k_lower_to_rowmajor<T><<<blocks0, 256, 0, s>>>(L, n, Lr, dinv); note_launch();
+  constexpr int RB = sizeof(T) == 4 ? 16 : 8;
+  const size_t smem = (size_t)n * RB * sizeof(T);
+  auto k = k_trsm_rows<T, RB>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<(unsigned)((p + RB - 1) / RB), RB * 32, smem, s>>>(X, ld, p, n, Lr, dinv); note_launch();
+}
+template void launch_trsm_lt<float>(float*, int64_t, int64_t, int, const double*, float*, double*, cudaStream_t);
+template void launch_trsm_lt<double>(double*, int64_t, int64_t, int, const double*, double*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------- FP64 Cholesky
+// Blocked right-looking Cholesky of the n x n SPD matrix A (column-major, lower triangle
+// used and overwritten by L, A = L L^T), one cooperative launch: per 32-wide panel, block 0
+// factors the diagonal block in shared memory, all blocks solve the panel below it, all
+// blocks update the trailing lower triangle.  A non-positive pivot sets kStatNotSpd.
+__global__ void __launch_bounds__(256) k_cholesky(double* __restrict__ A, int n, int* __restrict__ status) {
+  constexpr int NB = 32;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double D[NB][NB + 1];
+  __shared__ int bad;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int bs = min(NB, n - k0);
+    if (blockIdx.x == 0) {
+      if (threadIdx.x == 0) bad = 0;
+      for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+        const int i = e % bs, j = e / bs;
+        D[i][j] = A[(k0 + i) + (int64_t)(k0 + j) * n];
+      }
+      __syncthreads();
+      for (int j = 0; j < bs; ++j) {
+        if (threadIdx.x == 0) {
+          const double piv = D[j][j];
+          if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
+          D[j][j] = sqrt(fmax(piv, 0.0));
+        }
+        __syncthreads();
+        if (bad) break;
+        const double djj = D[j][j];
+        for (int i = j + 1 + threadIdx.x; i < bs; i += blockDim.x) D[i][j] /= djj;
+        __syncthreads();
+        for (int e = threadIdx.x; e < (bs - j - 1) * (bs - j - 1); e += blockDim.x) {
+          const int i = j + 1 + e % (bs - j - 1), c = j + 1 + e / (bs - j - 1);
+          if (c <= i) D[i][c] -= D[i][j] * D[c][j];
+        }
+        __syncthreads();
+      }
+      if (bad) {
+        if (threadIdx.x == 0) atomicOr(status, kStatNotSpd);
+      } else {
+        for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+          const int i = e % bs, j = e / bs;
+          if (j <= i) A[(k0 + i) + (int64_t)(k0 + j) * n] = D[i][j];
+        }
+      }
+    }
+    grid.sync();
+    if (*((volatile int*)status) & kStatNotSpd) return;
+    // panel solve: rows i >= k0+bs: L[i, k0:k0+bs] = A[i, k0:k0+bs] L_kk^{-T}
+    if (k0 + bs < n) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+        const int i = e % bs, j = e / bs;
+        D[i][j] = A[(k0 + i) + (int64_t)(k0 + j) * n];
+      }
+      __syncthreads();
+      for (int64_t i = k0 + bs + gtid; i < n; i += gthreads) {
+        double x[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) x[j] = j < bs ? A[i + (int64_t)(k0 + j) * n] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (j < bs) {
+            double v = x[j];
+#pragma unroll
+            for (int t = 0; t < NB; ++t)
+              if (t < j) v -= D[j][t] * x[t];
+            x[j] = v / D[j][j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (j < bs) A[i + (int64_t)(k0 + j) * n] = x[j];
+      }
+    }
+    grid.sync();
+    // trailing update of the lower triangle: A[i, c] -= sum_t L[i, k0+t] L[c, k0+t]
+    const int m = n - k0 - bs;
+    if (m > 0) {
+      const int64_t total = (int64_t)m * m;
+      for (int64_t e = gtid; e < total; e += gthreads) {
+        const int64_t i = e % m, c = e / m;
+        if (c > i) continue;
+        const int64_t gi = k0 + bs + i, gc = k0 + bs + c;
+        double s = 0.0;
+        for (int t = 0; t < bs; ++t) s += A[gi + (int64_t)(k0 + t) * n] * A[gc + (int64_t)(k0 + t) * n];
+        A[gi + gc * n] -= s;
+      }
+    }
+    grid.sync();
+  }
+}
+
+static int coop_blocks(const void* kernel, int threads, size_t smem) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  return std::max(1, std::min(per, 2)) * nsm;
+}
+
+cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s) {
+  const int blocks = coop_blocks((const void*)k_cholesky, 256, 0);
+  void* args[] = {&A, &n, &status};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void*)k_cholesky, blocks, 256, args, 0, s);
+}
+
+// ---------------------------------------------------------------------------- FP64 cyclic Jacobi
+// Two-sided cyclic Jacobi on the symmetric n x n matrix in A0 (column-major), parallel
+// (round-robin / circle) ordering: every round rotates n2/2 disjoint pairs (p, q) at once.
+// Each block recomputes the round's rotations (Golub-Van Loan sym. Schur 2x2:
+// tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2),
+// s = t c), then updates its share of the 2x2 blocks A[{p_k,q_k}, {p_k',q_k'}] <- J_k^T A J_k'
+// from the current buffer into the other buffer, and rotates the column pairs of V in place.
+// A pair is skipped when |a_pq| <= tol sqrt(|a_pp a_qq|); the sweeps stop when a whole sweep
+// skips every pair, or after max_sweeps.  Eigenvalues end on the diagonal of the buffer
+// reported in *final_buf (0 or 1).
+__device__ __forceinline__ int rr_index(int pos, int r, int n2) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + r) % (n2 - 1);
+}
+
+__global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double* __restrict__ A1,
+                                                double* __restrict__ V, int n, int max_sweeps, double tol,
+                                                unsigned int* __restrict__ counters, int* __restrict__ final_buf,
+                                                int* __restrict__ sweeps_out) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n2 = n + (n & 1);
+  const int npairs = n2 / 2;
+  double* cs = reinterpret_cast<double*>(smem_raw);  // [npairs] c
+  double* sn = cs + npairs;                          // [npairs] s
+  int* pi = reinterpret_cast<int*>(sn + npairs);     // [npairs] p
+  int* qi = pi + npairs;                             // [npairs] q
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  // V = I
+  for (int64_t e = gtid; e < (int64_t)n * n; e += gthreads) V[e] = (e % n == e / n) ? 1.0 : 0.0;
+  if (gtid == 0) {
+    counters[0] = 0u;
+    counters[1] = 0u;
+  }
+  grid.sync();
+  double* cur = A0;
+  double* nxt = A1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    unsigned int* cnt = counters + (sweep & 1);
+    if (gtid == 0) counters[(sweep + 1) & 1] = 0u;
+    for (int r = 0; r < n2 - 1; ++r) {
+      // rotations of this round (every block computes all of them)
+      for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+        int p = rr_index(k, r, n2), q = rr_index(n2 - 1 - k, r, n2);
+        if (p > q) {
+          const int t = p; p = q; q = t;
+        }
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double app = cur[p + (int64_t)p * n], aqq = cur[q + (int64_t)q * n], apq = cur[p + (int64_t)q * n];
+          if (apq != 0.0 && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            if (blockIdx.x == 0) atomicAdd(cnt, 1u);
+          }
+        }
+        cs[k] = c;
+        sn[k] = s;
+        pi[k] = p;
+        qi[k] = q;
+      }
+      __syncthreads();
+      // 2x2 block updates: block (k, k2) covers rows {p_k, q_k} and columns {p_k2, q_k2}
+      const int64_t nblk = (int64_t)npairs * npairs;
+      for (int64_t e = gtid; e < nblk; e += gthreads) {
+        const int k = (int)(e / npairs), k2 = (int)(e - (int64_t)k * npairs);
+        const int p = pi[k], q = qi[k], p2 = pi[k2], q2 = qi[k2];
+        const bool qok = q < n, q2ok = q2 < n;
+        const double c = cs[k], s = sn[k], c2 = cs[k2], s2 = sn[k2];
+        const double a00 = cur[p + (int64_t)p2 * n];
+        const double a01 = q2ok ? cur[p + (int64_t)q2 * n] : 0.0;
+        const double a10 = qok ? cur[q + (int64_t)p2 * n] : 0.0;
+        const double a11 = (qok && q2ok) ? cur[q + (int64_t)q2 * n] : 0.0;
+        // rows: J_k^T X
+        const double b00 = c * a00 - s * a10, b01 = c * a01 - s * a11;
+        const double b10 = s * a00 + c * a10, b11 = s * a01 + c * a11;
+        // columns: (.) J_k2
+        double y00 = c2 * b00 - s2 * b01, y01 = s2 * b00 + c2 * b01;
+        double y10 = c2 * b10 - s2 * b11, y11 = s2 * b10 + c2 * b11;
+        if (k == k2 && s != 0.0) {
+          y01 = 0.0;
+          y10 = 0.0;
+        }
+        nxt[p + (int64_t)p2 * n] = y00;
+        if (q2ok) nxt[p + (int64_t)q2 * n] = y01;
+        if (qok) nxt[q + (int64_t)p2 * n] = y10;
+        if (qok && q2ok) nxt[q + (int64_t)q2 * n] = y11;
+      }
+      // eigenvector columns: V[:, p], V[:, q]
+      const int64_t nv = (int64_t)npairs * n;
+      for (int64_t e = gtid; e < nv; e += gthreads) {
+        const int k = (int)(e / n), i = (int)(e - (int64_t)k * n);
+        const double s = sn[k];
+        if (s == 0.0) continue;
+        const int p = pi[k], q = qi[k];
+        const double c = cs[k];
+        const double vp = V[i + (int64_t)p * n], vq = V[i + (int64_t)q * n];
+        V[i + (int64_t)p * n] = c * vp - s * vq;
+        V[i + (int64_t)q * n] = s * vp + c * vq;
+      }
+      grid.sync();
+      double* t = cur; cur = nxt; nxt = t;
+    }
+    const unsigned int rotated = *((volatile unsigned int*)cnt);
+    grid.sync();
+    if (rotated == 0u) break;
+  }
+  if (gtid == 0) {
+    *final_buf = (cur == A0) ? 0 : 1;
+    *sweeps_out = sweep;
+  }
+}
+
+cudaError_t launch_jacobi(double* A0, double* A1, double* V, int n, int max_sweeps, double tol,
+                          unsigned int* counters, int* final_buf, int* sweeps, cudaStream_t s) {
+  const int n2 = n + (n & 1);
+  const size_t smem = (size_t)(n2 / 2) * (2 * sizeof(double) + 2 * sizeof(int));
+  cudaFuncSetAttribute((const void*)k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int blocks = coop_blocks((const void*)k_jacobi, 256, smem);
+  void* args[] = {&A0, &A1, &V, &n, &max_sweeps, &tol, &counters, &final_buf, &sweeps};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void*)k_jacobi, blocks, 256, args, smem, s);
+}
+
+// Sort the eigenpairs by decreasing eigenvalue: sig2[rank(j)] = diag(Afin)[j],
+// Vs[:, rank(j)] = V[:, j] (ties broken by index, so the permutation is deterministic).
+__global__ void k_eig_rank(const double* __restrict__ Afin, int n, double* __restrict__ sig2, int* __restrict__ dst) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* ev = reinterpret_cast<double*>(smem_raw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = Afin[i + (int64_t)i * n];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int rank = 0;
+    const double vi = ev[i];
+    for (int j = 0; j < n; ++j) {
+      const double vj = ev[j];
+      rank += (vj > vi) || (vj == vi && j < i);
+    }
+    dst[i] = rank;
+    sig2[rank] = vi;
+  }
+}
+__global__ void k_eig_gather(const double* __restrict__ V, int n, const int* __restrict__ dst, double* __restrict__ Vs) {
+  const int64_t total = (int64_t)n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int src = (int)(e / n), i = (int)(e - (int64_t)src * n);
+    Vs[i + (int64_t)dst[src] * n] = V[e];
+  }
+}
+void launch_eig_sort(const double* Afin, const double* V, int n, double* sig2, double* Vs, int* perm, cudaStream_t s) {
+  const size_t smem = (size_t)n * sizeof(double);
+  k_eig_rank<<<1, 1024, smem, s>>>(Afin, n, sig2, perm); note_launch();
+  const int blocks = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
+  k_eig_gather<<<blocks, 256, 0, s>>>(V, n, perm, Vs); note_launch();
+}
+
+// W = V diag(1/sigma) (column scale), lam = max(0, sigma^2 - nu) and 1/sigma for the U GEMM.
+__global__ void k_nystrom_lambda(const double* __restrict__ sig2, const double* __restrict__ nu, int n,
+                                 double* __restrict__ lam, double* __restrict__ inv_sigma) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double s2 = sig2[j];
+    lam[j] = fmax(0.0, s2 - *nu);
+    inv_sigma[j] = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+  }
+}
+void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* lam, double* inv_sigma,
+                           cudaStream_t s) {
+  k_nystrom_lambda<<<(n + 255) / 256, 256, 0, s>>>(sig2, nu, n, lam, inv_sigma); note_launch();
+}
+
+// mu = gamma * eps64 * lam[0] (Alg. 4), or the fixed value when fixed_mu > 0
+__global__ void k_set_mu(const double* __restrict__ lam, double fixed_mu, double gamma, double* __restrict__ mu) {
+  *mu = fixed_mu > 0.0 ? fixed_mu : gamma * 0x1p-52 * lam[0];
+}
+void launch_set_mu(const double* lam, double fixed_mu, double gamma, double* mu, cudaStream_t s) {
+  k_set_mu<<<1, 1, 0, s>>>(lam, fixed_mu, gamma, mu); note_launch();
+}
+
+}  // namespace ngd

@@ -1,0 +1,86 @@
+// Declarations of the dense kernels in linalg.cu.
+#pragma once
+
+#include "ngd_internal.cuh"
+
+namespace ngd {
+
+constexpr int kRedBlocks = 1024;   // maximum number of per-block partials of one reduction
+
+// Device-resident scalars of one preconditioned-CG solve.
+struct PcgScalars {
+  double rz, pq, alpha, beta, rn2, gn2, rtol2;
+  int done, iters, maxit, status, cur_iter;
+  unsigned int counter;
+};
+
+// Strided SIMT GEMM C(m,n) = sum_k A(m,k) B(k,n) (see k_gemm).
+template <typename T> struct GemmArgs {
+  int64_t M = 0, N = 0, K = 0;
+  const T* A = nullptr; int64_t sam = 0, sak = 0;
+  const T* B = nullptr; int64_t sbk = 0, sbn = 0;
+  int nsplit = 1;                     // K slices (FP64 partial per slice into out64)
+  double* out64 = nullptr; int64_t split_stride = 0;
+  T* outT = nullptr;
+  int64_t scm = 0, scn = 0;
+  const double* rowscale = nullptr;   // per-m factor (nullable)
+  const double* colscale = nullptr;   // per-n factor (nullable)
+  int accumulate = 0;                 // out64 += result instead of out64 = result (nsplit must be 1)
+};
+
+void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);
+template <typename T> void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s);
+
+template <typename T>
+void launch_rowdot(const T* J, int64_t ldJ, int64_t nrows, const T* v, const double* w, double* t_out,
+                   double* s_out, const int* done, cudaStream_t s);
+int coldot_nsplit(int64_t nrows, int64_t ldJ, int vn);
+template <typename T>
+void launch_coldot(const T* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
+                   const int* done, cudaStream_t st);
+void launch_coldot_finish(const double* part, int nsplit, int64_t p, int64_t ld_part, const double* v, double mu_h,
+                          const double* mu_d, double* y, int accumulate, const int* done, cudaStream_t s);
+
+void launch_pcg_init(const double* g, double* x, double* r, int64_t n, double* part, PcgScalars* sc, cudaStream_t s);
+void launch_pcg_first_dir(const double* r, const double* z, double* pv, int64_t n, double* part, PcgScalars* sc,
+                          cudaStream_t s);
+void launch_pcg_alpha(const double* pv, const double* q, int64_t n, double* part, PcgScalars* sc, cudaStream_t s);
+void launch_pcg_update_xr(double* x, double* r, const double* pv, const double* q, int64_t n, double* part,
+                          PcgScalars* sc, cudaStream_t s);
+void launch_pcg_beta(const double* r, const double* z, int64_t n, double* part, PcgScalars* sc, cudaStream_t s);
+void launch_pcg_update_p(double* pv, const double* z, int64_t n, PcgScalars* sc, cudaStream_t s);
+void launch_axpy_to(const double* x, const double* d, double alpha, double* y, int64_t n, cudaStream_t s);
+void launch_dot(const double* a, const double* b, int64_t n, double* part, double* out, cudaStream_t s);
+
+template <typename T>
+void launch_precond(const T* U, int64_t ld, int64_t p, int ell, const double* lam, double mu_h, const double* mu_d,
+                    const double* v, double* z, double* w1, const int* done, cudaStream_t s);
+
+template <typename T>
+void launch_philox_omega(T* Om, int64_t ld, int64_t p, int ell, uint64_t seed, uint64_t step, cudaStream_t s);
+
+template <typename T> void launch_gemm(const GemmArgs<T>& g, cudaStream_t s);
+void launch_sum_splits(const double* part, int nz, int64_t stride, int64_t n, double* out, cudaStream_t s);
+template <typename T>
+void launch_sum_splits_t(const double* part, int nz, int64_t stride, int64_t rows, int64_t cols, int64_t ldp, T* out,
+                         int64_t ldo, cudaStream_t s);
+
+void launch_compute_nu(const double* frob2, double u_in, double scale, double* nu_out, cudaStream_t s);
+template <typename T>
+void launch_frob2(const T* Y, int64_t ld, int64_t p, int ell, double* part, double* out, cudaStream_t s);
+template <typename T>
+void launch_shift_add(const T* src, const T* Om, const double* nu, T* dst, int64_t ld, int64_t p, int ell,
+                      cudaStream_t s);
+void launch_symmetrize(double* M, int n, cudaStream_t s);
+
+template <typename T>
+void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* Lr, double* dinv, cudaStream_t s);
+cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s);
+cudaError_t launch_jacobi(double* A0, double* A1, double* V, int n, int max_sweeps, double tol,
+                          unsigned int* counters, int* final_buf, int* sweeps, cudaStream_t s);
+void launch_eig_sort(const double* Afin, const double* V, int n, double* sig2, double* Vs, int* perm, cudaStream_t s);
+void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* lam, double* inv_sigma,
+                           cudaStream_t s);
+void launch_set_mu(const double* lam, double fixed_mu, double gamma, double* mu, cudaStream_t s);
+
+}  // namespace ngd

@@ -1,0 +1,317 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64 oracle.
+
+Tolerances (relative 2-norm unless noted):
+  FP64 path: residual/gradient/JVP/VJP 1e-11, Gramian matvec 1e-10 (the stated target),
+             preconditioned direction 1e-6 at a fixed iteration count.
+  FP32 path: residual/JVP/VJP 2e-5 (FP32 Taylor recurrences over <= 5 layers), Gramian matvec
+             1e-5 (the stated target), Omega 1e-6.
+  TF32 / BF16 sketch: 5e-3 / 4e-2 (operand rounding 2^-10 / 2^-8, error grows like sqrt(K) u).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import gramian, mlp, nystrom, philox, solve  # noqa: E402
+from paper_2505_11638_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ngd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_11638_gb300 import build
+    build.build()
+    from paper_2505_11638_gb300 import ngd as _ngd
+    _ngd.lib()
+    return _ngd
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+SMALL = [
+    dict(pde="poisson", d=2, widths=[2, 7, 5, 1], n_int=37, n_bnd=11),     # ragged tiles, odd widths
+    dict(pde="poisson", d=3, widths=[3, 16, 16, 16, 1], n_int=50, n_bnd=0),  # interior only
+    dict(pde="poisson", d=2, widths=[2, 8, 1], n_int=0, n_bnd=9),            # boundary only, one hidden layer
+    dict(pde="heat", d=4, widths=[4, 12, 9, 1], n_int=29, n_bnd=13),
+    dict(pde="poisson", d=10, widths=[10, 20, 20, 1], n_int=21, n_bnd=5),    # 12 Taylor channels
+    dict(pde="poisson", d=2, widths=[2, 3, 1], n_int=1, n_bnd=0),            # a single point
+]
+
+
+def small(case, seed=0):
+    c = dict(case)
+    pde = c.pop("pde")
+    return inputs.small_problem(pde=pde, seed=seed, **c)
+
+
+@pytest.mark.parametrize("case", range(len(SMALL)))
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_residual_gradient_jvp_vjp_small(ngd, case, dtype):
+    pr, th = small(SMALL[case], seed=case)
+    ctx = ngd.Context(pr, dtype=dtype)
+    t = dev(th)
+    r, loss = ctx.residual(t)
+    r_o, L_o = mlp.residual(pr, th)
+    tol = 1e-11 if dtype == "f64" else 2e-5
+    assert rel(host(r), r_o) <= tol
+    assert abs(loss - L_o) <= tol * max(abs(L_o), 1e-300)
+    g, r2, loss2 = ctx.gradient(t)
+    g_o = mlp.vjp(pr, th, pr.w * r_o)
+    assert rel(host(g), g_o) <= (1e-11 if dtype == "f64" else 5e-5)
+    rng = np.random.default_rng(case)
+    v = rng.standard_normal(pr.p)
+    c = rng.standard_normal(pr.n)
+    assert rel(host(ctx.jvp(t, dev(v))), mlp.jvp(pr, th, v)) <= tol
+    assert rel(host(ctx.vjp(t, dev(c))), mlp.vjp(pr, th, c)) <= (1e-11 if dtype == "f64" else 5e-5)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", [0, 3, 4])
+@pytest.mark.parametrize("dtype,mode", [("f64", "stored"), ("f64", "matrix_free"), ("f32", "stored"),
+                                        ("f32", "matrix_free")])
+def test_gramian_mv_small(ngd, case, dtype, mode):
+    pr, th = small(SMALL[case], seed=10 + case)
+    ctx = ngd.Context(pr, dtype=dtype, gv_mode=mode)
+    v = np.random.default_rng(1).standard_normal(pr.p)
+    y = host(ctx.gramian_mv(dev(th), dev(v), 1e-3))
+    y_o = gramian.gramian_mv(mlp.jacobian(pr, th), pr.w, v, 1e-3)
+    assert rel(y, y_o) <= (1e-10 if dtype == "f64" else 1e-5)
+    ctx.close()
+
+
+def _workload(name, n_int=None, n_bnd=None):
+    wl, ths = inputs.make_workload(name, seed=0)
+    pr = wl.problems[0]
+    if n_int is not None:
+        pr = inputs.subsample(pr, n_int, n_bnd)
+    return wl, pr, ths[0]
+
+
+@pytest.mark.parametrize("name,dtype", [("poisson2d", "f64"), ("poisson5d", "f32")])
+def test_gramian_mv_full_size(ngd, name, dtype):
+    """The matvec at the full point sets of the two smaller workloads, J formed explicitly by the oracle."""
+    wl, pr, th = _workload(name)
+    ctx = ngd.Context(pr, dtype=dtype)
+    rng = np.random.default_rng(2)
+    J = mlp.jacobian(pr, th)
+    for mu in [wl.mu, 0.0]:
+        v = rng.standard_normal(pr.p)
+        y = host(ctx.gramian_mv(dev(th) if mu == wl.mu else None, dev(v), mu))
+        y_o = gramian.gramian_mv(J, pr.w, v, mu)
+        assert rel(y, y_o) <= (1e-10 if dtype == "f64" else 1e-5), (name, mu)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["poisson10d", "heat4d"])
+def test_large_workloads_sampled(ngd, name):
+    """At the full sizes of the two large workloads: residuals and J rows on sampled points
+    (the oracle evaluates those points one block at a time) and exact identities of the matvec."""
+    wl, pr, th = _workload(name)
+    ctx = ngd.Context(pr, dtype="f32")
+    t = dev(th)
+    r, loss = ctx.residual(t)
+    rows = np.concatenate([np.arange(0, pr.n_int, pr.n_int // 40), pr.n_int + np.arange(0, pr.n_bnd, pr.n_bnd // 10),
+                           [pr.n - 1]])
+    sub = inputs.Problem(pr.name, pr.pde, pr.widths, pr.X[rows], pr.w[rows], pr.target[rows],
+                         int(np.sum(rows < pr.n_int)), int(np.sum(rows >= pr.n_int)), pr.kappa, pr.freq)
+    r_o, _ = mlp.residual(sub, th)
+    assert rel(host(r)[rows], r_o) <= 2e-5
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(pr.p)
+    jv = host(ctx.jvp(t, dev(v)))
+    assert rel(jv[rows], mlp.jacobian(sub, th) @ v) <= 2e-5
+    # Gramian identities at full size: v^T (G + mu I) v = sum_r w_r (J v)_r^2 + mu |v|^2, symmetry
+    u = rng.standard_normal(pr.p)
+    Gv = host(ctx.gramian_mv(t, dev(v), 1e-4))
+    Gu = host(ctx.gramian_mv(None, dev(u), 1e-4))
+    assert abs(v @ Gv - (np.sum(pr.w * jv * jv) + 1e-4 * v @ v)) <= 1e-5 * abs(v @ Gv)
+    assert abs(u @ Gv - v @ Gu) <= 1e-5 * np.sqrt(abs(u @ Gu) * abs(v @ Gv))
+    ctx.close()
+
+
+def test_test_matrix_matches_oracle_philox(ngd):
+    pr, th = small(SMALL[0], seed=20)
+    for dtype, tol in [("f64", 1e-12), ("f32", 2e-6)]:
+        ctx = ngd.Context(pr, dtype=dtype)
+        ell = 9
+        Om, Y = ctx.nystrom_sketch(dev(th), ell, seed=123456789012, step=5, prec=dtype)
+        Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 123456789012, 5))
+        assert rel(host(Om).T, Om_o) <= tol, dtype
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5), ("tf32", 5e-3), ("bf16", 4e-2)])
+def test_sketch_matches_oracle(ngd, prec, tol):
+    wl, pr, th = _workload("poisson5d", 700, 180) if prec != "f64" else _workload("poisson2d")
+    dtype = "f64" if prec == "f64" else "f32"
+    ctx = ngd.Context(pr, dtype=dtype)
+    ell = 130 if prec != "f64" else 100      # not a multiple of the 128-wide tensor-core tile
+    Om, Y = ctx.nystrom_sketch(dev(th), ell, seed=3, step=1, prec=prec)
+    J = mlp.jacobian(pr, th)
+    Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 3, 1))
+    Y_o = J.T @ (pr.w[:, None] * (J @ Om_o))
+    assert rel(host(Y).T, Y_o) <= tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype,prec", [("f64", "f64"), ("f32", "f32")])
+def test_factor_and_preconditioner_match_oracle(ngd, dtype, prec):
+    wl, pr, th = _workload("poisson2d") if dtype == "f64" else _workload("poisson5d", 600, 150)
+    ell = 60
+    J = mlp.jacobian(pr, th)
+    Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 11, 0))
+    Y_o = J.T @ (pr.w[:, None] * (J @ Om_o))
+    ctx = ngd.Context(pr, dtype=dtype)
+    wd = torch.float64 if dtype == "f64" else torch.float32
+    Om_d = torch.tensor(Om_o.T.copy(), dtype=wd, device="cuda")
+    Y_d = torch.tensor(Y_o.T.copy(), dtype=wd, device="cuda")
+    U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=prec)
+    # the oracle factors the same (rounded) inputs
+    U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, u_in=0.0 if prec == "f64" else 2.0 ** -20)
+    assert abs(nu - nu_o) <= 1e-12 * nu_o
+    lam_g = host(lam)
+    top = lam_o > 1e-6 * lam_o[0]
+    assert np.all(np.diff(lam_g) <= 0)
+    assert rel(lam_g[top], lam_o[top]) <= (1e-8 if dtype == "f64" else 1e-4)
+    mu = 1e-6 if dtype == "f64" else 1e-4
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        v = rng.standard_normal(pr.p)
+        z = host(ctx.precond_apply(ell, U, lam, mu, dev(v)))
+        z_o = nystrom.precond_apply(U_o, lam_o, mu, v)
+        assert rel(z, z_o) <= (1e-8 if dtype == "f64" else 2e-3)
+    # the preconditioner apply itself on identical factors is exact up to rounding
+    U64 = torch.tensor(U_o.T.copy(), dtype=wd, device="cuda")
+    z = host(ctx.precond_apply(ell, U64, dev(lam_o), mu, dev(v)))
+    z_o = nystrom.precond_apply(host(U64).T, lam_o, mu, v)
+    assert rel(z, z_o) <= 1e-12    # FP64 arithmetic, or double-float accumulation over FP32 U
+    ctx.close()
+
+
+def test_factor_reports_not_spd(ngd):
+    pr, th = small(SMALL[0], seed=30)
+    ctx = ngd.Context(pr, dtype="f64")
+    ell = 6
+    Om = nystrom.thin_qr(np.random.default_rng(0).standard_normal((pr.p, ell)))
+    Om_d = dev(Om.T.copy())
+    with pytest.raises(ngd.NGDError) as e:
+        ctx.nystrom_factor(ell, Om_d, dev(-5.0 * Om.T), prec="f64")   # Omega^T Y_nu = -5 I + nu I
+    assert e.value.name == "NOT_SPD"
+    ctx.close()
+
+
+def test_pcg_matches_oracle_at_fixed_iterations(ngd):
+    wl, pr, th = _workload("poisson2d")
+    J = mlp.jacobian(pr, th)
+    G = gramian.gramian(J, pr.w)
+    g_o, _, _ = mlp.gradient(pr, th)
+    ell, mu = 100, 1e-6
+    Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 5, 0))
+    U_o, lam_o, _ = nystrom.nystrom_factor(Om_o, G @ Om_o)
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    g, _, _ = ctx.gradient(t)
+    U_d = dev(U_o.T.copy())
+    for k in [1, 3, 10]:
+        d, it, rr = ctx.pcg_solve(None, g, mu, U_d, dev(lam_o), ell, rtol=0.0, maxit=k)
+        d_o, it_o, rr_o = solve.pcg(lambda v: G @ v + mu * v, g_o, lambda v: nystrom.precond_apply(U_o, lam_o, mu, v),
+                                    0.0, k)
+        assert it == it_o == k
+        assert rel(host(d), d_o) <= 1e-8, k
+        assert abs(rr - rr_o) <= 1e-6 * rr_o + 1e-8   # relres is relative to ||g||; rounding floor ~1e-9
+    # to tolerance: the true residual of the GPU direction, measured with the oracle's G
+    d, it, rr = ctx.pcg_solve(None, g, mu, U_d, dev(lam_o), ell, rtol=1e-10, maxit=2000)
+    res = (G + mu * np.eye(pr.p)) @ host(d) - g_o
+    assert rr <= 1e-10 and np.linalg.norm(res) <= 1e-8 * np.linalg.norm(g_o)
+    # unpreconditioned CG runs more iterations to the same tolerance
+    d2, it2, rr2 = ctx.pcg_solve(None, g, mu, None, None, 0, rtol=1e-10, maxit=5000)
+    assert it2 > it
+    ctx.close()
+
+
+def test_ngd_step_matches_oracle_fp64(ngd):
+    wl, pr, th = _workload("poisson2d")
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    info = ctx.step(t, ell=wl.ell, mu=wl.mu, rtol=wl.rtol, maxit=1000, seed=0, step=0, sketch="f64")
+    th1_o, info_o = solve.ngd_step(pr, th, ell=wl.ell, mu=wl.mu, rtol=0.0, maxit=info["pcg_iters"], seed=0, step=0)
+    assert info["loss_after"] < info["loss_before"]
+    assert abs(info["loss_before"] - info_o.loss_before) <= 1e-12 * info_o.loss_before
+    assert abs(info["lam1"] - info_o.lam1) <= 1e-9 * info_o.lam1
+    assert info["alpha"] == info_o.alpha
+    assert rel(host(t) - th, th1_o - th) <= 1e-6
+    assert info["relres"] <= wl.rtol
+    ctx.close()
+
+
+def test_ngd_step_fp32_paths(ngd):
+    """FP32 path: the F32 sketch converges to rtol; TF32 / BF16 sketches need a shift nu of their
+    unit roundoff, which truncates the captured spectrum (more PCG iterations, never a failure)."""
+    wl, pr, th = _workload("poisson5d", 1200, 300)
+    J = mlp.jacobian(pr, th)
+    g_o = mlp.vjp(pr, th, pr.w * mlp.residual(pr, th)[0])
+    iters = {}
+    for sketch in ["f32", "tf32", "bf16"]:
+        ctx = ngd.Context(pr, dtype="f32")
+        t = dev(th)
+        info = ctx.step(t, ell=200, mu=1e-7, rtol=1e-6, maxit=600, seed=1, step=0, sketch=sketch)
+        iters[sketch] = info["pcg_iters"]
+        assert info["loss_after"] < info["loss_before"], sketch
+        if sketch == "f32":
+            assert info["relres"] <= 1e-6
+            # the direction solves the oracle's FP64 system to the accuracy of the FP32 operator
+            d = (th - host(t)) / info["alpha"]
+            res = J.T @ (pr.w * (J @ d)) + 1e-7 * d - g_o
+            assert np.linalg.norm(res) <= 1e-3 * np.linalg.norm(g_o)
+        ctx.close()
+    assert iters["f32"] <= iters["tf32"] and iters["f32"] <= iters["bf16"], iters
+
+
+def test_heuristic_mu(ngd):
+    pr, th = small(SMALL[0], seed=40)
+    ctx = ngd.Context(pr, dtype="f64")
+    info = ctx.step(dev(th), ell=20, mu=None, rtol=1e-8, maxit=500, seed=2, step=3, sketch="f64")
+    assert info["mu"] == pytest.approx(10 * 2.0 ** -52 * info["lam1"], rel=1e-12)
+    ctx.close()
+
+
+def test_autograd_function_store_and_recompute(ngd):
+    pr, th = small(SMALL[3], seed=50)
+    for budget in [0, 1]:          # 0: unlimited (matrix-free keeps the tape); 1 byte: recompute
+        ctx = ngd.Context(pr, dtype="f64", gv_mode="matrix_free", mem_budget=budget)
+        t = dev(th).requires_grad_(True)
+        r = ngd.PinnResidual.apply(t, ctx)
+        c = torch.randn(pr.n, dtype=torch.float64, device="cuda")
+        (r * c).sum().backward()
+        assert rel(host(t.grad), mlp.vjp(pr, th, host(c))) <= 1e-11
+        ctx.close()
+
+
+def test_nonfinite_and_invalid(ngd):
+    pr, th = small(SMALL[0], seed=60)
+    ctx = ngd.Context(pr, dtype="f64")
+    with pytest.raises(ngd.NGDError) as e:
+        ctx.nystrom_sketch(dev(th), pr.p + 1, prec="f64")
+    assert e.value.name == "INVALID_ARG"
+    bad = th.copy()
+    bad[3] = np.nan
+    g, _, _ = ctx.gradient(dev(bad))
+    with pytest.raises(ngd.NGDError) as e:
+        ctx.pcg_solve(None, g, 1e-3, None, None, 0, rtol=1e-8, maxit=10)
+    assert e.value.name == "NONFINITE"
+    ctx.close()
