@@ -280,6 +280,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2: the FP32 Jacobian streamed by every matvec is 176 MB"},
             "gramian_mv_per_s": 1e3 / gv_ms * world,
             "pcg_iters_mean": float(np.mean([i["pcg_iters"] for i in infos])),
+            "jacobi_sweeps_mean": float(np.mean([i["jacobi_sweeps"] for i in infos])),
             "loss_first_last": [infos[0]["loss_before"], infos[-1]["loss_after"]],
             "phases_ms": phases,
             "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": pr.p * 8,

@@ -106,6 +106,7 @@ typedef struct {
   double loss_before, loss_after, alpha, mu, lam1, lam_ell, nu, relres;
   int pcg_iters, armijo_trials, shift_retries, status;
   double ms_linearize, ms_sketch, ms_factor, ms_pcg, ms_linesearch; /* CUDA-event phase times */
+  int jacobi_sweeps;      /* sweeps of the l x l eigen-solver in this step's factor */
 } ngd_step_info;
 
 /* ---------------------------------------------------------------- context */

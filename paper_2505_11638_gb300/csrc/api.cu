@@ -65,6 +65,7 @@ struct ngd_ctx {
   unsigned int* jac_cnt = nullptr;
   int* jac_info = nullptr;
   TcSketch* tc = nullptr;
+  int last_sweeps = 0;       // Jacobi sweeps of the last factor
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -407,12 +408,13 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
   launch_symmetrize(ctx->V, ell, ctx->stream);
   CK(cudaMemcpyAsync(ctx->A1, ctx->V, (size_t)ell * ell * 8, cudaMemcpyDeviceToDevice, ctx->stream));
   // Jacobi works on (A1, Vs as the second buffer) and accumulates rotations in V
-  CK(launch_jacobi(ctx->A1, ctx->Vs, ctx->V, ell, 40, 4.0 * std::ldexp(1.0, -53), ctx->jac_cnt, ctx->jac_info,
-                   ctx->jac_info + 1, ctx->stream));
+  CK(launch_jacobi(ctx->A1, ctx->Vs, ctx->V, ell, 40, 4.0 * std::ldexp(1.0, -53), std::ldexp(1.0, -56), ctx->jac_cnt,
+                   ctx->jac_info, ctx->jac_info + 1, ctx->stream));
   // the final buffer is A1 or Vs; sort the diagonal and gather eigenvectors into M (free now)
   CK(cudaMemcpyAsync(ctx->h_int + 2, ctx->jac_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   const double* Afin = ctx->h_int[2] == 0 ? ctx->A1 : ctx->Vs;
+  ctx->last_sweeps = ctx->h_int[3];
   launch_eig_sort(Afin, ctx->V, ell, ctx->sig2, ctx->M, ctx->perm, ctx->stream);
   launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
   // U = B V_sorted diag(1/sigma)
@@ -575,6 +577,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   inf.pcg_iters = iters;
   inf.armijo_trials = trials;
   inf.status = 0;
+  inf.jacobi_sweeps = ctx->last_sweeps;
   inf.ms_linearize = ev_ms(ctx, 0, 1);
   inf.ms_sketch = ev_ms(ctx, 1, 2);
   inf.ms_factor = ev_ms(ctx, 2, 3);

@@ -986,8 +986,9 @@ cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s) {
 // tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2),
 // s = t c), then updates its share of the 2x2 blocks A[{p_k,q_k}, {p_k',q_k'}] <- J_k^T A J_k'
 // from the current buffer into the other buffer, and rotates the column pairs of V in place.
-// A pair is skipped when |a_pq| <= tol sqrt(|a_pp a_qq|); the sweeps stop when a whole sweep
-// skips every pair, or after max_sweeps.  Eigenvalues end on the diagonal of the buffer
+// A pair is skipped when |a_pq| <= tol sqrt(|a_pp a_qq|) or |a_pq| <= tol_abs_rel trace(A) (the
+// eigenvalues are then accurate to ~eps ||A||, the accuracy of an SVD of B); the sweeps stop when
+// a whole sweep skips every pair, or after max_sweeps.  Eigenvalues end on the diagonal of the buffer
 // reported in *final_buf (0 or 1).
 __device__ __forceinline__ int rr_index(int pos, int r, int n2) {
   return pos == 0 ? 0 : 1 + (pos - 1 + r) % (n2 - 1);
@@ -995,8 +996,8 @@ __device__ __forceinline__ int rr_index(int pos, int r, int n2) {
 
 __global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double* __restrict__ A1,
                                                 double* __restrict__ V, int n, int max_sweeps, double tol,
-                                                unsigned int* __restrict__ counters, int* __restrict__ final_buf,
-                                                int* __restrict__ sweeps_out) {
+                                                double tol_abs_rel, unsigned int* __restrict__ counters,
+                                                int* __restrict__ final_buf, int* __restrict__ sweeps_out) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n2 = n + (n & 1);
@@ -1007,8 +1008,16 @@ __global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double*
   int* qi = pi + npairs;                             // [npairs] q
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  // V = I
+  // V = I; absolute skip threshold = tol_abs_rel * trace(A) (a bound on ||A||_2 for the PSD input)
   for (int64_t e = gtid; e < (int64_t)n * n; e += gthreads) V[e] = (e % n == e / n) ? 1.0 : 0.0;
+  __shared__ double s_tr;
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += fabs(A0[i + (int64_t)i * n]);
+    s_tr = tr;
+  }
+  __syncthreads();
+  const double tol_abs = tol_abs_rel * s_tr;
   if (gtid == 0) {
     counters[0] = 0u;
     counters[1] = 0u;
@@ -1030,7 +1039,7 @@ __global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double*
         double c = 1.0, s = 0.0;
         if (q < n) {
           const double app = cur[p + (int64_t)p * n], aqq = cur[q + (int64_t)q * n], apq = cur[p + (int64_t)q * n];
-          if (apq != 0.0 && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
+          if (fabs(apq) > tol_abs && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
             const double tau = (aqq - app) / (2.0 * apq);
             const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
@@ -1047,7 +1056,9 @@ __global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double*
       // 2x2 block updates: block (k, k2) covers rows {p_k, q_k} and columns {p_k2, q_k2}
       const int64_t nblk = (int64_t)npairs * npairs;
       for (int64_t e = gtid; e < nblk; e += gthreads) {
-        const int k = (int)(e / npairs), k2 = (int)(e - (int64_t)k * npairs);
+        // consecutive threads take consecutive row pairs of one column pair: the round-robin
+        // indices of neighbouring pairs are neighbours, so the loads and stores coalesce
+        const int k2 = (int)(e / npairs), k = (int)(e - (int64_t)k2 * npairs);
         const int p = pi[k], q = qi[k], p2 = pi[k2], q2 = qi[k2];
         const bool qok = q < n, q2ok = q2 < n;
         const double c = cs[k], s = sn[k], c2 = cs[k2], s2 = sn[k2];
@@ -1096,12 +1107,13 @@ __global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double*
 }
 
 cudaError_t launch_jacobi(double* A0, double* A1, double* V, int n, int max_sweeps, double tol,
-                          unsigned int* counters, int* final_buf, int* sweeps, cudaStream_t s) {
+                          double tol_abs_rel, unsigned int* counters, int* final_buf, int* sweeps,
+                          cudaStream_t s) {
   const int n2 = n + (n & 1);
   const size_t smem = (size_t)(n2 / 2) * (2 * sizeof(double) + 2 * sizeof(int));
   cudaFuncSetAttribute((const void*)k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int blocks = coop_blocks((const void*)k_jacobi, 256, smem);
-  void* args[] = {&A0, &A1, &V, &n, &max_sweeps, &tol, &counters, &final_buf, &sweeps};
+  void* args[] = {&A0, &A1, &V, &n, &max_sweeps, &tol, &tol_abs_rel, &counters, &final_buf, &sweeps};
   note_launch();
   return cudaLaunchCooperativeKernel((const void*)k_jacobi, blocks, 256, args, smem, s);
 }

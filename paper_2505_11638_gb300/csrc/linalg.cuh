@@ -77,7 +77,8 @@ template <typename T>
 void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* Lr, double* dinv, cudaStream_t s);
 cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s);
 cudaError_t launch_jacobi(double* A0, double* A1, double* V, int n, int max_sweeps, double tol,
-                          unsigned int* counters, int* final_buf, int* sweeps, cudaStream_t s);
+                          double tol_abs_rel, unsigned int* counters, int* final_buf, int* sweeps,
+                          cudaStream_t s);
 void launch_eig_sort(const double* Afin, const double* V, int n, double* sig2, double* Vs, int* perm, cudaStream_t s);
 void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* lam, double* inv_sigma,
                            cudaStream_t s);

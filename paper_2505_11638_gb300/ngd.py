@@ -58,7 +58,7 @@ class StepInfo(ctypes.Structure):
                 ("nu", ctypes.c_double), ("relres", ctypes.c_double), ("pcg_iters", ctypes.c_int),
                 ("armijo_trials", ctypes.c_int), ("shift_retries", ctypes.c_int), ("status", ctypes.c_int),
                 ("ms_linearize", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_factor", ctypes.c_double),
-                ("ms_pcg", ctypes.c_double), ("ms_linesearch", ctypes.c_double)]
+                ("ms_pcg", ctypes.c_double), ("ms_linesearch", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
