@@ -215,6 +215,27 @@ ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, dou
  * info: host or NULL.  Synchronises. */
 ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* opts, ngd_step_info* info);
 
+/* Nystrom preconditioner apply that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, e.g. applications whose device
+ * memory is owned by their own pool allocator, or latency-critical loops that cannot accept the
+ * device-wide synchronisation a cudaMalloc may imply.  It computes the same z as
+ * ngd_precond_apply, without a context:
+ *   z = (lam_ell + mu) U (Lambda + mu I)^{-1} U^T v + (I - U U^T) v.
+ * dtype: ngd_dtype of U (float64 or float32); U: device, p x ell column-major with leading
+ * dimension ldU >= p; lam: device ell float64 (descending); v, z: device p float64, distinct;
+ * mu >= 0; stream: cudaStream_t (NULL: legacy default stream).  Asynchronous.
+ * Scratch: a fixed array of NGD_NOALLOC_MAX_ELL doubles (8 KB) compiled into the library and
+ * held by every GPU that loads it until the process exits; ell > NGD_NOALLOC_MAX_ELL returns
+ * NGD_ERR_UNSUPPORTED, other bad arguments NGD_ERR_INVALID_ARG (no message: there is no context).
+ * The first call on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture starts.  All calls share the array and it
+ * keeps the last call's contents (every call overwrites the entries it reads, so nothing needs
+ * clearing); calls that overlap on the GPU (e.g. on two streams) race on it and must be
+ * serialised by the caller. */
+#define NGD_NOALLOC_MAX_ELL 1024
+ngd_status ngd_precond_apply_noalloc(int dtype, int64_t p, int ell, const void* U, int64_t ldU, const double* lam,
+                                     double mu, const double* v, double* z, void* stream);
+
 /* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
  * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,
  * c1 1e-4, rho 0.5, 30 trials. */

@@ -89,6 +89,7 @@ _SIGS = {
     "ngd_step": ([_P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)], _I),
     "ngd_default_step_opts": ([ctypes.POINTER(StepOpts)], None),
     "ngd_kernel_launches": ([], ctypes.c_uint64),
+    "ngd_precond_apply_noalloc": ([_I, ctypes.c_int64, _I, _P, ctypes.c_int64, _P, _D, _P, _P, _P], _I),
 }
 
 
