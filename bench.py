@@ -147,7 +147,7 @@ def oracle_steps(pr, theta, wl, k_max, budget_s):
     for k in range(k_max):
         t0 = time.perf_counter()
         th, info = solve.ngd_step(pr, th, ell=wl.ell, mu=wl.mu, rtol=wl.rtol, maxit=1000, seed=0, step=k,
-                                  u_in=0.0)
+                                  mant_bits=52)
         times.append(time.perf_counter() - t0)
         infos.append(info)
         if sum(times) > budget_s:

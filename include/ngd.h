@@ -180,8 +180,8 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
                               int prec, void* Omega, void* Y);
 
 /* Factor of App. A, remaining steps, given an orthonormal Omega and Y = G Omega:
- * nu = max(eps(||Y||_F), u_in ||Y||_F) with u_in the unit roundoff of 'prec'
- * (0 for F64), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
+ * nu = eps(||Y||_F) in the format of 'prec' (spacing 2^(floor(log2 x) - m) with m = 52, 23,
+ * 10, 7 mantissa bits for F64, F32, TF32, BF16), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
  * B = Y_nu C^{-1}, eigen-decomposition of B^T B in FP64 (cyclic Jacobi) gives
  * B = U Sigma V^T, lambda = max(0, Sigma^2 - nu), descending.
  * shift_scale multiplies nu (1 = the rule above; ngd_step retries with 8, 64).

@@ -8,10 +8,11 @@ App. A, Alg. randomized_nystrom, in the paper's order:
     B = Y_nu / C;  [U, Sigma, ~] = svd(B, 0);  Lambda = max(0, Sigma^2 - nu I).
 Readings where the paper is silent (shared with the CUDA side):
   * qr is the thin QR normalised so that R has a positive diagonal (unique).
-  * eps(x) is MATLAB's spacing of doubles at x.  When Y comes from a sketch whose
-    inputs were rounded to a unit roundoff u_in (TF32, BF16, FP32), the shift is
-    nu = max(eps(||Y||_F), u_in ||Y||_F) so that Omega^T Y_nu stays positive
-    definite despite the rounding of Y; u_in = 0 is the paper's FP64 algorithm.
+  * eps(x) is MATLAB's spacing at x in the precision Y was computed in: for a number
+    format with m explicit mantissa bits, eps_m(x) = 2^(floor(log2 x) - m).  m = 52 (FP64)
+    is the paper's algorithm; a sketch computed in FP32 (m = 23), TF32 (m = 10) or BF16
+    (m = 7) takes its own spacing, which keeps Omega^T Y_nu positive definite despite the
+    rounding of Y (as eps(single(x)) would in MATLAB).
   * chol reads the symmetric part (Omega^T Y_nu + Y_nu^T Omega)/2 and returns the
     upper factor C with C^T C = that matrix (MATLAB's chol reads one triangle; the
     two agree in exact arithmetic).
@@ -34,18 +35,25 @@ def thin_qr(Omega):
     return Q * s[None, :]
 
 
-def shift(normY: float, u_in: float = 0.0) -> float:
-    """nu = eps(||Y||_F), raised to u_in ||Y||_F for a rounded sketch (reading above)."""
-    return max(float(np.spacing(np.float64(normY))), u_in * normY)
+MANTISSA_BITS = {"f64": 52, "f32": 23, "tf32": 10, "bf16": 7}
 
 
-def nystrom_factor(Omega, Y, u_in: float = 0.0):
+def shift(normY: float, mant_bits: int = 52) -> float:
+    """nu = eps(||Y||_F) in a format with mant_bits explicit mantissa bits (reading above)."""
+    if not normY > 0.0:
+        return 0.0
+    return float(np.ldexp(1.0, int(np.floor(np.log2(normY))) - mant_bits))
+
+
+def nystrom_factor(Omega, Y, mant_bits: int = 52, shift_scale: float = 1.0):
     """Steps 4-9 of App. A given the orthonormal test matrix and Y = G Omega.
 
-    Returns U (p, ell), lambda_hat (ell, descending) and the shift nu.
-    Raises numpy.linalg.LinAlgError if Omega^T Y_nu is not positive definite.
+    mant_bits selects the precision whose eps gives the shift; shift_scale multiplies it (the
+    step retries a non-positive-definite core with 8x and 64x).  Returns U (p, ell),
+    lambda_hat (ell, descending) and the shift nu.  Raises numpy.linalg.LinAlgError if
+    Omega^T Y_nu is not positive definite.
     """
-    nu = shift(np.linalg.norm(Y, "fro"), u_in)
+    nu = shift_scale * shift(np.linalg.norm(Y, "fro"), mant_bits)
     Ynu = Y + nu * Omega
     M = Omega.T @ Ynu
     M = 0.5 * (M + M.T)
@@ -56,11 +64,11 @@ def nystrom_factor(Omega, Y, u_in: float = 0.0):
     return U, lam, nu
 
 
-def randomized_nystrom(G_apply, Omega_raw, u_in: float = 0.0):
+def randomized_nystrom(G_apply, Omega_raw, mant_bits: int = 52):
     """The whole of App. A: orthonormalise, sketch Y = G Omega, factor."""
     Omega = thin_qr(Omega_raw)
     Y = G_apply(Omega)
-    U, lam, nu = nystrom_factor(Omega, Y, u_in)
+    U, lam, nu = nystrom_factor(Omega, Y, mant_bits)
     return Omega, Y, U, lam, nu
 
 

@@ -88,7 +88,7 @@ class StepInfo:
     armijo_trials: int
 
 
-def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, u_in=0.0, gamma=10.0,
+def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gamma=10.0,
              c1=1e-4, rho=0.5, max_trials=30, return_parts=False):
     """One Nystrom-preconditioned matrix-free NGD step (Alg. 1 + Alg. 3 + Alg. 4, fixed ell).
 
@@ -103,7 +103,15 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, u_in=0.0, gamma=1
         return J.T @ (w[:, None] * (J @ V)) if V.ndim == 2 else _gram.gramian_mv(J, w, V)
 
     Omega_raw = _philox.gaussian_test_matrix(J.shape[1], ell, seed, step)
-    Omega, Y, U, lam, nu = _nys.randomized_nystrom(G_apply, Omega_raw, u_in)   # Alg. 4, line 1
+    Omega = _nys.thin_qr(Omega_raw)                                # Alg. 4, line 1 (App. A)
+    Y = G_apply(Omega)
+    for scale in (1.0, 8.0, 64.0):      # a non-positive-definite core is retried with a larger shift
+        try:
+            U, lam, nu = _nys.nystrom_factor(Omega, Y, mant_bits, scale)
+            break
+        except np.linalg.LinAlgError:
+            if scale == 64.0:
+                raise
     mu_eff = float(mu) if mu is not None else _nys.mu_from_lambda1(lam[0], gamma)  # Alg. 4, line 2
 
     def A(v):

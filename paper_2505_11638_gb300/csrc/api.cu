@@ -301,12 +301,14 @@ ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* 
 }
 
 // ------------------------------------------------------------------ sketch and factor (internal buffers, ld = ldP)
-double unit_roundoff(int prec) {
+// Explicit mantissa bits of the format the sketch Y is computed in: nu = eps(||Y||_F) in that
+// format (App. A step 4, read as MATLAB's eps of the sketch's precision).
+int mantissa_bits(int prec) {
   switch (prec) {
-    case NGD_SKETCH_TF32: return std::ldexp(1.0, -10);   // tensor cores read the top 19 bits (truncation)
-    case NGD_SKETCH_BF16: return std::ldexp(1.0, -8);
-    case NGD_SKETCH_F32: return std::ldexp(1.0, -20);    // FP32 products summed over 128-deep FP32 chunks
-    default: return 0.0;
+    case NGD_SKETCH_TF32: return 10;
+    case NGD_SKETCH_BF16: return 7;
+    case NGD_SKETCH_F32: return 23;
+    default: return 52;
   }
 }
 
@@ -398,7 +400,7 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
   T* Bm = (T*)ctx->B;
   TRY(clear_status(ctx));
   launch_frob2<T>(Y, ctx->ldP, ctx->p, ell, ctx->part, ctx->scal + kSFrob2, ctx->stream);
-  launch_compute_nu(ctx->scal + kSFrob2, unit_roundoff(prec), shift_scale, ctx->scal + kSNu, ctx->stream);
+  launch_compute_nu(ctx->scal + kSFrob2, mantissa_bits(prec), shift_scale, ctx->scal + kSNu, ctx->stream);
   launch_shift_add<T>(Y, Om, ctx->scal + kSNu, Bm, ctx->ldP, ctx->p, ell, ctx->stream);   // Y_nu
   TRY(gram_atb<T>(ctx, Om, Bm, ctx->p, ctx->ldP, ell, ctx->M));                          // Omega^T Y_nu
   launch_symmetrize(ctx->M, ell, ctx->stream);

@@ -731,20 +731,20 @@ template void launch_sum_splits_t<double>(const double*, int, int64_t, int64_t, 
                                           cudaStream_t);
 
 // ---------------------------------------------------------------------------- small elementwise helpers
-// Y_nu = Y + nu Omega with nu = scale * max(eps(||Y||_F), u_in ||Y||_F) computed on the device
-// from frob2 = ||Y||_F^2; stores nu in *nu_out.
-__device__ __forceinline__ double spacing_of(double x) {
-  if (!(x > 0.0) || !isfinite(x)) return 0.0;
-  int e;
-  frexp(x, &e);  // x = m 2^e, m in [0.5, 1)
-  return ldexp(1.0, e - 53);
+// nu = scale * eps_m(||Y||_F), the spacing at ||Y||_F of a format with m explicit mantissa bits
+// (2^(floor(log2 x) - m)), computed on the device from frob2 = ||Y||_F^2; stored in *nu_out.
+__global__ void k_compute_nu(const double* frob2, int mant_bits, double scale, double* nu_out) {
+  const double x = sqrt(*frob2);
+  double nu = 0.0;
+  if (x > 0.0 && isfinite(x)) {
+    int e;
+    frexp(x, &e);  // x = f 2^e, f in [0.5, 1): floor(log2 x) = e - 1
+    nu = ldexp(1.0, e - 1 - mant_bits);
+  }
+  *nu_out = scale * nu;
 }
-__global__ void k_compute_nu(const double* frob2, double u_in, double scale, double* nu_out) {
-  const double n = sqrt(*frob2);
-  *nu_out = scale * fmax(spacing_of(n), u_in * n);
-}
-void launch_compute_nu(const double* frob2, double u_in, double scale, double* nu_out, cudaStream_t s) {
-  k_compute_nu<<<1, 1, 0, s>>>(frob2, u_in, scale, nu_out); note_launch();
+void launch_compute_nu(const double* frob2, int mant_bits, double scale, double* nu_out, cudaStream_t s) {
+  k_compute_nu<<<1, 1, 0, s>>>(frob2, mant_bits, scale, nu_out); note_launch();
 }
 
 template <typename T>

@@ -65,7 +65,7 @@ template <typename T>
 void launch_sum_splits_t(const double* part, int nz, int64_t stride, int64_t rows, int64_t cols, int64_t ldp, T* out,
                          int64_t ldo, cudaStream_t s);
 
-void launch_compute_nu(const double* frob2, double u_in, double scale, double* nu_out, cudaStream_t s);
+void launch_compute_nu(const double* frob2, int mant_bits, double scale, double* nu_out, cudaStream_t s);
 template <typename T>
 void launch_frob2(const T* Y, int64_t ld, int64_t p, int ell, double* part, double* out, cudaStream_t s);
 template <typename T>

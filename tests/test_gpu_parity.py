@@ -182,7 +182,7 @@ def test_factor_and_preconditioner_match_oracle(ngd, dtype, prec):
     Y_d = torch.tensor(Y_o.T.copy(), dtype=wd, device="cuda")
     U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=prec)
     # the oracle factors the same (rounded) inputs
-    U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, u_in=0.0 if prec == "f64" else 2.0 ** -20)
+    U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, nystrom.MANTISSA_BITS[prec])
     assert abs(nu - nu_o) <= 1e-12 * nu_o
     lam_g = host(lam)
     top = lam_o > 1e-6 * lam_o[0]

@@ -160,11 +160,13 @@ def test_nystrom_invariant_under_right_multiplication():
     assert np.linalg.norm(G1 - G2, 2) <= 1e-10 * np.linalg.norm(G, 2)
 
 
-def test_shift_is_spacing_of_doubles():
-    for x in [1.0, 3.7, 1e-3, 123456.0]:
-        assert nystrom.shift(x) == np.spacing(x)
-        assert nystrom.shift(x) == 2.0 ** (np.floor(np.log2(x)) - 52)
-    assert nystrom.shift(8.0, 2.0 ** -10) == 8.0 * 2.0 ** -10
+def test_shift_is_spacing_in_the_sketch_precision():
+    for x in [1.0, 3.7, 1e-3, 123456.0, 9.6951]:
+        assert nystrom.shift(x) == np.spacing(x)                          # FP64: MATLAB eps(x)
+        assert nystrom.shift(x, 23) == float(np.spacing(np.float32(x)))   # FP32: eps(single(x))
+        assert nystrom.shift(x, 52) == 2.0 ** (np.floor(np.log2(x)) - 52)
+    assert nystrom.shift(8.0, 10) == 8.0 * 2.0 ** -10                       # TF32 spacing at 8
+    assert nystrom.shift(3.0, 7) == 2.0 * 2.0 ** -7                         # BF16 spacing at 3
 
 
 def test_preconditioner_exact_nystrom_gives_mu_identity():
