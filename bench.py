@@ -280,7 +280,6 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2: the FP32 Jacobian streamed by every matvec is 176 MB"},
             "gramian_mv_per_s": 1e3 / gv_ms * world,
             "pcg_iters_mean": float(np.mean([i["pcg_iters"] for i in infos])),
-            "jacobi_sweeps_mean": float(np.mean([i["jacobi_sweeps"] for i in infos])),
             "loss_first_last": [infos[0]["loss_before"], infos[-1]["loss_after"]],
             "phases_ms": phases,
             "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": pr.p * 8,
@@ -307,7 +306,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--sketch", default="f32", choices=["f32", "tf32", "bf16"])
+    ap.add_argument("--sketch", default="f64", choices=["f64", "f32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()

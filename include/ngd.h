@@ -54,9 +54,14 @@ typedef enum {
 
 typedef enum { NGD_F64 = 0, NGD_F32 = 1 } ngd_dtype;
 
-/* Arithmetic of the sketch GEMMs Z = J Omega and Y = J^T (w .* Z):
- *   F64  FP64 CUDA cores; F32 FP32 CUDA cores with FP64 cross-tile sums;
- *   TF32 / BF16 tcgen05 tensor cores (operands rounded, FP32 accumulation in TMEM). */
+/* Arithmetic of the sketch GEMMs Z = J Omega and Y = J^T (w .* Z) and of the factor:
+ *   F64  FP64-accurate.  In an F64 context: FP64 CUDA cores.  In an F32 context: the FP32
+ *        Jacobian and Omega are multiplied with double-float arithmetic on the FP32 pipes
+ *        (exact products, TwoSum accumulation), Y is float64 and the factor keeps FP64 accuracy;
+ *        only U is rounded to FP32.  Shift nu = eps64(||Y||_F), the paper's algorithm.
+ *   F32  FP32 CUDA cores with FP64 cross-tile sums; Y float32; shift eps32(||Y||_F).
+ *   TF32 / BF16 tcgen05 tensor cores (operands rounded, FP32 accumulation in TMEM); Y float32;
+ *        shift eps_TF32 / eps_BF16 (||Y||_F). */
 typedef enum { NGD_SKETCH_F64 = 0, NGD_SKETCH_F32 = 1, NGD_SKETCH_TF32 = 2, NGD_SKETCH_BF16 = 3 } ngd_sketch_prec;
 
 /* Interior residual: Poisson  r = Delta u + f  (Eq. energy_poisson);
@@ -106,7 +111,6 @@ typedef struct {
   double loss_before, loss_after, alpha, mu, lam1, lam_ell, nu, relres;
   int pcg_iters, armijo_trials, shift_retries, status;
   double ms_linearize, ms_sketch, ms_factor, ms_pcg, ms_linesearch; /* CUDA-event phase times */
-  int jacobi_sweeps;      /* sweeps of the l x l eigen-solver in this step's factor */
 } ngd_step_info;
 
 /* ---------------------------------------------------------------- context */
@@ -174,7 +178,8 @@ ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, do
  * layout in the implementation notes), Omega = thin QR factor with positive
  * diag(R) (CholeskyQR2), Y = G Omega = J^T (w .* (J Omega)) in the arithmetic
  * 'prec' (the only dense contraction of the path).
- * Omega, Y: device, p x ell column-major (leading dimension p), context dtype.
+ * Omega: device, p x ell column-major (leading dimension p), context dtype.  Y: same layout,
+ * float64 when prec = NGD_SKETCH_F64, else the context dtype.
  * ell <= min(p, 2048).  TF32/BF16 need an F32 context and the stored Jacobian. */
 ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step,
                               int prec, void* Omega, void* Y);
@@ -182,19 +187,23 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
 /* Factor of App. A, remaining steps, given an orthonormal Omega and Y = G Omega:
  * nu = eps(||Y||_F) in the format of 'prec' (spacing 2^(floor(log2 x) - m) with m = 52, 23,
  * 10, 7 mantissa bits for F64, F32, TF32, BF16), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
- * B = Y_nu C^{-1}, eigen-decomposition of B^T B in FP64 (cyclic Jacobi) gives
- * B = U Sigma V^T, lambda = max(0, Sigma^2 - nu), descending.
+ * B = Y_nu C^{-1}, eigen-decomposition of B^T B in FP64 (Householder tridiagonalization,
+ * multisection, twisted factorization, back-transform) gives B = U Sigma V^T, lambda = max(0, Sigma^2 - nu), descending.
  * shift_scale multiplies nu (1 = the rule above; ngd_step retries with 8, 64).
- * Omega, Y: device p x ell (context dtype), U: device p x ell out, lam: device ell
- * float64 out, nu_out: host or NULL (synchronises when non-NULL).
+ * Omega: device p x ell (context dtype); Y: device p x ell (float64 when prec = NGD_SKETCH_F64,
+ * else the context dtype); U: device p x ell out, float64 when prec = NGD_SKETCH_F64, else
+ * float32 (in an F32 context the preconditioner's cancellation in I - U U^T needs U in FP64 once
+ * the sketch resolves G's spectrum to FP64 level); lam: device ell float64 out, nu_out: host or
+ * NULL (synchronises when non-NULL).
  * NOT_SPD when C does not exist. */
 ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const void* Y, int prec,
                               double shift_scale, void* U, double* lam, double* nu_out);
 
 /* Nystrom preconditioner, Alg. 4 (scaled form of Eq. nystrom_inverse):
  * z = (lam_ell + mu) U (Lambda + mu I)^{-1} U^T v + (I - U U^T) v.
- * U: device p x ell (context dtype), lam: device ell, v, z: device p (no aliasing). */
-ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, const double* lam, double mu,
+ * U: device p x ell of ngd_dtype u_dtype (NGD_F64, or NGD_F32 in an F32 context), lam: device
+ * ell, v, z: device p (no aliasing).  Asynchronous on the context stream. */
+ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, int u_dtype, const double* lam, double mu,
                              const double* v, double* z);
 
 /* ---------------------------------------------------------------- solver */
@@ -202,10 +211,11 @@ ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, const double*
 /* Preconditioned CG for (G + mu I) d = g (Alg. 3; textbook pCG, x0 = 0), stopping
  * when ||r_k||_2 <= rtol ||g||_2 (recurrence residual, FP64) or after maxit
  * iterations.  ell = 0 or U = NULL runs unpreconditioned CG.  mu > 0.
- * theta NULL reuses the last linearization.  g, d: device p; iters, relres: host
- * (the call synchronises).  Returns BREAKDOWN if p^T (G + mu I) p <= 0. */
+ * theta NULL reuses the last linearization.  U: as for ngd_precond_apply, u_dtype its
+ * ngd_dtype.  g, d: device p; iters, relres: host (the call synchronises).  Returns BREAKDOWN
+ * if p^T (G + mu I) p <= 0. */
 ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, double mu,
-                         const void* U, const double* lam, int ell, double rtol, int maxit,
+                         const void* U, int u_dtype, const double* lam, int ell, double rtol, int maxit,
                          double* d, int* iters, double* relres);
 
 /* One Nystrom-preconditioned matrix-free NGD step (Alg. 1 with Alg. 3 and Alg. 4,

@@ -59,13 +59,11 @@ struct ngd_ctx {
   int ell_cap = 0;
   void *Om = nullptr, *Y = nullptr, *B = nullptr, *U = nullptr, *Lr = nullptr, *VsT = nullptr, *Zw = nullptr;
   double *M = nullptr, *A1 = nullptr, *V = nullptr, *Vs = nullptr, *sig2 = nullptr, *inv_sigma = nullptr;
-  double *lam = nullptr, *dinv = nullptr, *w1 = nullptr, *gpart = nullptr;
+  double *lam = nullptr, *dinv = nullptr, *w1 = nullptr, *gpart = nullptr, *eigws = nullptr;
+  double *Y64 = nullptr, *B64 = nullptr, *Zw64 = nullptr, *U64 = nullptr;  // FP64-accurate sketch of an FP32 J
   size_t gpart_elems = 0;
   int* perm = nullptr;
-  unsigned int* jac_cnt = nullptr;
-  int* jac_info = nullptr;
   TcSketch* tc = nullptr;
-  int last_sweeps = 0;       // Jacobi sweeps of the last factor
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -183,6 +181,16 @@ ngd_status ensure_ell(ngd_ctx* ctx, int ell) {
   TRY(dalloc(ctx, &ctx->dinv, ell * 8));
   TRY(dalloc(ctx, &ctx->w1, ell * 8));
   TRY(dalloc(ctx, &ctx->perm, ell * sizeof(int)));
+  TRY(dalloc(ctx, &ctx->eigws, sym_eig_workspace_doubles(ell) * 8));
+  if (ctx->dtype == NGD_F32) {
+    TRY(dalloc(ctx, &ctx->Y64, (size_t)ctx->ldP * ell * 8));
+    TRY(dalloc(ctx, &ctx->B64, (size_t)ctx->ldP * ell * 8));
+    TRY(dalloc(ctx, &ctx->Zw64, (size_t)ctx->N * ell * 8));
+    TRY(dalloc(ctx, &ctx->U64, (size_t)ctx->ldP * ell * 8));
+    CK(cudaMemsetAsync(ctx->U64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
+    CK(cudaMemsetAsync(ctx->Y64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
+    CK(cudaMemsetAsync(ctx->B64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
+  }
   ctx->ell_cap = ell;
   CK(cudaMemsetAsync(ctx->Om, 0, pe, ctx->stream));
   CK(cudaMemsetAsync(ctx->Y, 0, pe, ctx->stream));
@@ -259,7 +267,10 @@ ngd_status linearize(ngd_ctx* ctx, const double* theta) {
 template <typename T>
 ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_stored) {
   if (use_stored && ctx->stored_j && ctx->lin_valid) {
-    launch_coldot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, cot, ctx->colpart, ctx->colsplit, nullptr, ctx->stream);
+    if (std::is_same<T, float>::value)
+      launch_coldot_df((const float*)ctx->J, ctx->ldJ, ctx->N, cot, ctx->colpart, ctx->colsplit, nullptr, ctx->stream);
+    else
+      launch_coldot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, cot, ctx->colpart, ctx->colsplit, nullptr, ctx->stream);
     launch_coldot_finish(ctx->colpart, ctx->colsplit, ctx->p, ctx->ldJ, nullptr, 0.0, nullptr, out, 0, nullptr,
                          ctx->stream);
     return check_launch(ctx);
@@ -272,7 +283,10 @@ ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_st
                                       nullptr, tape, 0, ctx->stream);
     if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
     const int ns = coldot_nsplit(nr, ctx->ldJ, sizeof(T) == 4 ? 4 : 2);
-    launch_coldot<T>((const T*)ctx->J, ctx->ldJ, nr, cot + r0, ctx->colpart, ns, nullptr, ctx->stream);
+    if (std::is_same<T, float>::value)
+      launch_coldot_df((const float*)ctx->J, ctx->ldJ, nr, cot + r0, ctx->colpart, ns, nullptr, ctx->stream);
+    else
+      launch_coldot<T>((const T*)ctx->J, ctx->ldJ, nr, cot + r0, ctx->colpart, ns, nullptr, ctx->stream);
     launch_coldot_finish(ctx->colpart, ns, ctx->p, ctx->ldJ, nullptr, 0.0, nullptr, out, r0 > 0 ? 1 : 0, nullptr,
                          ctx->stream);
   }
@@ -283,10 +297,20 @@ ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_st
 template <typename T>
 ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* mu_d, double* y, const int* done) {
   if (ctx->stored_j) {
-    launch_d2t<T>(v, (T*)ctx->vT, ctx->p, ctx->ldJ, ctx->stream);
-    launch_rowdot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, (const T*)ctx->vT, ctx->ps.w, nullptr, ctx->svec, done,
-                     ctx->stream);
-    launch_coldot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->svec, ctx->colpart, ctx->colsplit, done, ctx->stream);
+    if (std::is_same<T, float>::value) {
+      float* vh = (float*)ctx->vT;
+      launch_split_df(v, vh, vh + ctx->ldJ, ctx->p, ctx->ldJ, ctx->stream);
+      launch_rowdot_df((const float*)ctx->J, ctx->ldJ, ctx->N, vh, vh + ctx->ldJ, ctx->ps.w, nullptr, ctx->svec,
+                       done, ctx->stream);
+      launch_coldot_df((const float*)ctx->J, ctx->ldJ, ctx->N, ctx->svec, ctx->colpart, ctx->colsplit, done,
+                       ctx->stream);
+    } else {
+      launch_d2t<T>(v, (T*)ctx->vT, ctx->p, ctx->ldJ, ctx->stream);
+      launch_rowdot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, (const T*)ctx->vT, ctx->ps.w, nullptr, ctx->svec, done,
+                       ctx->stream);
+      launch_coldot<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->svec, ctx->colpart, ctx->colsplit, done,
+                       ctx->stream);
+    }
     launch_coldot_finish(ctx->colpart, ctx->colsplit, ctx->p, ctx->ldJ, v, mu_h, mu_d, y, 0, done, ctx->stream);
     return check_launch(ctx);
   }
@@ -347,6 +371,25 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
     CK(e);
     return check_launch(ctx);
   }
+  if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64) {
+    // FP64-accurate sketch of the FP32 Jacobian (double-float arithmetic): Zw (FP64) = diag(w) J Om,
+    // Y64 = J^T Zw.  The Nystrom core then resolves G's spectrum down to eps64 ||Y||, as in the paper.
+    if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "the FP64-accurate sketch needs the stored Jacobian%s");
+    GemmDfArgs<float, float> g1;
+    g1.M = ctx->N; g1.N = ell; g1.K = ctx->p;
+    g1.A = (const float*)ctx->J; g1.sam = ctx->ldJ; g1.sak = 1;
+    g1.B = (const float*)Om; g1.sbk = 1; g1.sbn = ctx->ldP;
+    g1.out64 = ctx->Zw64; g1.scm = ell; g1.scn = 1;
+    g1.rowscale = ctx->ps.w;
+    launch_gemm_df<float, float>(g1, ctx->stream);
+    GemmDfArgs<float, double> g2;
+    g2.M = ctx->p; g2.N = ell; g2.K = ctx->N;
+    g2.A = (const float*)ctx->J; g2.sam = 1; g2.sak = ctx->ldJ;
+    g2.B = ctx->Zw64; g2.sbk = ell; g2.sbn = 1;
+    g2.out64 = ctx->Y64; g2.scm = 1; g2.scn = ctx->ldP;
+    launch_gemm_df<float, double>(g2, ctx->stream);
+    return check_launch(ctx);
+  }
   if (ctx->stored_j) {
     // Zw = diag(w) J Om  (N x ell, row-major), then Y = J^T Zw  (p x ell, column-major)
     GemmArgs<T> g1;
@@ -392,9 +435,67 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
   return check_launch(ctx);
 }
 
+// Factor of an FP64-accurate sketch in an FP32 context: Omega FP32 (exact values), Y, B and U in
+// FP64, products by the double-float GEMM.  U stays FP64: the apply of Alg. 4 scales the top
+// directions by (lam_ell + mu) / (lam_1 + mu), ~1e-7 at later steps of the 5-D Poisson problem, a
+// value formed by cancellation in I - U U^T that an FP32-rounded U perturbs by its own rounding.
+ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
+  const float* Om = (const float*)ctx->Om;
+  double* Bm = ctx->B64;
+  const int64_t p = ctx->p, ld = ctx->ldP;
+  TRY(clear_status(ctx));
+  launch_frob2<double>(ctx->Y64, ld, p, ell, ctx->part, ctx->scal + kSFrob2, ctx->stream);
+  launch_compute_nu(ctx->scal + kSFrob2, 52, shift_scale, ctx->scal + kSNu, ctx->stream);
+  launch_shift_add_mixed(ctx->Y64, Om, ctx->scal + kSNu, Bm, ld, p, ell, ctx->stream);      // Y_nu
+  {
+    GemmDfArgs<float, double> g;                                                           // Omega^T Y_nu
+    g.M = ell; g.N = ell; g.K = p;
+    g.A = Om; g.sam = ld; g.sak = 1;
+    g.B = Bm; g.sbk = 1; g.sbn = ld;
+    g.nsplit = choose_splits(ell, ell, p);
+    const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : g.K;
+    const int nz = (int)((g.K + kps - 1) / kps);
+    TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));
+    g.out64 = ctx->gpart; g.split_stride = (int64_t)ell * ell; g.scm = 1; g.scn = ell;
+    launch_gemm_df<float, double>(g, ctx->stream);
+    launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, ctx->M, ctx->stream);
+  }
+  launch_symmetrize(ctx->M, ell, ctx->stream);
+  CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));                                // = L L^T
+  launch_trsm_lt<double>(Bm, ld, p, ell, ctx->M, (double*)ctx->eigws, ctx->dinv, ctx->stream);  // B = Y_nu L^{-T}
+  {
+    GemmDfArgs<double, double> g;                                                          // S = B^T B
+    g.M = ell; g.N = ell; g.K = p;
+    g.A = Bm; g.sam = ld; g.sak = 1;
+    g.B = Bm; g.sbk = 1; g.sbn = ld;
+    g.nsplit = choose_splits(ell, ell, p);
+    const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : g.K;
+    const int nz = (int)((g.K + kps - 1) / kps);
+    TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));
+    g.out64 = ctx->gpart; g.split_stride = (int64_t)ell * ell; g.scm = 1; g.scn = ell;
+    launch_gemm_df<double, double>(g, ctx->stream);
+    launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, ctx->V, ctx->stream);
+  }
+  launch_symmetrize(ctx->V, ell, ctx->stream);
+  CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream));
+  launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
+  {
+    GemmDfArgs<double, double> g;                                                          // U = B V Sigma^{-1}
+    g.M = p; g.N = ell; g.K = ell;
+    g.A = Bm; g.sam = 1; g.sak = ld;
+    g.B = ctx->M; g.sbk = 1; g.sbn = ell;
+    g.out64 = ctx->U64; g.scm = 1; g.scn = ld;
+    g.colscale = ctx->inv_sigma;
+    launch_gemm_df<double, double>(g, ctx->stream);
+  }
+  TRY(check_launch(ctx));
+  return sync_status(ctx);
+}
+
 template <typename T>
 ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) {
   TRY(ensure_ell(ctx, ell));
+  if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64) return factor_df(ctx, ell, shift_scale);
   const T* Om = (const T*)ctx->Om;
   const T* Y = (const T*)ctx->Y;
   T* Bm = (T*)ctx->B;
@@ -408,16 +509,8 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
   launch_trsm_lt<T>(Bm, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->dinv, ctx->stream);  // B = Y_nu C^{-1}
   TRY(gram_atb<T>(ctx, Bm, Bm, ctx->p, ctx->ldP, ell, ctx->V));                          // S = B^T B
   launch_symmetrize(ctx->V, ell, ctx->stream);
-  CK(cudaMemcpyAsync(ctx->A1, ctx->V, (size_t)ell * ell * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-  // Jacobi works on (A1, Vs as the second buffer) and accumulates rotations in V
-  CK(launch_jacobi(ctx->A1, ctx->Vs, ctx->V, ell, 40, 4.0 * std::ldexp(1.0, -53), std::ldexp(1.0, -56), ctx->jac_cnt,
-                   ctx->jac_info, ctx->jac_info + 1, ctx->stream));
-  // the final buffer is A1 or Vs; sort the diagonal and gather eigenvectors into M (free now)
-  CK(cudaMemcpyAsync(ctx->h_int + 2, ctx->jac_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  const double* Afin = ctx->h_int[2] == 0 ? ctx->A1 : ctx->Vs;
-  ctx->last_sweeps = ctx->h_int[3];
-  launch_eig_sort(Afin, ctx->V, ell, ctx->sig2, ctx->M, ctx->perm, ctx->stream);
+  // S = V Sigma^2 V^T in FP64; sorted eigenvectors into M (free again after the triangular solve)
+  CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream));
   launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
   // U = B V_sorted diag(1/sigma)
   {
@@ -437,9 +530,19 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
 }
 
 // ------------------------------------------------------------------ PCG
+// P^{-1} v with U stored as float (u_f64 false) or double
+void precond(ngd_ctx* ctx, bool u_f64, const void* U, int64_t ldU, int ell, const double* lam, double mu_h,
+             const double* mu_d, const double* v, double* z, const int* done) {
+  if (u_f64)
+    launch_precond<double>((const double*)U, ldU, ctx->p, ell, lam, mu_h, mu_d, v, z, ctx->w1, done, ctx->stream);
+  else
+    launch_precond<float>((const float*)U, ldU, ctx->p, ell, lam, mu_h, mu_d, v, z, ctx->w1, done, ctx->stream);
+}
+
 template <typename T>
-ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double* mu_d, const void* U, int64_t ldU,
-                        const double* lam, int ell, double rtol, int maxit, double* dout, int* iters, double* relres) {
+ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double* mu_d, const void* U, bool u_f64,
+                        int64_t ldU, const double* lam, int ell, double rtol, int maxit, double* dout, int* iters,
+                        double* relres) {
   PcgScalars* h = ctx->h_pcg;
   memset(h, 0, sizeof(PcgScalars));
   h->rtol2 = rtol * rtol;
@@ -455,8 +558,7 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   const bool pre = U != nullptr && ell > 0;
   const int* done = &ctx->pcg->done;
   launch_pcg_init(g, x, r, p, ctx->part, ctx->pcg, ctx->stream);
-  if (pre)
-    launch_precond<T>((const T*)U, ldU, p, ell, lam, mu_h, mu_d, r, z, ctx->w1, nullptr, ctx->stream);
+  if (pre) precond(ctx, u_f64, U, ldU, ell, lam, mu_h, mu_d, r, z, nullptr);
   launch_pcg_first_dir(r, pre ? z : r, pv, p, ctx->part, ctx->pcg, ctx->stream);
   TRY(check_launch(ctx));
   const int chunk = 2;
@@ -466,7 +568,7 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
       TRY(gv_current<T>(ctx, pv, mu_h, mu_d, q, done));
       launch_pcg_alpha(pv, q, p, ctx->part, ctx->pcg, ctx->stream);
       launch_pcg_update_xr(x, r, pv, q, p, ctx->part, ctx->pcg, ctx->stream);
-      if (pre) launch_precond<T>((const T*)U, ldU, p, ell, lam, mu_h, mu_d, r, z, ctx->w1, done, ctx->stream);
+      if (pre) precond(ctx, u_f64, U, ldU, ell, lam, mu_h, mu_d, r, z, done);
       launch_pcg_beta(r, pre ? z : r, p, ctx->part, ctx->pcg, ctx->stream);
       launch_pcg_update_p(pv, pre ? z : r, p, ctx->pcg, ctx->stream);
     }
@@ -531,7 +633,9 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   // Alg. 3 line 3: pCG on (G + mu I) d = g with the Nystrom preconditioner of Alg. 4
   int iters = 0;
   double relres = 0.0;
-  TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, ctx->U, ctx->ldP, ctx->lam, o->ell, o->rtol, o->maxit,
+  const bool u_f64 = !std::is_same<T, float>::value || o->sketch == NGD_SKETCH_F64;
+  const void* Ust = std::is_same<T, float>::value && o->sketch == NGD_SKETCH_F64 ? (const void*)ctx->U64 : ctx->U;
+  TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, o->ell, o->rtol, o->maxit,
                       ctx->d, &iters, &relres));
   CK(cudaEventRecord(ctx->ev[4], ctx->stream));
   // Alg. 1 line 4: Armijo backtracking along theta - alpha d
@@ -579,7 +683,6 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   inf.pcg_iters = iters;
   inf.armijo_trials = trials;
   inf.status = 0;
-  inf.jacobi_sweeps = ctx->last_sweeps;
   inf.ms_linearize = ev_ms(ctx, 0, 1);
   inf.ms_sketch = ev_ms(ctx, 1, 2);
   inf.ms_factor = ev_ms(ctx, 2, 3);
@@ -710,7 +813,7 @@ ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
   if (dalloc(ctx, &ctx->J, (size_t)ctx->jrows * ctx->ldJ * ctx->elt) != NGD_OK) return fail(NGD_ERR_OOM);
   if (ctx->tape_allowed && dalloc(ctx, &ctx->tape, tbytes) != NGD_OK) return fail(NGD_ERR_OOM);
   if (dalloc(ctx, &ctx->prep, net.prep_size * ctx->elt) != NGD_OK || dalloc(ctx, &ctx->prep_t, net.prep_size * ctx->elt) != NGD_OK ||
-      dalloc(ctx, &ctx->vT, ctx->ldJ * ctx->elt) != NGD_OK || dalloc(ctx, &ctx->r, N * 8) != NGD_OK ||
+      dalloc(ctx, &ctx->vT, 2 * ctx->ldJ * ctx->elt) != NGD_OK || dalloc(ctx, &ctx->r, N * 8) != NGD_OK ||
       dalloc(ctx, &ctx->svec, N * 8) != NGD_OK || dalloc(ctx, &ctx->tvec, N * 8) != NGD_OK ||
       dalloc(ctx, &ctx->lpart, N * 8) != NGD_OK || dalloc(ctx, &ctx->part, kRedBlocks * 8) != NGD_OK ||
       dalloc(ctx, &ctx->colpart, (size_t)ctx->colsplit * ctx->ldJ * 8) != NGD_OK ||
@@ -719,8 +822,7 @@ ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
       dalloc(ctx, &ctx->rr, p * 8) != NGD_OK || dalloc(ctx, &ctx->z, p * 8) != NGD_OK ||
       dalloc(ctx, &ctx->pv, p * 8) != NGD_OK || dalloc(ctx, &ctx->q, p * 8) != NGD_OK ||
       dalloc(ctx, &ctx->g, p * 8) != NGD_OK || dalloc(ctx, &ctx->d, p * 8) != NGD_OK ||
-      dalloc(ctx, &ctx->theta_trial, p * 8) != NGD_OK || dalloc(ctx, &ctx->jac_cnt, 16) != NGD_OK ||
-      dalloc(ctx, &ctx->jac_info, 16) != NGD_OK)
+      dalloc(ctx, &ctx->theta_trial, p * 8) != NGD_OK)
     return fail(NGD_ERR_OOM);
   if (cudaMallocHost((void**)&ctx->h_scal, kSCount * 8) != cudaSuccess ||
       cudaMallocHost((void**)&ctx->h_int, 16 * sizeof(int)) != cudaSuccess ||
@@ -744,7 +846,7 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->lpart, ctx->colpart, ctx->scal, ctx->status, ctx->pcg, ctx->x, ctx->rr, ctx->z, ctx->pv, ctx->q,
                  ctx->g, ctx->d, ctx->theta_trial, ctx->Om, ctx->Y, ctx->B, ctx->U, ctx->Lr, ctx->VsT, ctx->Zw, ctx->M,
                  ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
-                 ctx->perm, ctx->jac_cnt, ctx->jac_info};
+                 ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -865,8 +967,6 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
   if (!valid_prec(prec)) return set_err(ctx, NGD_ERR_INVALID_ARG, "bad sketch precision%s");
   if (ctx->dtype == NGD_F64 && prec != NGD_SKETCH_F64)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
-  if (ctx->dtype == NGD_F32 && prec == NGD_SKETCH_F64)
-    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F32 context has no F64 sketch%s");
   return by_dtype(ctx, [&](auto z) -> ngd_status {
     using T = decltype(z);
     if (theta) TRY(linearize<T>(ctx, theta));
@@ -875,7 +975,11 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
     TRY(sync_status(ctx));
     const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
     CK(cudaMemcpy2DAsync(Omega, w, ctx->Om, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpy2DAsync(Y, w, ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+      CK(cudaMemcpy2DAsync(Y, (size_t)ctx->p * 8, ctx->Y64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemcpy2DAsync(Y, w, ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
     return check_launch(ctx);
   });
 }
@@ -891,9 +995,17 @@ ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const vo
     TRY(ensure_ell(ctx, ell));
     const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
     CK(cudaMemcpy2DAsync(ctx->Om, sp, Omega, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpy2DAsync(ctx->Y, sp, Y, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+      CK(cudaMemcpy2DAsync(ctx->Y64, (size_t)ctx->ldP * 8, Y, (size_t)ctx->p * 8, (size_t)ctx->p * 8, ell,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemcpy2DAsync(ctx->Y, sp, Y, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
     TRY(factor_internal<T>(ctx, ell, prec, shift_scale));
-    CK(cudaMemcpy2DAsync(U, w, ctx->U, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+      CK(cudaMemcpy2DAsync(U, (size_t)ctx->p * 8, ctx->U64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemcpy2DAsync(U, w, ctx->U, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(lam, ctx->lam, ell * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     if (nu_out) {
       CK(cudaMemcpyAsync(ctx->h_scal + kSNu, ctx->scal + kSNu, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -904,33 +1016,36 @@ ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const vo
   });
 }
 
-ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, const double* lam, double mu, const double* v,
-                             double* zout) {
+static bool valid_u_dtype(ngd_ctx* ctx, int u_dtype) {
+  return u_dtype == NGD_F64 || (u_dtype == NGD_F32 && ctx->dtype == NGD_F32);
+}
+
+ngd_status ngd_precond_apply(ngd_ctx* ctx, int ell, const void* U, int u_dtype, const double* lam, double mu,
+                             const double* v, double* zout) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!U || !lam || !v || !zout || v == zout) return set_err(ctx, NGD_ERR_INVALID_ARG, "NULL or aliased argument%s");
   if (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048) || !(mu >= 0.0))
     return set_err(ctx, NGD_ERR_INVALID_ARG, "ell/mu out of range%s");
-  return by_dtype(ctx, [&](auto z) -> ngd_status {
-    using T = decltype(z);
-    TRY(ensure_ell(ctx, ell));
-    launch_precond<T>((const T*)U, ctx->p, ctx->p, ell, lam, mu, nullptr, v, zout, ctx->w1, nullptr, ctx->stream);
-    return check_launch(ctx);
-  });
+  if (!valid_u_dtype(ctx, u_dtype)) return set_err(ctx, NGD_ERR_INVALID_ARG, "bad U dtype%s");
+  TRY(ensure_ell(ctx, ell));
+  precond(ctx, u_dtype == NGD_F64, U, ctx->p, ell, lam, mu, nullptr, v, zout, nullptr);
+  return check_launch(ctx);
 }
 
-ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, double mu, const void* U,
+ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, double mu, const void* U, int u_dtype,
                          const double* lam, int ell, double rtol, int maxit, double* dout, int* iters, double* relres) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!g || !dout || dout == g) return set_err(ctx, NGD_ERR_INVALID_ARG, "g/d NULL or aliased%s");
   if (!(mu > 0.0) || !(rtol >= 0.0) || maxit < 0) return set_err(ctx, NGD_ERR_INVALID_ARG, "mu/rtol/maxit%s");
-  if (U && (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048) || !lam))
-    return set_err(ctx, NGD_ERR_INVALID_ARG, "ell/lam%s");
+  if (U && (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048) || !lam || !valid_u_dtype(ctx, u_dtype)))
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "ell/lam/U dtype%s");
   return by_dtype(ctx, [&](auto z) -> ngd_status {
     using T = decltype(z);
     if (theta) TRY(linearize<T>(ctx, theta));
     if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
     if (U) TRY(ensure_ell(ctx, ell));
-    return pcg_internal<T>(ctx, g, mu, nullptr, U, ctx->p, lam, U ? ell : 0, rtol, maxit, dout, iters, relres);
+    return pcg_internal<T>(ctx, g, mu, nullptr, U, u_dtype == NGD_F64, ctx->p, lam, U ? ell : 0, rtol, maxit, dout,
+                           iters, relres);
   });
 }
 
@@ -940,8 +1055,8 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
   if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
       !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
-  if ((ctx->dtype == NGD_F64) != (o->sketch == NGD_SKETCH_F64))
-    return set_err(ctx, NGD_ERR_INVALID_ARG, "sketch precision does not match the context dtype%s");
+  if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
   return by_dtype(ctx, [&](auto z) -> ngd_status {
     using T = decltype(z);
     return step_impl<T>(ctx, theta, o, info);

@@ -1,8 +1,7 @@
 // Dense kernels of the NGD hot path: deterministic reductions, the stored-Jacobian
 // Gramian matvec, preconditioned-CG vector updates, the Nystrom preconditioner, the
 // Philox Gaussian test matrix, a tiled SIMT GEMM (FP64 / FP32 with FP64 cross-tile
-// sums), the row-wise triangular solve and the FP64 l x l core (blocked Cholesky,
-// cyclic Jacobi eigen-solver).
+// sums), the row-wise triangular solve and the FP64 blocked Cholesky of the l x l core.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -87,6 +86,24 @@ void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s) 
 }
 template void launch_d2t<float>(const double*, float*, int64_t, int64_t, cudaStream_t);
 template void launch_d2t<double>(const double*, double*, int64_t, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------- double-float helpers
+struct DF {  // unevaluated sum hi + lo
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float pe = fmaf(a, bh, -p);      // exact error of the product
+  const float t = s.hi + p;              // TwoSum(s.hi, p)
+  const float z = t - s.hi;
+  const float e = (s.hi - (t - z)) + (p - z);
+  s.hi = t;
+  s.lo += e + pe + a * bl;
+}
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
 
 // ---------------------------------------------------------------------------- stored-J matvec
 // t[n] = sum_j J[n, j] v[j] (v already in the working dtype, zero-padded to ldJ),
@@ -192,6 +209,97 @@ template void launch_coldot<float>(const float*, int64_t, int64_t, const double*
                                    cudaStream_t);
 template void launch_coldot<double>(const double*, int64_t, int64_t, const double*, double*, int, const int*,
                                     cudaStream_t);
+
+// FP32 Jacobian with FP64-accurate sums.  In the directions of G's small eigenvalues the
+// matvec is a sum of terms that cancel to ~mu / lambda_1 of their size (1e-9 for the 5-D
+// Poisson workload after a few steps), so FP32 accumulation noise (~1e-7 of the terms) hides
+// those directions from CG and it stalls.  Each FP32 product is made exact with fmaf and the
+// products are summed as double-float pairs (TwoSum), which costs ~11 FP32 operations per
+// Jacobian element and keeps the kernels bound by HBM, not by the scarce FP64 units.
+__global__ void k_split_df(const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo, int64_t n,
+                           int64_t npad) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += st) {
+    float h = 0.f, l = 0.f;
+    if (i < n) split_df(x[i], h, l);
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+void launch_split_df(const double* x, float* hi, float* lo, int64_t n, int64_t npad, cudaStream_t s) {
+  k_split_df<<<(int)std::min<int64_t>((npad + 255) / 256, 2048), 256, 0, s>>>(x, hi, lo, n, npad); note_launch();
+}
+
+__device__ __forceinline__ void df_add4(DF& acc, const float4& a, const float4& bh, const float4& bl) {
+  df_add_prod(acc, a.x, bh.x, bl.x);
+  df_add_prod(acc, a.y, bh.y, bl.y);
+  df_add_prod(acc, a.z, bh.z, bl.z);
+  df_add_prod(acc, a.w, bh.w, bl.w);
+}
+
+__global__ void __launch_bounds__(256) k_rowdot_df(const float* __restrict__ J, int64_t ldJ, int64_t nrows,
+                                                   const float* __restrict__ vh, const float* __restrict__ vl,
+                                                   const double* __restrict__ w, double* __restrict__ t_out,
+                                                   double* __restrict__ s_out, const int* __restrict__ done) {
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nv = ldJ / 4;
+  const float4* __restrict__ h4 = reinterpret_cast<const float4*>(vh);
+  const float4* __restrict__ l4 = reinterpret_cast<const float4*>(vl);
+  for (int64_t row = warp; row < nrows; row += nwarps) {
+    const float4* __restrict__ jr = reinterpret_cast<const float4*>(J + row * ldJ);
+    DF a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+    int64_t k = lane;
+    for (; k + 32 < nv; k += 64) {
+      df_add4(a0, jr[k], h4[k], l4[k]);
+      df_add4(a1, jr[k + 32], h4[k + 32], l4[k + 32]);
+    }
+    if (k < nv) df_add4(a0, jr[k], h4[k], l4[k]);
+    const double tsum = wsum(((double)a0.hi + (double)a0.lo) + ((double)a1.hi + (double)a1.lo));
+    if (lane == 0) {
+      if (t_out) t_out[row] = tsum;
+      if (s_out) s_out[row] = w ? w[row] * tsum : tsum;
+    }
+  }
+}
+
+void launch_rowdot_df(const float* J, int64_t ldJ, int64_t nrows, const float* vh, const float* vl, const double* w,
+                      double* t_out, double* s_out, const int* done, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((nrows * 32 + 255) / 256, 152 * 16);
+  k_rowdot_df<<<blocks, 256, 0, s>>>(J, ldJ, nrows, vh, vl, w, t_out, s_out, done); note_launch();
+}
+
+__global__ void __launch_bounds__(256) k_coldot_df(const float* __restrict__ J, int64_t ldJ, int64_t nrows,
+                                                   const double* __restrict__ sv, double* __restrict__ part,
+                                                   int64_t rows_per_split, const int* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (col >= ldJ) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r1 = min(nrows, r0 + rows_per_split);
+  DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int64_t n = r0; n < r1; ++n) {
+    float sh, sl;
+    split_df(sv[n], sh, sl);
+    const float4 jv = *reinterpret_cast<const float4*>(J + n * ldJ + col);
+    df_add_prod(acc[0], jv.x, sh, sl);
+    df_add_prod(acc[1], jv.y, sh, sl);
+    df_add_prod(acc[2], jv.z, sh, sl);
+    df_add_prod(acc[3], jv.w, sh, sl);
+  }
+  double* pp = part + (int64_t)blockIdx.y * ldJ + col;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) pp[e] = (double)acc[e].hi + (double)acc[e].lo;
+}
+
+void launch_coldot_df(const float* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
+                      const int* done, cudaStream_t st) {
+  const int64_t rps = (nrows + nsplit - 1) / nsplit;
+  dim3 grid((unsigned)((ldJ / 4 + 255) / 256), (unsigned)nsplit);
+  k_coldot_df<<<grid, 256, 0, st>>>(J, ldJ, nrows, s_vec, part, rps, done); note_launch();
+}
 
 // y[j] = (accumulate ? y[j] : 0) + sum_split part[split][j] + mu v[j]   (mu from device or host)
 __global__ void k_coldot_finish(const double* __restrict__ part, int nsplit, int64_t p, int64_t ld_part,
@@ -390,23 +498,6 @@ void launch_dot(const double* a, const double* b, int64_t n, double* part, doubl
 // with double-float (FP32 pair) accumulation: each FP32 product is split exactly with fmaf and
 // summed by TwoSum (Knuth), which keeps ~2^-44 relative accuracy on the FP32 pipes instead of the
 // scarce FP64 units.  FP64 U (double) uses FP64 arithmetic.
-struct DF {  // unevaluated sum hi + lo
-  float hi, lo;
-};
-__device__ __forceinline__ void df_add_prod(DF& s, float a, float bh, float bl) {
-  const float p = a * bh;
-  const float pe = fmaf(a, bh, -p);      // exact error of the product
-  const float t = s.hi + p;              // TwoSum(s.hi, p)
-  const float z = t - s.hi;
-  const float e = (s.hi - (t - z)) + (p - z);
-  s.hi = t;
-  s.lo += e + pe + a * bl;
-}
-__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
-}
-
 // w1[j] = sum_i U[i, j] v[i], four columns per block.
 __global__ void __launch_bounds__(256) k_utv_f(const float* __restrict__ U, int64_t ld, int64_t p, int ell,
                                                const double* __restrict__ v, double* __restrict__ w1,
@@ -693,6 +784,129 @@ int gemm_splits(const GemmArgs<float>& g) {  // number of z-slices launch_gemm w
   return (int)std::max<int64_t>(1, (g.K + kps - 1) / kps);
 }
 
+// ---------------------------------------------------------------------------- double-float GEMM
+// FP64-accurate C(m,n) = sum_k A(m,k) B(k,n) on the FP32 pipes (same strides as k_gemm).  Float
+// operands are exact FP32 values; double operands are split into FP32 hi + lo on load.  Every
+// product hi*hi is made exact with fmaf and summed by TwoSum; the cross terms hi*lo, lo*hi go
+// into the low word.  Relative accuracy ~2^-44 per term, at ~10-14 FP32 operations per
+// multiply-add instead of one FMA on the scarce FP64 units.
+template <typename T> struct IsDouble { static constexpr bool v = false; };
+template <> struct IsDouble<double> { static constexpr bool v = true; };
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_gemm_df(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A,
+                                                 int64_t sam, int64_t sak, const TB* __restrict__ B, int64_t sbk,
+                                                 int64_t sbn, int64_t k_per_split, double* __restrict__ out64,
+                                                 int64_t split_stride, float* __restrict__ out32, int64_t scm,
+                                                 int64_t scn, const double* __restrict__ rowscale,
+                                                 const double* __restrict__ colscale, int accumulate) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr bool AL = IsDouble<TA>::v, BL = IsDouble<TB>::v;
+  __shared__ float Ah[BK][BM + 1];
+  __shared__ float Al[AL ? BK : 1][AL ? BM + 1 : 1];
+  __shared__ float Bh[BK][BN + 1];
+  __shared__ float Bl[BL ? BK : 1][BL ? BN + 1 : 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kb = (int64_t)blockIdx.z * k_per_split;
+  const int64_t ke = min(K, kb + k_per_split);
+  DF acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.f, 0.f};
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int mm, kk;
+      if (sak == 1) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      const TA x = (gm < M && gk < ke) ? A[gm * sam + gk * sak] : TA(0);
+      if constexpr (AL) {
+        float h, l;
+        split_df((double)x, h, l);
+        Ah[kk][mm] = h;
+        Al[kk][mm] = l;
+      } else {
+        Ah[kk][mm] = (float)x;
+      }
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      int kk, nn;
+      if (sbk == 1) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      const TB x = (gn < N && gk < ke) ? B[gk * sbk + gn * sbn] : TB(0);
+      if constexpr (BL) {
+        float h, l;
+        split_df((double)x, h, l);
+        Bh[kk][nn] = h;
+        Bl[kk][nn] = l;
+      } else {
+        Bh[kk][nn] = (float)x;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      float ah[4], bh[4], al[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Ah[kk][ty + 16 * i];
+        bh[i] = Bh[kk][tx + 16 * i];
+        al[i] = AL ? Al[kk][ty + 16 * i] : 0.f;
+        bl[i] = BL ? Bl[kk][tx + 16 * i] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          DF& s = acc[i][j];
+          const float p = ah[i] * bh[j];
+          float lo = fmaf(ah[i], bh[j], -p);           // exact error of the product
+          if constexpr (BL) lo = fmaf(ah[i], bl[j], lo);
+          if constexpr (AL) lo = fmaf(al[i], bh[j], lo);
+          const float t = s.hi + p;                    // TwoSum(s.hi, p)
+          const float z = t - s.hi;
+          s.lo += ((s.hi - (t - z)) + (p - z)) + lo;
+          s.hi = t;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+    const double rs = rowscale ? rowscale[gm] : 1.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double v = ((double)acc[i][j].hi + (double)acc[i][j].lo) * rs;
+      if (colscale) v *= colscale[gn];
+      if (out64) {
+        double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
+        *o = accumulate ? *o + v : v;
+      } else {
+        out32[gm * scm + gn * scn] = (float)v;
+      }
+    }
+  }
+}
+
+template <typename TA, typename TB>
+void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s) {
+  const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : std::max<int64_t>(g.K, 1);
+  const int nz = (int)((g.K + kps - 1) / kps);
+  dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)std::max(nz, 1));
+  k_gemm_df<TA, TB><<<grid, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.sam, g.sak, g.B, g.sbk, g.sbn, kps, g.out64,
+                                         g.split_stride, g.out32, g.scm, g.scn, g.rowscale, g.colscale,
+                                         g.accumulate); note_launch();
+}
+template void launch_gemm_df<float, float>(const GemmDfArgs<float, float>&, cudaStream_t);
+template void launch_gemm_df<float, double>(const GemmDfArgs<float, double>&, cudaStream_t);
+template void launch_gemm_df<double, double>(const GemmDfArgs<double, double>&, cudaStream_t);
+template void launch_gemm_df<double, float>(const GemmDfArgs<double, float>&, cudaStream_t);
+
 // out[i] = sum_z part[z*stride + i] for i < n  (ordered, deterministic)
 __global__ void k_sum_splits(const double* __restrict__ part, int nz, int64_t stride, int64_t n,
                              double* __restrict__ out) {
@@ -792,6 +1006,24 @@ template void launch_shift_add<float>(const float*, const float*, const double*,
                                       cudaStream_t);
 template void launch_shift_add<double>(const double*, const double*, const double*, double*, int64_t, int64_t, int,
                                        cudaStream_t);
+
+// dst (double) = Y (double) + nu Om (float), p x ell column-major, padding rows zero
+__global__ void k_shift_add_mixed(const double* __restrict__ Y, const float* __restrict__ Om,
+                                  const double* __restrict__ nu, double* __restrict__ dst, int64_t ld, int64_t p,
+                                  int ell) {
+  const double nv = *nu;
+  const int64_t n = ld * ell;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int64_t i = e % ld;
+    dst[e] = i < p ? Y[e] + nv * (double)Om[e] : 0.0;
+  }
+}
+void launch_shift_add_mixed(const double* Y, const float* Om, const double* nu, double* dst, int64_t ld, int64_t p,
+                            int ell, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((ld * ell + 255) / 256, 8192);
+  k_shift_add_mixed<<<blocks, 256, 0, s>>>(Y, Om, nu, dst, ld, p, ell); note_launch();
+}
 
 // M = (M + M^T) / 2 in place (n x n column-major)
 __global__ void k_symmetrize(double* M, int n) {
@@ -977,178 +1209,6 @@ cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s) {
   void* args[] = {&A, &n, &status};
   note_launch();
   return cudaLaunchCooperativeKernel((const void*)k_cholesky, blocks, 256, args, 0, s);
-}
-
-// ---------------------------------------------------------------------------- FP64 cyclic Jacobi
-// Two-sided cyclic Jacobi on the symmetric n x n matrix in A0 (column-major), parallel
-// (round-robin / circle) ordering: every round rotates n2/2 disjoint pairs (p, q) at once.
-// Each block recomputes the round's rotations (Golub-Van Loan sym. Schur 2x2:
-// tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2),
-// s = t c), then updates its share of the 2x2 blocks A[{p_k,q_k}, {p_k',q_k'}] <- J_k^T A J_k'
-// from the current buffer into the other buffer, and rotates the column pairs of V in place.
-// A pair is skipped when |a_pq| <= tol sqrt(|a_pp a_qq|) or |a_pq| <= tol_abs_rel trace(A) (the
-// eigenvalues are then accurate to ~eps ||A||, the accuracy of an SVD of B); the sweeps stop when
-// a whole sweep skips every pair, or after max_sweeps.  Eigenvalues end on the diagonal of the buffer
-// reported in *final_buf (0 or 1).
-__device__ __forceinline__ int rr_index(int pos, int r, int n2) {
-  return pos == 0 ? 0 : 1 + (pos - 1 + r) % (n2 - 1);
-}
-
-__global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A0, double* __restrict__ A1,
-                                                double* __restrict__ V, int n, int max_sweeps, double tol,
-                                                double tol_abs_rel, unsigned int* __restrict__ counters,
-                                                int* __restrict__ final_buf, int* __restrict__ sweeps_out) {
-  cg::grid_group grid = cg::this_grid();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n2 = n + (n & 1);
-  const int npairs = n2 / 2;
-  double* cs = reinterpret_cast<double*>(smem_raw);  // [npairs] c
-  double* sn = cs + npairs;                          // [npairs] s
-  int* pi = reinterpret_cast<int*>(sn + npairs);     // [npairs] p
-  int* qi = pi + npairs;                             // [npairs] q
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  // V = I; absolute skip threshold = tol_abs_rel * trace(A) (a bound on ||A||_2 for the PSD input)
-  for (int64_t e = gtid; e < (int64_t)n * n; e += gthreads) V[e] = (e % n == e / n) ? 1.0 : 0.0;
-  __shared__ double s_tr;
-  if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += fabs(A0[i + (int64_t)i * n]);
-    s_tr = tr;
-  }
-  __syncthreads();
-  const double tol_abs = tol_abs_rel * s_tr;
-  if (gtid == 0) {
-    counters[0] = 0u;
-    counters[1] = 0u;
-  }
-  grid.sync();
-  double* cur = A0;
-  double* nxt = A1;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    unsigned int* cnt = counters + (sweep & 1);
-    if (gtid == 0) counters[(sweep + 1) & 1] = 0u;
-    for (int r = 0; r < n2 - 1; ++r) {
-      // rotations of this round (every block computes all of them)
-      for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
-        int p = rr_index(k, r, n2), q = rr_index(n2 - 1 - k, r, n2);
-        if (p > q) {
-          const int t = p; p = q; q = t;
-        }
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          const double app = cur[p + (int64_t)p * n], aqq = cur[q + (int64_t)q * n], apq = cur[p + (int64_t)q * n];
-          if (fabs(apq) > tol_abs && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-            if (blockIdx.x == 0) atomicAdd(cnt, 1u);
-          }
-        }
-        cs[k] = c;
-        sn[k] = s;
-        pi[k] = p;
-        qi[k] = q;
-      }
-      __syncthreads();
-      // 2x2 block updates: block (k, k2) covers rows {p_k, q_k} and columns {p_k2, q_k2}
-      const int64_t nblk = (int64_t)npairs * npairs;
-      for (int64_t e = gtid; e < nblk; e += gthreads) {
-        // consecutive threads take consecutive row pairs of one column pair: the round-robin
-        // indices of neighbouring pairs are neighbours, so the loads and stores coalesce
-        const int k2 = (int)(e / npairs), k = (int)(e - (int64_t)k2 * npairs);
-        const int p = pi[k], q = qi[k], p2 = pi[k2], q2 = qi[k2];
-        const bool qok = q < n, q2ok = q2 < n;
-        const double c = cs[k], s = sn[k], c2 = cs[k2], s2 = sn[k2];
-        const double a00 = cur[p + (int64_t)p2 * n];
-        const double a01 = q2ok ? cur[p + (int64_t)q2 * n] : 0.0;
-        const double a10 = qok ? cur[q + (int64_t)p2 * n] : 0.0;
-        const double a11 = (qok && q2ok) ? cur[q + (int64_t)q2 * n] : 0.0;
-        // rows: J_k^T X
-        const double b00 = c * a00 - s * a10, b01 = c * a01 - s * a11;
-        const double b10 = s * a00 + c * a10, b11 = s * a01 + c * a11;
-        // columns: (.) J_k2
-        double y00 = c2 * b00 - s2 * b01, y01 = s2 * b00 + c2 * b01;
-        double y10 = c2 * b10 - s2 * b11, y11 = s2 * b10 + c2 * b11;
-        if (k == k2 && s != 0.0) {
-          y01 = 0.0;
-          y10 = 0.0;
-        }
-        nxt[p + (int64_t)p2 * n] = y00;
-        if (q2ok) nxt[p + (int64_t)q2 * n] = y01;
-        if (qok) nxt[q + (int64_t)p2 * n] = y10;
-        if (qok && q2ok) nxt[q + (int64_t)q2 * n] = y11;
-      }
-      // eigenvector columns: V[:, p], V[:, q]
-      const int64_t nv = (int64_t)npairs * n;
-      for (int64_t e = gtid; e < nv; e += gthreads) {
-        const int k = (int)(e / n), i = (int)(e - (int64_t)k * n);
-        const double s = sn[k];
-        if (s == 0.0) continue;
-        const int p = pi[k], q = qi[k];
-        const double c = cs[k];
-        const double vp = V[i + (int64_t)p * n], vq = V[i + (int64_t)q * n];
-        V[i + (int64_t)p * n] = c * vp - s * vq;
-        V[i + (int64_t)q * n] = s * vp + c * vq;
-      }
-      grid.sync();
-      double* t = cur; cur = nxt; nxt = t;
-    }
-    const unsigned int rotated = *((volatile unsigned int*)cnt);
-    grid.sync();
-    if (rotated == 0u) break;
-  }
-  if (gtid == 0) {
-    *final_buf = (cur == A0) ? 0 : 1;
-    *sweeps_out = sweep;
-  }
-}
-
-cudaError_t launch_jacobi(double* A0, double* A1, double* V, int n, int max_sweeps, double tol,
-                          double tol_abs_rel, unsigned int* counters, int* final_buf, int* sweeps,
-                          cudaStream_t s) {
-  const int n2 = n + (n & 1);
-  const size_t smem = (size_t)(n2 / 2) * (2 * sizeof(double) + 2 * sizeof(int));
-  cudaFuncSetAttribute((const void*)k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int blocks = coop_blocks((const void*)k_jacobi, 256, smem);
-  void* args[] = {&A0, &A1, &V, &n, &max_sweeps, &tol, &tol_abs_rel, &counters, &final_buf, &sweeps};
-  note_launch();
-  return cudaLaunchCooperativeKernel((const void*)k_jacobi, blocks, 256, args, smem, s);
-}
-
-// Sort the eigenpairs by decreasing eigenvalue: sig2[rank(j)] = diag(Afin)[j],
-// Vs[:, rank(j)] = V[:, j] (ties broken by index, so the permutation is deterministic).
-__global__ void k_eig_rank(const double* __restrict__ Afin, int n, double* __restrict__ sig2, int* __restrict__ dst) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* ev = reinterpret_cast<double*>(smem_raw);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = Afin[i + (int64_t)i * n];
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int rank = 0;
-    const double vi = ev[i];
-    for (int j = 0; j < n; ++j) {
-      const double vj = ev[j];
-      rank += (vj > vi) || (vj == vi && j < i);
-    }
-    dst[i] = rank;
-    sig2[rank] = vi;
-  }
-}
-__global__ void k_eig_gather(const double* __restrict__ V, int n, const int* __restrict__ dst, double* __restrict__ Vs) {
-  const int64_t total = (int64_t)n * n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int src = (int)(e / n), i = (int)(e - (int64_t)src * n);
-    Vs[i + (int64_t)dst[src] * n] = V[e];
-  }
-}
-void launch_eig_sort(const double* Afin, const double* V, int n, double* sig2, double* Vs, int* perm, cudaStream_t s) {
-  const size_t smem = (size_t)n * sizeof(double);
-  k_eig_rank<<<1, 1024, smem, s>>>(Afin, n, sig2, perm); note_launch();
-  const int blocks = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
-  k_eig_gather<<<blocks, 256, 0, s>>>(V, n, perm, Vs); note_launch();
 }
 
 // W = V diag(1/sigma) (column scale), lam = max(0, sigma^2 - nu) and 1/sigma for the U GEMM.

@@ -28,6 +28,21 @@ template <typename T> struct GemmArgs {
   int accumulate = 0;                 // out64 += result instead of out64 = result (nsplit must be 1)
 };
 
+// FP64-accurate (double-float) SIMT GEMM, operands float or double, FP64 or FP32 output.
+template <typename TA, typename TB> struct GemmDfArgs {
+  int64_t M = 0, N = 0, K = 0;
+  const TA* A = nullptr; int64_t sam = 0, sak = 0;
+  const TB* B = nullptr; int64_t sbk = 0, sbn = 0;
+  int nsplit = 1;
+  double* out64 = nullptr; int64_t split_stride = 0;
+  float* out32 = nullptr;
+  int64_t scm = 0, scn = 0;
+  const double* rowscale = nullptr;
+  const double* colscale = nullptr;
+  int accumulate = 0;
+};
+template <typename TA, typename TB> void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s);
+
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);
 template <typename T> void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s);
 
@@ -38,6 +53,12 @@ int coldot_nsplit(int64_t nrows, int64_t ldJ, int vn);
 template <typename T>
 void launch_coldot(const T* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
                    const int* done, cudaStream_t st);
+// FP32 Jacobian, FP64-accurate sums (exact FP32 products, double-float accumulation)
+void launch_split_df(const double* x, float* hi, float* lo, int64_t n, int64_t npad, cudaStream_t s);
+void launch_rowdot_df(const float* J, int64_t ldJ, int64_t nrows, const float* vh, const float* vl, const double* w,
+                      double* t_out, double* s_out, const int* done, cudaStream_t s);
+void launch_coldot_df(const float* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
+                      const int* done, cudaStream_t st);
 void launch_coldot_finish(const double* part, int nsplit, int64_t p, int64_t ld_part, const double* v, double mu_h,
                           const double* mu_d, double* y, int accumulate, const int* done, cudaStream_t s);
 
@@ -72,14 +93,17 @@ template <typename T>
 void launch_shift_add(const T* src, const T* Om, const double* nu, T* dst, int64_t ld, int64_t p, int ell,
                       cudaStream_t s);
 void launch_symmetrize(double* M, int n, cudaStream_t s);
+void launch_shift_add_mixed(const double* Y, const float* Om, const double* nu, double* dst, int64_t ld, int64_t p,
+                            int ell, cudaStream_t s);
 
 template <typename T>
 void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* Lr, double* dinv, cudaStream_t s);
 cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s);
-cudaError_t launch_jacobi(double* A0, double* A1, double* V, int n, int max_sweeps, double tol,
-                          double tol_abs_rel, unsigned int* counters, int* final_buf, int* sweeps,
-                          cudaStream_t s);
-void launch_eig_sort(const double* Afin, const double* V, int n, double* sig2, double* Vs, int* perm, cudaStream_t s);
+// eigen.cu: FP64 symmetric eigen-decomposition (tridiagonal reduction, multisection, twisted
+// factorization, back-transform, CholeskyQR), eigenvalues decreasing.
+size_t sym_eig_workspace_doubles(int n);
+cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, double* ws, int* status,
+                           cudaStream_t s);
 void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* lam, double* inv_sigma,
                            cudaStream_t s);
 void launch_set_mu(const double* lam, double fixed_mu, double gamma, double* mu, cudaStream_t s);

@@ -58,7 +58,7 @@ class StepInfo(ctypes.Structure):
                 ("nu", ctypes.c_double), ("relres", ctypes.c_double), ("pcg_iters", ctypes.c_int),
                 ("armijo_trials", ctypes.c_int), ("shift_retries", ctypes.c_int), ("status", ctypes.c_int),
                 ("ms_linearize", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_factor", ctypes.c_double),
-                ("ms_pcg", ctypes.c_double), ("ms_linesearch", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int)]
+                ("ms_pcg", ctypes.c_double), ("ms_linesearch", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,8 +84,8 @@ _SIGS = {
     "ngd_gramian_mv": ([_P, _P, _P, _D, _P], _I),
     "ngd_nystrom_sketch": ([_P, _P, _I, _U64, _U64, _I, _P, _P], _I),
     "ngd_nystrom_factor": ([_P, _I, _P, _P, _I, _D, _P, _P, ctypes.POINTER(_D)], _I),
-    "ngd_precond_apply": ([_P, _I, _P, _P, _D, _P, _P], _I),
-    "ngd_pcg_solve": ([_P, _P, _P, _D, _P, _P, _I, _D, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "ngd_precond_apply": ([_P, _I, _P, _I, _P, _D, _P, _P], _I),
+    "ngd_pcg_solve": ([_P, _P, _P, _D, _P, _I, _P, _I, _D, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "ngd_step": ([_P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(StepInfo)], _I),
     "ngd_default_step_opts": ([ctypes.POINTER(StepOpts)], None),
     "ngd_kernel_launches": ([], ctypes.c_uint64),
@@ -184,17 +184,21 @@ def ngd_nystrom_factor(h, ell, Omega, Y, prec, shift_scale, U, lam):
     return nu.value
 
 
+def _u_dtype(U):
+    return DTYPES["f64"] if U is None or U.dtype == torch.float64 else DTYPES["f32"]
+
+
 def ngd_precond_apply(h, ell, U, lam, mu, v, z):
     lib().ngd_set_stream(h, _stream())
-    _check(h, lib().ngd_precond_apply(h, int(ell), _ptr(U), _ptr(lam), float(mu), _ptr(v), _ptr(z)))
+    _check(h, lib().ngd_precond_apply(h, int(ell), _ptr(U), _u_dtype(U), _ptr(lam), float(mu), _ptr(v), _ptr(z)))
 
 
 def ngd_pcg_solve(h, theta, g, mu, U, lam, ell, rtol, maxit, d):
     lib().ngd_set_stream(h, _stream())
     iters = ctypes.c_int(0)
     relres = ctypes.c_double(0.0)
-    _check(h, lib().ngd_pcg_solve(h, _ptr(theta), _ptr(g), float(mu), _ptr(U), _ptr(lam), int(ell), float(rtol),
-                                  int(maxit), _ptr(d), ctypes.byref(iters), ctypes.byref(relres)))
+    _check(h, lib().ngd_pcg_solve(h, _ptr(theta), _ptr(g), float(mu), _ptr(U), _u_dtype(U), _ptr(lam), int(ell),
+                                  float(rtol), int(maxit), _ptr(d), ctypes.byref(iters), ctypes.byref(relres)))
     return iters.value, relres.value
 
 
@@ -291,7 +295,7 @@ class Context:
 
     def nystrom_sketch(self, theta, ell, seed=0, step=0, prec="f64"):
         Om = torch.empty((ell, self.p), dtype=self.wdtype, device=self.device)   # column-major p x ell
-        Y = torch.empty_like(Om)
+        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
         ngd_nystrom_sketch(self.handle, theta, ell, seed, step, prec, Om, Y)
         if theta is not None:
             self.version += 1
@@ -299,8 +303,8 @@ class Context:
 
     def nystrom_factor(self, ell, Omega, Y, prec="f64", shift_scale=1.0):
         _need(Omega, self.wdtype, self.p * ell, "Omega")
-        _need(Y, self.wdtype, self.p * ell, "Y")
-        U = torch.empty((ell, self.p), dtype=self.wdtype, device=self.device)
+        _need(Y, torch.float64 if prec == "f64" else self.wdtype, self.p * ell, "Y")
+        U = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
         lam = self._vec(ell)
         nu = ngd_nystrom_factor(self.handle, ell, Omega, Y, prec, shift_scale, U, lam)
         return U, lam, nu

@@ -169,7 +169,25 @@ def test_sketch_matches_oracle(ngd, prec, tol):
     ctx.close()
 
 
-@pytest.mark.parametrize("dtype,prec", [("f64", "f64"), ("f32", "f32")])
+@pytest.mark.parametrize("prec,sym_tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_sketch_core_symmetry_fp32_context(ngd, prec, sym_tol):
+    """In an FP32 context the double-float sketch keeps Omega^T Y = Omega^T G Omega symmetric far
+    below FP32 rounding: G = J^T W J of the stored FP32 Jacobian is an exactly symmetric operator.
+    The FP32 pair carries 48 significant bits; its low word is summed in FP32 over the K = N
+    products, so the error grows like K u32^2 (~1e-13 relative at N = 1120; FP64 BLAS: ~1e-15).
+    FP32 arithmetic breaks the symmetry at its own rounding level."""
+    wl, pr, th = _workload("poisson5d", 900, 220)
+    ctx = ngd.Context(pr, dtype="f32")
+    Om, Y = ctx.nystrom_sketch(dev(th), 96, seed=4, step=0, prec=prec)
+    O, Yh = host(Om).T, host(Y).T
+    M = O.T @ Yh
+    assert np.linalg.norm(M - M.T) / np.linalg.norm(M) <= sym_tol
+    J = mlp.jacobian(pr, th)
+    assert rel(Yh, J.T @ (pr.w[:, None] * (J @ O))) <= 1e-5      # against the FP64 oracle Jacobian
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype,prec", [("f64", "f64"), ("f32", "f32"), ("f32", "f64")])
 def test_factor_and_preconditioner_match_oracle(ngd, dtype, prec):
     wl, pr, th = _workload("poisson2d") if dtype == "f64" else _workload("poisson5d", 600, 150)
     ell = 60
@@ -179,27 +197,60 @@ def test_factor_and_preconditioner_match_oracle(ngd, dtype, prec):
     ctx = ngd.Context(pr, dtype=dtype)
     wd = torch.float64 if dtype == "f64" else torch.float32
     Om_d = torch.tensor(Om_o.T.copy(), dtype=wd, device="cuda")
-    Y_d = torch.tensor(Y_o.T.copy(), dtype=wd, device="cuda")
+    # Y is float64 for the FP64-accurate factor; the oracle's Y is exact for the rounded Omega
+    Om_r = host(Om_d).T
+    Y_r = J.T @ (pr.w[:, None] * (J @ Om_r))
+    Y_d = torch.tensor(Y_r.T.copy(), dtype=torch.float64 if prec == "f64" else wd, device="cuda")
     U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=prec)
     # the oracle factors the same (rounded) inputs
-    U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, nystrom.MANTISSA_BITS[prec])
+    U_o, lam_o, nu_o = nystrom.nystrom_factor(Om_r, host(Y_d).T, nystrom.MANTISSA_BITS[prec])
     assert abs(nu - nu_o) <= 1e-12 * nu_o
     lam_g = host(lam)
     top = lam_o > 1e-6 * lam_o[0]
     assert np.all(np.diff(lam_g) <= 0)
-    assert rel(lam_g[top], lam_o[top]) <= (1e-8 if dtype == "f64" else 1e-4)
+    assert rel(lam_g[top], lam_o[top]) <= (1e-8 if prec == "f64" else 1e-4)
     mu = 1e-6 if dtype == "f64" else 1e-4
     rng = np.random.default_rng(4)
     for _ in range(3):
         v = rng.standard_normal(pr.p)
         z = host(ctx.precond_apply(ell, U, lam, mu, dev(v)))
         z_o = nystrom.precond_apply(U_o, lam_o, mu, v)
-        assert rel(z, z_o) <= (1e-8 if dtype == "f64" else 2e-3)
+        # U is FP64 after an FP64-accurate factor; an F32 factor stores U in FP32
+        assert rel(z, z_o) <= (1e-8 if prec == "f64" else 2e-3)
     # the preconditioner apply itself on identical factors is exact up to rounding
     U64 = torch.tensor(U_o.T.copy(), dtype=wd, device="cuda")
     z = host(ctx.precond_apply(ell, U64, dev(lam_o), mu, dev(v)))
     z_o = nystrom.precond_apply(host(U64).T, lam_o, mu, v)
     assert rel(z, z_o) <= 1e-12    # FP64 arithmetic, or double-float accumulation over FP32 U
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_factor_eigen_edge_sizes(ngd, dtype):
+    """The l x l eigen-solver at sizes that hit its edge cases: l = 1, 2 (no Householder step),
+    3, and around the 32-wide tiles of the tridiagonal reduction."""
+    pr, th = small(SMALL[3], seed=31)          # heat, p = 4*12+12+12*9+9+9+1 = 187
+    J = mlp.jacobian(pr, th)
+    G = J.T @ (pr.w[:, None] * J)
+    ctx = ngd.Context(pr, dtype=dtype)
+    wd = torch.float64 if dtype == "f64" else torch.float32
+    mb = nystrom.MANTISSA_BITS[dtype]
+    rng = np.random.default_rng(8)
+    for ell in [1, 2, 3, 31, 32, 33, 64, 65, 97]:
+        Om = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 17, ell))
+        Om_d = torch.tensor(np.ascontiguousarray(Om.T), dtype=wd, device="cuda")
+        Y_d = torch.tensor(np.ascontiguousarray((G @ Om).T), dtype=wd, device="cuda")
+        U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=dtype)
+        U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, mb)
+        lam_g = host(lam)
+        top = lam_o > 1e-6 * lam_o[0]
+        assert rel(lam_g[top], lam_o[top]) <= (1e-9 if dtype == "f64" else 1e-4), ell
+        Ug = host(U).T[:, top]     # columns below the core's noise floor are only an orthonormal completion
+        assert np.abs(Ug.T @ Ug - np.eye(int(top.sum()))).max() <= (1e-10 if dtype == "f64" else 2e-5), ell
+        v = rng.standard_normal(pr.p)
+        mu = 1e-5
+        z = host(ctx.precond_apply(ell, U, lam, mu, dev(v)))
+        assert rel(z, nystrom.precond_apply(U_o, lam_o, mu, v)) <= (1e-8 if dtype == "f64" else 2e-3), ell
     ctx.close()
 
 
@@ -260,26 +311,27 @@ def test_ngd_step_matches_oracle_fp64(ngd):
 
 
 def test_ngd_step_fp32_paths(ngd):
-    """FP32 path: the F32 sketch converges to rtol; TF32 / BF16 sketches need a shift nu of their
-    unit roundoff, which truncates the captured spectrum (more PCG iterations, never a failure)."""
+    """FP32 path: the FP64-accurate (double-float) and F32 sketches converge to rtol; TF32 / BF16
+    sketches need a shift of their own eps, which truncates the captured spectrum (more PCG
+    iterations, never a failure)."""
     wl, pr, th = _workload("poisson5d", 1200, 300)
     J = mlp.jacobian(pr, th)
     g_o = mlp.vjp(pr, th, pr.w * mlp.residual(pr, th)[0])
     iters = {}
-    for sketch in ["f32", "tf32", "bf16"]:
+    for sketch in ["f64", "f32", "tf32", "bf16"]:
         ctx = ngd.Context(pr, dtype="f32")
         t = dev(th)
         info = ctx.step(t, ell=200, mu=1e-7, rtol=1e-6, maxit=600, seed=1, step=0, sketch=sketch)
         iters[sketch] = info["pcg_iters"]
         assert info["loss_after"] < info["loss_before"], sketch
-        if sketch == "f32":
+        if sketch in ("f32", "f64"):
             assert info["relres"] <= 1e-6
             # the direction solves the oracle's FP64 system to the accuracy of the FP32 operator
             d = (th - host(t)) / info["alpha"]
             res = J.T @ (pr.w * (J @ d)) + 1e-7 * d - g_o
             assert np.linalg.norm(res) <= 1e-3 * np.linalg.norm(g_o)
         ctx.close()
-    assert iters["f32"] <= iters["tf32"] and iters["f32"] <= iters["bf16"], iters
+    assert iters["f64"] <= iters["f32"] <= iters["tf32"] and iters["f32"] <= iters["bf16"], iters
 
 
 def test_heuristic_mu(ngd):
