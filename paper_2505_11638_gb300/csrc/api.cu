@@ -1,6 +1,7 @@
 // C ABI of libngd (include/ngd.h): context, workspace and the orchestration of the
 // Nystrom-preconditioned matrix-free NGD step on one GPU.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -61,6 +62,11 @@ struct ngd_ctx {
   double *M = nullptr, *A1 = nullptr, *V = nullptr, *Vs = nullptr, *sig2 = nullptr, *inv_sigma = nullptr;
   double *lam = nullptr, *dinv = nullptr, *w1 = nullptr, *gpart = nullptr, *eigws = nullptr;
   double *Y64 = nullptr, *B64 = nullptr, *Zw64 = nullptr, *U64 = nullptr;  // FP64-accurate sketch of an FP32 J
+  // fused PCG (FP32 stored J): U as an FP32 pair, per-block matvec partials and reduction scratch
+  float *Uh = nullptr, *Ul = nullptr, *yph = nullptr, *ypl = nullptr;
+  float *vhf = nullptr, *whf = nullptr;   // split matvec vector (2 x ldJ), split weights (2 x N)
+  double* fred = nullptr;
+  float2 *w1p = nullptr, *w2f = nullptr;
   size_t gpart_elems = 0;
   int* perm = nullptr;
   TcSketch* tc = nullptr;
@@ -188,6 +194,10 @@ ngd_status ensure_ell(ngd_ctx* ctx, int ell) {
     TRY(dalloc(ctx, &ctx->Zw64, (size_t)ctx->N * ell * 8));
     TRY(dalloc(ctx, &ctx->U64, (size_t)ctx->ldP * ell * 8));
     CK(cudaMemsetAsync(ctx->U64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
+    TRY(dalloc(ctx, &ctx->Uh, (size_t)ctx->ldP * ell * 4));
+    TRY(dalloc(ctx, &ctx->Ul, (size_t)ctx->ldP * ell * 4));
+    TRY(dalloc(ctx, &ctx->w1p, (size_t)fused_pcg_blocks() * ell * sizeof(float2)));
+    TRY(dalloc(ctx, &ctx->w2f, (size_t)ell * sizeof(float2)));
     CK(cudaMemsetAsync(ctx->Y64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
     CK(cudaMemsetAsync(ctx->B64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
   }
@@ -250,6 +260,8 @@ ngd_status linearize(ngd_ctx* ctx, const double* theta) {
     nb = launch_jacobian<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, (T*)ctx->J, ctx->ldJ, ctx->r,
                             ctx->lpart, nullptr, 0, ctx->stream);
     if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
+    // the fused matvec reads the weights as FP32 pairs (the caller owns w: re-split per linearization)
+    if (ctx->whf) launch_split_df(ctx->ps.w, ctx->whf, ctx->whf + ctx->N, ctx->N, ctx->N, ctx->stream);
   } else {
     T* tape = ctx->tape_allowed ? (T*)ctx->tape : nullptr;
     nb = launch_forward<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, ctx->r, ctx->lpart, tape, 0,
@@ -297,6 +309,23 @@ ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_st
 template <typename T>
 ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* mu_d, double* y, const int* done) {
   if (ctx->stored_j) {
+    if (std::is_same<T, float>::value && !done && ctx->yph) {
+      // one pass over J in one cooperative kernel
+      FusedPcgArgs fa;
+      fa.J = (const float*)ctx->J; fa.ldJ = ctx->ldJ; fa.N = ctx->N; fa.p = ctx->p; fa.w = ctx->ps.w;
+      fa.mu_d = mu_d; fa.mu_h = mu_h;
+      fa.pv = const_cast<double*>(v); fa.q = y;
+      fa.wh = ctx->whf; fa.wl = ctx->whf + ctx->N;
+      fa.vhf = ctx->vhf; fa.vlf = ctx->vhf + ctx->ldJ;
+      fa.yph = ctx->yph; fa.ypl = ctx->ypl; fa.red = ctx->fred;
+      fa.mode = 1;
+      const cudaError_t e = launch_pcg_fused(fa, ctx->stream);
+      if (e != cudaErrorCooperativeLaunchTooLarge) {
+        CK(e);
+        return check_launch(ctx);
+      }
+      cudaGetLastError();
+    }
     if (std::is_same<T, float>::value) {
       float* vh = (float*)ctx->vT;
       launch_split_df(v, vh, vh + ctx->ldJ, ctx->p, ctx->ldJ, ctx->stream);
@@ -530,6 +559,14 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
 }
 
 // ------------------------------------------------------------------ PCG
+ngd_status pcg_result(ngd_ctx* ctx, const PcgScalars* h, int* iters, double* relres) {
+  if (iters) *iters = h->iters;
+  if (relres) *relres = h->gn2 > 0 ? std::sqrt(h->rn2 / h->gn2) : 0.0;
+  if (h->status & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
+  if (h->status & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value inside CG%s");
+  return NGD_OK;
+}
+
 // P^{-1} v with U stored as float (u_f64 false) or double
 void precond(ngd_ctx* ctx, bool u_f64, const void* U, int64_t ldU, int ell, const double* lam, double mu_h,
              const double* mu_d, const double* v, double* z, const int* done) {
@@ -557,6 +594,33 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   double* q = ctx->q;
   const bool pre = U != nullptr && ell > 0;
   const int* done = &ctx->pcg->done;
+  if (std::is_same<T, float>::value && ctx->stored_j && ctx->yph && fused_pcg_supported(p, ctx->ldJ, pre ? ell : 0)) {
+    // the whole solve in one cooperative kernel (pcg_fused.cu)
+    FusedPcgArgs fa;
+    fa.J = (const float*)ctx->J; fa.ldJ = ctx->ldJ; fa.N = ctx->N; fa.p = p; fa.w = ctx->ps.w;
+    if (pre) {
+      if (u_f64)
+        launch_split_transpose_df<double>((const double*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
+      else
+        launch_split_transpose_df<float>((const float*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
+      fa.Uh = ctx->Uh; fa.Ul = ctx->Ul; fa.lam = lam; fa.ell = ell;
+    }
+    fa.mu_d = mu_d; fa.mu_h = mu_h;
+    fa.g = g; fa.x = x; fa.r = r; fa.z = z; fa.pv = pv; fa.q = q;
+    fa.wh = ctx->whf; fa.wl = ctx->whf + ctx->N;
+    fa.vhf = ctx->vhf; fa.vlf = ctx->vhf + ctx->ldJ;
+    fa.yph = ctx->yph; fa.ypl = ctx->ypl; fa.red = ctx->fred; fa.w1p = ctx->w1p; fa.w2 = ctx->w2f;
+    fa.sc = ctx->pcg; fa.mode = 0;
+    const cudaError_t e = launch_pcg_fused(fa, ctx->stream);
+    if (e != cudaErrorCooperativeLaunchTooLarge) {
+      CK(e);
+      TRY(check_launch(ctx));
+      CK(cudaMemcpyAsync(h, ctx->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      return pcg_result(ctx, h, iters, relres);
+    }
+    cudaGetLastError();   // no co-resident grid: the multi-kernel solve below
+  }
   launch_pcg_init(g, x, r, p, ctx->part, ctx->pcg, ctx->stream);
   if (pre) precond(ctx, u_f64, U, ldU, ell, lam, mu_h, mu_d, r, z, nullptr);
   launch_pcg_first_dir(r, pre ? z : r, pv, p, ctx->part, ctx->pcg, ctx->stream);
@@ -577,11 +641,7 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
     CK(cudaStreamSynchronize(ctx->stream));
     if (h->done) break;
   }
-  if (iters) *iters = h->iters;
-  if (relres) *relres = h->gn2 > 0 ? std::sqrt(h->rn2 / h->gn2) : 0.0;
-  if (h->status & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
-  if (h->status & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value inside CG%s");
-  return NGD_OK;
+  return pcg_result(ctx, h, iters, relres);
 }
 
 template <typename T>
@@ -605,19 +665,37 @@ float ev_ms(ngd_ctx* ctx, int a, int b) {
   return ms;
 }
 
+// NVTX ranges around the phases of a step (host-side annotations for profilers; no-ops otherwise).
+// The range stack stays balanced on every return path.
+struct PhaseRange {
+  bool open = false;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~PhaseRange() {
+    if (open) nvtxRangePop();
+  }
+};
+
 template <typename T>
 ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_step_info* info) {
   ngd_step_info inf{};
   const int64_t p = ctx->p;
+  PhaseRange phase;
+  phase.next("linearize");
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
   // Alg. 1 line 2: gradient at theta (and the linearization the matvecs use)
   TRY(linearize<T>(ctx, theta));
   launch_mul(ctx->ps.w, ctx->r, ctx->svec, ctx->N, ctx->stream);
   TRY(vjp_current<T>(ctx, ctx->svec, ctx->g, true));
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  phase.next("sketch");
   // Alg. 4 line 1: randomized Nystrom (App. A), fresh Omega from (seed, step)
   TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch));
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+  phase.next("factor");
   double scale = 1.0;
   ngd_status fs = NGD_OK;
   for (int attempt = 0; attempt < 3; ++attempt) {
@@ -628,6 +706,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   }
   if (fs != NGD_OK) return fs;
   CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+  phase.next("pcg");
   // Alg. 4 line 2: mu (fixed, or gamma eps lambda_1)
   launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSMu, ctx->stream);
   // Alg. 3 line 3: pCG on (G + mu I) d = g with the Nystrom preconditioner of Alg. 4
@@ -638,6 +717,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, o->ell, o->rtol, o->maxit,
                       ctx->d, &iters, &relres));
   CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+  phase.next("linesearch");
   // Alg. 1 line 4: Armijo backtracking along theta - alpha d
   launch_dot(ctx->g, ctx->d, p, ctx->part, ctx->scal + kSDot, ctx->stream);
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -824,6 +904,14 @@ ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
       dalloc(ctx, &ctx->g, p * 8) != NGD_OK || dalloc(ctx, &ctx->d, p * 8) != NGD_OK ||
       dalloc(ctx, &ctx->theta_trial, p * 8) != NGD_OK)
     return fail(NGD_ERR_OOM);
+  if (ctx->dtype == NGD_F32 && ctx->stored_j && fused_pcg_supported(p, ctx->ldJ, 0)) {
+    const size_t nb = (size_t)fused_pcg_blocks();
+    if (dalloc(ctx, &ctx->yph, nb * ctx->ldJ * 4) != NGD_OK || dalloc(ctx, &ctx->ypl, nb * ctx->ldJ * 4) != NGD_OK ||
+        dalloc(ctx, &ctx->fred, nb * 4 * 8) != NGD_OK || dalloc(ctx, &ctx->vhf, 2 * ctx->ldJ * 4) != NGD_OK ||
+        dalloc(ctx, &ctx->whf, 2 * N * 4) != NGD_OK)
+      return fail(NGD_ERR_OOM);
+    if (cudaMemsetAsync(ctx->vhf, 0, 2 * ctx->ldJ * 4, ctx->stream) != cudaSuccess) return fail(NGD_ERR_CUDA);
+  }
   if (cudaMallocHost((void**)&ctx->h_scal, kSCount * 8) != cudaSuccess ||
       cudaMallocHost((void**)&ctx->h_int, 16 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost((void**)&ctx->h_pcg, sizeof(PcgScalars)) != cudaSuccess)
@@ -846,7 +934,8 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->lpart, ctx->colpart, ctx->scal, ctx->status, ctx->pcg, ctx->x, ctx->rr, ctx->z, ctx->pv, ctx->q,
                  ctx->g, ctx->d, ctx->theta_trial, ctx->Om, ctx->Y, ctx->B, ctx->U, ctx->Lr, ctx->VsT, ctx->Zw, ctx->M,
                  ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
-                 ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64};
+                 ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64, ctx->Uh, ctx->Ul,
+                 ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "linalg.cuh"
 
 namespace cg = cooperative_groups;
@@ -87,23 +88,6 @@ void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s) 
 template void launch_d2t<float>(const double*, float*, int64_t, int64_t, cudaStream_t);
 template void launch_d2t<double>(const double*, double*, int64_t, int64_t, cudaStream_t);
 
-// ---------------------------------------------------------------------------- double-float helpers
-struct DF {  // unevaluated sum hi + lo
-  float hi, lo;
-};
-__device__ __forceinline__ void df_add_prod(DF& s, float a, float bh, float bl) {
-  const float p = a * bh;
-  const float pe = fmaf(a, bh, -p);      // exact error of the product
-  const float t = s.hi + p;              // TwoSum(s.hi, p)
-  const float z = t - s.hi;
-  const float e = (s.hi - (t - z)) + (p - z);
-  s.hi = t;
-  s.lo += e + pe + a * bl;
-}
-__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
-}
 
 // ---------------------------------------------------------------------------- stored-J matvec
 // t[n] = sum_j J[n, j] v[j] (v already in the working dtype, zero-padded to ldJ),

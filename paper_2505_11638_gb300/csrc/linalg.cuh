@@ -108,4 +108,29 @@ void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* 
                            cudaStream_t s);
 void launch_set_mu(const double* lam, double fixed_mu, double gamma, double* mu, cudaStream_t s);
 
+// Whole preconditioned CG for an FP32 stored Jacobian in one cooperative kernel (pcg_fused.cu).
+struct FusedPcgArgs {
+  const float* J = nullptr; int64_t ldJ = 0, N = 0, p = 0;   // J: N x ldJ row-major, zero beyond column p
+  const double* w = nullptr;                                 // residual weights (N)
+  const float *wh = nullptr, *wl = nullptr;                  // the weights split into FP32 pairs (N)
+  const float* Uh = nullptr; const float* Ul = nullptr;      // U = Uh + Ul, j-major: U[j, k] at j * ell + k
+  const double* lam = nullptr; int ell = 0;                  // ell = 0: no preconditioner
+  const double* mu_d = nullptr; double mu_h = 0.0;           // mu from device (if set) or host
+  const double* g = nullptr;                                 // right-hand side (p)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;   // p each
+  float *vhf = nullptr, *vlf = nullptr;                      // matvec vector split into FP32 pairs (ldJ each,
+                                                             // zero beyond p)
+  float *yph = nullptr, *ypl = nullptr;                      // fused_pcg_blocks() x ldJ each
+  double* red = nullptr;                                     // fused_pcg_blocks() x 4
+  float2* w1p = nullptr;                                     // fused_pcg_blocks() x ell
+  float2* w2 = nullptr;                                      // ell
+  PcgScalars* sc = nullptr;                                  // rtol2, maxit in; iterations and status out
+  int mode = 0;                                              // 0: PCG; 1: q = (G + mu I) pv only
+};
+int fused_pcg_blocks();
+bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell);
+cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s);
+template <typename TU>
+void launch_split_transpose_df(const TU* U, int64_t ldu, int64_t p, int ell, float* Uh, float* Ul, cudaStream_t s);
+
 }  // namespace ngd

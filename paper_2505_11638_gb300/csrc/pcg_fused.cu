@@ -1,0 +1,614 @@
+// Whole preconditioned CG (Alg. 3, textbook pCG with x0 = 0) for an FP32 stored Jacobian in one
+// cooperative persistent kernel: one block per SM, grid barriers between the dependent phases of
+// an iteration instead of kernel launches and host round trips.
+//
+// Per iteration (G = number of blocks; block b owns a contiguous slice of J's rows, of the
+// parameter index j and of the Nystrom index k):
+//   A  row pass over J: t_n = J_n . p, s_n = w_n t_n, y_b += s_n J_n for the block's rows; one
+//      read of J (cp.async ring, L2 evict-first), double-float arithmetic throughout
+//   B  q_j = sum_b y_b[j] + mu p_j on the block's j slice; partial p . q
+//   C  alpha = r.z / p.q; x += alpha p, r -= alpha q; partial ||r||^2; partial U^T r
+//   D  convergence test on ||r||; w2_k = ((lam_ell + mu) / (lam_k + mu) - 1) (U^T r)_k
+//   E  z = r + U w2 (Alg. 4, scaled form); partial r . z
+//   F  beta = r.z_new / r.z, p = z + beta p
+// The preconditioner's U is held as an FP32 pair (Uh + Ul, ~48 bits) in j-major order (U[j, k]
+// at j * ell + k, so a block's j slice is one contiguous run): its apply scales the top
+// directions by (lam_ell + mu) / (lam_1 + mu) ~ 1e-7, which FP32 U cannot represent, and FP64
+// arithmetic runs ~60x slower than FP32 on GB300.  Grid-wide sums are formed identically in
+// every block (same operands, same order), so all blocks take the same branch.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "df.cuh"
+#include "linalg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ngd {
+namespace {
+
+constexpr int kT = 256;            // threads per block (one block per SM, 8 warps)
+constexpr int kW = kT / 32;        // warps per block
+constexpr int kNG = kT / 64;       // column groups in the j-slice phases
+constexpr int kMaxSlice = 128;     // largest j slice per block (p <= kMaxSlice * G)
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, uint64_t pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Block-wide sum, the same value in every thread and in every block given the same inputs.
+// red: kT + 1 doubles.  Only warp 0 does FP64 arithmetic (the FP64 pipe is narrow on GB300).
+__device__ __forceinline__ double block_allsum(double v, double* red) {
+  __syncthreads();
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kT / 32; ++i) s += red[threadIdx.x + 32 * i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[kT] = s;
+  }
+  __syncthreads();
+  return red[kT];
+}
+
+// sum over blocks of red[b * 4 + slot] (G <= kT)
+__device__ __forceinline__ double grid_total(const double* red, int slot, double* sred) {
+  const double v = (int)threadIdx.x < (int)gridDim.x ? __ldcg(red + threadIdx.x * 4 + slot) : 0.0;
+  return block_allsum(v, sred);
+}
+
+constexpr int kR = 2;              // J rows per block-wide reduction round of phase A
+
+struct Smem {
+  DF wred[2][kR][kW];
+  double dred[kT + 1];
+  DF cgrp[kNG][64];
+  float2 rs[kMaxSlice];
+};
+
+// Phase A: y_b = sum over the block's rows n of w_n (J_n . v) J_n, written as an FP32 pair.
+// Rows are taken kR at a time (one block barrier per round); row n sits in ring stage n % S and
+// is prefetched S - kR rows ahead.  Each thread copies and reads back only its own 16-byte slots,
+// so no barrier guards the ring: row n's stage is refilled one round after it was consumed.
+// Slots past the end of a row are never copied and stay zero (cleared here), so the arithmetic
+// runs unguarded.  v arrives split (a.vhf + a.vlf); its high words live in registers, its low
+// words in shared memory (vls, read back by the thread that wrote them).  Arithmetic is packed:
+// two columns per f32x2 instruction.
+template <int C4, int S>
+__device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, float4* vls, Smem& sm) {
+  static_assert(S % kR == 0 && S > kR, "ring stages");
+  constexpr int D = S - kR;                      // prefetch distance in rows
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int nv4 = (int)(a.ldJ / 4);
+  const int64_t rb0 = a.N * b / G, rb1 = a.N * (b + 1) / G;
+  const int nrows = (int)(rb1 - rb0);
+  f2x vh[C4][2], nvh[C4][2];
+  DF2 ya[C4][2];
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < C4; ++c) {
+    const int s = tid + c * kT;
+    const float4 h = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vhf) + s) : zero4;
+    vls[s] = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vlf) + s) : zero4;
+    vh[c][0] = pk2(h.x, h.y);
+    vh[c][1] = pk2(h.z, h.w);
+    nvh[c][0] = pk2(-h.x, -h.y);
+    nvh[c][1] = pk2(-h.z, -h.w);
+    ya[c][0] = DF2{0ull, 0ull};
+    ya[c][1] = DF2{0ull, 0ull};
+    if (s >= nv4) {
+#pragma unroll
+      for (int st = 0; st < S; ++st) ring[(st * C4 + c) * kT + tid] = zero4;
+    }
+  }
+  const uint64_t pol = evict_first_policy();
+  auto issue = [&](int k) {                      // row rb0 + k into stage k % S (one commit group)
+    if (k < nrows) {
+      const float4* src = reinterpret_cast<const float4*>(a.J + (rb0 + k) * a.ldJ) + tid;
+      float4* dst = ring + (k % S) * C4 * kT + tid;
+#pragma unroll
+      for (int c = 0; c < C4; ++c)
+        if (tid + c * kT < nv4) cp_async16(dst + c * kT, src + c * kT, pol);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int i = 0; i < D; ++i) issue(i);
+  for (int k0 = 0, round = 0; k0 < nrows; k0 += kR, ++round) {
+#pragma unroll
+    for (int i = 0; i < kR; ++i) issue(k0 + D + i);
+    float wh[kR], wl[kR];
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      const bool in = k0 + i < nrows;
+      wh[i] = in ? __ldg(a.wh + rb0 + k0 + i) : 0.f;
+      wl[i] = in ? __ldg(a.wl + rb0 + k0 + i) : 0.f;
+    }
+    cp_async_wait<D>();
+    DF t[kR];
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + ((k0 + i) % S) * C4 * kT + tid);
+      const ulonglong2* lvp = reinterpret_cast<const ulonglong2*>(vls + tid);
+      DF2 d0{0ull, 0ull}, d1{0ull, 0ull};
+      if (k0 + i < nrows) {                      // uniform in the block
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+          {
+            const ulonglong2 jv = row[c * kT];
+            const ulonglong2 lv = lvp[c * kT];
+            df2_add_prod(d0, jv.x, vh[c][0], nvh[c][0], lv.x);
+            df2_add_prod(d1, jv.y, vh[c][1], nvh[c][1], lv.y);
+          }
+        }
+      }
+      DF q0, q1, q2, q3;
+      df2_split(d0, q0, q1);
+      df2_split(d1, q2, q3);
+      t[i] = df_add(df_add(q0, q1), df_add(q2, q3));
+    }
+    static_assert(kR == 2, "two rows per round: one reduce-scatter");
+    const DF ts = warp_reduce_scatter2(t[0], t[1]);     // lane 0: row 0, lane 16: row 1
+    const int par = round & 1;
+    if ((lane & 15) == 0) sm.wred[par][lane >> 4][warp] = ts;
+    __syncthreads();
+    // every warp combines the kW warp sums with a 3-level butterfly over lanes 0..kW-1
+    f2x sh[kR], nsh[kR], sl[kR];
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      DF s = lane < kW ? sm.wred[par][i][lane] : DF{0.f, 0.f};
+#pragma unroll
+      for (int o = kW / 2; o > 0; o >>= 1) {
+        const DF u{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+        s = df_add(s, u);
+      }
+      s = DF{__shfl_sync(0xffffffffu, s.hi, 0), __shfl_sync(0xffffffffu, s.lo, 0)};
+      const DF sn = df_mul(s, wh[i], wl[i]);
+      sh[i] = pk2(sn.hi, sn.hi);
+      nsh[i] = pk2(-sn.hi, -sn.hi);
+      sl[i] = pk2(sn.lo, sn.lo);
+    }
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      if (k0 + i >= nrows) break;              // uniform in the block
+      const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + ((k0 + i) % S) * C4 * kT + tid);
+#pragma unroll
+      for (int c = 0; c < C4; ++c) {
+        {
+          const ulonglong2 jv = row[c * kT];
+          df2_add_prod(ya[c][0], jv.x, sh[i], nsh[i], sl[i]);
+          df2_add_prod(ya[c][1], jv.y, sh[i], nsh[i], sl[i]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  float4* oh = reinterpret_cast<float4*>(a.yph + (int64_t)b * a.ldJ);
+  float4* ol = reinterpret_cast<float4*>(a.ypl + (int64_t)b * a.ldJ);
+#pragma unroll
+  for (int c = 0; c < C4; ++c) {
+    const int s = tid + c * kT;
+    if (s < nv4) {
+      float h0, h1, h2, h3, l0, l1, l2, l3;
+      upk2(ya[c][0].hi, h0, h1);
+      upk2(ya[c][1].hi, h2, h3);
+      upk2(ya[c][0].lo, l0, l1);
+      upk2(ya[c][1].lo, l2, l3);
+      __stcg(oh + s, make_float4(h0, h1, h2, h3));
+      __stcg(ol + s, make_float4(l0, l1, l2, l3));
+    }
+  }
+}
+
+// The block's j slice of v, split into FP32 pairs for phase A.
+__device__ __forceinline__ void split_slice(const FusedPcgArgs& a, const double* v) {
+  const int G = gridDim.x, b = blockIdx.x;
+  const int64_t cb0 = a.p * b / G, cb1 = a.p * (b + 1) / G;
+  for (int64_t j = cb0 + threadIdx.x; j < cb1; j += kT) {
+    float h, l;
+    split_df(v[j], h, l);
+    __stcg(a.vhf + j, h);
+    __stcg(a.vlf + j, l);
+  }
+}
+
+// Phase B: q_j = sum_b y_b[j] + mu v_j on the block's j slice; returns the block's sum of v_j q_j.
+__device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double* v, double mu, double* q, Smem& sm) {
+  const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+  const int64_t cb0 = a.p * b / G, cb1 = a.p * (b + 1) / G;
+  const int jj = tid & 63, grp = tid >> 6;
+  double vq = 0.0;
+  for (int64_t j0 = cb0; j0 < cb1; j0 += 64) {
+    const int64_t j = j0 + jj;
+    DF acc{0.f, 0.f};
+    if (j < cb1) {
+      for (int bb0 = grp; bb0 < G; bb0 += 8 * kNG) {   // eight partials in flight per thread
+        float hv[8], lv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int bb = bb0 + u * kNG;
+          hv[u] = bb < G ? __ldcg(a.yph + (int64_t)bb * a.ldJ + j) : 0.f;
+          lv[u] = bb < G ? __ldcg(a.ypl + (int64_t)bb * a.ldJ + j) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = df_add(acc, DF{hv[u], lv[u]});
+      }
+    }
+    sm.cgrp[grp][jj] = acc;
+    __syncthreads();
+    if (grp == 0 && j < cb1) {
+      DF s = sm.cgrp[0][jj];
+#pragma unroll
+      for (int g2 = 1; g2 < kNG; ++g2) s = df_add(s, sm.cgrp[g2][jj]);
+      const double vj = __ldcg(v + j);
+      const double qj = df_to_double(s) + mu * vj;
+      q[j] = qj;
+      vq += vj * qj;
+    }
+    __syncthreads();
+  }
+  return vq;
+}
+
+// Partial U^T r over the block's j slice (r_j already split into sm.rs): a thread takes up to
+// kKT values of k at once, the slice's rows of U read in order (coalesced across k).
+constexpr int kKT = 2;             // k values per thread per pass (ell <= kKT * kT in one pass)
+__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm) {
+  for (int k0 = threadIdx.x; k0 < a.ell; k0 += kKT * kT) {
+    const float* uh = a.Uh + cb0 * a.ell + k0;
+    const float* ul = a.Ul + cb0 * a.ell + k0;
+    bool in[kKT];
+    DF acc[kKT][2];
+#pragma unroll
+    for (int u = 0; u < kKT; ++u) {
+      in[u] = k0 + u * kT < a.ell;
+      acc[u][0] = acc[u][1] = DF{0.f, 0.f};
+    }
+    int jj = 0;
+#pragma unroll 2
+    for (; jj + 1 < ncol; jj += 2) {
+      const float2 r0 = sm.rs[jj], r1 = sm.rs[jj + 1];
+#pragma unroll
+      for (int u = 0; u < kKT; ++u) {
+        if (in[u]) {
+          const int64_t o0 = (int64_t)jj * a.ell + u * kT, o1 = o0 + a.ell;
+          df_add_prod2(acc[u][0], __ldg(uh + o0), __ldg(ul + o0), r0.x, r0.y);
+          df_add_prod2(acc[u][1], __ldg(uh + o1), __ldg(ul + o1), r1.x, r1.y);
+        }
+      }
+    }
+    if (jj < ncol) {
+      const float2 r0 = sm.rs[jj];
+#pragma unroll
+      for (int u = 0; u < kKT; ++u)
+        if (in[u]) {
+          const int64_t o0 = (int64_t)jj * a.ell + u * kT;
+          df_add_prod2(acc[u][0], __ldg(uh + o0), __ldg(ul + o0), r0.x, r0.y);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kKT; ++u) {
+      if (in[u]) {
+        const DF s = df_add(acc[u][0], acc[u][1]);
+        __stcg(a.w1p + (int64_t)blockIdx.x * a.ell + k0 + u * kT, make_float2(s.hi, s.lo));
+      }
+    }
+  }
+}
+
+template <int C4, int S>
+__global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float4* ring = reinterpret_cast<float4*>(dsm);
+  float4* vls = ring + (int64_t)S * C4 * kT;             // low words of the matvec's vector
+  float2* w2s = reinterpret_cast<float2*>(dsm);          // phase E only (aliases the ring)
+  __shared__ Smem sm;
+  const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+  const double mu = a.mu_d ? *a.mu_d : a.mu_h;
+
+  if (a.mode == 1) {                                     // q = (G + mu I) v, v = a.pv
+    split_slice(a, a.pv);
+    grid.sync();
+    gv_rows<C4, S>(a, ring, vls, sm);
+    grid.sync();
+    gv_finish(a, a.pv, mu, a.q, sm);
+    return;
+  }
+
+  const int64_t cb0 = a.p * b / G, cb1 = a.p * (b + 1) / G;
+  const int ncol = (int)(cb1 - cb0);
+  const int kb0 = (int)((int64_t)a.ell * b / G), kb1 = (int)((int64_t)a.ell * (b + 1) / G);
+  const bool pre = a.ell > 0;
+  PcgScalars* sc = a.sc;
+  const double rtol2 = sc->rtol2;
+  const int maxit = sc->maxit;
+
+  // x = 0, r = g, ||g||^2, U^T r
+  double rr = 0.0;
+  for (int jj = tid; jj < ncol; jj += kT) {
+    const double gj = a.g[cb0 + jj];
+    a.x[cb0 + jj] = 0.0;
+    a.r[cb0 + jj] = gj;
+    rr += gj * gj;
+    float h, l;
+    split_df(gj, h, l);
+    sm.rs[jj] = make_float2(h, l);
+  }
+  rr = block_allsum(rr, sm.dred);
+  if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
+  if (pre) utr_partial(a, cb0, ncol, sm);
+  grid.sync();
+
+  int it = 0, status = 0;
+  double gn2 = 0.0, rn2 = 0.0, rz = 0.0, alpha = 0.0, beta = 0.0, pq = 0.0;
+  for (;;) {
+    // D: convergence test; finish U^T r and scale it
+    rn2 = grid_total(a.red, 1, sm.dred);
+    bool done;
+    if (it == 0) {
+      gn2 = rn2;
+      done = rn2 == 0.0 || maxit <= 0;
+    } else {
+      done = rn2 <= rtol2 * gn2 || it >= maxit;
+    }
+    if (!isfinite(rn2)) {
+      status |= kStatNonFinite;
+      done = true;
+    }
+    if (done) break;
+    if (pre) {
+      const int lane = tid & 31, warp = tid >> 5;
+      const double lam_l = a.lam[a.ell - 1];
+      for (int k = kb0 + warp; k < kb1; k += kW) {
+        DF acc{0.f, 0.f};
+#pragma unroll 4
+        for (int bb = lane; bb < G; bb += 32) {
+          const float2 t = __ldcg(a.w1p + (int64_t)bb * a.ell + k);
+          acc = df_add(acc, DF{t.x, t.y});
+        }
+        acc = warp_sum_df(acc);
+        if (lane == 0) {
+          const double w2 = ((lam_l + mu) / (a.lam[k] + mu) - 1.0) * df_to_double(acc);
+          float h, l;
+          split_df(w2, h, l);
+          __stcg(a.w2 + k, make_float2(h, l));
+        }
+      }
+      grid.sync();
+    }
+    // E: z = P^{-1} r on the j slice, r . z
+    double rzp = 0.0;
+    if (pre) {
+      for (int k = tid; k < a.ell; k += kT) w2s[k] = __ldcg(a.w2 + k);
+      __syncthreads();
+      // a warp takes eight rows of U at once (j-major: each row contiguous), lanes over k
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int j0 = 8 * warp; j0 < ncol; j0 += 8 * kW) {
+        const int nq = min(8, ncol - j0);
+        DF acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
+        const float* uh0 = a.Uh + (cb0 + j0) * a.ell;
+        const float* ul0 = a.Ul + (cb0 + j0) * a.ell;
+#pragma unroll 2
+        for (int k = lane; k < a.ell; k += 32) {
+          const float2 ww = w2s[k];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < nq)
+              df_add_prod2(acc[q], __ldg(uh0 + (int64_t)q * a.ell + k), __ldg(ul0 + (int64_t)q * a.ell + k), ww.x,
+                           ww.y);
+        }
+        const DF s = warp_reduce_scatter8(acc);          // lane L: row j0 + (L >> 2)
+        const int q = lane >> 2;
+        if ((lane & 3) == 0 && q < nq) {
+          const int64_t j = cb0 + j0 + q;
+          const double rj = a.r[j], zj = rj + df_to_double(s);
+          a.z[j] = zj;
+          rzp += rj * zj;
+        }
+      }
+    } else {
+      for (int jj = tid; jj < ncol; jj += kT) {
+        const double rj = a.r[cb0 + jj];
+        a.z[cb0 + jj] = rj;
+        rzp += rj * rj;
+      }
+    }
+    rzp = block_allsum(rzp, sm.dred);
+    if (tid == 0) __stcg(a.red + b * 4 + 2, rzp);
+    grid.sync();
+    // F: beta, new direction
+    {
+      const double rz_new = grid_total(a.red, 2, sm.dred);
+      beta = it == 0 ? 0.0 : rz_new / rz;
+      for (int jj = tid; jj < ncol; jj += kT) {
+        const int64_t j = cb0 + jj;
+        const double pj = it == 0 ? a.z[j] : a.z[j] + beta * a.pv[j];
+        a.pv[j] = pj;
+        float h, l;
+        split_df(pj, h, l);
+        __stcg(a.vhf + j, h);
+        __stcg(a.vlf + j, l);
+      }
+      rz = rz_new;
+    }
+    grid.sync();
+    // A, B: q = (G + mu I) p, p . q
+    gv_rows<C4, S>(a, ring, vls, sm);
+    grid.sync();
+    {
+      double pqp = gv_finish(a, a.pv, mu, a.q, sm);
+      pqp = block_allsum(pqp, sm.dred);
+      if (tid == 0) __stcg(a.red + b * 4 + 0, pqp);
+    }
+    grid.sync();
+    // C: alpha, x and r, ||r||^2, U^T r
+    pq = grid_total(a.red, 0, sm.dred);
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      status |= isfinite(pq) ? kStatBreakdown : kStatNonFinite;
+      break;
+    }
+    alpha = rz / pq;
+    rr = 0.0;
+    for (int jj = tid; jj < ncol; jj += kT) {
+      const int64_t j = cb0 + jj;
+      a.x[j] += alpha * a.pv[j];
+      const double rj = a.r[j] - alpha * a.q[j];
+      a.r[j] = rj;
+      rr += rj * rj;
+      float h, l;
+      split_df(rj, h, l);
+      sm.rs[jj] = make_float2(h, l);
+    }
+    rr = block_allsum(rr, sm.dred);
+    if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
+    if (pre) utr_partial(a, cb0, ncol, sm);
+    ++it;
+    grid.sync();
+  }
+  if (b == 0 && tid == 0) {
+    sc->gn2 = gn2;
+    sc->rn2 = rn2;
+    sc->rz = rz;
+    sc->pq = pq;
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->iters = it;
+    sc->cur_iter = it;
+    sc->status |= status;
+    sc->done = 1;
+  }
+}
+
+constexpr int kMaxC4 = 9;        // p <= 4 * kT * kMaxC4 = 9216
+constexpr int kSmemBudget = 210 * 1024;
+
+// ring stages (plus one stage-sized slot for v's low words): a multiple of kR, at most 8
+template <int C4>
+constexpr int stages_for() {
+  return std::min(8, kSmemBudget / (C4 * kT * 16) - 1) / kR * kR;
+}
+
+template <int C4>
+cudaError_t launch_c4(const FusedPcgArgs& a, int G, cudaStream_t s) {
+  constexpr int S = stages_for<C4>();
+  static_assert(S >= 2 * kR, "shared-memory ring too small");
+  auto kern = k_pcg_fused<C4, S>;
+  // dynamic shared memory: the ring, or the scaled U^T r of phase E (ell <= 2048), whichever is larger
+  constexpr size_t smem = std::max((size_t)(S + 1) * C4 * kT * 16, (size_t)2048 * sizeof(float2));
+  static std::mutex mu;
+  static int configured_dev = -1, per_sm = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (configured_dev != dev) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem);
+      if (e != cudaSuccess) return e;
+      configured_dev = dev;
+    }
+  }
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  FusedPcgArgs args = a;
+  void* params[] = {&args};
+  e = cudaLaunchCooperativeKernel((const void*)kern, G, kT, params, smem, s);
+  note_launch();
+  return e;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return n;
+}
+
+}  // namespace
+
+int fused_pcg_blocks() { return std::min(num_sms(), kT); }
+
+bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell) {
+  const int G = fused_pcg_blocks();
+  const int64_t c4 = (ldJ / 4 + kT - 1) / kT;
+  return G >= 1 && ldJ % 4 == 0 && c4 >= 1 && c4 <= kMaxC4 && (p + G - 1) / G <= kMaxSlice && ell >= 0 &&
+         ell <= 2048;
+}
+
+cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s) {
+  if (!fused_pcg_supported(a.p, a.ldJ, a.ell)) return cudaErrorInvalidValue;
+  const int G = fused_pcg_blocks();
+  switch ((a.ldJ / 4 + kT - 1) / kT) {
+    case 1: return launch_c4<1>(a, G, s);
+    case 2: return launch_c4<2>(a, G, s);
+    case 3: return launch_c4<3>(a, G, s);
+    case 4: return launch_c4<4>(a, G, s);
+    case 5: return launch_c4<5>(a, G, s);
+    case 6: return launch_c4<6>(a, G, s);
+    case 7: return launch_c4<7>(a, G, s);
+    case 8: return launch_c4<8>(a, G, s);
+    default: return launch_c4<9>(a, G, s);
+  }
+}
+
+// U (column-major, leading dimension ldu, p x ell, float or double) -> Uh + Ul in j-major order
+// (U[j, k] at j * ell + k); 32 x 32 tiles transposed through shared memory.
+template <typename TU>
+__global__ void k_split_transpose_df(const TU* __restrict__ U, int64_t ldu, int64_t p, int ell, float* __restrict__ Uh,
+                                     float* __restrict__ Ul) {
+  __shared__ float th[32][33], tl[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t j = j0 + tx;
+    const int k = k0 + i;
+    float h = 0.f, l = 0.f;
+    if (j < p && k < ell) split_df((double)U[j + (int64_t)k * ldu], h, l);
+    th[i][tx] = h;
+    tl[i][tx] = l;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t j = j0 + i;
+    const int k = k0 + tx;
+    if (j < p && k < ell) {
+      Uh[j * ell + k] = th[tx][i];
+      Ul[j * ell + k] = tl[tx][i];
+    }
+  }
+}
+template <typename TU>
+void launch_split_transpose_df(const TU* U, int64_t ldu, int64_t p, int ell, float* Uh, float* Ul, cudaStream_t s) {
+  dim3 grid((unsigned)((p + 31) / 32), (unsigned)((ell + 31) / 32));
+  k_split_transpose_df<TU><<<grid, 256, 0, s>>>(U, ldu, p, ell, Uh, Ul); note_launch();
+}
+template void launch_split_transpose_df<float>(const float*, int64_t, int64_t, int, float*, float*, cudaStream_t);
+template void launch_split_transpose_df<double>(const double*, int64_t, int64_t, int, float*, float*, cudaStream_t);
+
+}  // namespace ngd

@@ -295,6 +295,62 @@ def test_pcg_matches_oracle_at_fixed_iterations(ngd):
     ctx.close()
 
 
+def test_fp32_matvec_symmetry_and_linearity(ngd):
+    """The FP32-context matvec (one pass over the stored FP32 Jacobian, double-float sums): for
+    that J, G = J^T W J is exactly symmetric and linear, so u.(Gv) = v.(Gu) and G(u + 2v) =
+    Gu + 2Gv hold to the pair's ~48-bit precision; FP32 sums would break both at ~1e-7."""
+    wl, pr, th = _workload("poisson5d")
+    ctx = ngd.Context(pr, dtype="f32")
+    rng = np.random.default_rng(12)
+    u, v = rng.standard_normal(pr.p), rng.standard_normal(pr.p)
+    Gu = host(ctx.gramian_mv(dev(th), dev(u), 0.0))
+    Gv = host(ctx.gramian_mv(None, dev(v), 0.0))
+    Guv = host(ctx.gramian_mv(None, dev(u + 2.0 * v), 0.0))
+    assert abs(u @ Gv - v @ Gu) <= 1e-11 * np.linalg.norm(u) * np.linalg.norm(Gv)
+    assert rel(Guv, Gu + 2.0 * Gv) <= 1e-11
+    assert v @ Gv > 0.0
+    ctx.close()
+
+
+@pytest.mark.parametrize("precond", ["f64", "f32", "none"])
+def test_pcg_fp32_context(ngd, precond):
+    """PCG in an FP32 context (the whole solve in one cooperative kernel).  To rtol 1e-8: the
+    true residual of the returned direction, measured with the context's own matvec, meets the
+    tolerance; iterations and direction agree with the FP64 oracle on the FP64 Jacobian up to
+    the FP32 Jacobian's rounding (~2e-4 in d at mu = 1e-5, a few iterations)."""
+    wl, pr, th = _workload("poisson5d", 900, 220)
+    J = mlp.jacobian(pr, th)
+    G = gramian.gramian(J, pr.w)
+    g_o, _, _ = mlp.gradient(pr, th)
+    ell, mu = 60, 1e-5
+    Om = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 5, 0))
+    U_o, lam_o, _ = nystrom.nystrom_factor(Om, G @ Om)
+    ctx = ngd.Context(pr, dtype="f32")
+    g, _, _ = ctx.gradient(dev(th))
+    if precond == "none":
+        d, it, rr = ctx.pcg_solve(None, g, mu, None, None, 0, rtol=1e-8, maxit=3000)
+        Pinv = None
+    else:
+        wd = torch.float64 if precond == "f64" else torch.float32
+        U_d = torch.tensor(np.ascontiguousarray(U_o.T), dtype=wd, device="cuda")
+        d, it, rr = ctx.pcg_solve(None, g, mu, U_d, dev(lam_o), ell, rtol=1e-8, maxit=3000)
+        U_p = host(U_d).T
+
+        def Pinv(v):
+            return nystrom.precond_apply(U_p, lam_o, mu, v)
+    d_o, it_o, rr_o = solve.pcg(lambda v: G @ v + mu * v, g_o, Pinv, 1e-8, 3000)
+    assert rr <= 1e-8
+    res = host(ctx.gramian_mv(None, d, mu)) - host(g)
+    assert np.linalg.norm(res) <= 1e-7 * np.linalg.norm(host(g))
+    # unpreconditioned CG runs ~250 iterations here, where rounding alone moves the count by ~10%
+    assert abs(it - it_o) <= max(3, (0.25 if precond == "none" else 0.1) * it_o), (it, it_o)
+    assert rel(host(d), d_o) <= 2e-3
+    # a fixed iteration count stops there exactly
+    d3, it3, rr3 = ctx.pcg_solve(None, g, mu, None, None, 0, rtol=0.0, maxit=3)
+    assert it3 == 3 and rr3 > 0.0
+    ctx.close()
+
+
 def test_ngd_step_matches_oracle_fp64(ngd):
     wl, pr, th = _workload("poisson2d")
     ctx = ngd.Context(pr, dtype="f64")
