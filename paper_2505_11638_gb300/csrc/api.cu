@@ -372,7 +372,7 @@ ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell) {
     TRY(gram_atb<T>(ctx, Om, Om, ctx->p, ctx->ldP, ell, ctx->M));
     launch_symmetrize(ctx->M, ell, ctx->stream);
     CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));
-    launch_trsm_lt<T>(Om, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->dinv, ctx->stream);
+    launch_trsm_lt<T>(Om, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->stream);
   }
   return check_launch(ctx);
 }
@@ -491,7 +491,7 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
   }
   launch_symmetrize(ctx->M, ell, ctx->stream);
   CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));                                // = L L^T
-  launch_trsm_lt<double>(Bm, ld, p, ell, ctx->M, (double*)ctx->eigws, ctx->dinv, ctx->stream);  // B = Y_nu L^{-T}
+  launch_trsm_lt<double>(Bm, ld, p, ell, ctx->M, (double*)ctx->eigws, ctx->stream);  // B = Y_nu L^{-T}
   {
     GemmDfArgs<double, double> g;                                                          // S = B^T B
     g.M = ell; g.N = ell; g.K = p;
@@ -535,7 +535,7 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
   TRY(gram_atb<T>(ctx, Om, Bm, ctx->p, ctx->ldP, ell, ctx->M));                          // Omega^T Y_nu
   launch_symmetrize(ctx->M, ell, ctx->stream);
   CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));                            // = L L^T, C = L^T
-  launch_trsm_lt<T>(Bm, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->dinv, ctx->stream);  // B = Y_nu C^{-1}
+  launch_trsm_lt<T>(Bm, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->stream);  // B = Y_nu C^{-1}
   TRY(gram_atb<T>(ctx, Bm, Bm, ctx->p, ctx->ldP, ell, ctx->V));                          // S = B^T B
   launch_symmetrize(ctx->V, ell, ctx->stream);
   // S = V Sigma^2 V^T in FP64; sorted eigenvectors into M (free again after the triangular solve)

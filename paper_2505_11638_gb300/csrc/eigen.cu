@@ -157,37 +157,208 @@ __global__ void __launch_bounds__(256) k_tridiag(double* __restrict__ A, int n, 
   }
 }
 
+// Distributed variant for n small enough that each block can hold its share of A: column j
+// lives in the shared memory of block j % G for the whole reduction, so per column only the
+// Householder vector v and p = tau A22 v cross the grid (through L2), with two grid barriers:
+//   owner of column k: v, tau (d_k, e_k)            -> barrier
+//   every block: p_j = tau A[:, j] . v for its columns j > k (A symmetric), partial v . p -> barrier
+//   every block: K = tau/2 v . p, w = p - K v, A[:, j] -= v w_j + w v_j for its columns;
+//   the owner of column k + 1 then forms the next reflector.
+// vbuf, pbuf: n doubles each; red: G doubles.
+namespace {
+
+// Householder reflector of the trailing part of column k held in col (full column, length n).
+__device__ void house_from_col(const double* __restrict__ col, int n, int k, double* __restrict__ d,
+                               double* __restrict__ e, double* __restrict__ tau, double* __restrict__ Vh,
+                               double* __restrict__ vbuf, double* red8, double* s_bc) {
+  const int m = n - k - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double x = col[k + 1 + i];
+    s2 += x * x;
+  }
+  s2 = wsum_d(s2);
+  if (lane == 0) red8[warp] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tsum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += red8[w];
+    const double x0 = col[k + 1];
+    const double sig = sqrt(tsum);
+    double alpha, tu, v0;
+    if (tsum - x0 * x0 <= 0.0) {      // nothing below the subdiagonal: H = I
+      alpha = x0;
+      tu = 0.0;
+      v0 = 0.0;
+    } else {
+      alpha = x0 >= 0.0 ? -sig : sig;
+      v0 = x0 - alpha;
+      tu = 2.0 / (2.0 * (tsum + fabs(x0) * sig));
+    }
+    d[k] = col[k];
+    e[k] = alpha;
+    tau[k] = tu;
+    s_bc[0] = v0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double vi = i == 0 ? s_bc[0] : col[k + 1 + i];
+    __stcg(vbuf + i, vi);
+    Vh[(int64_t)k * n + i] = vi;
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_tridiag_dist(const double* __restrict__ A, int n, double* __restrict__ d,
+                                                      double* __restrict__ e, double* __restrict__ tau,
+                                                      double* __restrict__ Vh, double* __restrict__ vbuf,
+                                                      double* __restrict__ pbuf, double* __restrict__ red) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int ncl = (n + G - 1) / G;
+  double* cols = reinterpret_cast<double*>(smem_raw);    // [ncl][n]
+  double* vs = cols + (int64_t)ncl * n;                   // [n]
+  double* ws = vs + n;                                    // [n]
+  __shared__ double red8[8];
+  __shared__ double s_bc[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int s = 0; s < ncl; ++s) {
+    const int j = b + s * G;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cols[(int64_t)s * n + i] = j < n ? A[i + (int64_t)j * n] : 0.0;
+  }
+  __syncthreads();
+  if (n >= 3 && b == 0) house_from_col(cols, n, 0, d, e, tau, Vh, vbuf, red8, s_bc);
+  grid.sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    const double tk = __ldcg(tau + k);
+    const int s_first = (k + 1 - b + G - 1) / G;          // first local slot with column j > k
+    if (tk != 0.0) {                                      // uniform: every block reads the same tau
+      for (int i = threadIdx.x; i < m; i += blockDim.x) vs[i] = __ldcg(vbuf + i);
+      __syncthreads();
+      // p_j = tau A[k+1:, j] . v for owned columns j > k, one warp per column
+      double part = 0.0;
+      for (int s = s_first + warp; s < ncl; s += (int)(blockDim.x >> 5)) {
+        const int j = b + s * G;
+        if (j >= n) break;
+        const double* col = cols + (int64_t)s * n + k + 1;
+        double acc = 0.0;
+        for (int i = lane; i < m; i += 32) acc += col[i] * vs[i];
+        const double pj = tk * wsum_d(acc);
+        if (lane == 0) {
+          __stcg(pbuf + (j - k - 1), pj);
+          part += vs[j - k - 1] * pj;
+        }
+      }
+      if (lane == 0) red8[warp] = part;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sb += red8[w];
+        __stcg(red + b, sb);
+      }
+      grid.sync();
+      // K = tau/2 v . p (summed over blocks in block order), w = p - K v, rank-2 update
+      if (warp == 0) {
+        double sv = 0.0;
+        for (int q = lane; q < G; q += 32) sv += __ldcg(red + q);
+        sv = wsum_d(sv);
+        if (lane == 0) s_bc[1] = 0.5 * tk * sv;
+      }
+      __syncthreads();
+      const double K = s_bc[1];
+      for (int i = threadIdx.x; i < m; i += blockDim.x) ws[i] = __ldcg(pbuf + i) - K * vs[i];
+      __syncthreads();
+      for (int s = s_first; s < ncl; ++s) {
+        const int j = b + s * G;
+        if (j >= n) break;
+        double* col = cols + (int64_t)s * n + k + 1;
+        const double wj = ws[j - k - 1], vj = vs[j - k - 1];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] -= vs[i] * wj + ws[i] * vj;
+      }
+      __syncthreads();
+    } else {
+      grid.sync();                                        // keep the barrier count uniform
+    }
+    // the owner of column k + 1 forms the next reflector from its updated column
+    if (k + 3 < n && (k + 1) % G == b) house_from_col(cols + (int64_t)((k + 1) / G) * n, n, k + 1, d, e, tau, Vh, vbuf,
+                                                       red8, s_bc);
+    grid.sync();
+  }
+  // the last 2 x 2 block
+  if (threadIdx.x == 0) {
+    if (n >= 2) {
+      if ((n - 2) % G == b) {
+        const double* c = cols + (int64_t)((n - 2) / G) * n;
+        d[n - 2] = c[n - 2];
+        e[n - 2] = c[n - 1];
+      }
+      if ((n - 1) % G == b) d[n - 1] = cols[(int64_t)((n - 1) / G) * n + n - 1];
+    } else if (b == 0) {
+      d[0] = cols[0];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------- 2. eigenvalues
-// lam_asc[i] (ascending), one warp per eigenvalue: 32 Sturm counts (number of negative LDL^T
-// pivots of T - x I) per step shrink the bracket 33-fold, down to a relative width 2 eps (so
-// that eigenvalues far below eps ||T|| stay apart and their twisted vectors differ).
+// lam_asc[i] (ascending), one warp per eigenvalue: 32 Sturm counts per step shrink the bracket
+// 33-fold, down to a relative width 2 eps (so that eigenvalues far below eps ||T|| stay apart
+// and their twisted vectors differ).  The count of eigenvalues below x is the number of sign
+// changes of the leading principal minors p_j(x) = (d_j - x) p_{j-1} - e_{j-1}^2 p_{j-2}
+// (Sturm sequence), evaluated without divisions (FP64 division is slow on this GPU) and kept in
+// range by exact power-of-two rescaling; a minor that is exactly zero takes the sign opposite to
+// its predecessor (a negative pivot, as in LAPACK's pivmin rule).
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                                           double x) {
+  double pm = 1.0, pc = d[0] - x;
+  if (pc == 0.0) pc = -0x1p-1000;
+  int c = pc < 0.0;
+  for (int j = 1; j < n; ++j) {
+    double pn = fma(d[j] - x, pc, -e2[j - 1] * pm);
+    if (pn == 0.0) pn = pc < 0.0 ? 0x1p-1000 * fabs(pc) : -0x1p-1000 * fabs(pc);
+    c += (pn < 0.0) != (pc < 0.0);
+    pm = pc;
+    pc = pn;
+    const int ex = max((int)((__double_as_longlong(pc) >> 52) & 0x7ff), (int)((__double_as_longlong(pm) >> 52) & 0x7ff));
+    if (ex > 1023 + 600 || ex < 1023 - 600) {            // rescale both terms by 2^(1023 - ex)
+      const double sc = __longlong_as_double((long long)(2046 - ex) << 52);
+      pc *= sc;
+      pm *= sc;
+    }
+  }
+  return c;
+}
+
 __global__ void k_multisect(const double* __restrict__ d, const double* __restrict__ e, int n,
                             double* __restrict__ lam_asc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* ds = reinterpret_cast<double*>(smem_raw);   // [n]
+  double* e2 = ds + n;                                // [n]
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    ds[j] = d[j];
+    e2[j] = j + 1 < n ? e[j] * e[j] : 0.0;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n) return;
-  double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
+  double lo = DBL_MAX, hi = -DBL_MAX;
   for (int j = 0; j < n; ++j) {       // Gershgorin interval
     const double ej = j + 1 < n ? fabs(e[j]) : 0.0, ejm = j > 0 ? fabs(e[j - 1]) : 0.0;
-    lo = fmin(lo, d[j] - ej - ejm);
-    hi = fmax(hi, d[j] + ej + ejm);
-    emax = fmax(emax, ej * ej);
+    lo = fmin(lo, ds[j] - ej - ejm);
+    hi = fmax(hi, ds[j] + ej + ejm);
   }
-  const double pivmin = DBL_MIN * fmax(1.0, emax);
   const double span = fmax(hi - lo, fmax(fabs(hi), fabs(lo)));
-  const double atol = 2.0 * DBL_EPSILON * span;
-  double a = lo - atol - pivmin, b = hi + atol + pivmin;
+  const double atol = 2.0 * DBL_EPSILON * span + DBL_MIN;
+  double a = lo - atol, b = hi + atol;
   for (int it = 0; it < 96; ++it) {
-    if (b - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)) + 4.0 * pivmin) break;
+    if (b - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)) + 4.0 * DBL_MIN) break;
     const double h = (b - a) / 33.0;
     const double x = a + h * (lane + 1);
-    double q = d[0] - x;
-    int c = q < 0.0;
-    for (int j = 1; j < n; ++j) {
-      if (fabs(q) < pivmin) q = -pivmin;
-      q = d[j] - x - (e[j - 1] * e[j - 1]) / q;
-      c += q < 0.0;
-    }
+    const int c = sturm_count(ds, e2, n, x);
     const unsigned mask = __ballot_sync(0xffffffffu, c > i);
     if (mask == 0u) {
       a = a + h * 32.0;
@@ -257,13 +428,15 @@ __global__ void k_twisted(const double* __restrict__ d, const double* __restrict
 
 // ---------------------------------------------------------------------------- 4. back-transform
 // V[:, c] = H_0 H_1 ... H_{n-3} Z[:, c_src] with c_src = n-1-c (descending eigenvalues); one warp
-// per column, H_k = I - tau_k v_k v_k^T acting on rows k+1..n-1.
-__global__ void k_backtransform(const double* __restrict__ Z, int n, const double* __restrict__ tau,
-                                const double* __restrict__ Vh, double* __restrict__ V) {
-  const int lane = threadIdx.x & 31;
+// per column, the column held in shared memory, H_k = I - tau_k v_k v_k^T acting on rows k+1..n-1.
+__global__ void __launch_bounds__(128) k_backtransform(const double* __restrict__ Z, int n,
+                                                       const double* __restrict__ tau, const double* __restrict__ Vh,
+                                                       double* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* out = reinterpret_cast<double*>(smem_raw) + (int64_t)warp * n;
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= n) return;
-  double* out = V + (int64_t)c * n;
   const double* src = Z + (int64_t)(n - 1 - c) * n;
   for (int i = lane; i < n; i += 32) out[i] = src[i];
   __syncwarp();
@@ -278,6 +451,8 @@ __global__ void k_backtransform(const double* __restrict__ Z, int n, const doubl
     for (int i = lane; i < m; i += 32) out[k + 1 + i] -= s * vk[i];
     __syncwarp();
   }
+  double* dst = V + (int64_t)c * n;
+  for (int i = lane; i < n; i += 32) dst[i] = out[i];
 }
 
 __global__ void k_add_diag(double* __restrict__ G, int n, double sh) {
@@ -302,7 +477,7 @@ int coop_grid(const void* kernel, int threads, size_t smem) {
 
 size_t sym_eig_workspace_doubles(int n) {
   const size_t nt = (size_t)(n - 1 + 31) / 32 + 1;
-  return 4 * (size_t)n * n + nt * 32 * nt + nt * nt + 6 * (size_t)n;
+  return 4 * (size_t)n * n + nt * 32 * nt + nt * nt + 8 * (size_t)n + 1024;
 }
 
 // Eigen-decomposition of the symmetric n x n matrix S (column-major): lam_desc (n, decreasing),
@@ -322,11 +497,31 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
   double* e = d + n;
   double* tau = e + n;
   double* lam_asc = tau + n;
+  double* vbuf = lam_asc + n;        // distributed reduction: v, p (n each), per-block partials (<= 1024)
+  double* pbuf = vbuf + n;
+  double* redb = pbuf + n;
   cudaError_t err = cudaMemcpyAsync(A, S, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (err != cudaSuccess) return err;
   cudaMemsetAsync(tau, 0, n * sizeof(double), s);
   cudaMemsetAsync(e, 0, n * sizeof(double), s);
-  {
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int gdist = std::max(1, std::min(nsm, 1024));
+  const size_t dist_smem = (size_t)((n + gdist - 1) / gdist + 2) * n * sizeof(double);
+  if (dist_smem <= 200 * 1024) {
+    // A stays in shared memory across the grid, one block per SM
+    cudaFuncSetAttribute((const void*)k_tridiag_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dist_smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_tridiag_dist, 256, dist_smem);
+    if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+    int nn_ = n;
+    const double* Ac = A;
+    void* args[] = {&Ac, &nn_, &d, &e, &tau, &Vh, &vbuf, &pbuf, &redb};
+    note_launch();
+    err = cudaLaunchCooperativeKernel((const void*)k_tridiag_dist, gdist, 256, args, dist_smem, s);
+    if (err != cudaSuccess) return err;
+  } else {
     const size_t smem = (size_t)n * sizeof(double);
     cudaFuncSetAttribute((const void*)k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int blocks = coop_grid((const void*)k_tridiag, 256, smem);
@@ -336,9 +531,17 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
     err = cudaLaunchCooperativeKernel((const void*)k_tridiag, blocks, 256, args, smem, s);
     if (err != cudaSuccess) return err;
   }
-  k_multisect<<<(n * 32 + 255) / 256, 256, 0, s>>>(d, e, n, lam_asc); note_launch();
-  k_twisted<<<(n + 127) / 128, 128, 0, s>>>(d, e, n, lam_asc, Z, A, LU); note_launch();
-  k_backtransform<<<(n * 32 + 127) / 128, 128, 0, s>>>(Z, n, tau, Vh, V); note_launch();
+  {
+    const size_t smem = 2 * (size_t)n * sizeof(double);
+    cudaFuncSetAttribute((const void*)k_multisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_multisect<<<(n * 32 + 127) / 128, 128, smem, s>>>(d, e, n, lam_asc); note_launch();
+  }
+  k_twisted<<<(n + 7) / 8, 8, 0, s>>>(d, e, n, lam_asc, Z, A, LU); note_launch();
+  {
+    const size_t smem = 4 * (size_t)n * sizeof(double);
+    cudaFuncSetAttribute((const void*)k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_backtransform<<<(n * 32 + 127) / 128, 128, smem, s>>>(Z, n, tau, Vh, V); note_launch();
+  }
   k_reverse<<<(n + 255) / 256, 256, 0, s>>>(lam_asc, n, lam_desc); note_launch();
   // shifted CholeskyQR, then CholeskyQR2: G = V^T V (+ s I), G = L L^T, V <- V L^{-T}
   for (int pass = 0; pass < 3; ++pass) {
@@ -356,7 +559,7 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
     }
     err = launch_cholesky(Z, n, status, s);
     if (err != cudaSuccess) return err;
-    launch_trsm_lt<double>(V, n, n, n, Z, LU, lam_asc, s);
+    launch_trsm_lt<double>(V, n, n, n, Z, LU, s);
   }
   return cudaGetLastError();
 }

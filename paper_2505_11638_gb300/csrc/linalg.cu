@@ -746,8 +746,10 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, c
       if (out64) {
         double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
         *o = accumulate ? *o + v : v;
-      } else
-        outT[gm * scm + gn * scn] = (T)v;
+      } else {
+        T* o = outT + gm * scm + gn * scn;
+        *o = accumulate ? (T)((double)*o + v) : (T)v;
+      }
     }
   }
 }
@@ -871,7 +873,8 @@ __global__ void __launch_bounds__(256) k_gemm_df(int64_t M, int64_t N, int64_t K
         double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
         *o = accumulate ? *o + v : v;
       } else {
-        out32[gm * scm + gn * scn] = (float)v;
+        float* o = out32 + gm * scm + gn * scn;
+        *o = accumulate ? (float)((double)*o + v) : (float)v;
       }
     }
   }
@@ -1028,152 +1031,206 @@ void launch_symmetrize(double* M, int n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------- triangular solve
-// X (p x ell, column-major) <- X L^{-T} with L lower (FP64, column-major n x n): row-wise
-// forward substitution x_j = (x_j - sum_{t<j} L[j,t] x_t) / L[j,j].  Lr = L row-major in T,
-// dinv = 1 / diag(L).  RB rows per block, one warp per row, the rows staged in shared memory.
+// X (p x n, column-major, leading dimension ld) <- X L^{-T}, L lower (FP64, column-major n x n):
+// blocked by 32-column panels, right-looking.  Per panel the rows are solved by forward
+// substitution (x_j = (x_j - sum_{t<j} L[j,t] x_t) / L[j,j], one thread per row, FP64), then
+// the trailing columns take the panel's contribution by a GEMM with W = -L^T
+// (X[:, J'] += X[:, J] W[J, J']).  The GEMM runs in double-float arithmetic for double X (FP64
+// accuracy on the FP32 pipes) and in FP32 for float X.
 template <typename T>
-__global__ void k_lower_to_rowmajor(const double* __restrict__ L, int n, T* __restrict__ Lr, double* __restrict__ dinv) {
+__global__ void k_neg_transpose(const double* __restrict__ L, int n, T* __restrict__ W) {
   const int64_t total = (int64_t)n * n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int j = (int)(e / n), t = (int)(e % n);  // Lr[j*n + t] = L[j, t]
-    Lr[e] = t <= j ? (T)L[j + (int64_t)t * n] : T(0);
-    if (t == j) dinv[j] = 1.0 / L[j + (int64_t)j * n];
-  }
-}
-
-template <typename T, int RB>
-__global__ void __launch_bounds__(RB * 32) k_trsm_rows(T* __restrict__ X, int64_t ld, int64_t p, int n,
-                                                      const T* __restrict__ Lr, const double* __restrict__ dinv) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);  // [n][RB]
-  const int64_t r0 = (int64_t)blockIdx.x * RB;
-  const int rows = (int)min((int64_t)RB, p - r0);
-  // coalesced load: for each column t, RB consecutive rows
-  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
-    const int t = e / RB, rr = e - t * RB;
-    xs[e] = rr < rows ? X[r0 + rr + (int64_t)t * ld] : T(0);
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < rows) {
-    for (int j = 0; j < n; ++j) {
-      const T* lrow = Lr + (int64_t)j * n;
-      T acc = T(0);
-      for (int t = lane; t < j; t += 32) acc += lrow[t] * xs[t * RB + warp];
-      acc = wsum(acc);
-      if (lane == 0) xs[j * RB + warp] = (T)(((double)xs[j * RB + warp] - (double)acc) * dinv[j]);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
-    const int t = e / RB, rr = e - t * RB;
-    if (rr < rows) X[r0 + rr + (int64_t)t * ld] = xs[e];
+    const int tt = (int)(e % n), j = (int)(e / n);  // W[tt + j n] = -L[j, tt] for j > tt
+    W[e] = j > tt ? (T)(-L[j + (int64_t)tt * n]) : T(0);
   }
 }
 
 template <typename T>
-void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* Lr, double* dinv, cudaStream_t s) {
-  const int blocks0 = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
-  k_lower_to_rowmajor<T><<<blocks0, 256, 0, s>>>(L, n, Lr, dinv); note_launch();
-  constexpr int RB = sizeof(T) == 4 ? 16 : 8;
-  const size_t smem = (size_t)n * RB * sizeof(T);
-  auto k = k_trsm_rows<T, RB>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<(unsigned)((p + RB - 1) / RB), RB * 32, smem, s>>>(X, ld, p, n, Lr, dinv); note_launch();
+__global__ void __launch_bounds__(128) k_trsm_panel(T* __restrict__ X, int64_t ld, int64_t p,
+                                                   const double* __restrict__ L, int n, int b0, int bs) {
+  __shared__ double Ls[32][33];
+  __shared__ double rinv[32];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int i = e % 32, j = e / 32;
+    Ls[i][j] = (i < bs && j <= i) ? L[(b0 + i) + (int64_t)(b0 + j) * n] : 0.0;
+  }
+  if (threadIdx.x < 32) rinv[threadIdx.x] = threadIdx.x < bs ? 1.0 / L[(int64_t)(b0 + threadIdx.x) * (n + 1)] : 0.0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // rows spread over the blocks first, so that few rows still occupy many SMs
+  for (int64_t row = blockIdx.x + (int64_t)gridDim.x * threadIdx.x; row < p; row += stride) {
+    T* xr = X + row + (int64_t)b0 * ld;
+    double x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = j < bs ? (double)xr[(int64_t)j * ld] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {          // column-oriented substitution: x_j final, then eliminated
+      x[j] *= rinv[j];
+#pragma unroll
+      for (int c = j + 1; c < 32; ++c) x[c] -= Ls[c][j] * x[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < bs) xr[(int64_t)j * ld] = (T)x[j];
+  }
 }
-template void launch_trsm_lt<float>(float*, int64_t, int64_t, int, const double*, float*, double*, cudaStream_t);
-template void launch_trsm_lt<double>(double*, int64_t, int64_t, int, const double*, double*, double*, cudaStream_t);
+
+// W: n x n scratch of T.
+template <typename T>
+void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* W, cudaStream_t s) {
+  const int blocks0 = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
+  k_neg_transpose<T><<<blocks0, 256, 0, s>>>(L, n, W); note_launch();
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int pblocks = (int)std::min<int64_t>(std::max<int64_t>((p + 127) / 128, nsm), 4096);
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int bs = std::min(32, n - b0);
+    k_trsm_panel<T><<<pblocks, 128, 0, s>>>(X, ld, p, L, n, b0, bs); note_launch();
+    const int c0 = b0 + bs;
+    if (c0 >= n) break;
+    if (std::is_same<T, double>::value) {
+      GemmDfArgs<double, double> g;
+      g.M = p; g.N = n - c0; g.K = bs;
+      g.A = (const double*)X + (int64_t)b0 * ld; g.sam = 1; g.sak = ld;
+      g.B = (const double*)W + b0 + (int64_t)c0 * n; g.sbk = 1; g.sbn = n;
+      g.out64 = (double*)X + (int64_t)c0 * ld; g.scm = 1; g.scn = ld;
+      g.accumulate = 1;
+      launch_gemm_df<double, double>(g, s);
+    } else {
+      GemmArgs<T> g;
+      g.M = p; g.N = n - c0; g.K = bs;
+      g.A = X + (int64_t)b0 * ld; g.sam = 1; g.sak = ld;
+      g.B = W + b0 + (int64_t)c0 * n; g.sbk = 1; g.sbn = n;
+      g.outT = X + (int64_t)c0 * ld; g.scm = 1; g.scn = ld;
+      g.accumulate = 1;
+      launch_gemm<T>(g, s);
+    }
+  }
+}
+template void launch_trsm_lt<float>(float*, int64_t, int64_t, int, const double*, float*, cudaStream_t);
+template void launch_trsm_lt<double>(double*, int64_t, int64_t, int, const double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------- FP64 Cholesky
-// Blocked right-looking Cholesky of the n x n SPD matrix A (column-major, lower triangle
-// used and overwritten by L, A = L L^T), one cooperative launch: per 32-wide panel, block 0
-// factors the diagonal block in shared memory, all blocks solve the panel below it, all
-// blocks update the trailing lower triangle.  A non-positive pivot sets kStatNotSpd.
+// Blocked right-looking Cholesky of the n x n SPD matrix A (column-major, lower triangle used
+// and overwritten by L, A = L L^T) in one cooperative launch, two grid barriers per 32-wide
+// panel:
+//   (a) all blocks solve the panel rows below the diagonal block (one thread per row, FP64);
+//   (b) all blocks update the trailing lower triangle in 32 x 32 tiles staged in shared memory;
+//       the block that updates the next diagonal tile factors it right away with one warp
+//       (lane i holds row i, columns eliminated by shuffles).
+// A non-positive or non-finite pivot sets kStatNotSpd; every block then leaves at the next barrier.
+namespace {
+constexpr int kCholNB = 32;
+
+// Factor the bs x bs diagonal block at (k0, k0) in place with warp 0 of the calling block.
+__device__ void chol_diag_block(double* __restrict__ A, int n, int k0, int bs, int* __restrict__ status) {
+  if (threadIdx.x >= 32) return;
+  const int i = threadIdx.x;
+  double a[kCholNB];
+#pragma unroll
+  for (int j = 0; j < kCholNB; ++j) a[j] = (i < bs && j <= i && j < bs) ? A[(k0 + i) + (int64_t)(k0 + j) * n] : 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < kCholNB; ++j) {
+    if (j < bs && !bad) {
+      const double piv = __shfl_sync(0xffffffffu, a[j], j);
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        bad = true;                         // uniform: every lane read the same pivot
+      } else {
+        const double d = sqrt(piv), r = 1.0 / d;
+        a[j] = i == j ? d : (i > j ? a[j] * r : 0.0);
+#pragma unroll
+        for (int c = j + 1; c < kCholNB; ++c) {
+          const double lcj = __shfl_sync(0xffffffffu, a[j], c);
+          if (c < bs && i >= c) a[c] -= a[j] * lcj;
+        }
+      }
+    }
+  }
+  if (bad) {
+    if (i == 0) atomicOr(status, kStatNotSpd);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < kCholNB; ++j)
+    if (i < bs && j <= i && j < bs) A[(k0 + i) + (int64_t)(k0 + j) * n] = a[j];
+}
+}  // namespace
+
 __global__ void __launch_bounds__(256) k_cholesky(double* __restrict__ A, int n, int* __restrict__ status) {
-  constexpr int NB = 32;
+  constexpr int NB = kCholNB;
   cg::grid_group grid = cg::this_grid();
   __shared__ double D[NB][NB + 1];
-  __shared__ int bad;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double rinv[NB];
+  __shared__ double Pi[NB][NB + 1], Pj[NB][NB + 1];
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  if (blockIdx.x == 0) chol_diag_block(A, n, 0, min(NB, n), status);
+  grid.sync();
   for (int k0 = 0; k0 < n; k0 += NB) {
-    const int bs = min(NB, n - k0);
-    if (blockIdx.x == 0) {
-      if (threadIdx.x == 0) bad = 0;
-      for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
-        const int i = e % bs, j = e / bs;
-        D[i][j] = A[(k0 + i) + (int64_t)(k0 + j) * n];
-      }
-      __syncthreads();
-      for (int j = 0; j < bs; ++j) {
-        if (threadIdx.x == 0) {
-          const double piv = D[j][j];
-          if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
-          D[j][j] = sqrt(fmax(piv, 0.0));
-        }
-        __syncthreads();
-        if (bad) break;
-        const double djj = D[j][j];
-        for (int i = j + 1 + threadIdx.x; i < bs; i += blockDim.x) D[i][j] /= djj;
-        __syncthreads();
-        for (int e = threadIdx.x; e < (bs - j - 1) * (bs - j - 1); e += blockDim.x) {
-          const int i = j + 1 + e % (bs - j - 1), c = j + 1 + e / (bs - j - 1);
-          if (c <= i) D[i][c] -= D[i][j] * D[c][j];
-        }
-        __syncthreads();
-      }
-      if (bad) {
-        if (threadIdx.x == 0) atomicOr(status, kStatNotSpd);
-      } else {
-        for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
-          const int i = e % bs, j = e / bs;
-          if (j <= i) A[(k0 + i) + (int64_t)(k0 + j) * n] = D[i][j];
-        }
-      }
-    }
-    grid.sync();
     if (*((volatile int*)status) & kStatNotSpd) return;
-    // panel solve: rows i >= k0+bs: L[i, k0:k0+bs] = A[i, k0:k0+bs] L_kk^{-T}
-    if (k0 + bs < n) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
-        const int i = e % bs, j = e / bs;
-        D[i][j] = A[(k0 + i) + (int64_t)(k0 + j) * n];
+    const int bs = min(NB, n - k0);
+    const int r0 = k0 + bs, m = n - r0;
+    if (m <= 0) break;
+    // (a) panel rows: L[i, k0:k0+bs] = A[i, k0:k0+bs] L_kk^{-T}
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int i = e % NB, j = e / NB;
+      D[i][j] = (i < bs && j <= i) ? A[(k0 + i) + (int64_t)(k0 + j) * n] : 0.0;
+    }
+    if (threadIdx.x < NB) rinv[threadIdx.x] = threadIdx.x < bs ? 1.0 / A[(int64_t)(k0 + threadIdx.x) * (n + 1)] : 0.0;
+    __syncthreads();
+    // rows spread over the blocks first (few rows: one or two per SM)
+    for (int64_t i = r0 + blockIdx.x + (int64_t)gridDim.x * threadIdx.x; i < n; i += gthreads) {
+      double x[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) x[j] = j < bs ? A[i + (int64_t)(k0 + j) * n] : 0.0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        x[j] *= rinv[j];
+#pragma unroll
+        for (int c = j + 1; c < NB; ++c) x[c] -= D[c][j] * x[j];
       }
-      __syncthreads();
-      for (int64_t i = k0 + bs + gtid; i < n; i += gthreads) {
-        double x[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) x[j] = j < bs ? A[i + (int64_t)(k0 + j) * n] : 0.0;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (j < bs) {
-            double v = x[j];
-#pragma unroll
-            for (int t = 0; t < NB; ++t)
-              if (t < j) v -= D[j][t] * x[t];
-            x[j] = v / D[j][j];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-          if (j < bs) A[i + (int64_t)(k0 + j) * n] = x[j];
-      }
+      for (int j = 0; j < NB; ++j)
+        if (j < bs) A[i + (int64_t)(k0 + j) * n] = x[j];
     }
     grid.sync();
-    // trailing update of the lower triangle: A[i, c] -= sum_t L[i, k0+t] L[c, k0+t]
-    const int m = n - k0 - bs;
-    if (m > 0) {
-      const int64_t total = (int64_t)m * m;
-      for (int64_t e = gtid; e < total; e += gthreads) {
-        const int64_t i = e % m, c = e / m;
-        if (c > i) continue;
-        const int64_t gi = k0 + bs + i, gc = k0 + bs + c;
-        double s = 0.0;
-        for (int t = 0; t < bs; ++t) s += A[gi + (int64_t)(k0 + t) * n] * A[gc + (int64_t)(k0 + t) * n];
-        A[gi + gc * n] -= s;
+    // (b) trailing update of the lower triangle in 32 x 32 tiles: A[I, J] -= P_I P_J^T with
+    //     P = L[:, k0:k0+bs]; tile (0, 0) (the next diagonal block) goes to block 0 first
+    const int nt = (m + NB - 1) / NB;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
+      int ti = 0;                           // tile (ti, tj), tj <= ti, in row-major lower order
+      while ((ti + 1) * (ti + 2) / 2 <= tIdx) ++ti;
+      const int tj = tIdx - ti * (ti + 1) / 2;
+      const int ri = r0 + ti * NB, rj = r0 + tj * NB;
+      __syncthreads();
+      for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        Pi[r][c] = (ri + r < n && c < bs) ? A[(ri + r) + (int64_t)(k0 + c) * n] : 0.0;
+        Pj[r][c] = (rj + r < n && c < bs) ? A[(rj + r) + (int64_t)(k0 + c) * n] : 0.0;
+      }
+      __syncthreads();
+      const int r = threadIdx.x % NB;
+#pragma unroll
+      for (int q = 0; q < NB * NB / 256; ++q) {
+        const int c = threadIdx.x / NB + q * (256 / NB);
+        const int gi = ri + r, gj = rj + c;
+        if (gi < n && gj < n && gj <= gi) {
+          double s = 0.0;
+#pragma unroll
+          for (int t = 0; t < NB; ++t) s += Pi[r][t] * Pj[c][t];
+          A[gi + (int64_t)gj * n] -= s;
+        }
+      }
+      if (tIdx == 0) {                      // the next diagonal block is final: factor it
+        __syncthreads();
+        chol_diag_block(A, n, r0, min(NB, m), status);
       }
     }
     grid.sync();

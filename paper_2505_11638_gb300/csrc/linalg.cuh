@@ -97,7 +97,7 @@ void launch_shift_add_mixed(const double* Y, const float* Om, const double* nu, 
                             int ell, cudaStream_t s);
 
 template <typename T>
-void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* Lr, double* dinv, cudaStream_t s);
+void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* W, cudaStream_t s);
 cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s);
 // eigen.cu: FP64 symmetric eigen-decomposition (tridiagonal reduction, multisection, twisted
 // factorization, back-transform, CholeskyQR), eigenvalues decreasing.
