@@ -194,8 +194,8 @@ ngd_status ensure_ell(ngd_ctx* ctx, int ell) {
     TRY(dalloc(ctx, &ctx->Zw64, (size_t)ctx->N * ell * 8));
     TRY(dalloc(ctx, &ctx->U64, (size_t)ctx->ldP * ell * 8));
     CK(cudaMemsetAsync(ctx->U64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
-    TRY(dalloc(ctx, &ctx->Uh, (size_t)ctx->ldP * ell * 4));
-    TRY(dalloc(ctx, &ctx->Ul, (size_t)ctx->ldP * ell * 4));
+    TRY(dalloc(ctx, &ctx->Uh, (size_t)ctx->ldP * ((ell + 3) / 4 * 4) * 4));
+    TRY(dalloc(ctx, &ctx->Ul, (size_t)ctx->ldP * ((ell + 3) / 4 * 4) * 4));
     TRY(dalloc(ctx, &ctx->w1p, (size_t)fused_pcg_blocks() * ell * sizeof(float2)));
     TRY(dalloc(ctx, &ctx->w2f, (size_t)ell * sizeof(float2)));
     CK(cudaMemsetAsync(ctx->Y64, 0, (size_t)ctx->ldP * ell * 8, ctx->stream));
@@ -603,7 +603,7 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
         launch_split_transpose_df<double>((const double*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
       else
         launch_split_transpose_df<float>((const float*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
-      fa.Uh = ctx->Uh; fa.Ul = ctx->Ul; fa.lam = lam; fa.ell = ell;
+      fa.Uh = ctx->Uh; fa.Ul = ctx->Ul; fa.lam = lam; fa.ell = ell; fa.ldu = (ell + 3) / 4 * 4;
     }
     fa.mu_d = mu_d; fa.mu_h = mu_h;
     fa.g = g; fa.x = x; fa.r = r; fa.z = z; fa.pv = pv; fa.q = q;

@@ -545,12 +545,12 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
   k_reverse<<<(n + 255) / 256, 256, 0, s>>>(lam_asc, n, lam_desc); note_launch();
   // shifted CholeskyQR, then CholeskyQR2: G = V^T V (+ s I), G = L L^T, V <- V L^{-T}
   for (int pass = 0; pass < 3; ++pass) {
-    GemmArgs<double> g;
+    GemmDfArgs<double, double> g;          // FP64-accurate Gram on the FP32 pipes
     g.M = n; g.N = n; g.K = n;
     g.A = V; g.sam = n; g.sak = 1;
     g.B = V; g.sbk = 1; g.sbn = n;
-    g.outT = Z; g.scm = 1; g.scn = n;
-    launch_gemm<double>(g, s);
+    g.out64 = Z; g.scm = 1; g.scn = n;
+    launch_gemm_df<double, double>(g, s);
     launch_symmetrize(Z, n, s);
     // shift 1e-12 n on the first pass: far above the rounding of the Gram matrix of n unit columns
     // (~eps n), far below the unit diagonal

@@ -1118,15 +1118,16 @@ template void launch_trsm_lt<double>(double*, int64_t, int64_t, int, const doubl
 
 // ---------------------------------------------------------------------------- FP64 Cholesky
 // Blocked right-looking Cholesky of the n x n SPD matrix A (column-major, lower triangle used
-// and overwritten by L, A = L L^T) in one cooperative launch, two grid barriers per 32-wide
-// panel:
+// and overwritten by L, A = L L^T) in one cooperative launch, two grid barriers per 16-wide
+// panel (FP64 latency on GB300 is ~64 cycles per operation, ~1100 for a square root and a
+// division, so the sequential chain through the diagonal blocks sets the time):
 //   (a) all blocks solve the panel rows below the diagonal block (one thread per row, FP64);
-//   (b) all blocks update the trailing lower triangle in 32 x 32 tiles staged in shared memory;
+//   (b) all blocks update the trailing lower triangle in 16 x 16 tiles staged in shared memory;
 //       the block that updates the next diagonal tile factors it right away with one warp
 //       (lane i holds row i, columns eliminated by shuffles).
 // A non-positive or non-finite pivot sets kStatNotSpd; every block then leaves at the next barrier.
 namespace {
-constexpr int kCholNB = 32;
+constexpr int kCholNB = 16;        // short panels: the per-column FP64 chain is the critical path
 
 // Factor the bs x bs diagonal block at (k0, k0) in place with warp 0 of the calling block.
 __device__ void chol_diag_block(double* __restrict__ A, int n, int k0, int bs, int* __restrict__ status) {
@@ -1143,7 +1144,7 @@ __device__ void chol_diag_block(double* __restrict__ A, int n, int k0, int bs, i
       if (!(piv > 0.0) || !isfinite(piv)) {
         bad = true;                         // uniform: every lane read the same pivot
       } else {
-        const double d = sqrt(piv), r = 1.0 / d;
+        const double r = rsqrt(piv), d = piv * r;   // one reciprocal square root per column
         a[j] = i == j ? d : (i > j ? a[j] * r : 0.0);
 #pragma unroll
         for (int c = j + 1; c < kCholNB; ++c) {

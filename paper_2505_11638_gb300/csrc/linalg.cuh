@@ -113,8 +113,9 @@ struct FusedPcgArgs {
   const float* J = nullptr; int64_t ldJ = 0, N = 0, p = 0;   // J: N x ldJ row-major, zero beyond column p
   const double* w = nullptr;                                 // residual weights (N)
   const float *wh = nullptr, *wl = nullptr;                  // the weights split into FP32 pairs (N)
-  const float* Uh = nullptr; const float* Ul = nullptr;      // U = Uh + Ul, j-major: U[j, k] at j * ell + k
-  const double* lam = nullptr; int ell = 0;                  // ell = 0: no preconditioner
+  const float* Uh = nullptr; const float* Ul = nullptr;      // U = Uh + Ul, j-major: U[j, k] at j * ldu + k
+  const double* lam = nullptr; int ell = 0, ldu = 0;         // ell = 0: no preconditioner; ldu = ell rounded
+                                                             // up to a multiple of 4 (zero padding)
   const double* mu_d = nullptr; double mu_h = 0.0;           // mu from device (if set) or host
   const double* g = nullptr;                                 // right-hand side (p)
   double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;   // p each

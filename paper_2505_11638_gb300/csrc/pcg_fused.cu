@@ -32,7 +32,6 @@ namespace {
 
 constexpr int kT = 256;            // threads per block (one block per SM, 8 warps)
 constexpr int kW = kT / 32;        // warps per block
-constexpr int kNG = kT / 64;       // column groups in the j-slice phases
 constexpr int kMaxSlice = 128;     // largest j slice per block (p <= kMaxSlice * G)
 
 __device__ __forceinline__ uint64_t evict_first_policy() {
@@ -76,10 +75,17 @@ __device__ __forceinline__ double grid_total(const double* red, int slot, double
 
 constexpr int kR = 2;              // J rows per block-wide reduction round of phase A
 
+// The block's slice [c0, c1) of the parameter index j: starts on multiples of 4, so that the
+// slice's parts of 4-aligned arrays are read as float4.
+__device__ __forceinline__ void col_slice(int64_t p, int b, int G, int64_t& c0, int64_t& c1) {
+  const int64_t n4 = (p + 3) / 4;
+  c0 = 4 * (n4 * b / G);
+  c1 = min(p, 4 * (n4 * (b + 1) / G));
+}
+
 struct Smem {
   DF wred[2][kR][kW];
   double dred[kT + 1];
-  DF cgrp[kNG][64];
   float2 rs[kMaxSlice];
 };
 
@@ -220,8 +226,8 @@ __device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, flo
 
 // The block's j slice of v, split into FP32 pairs for phase A.
 __device__ __forceinline__ void split_slice(const FusedPcgArgs& a, const double* v) {
-  const int G = gridDim.x, b = blockIdx.x;
-  const int64_t cb0 = a.p * b / G, cb1 = a.p * (b + 1) / G;
+  int64_t cb0, cb1;
+  col_slice(a.p, blockIdx.x, gridDim.x, cb0, cb1);
   for (int64_t j = cb0 + threadIdx.x; j < cb1; j += kT) {
     float h, l;
     split_df(v[j], h, l);
@@ -231,86 +237,88 @@ __device__ __forceinline__ void split_slice(const FusedPcgArgs& a, const double*
 }
 
 // Phase B: q_j = sum_b y_b[j] + mu v_j on the block's j slice; returns the block's sum of v_j q_j.
-__device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double* v, double mu, double* q, Smem& sm) {
-  const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
-  const int64_t cb0 = a.p * b / G, cb1 = a.p * (b + 1) / G;
-  const int jj = tid & 63, grp = tid >> 6;
+// Thread (c4, g): columns 4 c4 .. 4 c4 + 3 of the slice, partials b = g, g + 8, ...; scr: shared
+// scratch of 8 x 32 x 4 double-float values.
+__device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double* v, double mu, double* q, DF* scr) {
+  const int tid = threadIdx.x, G = gridDim.x;
+  int64_t cb0, cb1;
+  col_slice(a.p, blockIdx.x, G, cb0, cb1);
+  const int c4 = tid & 31, g = tid >> 5;                 // 32 column quads x 8 partial groups
   double vq = 0.0;
-  for (int64_t j0 = cb0; j0 < cb1; j0 += 64) {
-    const int64_t j = j0 + jj;
-    DF acc{0.f, 0.f};
+  for (int64_t j0 = cb0; j0 < cb1; j0 += 128) {
+    const int64_t j = j0 + 4 * c4;
+    DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (j < cb1) {
-      for (int bb0 = grp; bb0 < G; bb0 += 8 * kNG) {   // eight partials in flight per thread
-        float hv[8], lv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int bb = bb0 + u * kNG;
-          hv[u] = bb < G ? __ldcg(a.yph + (int64_t)bb * a.ldJ + j) : 0.f;
-          lv[u] = bb < G ? __ldcg(a.ypl + (int64_t)bb * a.ldJ + j) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc = df_add(acc, DF{hv[u], lv[u]});
+#pragma unroll 4
+      for (int bb = g; bb < G; bb += 8) {
+        const float4 h = __ldcg(reinterpret_cast<const float4*>(a.yph + (int64_t)bb * a.ldJ + j));
+        const float4 l = __ldcg(reinterpret_cast<const float4*>(a.ypl + (int64_t)bb * a.ldJ + j));
+        acc[0] = df_add(acc[0], DF{h.x, l.x});
+        acc[1] = df_add(acc[1], DF{h.y, l.y});
+        acc[2] = df_add(acc[2], DF{h.z, l.z});
+        acc[3] = df_add(acc[3], DF{h.w, l.w});
       }
     }
-    sm.cgrp[grp][jj] = acc;
-    __syncthreads();
-    if (grp == 0 && j < cb1) {
-      DF s = sm.cgrp[0][jj];
 #pragma unroll
-      for (int g2 = 1; g2 < kNG; ++g2) s = df_add(s, sm.cgrp[g2][jj]);
-      const double vj = __ldcg(v + j);
-      const double qj = df_to_double(s) + mu * vj;
-      q[j] = qj;
-      vq += vj * qj;
+    for (int e = 0; e < 4; ++e) scr[(g * 32 + c4) * 4 + e] = acc[e];
+    __syncthreads();
+    if (tid < 128) {
+      const int cc = tid >> 2, e = tid & 3;              // one thread per column
+      const int64_t jc = j0 + tid;
+      if (jc < cb1) {
+        DF s = scr[cc * 4 + e];
+#pragma unroll
+        for (int g2 = 1; g2 < 8; ++g2) s = df_add(s, scr[(g2 * 32 + cc) * 4 + e]);
+        const double vj = __ldcg(v + jc);
+        const double qj = df_to_double(s) + mu * vj;
+        q[jc] = qj;
+        vq += vj * qj;
+      }
     }
     __syncthreads();
   }
   return vq;
 }
 
-// Partial U^T r over the block's j slice (r_j already split into sm.rs): a thread takes up to
-// kKT values of k at once, the slice's rows of U read in order (coalesced across k).
-constexpr int kKT = 2;             // k values per thread per pass (ell <= kKT * kT in one pass)
-__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm) {
-  for (int k0 = threadIdx.x; k0 < a.ell; k0 += kKT * kT) {
-    const float* uh = a.Uh + cb0 * a.ell + k0;
-    const float* ul = a.Ul + cb0 * a.ell + k0;
-    bool in[kKT];
-    DF acc[kKT][2];
-#pragma unroll
-    for (int u = 0; u < kKT; ++u) {
-      in[u] = k0 + u * kT < a.ell;
-      acc[u][0] = acc[u][1] = DF{0.f, 0.f};
+// Partial U^T r over the block's j slice (r_j already split into sm.rs): thread (k4, half) takes
+// the four k of quad k4 (U rows padded to ldu, a multiple of 4: one float4 per row and word)
+// and every other row of the slice; the two halves are combined through shared memory (scr:
+// kT / 2 x 4 double-float values).
+__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm, DF* scr) {
+  const int nk4 = a.ldu / 4;
+  const int half = threadIdx.x / (kT / 2), tq = threadIdx.x % (kT / 2);
+  for (int base = 0; base < nk4; base += kT / 2) {
+    const int k4 = base + tq;
+    DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (k4 < nk4) {
+      const float4* uh = reinterpret_cast<const float4*>(a.Uh + cb0 * a.ldu) + k4;
+      const float4* ul = reinterpret_cast<const float4*>(a.Ul + cb0 * a.ldu) + k4;
+#pragma unroll 4
+      for (int jj = half; jj < ncol; jj += 2) {
+        const float2 rr = sm.rs[jj];
+        const float4 h = __ldg(uh + (int64_t)jj * nk4), l = __ldg(ul + (int64_t)jj * nk4);
+        df_add_prod2(acc[0], h.x, l.x, rr.x, rr.y);
+        df_add_prod2(acc[1], h.y, l.y, rr.x, rr.y);
+        df_add_prod2(acc[2], h.z, l.z, rr.x, rr.y);
+        df_add_prod2(acc[3], h.w, l.w, rr.x, rr.y);
+      }
     }
-    int jj = 0;
-#pragma unroll 2
-    for (; jj + 1 < ncol; jj += 2) {
-      const float2 r0 = sm.rs[jj], r1 = sm.rs[jj + 1];
+    if (half == 1) {
 #pragma unroll
-      for (int u = 0; u < kKT; ++u) {
-        if (in[u]) {
-          const int64_t o0 = (int64_t)jj * a.ell + u * kT, o1 = o0 + a.ell;
-          df_add_prod2(acc[u][0], __ldg(uh + o0), __ldg(ul + o0), r0.x, r0.y);
-          df_add_prod2(acc[u][1], __ldg(uh + o1), __ldg(ul + o1), r1.x, r1.y);
+      for (int e = 0; e < 4; ++e) scr[tq * 4 + e] = acc[e];
+    }
+    __syncthreads();
+    if (half == 0 && k4 < nk4) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = 4 * k4 + e;
+        if (k < a.ell) {
+          const DF s = df_add(acc[e], scr[tq * 4 + e]);
+          __stcg(a.w1p + (int64_t)blockIdx.x * a.ell + k, make_float2(s.hi, s.lo));
         }
       }
     }
-    if (jj < ncol) {
-      const float2 r0 = sm.rs[jj];
-#pragma unroll
-      for (int u = 0; u < kKT; ++u)
-        if (in[u]) {
-          const int64_t o0 = (int64_t)jj * a.ell + u * kT;
-          df_add_prod2(acc[u][0], __ldg(uh + o0), __ldg(ul + o0), r0.x, r0.y);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < kKT; ++u) {
-      if (in[u]) {
-        const DF s = df_add(acc[u][0], acc[u][1]);
-        __stcg(a.w1p + (int64_t)blockIdx.x * a.ell + k0 + u * kT, make_float2(s.hi, s.lo));
-      }
-    }
+    __syncthreads();
   }
 }
 
@@ -321,6 +329,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   float4* ring = reinterpret_cast<float4*>(dsm);
   float4* vls = ring + (int64_t)S * C4 * kT;             // low words of the matvec's vector
   float2* w2s = reinterpret_cast<float2*>(dsm);          // phase E only (aliases the ring)
+  DF* scr = reinterpret_cast<DF*>(dsm);                  // phases B, C only (aliases the ring)
   __shared__ Smem sm;
   const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
   const double mu = a.mu_d ? *a.mu_d : a.mu_h;
@@ -330,11 +339,12 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     grid.sync();
     gv_rows<C4, S>(a, ring, vls, sm);
     grid.sync();
-    gv_finish(a, a.pv, mu, a.q, sm);
+    gv_finish(a, a.pv, mu, a.q, scr);
     return;
   }
 
-  const int64_t cb0 = a.p * b / G, cb1 = a.p * (b + 1) / G;
+  int64_t cb0, cb1;
+  col_slice(a.p, b, G, cb0, cb1);
   const int ncol = (int)(cb1 - cb0);
   const int kb0 = (int)((int64_t)a.ell * b / G), kb1 = (int)((int64_t)a.ell * (b + 1) / G);
   const bool pre = a.ell > 0;
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   }
   rr = block_allsum(rr, sm.dred);
   if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
-  if (pre) utr_partial(a, cb0, ncol, sm);
+  if (pre) utr_partial(a, cb0, ncol, sm, scr);
   grid.sync();
 
   int it = 0, status = 0;
@@ -398,25 +408,31 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     // E: z = P^{-1} r on the j slice, r . z
     double rzp = 0.0;
     if (pre) {
-      for (int k = tid; k < a.ell; k += kT) w2s[k] = __ldcg(a.w2 + k);
+      for (int k = tid; k < a.ldu; k += kT) w2s[k] = k < a.ell ? __ldcg(a.w2 + k) : make_float2(0.f, 0.f);
       __syncthreads();
-      // a warp takes eight rows of U at once (j-major: each row contiguous), lanes over k
+      // a warp takes eight rows of U at once (j-major, rows padded to ldu), lanes over k quads
       const int lane = tid & 31, warp = tid >> 5;
+      const int nk4 = a.ldu / 4;
       for (int j0 = 8 * warp; j0 < ncol; j0 += 8 * kW) {
         const int nq = min(8, ncol - j0);
         DF acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
-        const float* uh0 = a.Uh + (cb0 + j0) * a.ell;
-        const float* ul0 = a.Ul + (cb0 + j0) * a.ell;
-#pragma unroll 2
-        for (int k = lane; k < a.ell; k += 32) {
-          const float2 ww = w2s[k];
+        const float4* uh0 = reinterpret_cast<const float4*>(a.Uh + (cb0 + j0) * a.ldu);
+        const float4* ul0 = reinterpret_cast<const float4*>(a.Ul + (cb0 + j0) * a.ldu);
+        for (int k4 = lane; k4 < nk4; k4 += 32) {
+          const float4 wa = reinterpret_cast<const float4*>(w2s)[2 * k4];       // w2[4 k4], w2[4 k4 + 1]
+          const float4 wb = reinterpret_cast<const float4*>(w2s)[2 * k4 + 1];   // w2[4 k4 + 2], w2[4 k4 + 3]
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (q < nq)
-              df_add_prod2(acc[q], __ldg(uh0 + (int64_t)q * a.ell + k), __ldg(ul0 + (int64_t)q * a.ell + k), ww.x,
-                           ww.y);
+          for (int q = 0; q < 8; ++q) {
+            if (q < nq) {
+              const float4 h = __ldg(uh0 + (int64_t)q * nk4 + k4), l = __ldg(ul0 + (int64_t)q * nk4 + k4);
+              df_add_prod2(acc[q], h.x, l.x, wa.x, wa.y);
+              df_add_prod2(acc[q], h.y, l.y, wa.z, wa.w);
+              df_add_prod2(acc[q], h.z, l.z, wb.x, wb.y);
+              df_add_prod2(acc[q], h.w, l.w, wb.z, wb.w);
+            }
+          }
         }
         const DF s = warp_reduce_scatter8(acc);          // lane L: row j0 + (L >> 2)
         const int q = lane >> 2;
@@ -457,7 +473,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     gv_rows<C4, S>(a, ring, vls, sm);
     grid.sync();
     {
-      double pqp = gv_finish(a, a.pv, mu, a.q, sm);
+      double pqp = gv_finish(a, a.pv, mu, a.q, scr);
       pqp = block_allsum(pqp, sm.dred);
       if (tid == 0) __stcg(a.red + b * 4 + 0, pqp);
     }
@@ -482,7 +498,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     }
     rr = block_allsum(rr, sm.dred);
     if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
-    if (pre) utr_partial(a, cb0, ncol, sm);
+    if (pre) utr_partial(a, cb0, ncol, sm, scr);
     ++it;
     grid.sync();
   }
@@ -556,8 +572,8 @@ int fused_pcg_blocks() { return std::min(num_sms(), kT); }
 bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell) {
   const int G = fused_pcg_blocks();
   const int64_t c4 = (ldJ / 4 + kT - 1) / kT;
-  return G >= 1 && ldJ % 4 == 0 && c4 >= 1 && c4 <= kMaxC4 && (p + G - 1) / G <= kMaxSlice && ell >= 0 &&
-         ell <= 2048;
+  return G >= 1 && ldJ % 4 == 0 && c4 >= 1 && c4 <= kMaxC4 && 4 * (((p + 3) / 4 + G - 1) / G) <= kMaxSlice &&
+         ell >= 0 && ell <= 2048;
 }
 
 cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s) {
@@ -577,7 +593,8 @@ cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s) {
 }
 
 // U (column-major, leading dimension ldu, p x ell, float or double) -> Uh + Ul in j-major order
-// (U[j, k] at j * ell + k); 32 x 32 tiles transposed through shared memory.
+// with rows padded to ldr = ell rounded up to a multiple of 4 (U[j, k] at j * ldr + k, zero for
+// k >= ell); 32 x 32 tiles transposed through shared memory.
 template <typename TU>
 __global__ void k_split_transpose_df(const TU* __restrict__ U, int64_t ldu, int64_t p, int ell, float* __restrict__ Uh,
                                      float* __restrict__ Ul) {
@@ -594,18 +611,19 @@ __global__ void k_split_transpose_df(const TU* __restrict__ U, int64_t ldu, int6
     tl[i][tx] = l;
   }
   __syncthreads();
+  const int ldr = (ell + 3) / 4 * 4;
   for (int i = ty; i < 32; i += 8) {
     const int64_t j = j0 + i;
     const int k = k0 + tx;
-    if (j < p && k < ell) {
-      Uh[j * ell + k] = th[tx][i];
-      Ul[j * ell + k] = tl[tx][i];
+    if (j < p && k < ldr) {
+      Uh[j * ldr + k] = th[tx][i];   // zero for k >= ell (tile loaded as zero there)
+      Ul[j * ldr + k] = tl[tx][i];
     }
   }
 }
 template <typename TU>
 void launch_split_transpose_df(const TU* U, int64_t ldu, int64_t p, int ell, float* Uh, float* Ul, cudaStream_t s) {
-  dim3 grid((unsigned)((p + 31) / 32), (unsigned)((ell + 31) / 32));
+  dim3 grid((unsigned)((p + 31) / 32), (unsigned)((ell + 3) / 4 * 4 + 31) / 32);
   k_split_transpose_df<TU><<<grid, 256, 0, s>>>(U, ldu, p, ell, Uh, Ul); note_launch();
 }
 template void launch_split_transpose_df<float>(const float*, int64_t, int64_t, int, float*, float*, cudaStream_t);
