@@ -5,7 +5,11 @@ points, FP32 activations and Jacobian, FP64 CG reductions, ell = 500, mu = 1e-7,
 synthetic Monte-Carlo points drawn from a fixed seed.  One step = one ngd_step: gradient and
 Jacobian, Gaussian test matrix, sketch, Nystrom factor, preconditioned CG, Armijo, update.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sketch f32|tf32|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sketch f64|f32|tf32|bf16]
+
+--sketch f64 (default) forms the sketch and the Nystrom factor in FP64-accurate arithmetic
+(double-float on the FP32 pipes for the FP32 Jacobian); f32/tf32/bf16 are the lower-precision
+variants of the precision study (larger shift nu, more PCG iterations).
 
 N > 1 runs under torchrun: every rank steps an independent replica (its own seed), with no
 data-path collective; the barrier and the max-over-ranks timing use the process group.
@@ -109,14 +113,15 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it still matches the sources."""
+def profiled_traffic(kernel: str, field: str = "traffic_bytes_per_launch"):
+    """DRAM bytes (per launch, or per the unit `field` names) of `kernel` from a committed ncu
+    summary, if that summary was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", f"{kernel}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(field + r":\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
     if not m or not s or s.group(1) != kernel_source_sha():
         return None
@@ -245,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     barrier()
 
-    # Gramian matvecs/s and the roofline of the matvec kernels, timed alone on the context stream
+    # The Gramian matvec alone (ngd_gramian_mv: k_pcg_fused in matvec mode), timed on the context stream
     v = torch.randn(pr.p, dtype=torch.float64, device="cuda")
     ctx.gramian_mv(theta, v, wl.mu)
     y = torch.empty_like(v)
@@ -262,16 +267,41 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     gv_ms = ev0.elapsed_time(ev1) / reps
     ldJ = (pr.p + 31) // 32 * 32
-    gv_bytes = 2.0 * pr.n * ldJ * 4 + 6.0 * pr.p * 8 + 3.0 * pr.n * 8
+    j_bytes = float(pr.n * ldJ * (4 if wl.dtype == "f32" else 8))
+
+    # Roofline of the dominant kernel, k_pcg_fused (the whole preconditioned CG in one launch), per
+    # CG iteration: PCG at the final theta with a fresh Nystrom factor, rtol 0 and two fixed
+    # iteration counts; the difference cancels the per-solve setup.  Algorithmic DRAM bytes per
+    # iteration: one read of J plus ~12 p-vectors of float64 (U, 2 p l 8 bytes, is read from L2).
+    g_fin, _, _ = ctx.gradient(theta)
+    Om_f, Y_f = ctx.nystrom_sketch(None, wl.ell, seed=rank, step=10 ** 6, prec=args.sketch)
+    U_f, lam_f, _ = ctx.nystrom_factor(wl.ell, Om_f, Y_f, args.sketch)
+
+    def pcg_ms(k):
+        ctx.pcg_solve(None, g_fin, wl.mu, U_f, lam_f, wl.ell, rtol=0.0, maxit=k)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, it, _ = ctx.pcg_solve(None, g_fin, wl.mu, U_f, lam_f, wl.ell, rtol=0.0, maxit=k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), it
+
+    t_lo, k_lo = pcg_ms(20)
+    t_hi, k_hi = pcg_ms(220)
+    us_it = (t_hi - t_lo) / max(k_hi - k_lo, 1) * 1e3
+    bytes_it = j_bytes + 12.0 * pr.p * 8
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    achieved = gv_bytes / (gv_ms * 1e-3) / 1e9
-    roofline = {"kernel": "gramian_mv (k_rowdot + k_coldot: J streamed twice, FP32)", "bound": "hbm",
-                "achieved": achieved, "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-                "frac": achieved / (hbm if hbm else 6800.0),
+    peak = hbm if hbm else 6800.0
+    achieved = bytes_it / (us_it * 1e-6) / 1e9
+    roofline = {"kernel": "k_pcg_fused (whole PCG, one launch); unit: one CG iteration", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if hbm else "fallback 6.8 TB/s",
-                "traffic": profiled_traffic("gramian_mv_poisson5d"), "bytes_per_launch": gv_bytes,
-                "ms_per_launch": gv_ms}
+                "traffic": profiled_traffic("k_pcg_fused_poisson5d", "traffic_bytes_per_iteration"),
+                "bytes_per_iteration": bytes_it,
+                "us_per_iteration": us_it,
+                "matvec": {"kernel": "k_pcg_fused, matvec mode (ngd_gramian_mv)", "us": gv_ms * 1e3,
+                           "bytes": j_bytes, "GB/s": j_bytes / (gv_ms * 1e-3) / 1e9}}
 
     phases = {k: float(np.mean([i[k] for i in infos])) for k in
               ["ms_linearize", "ms_sketch", "ms_factor", "ms_pcg", "ms_linesearch"]}

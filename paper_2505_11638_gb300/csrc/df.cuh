@@ -178,6 +178,18 @@ __device__ __forceinline__ void df2_add_prod(DF2& s, f2x a, f2x bh, f2x nbh, f2x
   s.lo = add2(add2(fma2(a, bl, s.lo), pe), e);
 }
 
+// the same with the negated product formed from a with both sign bits flipped (an integer
+// operation off the FP32 pipe) instead of a stored -bh
+__device__ __forceinline__ void df2_add_prod_nj(DF2& s, f2x a, f2x bh, f2x bl) {
+  const f2x pn = mul2(a ^ 0x8000000080000000ull, bh);
+  const f2x pe = fma2(a, bh, pn);
+  const f2x t = sub2(s.hi, pn);
+  const f2x z = sub2(t, s.hi);
+  const f2x e = sub2(sub2(s.hi, sub2(t, z)), add2(pn, z));
+  s.hi = t;
+  s.lo = add2(add2(fma2(a, bl, s.lo), pe), e);
+}
+
 __device__ __forceinline__ void df2_split(DF2 s, DF& a, DF& b) {
   upk2(s.hi, a.hi, b.hi);
   upk2(s.lo, a.lo, b.lo);

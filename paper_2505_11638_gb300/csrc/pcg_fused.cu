@@ -30,7 +30,7 @@ namespace cg = cooperative_groups;
 namespace ngd {
 namespace {
 
-constexpr int kT = 256;            // threads per block (one block per SM, 8 warps)
+constexpr int kT = 384;            // threads per block (one block per SM, 12 warps)
 constexpr int kW = kT / 32;        // warps per block
 constexpr int kMaxSlice = 128;     // largest j slice per block (p <= kMaxSlice * G)
 
@@ -73,7 +73,6 @@ __device__ __forceinline__ double grid_total(const double* red, int slot, double
   return block_allsum(v, sred);
 }
 
-constexpr int kR = 2;              // J rows per block-wide reduction round of phase A
 
 // The block's slice [c0, c1) of the parameter index j: starts on multiples of 4, so that the
 // slice's parts of 4-aligned arrays are read as float4.
@@ -84,142 +83,143 @@ __device__ __forceinline__ void col_slice(int64_t p, int b, int G, int64_t& c0, 
 }
 
 struct Smem {
-  DF wred[2][kR][kW];
+  DF dpart[6][kT / 64];             // phase A: per ring stage, the dot group's warp sums
   double dred[kT + 1];
   float2 rs[kMaxSlice];
 };
 
 // Phase A: y_b = sum over the block's rows n of w_n (J_n . v) J_n, written as an FP32 pair.
-// Rows are taken kR at a time (one block barrier per round); row n sits in ring stage n % S and
-// is prefetched S - kR rows ahead.  Each thread copies and reads back only its own 16-byte slots,
-// so no barrier guards the ring: row n's stage is refilled one round after it was consumed.
-// Slots past the end of a row are never copied and stay zero (cleared here), so the arithmetic
-// runs unguarded.  v arrives split (a.vhf + a.vlf); its high words live in registers, its low
-// words in shared memory (vls, read back by the thread that wrote them).  Arithmetic is packed:
-// two columns per f32x2 instruction.
-template <int C4, int S>
+// Warp-specialised: the first half of the warps (the dot group) stream the rows into a
+// shared-memory ring with cp.async and form s_n = w_n (J_n . v); the second half (the update
+// group) adds s_n J_n into the block's partial y.  Both groups cover every 16-byte slot of a row
+// (thread g of either group owns slots g + kGT c, c < CG), so the update of row n overlaps the
+// dot product and reduction of later rows.  Hand-over through named barriers, per ring stage st:
+//   FULL[st]  : the dot group arrives after row n's data landed and its warp sums of J_n . v
+//               are in sm.dpart[st]; the update group waits on it and forms s_n;
+//   EMPTY[st] : the update group arrives after its last read of row n, if row n + S exists;
+//               the dot group waits on it before copying row n + S into the stage.
+// Each barrier has at most one generation outstanding, and both groups follow the same row
+// count, so arrivals and waits pair up.  Slots past the end of a row are never copied and stay
+// zero (cleared here by their owners before the first FULL arrival).  v arrives split
+// (a.vhf + a.vlf): high words in the dot group's registers, low words in shared memory.
+constexpr int kGT = kT / 2;         // threads per group
+constexpr int kMaxStages = 6;
+constexpr int kBarFull = 1, kBarEmpty = 1 + kMaxStages;   // named barriers 1..12
+
+__device__ __forceinline__ void nbar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <int CG, int S>
 __device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, float4* vls, Smem& sm) {
-  static_assert(S % kR == 0 && S > kR, "ring stages");
-  constexpr int D = S - kR;                      // prefetch distance in rows
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int PD = S - 2;                      // rows prefetched ahead of the dot group
+  static_assert(S >= 3 && S <= kMaxStages, "ring stages");
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int g = tid % kGT;
+  const bool dot_group = tid < kGT;
   const int G = gridDim.x, b = blockIdx.x;
   const int nv4 = (int)(a.ldJ / 4);
   const int64_t rb0 = a.N * b / G, rb1 = a.N * (b + 1) / G;
   const int nrows = (int)(rb1 - rb0);
-  f2x vh[C4][2], nvh[C4][2];
-  DF2 ya[C4][2];
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (dot_group) {
+    const int dw = tid >> 5;                     // warp of the dot group
+    f2x vh[CG][2];
 #pragma unroll
-  for (int c = 0; c < C4; ++c) {
-    const int s = tid + c * kT;
-    const float4 h = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vhf) + s) : zero4;
-    vls[s] = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vlf) + s) : zero4;
-    vh[c][0] = pk2(h.x, h.y);
-    vh[c][1] = pk2(h.z, h.w);
-    nvh[c][0] = pk2(-h.x, -h.y);
-    nvh[c][1] = pk2(-h.z, -h.w);
-    ya[c][0] = DF2{0ull, 0ull};
-    ya[c][1] = DF2{0ull, 0ull};
-    if (s >= nv4) {
+    for (int c = 0; c < CG; ++c) {
+      const int s = g + c * kGT;
+      const float4 h = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vhf) + s) : zero4;
+      vls[s] = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vlf) + s) : zero4;
+      vh[c][0] = pk2(h.x, h.y);
+      vh[c][1] = pk2(h.z, h.w);
+      if (s >= nv4) {
 #pragma unroll
-      for (int st = 0; st < S; ++st) ring[(st * C4 + c) * kT + tid] = zero4;
+        for (int st = 0; st < S; ++st) ring[(st * CG + c) * kGT + g] = zero4;
+      }
     }
-  }
-  const uint64_t pol = evict_first_policy();
-  auto issue = [&](int k) {                      // row rb0 + k into stage k % S (one commit group)
-    if (k < nrows) {
-      const float4* src = reinterpret_cast<const float4*>(a.J + (rb0 + k) * a.ldJ) + tid;
-      float4* dst = ring + (k % S) * C4 * kT + tid;
+    const uint64_t pol = evict_first_policy();
+    auto issue = [&](int k) {                    // row rb0 + k into stage k % S (one commit group)
+      if (k < nrows) {
+        if (k >= S) nbar_sync(kBarEmpty + k % S, kT);
+        const float4* src = reinterpret_cast<const float4*>(a.J + (rb0 + k) * a.ldJ) + g;
+        float4* dst = ring + (k % S) * CG * kGT + g;
 #pragma unroll
-      for (int c = 0; c < C4; ++c)
-        if (tid + c * kT < nv4) cp_async16(dst + c * kT, src + c * kT, pol);
-    }
-    cp_async_commit();
-  };
+        for (int c = 0; c < CG; ++c)
+          if (g + c * kGT < nv4) cp_async16(dst + c * kGT, src + c * kGT, pol);
+      }
+      cp_async_commit();
+    };
 #pragma unroll
-  for (int i = 0; i < D; ++i) issue(i);
-  for (int k0 = 0, round = 0; k0 < nrows; k0 += kR, ++round) {
+    for (int i = 0; i < PD; ++i) issue(i);
+    for (int k = 0; k < nrows; ++k) {
+      issue(k + PD);
+      cp_async_wait<PD>();
+      const int st = k % S;
+      const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + st * CG * kGT + g);
+      const ulonglong2* lvp = reinterpret_cast<const ulonglong2*>(vls + g);
+      DF2 d0{0ull, 0ull}, d1{0ull, 0ull}, d2{0ull, 0ull}, d3{0ull, 0ull};
 #pragma unroll
-    for (int i = 0; i < kR; ++i) issue(k0 + D + i);
-    float wh[kR], wl[kR];
-#pragma unroll
-    for (int i = 0; i < kR; ++i) {
-      const bool in = k0 + i < nrows;
-      wh[i] = in ? __ldg(a.wh + rb0 + k0 + i) : 0.f;
-      wl[i] = in ? __ldg(a.wl + rb0 + k0 + i) : 0.f;
-    }
-    cp_async_wait<D>();
-    DF t[kR];
-#pragma unroll
-    for (int i = 0; i < kR; ++i) {
-      const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + ((k0 + i) % S) * C4 * kT + tid);
-      const ulonglong2* lvp = reinterpret_cast<const ulonglong2*>(vls + tid);
-      DF2 d0{0ull, 0ull}, d1{0ull, 0ull};
-      if (k0 + i < nrows) {                      // uniform in the block
-#pragma unroll
-        for (int c = 0; c < C4; ++c) {
-          {
-            const ulonglong2 jv = row[c * kT];
-            const ulonglong2 lv = lvp[c * kT];
-            df2_add_prod(d0, jv.x, vh[c][0], nvh[c][0], lv.x);
-            df2_add_prod(d1, jv.y, vh[c][1], nvh[c][1], lv.y);
-          }
+      for (int c = 0; c < CG; c += 2) {
+        const ulonglong2 jv = row[c * kGT], lv = lvp[c * kGT];
+        df2_add_prod_nj(d0, jv.x, vh[c][0], lv.x);
+        df2_add_prod_nj(d1, jv.y, vh[c][1], lv.y);
+        if (c + 1 < CG) {
+          const ulonglong2 jw = row[(c + 1) * kGT], lw = lvp[(c + 1) * kGT];
+          df2_add_prod_nj(d2, jw.x, vh[c + 1][0], lw.x);
+          df2_add_prod_nj(d3, jw.y, vh[c + 1][1], lw.y);
         }
       }
-      DF q0, q1, q2, q3;
-      df2_split(d0, q0, q1);
-      df2_split(d1, q2, q3);
-      t[i] = df_add(df_add(q0, q1), df_add(q2, q3));
+      DF q[8];
+      df2_split(d0, q[0], q[1]);
+      df2_split(d1, q[2], q[3]);
+      df2_split(d2, q[4], q[5]);
+      df2_split(d3, q[6], q[7]);
+      DF t = df_add(df_add(df_add(q[0], q[1]), df_add(q[2], q[3])), df_add(df_add(q[4], q[5]), df_add(q[6], q[7])));
+      t = warp_sum_df(t);
+      if (lane == 0) sm.dpart[st][dw] = t;
+      nbar_arrive(kBarFull + st, kT);
     }
-    static_assert(kR == 2, "two rows per round: one reduce-scatter");
-    const DF ts = warp_reduce_scatter2(t[0], t[1]);     // lane 0: row 0, lane 16: row 1
-    const int par = round & 1;
-    if ((lane & 15) == 0) sm.wred[par][lane >> 4][warp] = ts;
-    __syncthreads();
-    // every warp combines the kW warp sums with a 3-level butterfly over lanes 0..kW-1
-    f2x sh[kR], nsh[kR], sl[kR];
+    cp_async_wait<0>();
+  } else {
+    DF2 ya[CG][2];
 #pragma unroll
-    for (int i = 0; i < kR; ++i) {
-      DF s = lane < kW ? sm.wred[par][i][lane] : DF{0.f, 0.f};
+    for (int c = 0; c < CG; ++c) ya[c][0] = ya[c][1] = DF2{0ull, 0ull};
+    for (int k = 0; k < nrows; ++k) {
+      const int st = k % S;
+      const float wh = __ldg(a.wh + rb0 + k), wl = __ldg(a.wl + rb0 + k);
+      nbar_sync(kBarFull + st, kT);
+      // every thread of the update group combines the dot group's warp sums itself
+      DF s = sm.dpart[st][0];
 #pragma unroll
-      for (int o = kW / 2; o > 0; o >>= 1) {
-        const DF u{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
-        s = df_add(s, u);
+      for (int w = 1; w < kGT / 32; ++w) s = df_add(s, sm.dpart[st][w]);
+      const DF sn = df_mul(s, wh, wl);
+      const f2x sh = pk2(sn.hi, sn.hi), nsh = pk2(-sn.hi, -sn.hi), sl = pk2(sn.lo, sn.lo);
+      const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + st * CG * kGT + g);
+#pragma unroll
+      for (int c = 0; c < CG; ++c) {
+        const ulonglong2 jv = row[c * kGT];
+        df2_add_prod(ya[c][0], jv.x, sh, nsh, sl);
+        df2_add_prod(ya[c][1], jv.y, sh, nsh, sl);
       }
-      s = DF{__shfl_sync(0xffffffffu, s.hi, 0), __shfl_sync(0xffffffffu, s.lo, 0)};
-      const DF sn = df_mul(s, wh[i], wl[i]);
-      sh[i] = pk2(sn.hi, sn.hi);
-      nsh[i] = pk2(-sn.hi, -sn.hi);
-      sl[i] = pk2(sn.lo, sn.lo);
+      if (k + S < nrows) nbar_arrive(kBarEmpty + st, kT);
     }
+    float4* oh = reinterpret_cast<float4*>(a.yph + (int64_t)b * a.ldJ);
+    float4* ol = reinterpret_cast<float4*>(a.ypl + (int64_t)b * a.ldJ);
 #pragma unroll
-    for (int i = 0; i < kR; ++i) {
-      if (k0 + i >= nrows) break;              // uniform in the block
-      const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + ((k0 + i) % S) * C4 * kT + tid);
-#pragma unroll
-      for (int c = 0; c < C4; ++c) {
-        {
-          const ulonglong2 jv = row[c * kT];
-          df2_add_prod(ya[c][0], jv.x, sh[i], nsh[i], sl[i]);
-          df2_add_prod(ya[c][1], jv.y, sh[i], nsh[i], sl[i]);
-        }
+    for (int c = 0; c < CG; ++c) {
+      const int s = g + c * kGT;
+      if (s < nv4) {
+        float h0, h1, h2, h3, l0, l1, l2, l3;
+        upk2(ya[c][0].hi, h0, h1);
+        upk2(ya[c][1].hi, h2, h3);
+        upk2(ya[c][0].lo, l0, l1);
+        upk2(ya[c][1].lo, l2, l3);
+        __stcg(oh + s, make_float4(h0, h1, h2, h3));
+        __stcg(ol + s, make_float4(l0, l1, l2, l3));
       }
-    }
-  }
-  cp_async_wait<0>();
-  float4* oh = reinterpret_cast<float4*>(a.yph + (int64_t)b * a.ldJ);
-  float4* ol = reinterpret_cast<float4*>(a.ypl + (int64_t)b * a.ldJ);
-#pragma unroll
-  for (int c = 0; c < C4; ++c) {
-    const int s = tid + c * kT;
-    if (s < nv4) {
-      float h0, h1, h2, h3, l0, l1, l2, l3;
-      upk2(ya[c][0].hi, h0, h1);
-      upk2(ya[c][1].hi, h2, h3);
-      upk2(ya[c][0].lo, l0, l1);
-      upk2(ya[c][1].lo, l2, l3);
-      __stcg(oh + s, make_float4(h0, h1, h2, h3));
-      __stcg(ol + s, make_float4(l0, l1, l2, l3));
     }
   }
 }
@@ -237,20 +237,20 @@ __device__ __forceinline__ void split_slice(const FusedPcgArgs& a, const double*
 }
 
 // Phase B: q_j = sum_b y_b[j] + mu v_j on the block's j slice; returns the block's sum of v_j q_j.
-// Thread (c4, g): columns 4 c4 .. 4 c4 + 3 of the slice, partials b = g, g + 8, ...; scr: shared
-// scratch of 8 x 32 x 4 double-float values.
+// Thread (c4, g): columns 4 c4 .. 4 c4 + 3 of the slice, partials b = g, g + kW, ...; scr: shared
+// scratch of kW x 32 x 4 double-float values.
 __device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double* v, double mu, double* q, DF* scr) {
   const int tid = threadIdx.x, G = gridDim.x;
   int64_t cb0, cb1;
   col_slice(a.p, blockIdx.x, G, cb0, cb1);
-  const int c4 = tid & 31, g = tid >> 5;                 // 32 column quads x 8 partial groups
+  const int c4 = tid & 31, g = tid >> 5;                 // 32 column quads x kW partial groups
   double vq = 0.0;
   for (int64_t j0 = cb0; j0 < cb1; j0 += 128) {
     const int64_t j = j0 + 4 * c4;
     DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (j < cb1) {
 #pragma unroll 4
-      for (int bb = g; bb < G; bb += 8) {
+      for (int bb = g; bb < G; bb += kW) {
         const float4 h = __ldcg(reinterpret_cast<const float4*>(a.yph + (int64_t)bb * a.ldJ + j));
         const float4 l = __ldcg(reinterpret_cast<const float4*>(a.ypl + (int64_t)bb * a.ldJ + j));
         acc[0] = df_add(acc[0], DF{h.x, l.x});
@@ -268,7 +268,7 @@ __device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double*
       if (jc < cb1) {
         DF s = scr[cc * 4 + e];
 #pragma unroll
-        for (int g2 = 1; g2 < 8; ++g2) s = df_add(s, scr[(g2 * 32 + cc) * 4 + e]);
+        for (int g2 = 1; g2 < kW; ++g2) s = df_add(s, scr[(g2 * 32 + cc) * 4 + e]);
         const double vj = __ldcg(v + jc);
         const double qj = df_to_double(s) + mu * vj;
         q[jc] = qj;
@@ -322,12 +322,12 @@ __device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, 
   }
 }
 
-template <int C4, int S>
+template <int CG, int S>
 __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
   float4* ring = reinterpret_cast<float4*>(dsm);
-  float4* vls = ring + (int64_t)S * C4 * kT;             // low words of the matvec's vector
+  float4* vls = ring + (int64_t)S * CG * kGT;            // low words of the matvec's vector
   float2* w2s = reinterpret_cast<float2*>(dsm);          // phase E only (aliases the ring)
   DF* scr = reinterpret_cast<DF*>(dsm);                  // phases B, C only (aliases the ring)
   __shared__ Smem sm;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   if (a.mode == 1) {                                     // q = (G + mu I) v, v = a.pv
     split_slice(a, a.pv);
     grid.sync();
-    gv_rows<C4, S>(a, ring, vls, sm);
+    gv_rows<CG, S>(a, ring, vls, sm);
     grid.sync();
     gv_finish(a, a.pv, mu, a.q, scr);
     return;
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     }
     grid.sync();
     // A, B: q = (G + mu I) p, p . q
-    gv_rows<C4, S>(a, ring, vls, sm);
+    gv_rows<CG, S>(a, ring, vls, sm);
     grid.sync();
     {
       double pqp = gv_finish(a, a.pv, mu, a.q, scr);
@@ -516,22 +516,22 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   }
 }
 
-constexpr int kMaxC4 = 9;        // p <= 4 * kT * kMaxC4 = 9216
+constexpr int kMaxCG = 12;       // slots per group thread: p <= 4 * kGT * kMaxCG = 9216
 constexpr int kSmemBudget = 210 * 1024;
 
-// ring stages (plus one stage-sized slot for v's low words): a multiple of kR, at most 8
-template <int C4>
+// ring stages (plus one stage-sized slot for v's low words), at most kMaxStages
+template <int CG>
 constexpr int stages_for() {
-  return std::min(8, kSmemBudget / (C4 * kT * 16) - 1) / kR * kR;
+  return std::min(kMaxStages, kSmemBudget / (CG * kGT * 16) - 1);
 }
 
-template <int C4>
-cudaError_t launch_c4(const FusedPcgArgs& a, int G, cudaStream_t s) {
-  constexpr int S = stages_for<C4>();
-  static_assert(S >= 2 * kR, "shared-memory ring too small");
-  auto kern = k_pcg_fused<C4, S>;
+template <int CG>
+cudaError_t launch_cg(const FusedPcgArgs& a, int G, cudaStream_t s) {
+  constexpr int S = stages_for<CG>();
+  static_assert(S >= 3, "shared-memory ring too small");
+  auto kern = k_pcg_fused<CG, S>;
   // dynamic shared memory: the ring, or the scaled U^T r of phase E (ell <= 2048), whichever is larger
-  constexpr size_t smem = std::max((size_t)(S + 1) * C4 * kT * 16, (size_t)2048 * sizeof(float2));
+  constexpr size_t smem = std::max((size_t)(S + 1) * CG * kGT * 16, (size_t)2048 * sizeof(float2));
   static std::mutex mu;
   static int configured_dev = -1, per_sm = 0;
   int dev = 0;
@@ -571,24 +571,21 @@ int fused_pcg_blocks() { return std::min(num_sms(), kT); }
 
 bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell) {
   const int G = fused_pcg_blocks();
-  const int64_t c4 = (ldJ / 4 + kT - 1) / kT;
-  return G >= 1 && ldJ % 4 == 0 && c4 >= 1 && c4 <= kMaxC4 && 4 * (((p + 3) / 4 + G - 1) / G) <= kMaxSlice &&
+  const int64_t cg = (ldJ / 4 + kGT - 1) / kGT;
+  return G >= 1 && ldJ % 4 == 0 && cg >= 1 && cg <= kMaxCG && 4 * (((p + 3) / 4 + G - 1) / G) <= kMaxSlice &&
          ell >= 0 && ell <= 2048;
 }
 
 cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s) {
   if (!fused_pcg_supported(a.p, a.ldJ, a.ell)) return cudaErrorInvalidValue;
   const int G = fused_pcg_blocks();
-  switch ((a.ldJ / 4 + kT - 1) / kT) {
-    case 1: return launch_c4<1>(a, G, s);
-    case 2: return launch_c4<2>(a, G, s);
-    case 3: return launch_c4<3>(a, G, s);
-    case 4: return launch_c4<4>(a, G, s);
-    case 5: return launch_c4<5>(a, G, s);
-    case 6: return launch_c4<6>(a, G, s);
-    case 7: return launch_c4<7>(a, G, s);
-    case 8: return launch_c4<8>(a, G, s);
-    default: return launch_c4<9>(a, G, s);
+  switch (((a.ldJ / 4 + kGT - 1) / kGT + 1) / 2) {     // slots per group thread, rounded up to even
+    case 1: return launch_cg<2>(a, G, s);
+    case 2: return launch_cg<4>(a, G, s);
+    case 3: return launch_cg<6>(a, G, s);
+    case 4: return launch_cg<8>(a, G, s);
+    case 5: return launch_cg<10>(a, G, s);
+    default: return launch_cg<12>(a, G, s);
   }
 }
 
