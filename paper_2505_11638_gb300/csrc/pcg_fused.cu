@@ -56,9 +56,15 @@ __device__ __forceinline__ double block_allsum(double v, double* red) {
   red[threadIdx.x] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double s = 0.0;
+    // pairwise tree over the kT / 32 values of each lane: short FP64 dependency chains
+    double v8[kT / 32];
 #pragma unroll
-    for (int i = 0; i < kT / 32; ++i) s += red[threadIdx.x + 32 * i];
+    for (int i = 0; i < kT / 32; ++i) v8[i] = red[threadIdx.x + 32 * i];
+#pragma unroll
+    for (int w = 1; w < kT / 32; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < kT / 32; i += 2 * w) v8[i] += v8[i + w];
+    double s = v8[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) red[kT] = s;
@@ -82,7 +88,10 @@ __device__ __forceinline__ void col_slice(int64_t p, int b, int G, int64_t& c0, 
   c1 = min(p, 4 * (n4 * (b + 1) / G));
 }
 
+constexpr int kMaxKSlice = 16;     // largest k slice per block (ell <= kMaxKSlice * G)
+
 struct Smem {
+  double coef[kMaxKSlice];          // (lam_ell + mu) / (lam_k + mu) - 1 for the block's k slice
   DF dpart[6][kT / 64];             // phase A: per ring stage, the dot group's warp sums
   double dred[kT + 1];
   float2 rs[kMaxSlice];
@@ -101,7 +110,7 @@ struct Smem {
 // Each barrier has at most one generation outstanding, and both groups follow the same row
 // count, so arrivals and waits pair up.  Slots past the end of a row are never copied and stay
 // zero (cleared here by their owners before the first FULL arrival).  v arrives split
-// (a.vhf + a.vlf): high words in the dot group's registers, low words in shared memory.
+// (a.vhf + a.vlf), both words in the dot group's registers.
 constexpr int kGT = kT / 2;         // threads per group
 constexpr int kMaxStages = 6;
 constexpr int kBarFull = 1, kBarEmpty = 1 + kMaxStages;   // named barriers 1..12
@@ -114,7 +123,7 @@ __device__ __forceinline__ void nbar_arrive(int id, int count) {
 }
 
 template <int CG, int S>
-__device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, float4* vls, Smem& sm) {
+__device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, Smem& sm) {
   constexpr int PD = S - 2;                      // rows prefetched ahead of the dot group
   static_assert(S >= 3 && S <= kMaxStages, "ring stages");
   const int tid = threadIdx.x, lane = tid & 31;
@@ -127,14 +136,16 @@ __device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, flo
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (dot_group) {
     const int dw = tid >> 5;                     // warp of the dot group
-    f2x vh[CG][2];
+    f2x vh[CG][2], vl[CG][2];
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       const int s = g + c * kGT;
       const float4 h = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vhf) + s) : zero4;
-      vls[s] = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vlf) + s) : zero4;
+      const float4 l = s < nv4 ? __ldcg(reinterpret_cast<const float4*>(a.vlf) + s) : zero4;
       vh[c][0] = pk2(h.x, h.y);
       vh[c][1] = pk2(h.z, h.w);
+      vl[c][0] = pk2(l.x, l.y);
+      vl[c][1] = pk2(l.z, l.w);
       if (s >= nv4) {
 #pragma unroll
         for (int st = 0; st < S; ++st) ring[(st * CG + c) * kGT + g] = zero4;
@@ -159,17 +170,16 @@ __device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, flo
       cp_async_wait<PD>();
       const int st = k % S;
       const ulonglong2* row = reinterpret_cast<const ulonglong2*>(ring + st * CG * kGT + g);
-      const ulonglong2* lvp = reinterpret_cast<const ulonglong2*>(vls + g);
       DF2 d0{0ull, 0ull}, d1{0ull, 0ull}, d2{0ull, 0ull}, d3{0ull, 0ull};
 #pragma unroll
       for (int c = 0; c < CG; c += 2) {
-        const ulonglong2 jv = row[c * kGT], lv = lvp[c * kGT];
-        df2_add_prod_nj(d0, jv.x, vh[c][0], lv.x);
-        df2_add_prod_nj(d1, jv.y, vh[c][1], lv.y);
+        const ulonglong2 jv = row[c * kGT];
+        df2_add_prod_nj(d0, jv.x, vh[c][0], vl[c][0]);
+        df2_add_prod_nj(d1, jv.y, vh[c][1], vl[c][1]);
         if (c + 1 < CG) {
-          const ulonglong2 jw = row[(c + 1) * kGT], lw = lvp[(c + 1) * kGT];
-          df2_add_prod_nj(d2, jw.x, vh[c + 1][0], lw.x);
-          df2_add_prod_nj(d3, jw.y, vh[c + 1][1], lw.y);
+          const ulonglong2 jw = row[(c + 1) * kGT];
+          df2_add_prod_nj(d2, jw.x, vh[c + 1][0], vl[c + 1][0]);
+          df2_add_prod_nj(d3, jw.y, vh[c + 1][1], vl[c + 1][1]);
         }
       }
       DF q[8];
@@ -327,7 +337,6 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
   float4* ring = reinterpret_cast<float4*>(dsm);
-  float4* vls = ring + (int64_t)S * CG * kGT;            // low words of the matvec's vector
   float2* w2s = reinterpret_cast<float2*>(dsm);          // phase E only (aliases the ring)
   DF* scr = reinterpret_cast<DF*>(dsm);                  // phases B, C only (aliases the ring)
   __shared__ Smem sm;
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   if (a.mode == 1) {                                     // q = (G + mu I) v, v = a.pv
     split_slice(a, a.pv);
     grid.sync();
-    gv_rows<CG, S>(a, ring, vls, sm);
+    gv_rows<CG, S>(a, ring, sm);
     grid.sync();
     gv_finish(a, a.pv, mu, a.q, scr);
     return;
@@ -348,6 +357,10 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   const int ncol = (int)(cb1 - cb0);
   const int kb0 = (int)((int64_t)a.ell * b / G), kb1 = (int)((int64_t)a.ell * (b + 1) / G);
   const bool pre = a.ell > 0;
+  if (pre && tid < kb1 - kb0) {     // the scaled preconditioner's coefficients, once per solve
+    const double lam_l = a.lam[a.ell - 1];
+    sm.coef[tid] = (lam_l + mu) / (a.lam[kb0 + tid] + mu) - 1.0;
+  }
   PcgScalars* sc = a.sc;
   const double rtol2 = sc->rtol2;
   const int maxit = sc->maxit;
@@ -387,7 +400,6 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     if (done) break;
     if (pre) {
       const int lane = tid & 31, warp = tid >> 5;
-      const double lam_l = a.lam[a.ell - 1];
       for (int k = kb0 + warp; k < kb1; k += kW) {
         DF acc{0.f, 0.f};
 #pragma unroll 4
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
         }
         acc = warp_sum_df(acc);
         if (lane == 0) {
-          const double w2 = ((lam_l + mu) / (a.lam[k] + mu) - 1.0) * df_to_double(acc);
+          const double w2 = sm.coef[k - kb0] * df_to_double(acc);
           float h, l;
           split_df(w2, h, l);
           __stcg(a.w2 + k, make_float2(h, l));
@@ -410,33 +422,48 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     if (pre) {
       for (int k = tid; k < a.ldu; k += kT) w2s[k] = k < a.ell ? __ldcg(a.w2 + k) : make_float2(0.f, 0.f);
       __syncthreads();
-      // a warp takes eight rows of U at once (j-major, rows padded to ldu), lanes over k quads
+      // a warp takes two rows of U at a time (j-major, rows padded to ldu), lanes over k quads;
+      // every load of the pair is issued before the arithmetic
       const int lane = tid & 31, warp = tid >> 5;
       const int nk4 = a.ldu / 4;
-      for (int j0 = 8 * warp; j0 < ncol; j0 += 8 * kW) {
-        const int nq = min(8, ncol - j0);
-        DF acc[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = DF{0.f, 0.f};
+      constexpr int kQ = 16;                               // k quads per lane: ell <= 32 * 4 * kQ = 2048
+      for (int j0 = 2 * warp; j0 < ncol; j0 += 2 * kW) {
+        const bool two = j0 + 1 < ncol;
         const float4* uh0 = reinterpret_cast<const float4*>(a.Uh + (cb0 + j0) * a.ldu);
         const float4* ul0 = reinterpret_cast<const float4*>(a.Ul + (cb0 + j0) * a.ldu);
-        for (int k4 = lane; k4 < nk4; k4 += 32) {
-          const float4 wa = reinterpret_cast<const float4*>(w2s)[2 * k4];       // w2[4 k4], w2[4 k4 + 1]
-          const float4 wb = reinterpret_cast<const float4*>(w2s)[2 * k4 + 1];   // w2[4 k4 + 2], w2[4 k4 + 3]
+        DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
+        for (int q0 = 0; q0 < kQ; q0 += 4) {
+          if (q0 * 32 >= nk4) break;
+          float4 h0[4], l0[4], h1[4], l1[4];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (q < nq) {
-              const float4 h = __ldg(uh0 + (int64_t)q * nk4 + k4), l = __ldg(ul0 + (int64_t)q * nk4 + k4);
-              df_add_prod2(acc[q], h.x, l.x, wa.x, wa.y);
-              df_add_prod2(acc[q], h.y, l.y, wa.z, wa.w);
-              df_add_prod2(acc[q], h.z, l.z, wb.x, wb.y);
-              df_add_prod2(acc[q], h.w, l.w, wb.z, wb.w);
+          for (int i = 0; i < 4; ++i) {
+            const int k4 = lane + 32 * (q0 + i);
+            const bool in = k4 < nk4;
+            h0[i] = in ? __ldg(uh0 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            l0[i] = in ? __ldg(ul0 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            h1[i] = in && two ? __ldg(uh0 + nk4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            l1[i] = in && two ? __ldg(ul0 + nk4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k4 = lane + 32 * (q0 + i);
+            if (k4 < nk4) {
+              const float4 wa = reinterpret_cast<const float4*>(w2s)[2 * k4];       // w2[4 k4], w2[4 k4 + 1]
+              const float4 wb = reinterpret_cast<const float4*>(w2s)[2 * k4 + 1];   // w2[4 k4 + 2], w2[4 k4 + 3]
+              df_add_prod2(acc0, h0[i].x, l0[i].x, wa.x, wa.y);
+              df_add_prod2(acc0, h0[i].y, l0[i].y, wa.z, wa.w);
+              df_add_prod2(acc0, h0[i].z, l0[i].z, wb.x, wb.y);
+              df_add_prod2(acc0, h0[i].w, l0[i].w, wb.z, wb.w);
+              df_add_prod2(acc1, h1[i].x, l1[i].x, wa.x, wa.y);
+              df_add_prod2(acc1, h1[i].y, l1[i].y, wa.z, wa.w);
+              df_add_prod2(acc1, h1[i].z, l1[i].z, wb.x, wb.y);
+              df_add_prod2(acc1, h1[i].w, l1[i].w, wb.z, wb.w);
             }
           }
         }
-        const DF s = warp_reduce_scatter8(acc);          // lane L: row j0 + (L >> 2)
-        const int q = lane >> 2;
-        if ((lane & 3) == 0 && q < nq) {
+        const DF s = warp_reduce_scatter2(acc0, acc1);     // lanes 0..15: row j0, 16..31: row j0 + 1
+        const int q = lane >> 4;
+        if ((lane & 15) == 0 && (q == 0 || two)) {
           const int64_t j = cb0 + j0 + q;
           const double rj = a.r[j], zj = rj + df_to_double(s);
           a.z[j] = zj;
@@ -470,7 +497,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     }
     grid.sync();
     // A, B: q = (G + mu I) p, p . q
-    gv_rows<CG, S>(a, ring, vls, sm);
+    gv_rows<CG, S>(a, ring, sm);
     grid.sync();
     {
       double pqp = gv_finish(a, a.pv, mu, a.q, scr);
@@ -519,10 +546,10 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
 constexpr int kMaxCG = 12;       // slots per group thread: p <= 4 * kGT * kMaxCG = 9216
 constexpr int kSmemBudget = 210 * 1024;
 
-// ring stages (plus one stage-sized slot for v's low words), at most kMaxStages
+// ring stages, at most kMaxStages
 template <int CG>
 constexpr int stages_for() {
-  return std::min(kMaxStages, kSmemBudget / (CG * kGT * 16) - 1);
+  return std::min(kMaxStages, kSmemBudget / (CG * kGT * 16));
 }
 
 template <int CG>
@@ -531,7 +558,7 @@ cudaError_t launch_cg(const FusedPcgArgs& a, int G, cudaStream_t s) {
   static_assert(S >= 3, "shared-memory ring too small");
   auto kern = k_pcg_fused<CG, S>;
   // dynamic shared memory: the ring, or the scaled U^T r of phase E (ell <= 2048), whichever is larger
-  constexpr size_t smem = std::max((size_t)(S + 1) * CG * kGT * 16, (size_t)2048 * sizeof(float2));
+  constexpr size_t smem = std::max((size_t)S * CG * kGT * 16, (size_t)2048 * sizeof(float2));
   static std::mutex mu;
   static int configured_dev = -1, per_sm = 0;
   int dev = 0;
@@ -573,7 +600,7 @@ bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell) {
   const int G = fused_pcg_blocks();
   const int64_t cg = (ldJ / 4 + kGT - 1) / kGT;
   return G >= 1 && ldJ % 4 == 0 && cg >= 1 && cg <= kMaxCG && 4 * (((p + 3) / 4 + G - 1) / G) <= kMaxSlice &&
-         ell >= 0 && ell <= 2048;
+         ell >= 0 && ell <= 2048 && ell <= kMaxKSlice * G;
 }
 
 cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s) {
