@@ -333,6 +333,71 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_batch(args, rank, world, local_rank):
+    """The batching form: every step is one ngd_batch_step over the 64 problems of batch64."""
+    import torch
+    from paper_2505_11638_gb300 import build, inputs, ngd
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    wl, thetas0 = inputs.make_workload("batch64", seed=rank * 1000)
+    batch = ngd.Batch(wl.problems, dtype=wl.dtype)
+    opts = dict(ell=wl.ell, mu=None, rtol=wl.rtol, maxit=1000, sketch=args.sketch, seed=rank)
+    thetas = [torch.tensor(th, device="cuda") for th in thetas0]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for k in range(args.warmup):
+        batch.step(thetas, step=k, **opts)
+    for th, th0 in zip(thetas, thetas0):
+        th.copy_(torch.tensor(th0, device="cuda"))
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    l0 = ngd.ngd_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for k in range(args.steps):
+        infos.append(batch.step(thetas, step=k, **opts))
+    e1.record(stream)
+    barrier()
+    launches = ngd.ngd_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_prob = len(wl.problems)
+    value = world * args.steps * n_prob / (ms * 1e-3)
+    iters = [i["pcg_iters"] for step in infos for i in step]
+    line = {"metric": "NGD problem-steps/s at PCG rtol 1e-6 (batching form)", "value": value,
+            "unit": "problem-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "problems": n_prob, "N_total": int(sum(pr.n for pr in wl.problems)),
+                       "p_each": wl.problems[0].p, "ell": wl.ell, "mu": "rule", "rtol": wl.rtol,
+                       "sketch": args.sketch},
+            "pcg_iters_mean": float(np.mean(iters)), "pcg_iters_max": int(np.max(iters)),
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,10 +406,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sketch", default="f64", choices=["f64", "f32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"],
+                    help="batch64: the batching form, 64 problems of uneven size per step (ngd_batch_step)")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch64":
+        return run_batch(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

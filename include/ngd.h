@@ -186,10 +186,11 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
 
 /* Factor of App. A, remaining steps, given an orthonormal Omega and Y = G Omega:
  * nu = eps(||Y||_F) in the format of 'prec' (spacing 2^(floor(log2 x) - m) with m = 52, 23,
- * 10, 7 mantissa bits for F64, F32, TF32, BF16), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
+ * 10, 7 mantissa bits for F64, F32, TF32, BF16; m = 48 for F64 in an F32 context, whose sketch
+ * and factor run in double-float), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
  * B = Y_nu C^{-1}, eigen-decomposition of B^T B in FP64 (Householder tridiagonalization,
  * multisection, twisted factorization, back-transform) gives B = U Sigma V^T, lambda = max(0, Sigma^2 - nu), descending.
- * shift_scale multiplies nu (1 = the rule above; ngd_step retries with 8, 64).
+ * shift_scale multiplies nu (1 = the rule above; ngd_step retries with 8, 64, ..., 8^5).
  * Omega: device p x ell (context dtype); Y: device p x ell (float64 when prec = NGD_SKETCH_F64,
  * else the context dtype); U: device p x ell out, float64 when prec = NGD_SKETCH_F64, else
  * float32 (in an F32 context the preconditioner's cancellation in I - U U^T needs U in FP64 once
@@ -220,7 +221,7 @@ ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, dou
 
 /* One Nystrom-preconditioned matrix-free NGD step (Alg. 1 with Alg. 3 and Alg. 4,
  * fixed ell): gradient, sketch with a fresh Omega, factor (retrying with an
- * 8x / 64x shift on NOT_SPD), mu (fixed or the Alg. 4 rule), pCG, Armijo
+ * 8x, 64x, ..., 8^5x shift on NOT_SPD), mu (fixed or the Alg. 4 rule), pCG, Armijo
  * backtracking along theta - alpha d, update.  theta: device p, updated in place.
  * info: host or NULL.  Synchronises. */
 ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* opts, ngd_step_info* info);
@@ -245,6 +246,26 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* opts, ngd_
 #define NGD_NOALLOC_MAX_ELL 1024
 ngd_status ngd_precond_apply_noalloc(int dtype, int64_t p, int ell, const void* U, int64_t ldU, const double* lam,
                                      double mu, const double* v, double* z, void* stream);
+
+/* ---------------------------------------------------------------- batching form */
+
+/* Many independent PINN problems (networks, point sets and parameters of their own; uneven
+ * point counts allowed) stepped together, as in the paper's repeated-problem experiments.
+ * ngd_batch_create makes one context per description (same rules as ngd_create); every context
+ * enqueues on descs[0].stream, so a batch step is one ordered stream of work.
+ * ngd_batch_step runs one NGD step (Alg. 1 with Alg. 3 and Alg. 4) for every problem i, with
+ * the options in opts and the Philox key opts->seed + i (a distinct test matrix per problem).
+ * thetas: host array of n device pointers (each p_i float64, updated in place); infos: host
+ * array of n entries or NULL.  Synchronises.  The first failing problem stops the step; its
+ * status is returned and ngd_batch_last_error names the problem.
+ * Errors: as ngd_create / ngd_step; INVALID_ARG for n < 1 or a NULL argument. */
+typedef struct ngd_batch ngd_batch;
+ngd_status ngd_batch_create(const ngd_problem_desc* descs, int n, ngd_batch** out);
+void ngd_batch_destroy(ngd_batch* batch);
+int ngd_batch_size(const ngd_batch* batch);
+ngd_ctx* ngd_batch_context(ngd_batch* batch, int i);   /* problem i's context (NULL if out of range) */
+const char* ngd_batch_last_error(const ngd_batch* batch);
+ngd_status ngd_batch_step(ngd_batch* batch, double* const* thetas, const ngd_step_opts* opts, ngd_step_info* infos);
 
 /* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
  * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,

@@ -10,9 +10,10 @@ Readings where the paper is silent (shared with the CUDA side):
   * qr is the thin QR normalised so that R has a positive diagonal (unique).
   * eps(x) is MATLAB's spacing at x in the precision Y was computed in: for a number
     format with m explicit mantissa bits, eps_m(x) = 2^(floor(log2 x) - m).  m = 52 (FP64)
-    is the paper's algorithm; a sketch computed in FP32 (m = 23), TF32 (m = 10) or BF16
-    (m = 7) takes its own spacing, which keeps Omega^T Y_nu positive definite despite the
-    rounding of Y (as eps(single(x)) would in MATLAB).
+    is the paper's algorithm; a sketch computed in double-float (pairs of FP32, 48 bits,
+    "df"), FP32 (m = 23), TF32 (m = 10) or BF16 (m = 7) takes its own spacing, which keeps
+    Omega^T Y_nu positive definite despite the rounding of Y (as eps(single(x)) would in
+    MATLAB).
   * chol reads the symmetric part (Omega^T Y_nu + Y_nu^T Omega)/2 and returns the
     upper factor C with C^T C = that matrix (MATLAB's chol reads one triangle; the
     two agree in exact arithmetic).
@@ -35,7 +36,7 @@ def thin_qr(Omega):
     return Q * s[None, :]
 
 
-MANTISSA_BITS = {"f64": 52, "f32": 23, "tf32": 10, "bf16": 7}
+MANTISSA_BITS = {"f64": 52, "df": 48, "f32": 23, "tf32": 10, "bf16": 7}
 
 
 def shift(normY: float, mant_bits: int = 52) -> float:

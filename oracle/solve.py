@@ -28,6 +28,12 @@ from . import nystrom as _nys
 from . import philox as _philox
 
 
+# Shift multipliers tried in turn when Omega^T Y_nu is not positive definite (reading: the paper
+# fixes nu = eps(||Y||_F) and is silent on failures; the noise of a sketch summed over thousands
+# of terms can exceed one spacing, so the shift grows by 8x up to 8^5).
+SHIFT_SCALES = (1.0, 8.0, 64.0, 512.0, 4096.0, 32768.0)
+
+
 class Breakdown(RuntimeError):
     """p^T (G + mu I) p <= 0 inside CG."""
 
@@ -105,12 +111,12 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
     Omega_raw = _philox.gaussian_test_matrix(J.shape[1], ell, seed, step)
     Omega = _nys.thin_qr(Omega_raw)                                # Alg. 4, line 1 (App. A)
     Y = G_apply(Omega)
-    for scale in (1.0, 8.0, 64.0):      # a non-positive-definite core is retried with a larger shift
+    for scale in SHIFT_SCALES:          # a non-positive-definite core is retried with a larger shift
         try:
             U, lam, nu = _nys.nystrom_factor(Omega, Y, mant_bits, scale)
             break
         except np.linalg.LinAlgError:
-            if scale == 64.0:
+            if scale == SHIFT_SCALES[-1]:
                 raise
     mu_eff = float(mu) if mu is not None else _nys.mu_from_lambda1(lam[0], gamma)  # Alg. 4, line 2
 

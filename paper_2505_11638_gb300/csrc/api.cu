@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -78,6 +79,8 @@ struct ngd_ctx {
 };
 
 enum { kSLoss = 0, kSFrob2 = 1, kSNu = 2, kSMu = 3, kSDot = 4, kSCount = 8 };
+// factor attempts of ngd_step: the shift nu times 1, 8, 64, ... on NOT_SPD
+constexpr int kShiftAttempts = 6;
 
 namespace {
 
@@ -474,7 +477,8 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
   const int64_t p = ctx->p, ld = ctx->ldP;
   TRY(clear_status(ctx));
   launch_frob2<double>(ctx->Y64, ld, p, ell, ctx->part, ctx->scal + kSFrob2, ctx->stream);
-  launch_compute_nu(ctx->scal + kSFrob2, 52, shift_scale, ctx->scal + kSNu, ctx->stream);
+  // the double-float format carries 48 significant bits: nu = eps_48(||Y||_F)
+  launch_compute_nu(ctx->scal + kSFrob2, 48, shift_scale, ctx->scal + kSNu, ctx->stream);
   launch_shift_add_mixed(ctx->Y64, Om, ctx->scal + kSNu, Bm, ld, p, ell, ctx->stream);      // Y_nu
   {
     GemmDfArgs<float, double> g;                                                           // Omega^T Y_nu
@@ -698,7 +702,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   phase.next("factor");
   double scale = 1.0;
   ngd_status fs = NGD_OK;
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  for (int attempt = 0; attempt < kShiftAttempts; ++attempt) {
     fs = factor_internal<T>(ctx, o->ell, o->sketch, scale);
     if (fs != NGD_ERR_NOT_SPD) break;
     inf.shift_retries++;
@@ -1150,6 +1154,72 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
     using T = decltype(z);
     return step_impl<T>(ctx, theta, o, info);
   });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batching form
+struct ngd_batch {
+  std::vector<ngd_ctx*> ctx;
+  std::string err;
+};
+
+extern "C" {
+
+ngd_status ngd_batch_create(const ngd_problem_desc* descs, int n, ngd_batch** out) {
+  if (!out) return NGD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!descs || n < 1) return NGD_ERR_INVALID_ARG;
+  ngd_batch* b = new (std::nothrow) ngd_batch;
+  if (!b) return NGD_ERR_OOM;
+  for (int i = 0; i < n; ++i) {
+    ngd_problem_desc d = descs[i];
+    d.stream = descs[0].stream;
+    ngd_ctx* c = nullptr;
+    const ngd_status st = ngd_create(&d, &c);
+    if (st != NGD_OK) {
+      for (ngd_ctx* q : b->ctx) ngd_destroy(q);
+      delete b;
+      return st;
+    }
+    b->ctx.push_back(c);
+  }
+  *out = b;
+  return NGD_OK;
+}
+
+void ngd_batch_destroy(ngd_batch* b) {
+  if (!b) return;
+  for (ngd_ctx* c : b->ctx) ngd_destroy(c);
+  delete b;
+}
+
+int ngd_batch_size(const ngd_batch* b) { return b ? (int)b->ctx.size() : 0; }
+
+ngd_ctx* ngd_batch_context(ngd_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+  return b->ctx[i];
+}
+
+const char* ngd_batch_last_error(const ngd_batch* b) { return b ? b->err.c_str() : ""; }
+
+ngd_status ngd_batch_step(ngd_batch* b, double* const* thetas, const ngd_step_opts* opts, ngd_step_info* infos) {
+  if (!b) return NGD_ERR_INVALID_ARG;
+  if (!thetas || !opts) {
+    b->err = "thetas/opts NULL";
+    return NGD_ERR_INVALID_ARG;
+  }
+  b->err.clear();
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    ngd_step_opts o = *opts;
+    o.seed = opts->seed + i;
+    const ngd_status st = ngd_step(b->ctx[i], thetas[i], &o, infos ? infos + i : nullptr);
+    if (st != NGD_OK) {
+      b->err = "problem " + std::to_string(i) + ": " + ngd_last_error(b->ctx[i]);
+      return st;
+    }
+  }
+  return NGD_OK;
 }
 
 }  // extern "C"

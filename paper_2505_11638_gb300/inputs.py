@@ -206,7 +206,7 @@ def make_workload(name: str, seed: int = 0) -> tuple[Workload, list[np.ndarray]]
             n_int = int(rng.integers(1000, 8001))
             k = int(rng.integers(1, 5))
             probs.append(poisson_problem(f"{name}[{j}]", 3, widths, n_int, n_int // 4, rng, freq=float(k)))
-        wl = Workload(name, probs, "f32", ell=200, mu=None, rtol=1e-6, steps=1, sketch="tf32")
+        wl = Workload(name, probs, "f32", ell=200, mu=None, rtol=1e-6, steps=1, sketch="f64")
     else:  # pragma: no cover
         raise KeyError(name)
     thetas = [glorot_theta(pr.widths, rng) for pr in wl.problems]

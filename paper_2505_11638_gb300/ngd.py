@@ -90,6 +90,12 @@ _SIGS = {
     "ngd_default_step_opts": ([ctypes.POINTER(StepOpts)], None),
     "ngd_kernel_launches": ([], ctypes.c_uint64),
     "ngd_precond_apply_noalloc": ([_I, ctypes.c_int64, _I, _P, ctypes.c_int64, _P, _D, _P, _P, _P], _I),
+    "ngd_batch_create": ([_P, _I, ctypes.POINTER(_P)], _I),
+    "ngd_batch_destroy": ([_P], None),
+    "ngd_batch_size": ([_P], _I),
+    "ngd_batch_context": ([_P, _I], _P),
+    "ngd_batch_last_error": ([_P], ctypes.c_char_p),
+    "ngd_batch_step": ([_P, _P, ctypes.POINTER(StepOpts), _P], _I),
 }
 
 
@@ -359,3 +365,65 @@ class PinnResidual(torch.autograd.Function):
         reuse = ngd.version == ctx.version
         g = ngd.vjp(None if reuse else theta, grad_r.contiguous().to(torch.float64))
         return g, None
+
+
+class Batch:
+    """Many independent problems stepped together (``ngd_batch_*``): one context per problem,
+    all on the current stream; ``step`` runs one NGD step for every problem."""
+
+    def __init__(self, problems, dtype: str = "f32", device: str | torch.device = "cuda"):
+        dev = torch.device(device)
+        self.device = dev
+        self.dtype = dtype
+        self._keep = []
+        n = len(problems)
+        descs = (ProblemDesc * n)()
+        for i, pr in enumerate(problems):
+            X = torch.as_tensor(pr.X, dtype=torch.float64, device=dev).contiguous()
+            w = torch.as_tensor(pr.w, dtype=torch.float64, device=dev).contiguous()
+            tg = torch.as_tensor(pr.target, dtype=torch.float64, device=dev).contiguous()
+            widths = (ctypes.c_int * len(pr.widths))(*pr.widths)
+            self._keep += [X, w, tg, widths]
+            descs[i] = ProblemDesc(pde=PDES[pr.pde], kappa=float(getattr(pr, "kappa", 0.0)),
+                                   n_layers=len(pr.widths) - 1, widths=widths, n_int=int(pr.n_int),
+                                   n_bnd=int(pr.n_bnd), X=X.data_ptr(), w=w.data_ptr(), target=tg.data_ptr(),
+                                   dtype=DTYPES[dtype], gv_mode=GV_MODES["auto"], mem_budget=0,
+                                   stream=torch.cuda.current_stream(dev).cuda_stream)
+        h = ctypes.c_void_p()
+        st = lib().ngd_batch_create(descs, n, ctypes.byref(h))
+        if st != NGD_OK:
+            raise NGDError(st, "ngd_batch_create failed")
+        self.handle = h
+        self.n = n
+        self.p = [int(lib().ngd_num_params(lib().ngd_batch_context(h, i))) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ngd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, thetas, **kw):
+        """thetas: list of float64 device tensors (one per problem), updated in place."""
+        assert len(thetas) == self.n
+        for th, p in zip(thetas, self.p):
+            _need(th, torch.float64, p, "theta")
+        o = ngd_default_step_opts()
+        for k, v in kw.items():
+            if k == "sketch":
+                v = SKETCH[v]
+            if k == "mu" and v is None:
+                v = 0.0
+            setattr(o, k, v)
+        ptrs = (ctypes.c_void_p * self.n)(*[th.data_ptr() for th in thetas])
+        infos = (StepInfo * self.n)()
+        st = lib().ngd_batch_step(self.handle, ptrs, ctypes.byref(o), infos)
+        if st != NGD_OK:
+            msg = lib().ngd_batch_last_error(self.handle).decode()
+            raise NGDError(st, msg)
+        return [infos[i].as_dict() for i in range(self.n)]

@@ -203,7 +203,9 @@ def test_factor_and_preconditioner_match_oracle(ngd, dtype, prec):
     Y_d = torch.tensor(Y_r.T.copy(), dtype=torch.float64 if prec == "f64" else wd, device="cuda")
     U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=prec)
     # the oracle factors the same (rounded) inputs
-    U_o, lam_o, nu_o = nystrom.nystrom_factor(Om_r, host(Y_d).T, nystrom.MANTISSA_BITS[prec])
+    # an FP64-accurate factor in an FP32 context runs in double-float (48-bit spacing)
+    mb = nystrom.MANTISSA_BITS["df" if (prec == "f64" and dtype == "f32") else prec]
+    U_o, lam_o, nu_o = nystrom.nystrom_factor(Om_r, host(Y_d).T, mb)
     assert abs(nu - nu_o) <= 1e-12 * nu_o
     lam_g = host(lam)
     top = lam_o > 1e-6 * lam_o[0]
@@ -364,6 +366,36 @@ def test_ngd_step_matches_oracle_fp64(ngd):
     assert rel(host(t) - th, th1_o - th) <= 1e-6
     assert info["relres"] <= wl.rtol
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_step_matches_oracle(ngd, dtype):
+    """Batching form: problems of uneven sizes (and different source frequencies) stepped by one
+    ngd_batch_step; problem i uses Philox key seed + i.  Each problem's step matches the oracle's
+    step on that problem (FP64: to the PCG direction tolerance; FP32: the FP64-accurate sketch)."""
+    probs, thetas = [], []
+    for i, (n_int, n_bnd, k) in enumerate([(600, 150, 1.0), (1100, 275, 3.0), (350, 87, 2.0)]):
+        pr, th = inputs.small_problem(d=3, widths=[3, 24, 24, 1], n_int=n_int, n_bnd=n_bnd, seed=40 + i, freq=k)
+        probs.append(pr)
+        thetas.append(th)
+    batch = ngd.Batch(probs, dtype=dtype)
+    ts = [dev(th) for th in thetas]
+    ell, mu, rtol = 60, 1e-6, (1e-10 if dtype == "f64" else 1e-7)
+    infos = batch.step(ts, ell=ell, mu=mu, rtol=rtol, maxit=2000, seed=7, step=3, sketch="f64")
+    assert len(infos) == 3
+    for i, (pr, th, info) in enumerate(zip(probs, thetas, infos)):
+        th1_o, info_o = solve.ngd_step(pr, th, ell=ell, mu=mu, rtol=0.0, maxit=info["pcg_iters"], seed=7 + i, step=3)
+        assert info["relres"] <= rtol, i
+        assert info["loss_after"] < info["loss_before"], i
+        if dtype == "f64":
+            assert abs(info["lam1"] - info_o.lam1) <= 1e-9 * info_o.lam1, i
+            assert info["alpha"] == info_o.alpha, i
+            assert rel(host(ts[i]) - th, th1_o - th) <= 1e-6, i
+        else:
+            # FP32 residuals and Jacobian: the direction agrees to the FP32 rounding of J
+            assert abs(info["lam1"] - info_o.lam1) <= 1e-4 * info_o.lam1, i
+            assert rel(host(ts[i]) - th, th1_o - th) <= 5e-3, i
+    batch.close()
 
 
 def test_ngd_step_fp32_paths(ngd):
