@@ -398,6 +398,66 @@ def run_batch(args, rank, world, local_rank):
     return 0
 
 
+def run_precision_study(args, rank):
+    """Precision form (10-D Poisson, p = 51073, N = 20480, ell = 1000): the same NGD steps from
+    the same theta0 with the sketch and factor in FP64 (FP64 context), FP64-accurate double-float
+    (FP32 context), TF32 and BF16 (tcgen05, FP32 accumulation); PCG iterations, time per step,
+    loss and relative L2 error of u_theta on 4096 independent points."""
+    import torch
+    from paper_2505_11638_gb300 import build, inputs, ngd
+
+    if rank != 0:
+        return 0
+    build.build()
+    wl, thetas = inputs.make_workload("poisson10d", seed=0)
+    pr = wl.problems[0]
+    xe = inputs.eval_points(pr, 4096, seed=0)
+    ue = inputs.u_star(pr, xe)
+    ev = inputs.Problem(name="eval", pde=pr.pde, widths=pr.widths, X=xe, w=np.full(len(xe), 1.0 / len(xe)),
+                        target=ue, n_int=0, n_bnd=len(xe), freq=pr.freq)
+    peaks = measured_peaks()
+    bf16_peak = peaks.get("bf16_tflops", 1881.0)
+    sketch_flop = 4.0 * pr.n * pr.p * wl.ell
+    forms = [("fp64", "f64", "f64"), ("double-float", "f32", "f64"), ("tf32", "f32", "tf32"), ("bf16", "f32", "bf16")]
+    out = {}
+    for name, dtype, sketch in forms:
+        ctx = ngd.Context(pr, dtype=dtype)
+        ectx = ngd.Context(ev, dtype="f64")
+        theta = torch.tensor(thetas[0], device="cuda")
+        infos = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for k in range(args.steps):
+            infos.append(ctx.step(theta, ell=wl.ell, mu=None, rtol=wl.rtol, maxit=500, seed=0, step=k, sketch=sketch))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        r, _ = ectx.residual(theta)
+        l2 = float(torch.linalg.norm(r).item() / np.linalg.norm(ue))
+        ms_sketch = float(np.mean([i["ms_sketch"] for i in infos]))
+        entry = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "pcg_iters": [i["pcg_iters"] for i in infos],
+                 "relres": [i["relres"] for i in infos], "loss": infos[-1]["loss_after"], "rel_l2_error": l2,
+                 "ms_sketch": ms_sketch, "ms_factor": float(np.mean([i["ms_factor"] for i in infos])),
+                 "ms_pcg": float(np.mean([i["ms_pcg"] for i in infos])),
+                 "sketch_tflops": sketch_flop / (ms_sketch * 1e-3) / 1e12}
+        if sketch in ("tf32", "bf16"):
+            peak = bf16_peak * (0.5 if sketch == "tf32" else 1.0)
+            entry["sketch_roofline"] = {"bound": "tensor", "achieved": entry["sketch_tflops"], "peak": peak,
+                                        "unit": "TFLOP/s", "frac": entry["sketch_tflops"] / peak,
+                                        "note": "time includes the test matrix and its CholeskyQR2"}
+        out[name] = entry
+        ctx.close()
+        ectx.close()
+        del theta
+        torch.cuda.empty_cache()
+    line = {"metric": "precision form: NGD steps/s, PCG iterations and L2 error per sketch precision",
+            "config": {"workload": "poisson10d", "N": pr.n, "p": pr.p, "ell": wl.ell, "mu": "rule",
+                       "rtol": wl.rtol, "steps": args.steps}, "data": "synthetic", "forms": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,10 +468,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"],
                     help="batch64: the batching form, 64 problems of uneven size per step (ngd_batch_step)")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="the precision form on poisson10d: all-FP64 GPU path vs FP64-accurate (double-float) "
+                         "vs TF32 / BF16 tensor-core sketches, --steps NGD steps each")
     args = ap.parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.precision_study:
+        return run_precision_study(args, rank)
     if args.workload == "batch64":
         return run_batch(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)

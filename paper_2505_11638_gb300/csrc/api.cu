@@ -871,7 +871,11 @@ ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
     ngd_destroy(ctx);
     return st;
   };
-  if (jac_smem_per_point(net, ctx->elt) * 4 > 200 * 1024 || jvp_smem_per_point(net, ctx->elt) * 2 > 200 * 1024)
+  // the Taylor kernels stage whole points in shared memory: at least one tile of 4 (C <= 8 channels)
+  // or 2 points for the Jacobian, 2 or 1 for the JVP, must fit the 200 KB budget
+  const size_t jac_pts = net.C <= 8 ? 4 : 2, jvp_pts = net.C <= 8 ? 2 : 1;
+  if (jac_smem_per_point(net, ctx->elt) * jac_pts > 200 * 1024 ||
+      jvp_smem_per_point(net, ctx->elt) * jvp_pts > 200 * 1024)
     return fail(NGD_ERR_UNSUPPORTED);
 
   const size_t jbytes = (size_t)ctx->N * ctx->ldJ * ctx->elt;
