@@ -128,6 +128,23 @@ def profiled_traffic(kernel: str, field: str = "traffic_bytes_per_launch"):
     return float(m.group(1))
 
 
+# ------------------------------------------------------------------ ranks (N > 1: independent replicas)
+def replica_seed(rank: int) -> int:
+    """Seed offset of rank's replica: the same workload shape with its own points and theta0."""
+    return rank * 1000
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest x over the ranks of the process group (x itself without one): a run's time is
+    its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_problem(seed_offset: int = 0):
     from paper_2505_11638_gb300 import inputs
     wl, thetas = inputs.make_workload(WORKLOAD, seed=seed_offset)
@@ -195,7 +212,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build.build()
     ngd.lib()
-    wl, pr, theta0 = make_problem(seed_offset=rank * 1000)
+    wl, pr, theta0 = make_problem(seed_offset=replica_seed(rank))
     ctx = ngd.Context(pr, dtype=wl.dtype)
     opts = dict(ell=wl.ell, mu=wl.mu, rtol=wl.rtol, maxit=1000, sketch=args.sketch, seed=rank)
     theta = torch.tensor(theta0, device="cuda")
@@ -227,11 +244,7 @@ def run_ours(args, rank, world, local_rank):
     launches = ngd.ngd_kernel_launches() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     ms_per_step = ms_max / args.steps
     value = world * 1e3 / ms_per_step
 
@@ -247,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
         h_theta.copy_(theta, non_blocking=True)
         torch.cuda.synchronize()
         _ = info["loss_after"]
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
     barrier()
 
     # The Gramian matvec alone (ngd_gramian_mv: k_pcg_fused in matvec mode), timed on the context stream
@@ -345,7 +358,7 @@ def run_batch(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
     build.build()
-    wl, thetas0 = inputs.make_workload("batch64", seed=rank * 1000)
+    wl, thetas0 = inputs.make_workload("batch64", seed=replica_seed(rank))
     batch = ngd.Batch(wl.problems, dtype=wl.dtype)
     opts = dict(ell=wl.ell, mu=None, rtol=wl.rtol, maxit=1000, sketch=args.sketch, seed=rank)
     thetas = [torch.tensor(th, device="cuda") for th in thetas0]
@@ -373,11 +386,7 @@ def run_batch(args, rank, world, local_rank):
     barrier()
     launches = ngd.ngd_kernel_launches() - l0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     n_prob = len(wl.problems)
     value = world * args.steps * n_prob / (ms * 1e-3)
     iters = [i["pcg_iters"] for step in infos for i in step]
