@@ -94,7 +94,8 @@ struct Smem {
   double coef[kMaxKSlice];          // (lam_ell + mu) / (lam_k + mu) - 1 for the block's k slice
   DF dpart[6][kT / 64];             // phase A: per ring stage, the dot group's warp sums
   double dred[kT + 1];
-  float2 rs[kMaxSlice];
+  float2 rs[kMaxSlice];               // r on the block's j slice, split (phase C -> U^T r)
+  double rd[kMaxSlice];               // r on the block's j slice (phase C -> phase E)
 };
 
 // Phase A: y_b = sum over the block's rows n of w_n (J_n . v) J_n, written as an FP32 pair.
@@ -290,46 +291,183 @@ __device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double*
   return vq;
 }
 
-// Partial U^T r over the block's j slice (r_j already split into sm.rs): thread (k4, half) takes
-// the four k of quad k4 (U rows padded to ldu, a multiple of 4: one float4 per row and word)
-// and every other row of the slice; the two halves are combined through shared memory (scr:
-// kT / 2 x 4 double-float values).
-__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm, DF* scr) {
+// The block's j slice of U (rows cb0 .. cb0 + ncol of Uh and Ul, ldu words each, contiguous)
+// passes through dynamic shared memory for the preconditioner: after a 16 KB head (the scaled
+// U^T r of phase E, or scratch) come two buffers of R rows; chunk i of the slice goes to buffer
+// i % 2, chunk 0 holding the remainder rows so that the later chunks are full.  Phase C walks
+// the chunks upwards and phase E downwards, so E starts on the two chunks C left resident and
+// copies only the others, each while the previous chunk is being used (cp.async groups).  The
+// row pass (phase A) reuses the space as its ring, so C always copies the whole slice.
+constexpr int kHead = 16 * 1024;
+
+struct UStage {
+  float* buf0;                       // buffer b at buf0 + b * bstride: R * ldu high, then R * ldu low words
+  int bstride, R, nch, len0;
+  __device__ __forceinline__ float* buf(int i) const { return buf0 + (i & 1) * bstride; }
+  __device__ __forceinline__ int start(int i) const { return i == 0 ? 0 : len0 + (i - 1) * R; }
+  __device__ __forceinline__ int len(int i) const { return i == 0 ? len0 : R; }
+};
+
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));   // volatile: not hoisted out of the CG loop
+  return v;
+}
+
+__device__ __forceinline__ UStage ustage(const FusedPcgArgs& a, unsigned char* dsm, int ncol) {
+  UStage st;
+  const unsigned half = ((dyn_smem_bytes() - kHead) / 2) & ~15u;
+  st.buf0 = reinterpret_cast<float*>(dsm + kHead);
+  st.bstride = (int)(half / 4);
+  st.R = (int)(half / (8u * (unsigned)a.ldu));
+  st.nch = ncol > 0 ? (ncol + st.R - 1) / st.R : 0;
+  st.len0 = ncol - (st.nch - 1) * st.R;
+  return st;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+// Copy chunk i of the slice into its buffer (one commit group).
+__device__ __forceinline__ void ustage_issue(const FusedPcgArgs& a, const UStage& st, int64_t cb0, int i) {
+  const int n16 = st.len(i) * a.ldu / 4;
+  const int64_t off = (cb0 + st.start(i)) * a.ldu;
+  float* dh = st.buf(i);
+  float* dl = dh + st.R * a.ldu;
+  for (int e = threadIdx.x; e < 2 * n16; e += kT) {
+    const bool lo = e >= n16;
+    const int o = 4 * (lo ? e - n16 : e);
+    cp_async16((lo ? dl : dh) + o, (lo ? a.Ul : a.Uh) + off + o);
+  }
+  cp_async_commit();
+}
+
+// Phase C's partial U^T r over the block's j slice (r_j already split into sm.rs), written to
+// w1p[b, :].  Thread (grp, t) takes k quads t, t + nthr (U rows padded to ldu, a multiple of 4)
+// and rows grp, grp + ngrp, ... of every chunk; the ngrp row groups are combined at the end
+// through the head of shared memory.  Leaves the last two chunks in their buffers.
+constexpr int kUQ = 2;             // k quads per thread: ell <= kUQ * 4 * kT
+__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm,
+                                            unsigned char* dsm) {
+  const UStage st = ustage(a, dsm, ncol);
   const int nk4 = a.ldu / 4;
-  const int half = threadIdx.x / (kT / 2), tq = threadIdx.x % (kT / 2);
-  for (int base = 0; base < nk4; base += kT / 2) {
-    const int k4 = base + tq;
-    DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    if (k4 < nk4) {
-      const float4* uh = reinterpret_cast<const float4*>(a.Uh + cb0 * a.ldu) + k4;
-      const float4* ul = reinterpret_cast<const float4*>(a.Ul + cb0 * a.ldu) + k4;
-#pragma unroll 4
-      for (int jj = half; jj < ncol; jj += 2) {
-        const float2 rr = sm.rs[jj];
-        const float4 h = __ldg(uh + (int64_t)jj * nk4), l = __ldg(ul + (int64_t)jj * nk4);
-        df_add_prod2(acc[0], h.x, l.x, rr.x, rr.y);
-        df_add_prod2(acc[1], h.y, l.y, rr.x, rr.y);
-        df_add_prod2(acc[2], h.z, l.z, rr.x, rr.y);
-        df_add_prod2(acc[3], h.w, l.w, rr.x, rr.y);
-      }
-    }
-    if (half == 1) {
+  const int ngrp = max(1, min(8, kT / nk4)), nthr = kT / ngrp;
+  const int grp = threadIdx.x / nthr, t = threadIdx.x % nthr;
+  DF acc[kUQ][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) scr[tq * 4 + e] = acc[e];
-    }
+  for (int q = 0; q < kUQ; ++q)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[q][e] = DF{0.f, 0.f};
+  if (st.nch > 0) ustage_issue(a, st, cb0, 0);
+  if (st.nch > 1) ustage_issue(a, st, cb0, 1);
+  for (int i = 0; i < st.nch; ++i) {
+    if (i + 1 < st.nch) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncthreads();
-    if (half == 0 && k4 < nk4) {
+    const int r0 = st.start(i), nr = st.len(i);
+    const float4* bh = reinterpret_cast<const float4*>(st.buf(i));
+    const float4* bl = bh + st.R * nk4;
+    if (grp < ngrp) {
+#pragma unroll 2
+      for (int rr = grp; rr < nr; rr += ngrp) {
+        const float2 rv = sm.rs[r0 + rr];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = 4 * k4 + e;
-        if (k < a.ell) {
-          const DF s = df_add(acc[e], scr[tq * 4 + e]);
-          __stcg(a.w1p + (int64_t)blockIdx.x * a.ell + k, make_float2(s.hi, s.lo));
+        for (int q = 0; q < kUQ; ++q) {
+          const int k4 = t + q * nthr;
+          if (k4 < nk4) {
+            const float4 h = bh[rr * nk4 + k4], l = bl[rr * nk4 + k4];
+            df_add_prod2(acc[q][0], h.x, l.x, rv.x, rv.y);
+            df_add_prod2(acc[q][1], h.y, l.y, rv.x, rv.y);
+            df_add_prod2(acc[q][2], h.z, l.z, rv.x, rv.y);
+            df_add_prod2(acc[q][3], h.w, l.w, rv.x, rv.y);
+          }
         }
       }
     }
-    __syncthreads();
+    if (i + 2 < st.nch) {
+      __syncthreads();
+      ustage_issue(a, st, cb0, i + 2);
+    }
   }
+  DF* scr = reinterpret_cast<DF*>(dsm);             // (ngrp - 1) x nthr x 4 values (ngrp > 1: one quad)
+  if (ngrp > 1 && grp >= 1 && grp < ngrp) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) scr[((grp - 1) * nthr + t) * 4 + e] = acc[0][e];
+  }
+  __syncthreads();
+  if (grp == 0) {
+#pragma unroll
+    for (int q = 0; q < kUQ; ++q) {
+      const int k4 = t + q * nthr;
+      if (k4 < nk4) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 4 * k4 + e;
+          DF s = acc[q][e];
+          for (int g2 = 1; g2 < ngrp; ++g2) s = df_add(s, scr[((g2 - 1) * nthr + t) * 4 + e]);
+          if (k < a.ell) __stcg(a.w1p + (int64_t)blockIdx.x * a.ell + k, make_float2(s.hi, s.lo));
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Phase E: z_j = r_j + sum_k U[j, k] w2[k] on the block's j slice (w2 in the head of shared
+// memory), chunks taken downwards starting with the two that phase C left resident; a warp takes
+// two rows of a chunk at a time, lanes over k quads.  Returns the thread's part of r . z.
+__device__ __forceinline__ double precond_rows(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm,
+                                               unsigned char* dsm) {
+  const UStage st = ustage(a, dsm, ncol);
+  const float2* w2s = reinterpret_cast<const float2*>(dsm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nk4 = a.ldu / 4;
+  double rzp = 0.0;
+  for (int i = st.nch - 1; i >= 0; --i) {
+    if (i >= 1 && i + 2 <= st.nch) cp_async_wait<1>();   // chunk i - 1 may still be in flight
+    else cp_async_wait<0>();
+    __syncthreads();
+    const int r0 = st.start(i), nr = st.len(i);
+    const float4* bh = reinterpret_cast<const float4*>(st.buf(i));
+    const float4* bl = bh + st.R * nk4;
+    for (int j0 = 2 * warp; j0 < nr; j0 += 2 * kW) {
+      const bool two = j0 + 1 < nr;
+      const float4* uh0 = bh + j0 * nk4;
+      const float4* ul0 = bl + j0 * nk4;
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
+#pragma unroll 1
+      for (int k4 = lane; k4 < nk4; k4 += 32) {
+        const float4 wa = reinterpret_cast<const float4*>(w2s)[2 * k4];       // w2[4 k4], w2[4 k4 + 1]
+        const float4 wb = reinterpret_cast<const float4*>(w2s)[2 * k4 + 1];   // w2[4 k4 + 2], w2[4 k4 + 3]
+        const float4 h0 = uh0[k4], l0 = ul0[k4];
+        const float4 h1 = two ? uh0[nk4 + k4] : zero4, l1 = two ? ul0[nk4 + k4] : zero4;
+        df_add_prod2(acc0, h0.x, l0.x, wa.x, wa.y);
+        df_add_prod2(acc0, h0.y, l0.y, wa.z, wa.w);
+        df_add_prod2(acc0, h0.z, l0.z, wb.x, wb.y);
+        df_add_prod2(acc0, h0.w, l0.w, wb.z, wb.w);
+        df_add_prod2(acc1, h1.x, l1.x, wa.x, wa.y);
+        df_add_prod2(acc1, h1.y, l1.y, wa.z, wa.w);
+        df_add_prod2(acc1, h1.z, l1.z, wb.x, wb.y);
+        df_add_prod2(acc1, h1.w, l1.w, wb.z, wb.w);
+      }
+      const DF s = warp_reduce_scatter2(acc0, acc1);     // lanes 0..15: row j0, 16..31: row j0 + 1
+      const int q = lane >> 4;
+      if ((lane & 15) == 0 && (q == 0 || two)) {
+        const int jj = r0 + j0 + q;
+        const double rj = sm.rd[jj], zj = rj + df_to_double(s);
+        a.z[cb0 + jj] = zj;
+        rzp += rj * zj;
+      }
+    }
+    if (i >= 2) {
+      __syncthreads();
+      ustage_issue(a, st, cb0, i - 2);
+    }
+  }
+  return rzp;
 }
 
 template <int CG, int S>
@@ -338,7 +476,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   float4* ring = reinterpret_cast<float4*>(dsm);
   float2* w2s = reinterpret_cast<float2*>(dsm);          // phase E only (aliases the ring)
-  DF* scr = reinterpret_cast<DF*>(dsm);                  // phases B, C only (aliases the ring)
+  DF* scr = reinterpret_cast<DF*>(dsm);                  // phase B only (aliases the ring)
   __shared__ Smem sm;
   const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
   const double mu = a.mu_d ? *a.mu_d : a.mu_h;
@@ -375,10 +513,11 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     float h, l;
     split_df(gj, h, l);
     sm.rs[jj] = make_float2(h, l);
+    sm.rd[jj] = gj;
   }
   rr = block_allsum(rr, sm.dred);
   if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
-  if (pre) utr_partial(a, cb0, ncol, sm, scr);
+  if (pre) utr_partial(a, cb0, ncol, sm, dsm);
   grid.sync();
 
   int it = 0, status = 0;
@@ -422,54 +561,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     if (pre) {
       for (int k = tid; k < a.ldu; k += kT) w2s[k] = k < a.ell ? __ldcg(a.w2 + k) : make_float2(0.f, 0.f);
       __syncthreads();
-      // a warp takes two rows of U at a time (j-major, rows padded to ldu), lanes over k quads;
-      // every load of the pair is issued before the arithmetic
-      const int lane = tid & 31, warp = tid >> 5;
-      const int nk4 = a.ldu / 4;
-      constexpr int kQ = 16;                               // k quads per lane: ell <= 32 * 4 * kQ = 2048
-      for (int j0 = 2 * warp; j0 < ncol; j0 += 2 * kW) {
-        const bool two = j0 + 1 < ncol;
-        const float4* uh0 = reinterpret_cast<const float4*>(a.Uh + (cb0 + j0) * a.ldu);
-        const float4* ul0 = reinterpret_cast<const float4*>(a.Ul + (cb0 + j0) * a.ldu);
-        DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
-        for (int q0 = 0; q0 < kQ; q0 += 4) {
-          if (q0 * 32 >= nk4) break;
-          float4 h0[4], l0[4], h1[4], l1[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k4 = lane + 32 * (q0 + i);
-            const bool in = k4 < nk4;
-            h0[i] = in ? __ldg(uh0 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            l0[i] = in ? __ldg(ul0 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            h1[i] = in && two ? __ldg(uh0 + nk4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            l1[i] = in && two ? __ldg(ul0 + nk4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k4 = lane + 32 * (q0 + i);
-            if (k4 < nk4) {
-              const float4 wa = reinterpret_cast<const float4*>(w2s)[2 * k4];       // w2[4 k4], w2[4 k4 + 1]
-              const float4 wb = reinterpret_cast<const float4*>(w2s)[2 * k4 + 1];   // w2[4 k4 + 2], w2[4 k4 + 3]
-              df_add_prod2(acc0, h0[i].x, l0[i].x, wa.x, wa.y);
-              df_add_prod2(acc0, h0[i].y, l0[i].y, wa.z, wa.w);
-              df_add_prod2(acc0, h0[i].z, l0[i].z, wb.x, wb.y);
-              df_add_prod2(acc0, h0[i].w, l0[i].w, wb.z, wb.w);
-              df_add_prod2(acc1, h1[i].x, l1[i].x, wa.x, wa.y);
-              df_add_prod2(acc1, h1[i].y, l1[i].y, wa.z, wa.w);
-              df_add_prod2(acc1, h1[i].z, l1[i].z, wb.x, wb.y);
-              df_add_prod2(acc1, h1[i].w, l1[i].w, wb.z, wb.w);
-            }
-          }
-        }
-        const DF s = warp_reduce_scatter2(acc0, acc1);     // lanes 0..15: row j0, 16..31: row j0 + 1
-        const int q = lane >> 4;
-        if ((lane & 15) == 0 && (q == 0 || two)) {
-          const int64_t j = cb0 + j0 + q;
-          const double rj = a.r[j], zj = rj + df_to_double(s);
-          a.z[j] = zj;
-          rzp += rj * zj;
-        }
-      }
+      rzp = precond_rows(a, cb0, ncol, sm, dsm);
     } else {
       for (int jj = tid; jj < ncol; jj += kT) {
         const double rj = a.r[cb0 + jj];
@@ -522,10 +614,11 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
       float h, l;
       split_df(rj, h, l);
       sm.rs[jj] = make_float2(h, l);
+      sm.rd[jj] = rj;
     }
     rr = block_allsum(rr, sm.dred);
     if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
-    if (pre) utr_partial(a, cb0, ncol, sm, scr);
+    if (pre) utr_partial(a, cb0, ncol, sm, dsm);
     ++it;
     grid.sync();
   }
@@ -557,8 +650,10 @@ cudaError_t launch_cg(const FusedPcgArgs& a, int G, cudaStream_t s) {
   constexpr int S = stages_for<CG>();
   static_assert(S >= 3, "shared-memory ring too small");
   auto kern = k_pcg_fused<CG, S>;
-  // dynamic shared memory: the ring, or the scaled U^T r of phase E (ell <= 2048), whichever is larger
-  constexpr size_t smem = std::max((size_t)S * CG * kGT * 16, (size_t)2048 * sizeof(float2));
+  // dynamic shared memory: the whole budget (one block per SM in any case), shared by the ring of
+  // phase A and the head plus the two U buffers of phases C and E (16 KB + 2 rows of U at least)
+  constexpr size_t smem = kSmemBudget;
+  static_assert((size_t)S * CG * kGT * 16 <= smem && kHead + 2 * 8 * 2048 <= smem, "dynamic shared memory");
   static std::mutex mu;
   static int configured_dev = -1, per_sm = 0;
   int dev = 0;
