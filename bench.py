@@ -105,25 +105,30 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_sha():
+# the source files each profiled kernel is compiled from (its translation unit and the headers it
+# includes from the package): a committed ncu summary counts only while these are unchanged
+KERNEL_SOURCES = {"k_pcg_fused": ["pcg_fused.cu", "df.cuh", "linalg.cuh"]}
+
+
+def kernel_source_sha(kernel: str = "k_pcg_fused"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_11638_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, field: str = "traffic_bytes_per_launch"):
-    """DRAM bytes (per launch, or per the unit `field` names) of `kernel` from a committed ncu
-    summary, if that summary was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+def profiled_traffic(profile: str, kernel: str, field: str = "traffic_bytes_per_launch"):
+    """DRAM bytes (per launch, or per the unit `field` names) of `kernel` from the committed ncu
+    summary profiles/<profile>.md, if that summary was taken on the kernel's current sources."""
+    path = os.path.join(ROOT, "profiles", f"{profile}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m = re.search(field + r":\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != kernel_source_sha():
+    if not m or not s or s.group(1) != kernel_source_sha(kernel):
         return None
     return float(m.group(1))
 
@@ -310,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"kernel": "k_pcg_fused (whole PCG, one launch); unit: one CG iteration", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if hbm else "fallback 6.8 TB/s",
-                "traffic": profiled_traffic("k_pcg_fused_poisson5d", "traffic_bytes_per_iteration"),
+                "traffic": profiled_traffic("k_pcg_fused_poisson5d", "k_pcg_fused", "traffic_bytes_per_iteration"),
                 "bytes_per_iteration": bytes_it,
                 "us_per_iteration": us_it,
                 "matvec": {"kernel": "k_pcg_fused, matvec mode (ngd_gramian_mv)", "us": gv_ms * 1e3,
