@@ -107,7 +107,7 @@ def measured_peaks():
 
 # the source files each profiled kernel is compiled from (its translation unit and the headers it
 # includes from the package): a committed ncu summary counts only while these are unchanged
-KERNEL_SOURCES = {"k_pcg_fused": ["pcg_fused.cu", "df.cuh", "linalg.cuh"]}
+KERNEL_SOURCES = {"k_pcg_fused": ["pcg_fused.cu", "df.cuh"]}
 
 
 def kernel_source_sha(kernel: str = "k_pcg_fused"):

@@ -219,6 +219,12 @@ ngd_status ensure_gpart(ngd_ctx* ctx, size_t elems) {
   return NGD_OK;
 }
 
+// Number of K slices launch_gemm_df makes of K for a requested split count.
+int split_count(int64_t K, int nsplit) {
+  const int64_t kps = nsplit > 1 ? ((K + nsplit - 1) / nsplit + 15) / 16 * 16 : std::max<int64_t>(K, 1);
+  return (int)((K + kps - 1) / kps);
+}
+
 // K-splits for an M x N output with a long K (tall-skinny products), so that ~1200 tiles run.
 int choose_splits(int64_t M, int64_t N, int64_t K) {
   const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
@@ -407,19 +413,42 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
     // FP64-accurate sketch of the FP32 Jacobian (double-float arithmetic): Zw (FP64) = diag(w) J Om,
     // Y64 = J^T Zw.  The Nystrom core then resolves G's spectrum down to eps64 ||Y||, as in the paper.
     if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "the FP64-accurate sketch needs the stored Jacobian%s");
+    // K is split where that fills the GPU's block slots more evenly; the slices' FP64 partials
+    // are then added in a fixed order
     GemmDfArgs<float, float> g1;
     g1.M = ctx->N; g1.N = ell; g1.K = ctx->p;
     g1.A = (const float*)ctx->J; g1.sam = ctx->ldJ; g1.sak = 1;
     g1.B = (const float*)Om; g1.sbk = 1; g1.sbn = ctx->ldP;
-    g1.out64 = ctx->Zw64; g1.scm = ell; g1.scn = 1;
+    g1.scm = ell; g1.scn = 1;
     g1.rowscale = ctx->ps.w;
-    launch_gemm_df<float, float>(g1, ctx->stream);
+    g1.nsplit = gemm_df_splits(g1.M, g1.N, g1.K);
+    const int nz1 = split_count(g1.K, g1.nsplit);
+    if (nz1 > 1) {
+      TRY(ensure_gpart(ctx, (size_t)nz1 * ctx->N * ell));
+      g1.out64 = ctx->gpart; g1.split_stride = (int64_t)ctx->N * ell;
+      launch_gemm_df<float, float>(g1, ctx->stream);
+      launch_sum_splits(ctx->gpart, nz1, (int64_t)ctx->N * ell, (int64_t)ctx->N * ell, ctx->Zw64, ctx->stream);
+    } else {
+      g1.out64 = ctx->Zw64;
+      launch_gemm_df<float, float>(g1, ctx->stream);
+    }
     GemmDfArgs<float, double> g2;
     g2.M = ctx->p; g2.N = ell; g2.K = ctx->N;
     g2.A = (const float*)ctx->J; g2.sam = 1; g2.sak = ctx->ldJ;
     g2.B = ctx->Zw64; g2.sbk = ell; g2.sbn = 1;
-    g2.out64 = ctx->Y64; g2.scm = 1; g2.scn = ctx->ldP;
-    launch_gemm_df<float, double>(g2, ctx->stream);
+    g2.scm = 1; g2.scn = ctx->ldP;
+    g2.nsplit = gemm_df_splits(g2.M, g2.N, g2.K);
+    const int nz2 = split_count(g2.K, g2.nsplit);
+    if (nz2 > 1) {
+      TRY(ensure_gpart(ctx, (size_t)nz2 * ctx->ldP * ell));
+      g2.out64 = ctx->gpart; g2.split_stride = (int64_t)ctx->ldP * ell;
+      launch_gemm_df<float, double>(g2, ctx->stream);
+      launch_sum_splits_t<double>(ctx->gpart, nz2, (int64_t)ctx->ldP * ell, ctx->p, ell, ctx->ldP, ctx->Y64, ctx->ldP,
+                                  ctx->stream);
+    } else {
+      g2.out64 = ctx->Y64;
+      launch_gemm_df<float, double>(g2, ctx->stream);
+    }
     return check_launch(ctx);
   }
   if (ctx->stored_j) {

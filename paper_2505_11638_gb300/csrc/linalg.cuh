@@ -42,6 +42,8 @@ template <typename TA, typename TB> struct GemmDfArgs {
   int accumulate = 0;
 };
 template <typename TA, typename TB> void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s);
+// K slices that fill the GPU's block slots most evenly for an M x N double-float GEMM
+int gemm_df_splits(int64_t M, int64_t N, int64_t K);
 
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);
 template <typename T> void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s);
