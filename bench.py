@@ -472,6 +472,70 @@ def run_precision_study(args, rank):
     return 0
 
 
+def run_train(args, rank):
+    """NystromNGD training run on the paper's 3-D Poisson PINN (poisson3d: MLP 3-64-64-64-1,
+    p = 8641, 10000 + 1000 points): Alg. 1 with Alg. 3 and Alg. 4, adaptive rank from 20 up to
+    500 in steps of 20, damping max(gamma eps lambda_hat_1, 1e-4 L^2), pCG capped at 20
+    iterations (the paper's settings for its NGD runs).  Reports NGD steps/s over the run (CUDA
+    events around every step), the rank trajectory, and the relative L2 and H1 errors of u_theta
+    against u* on 10x the training points (independent, interior), every 10 steps."""
+    import torch
+    from paper_2505_11638_gb300 import build, inputs, ngd
+
+    if rank != 0:
+        return 0
+    build.build()
+    wl, thetas = inputs.make_workload("poisson3d", seed=0)
+    pr = wl.problems[0]
+    ctx = ngd.Context(pr, dtype=wl.dtype)
+    xe = inputs.eval_points(pr, 10 * pr.n, seed=0)
+    ue, ge = inputs.u_star(pr, xe), inputs.grad_u_star(pr, xe)
+    ev = inputs.Problem(name="eval", pde=pr.pde, widths=pr.widths, X=xe, w=np.full(len(xe), 1.0 / len(xe)),
+                        target=ue, n_int=0, n_bnd=len(xe), freq=pr.freq)
+    ectx = ngd.Context(ev, dtype="f64", gv_mode="matrix_free", mem_budget=1)
+    ue_t, ge_t = torch.tensor(ue, device="cuda"), torch.tensor(ge, device="cuda")
+    norm_l2 = float(torch.linalg.norm(ue_t))
+    norm_h1 = float(torch.sqrt((ue_t ** 2).sum() + (ge_t ** 2).sum()))
+
+    def errors(theta):
+        out = ectx.eval(theta)
+        du, dg = out[:, 0] - ue_t, out[:, 1:1 + pr.d] - ge_t
+        return (float(torch.linalg.norm(du)) / norm_l2,
+                float(torch.sqrt((du ** 2).sum() + (dg ** 2).sum())) / norm_h1)
+
+    theta = torch.tensor(thetas[0], device="cuda")
+    opts = dict(mu=None, mu_loss_coef=1e-4, ell_max=500, ell_delta=20, rtol=wl.rtol, maxit=20, sketch=args.sketch,
+                seed=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ell, total_ms, log, ells = wl.ell, 0.0, [], []
+    l2, h1 = errors(theta)
+    log.append({"step": 0, "seconds": 0.0, "ell": ell, "loss": None, "rel_l2": l2, "rel_h1": h1})
+    for k in range(args.train_steps):
+        e0.record(stream)
+        info = ctx.step(theta, ell=ell, step=k, **opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        ells.append(ell)
+        ell = info["ell_next"]
+        if (k + 1) % 10 == 0 or k + 1 == args.train_steps:
+            l2, h1 = errors(theta)
+            log.append({"step": k + 1, "seconds": total_ms / 1e3, "ell": ells[-1], "loss": info["loss_after"],
+                        "mu": info["mu"], "pcg_iters": info["pcg_iters"], "rel_l2": l2, "rel_h1": h1})
+    line = {"metric": "NystromNGD training run: NGD steps/s, rank trajectory and relative errors",
+            "value": args.train_steps / (total_ms / 1e3), "unit": "steps/s", "n_gpus": 1,
+            "steps": args.train_steps, "ms_per_step": total_ms / args.train_steps, "data": "synthetic",
+            "config": {"workload": "poisson3d", "N": pr.n, "p": pr.p, "ell0": wl.ell, "ell_max": 500,
+                       "ell_delta": 20, "mu": "max(10 eps lambda_1, 1e-4 L^2)", "pcg_maxit": 20,
+                       "sketch": args.sketch, "eval_points": len(xe)},
+            "final": log[-1], "ell_trajectory": ells, "log": log}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    ectx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,6 +546,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"],
                     help="batch64: the batching form, 64 problems of uneven size per step (ngd_batch_step)")
+    ap.add_argument("--train", action="store_true",
+                    help="a NystromNGD training run (adaptive rank and damping) on the 3-D Poisson PINN, "
+                         "--train-steps NGD steps, with L2/H1 errors every 10 steps")
+    ap.add_argument("--train-steps", type=int, default=200)
     ap.add_argument("--precision-study", action="store_true",
                     help="the precision form on poisson10d: all-FP64 GPU path vs FP64-accurate (double-float) "
                          "vs TF32 / BF16 tensor-core sketches, --steps NGD steps each")
@@ -491,6 +559,8 @@ def main():
         return run_reference(args, rank, world)
     if args.precision_study:
         return run_precision_study(args, rank)
+    if args.train:
+        return run_train(args, rank)
     if args.workload == "batch64":
         return run_batch(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)

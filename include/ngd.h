@@ -105,12 +105,22 @@ typedef struct {
   double armijo_c1;       /* sufficient-decrease constant (default 1e-4) */
   double armijo_rho;      /* backtracking factor (default 0.5) */
   int armijo_max;         /* maximum number of trial steps (default 30) */
+  double mu_loss_coef;    /* c of the adaptive damping of Sec. 5, mu = max(gamma eps lambda_hat_1,
+                             c L(theta)^2) when mu <= 0 (the paper's runs: 1e-4); 0: mu = gamma eps
+                             lambda_hat_1 (Alg. 4) */
+  int ell_max;            /* rank adaptivity of Alg. 4: 0 = off (ell_next = ell); otherwise the cap
+                             l_max >= 1 of ell_next */
+  int ell_delta;          /* rank increase delta_l of Alg. 4 (the paper's runs: 20), >= 0 */
 } ngd_step_opts;
 
 typedef struct {
   double loss_before, loss_after, alpha, mu, lam1, lam_ell, nu, relres;
   int pcg_iters, armijo_trials, shift_retries, status;
   double ms_linearize, ms_sketch, ms_factor, ms_pcg, ms_linesearch; /* CUDA-event phase times */
+  int ell_next;           /* rank for the next step (Alg. 4 rule; = ell when ell_max = 0):
+                             min(ell + ell_delta, ell_max) if lambda_hat_ell > 10 mu, else
+                             min(i + 1, ell_max) with i the first (1-based) index of lambda_hat
+                             below 10 mu (ell if there is none) */
 } ngd_step_info;
 
 /* ---------------------------------------------------------------- context */
@@ -150,6 +160,17 @@ ngd_status ngd_set_stream(ngd_ctx* ctx, void* stream);
  * a following ngd_vjp(ctx, NULL, ...). */
 ngd_status ngd_residual(ngd_ctx* ctx, const double* theta, double* r, double* loss);
 
+/* The network's output channels at the context's points (Sec. 2.2.1 forward Laplacian): for
+ * point n, out[n * (d + 2) + c] holds u_theta (c = 0), the d first derivatives (c = 1 .. d, in
+ * input order; coordinate 0 is t for NGD_PDE_HEAT) and the Laplacian over the spatial
+ * coordinates (c = d + 1), computed by the same kernel as ngd_residual in the context's
+ * working precision and written as float64.  Used to evaluate L2 and H1 errors against a known
+ * solution on a separate set of points (a context built on those points).
+ * theta: device p (float64); out: device N (d + 2) float64, caller-owned.  Asynchronous; also
+ * leaves the residuals and the loss in the context as ngd_residual does.
+ * Errors: INVALID_ARG (NULL pointer), UNSUPPORTED (network too wide), CUDA. */
+ngd_status ngd_eval(ngd_ctx* ctx, const double* theta, double* out);
+
 /* Jacobian-vector product Jv (forward-mode tangents of the Taylor-mode forward;
  * Thm. 1 consequence, Sec. 3.2).  v: device p, out: device N. */
 ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* out);
@@ -160,7 +181,7 @@ ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* o
  * cot: device N, out: device p. */
 ngd_status ngd_vjp(ngd_ctx* ctx, const double* theta, const double* cot, double* out);
 
-/* Gradient g = grad L = J^T (w .* r) (Alg. 1 line 2), residual r (device N or NULL)
+/* Gradient g = grad L = J^T (w .* r) (the gradient of Alg. 1), residual r (device N or NULL)
  * and loss (host or NULL, synchronises when non-NULL).  Linearizes at theta. */
 ngd_status ngd_gradient(ngd_ctx* ctx, const double* theta, double* g, double* r, double* loss);
 
@@ -219,11 +240,15 @@ ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, dou
                          const void* U, int u_dtype, const double* lam, int ell, double rtol, int maxit,
                          double* d, int* iters, double* relres);
 
-/* One Nystrom-preconditioned matrix-free NGD step (Alg. 1 with Alg. 3 and Alg. 4,
- * fixed ell): gradient, sketch with a fresh Omega, factor (retrying with an
- * 8x, 64x, ..., 8^5x shift on NOT_SPD), mu (fixed or the Alg. 4 rule), pCG, Armijo
- * backtracking along theta - alpha d, update.  theta: device p, updated in place.
- * info: host or NULL.  Synchronises. */
+/* One Nystrom-preconditioned matrix-free NGD step (Alg. 1 with Alg. 3 and Alg. 4):
+ * gradient, sketch of rank opts->ell with a fresh Omega, factor (retrying with an
+ * 8x, 64x, ..., 8^5x shift on NOT_SPD), mu (fixed, the Alg. 4 rule, or the adaptive
+ * max(gamma eps lambda_hat_1, c L^2) of Sec. 5), pCG, Armijo backtracking along
+ * theta - alpha d, update, and the rank for the next step (info->ell_next, Alg. 4).
+ * A training loop passes info->ell_next as the next step's ell.  theta: device p,
+ * updated in place.  info: host or NULL.  Synchronises.
+ * Errors: INVALID_ARG (bad options: ell outside [1, min(p, 2048)], ell_max < 0 or above
+ * that range, ell_delta < 0, ...), NOT_SPD, BREAKDOWN, NONFINITE, CUDA. */
 ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* opts, ngd_step_info* info);
 
 /* Nystrom preconditioner apply that allocates nothing.  The paper has no counterpart: this
@@ -269,7 +294,7 @@ ngd_status ngd_batch_step(ngd_batch* batch, double* const* thetas, const ngd_ste
 
 /* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
  * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,
- * c1 1e-4, rho 0.5, 30 trials. */
+ * c1 1e-4, rho 0.5, 30 trials, mu_loss_coef 0, ell_max 0 (fixed rank), ell_delta 20. */
 void ngd_default_step_opts(ngd_step_opts* opts);
 
 #ifdef __cplusplus

@@ -205,7 +205,7 @@ def vjp(problem, theta, cot):
 
 
 def gradient(problem, theta):
-    """grad L = J^T (w * r) (Alg. 1 line 2), with r and L."""
+    """grad L = J^T (w * r) (the gradient of Alg. 1), with r and L."""
     r, L = residual(problem, theta)
     return vjp(problem, theta, problem.w * r), r, L
 

@@ -85,5 +85,29 @@ def precond_apply(U, lam, mu, v):
 
 
 def mu_from_lambda1(lam1: float, gamma: float = 10.0, eps: float = EPS64) -> float:
-    """mu = gamma * eps_mach * lambda_hat_1 (Sec. 4.3, Alg. 4 second step)."""
+    """mu = gamma * eps_mach * lambda_hat_1 (Sec. 4.3 and Alg. 4)."""
     return gamma * eps * lam1
+
+
+def mu_adaptive(lam1: float, loss: float, gamma: float = 10.0, coef: float = 1e-4, eps: float = EPS64) -> float:
+    """The damping of the paper's experiments (Sec. 5): the larger of the Alg. 4 value and
+    coef L(theta)^2, which regularises more strongly while the loss is large."""
+    return max(mu_from_lambda1(lam1, gamma, eps), coef * loss * loss)
+
+
+def next_rank(lam, mu: float, ell: int, ell_max: int, delta: int) -> int:
+    """Rank of the next sketch (the rank update of Alg. 4), with the paper's 1-based index i.
+
+    lambda_hat_ell > 10 mu: the approximation has not reached the decay yet, grow by delta up
+    to ell_max.  Otherwise shrink to one past the first eigenvalue below 10 mu,
+    min(min{i : lambda_hat_i < 10 mu} + 1, ell_max).  Reading where the paper is silent: when
+    lambda_hat_ell equals 10 mu exactly no index qualifies, and the rank stays ell.
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    assert lam.shape == (ell,)
+    if lam[ell - 1] > 10.0 * mu:
+        return min(ell + delta, ell_max)
+    below = [i for i in range(1, ell + 1) if lam[i - 1] < 10.0 * mu]
+    if not below:
+        return ell
+    return min(below[0] + 1, ell_max)

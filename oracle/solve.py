@@ -92,16 +92,19 @@ class StepInfo:
     pcg_iters: int
     relres: float
     armijo_trials: int
+    ell_next: int = 0
 
 
 def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gamma=10.0,
-             c1=1e-4, rho=0.5, max_trials=30, return_parts=False):
-    """One Nystrom-preconditioned matrix-free NGD step (Alg. 1 + Alg. 3 + Alg. 4, fixed ell).
+             c1=1e-4, rho=0.5, max_trials=30, return_parts=False, mu_loss_coef=0.0, ell_max=0, ell_delta=20):
+    """One Nystrom-preconditioned matrix-free NGD step (Alg. 1 + Alg. 3 + Alg. 4).
 
-    mu=None selects mu = gamma eps lambda_hat_1 (Alg. 4).  maxit caps pCG; rtol=0
-    runs exactly maxit iterations (for comparisons at a fixed iteration count).
+    mu=None selects mu = gamma eps lambda_hat_1 (Alg. 4), raised to mu_loss_coef L(theta)^2 when
+    mu_loss_coef > 0 (the damping of Sec. 5).  maxit caps pCG; rtol=0 runs exactly maxit
+    iterations (for comparisons at a fixed iteration count).  ell_max > 0 applies the rank rule
+    of Alg. 4 to the returned info.ell_next (otherwise ell_next = ell).
     """
-    g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1, line 2
+    g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1: gradient
     J = _mlp.jacobian(problem, theta)                              # 'precompute Jacobian only'
     w = problem.w
 
@@ -109,7 +112,7 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
         return J.T @ (w[:, None] * (J @ V)) if V.ndim == 2 else _gram.gramian_mv(J, w, V)
 
     Omega_raw = _philox.gaussian_test_matrix(J.shape[1], ell, seed, step)
-    Omega = _nys.thin_qr(Omega_raw)                                # Alg. 4, line 1 (App. A)
+    Omega = _nys.thin_qr(Omega_raw)                                # Alg. 4: randomized Nystrom (App. A)
     Y = G_apply(Omega)
     for scale in SHIFT_SCALES:          # a non-positive-definite core is retried with a larger shift
         try:
@@ -118,7 +121,12 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
         except np.linalg.LinAlgError:
             if scale == SHIFT_SCALES[-1]:
                 raise
-    mu_eff = float(mu) if mu is not None else _nys.mu_from_lambda1(lam[0], gamma)  # Alg. 4, line 2
+    if mu is not None:
+        mu_eff = float(mu)
+    elif mu_loss_coef > 0.0:
+        mu_eff = _nys.mu_adaptive(lam[0], L0, gamma, mu_loss_coef)  # Sec. 5 damping
+    else:
+        mu_eff = _nys.mu_from_lambda1(lam[0], gamma)                 # Alg. 4: damping
 
     def A(v):
         return _gram.gramian_mv(J, w, v, mu_eff)
@@ -126,14 +134,37 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
     def Pinv(v):
         return _nys.precond_apply(U, lam, mu_eff, v)
 
-    d, iters, relres = pcg(A, g, Pinv, rtol, maxit)                # Alg. 3, line 3
+    d, iters, relres = pcg(A, g, Pinv, rtol, maxit)                # Alg. 3: direction by pCG
 
     def loss_fn(th):
         return _mlp.residual(problem, th)[1]
 
-    alpha, L1, trials = armijo(loss_fn, theta, d, g, L0, c1, rho, max_trials)   # Alg. 1, line 4
-    info = StepInfo(L0, L1, alpha, mu_eff, float(lam[0]), float(lam[-1]), nu, iters, relres, trials)
-    theta_new = theta - alpha * d                                   # Alg. 1, line 5
+    alpha, L1, trials = armijo(loss_fn, theta, d, g, L0, c1, rho, max_trials)   # Alg. 1: line search
+    ell_next = _nys.next_rank(lam, mu_eff, ell, ell_max, ell_delta) if ell_max > 0 else ell   # Alg. 4
+    info = StepInfo(L0, L1, alpha, mu_eff, float(lam[0]), float(lam[-1]), nu, iters, relres, trials, ell_next)
+    theta_new = theta - alpha * d                                   # Alg. 1: update
     if return_parts:
         return theta_new, info, dict(g=g, r=r, J=J, Omega=Omega, Y=Y, U=U, lam=lam, d=d)
     return theta_new, info
+
+
+def nystrom_ngd(problem, theta0, steps, ell0, ell_max, ell_delta=20, rtol=1e-6, maxit=20, seed=0,
+                gamma=10.0, mu_loss_coef=1e-4, mant_bits=52, pcg_iters=None):
+    """NystromNGD over several steps (Alg. 1 with Alg. 3 and Alg. 4): adaptive damping and rank.
+
+    Step k draws its test matrix from the Philox counter (seed, k) with rank ell_k, and
+    ell_{k+1} = info.ell_next.  pcg_iters (a list) replays fixed iteration counts (rtol 0)
+    instead of the rtol stop, for comparisons at equal iteration counts.
+    Returns (theta, [StepInfo per step], [ell per step]).
+    """
+    theta = np.asarray(theta0, dtype=np.float64).copy()
+    ell = int(ell0)
+    infos, ells = [], []
+    for k in range(steps):
+        it_rtol, it_max = (0.0, int(pcg_iters[k])) if pcg_iters is not None else (rtol, maxit)
+        theta, info = ngd_step(problem, theta, ell, None, it_rtol, it_max, seed, k, mant_bits=mant_bits,
+                               gamma=gamma, mu_loss_coef=mu_loss_coef, ell_max=ell_max, ell_delta=ell_delta)
+        infos.append(info)
+        ells.append(ell)
+        ell = info.ell_next
+    return theta, infos, ells

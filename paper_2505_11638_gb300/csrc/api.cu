@@ -364,7 +364,7 @@ ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* 
 
 // ------------------------------------------------------------------ sketch and factor (internal buffers, ld = ldP)
 // Explicit mantissa bits of the format the sketch Y is computed in: nu = eps(||Y||_F) in that
-// format (App. A step 4, read as MATLAB's eps of the sketch's precision).
+// format (the shift of App. A, read as MATLAB's eps of the sketch's precision).
 int mantissa_bits(int prec) {
   switch (prec) {
     case NGD_SKETCH_TF32: return 10;
@@ -719,13 +719,13 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   PhaseRange phase;
   phase.next("linearize");
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-  // Alg. 1 line 2: gradient at theta (and the linearization the matvecs use)
+  // Alg. 1, gradient: at theta (and the linearization the matvecs use)
   TRY(linearize<T>(ctx, theta));
   launch_mul(ctx->ps.w, ctx->r, ctx->svec, ctx->N, ctx->stream);
   TRY(vjp_current<T>(ctx, ctx->svec, ctx->g, true));
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
   phase.next("sketch");
-  // Alg. 4 line 1: randomized Nystrom (App. A), fresh Omega from (seed, step)
+  // Alg. 4, randomized Nystrom (App. A): fresh Omega from (seed, step)
   TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch));
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
   phase.next("factor");
@@ -740,9 +740,9 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   if (fs != NGD_OK) return fs;
   CK(cudaEventRecord(ctx->ev[3], ctx->stream));
   phase.next("pcg");
-  // Alg. 4 line 2: mu (fixed, or gamma eps lambda_1)
-  launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSMu, ctx->stream);
-  // Alg. 3 line 3: pCG on (G + mu I) d = g with the Nystrom preconditioner of Alg. 4
+  // Alg. 4, damping: mu fixed, gamma eps lambda_1, or the Sec. 5 maximum with c L^2
+  launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, ctx->stream);
+  // Alg. 3, direction: pCG on (G + mu I) d = g with the Nystrom preconditioner of Alg. 4
   int iters = 0;
   double relres = 0.0;
   const bool u_f64 = !std::is_same<T, float>::value || o->sketch == NGD_SKETCH_F64;
@@ -751,17 +751,30 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
                       ctx->d, &iters, &relres));
   CK(cudaEventRecord(ctx->ev[4], ctx->stream));
   phase.next("linesearch");
-  // Alg. 1 line 4: Armijo backtracking along theta - alpha d
+  // Alg. 1, line search: Armijo backtracking along theta - alpha d
   launch_dot(ctx->g, ctx->d, p, ctx->part, ctx->scal + kSDot, ctx->stream);
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   const double L0 = ctx->h_scal[kSLoss], slope = ctx->h_scal[kSDot], mu = ctx->h_scal[kSMu], nu = ctx->h_scal[kSNu];
-  double lam_h[2] = {0, 0};
-  CK(cudaMemcpyAsync(ctx->h_scal + 6, ctx->lam, 8, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->h_scal + 7, ctx->lam + (o->ell - 1), 8, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> lam_all((size_t)o->ell);
+  CK(cudaMemcpyAsync(lam_all.data(), ctx->lam, (size_t)o->ell * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  lam_h[0] = ctx->h_scal[6];
-  lam_h[1] = ctx->h_scal[7];
+  const double lam_h[2] = {lam_all[0], lam_all[(size_t)o->ell - 1]};
+  // Alg. 4: rank of the next step's sketch
+  int ell_next = o->ell;
+  if (o->ell_max > 0) {
+    if (lam_h[1] > 10.0 * mu) {
+      ell_next = std::min(o->ell + o->ell_delta, o->ell_max);
+    } else {
+      int first = -1;                      // first 0-based index with lambda_hat < 10 mu
+      for (int i = 0; i < o->ell; ++i)
+        if (lam_all[(size_t)i] < 10.0 * mu) {
+          first = i;
+          break;
+        }
+      ell_next = first < 0 ? o->ell : std::min(first + 2, o->ell_max);
+    }
+  }
   double alpha = 1.0, L1 = L0;
   int trials = 0;
   bool accepted = false;
@@ -778,7 +791,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
     alpha *= o->armijo_rho;
   }
   if (!accepted) alpha = 0.0;
-  // Alg. 1 line 5
+  // Alg. 1, update
   if (alpha != 0.0) launch_axpy_to(theta, ctx->d, alpha, theta, p, ctx->stream);
   CK(cudaEventRecord(ctx->ev[5], ctx->stream));
   CK(cudaEventSynchronize(ctx->ev[5]));
@@ -801,6 +814,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   inf.ms_factor = ev_ms(ctx, 2, 3);
   inf.ms_pcg = ev_ms(ctx, 3, 4);
   inf.ms_linesearch = ev_ms(ctx, 4, 5);
+  inf.ell_next = ell_next;
   if (info) *info = inf;
   return check_launch(ctx);
 }
@@ -823,6 +837,9 @@ void ngd_default_step_opts(ngd_step_opts* o) {
   o->armijo_c1 = 1e-4;
   o->armijo_rho = 0.5;
   o->armijo_max = 30;
+  o->mu_loss_coef = 0.0;
+  o->ell_max = 0;
+  o->ell_delta = 20;
 }
 
 ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
@@ -1019,6 +1036,22 @@ ngd_status ngd_residual(ngd_ctx* ctx, const double* theta, double* r, double* lo
   });
 }
 
+ngd_status ngd_eval(ngd_ctx* ctx, const double* theta, double* out) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!theta || !out) return set_err(ctx, NGD_ERR_INVALID_ARG, "theta/out is NULL%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    TRY(prep_theta<T>(ctx, theta));
+    const int nb = launch_forward<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, ctx->r, ctx->lpart, nullptr,
+                                     0, ctx->stream, out);
+    if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the forward kernel%s");
+    launch_sum_partials(ctx->lpart, nb, 0.5, ctx->scal + kSLoss, ctx->stream);
+    ctx->tape_valid = false;
+    ctx->lin_valid = !ctx->stored_j;
+    return check_launch(ctx);
+  });
+}
+
 ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* out) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!v || !out) return set_err(ctx, NGD_ERR_INVALID_ARG, "v/out is NULL%s");
@@ -1179,7 +1212,9 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!theta || !o) return set_err(ctx, NGD_ERR_INVALID_ARG, "theta/opts NULL%s");
   if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
-      !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1)
+      !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1 ||
+      !(o->mu_loss_coef >= 0.0) || o->ell_max < 0 || o->ell_max > std::min<int64_t>(ctx->p, 2048) ||
+      o->ell_delta < 0)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
   if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");

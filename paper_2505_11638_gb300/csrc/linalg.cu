@@ -1518,11 +1518,17 @@ void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* 
 }
 
 // mu = gamma * eps64 * lam[0] (Alg. 4), or the fixed value when fixed_mu > 0
-__global__ void k_set_mu(const double* __restrict__ lam, double fixed_mu, double gamma, double* __restrict__ mu) {
-  *mu = fixed_mu > 0.0 ? fixed_mu : gamma * 0x1p-52 * lam[0];
+// mu: the fixed value if positive, else gamma eps64 lambda_hat_1 (Alg. 4), raised to c L^2 when the
+// adaptive damping of Sec. 5 is on (c > 0; loss = L(theta) on the device)
+__global__ void k_set_mu(const double* __restrict__ lam, double fixed_mu, double gamma, const double* __restrict__ loss,
+                         double c, double* __restrict__ mu) {
+  double m = fixed_mu > 0.0 ? fixed_mu : gamma * 0x1p-52 * lam[0];
+  if (!(fixed_mu > 0.0) && c > 0.0) m = fmax(m, c * (*loss) * (*loss));
+  *mu = m;
 }
-void launch_set_mu(const double* lam, double fixed_mu, double gamma, double* mu, cudaStream_t s) {
-  k_set_mu<<<1, 1, 0, s>>>(lam, fixed_mu, gamma, mu); note_launch();
+void launch_set_mu(const double* lam, double fixed_mu, double gamma, const double* loss, double c, double* mu,
+                   cudaStream_t s) {
+  k_set_mu<<<1, 1, 0, s>>>(lam, fixed_mu, gamma, loss, c, mu); note_launch();
 }
 
 }  // namespace ngd

@@ -108,7 +108,8 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
                            cudaStream_t s);
 void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* lam, double* inv_sigma,
                            cudaStream_t s);
-void launch_set_mu(const double* lam, double fixed_mu, double gamma, double* mu, cudaStream_t s);
+void launch_set_mu(const double* lam, double fixed_mu, double gamma, const double* loss, double c, double* mu,
+                   cudaStream_t s);
 
 // Whole preconditioned CG for an FP32 stored Jacobian in one cooperative kernel (pcg_fused.cu).
 struct FusedPcgArgs {

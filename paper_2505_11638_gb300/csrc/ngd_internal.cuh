@@ -66,8 +66,10 @@ size_t jvp_smem_per_point(const NetDesc& net, size_t elt);
 // Residuals r (nullable) and per-block loss partials for rows [row0, row0+nrows).
 // tape (nullable): store the Taylor coefficients (t, grad a, Delta a per hidden layer).
 template <typename T>
+// chan (nullable): the C = d + 2 output channels (u, grad u, Delta u) of each point as float64,
+// chan[row * C + c].
 int launch_forward(const NetDesc& net, const PointSet& ps, const T* prep, int64_t row0, int64_t nrows,
-                   double* r, double* loss_part, T* tape, int tp, cudaStream_t s);
+                   double* r, double* loss_part, T* tape, int tp, cudaStream_t s, double* chan = nullptr);
 
 // Jacobian rows J[row - row0, :] (row stride ldJ) for rows [row0, row0+nrows), plus r and
 // loss partials (when not from_tape).  tape_in non-null: reverse pass from stored coefficients.

@@ -215,7 +215,7 @@ __device__ __forceinline__ void residual_and_loss(const NetDesc& net, const Poin
 template <typename T, int MAXC, int PP>
 __global__ void __launch_bounds__(kThreads) k_forward(NetDesc net, PointSet ps, const T* __restrict__ prep,
                                                        int64_t row0, int64_t nrows, int TP, double* r_out,
-                                                       double* loss_part, T* tape_g) {
+                                                       double* loss_part, T* tape_g, double* chan_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -237,6 +237,9 @@ __global__ void __launch_bounds__(kThreads) k_forward(NetDesc net, PointSet ps, 
   }
   fwd_output<T, MAXC>(net, prep, bufA, pstride, maxw, npts, outc);
   __syncthreads();
+  if (chan_out) {                        // u, grad u, Delta u of each point, as float64
+    for (int e = threadIdx.x; e < npts * C; e += blockDim.x) chan_out[trow0 * C + e] = (double)outc[e];
+  }
   residual_and_loss<T>(net, ps, trow0, npts, outc, r_out, loss_part, red);
 }
 
@@ -598,7 +601,7 @@ static void set_smem(Kern k, size_t bytes) {
 
 template <typename T, int MAXC>
 static int fwd_dispatch(const NetDesc& net, const PointSet& ps, const T* prep, int64_t row0, int64_t nrows,
-                        double* r, double* loss_part, T* tape, int tp_req, cudaStream_t s) {
+                        double* r, double* loss_part, T* tape, int tp_req, cudaStream_t s, double* chan) {
   constexpr int PP = fwd_pp<MAXC>();
   const size_t ppb = fwd_smem_per_point(net, sizeof(T));
   const int tp = pick_tp(ppb, PP, tp_req);
@@ -607,23 +610,23 @@ static int fwd_dispatch(const NetDesc& net, const PointSet& ps, const T* prep, i
   auto k = k_forward<T, MAXC, PP>;
   set_smem(k, smem);
   const int blocks = (int)((nrows + tp - 1) / tp);
-  k<<<blocks, kThreads, smem, s>>>(net, ps, prep, row0, nrows, tp, r, loss_part, tape); note_launch();
+  k<<<blocks, kThreads, smem, s>>>(net, ps, prep, row0, nrows, tp, r, loss_part, tape, chan); note_launch();
   return blocks;
 }
 
 template <typename T>
 int launch_forward(const NetDesc& net, const PointSet& ps, const T* prep, int64_t row0, int64_t nrows, double* r,
-                   double* loss_part, T* tape, int tp, cudaStream_t s) {
+                   double* loss_part, T* tape, int tp, cudaStream_t s, double* chan) {
   if (nrows <= 0) return 0;
-  if (net.C <= 4) return fwd_dispatch<T, 4>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s);
-  if (net.C <= 8) return fwd_dispatch<T, 8>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s);
-  if (net.C <= 12) return fwd_dispatch<T, 12>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s);
-  return fwd_dispatch<T, 18>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s);
+  if (net.C <= 4) return fwd_dispatch<T, 4>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s, chan);
+  if (net.C <= 8) return fwd_dispatch<T, 8>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s, chan);
+  if (net.C <= 12) return fwd_dispatch<T, 12>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s, chan);
+  return fwd_dispatch<T, 18>(net, ps, prep, row0, nrows, r, loss_part, tape, tp, s, chan);
 }
 template int launch_forward<float>(const NetDesc&, const PointSet&, const float*, int64_t, int64_t, double*, double*,
-                                   float*, int, cudaStream_t);
+                                   float*, int, cudaStream_t, double*);
 template int launch_forward<double>(const NetDesc&, const PointSet&, const double*, int64_t, int64_t, double*,
-                                    double*, double*, int, cudaStream_t);
+                                    double*, double*, int, cudaStream_t, double*);
 
 template <typename T, int MAXC>
 static int jac_dispatch(const NetDesc& net, const PointSet& ps, const T* prep, int64_t row0, int64_t nrows, T* J,

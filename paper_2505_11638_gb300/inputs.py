@@ -21,6 +21,9 @@ and kept fixed for the run, Sec. 5 "Discretization and sampling strategies"):
 * ``batch64``     64 independent Poisson problems on [0,1]^3 with
                    u*_j = prod sin(k_j pi x_i), k_j in {1..4}, MLP 3-64x3-1,
                    N_int,j uniform in [1000, 8000], N_bnd,j = floor(N_int,j / 4).
+* ``poisson3d``   [0,1]^3, u* = prod sin(pi x_i), MLP 3-64-64-64-1 (p = 8641), 10000 interior +
+                   1000 boundary points: the paper's 3-D Poisson PINN, trained by NystromNGD
+                   (adaptive rank from 20 up to 500, adaptive damping, pCG capped at 20 iterations).
 
 Layout conventions (shared with the C ABI):
   X       (N, d) float64, row-major, interior rows first, then boundary rows.
@@ -166,13 +169,32 @@ def u_star(problem: Problem, x: np.ndarray) -> np.ndarray:
     return np.exp(-3.0 * problem.kappa * math.pi ** 2 * x[:, 0]) * _sin_product(x[:, 1:], 1.0)
 
 
+def grad_u_star(problem: Problem, x: np.ndarray) -> np.ndarray:
+    """First derivatives (n, d) of the manufactured solution of ``problem`` at points x (n, d)."""
+    if problem.pde == POISSON:
+        k = problem.freq * math.pi
+        s, c = np.sin(k * x), np.cos(k * x)
+        out = np.empty_like(x)
+        for i in range(x.shape[1]):
+            out[:, i] = k * c[:, i] * np.prod(np.delete(s, i, axis=1), axis=1)
+        return out
+    kappa = problem.kappa
+    e = np.exp(-3.0 * kappa * math.pi ** 2 * x[:, 0])
+    s, c = np.sin(math.pi * x[:, 1:]), np.cos(math.pi * x[:, 1:])
+    out = np.empty_like(x)
+    out[:, 0] = -3.0 * kappa * math.pi ** 2 * e * np.prod(s, axis=1)
+    for i in range(3):
+        out[:, 1 + i] = math.pi * e * c[:, i] * np.prod(np.delete(s, i, axis=1), axis=1)
+    return out
+
+
 def eval_points(problem: Problem, n_eval: int, seed: int) -> np.ndarray:
     """Independent interior points for error evaluation (10x the training set in the paper)."""
     rng = np.random.default_rng(seed + 7919)
     return rng.uniform(0.0, 1.0, size=(n_eval, problem.d))
 
 
-WORKLOADS = ("poisson2d", "poisson5d", "poisson10d", "heat4d", "batch64")
+WORKLOADS = ("poisson2d", "poisson5d", "poisson10d", "heat4d", "batch64", "poisson3d")
 
 
 def make_workload(name: str, seed: int = 0) -> tuple[Workload, list[np.ndarray]]:
@@ -207,6 +229,12 @@ def make_workload(name: str, seed: int = 0) -> tuple[Workload, list[np.ndarray]]
             k = int(rng.integers(1, 5))
             probs.append(poisson_problem(f"{name}[{j}]", 3, widths, n_int, n_int // 4, rng, freq=float(k)))
         wl = Workload(name, probs, "f32", ell=200, mu=None, rtol=1e-6, steps=1, sketch="f64")
+    elif name == "poisson3d":
+        # the paper's 3-D Poisson PINN (MLP 3-64-64-64-1, 10k interior + 1k boundary points),
+        # trained by NystromNGD: adaptive rank up to 500 in steps of 20, pCG capped at 20 iterations
+        widths = [3, 64, 64, 64, 1]
+        prob = poisson_problem(name, 3, widths, 10000, 1000, rng)
+        wl = Workload(name, [prob], "f32", ell=20, mu=None, rtol=1e-10, steps=200, sketch="f64")
     else:  # pragma: no cover
         raise KeyError(name)
     thetas = [glorot_theta(pr.widths, rng) for pr in wl.problems]

@@ -49,7 +49,8 @@ class StepOpts(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("mu", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("sketch", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64), ("armijo_c1", ctypes.c_double),
-                ("armijo_rho", ctypes.c_double), ("armijo_max", ctypes.c_int)]
+                ("armijo_rho", ctypes.c_double), ("armijo_max", ctypes.c_int), ("mu_loss_coef", ctypes.c_double),
+                ("ell_max", ctypes.c_int), ("ell_delta", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -58,7 +59,7 @@ class StepInfo(ctypes.Structure):
                 ("nu", ctypes.c_double), ("relres", ctypes.c_double), ("pcg_iters", ctypes.c_int),
                 ("armijo_trials", ctypes.c_int), ("shift_retries", ctypes.c_int), ("status", ctypes.c_int),
                 ("ms_linearize", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_factor", ctypes.c_double),
-                ("ms_pcg", ctypes.c_double), ("ms_linesearch", ctypes.c_double)]
+                ("ms_pcg", ctypes.c_double), ("ms_linesearch", ctypes.c_double), ("ell_next", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +79,7 @@ _SIGS = {
     "ngd_num_points": ([_P], ctypes.c_int64),
     "ngd_set_stream": ([_P, _P], _I),
     "ngd_residual": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
+    "ngd_eval": ([_P, _P, _P], _I),
     "ngd_jvp": ([_P, _P, _P, _P], _I),
     "ngd_vjp": ([_P, _P, _P, _P], _I),
     "ngd_gradient": ([_P, _P, _P, _P, ctypes.POINTER(_D)], _I),
@@ -152,6 +154,11 @@ def ngd_residual(h, theta, r, want_loss=True):
     loss = ctypes.c_double(0.0)
     _check(h, lib().ngd_residual(h, _ptr(theta), _ptr(r), ctypes.byref(loss) if want_loss else None))
     return loss.value if want_loss else None
+
+
+def ngd_eval(h, theta, out):
+    lib().ngd_set_stream(h, _stream())
+    _check(h, lib().ngd_eval(h, _ptr(theta), _ptr(out)))
 
 
 def ngd_jvp(h, theta, v, out):
@@ -270,6 +277,14 @@ class Context:
         loss = ngd_residual(self.handle, theta, r)
         self.version += 1
         return r, loss
+
+    def eval(self, theta):
+        """(N, d + 2) float64: u, grad u (d) and Delta u of the network at the context's points."""
+        _need(theta, torch.float64, self.p, "theta")
+        out = torch.empty(self.N, self.problem.widths[0] + 2, dtype=torch.float64, device=self.device)
+        ngd_eval(self.handle, theta, out)
+        self.version += 1
+        return out
 
     def jvp(self, theta, v):
         _need(v, torch.float64, self.p, "v")

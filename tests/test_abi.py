@@ -64,3 +64,43 @@ def test_create_rejects_bad_descriptions_before_touching_the_gpu(lib):
         d = ngd.ProblemDesc(**kw)
         assert ngd.lib().ngd_create(ctypes.byref(d), ctypes.byref(h)) == 1, bad
     assert ngd.lib().ngd_last_error(None) == b"null context"
+
+
+def _c_layout(struct: str, fields):
+    """sizeof and offsetof of a struct of include/ngd.h, from a C program compiled with gcc."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    body = "\n".join(f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"ngd.h\"\n"
+           f"int main(void) {{\n  printf(\"%zu\\n\", sizeof({struct}));\n{body}\n  return 0;\n}}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("cname,pyname", [("ngd_step_opts", "StepOpts"), ("ngd_step_info", "StepInfo"),
+                                          ("ngd_problem_desc", "ProblemDesc")])
+def test_binding_structs_match_the_header_layout(cname, pyname):
+    from paper_2505_11638_gb300 import ngd
+
+    cls = getattr(ngd, pyname)
+    fields = [f for f, _ in cls._fields_]
+    size, offsets = _c_layout(cname, fields)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offsets
+
+
+def test_default_step_opts_fill_the_adaptive_fields(lib):
+    from paper_2505_11638_gb300 import ngd
+
+    o = ngd.ngd_default_step_opts()
+    assert o.mu_loss_coef == 0.0 and o.ell_max == 0 and o.ell_delta == 20

@@ -455,3 +455,71 @@ def test_nonfinite_and_invalid(ngd):
         ctx.pcg_solve(None, g, 1e-3, None, None, 0, rtol=1e-8, maxit=10)
     assert e.value.name == "NONFINITE"
     ctx.close()
+
+
+@pytest.mark.parametrize("case", [0, 3, 4])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_eval_channels_match_oracle_forward(ngd, case, dtype):
+    """ngd_eval: u, grad u and Delta u at the context's points against the oracle's hand-derived
+    forward Laplacian (FP64 path 1e-11, FP32 path 2e-5)."""
+    pr, th = small(SMALL[case], seed=60 + case)
+    ctx = ngd.Context(pr, dtype=dtype)
+    out = host(ctx.eval(dev(th)))
+    u, gu, lu, _ = mlp.taylor_forward(th, pr.widths, pr.X, mlp.spatial_mask(pr.pde, pr.d))
+    ref = np.concatenate([u[:, None], gu, lu[:, None]], axis=1)
+    tol = 1e-11 if dtype == "f64" else 2e-5
+    assert out.shape == ref.shape
+    for c in range(ref.shape[1]):
+        assert rel(out[:, c], ref[:, c]) <= tol, c
+    ctx.close()
+
+
+def _guarded_rank(lam, mu, ell, ell_max, delta, band=1e-6):
+    """Alg. 4's rank from the oracle's spectrum, or None when an eigenvalue lies within `band`
+    (relative) of 10 mu, where the two sides' last bits may legitimately decide differently."""
+    lam = np.asarray(lam)
+    if np.any(np.abs(lam - 10.0 * mu) <= band * 10.0 * mu):
+        return None
+    return nystrom.next_rank(lam, mu, ell, ell_max, delta)
+
+
+def test_step_adaptive_damping_and_rank_match_oracle(ngd):
+    """One step with the damping of Sec. 5 (mu = max(gamma eps lambda_1, 1e-4 L^2)) and Alg. 4's
+    rank update: mu, ell_next and the update agree with the oracle step (same Omega stream, same
+    PCG iteration count)."""
+    pr, th = small(SMALL[0], seed=71)
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    ell, ell_max, delta = 12, 30, 6
+    info = ctx.step(t, ell=ell, mu=None, mu_loss_coef=1e-4, ell_max=ell_max, ell_delta=delta, rtol=1e-10,
+                    maxit=500, seed=5, step=2, sketch="f64")
+    th1_o, info_o, parts = solve.ngd_step(pr, th, ell=ell, mu=None, rtol=0.0, maxit=info["pcg_iters"], seed=5, step=2,
+                                          mu_loss_coef=1e-4, ell_max=ell_max, ell_delta=delta, return_parts=True)
+    assert info["mu"] == pytest.approx(max(10 * 2.0 ** -52 * info["lam1"], 1e-4 * info["loss_before"] ** 2), rel=1e-14)
+    assert info["mu"] == pytest.approx(info_o.mu, rel=1e-10)
+    want = _guarded_rank(parts["lam"], info_o.mu, ell, ell_max, delta)
+    if want is not None:
+        assert info["ell_next"] == want == info_o.ell_next
+    assert rel(host(t) - th, th1_o - th) <= 1e-6
+    ctx.close()
+
+
+def test_nystrom_ngd_run_matches_oracle(ngd):
+    """Four NystromNGD steps (adaptive damping and rank, Alg. 4 with Sec. 5) from the same theta:
+    the GPU's rank sequence is the oracle's, and the parameters after the run agree (the oracle
+    replays the GPU's PCG iteration counts)."""
+    pr, th = small(SMALL[1], seed=72)
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    ell, ells, iters = 6, [], []
+    for k in range(4):
+        ells.append(ell)
+        info = ctx.step(t, ell=ell, mu=None, mu_loss_coef=1e-4, ell_max=24, ell_delta=6, rtol=1e-10, maxit=500,
+                        seed=9, step=k, sketch="f64")
+        iters.append(info["pcg_iters"])
+        ell = info["ell_next"]
+    th_o, infos_o, ells_o = solve.nystrom_ngd(pr, th, steps=4, ell0=6, ell_max=24, ell_delta=6, seed=9,
+                                              mu_loss_coef=1e-4, pcg_iters=iters)
+    assert ells == ells_o
+    assert rel(host(t) - th, th_o - th) <= 1e-6
+    ctx.close()

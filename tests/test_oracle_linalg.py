@@ -264,3 +264,49 @@ def test_ngd_step_decreases_loss_and_matches_direct():
     # the heuristic mu of Alg. 4
     _, info2 = solve.ngd_step(pr, theta, ell=30, mu=None, rtol=1e-8, maxit=100, seed=5, step=0)
     assert info2.mu == pytest.approx(10 * 2.0 ** -52 * info2.lam1)
+
+
+# ---------------------------------------------------------------------------- NystromNGD control (Alg. 4, Sec. 5)
+def test_next_rank_rule_on_constructed_spectra():
+    """Alg. 4's rank update, worked by hand on spectra whose crossing of 10 mu is placed."""
+    mu = 0.01                                            # 10 mu = 0.1
+    # lambda_hat_ell above 10 mu: grow by delta, capped by ell_max
+    assert nystrom.next_rank([10.0, 5.0, 2.0, 1.0], mu, 4, 30, 20) == 24
+    assert nystrom.next_rank([10.0, 5.0, 2.0, 1.0], mu, 4, 10, 20) == 10
+    assert nystrom.next_rank([10.0, 5.0, 2.0, 1.0], mu, 4, 4, 20) == 4
+    # decay reached: one past the first (1-based) index below 10 mu
+    assert nystrom.next_rank([10.0, 5.0, 0.05, 0.01], mu, 4, 30, 20) == 4      # i = 3
+    assert nystrom.next_rank([10.0, 0.05, 0.01, 0.0], mu, 4, 30, 20) == 3      # i = 2
+    assert nystrom.next_rank([0.09, 0.05, 0.01, 0.0], mu, 4, 30, 20) == 2      # i = 1
+    lam = np.concatenate([np.full(7, 3.0), np.full(3, 1e-9)])
+    assert nystrom.next_rank(lam, mu, 10, 30, 20) == 9                         # i = 8
+    assert nystrom.next_rank(lam, mu, 10, 5, 20) == 5                          # capped
+    # lambda_hat_ell exactly 10 mu: no index is below it, the rank stays (reading)
+    assert nystrom.next_rank([1.0, 0.5, 0.1], mu, 3, 30, 20) == 3
+    # 0.1 is not below 10 mu, 0.0999 is
+    assert nystrom.next_rank([1.0, 0.1, 0.0999], mu, 3, 30, 20) == 4
+
+
+def test_adaptive_damping_is_the_larger_of_the_two_rules():
+    eps = 2.0 ** -52
+    assert nystrom.mu_adaptive(1e3, 1e-6, gamma=10.0, coef=1e-4) == 10.0 * eps * 1e3   # late: Alg. 4 value
+    assert nystrom.mu_adaptive(1e3, 2.0, gamma=10.0, coef=1e-4) == 4e-4                # early: 1e-4 L^2
+    assert nystrom.mu_adaptive(0.0, 0.0) == 0.0
+
+
+def test_nystrom_ngd_grows_the_rank_then_caps_it_and_decreases_the_loss():
+    pr, th = inputs.small_problem(d=2, widths=[2, 6, 5, 1], n_int=30, n_bnd=10, seed=3)
+    theta, infos, ells = solve.nystrom_ngd(pr, th, steps=5, ell0=4, ell_max=14, ell_delta=4, rtol=1e-10,
+                                           maxit=400, seed=1, mu_loss_coef=1e-4)
+    for k, info in enumerate(infos):
+        expect_grow = info.lam_ell > 10.0 * info.mu
+        if expect_grow:
+            assert info.ell_next == min(ells[k] + 4, 14)
+        else:
+            assert info.ell_next <= ells[k] + 1
+        assert info.mu >= 1e-4 * info.loss_before ** 2 * (1 - 1e-15)
+        assert info.loss_after <= info.loss_before
+        if k + 1 < len(ells):
+            assert ells[k + 1] == info.ell_next
+    assert ells[0] == 4 and max(ells) <= 14
+    assert infos[-1].loss_after < infos[0].loss_before

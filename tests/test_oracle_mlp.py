@@ -173,3 +173,18 @@ def test_theta_layout_row_major():
     (W1, b1), (W2, b2) = mlp.unpack(theta, widths)
     assert W1[1, 0] == 2 and W1[2, 1] == 5 and b1.tolist() == [6, 7, 8]
     assert W2.tolist() == [[9, 10, 11]] and b2.tolist() == [12]
+
+
+@pytest.mark.parametrize("name", ["poisson3d", "heat4d"])
+def test_grad_u_star_matches_central_differences(name):
+    """The manufactured solution's gradient (used for H1 errors) against central differences."""
+    wl, _ = inputs.make_workload(name, seed=0)
+    pr = wl.problems[0]
+    x = inputs.eval_points(pr, 64, seed=1)
+    g = inputs.grad_u_star(pr, x)
+    h = 1e-6
+    for i in range(pr.d):
+        e = np.zeros(pr.d)
+        e[i] = h
+        fd = (inputs.u_star(pr, x + e) - inputs.u_star(pr, x - e)) / (2 * h)
+        np.testing.assert_allclose(g[:, i], fd, rtol=1e-7, atol=1e-8)
