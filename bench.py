@@ -476,7 +476,8 @@ def run_train(args, rank):
     """NystromNGD training run on the paper's 3-D Poisson PINN (poisson3d: MLP 3-64-64-64-1,
     p = 8641, 10000 + 1000 points): Alg. 1 with Alg. 3 and Alg. 4, adaptive rank from 20 up to
     500 in steps of 20, damping max(gamma eps lambda_hat_1, 1e-4 L^2), pCG capped at 20
-    iterations (the paper's settings for its NGD runs).  Reports NGD steps/s over the run (CUDA
+    iterations (the paper's settings for its NGD runs); --test-matrix picks the Gaussian or the
+    sampling test matrix.  Reports NGD steps/s over the run (CUDA
     events around every step), the rank trajectory, and the relative L2 and H1 errors of u_theta
     against u* on 10x the training points (independent, interior), every 10 steps."""
     import torch
@@ -505,7 +506,7 @@ def run_train(args, rank):
 
     theta = torch.tensor(thetas[0], device="cuda")
     opts = dict(mu=None, mu_loss_coef=1e-4, ell_max=500, ell_delta=20, rtol=wl.rtol, maxit=20, sketch=args.sketch,
-                seed=0)
+                seed=0, test_matrix=args.test_matrix)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
     ell, total_ms, log, ells = wl.ell, 0.0, [], []
@@ -528,7 +529,7 @@ def run_train(args, rank):
             "steps": args.train_steps, "ms_per_step": total_ms / args.train_steps, "data": "synthetic",
             "config": {"workload": "poisson3d", "N": pr.n, "p": pr.p, "ell0": wl.ell, "ell_max": 500,
                        "ell_delta": 20, "mu": "max(10 eps lambda_1, 1e-4 L^2)", "pcg_maxit": 20,
-                       "sketch": args.sketch, "eval_points": len(xe)},
+                       "sketch": args.sketch, "test_matrix": args.test_matrix, "eval_points": len(xe)},
             "final": log[-1], "ell_trajectory": ells, "log": log}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -550,6 +551,9 @@ def main():
                     help="a NystromNGD training run (adaptive rank and damping) on the 3-D Poisson PINN, "
                          "--train-steps NGD steps, with L2/H1 errors every 10 steps")
     ap.add_argument("--train-steps", type=int, default=200)
+    ap.add_argument("--test-matrix", default="gaussian", choices=["gaussian", "sampling"],
+                    help="test matrix of the Nystrom sketch in --train (sampling: columns drawn proportionally "
+                         "to diag G)")
     ap.add_argument("--precision-study", action="store_true",
                     help="the precision form on poisson10d: all-FP64 GPU path vs FP64-accurate (double-float) "
                          "vs TF32 / BF16 tensor-core sketches, --steps NGD steps each")

@@ -93,6 +93,13 @@ typedef struct {
   void* stream;           /* cudaStream_t the context enqueues on (NULL: legacy default stream) */
 } ngd_problem_desc;
 
+/* Test matrix of the randomized Nystrom approximation (Sec. 3, Eq. nystrom_approx):
+ * NGD_TEST_GAUSSIAN    standard normal entries (Philox, see ngd_nystrom_sketch), thin QR;
+ * NGD_TEST_SAMPLING    ell distinct columns of the identity, drawn one after another with
+ *                      probabilities proportional to diag G among those not yet drawn
+ *                      ("NystromNGD Sampling", Sec. 5), see ngd_nystrom_sketch_sampled. */
+typedef enum { NGD_TEST_GAUSSIAN = 0, NGD_TEST_SAMPLING = 1 } ngd_test_matrix;
+
 typedef struct {
   int ell;                /* Nystrom rank (sketch size), 1 <= ell <= min(p, 2048) */
   double mu;              /* damping; mu <= 0 selects mu = gamma eps lambda_hat_1 (Alg. 4) */
@@ -111,6 +118,7 @@ typedef struct {
   int ell_max;            /* rank adaptivity of Alg. 4: 0 = off (ell_next = ell); otherwise the cap
                              l_max >= 1 of ell_next */
   int ell_delta;          /* rank increase delta_l of Alg. 4 (the paper's runs: 20), >= 0 */
+  int test_matrix;        /* ngd_test_matrix of the sketch (default NGD_TEST_GAUSSIAN) */
 } ngd_step_opts;
 
 typedef struct {
@@ -194,7 +202,7 @@ ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, do
 
 /* ---------------------------------------------------------------- Nystrom */
 
-/* Sketch of App. A, Alg. randomized_nystrom, first three steps:
+/* Sketch of App. A (Alg. randomized_nystrom): the test matrix and Y = G Omega.
  * Omega_raw = randn(p, ell) from Philox4x32-10 (key = seed, counter word = step,
  * layout in the implementation notes), Omega = thin QR factor with positive
  * diag(R) (CholeskyQR2), Y = G Omega = J^T (w .* (J Omega)) in the arithmetic
@@ -205,7 +213,26 @@ ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, do
 ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step,
                               int prec, void* Omega, void* Y);
 
-/* Factor of App. A, remaining steps, given an orthonormal Omega and Y = G Omega:
+/* Gramian diagonal diag(G) = sum_r w_r (d r_r / d theta)^2 elementwise (Eq. gram_diagonal), at
+ * theta (NULL: the current linearization): stored J read once, or J recomputed by point blocks
+ * in matrix-free mode; FP64 accumulation over row slices added in a fixed order.
+ * d: device p float64, caller-owned.  Asynchronous.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+ngd_status ngd_gramian_diag(ngd_ctx* ctx, const double* theta, double* d);
+
+/* Randomized Nystrom sketch with the sampling test matrix (NGD_TEST_SAMPLING): diag G, then ell
+ * distinct parameter indices S by an exponential race (Efraimidis & Spirakis, 2006): the ell
+ * smallest keys E_j = -ln(u_j) / (diag G)_j, ties to the smaller index, u_j the 52-bit uniform of
+ * Philox4x32-10 words (x0, x1) at counter (j, 2^32 - 1, step mod 2^32, step >> 32) and key
+ * (seed mod 2^32, seed >> 32) (the Gaussian test matrix never uses column 2^32 - 1); this is
+ * sampling without replacement proportionally to diag G.  Omega = I[:, S] (S increasing, already
+ * orthonormal), Y = G Omega = G[:, S] (stored J: a gather of the sampled Jacobian columns and
+ * one product J^T (w .* J[:, S])).  Outputs as ngd_nystrom_sketch, plus idx: device ell int32,
+ * S in increasing order.  Synchronises.  Errors: as ngd_nystrom_sketch; INVALID_ARG also when
+ * fewer than ell entries of diag G are positive. */
+ngd_status ngd_nystrom_sketch_sampled(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step,
+                                      int prec, int* idx, void* Omega, void* Y);
+
+/* Factor of App. A (Alg. randomized_nystrom) given an orthonormal Omega and Y = G Omega:
  * nu = eps(||Y||_F) in the format of 'prec' (spacing 2^(floor(log2 x) - m) with m = 52, 23,
  * 10, 7 mantissa bits for F64, F32, TF32, BF16; m = 48 for F64 in an F32 context, whose sketch
  * and factor run in double-float), Y_nu = Y + nu Omega, C = chol(sym(Omega^T Y_nu)) in FP64,
@@ -294,7 +321,8 @@ ngd_status ngd_batch_step(ngd_batch* batch, double* const* thetas, const ngd_ste
 
 /* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
  * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,
- * c1 1e-4, rho 0.5, 30 trials, mu_loss_coef 0, ell_max 0 (fixed rank), ell_delta 20. */
+ * c1 1e-4, rho 0.5, 30 trials, mu_loss_coef 0, ell_max 0 (fixed rank), ell_delta 20,
+ * Gaussian test matrix. */
 void ngd_default_step_opts(ngd_step_opts* opts);
 
 #ifdef __cplusplus

@@ -17,6 +17,12 @@ Readings where the paper is silent (shared with the CUDA side):
   * chol reads the symmetric part (Omega^T Y_nu + Y_nu^T Omega)/2 and returns the
     upper factor C with C^T C = that matrix (MATLAB's chol reads one triangle; the
     two agree in exact arithmetic).
+Sampling test matrix (Sec. 3: columns of the identity; Sec. 5: drawn with probabilities
+proportional to diag G): ell distinct indices drawn one after another, each with probability
+proportional to diag G among the indices not yet drawn (reading: without replacement, since a
+repeated column adds nothing to Omega).  Realised as an exponential race (Efraimidis & Spirakis,
+2006): the ell smallest keys -ln(u_j) / (diag G)_j, ties to the smaller index, with u_j from
+philox.sampling_uniforms; Omega = I[:, S] with S increasing.
 Preconditioner, Alg. 4 (scaled form of Eq. nystrom_inverse):
     P^{-1} v = (lambda_ell + mu) U (Lambda + mu I)^{-1} U^T v + (I - U U^T) v.
 """
@@ -24,6 +30,8 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg
+
+from . import philox as _philox
 
 EPS64 = 2.0 ** -52
 
@@ -71,6 +79,27 @@ def randomized_nystrom(G_apply, Omega_raw, mant_bits: int = 52):
     Y = G_apply(Omega)
     U, lam, nu = nystrom_factor(Omega, Y, mant_bits)
     return Omega, Y, U, lam, nu
+
+
+def sampling_indices(diag, ell: int, seed: int, step: int) -> np.ndarray:
+    """S: ell distinct indices, increasing, sampled proportionally to diag (see the module notes).
+    Indices with diag <= 0 are never drawn; raises ValueError if fewer than ell are positive."""
+    diag = np.asarray(diag, dtype=np.float64)
+    pos = (diag > 0.0) & np.isfinite(diag)
+    if int(pos.sum()) < ell:
+        raise ValueError("fewer positive diagonal entries than the sample size")
+    u = _philox.sampling_uniforms(diag.size, seed, step)
+    keys = np.full(diag.size, np.inf)
+    keys[pos] = -np.log(u[pos]) / diag[pos]
+    order = np.lexsort((np.arange(diag.size), keys))     # by key, then by index
+    return np.sort(order[:ell])
+
+
+def selection_matrix(idx, p: int) -> np.ndarray:
+    """Omega = I[:, idx] (p, ell)."""
+    Om = np.zeros((p, len(idx)))
+    Om[np.asarray(idx), np.arange(len(idx))] = 1.0
+    return Om
 
 
 def nystrom_matrix(U, lam):

@@ -20,6 +20,10 @@ gives four words x0..x3.  Two 52-bit uniforms
 (every value of (m + 1/2) 2^-52 with m < 2^52 is exact and lies strictly in (0, 1))
 feed Box-Muller (Box & Muller 1958):
     Omega[2m, j] = sqrt(-2 ln u1) cos(2 pi u2),   Omega[2m+1, j] = sqrt(-2 ln u1) sin(2 pi u2).
+
+The sampling test matrix draws one uniform per parameter index j from the block at
+    counter = (j, 2^32 - 1, step mod 2^32, step >> 32),  key as above,
+u_j = ((x0 << 20) ^ (x1 >> 12) + 1/2) 2^-52 (column 2^32 - 1 is never a Gaussian column).
 """
 from __future__ import annotations
 
@@ -78,3 +82,15 @@ def gaussian_test_matrix(p: int, ell: int, seed: int, step: int) -> np.ndarray:
     out[0::2] = z0
     out[1::2] = z1
     return out[:p]
+
+
+def sampling_uniforms(p: int, seed: int, step: int) -> np.ndarray:
+    """u_j in (0, 1), j < p, of the sampling test matrix (counter layout above)."""
+    j = np.arange(p, dtype=np.uint64)
+    ctr = np.stack([j, np.full_like(j, np.uint64(0xFFFFFFFF)),
+                    np.full_like(j, np.uint64(step) & MASK32),
+                    np.full_like(j, np.uint64(step) >> np.uint64(32))], axis=-1)
+    key = np.stack([np.full_like(j, np.uint64(seed) & MASK32),
+                    np.full_like(j, np.uint64(seed) >> np.uint64(32))], axis=-1)
+    x = philox4x32_10(ctr, key)
+    return uniform52(x[..., 0], x[..., 1])

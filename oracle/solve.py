@@ -96,13 +96,15 @@ class StepInfo:
 
 
 def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gamma=10.0,
-             c1=1e-4, rho=0.5, max_trials=30, return_parts=False, mu_loss_coef=0.0, ell_max=0, ell_delta=20):
+             c1=1e-4, rho=0.5, max_trials=30, return_parts=False, mu_loss_coef=0.0, ell_max=0, ell_delta=20,
+             test_matrix="gaussian"):
     """One Nystrom-preconditioned matrix-free NGD step (Alg. 1 + Alg. 3 + Alg. 4).
 
     mu=None selects mu = gamma eps lambda_hat_1 (Alg. 4), raised to mu_loss_coef L(theta)^2 when
     mu_loss_coef > 0 (the damping of Sec. 5).  maxit caps pCG; rtol=0 runs exactly maxit
     iterations (for comparisons at a fixed iteration count).  ell_max > 0 applies the rank rule
-    of Alg. 4 to the returned info.ell_next (otherwise ell_next = ell).
+    of Alg. 4 to the returned info.ell_next (otherwise ell_next = ell).  test_matrix "sampling"
+    draws Omega = I[:, S] with S sampled proportionally to diag G (Sec. 3 and Sec. 5).
     """
     g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1: gradient
     J = _mlp.jacobian(problem, theta)                              # 'precompute Jacobian only'
@@ -111,8 +113,12 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
     def G_apply(V):
         return J.T @ (w[:, None] * (J @ V)) if V.ndim == 2 else _gram.gramian_mv(J, w, V)
 
-    Omega_raw = _philox.gaussian_test_matrix(J.shape[1], ell, seed, step)
-    Omega = _nys.thin_qr(Omega_raw)                                # Alg. 4: randomized Nystrom (App. A)
+    if test_matrix == "sampling":
+        S = _nys.sampling_indices(_gram.gramian_diag(J, w), ell, seed, step)
+        Omega = _nys.selection_matrix(S, J.shape[1])                # columns of the identity
+    else:
+        Omega_raw = _philox.gaussian_test_matrix(J.shape[1], ell, seed, step)
+        Omega = _nys.thin_qr(Omega_raw)                            # Alg. 4: randomized Nystrom (App. A)
     Y = G_apply(Omega)
     for scale in SHIFT_SCALES:          # a non-positive-definite core is retried with a larger shift
         try:

@@ -71,6 +71,10 @@ struct ngd_ctx {
   size_t gpart_elems = 0;
   int* perm = nullptr;
   TcSketch* tc = nullptr;
+  // sampling test matrix: diag G, race keys, selected columns (grown on demand)
+  double* gdiag = nullptr;
+  unsigned long long* samp_keys = nullptr;
+  int* samp_idx = nullptr;
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -135,6 +139,8 @@ ngd_status sync_status(ngd_ctx* ctx) {
   if (st & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
   if (st & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value in a reduction%s");
   if (st & kStatTimeout) return set_err(ctx, NGD_ERR_TIMEOUT, "device wait timed out%s");
+  if (st & kStatSample)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "fewer positive diagonal entries of G than the sample size ell%s");
   return NGD_OK;
 }
 
@@ -386,15 +392,105 @@ ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell) {
   return check_launch(ctx);
 }
 
+ngd_status ensure_sampling(ngd_ctx* ctx) {
+  if (ctx->gdiag) return NGD_OK;
+  TRY(dalloc(ctx, &ctx->gdiag, (size_t)ctx->p * 8));
+  TRY(dalloc(ctx, &ctx->samp_keys, (size_t)ctx->p * 8));
+  TRY(dalloc(ctx, &ctx->samp_idx, (size_t)2048 * sizeof(int)));
+  // valid indices before the first selection: a failed selection leaves them in place
+  CK(cudaMemsetAsync(ctx->samp_idx, 0, (size_t)2048 * sizeof(int), ctx->stream));
+  return NGD_OK;
+}
+
+// diag(G) = sum_n w_n J[n, :]^2 (Eq. gram_diagonal) at the current linearization, into out (p):
+// stored J read once; matrix-free J recomputed by point blocks.  FP64 partials over row slices,
+// added in a fixed order.
 template <typename T>
-ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, int prec) {
+ngd_status gram_diag_internal(ngd_ctx* ctx, double* out) {
+  const int64_t p = ctx->p;
+  constexpr int kSplits = 64;
+  TRY(ensure_gpart(ctx, (size_t)kSplits * p));
+  int nz = 0;
+  if (ctx->stored_j) {
+    nz = launch_gram_diag<T>((const T*)ctx->J, ctx->ldJ, ctx->N, p, ctx->ps.w, ctx->gpart, p, kSplits, 0, ctx->stream);
+  } else {
+    for (int64_t r0 = 0; r0 < ctx->N; r0 += ctx->jrows) {
+      const int64_t nr = std::min(ctx->jrows, ctx->N - r0);
+      if (launch_jacobian<T>(ctx->net, ctx->ps, (const T*)ctx->prep, r0, nr, (T*)ctx->J, ctx->ldJ, nullptr, nullptr,
+                             ctx->tape_valid ? (const T*)ctx->tape : nullptr, 0, ctx->stream) <= 0)
+        return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
+      const int z = launch_gram_diag<T>((const T*)ctx->J, ctx->ldJ, nr, p, ctx->ps.w + r0, ctx->gpart, p, kSplits,
+                                        r0 > 0 ? 1 : 0, ctx->stream);
+      if (r0 == 0) nz = z;                 // the first block is the largest: it sets every partial
+    }
+  }
+  launch_sum_splits(ctx->gpart, nz, p, p, out, ctx->stream);
+  return check_launch(ctx);
+}
+
+// Y = J^T Zw for a stored J and Zw = diag(w) J Omega already formed (FP64-accurate form: Zw64, Y64)
+ngd_status sketch_second_df(ngd_ctx* ctx, int ell) {
+  GemmDfArgs<float, double> g2;
+  g2.M = ctx->p; g2.N = ell; g2.K = ctx->N;
+  g2.A = (const float*)ctx->J; g2.sam = 1; g2.sak = ctx->ldJ;
+  g2.B = ctx->Zw64; g2.sbk = ell; g2.sbn = 1;
+  g2.scm = 1; g2.scn = ctx->ldP;
+  g2.nsplit = gemm_df_splits(g2.M, g2.N, g2.K);
+  const int nz2 = split_count(g2.K, g2.nsplit);
+  if (nz2 > 1) {
+    TRY(ensure_gpart(ctx, (size_t)nz2 * ctx->ldP * ell));
+    g2.out64 = ctx->gpart; g2.split_stride = (int64_t)ctx->ldP * ell;
+    launch_gemm_df<float, double>(g2, ctx->stream);
+    launch_sum_splits_t<double>(ctx->gpart, nz2, (int64_t)ctx->ldP * ell, ctx->p, ell, ctx->ldP, ctx->Y64, ctx->ldP,
+                                ctx->stream);
+  } else {
+    g2.out64 = ctx->Y64;
+    launch_gemm_df<float, double>(g2, ctx->stream);
+  }
+  return check_launch(ctx);
+}
+
+template <typename T>
+ngd_status sketch_second_t(ngd_ctx* ctx, int ell) {
+  GemmArgs<T> g2;
+  g2.M = ctx->p; g2.N = ell; g2.K = ctx->N;
+  g2.A = (const T*)ctx->J; g2.sam = 1; g2.sak = ctx->ldJ;
+  g2.B = (const T*)ctx->Zw; g2.sbk = ell; g2.sbn = 1;
+  g2.outT = (T*)ctx->Y; g2.scm = 1; g2.scn = ctx->ldP;
+  launch_gemm<T>(g2, ctx->stream);
+  return check_launch(ctx);
+}
+
+// test_matrix: 0 Gaussian (Philox, thin QR); 1 columns of the identity sampled with probabilities
+// proportional to diag G (the "sampling" test matrix of Sec. 3), already orthonormal.
+template <typename T>
+ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, int prec, int test_matrix = 0) {
   TRY(ensure_ell(ctx, ell));
   T* Om = (T*)ctx->Om;
   T* Y = (T*)ctx->Y;
   CK(cudaMemsetAsync(Om, 0, (size_t)ctx->ldP * ell * sizeof(T), ctx->stream));
-  launch_philox_omega<T>(Om, ctx->ldP, ctx->p, ell, seed, step, ctx->stream);
   TRY(clear_status(ctx));
-  TRY(thin_qr_inplace<T>(ctx, Om, ell));
+  if (test_matrix == 1) {
+    TRY(ensure_sampling(ctx));
+    TRY(gram_diag_internal<T>(ctx, ctx->gdiag));
+    launch_sample_indices(ctx->gdiag, ctx->p, ell, seed, step, ctx->samp_keys, ctx->samp_idx, ctx->status,
+                          ctx->stream);
+    launch_selection_omega<T>(Om, ctx->ldP, ctx->samp_idx, ell, ctx->stream);
+    // G Omega = G[:, S]: the first product is a gather of Jacobian columns
+    if (ctx->stored_j && prec != NGD_SKETCH_TF32 && prec != NGD_SKETCH_BF16) {
+      if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64) {
+        launch_gather_cols<float, double>((const float*)ctx->J, ctx->ldJ, ctx->N, ctx->samp_idx, ell, ctx->ps.w,
+                                          ctx->Zw64, ctx->stream);
+        return sketch_second_df(ctx, ell);
+      }
+      launch_gather_cols<T, T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->samp_idx, ell, ctx->ps.w, (T*)ctx->Zw,
+                               ctx->stream);
+      return sketch_second_t<T>(ctx, ell);
+    }
+  } else {
+    launch_philox_omega<T>(Om, ctx->ldP, ctx->p, ell, seed, step, ctx->stream);
+    TRY(thin_qr_inplace<T>(ctx, Om, ell));
+  }
   if (prec == NGD_SKETCH_TF32 || prec == NGD_SKETCH_BF16) {
     if (!std::is_same<T, float>::value) return set_err(ctx, NGD_ERR_INVALID_ARG, "TF32/BF16 sketch needs an F32 context%s");
     if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "TF32/BF16 sketch needs the stored Jacobian%s");
@@ -726,7 +822,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
   phase.next("sketch");
   // Alg. 4, randomized Nystrom (App. A): fresh Omega from (seed, step)
-  TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch));
+  TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch, o->test_matrix));
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
   phase.next("factor");
   double scale = 1.0;
@@ -840,6 +936,7 @@ void ngd_default_step_opts(ngd_step_opts* o) {
   o->mu_loss_coef = 0.0;
   o->ell_max = 0;
   o->ell_delta = 20;
+  o->test_matrix = 0;
 }
 
 ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
@@ -989,7 +1086,8 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->g, ctx->d, ctx->theta_trial, ctx->Om, ctx->Y, ctx->B, ctx->U, ctx->Lr, ctx->VsT, ctx->Zw, ctx->M,
                  ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
                  ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64, ctx->Uh, ctx->Ul,
-                 ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf};
+                 ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf, ctx->gdiag,
+                 ctx->samp_keys, ctx->samp_idx};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -1143,6 +1241,44 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
   });
 }
 
+ngd_status ngd_gramian_diag(ngd_ctx* ctx, const double* theta, double* d) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!d) return set_err(ctx, NGD_ERR_INVALID_ARG, "d is NULL%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    return gram_diag_internal<T>(ctx, d);
+  });
+}
+
+ngd_status ngd_nystrom_sketch_sampled(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step,
+                                      int prec, int* idx, void* Omega, void* Y) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!Omega || !Y || !idx) return set_err(ctx, NGD_ERR_INVALID_ARG, "idx/Omega/Y is NULL%s");
+  if (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048)) return set_err(ctx, NGD_ERR_INVALID_ARG, "ell out of range%s");
+  if (!valid_prec(prec)) return set_err(ctx, NGD_ERR_INVALID_ARG, "bad sketch precision%s");
+  if (ctx->dtype == NGD_F64 && prec != NGD_SKETCH_F64)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    TRY(sketch_internal<T>(ctx, ell, seed, step, prec, 1));
+    TRY(sync_status(ctx));
+    const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
+    CK(cudaMemcpyAsync(idx, ctx->samp_idx, (size_t)ell * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpy2DAsync(Omega, w, ctx->Om, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+      CK(cudaMemcpy2DAsync(Y, (size_t)ctx->p * 8, ctx->Y64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemcpy2DAsync(Y, w, ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_launch(ctx);
+  });
+}
+
 ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const void* Y, int prec, double shift_scale,
                               void* U, double* lam, double* nu_out) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
@@ -1214,7 +1350,7 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
   if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
       !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1 ||
       !(o->mu_loss_coef >= 0.0) || o->ell_max < 0 || o->ell_max > std::min<int64_t>(ctx->p, 2048) ||
-      o->ell_delta < 0)
+      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
   if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");

@@ -4,6 +4,7 @@
 // sums), the row-wise triangular solve and the FP64 blocked Cholesky of the l x l core.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <algorithm>
 
@@ -662,6 +663,187 @@ void launch_philox_omega(T* Om, int64_t ld, int64_t p, int ell, uint64_t seed, u
 }
 template void launch_philox_omega<float>(float*, int64_t, int64_t, int, uint64_t, uint64_t, cudaStream_t);
 template void launch_philox_omega<double>(double*, int64_t, int64_t, int, uint64_t, uint64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------- sampling test matrix
+// diag(G)_j = sum_n w_n J[n, j]^2 (Eq. gram_diagonal) over the nrows rows of J (row n at J + n ldJ,
+// weight w[n]), FP64 accumulation; rows split z (rows_per_split each) into part[z * ldp + j]
+// (added to it when accumulate).  Threads of a warp take consecutive j: coalesced rows of J.
+template <typename T>
+__global__ void k_gram_diag(const T* __restrict__ J, int64_t ldJ, int64_t nrows, int64_t p, const double* __restrict__ w,
+                            int64_t rows_per_split, double* __restrict__ part, int64_t ldp, int accumulate) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_split, r1 = min(nrows, r0 + rows_per_split);
+  double s = 0.0;
+  for (int64_t r = r0; r < r1; ++r) {
+    const double x = (double)J[r * ldJ + j];
+    s += w[r] * x * x;
+  }
+  double* o = part + (int64_t)blockIdx.y * ldp + j;
+  *o = accumulate ? *o + s : s;
+}
+template <typename T>
+int launch_gram_diag(const T* J, int64_t ldJ, int64_t nrows, int64_t p, const double* w, double* part, int64_t ldp,
+                     int max_splits, int accumulate, cudaStream_t s) {
+  const int64_t rps = std::max<int64_t>(64, (nrows + max_splits - 1) / max_splits);
+  const int nz = (int)std::max<int64_t>(1, (nrows + rps - 1) / rps);
+  dim3 grid((unsigned)((p + 255) / 256), (unsigned)nz);
+  k_gram_diag<T><<<grid, 256, 0, s>>>(J, ldJ, nrows, p, w, rps, part, ldp, accumulate); note_launch();
+  return nz;
+}
+template int launch_gram_diag<float>(const float*, int64_t, int64_t, int64_t, const double*, double*, int64_t, int,
+                                     int, cudaStream_t);
+template int launch_gram_diag<double>(const double*, int64_t, int64_t, int64_t, const double*, double*, int64_t, int,
+                                      int, cudaStream_t);
+
+// Keys of an exponential race (Efraimidis & Spirakis, 2006): the ell smallest of
+// E_j = -ln(u_j) / d_j, u_j uniform from the Philox counter (j, 2^32 - 1, step_lo, step_hi) and key
+// (seed_lo, seed_hi), are a sample of ell distinct indices drawn one after another with
+// probabilities proportional to d among those not yet drawn.  d_j <= 0 (or not finite) never
+// wins (key +inf).  Keys are stored as the bits of the non-negative double, which order like it.
+__global__ void k_sample_keys(const double* __restrict__ d, int64_t p, uint64_t seed, uint64_t step,
+                              unsigned long long* __restrict__ keys) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += st) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, 0xFFFFFFFFu, (uint32_t)step, (uint32_t)(step >> 32)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double dj = d[j];
+    const double e = (dj > 0.0 && isfinite(dj)) ? -log(uniform52(x.x, x.y)) / dj : CUDART_INF;
+    keys[j] = (unsigned long long)__double_as_longlong(e);
+  }
+}
+
+// number of keys <= t over the block (every thread gets it); s: 33 shared words
+__device__ long long block_count_le(const unsigned long long* __restrict__ keys, int64_t p, unsigned long long t,
+                                   long long* s) {
+  long long c = 0;
+  for (int64_t j = threadIdx.x; j < p; j += blockDim.x) c += keys[j] <= t ? 1 : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t2 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t2 += s[w];
+    s[32] = t2;
+  }
+  __syncthreads();
+  const long long r = s[32];
+  __syncthreads();
+  return r;
+}
+
+// exclusive prefix sum of v over the threads of the block in thread order; s: 33 shared words
+__device__ long long block_exclusive_scan(long long v, long long* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = lane < nw ? s[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s[lane] = w;
+  }
+  __syncthreads();
+  const long long r = (warp > 0 ? s[warp - 1] : 0) + x - v;
+  __syncthreads();
+  return r;
+}
+
+// The ell smallest keys (ties to the smaller index), written to idx in increasing index order:
+// one block finds the ell-th smallest key T by bisection on its bits, then takes every key below
+// T and the first ell - #(below) keys equal to T.  Fewer than ell finite keys: status bit
+// kStatSample, idx untouched.
+__global__ void __launch_bounds__(1024) k_sample_select(const unsigned long long* __restrict__ keys, int64_t p, int ell,
+                                                        int* __restrict__ idx, int* __restrict__ status) {
+  __shared__ long long s[33];
+  const unsigned long long kInf = 0x7FF0000000000000ull;
+  if (block_count_le(keys, p, kInf - 1, s) < ell) {
+    if (threadIdx.x == 0) atomicOr(status, kStatSample);
+    return;
+  }
+  unsigned long long lo = 0, hi = kInf - 1;
+  while (lo < hi) {
+    const unsigned long long mid = lo + (hi - lo) / 2;
+    if (block_count_le(keys, p, mid, s) >= ell) hi = mid;
+    else lo = mid + 1;
+  }
+  const unsigned long long T = lo;
+  const long long need = ell - (T > 0 ? block_count_le(keys, p, T - 1, s) : 0);
+  const int64_t chunk = (p + blockDim.x - 1) / blockDim.x;
+  const int64_t j0 = min(p, (int64_t)threadIdx.x * chunk), j1 = min(p, j0 + chunk);
+  long long eq = 0;
+  for (int64_t j = j0; j < j1; ++j) eq += keys[j] == T ? 1 : 0;
+  const long long eq_base = block_exclusive_scan(eq, s);
+  long long sel = 0, e = eq_base;
+  for (int64_t j = j0; j < j1; ++j) {
+    const unsigned long long k = keys[j];
+    if (k < T) ++sel;
+    else if (k == T) sel += (e++ < need) ? 1 : 0;
+  }
+  long long o = block_exclusive_scan(sel, s);
+  e = eq_base;
+  for (int64_t j = j0; j < j1; ++j) {
+    const unsigned long long k = keys[j];
+    bool take = k < T;
+    if (k == T) take = e++ < need;
+    if (take) idx[o++] = (int)j;
+  }
+}
+
+void launch_sample_indices(const double* d, int64_t p, int ell, uint64_t seed, uint64_t step,
+                           unsigned long long* keys, int* idx, int* status, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((p + 255) / 256, 1024);
+  k_sample_keys<<<blocks, 256, 0, s>>>(d, p, seed, step, keys); note_launch();
+  k_sample_select<<<1, 1024, 0, s>>>(keys, p, ell, idx, status); note_launch();
+}
+
+// Omega[idx_k + k ld] = 1 (the rest already zero): the column-selection test matrix
+template <typename T>
+__global__ void k_selection_omega(T* __restrict__ Om, int64_t ld, const int* __restrict__ idx, int ell) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < ell) Om[(int64_t)idx[k] + (int64_t)k * ld] = T(1);
+}
+template <typename T>
+void launch_selection_omega(T* Om, int64_t ld, const int* idx, int ell, cudaStream_t s) {
+  k_selection_omega<T><<<(ell + 255) / 256, 256, 0, s>>>(Om, ld, idx, ell); note_launch();
+}
+template void launch_selection_omega<float>(float*, int64_t, const int*, int, cudaStream_t);
+template void launch_selection_omega<double>(double*, int64_t, const int*, int, cudaStream_t);
+
+// Zw[n ell + k] = w_n J[n, idx_k] (N x ell, row-major): diag(w) J Omega for a column-selection Omega
+template <typename T, typename TO>
+__global__ void k_gather_cols(const T* __restrict__ J, int64_t ldJ, int64_t N, const int* __restrict__ idx, int ell,
+                              const double* __restrict__ w, TO* __restrict__ Zw) {
+  const int64_t total = N * ell;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st) {
+    const int64_t n = e / ell;
+    const int k = (int)(e - n * ell);
+    Zw[e] = (TO)(w[n] * (double)J[n * ldJ + idx[k]]);
+  }
+}
+template <typename T, typename TO>
+void launch_gather_cols(const T* J, int64_t ldJ, int64_t N, const int* idx, int ell, const double* w, TO* Zw,
+                        cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((N * ell + 255) / 256, 8192);
+  k_gather_cols<T, TO><<<blocks, 256, 0, s>>>(J, ldJ, N, idx, ell, w, Zw); note_launch();
+}
+template void launch_gather_cols<float, double>(const float*, int64_t, int64_t, const int*, int, const double*,
+                                                double*, cudaStream_t);
+template void launch_gather_cols<float, float>(const float*, int64_t, int64_t, const int*, int, const double*, float*,
+                                               cudaStream_t);
+template void launch_gather_cols<double, double>(const double*, int64_t, int64_t, const int*, int, const double*,
+                                                 double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------- SIMT GEMM
 // C(m, n) = sum_k A(m, k) B(k, n) with element strides; A(m,k) = A[m*sam + k*sak],

@@ -45,6 +45,18 @@ template <typename TA, typename TB> void launch_gemm_df(const GemmDfArgs<TA, TB>
 // K slices that fill the GPU's block slots most evenly for an M x N double-float GEMM
 int gemm_df_splits(int64_t M, int64_t N, int64_t K);
 
+// sampling test matrix (column selection with probabilities proportional to diag G)
+template <typename T>
+int launch_gram_diag(const T* J, int64_t ldJ, int64_t nrows, int64_t p, const double* w, double* part, int64_t ldp,
+                     int max_splits, int accumulate, cudaStream_t s);
+void launch_sample_indices(const double* d, int64_t p, int ell, uint64_t seed, uint64_t step,
+                           unsigned long long* keys, int* idx, int* status, cudaStream_t s);
+template <typename T> void launch_selection_omega(T* Om, int64_t ld, const int* idx, int ell, cudaStream_t s);
+template <typename T, typename TO>
+void launch_gather_cols(const T* J, int64_t ldJ, int64_t N, const int* idx, int ell, const double* w, TO* Zw,
+                        cudaStream_t s);
+
+
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);
 template <typename T> void launch_d2t(const double* x, T* y, int64_t n, int64_t npad, cudaStream_t s);
 

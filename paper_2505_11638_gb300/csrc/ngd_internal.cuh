@@ -20,6 +20,7 @@ enum : int {
   kStatBreakdown = 2,
   kStatNonFinite = 4,
   kStatTimeout = 8,
+  kStatSample = 16,      // fewer positive diagonal entries of G than the sample size
 };
 
 // Network description passed by value to the kernels.

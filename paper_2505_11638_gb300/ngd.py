@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_SPD", 5:
                 7: "NONFINITE", 8: "TIMEOUT", 9: "UNSUPPORTED"}
 DTYPES = {"f64": 0, "f32": 1}
 SKETCH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+TEST_MATRIX = {"gaussian": 0, "sampling": 1}
 PDES = {"poisson": 0, "heat": 1}
 GV_MODES = {"auto": 0, "stored": 1, "matrix_free": 2}
 
@@ -50,7 +51,7 @@ class StepOpts(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("sketch", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64), ("armijo_c1", ctypes.c_double),
                 ("armijo_rho", ctypes.c_double), ("armijo_max", ctypes.c_int), ("mu_loss_coef", ctypes.c_double),
-                ("ell_max", ctypes.c_int), ("ell_delta", ctypes.c_int)]
+                ("ell_max", ctypes.c_int), ("ell_delta", ctypes.c_int), ("test_matrix", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -85,6 +86,8 @@ _SIGS = {
     "ngd_gradient": ([_P, _P, _P, _P, ctypes.POINTER(_D)], _I),
     "ngd_gramian_mv": ([_P, _P, _P, _D, _P], _I),
     "ngd_nystrom_sketch": ([_P, _P, _I, _U64, _U64, _I, _P, _P], _I),
+    "ngd_nystrom_sketch_sampled": ([_P, _P, _I, _U64, _U64, _I, _P, _P, _P], _I),
+    "ngd_gramian_diag": ([_P, _P, _P], _I),
     "ngd_nystrom_factor": ([_P, _I, _P, _P, _I, _D, _P, _P, ctypes.POINTER(_D)], _I),
     "ngd_precond_apply": ([_P, _I, _P, _I, _P, _D, _P, _P], _I),
     "ngd_pcg_solve": ([_P, _P, _P, _D, _P, _I, _P, _I, _D, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
@@ -187,6 +190,17 @@ def ngd_nystrom_sketch(h, theta, ell, seed, step, prec, Omega, Y):
     lib().ngd_set_stream(h, _stream())
     _check(h, lib().ngd_nystrom_sketch(h, _ptr(theta), int(ell), int(seed), int(step), SKETCH[prec], _ptr(Omega),
                                        _ptr(Y)))
+
+
+def ngd_nystrom_sketch_sampled(h, theta, ell, seed, step, prec, idx, Omega, Y):
+    lib().ngd_set_stream(h, _stream())
+    _check(h, lib().ngd_nystrom_sketch_sampled(h, _ptr(theta), int(ell), int(seed), int(step), SKETCH[prec],
+                                               _ptr(idx), _ptr(Omega), _ptr(Y)))
+
+
+def ngd_gramian_diag(h, theta, d):
+    lib().ngd_set_stream(h, _stream())
+    _check(h, lib().ngd_gramian_diag(h, _ptr(theta), _ptr(d)))
 
 
 def ngd_nystrom_factor(h, ell, Omega, Y, prec, shift_scale, U, lam):
@@ -322,6 +336,23 @@ class Context:
             self.version += 1
         return Om, Y
 
+    def nystrom_sketch_sampled(self, theta, ell, seed=0, step=0, prec="f64"):
+        """The sampling test matrix: returns (idx, Omega, Y), idx the sampled parameter indices."""
+        idx = torch.empty(ell, dtype=torch.int32, device=self.device)
+        Om = torch.empty((ell, self.p), dtype=self.wdtype, device=self.device)
+        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
+        ngd_nystrom_sketch_sampled(self.handle, theta, ell, seed, step, prec, idx, Om, Y)
+        if theta is not None:
+            self.version += 1
+        return idx, Om, Y
+
+    def gramian_diag(self, theta):
+        d = self._vec(self.p)
+        ngd_gramian_diag(self.handle, theta, d)
+        if theta is not None:
+            self.version += 1
+        return d
+
     def nystrom_factor(self, ell, Omega, Y, prec="f64", shift_scale=1.0):
         _need(Omega, self.wdtype, self.p * ell, "Omega")
         _need(Y, torch.float64 if prec == "f64" else self.wdtype, self.p * ell, "Y")
@@ -349,6 +380,8 @@ class Context:
         for k, v in kw.items():
             if k == "sketch":
                 v = SKETCH[v]
+            if k == "test_matrix":
+                v = TEST_MATRIX[v]
             if k == "mu" and v is None:
                 v = 0.0
             setattr(o, k, v)

@@ -523,3 +523,64 @@ def test_nystrom_ngd_run_matches_oracle(ngd):
     assert ells == ells_o
     assert rel(host(t) - th, th_o - th) <= 1e-6
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("mode", ["stored", "matrix_free"])
+def test_gramian_diag_matches_oracle(ngd, dtype, mode):
+    """ngd_gramian_diag against diag(J^T W J) of the oracle's Jacobian (FP64 1e-12, FP32 2e-5)."""
+    pr, th = small(SMALL[0], seed=80)
+    ctx = ngd.Context(pr, dtype=dtype, gv_mode=mode)
+    d = host(ctx.gramian_diag(dev(th)))
+    d_o = gramian.gramian_diag(mlp.jacobian(pr, th), pr.w)
+    assert rel(d, d_o) <= (1e-12 if dtype == "f64" else 2e-5)
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype,prec", [("f64", "f64"), ("f32", "f64"), ("f32", "f32")])
+def test_sampled_sketch_matches_oracle(ngd, dtype, prec):
+    """The sampling test matrix: the sampled indices are the oracle's exponential race on the same
+    FP64 diagonal (bit-exact integers), Omega = I[:, S], and Y = G[:, S]."""
+    pr, th = small(SMALL[1], seed=81)
+    ctx = ngd.Context(pr, dtype=dtype)
+    ell = 15
+    idx, Om, Y = ctx.nystrom_sketch_sampled(dev(th), ell, seed=6, step=4, prec=prec)
+    d_gpu = host(ctx.gramian_diag(None))
+    S = nystrom.sampling_indices(d_gpu, ell, seed=6, step=4)
+    assert [int(i) for i in idx.cpu().tolist()] == [int(i) for i in S]
+    assert np.array_equal(host(Om).reshape(ell, -1).T, nystrom.selection_matrix(S, pr.p))
+    G = gramian.gramian(mlp.jacobian(pr, th), pr.w)
+    Yg = host(Y).reshape(ell, -1).T
+    assert rel(Yg, G[:, S]) <= (1e-10 if dtype == "f64" else 1e-5)
+    ctx.close()
+
+
+def test_ngd_step_sampling_test_matrix_matches_oracle(ngd):
+    """One NystromNGD Sampling step: the same S, factor, PCG (same iteration count) and update as
+    the oracle."""
+    pr, th = small(SMALL[0], seed=82)
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    info = ctx.step(t, ell=14, mu=1e-6, rtol=1e-10, maxit=500, seed=3, step=2, sketch="f64", test_matrix="sampling")
+    th1_o, info_o = solve.ngd_step(pr, th, ell=14, mu=1e-6, rtol=0.0, maxit=info["pcg_iters"], seed=3, step=2,
+                                   test_matrix="sampling")
+    assert info["loss_after"] < info["loss_before"]
+    assert abs(info["lam1"] - info_o.lam1) <= 1e-9 * info_o.lam1
+    assert rel(host(t) - th, th1_o - th) <= 1e-6
+    ctx.close()
+
+
+def test_sampling_rejects_too_few_positive_diagonal_entries(ngd):
+    """A one-point problem has a rank-one G: asking for more columns than diag G has positive
+    entries is an error reported through the status word (no GPU fault)."""
+    pr, th = small(SMALL[5], seed=83)             # a single point
+    ctx = ngd.Context(pr, dtype="f64")
+    ell = min(pr.p, 2048)
+    d = host(ctx.gramian_diag(dev(th)))
+    npos = int(np.sum(d > 0))
+    if npos >= ell:
+        pytest.skip("every diagonal entry is positive")
+    with pytest.raises(ngd.NGDError) as e:
+        ctx.nystrom_sketch_sampled(dev(th), ell, seed=1, step=0)
+    assert e.value.name == "INVALID_ARG"
+    ctx.close()

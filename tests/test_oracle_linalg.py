@@ -310,3 +310,54 @@ def test_nystrom_ngd_grows_the_rank_then_caps_it_and_decreases_the_loss():
             assert ells[k + 1] == info.ell_next
     assert ells[0] == 4 and max(ells) <= 14
     assert infos[-1].loss_after < infos[0].loss_before
+
+
+# ---------------------------------------------------------------------------- sampling test matrix (Sec. 3, Sec. 5)
+def test_sampling_takes_the_only_positive_entries_and_rejects_too_few():
+    d = np.array([0.0, 2.0, 0.0, 5.0, -1.0, 1e-300])
+    assert list(nystrom.sampling_indices(d, 3, seed=4, step=1)) == [1, 3, 5]
+    with pytest.raises(ValueError):
+        nystrom.sampling_indices(d, 4, seed=4, step=1)
+
+
+def test_sampling_matches_sequential_draws_without_replacement():
+    """Inclusion frequencies of the exponential race against the exact probabilities of drawing two
+    indices one after another proportionally to the weights among those left (brute force)."""
+    wts = np.array([4.0, 3.0, 2.0, 1.0])
+    W = wts.sum()
+    pair = {}
+    for i in range(4):
+        for j in range(4):
+            if i != j:
+                key = tuple(sorted((i, j)))
+                pair[key] = pair.get(key, 0.0) + wts[i] / W * wts[j] / (W - wts[i])
+    n = 6000
+    counts = {}
+    for seed in range(n):
+        key = tuple(int(x) for x in nystrom.sampling_indices(wts, 2, seed=seed, step=3))
+        counts[key] = counts.get(key, 0) + 1
+    assert set(counts) <= set(pair)
+    for key, pr in pair.items():
+        f = counts.get(key, 0) / n
+        assert abs(f - pr) <= 4.5 * np.sqrt(pr * (1 - pr) / n), (key, f, pr)
+
+
+def test_sampled_nystrom_is_the_column_nystrom_approximation():
+    """With Omega = I[:, S], App. A reproduces Eq. nystrom_approx: G[:, S] G[S, S]^{-1} G[S, :]."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((40, 25))
+    G = A.T @ A / 40.0
+    S = nystrom.sampling_indices(np.diag(G), 8, seed=2, step=0)
+    Om = nystrom.selection_matrix(S, 25)
+    assert np.array_equal(np.abs(nystrom.thin_qr(Om)), Om)            # already orthonormal
+    U, lam, nu = nystrom.nystrom_factor(Om, G @ Om)
+    Ghat = nystrom.nystrom_matrix(U, lam)
+    ref = G[:, S] @ np.linalg.solve(G[np.ix_(S, S)], G[S, :])
+    assert np.linalg.norm(Ghat - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_ngd_step_with_sampling_test_matrix_decreases_the_loss():
+    pr, th = inputs.small_problem(d=2, widths=[2, 6, 5, 1], n_int=30, n_bnd=10, seed=5)
+    th1, info = solve.ngd_step(pr, th, ell=12, mu=None, rtol=1e-10, maxit=400, seed=3, step=1,
+                               test_matrix="sampling")
+    assert info.loss_after < info.loss_before
