@@ -140,3 +140,67 @@ def next_rank(lam, mu: float, ell: int, ell_max: int, delta: int) -> int:
     if not below:
         return ell
     return min(below[0] + 1, ell_max)
+
+
+# ----------------------------------------------------------------------------- RPCholesky (Sec. 3, App. B)
+# Block RPCholesky (the paper's block variant, after Epperly et al.): rounds of b pivots sampled
+# i.i.d. proportionally to the residual diagonal d, then the residual block
+#     C = G[:, S'] - F F[S', :]^T,  R = chol(C[S', S']),  new columns of F = C R^{-1},
+#     d <- d - squared row norms of the new columns,
+# stopping when sum(d) < eps or after t rounds.  Readings (the paper is silent):
+#   * sample k of round i is the winner of an exponential race, argmin_j -ln(u_jk) / d_j, with u_jk
+#     from Philox at counter (j, 2^30 + i b + k, step) (philox.rpchol_uniforms); the b winners are
+#     made unique (S' increasing);
+#   * d is clamped at 0 after each round and set to 0 on the pivots (their residual is zero);
+#   * a round whose pivot block C[S', S'] is not numerically positive definite ends the
+#     factorization with the columns found so far.
+def rpcholesky_block(G_cols, d0, b: int, t: int, eps: float, seed: int, step: int):
+    """F (p, r) with G ~ F F^T, and the pivots in selection order.  G_cols(S) returns G[:, S]."""
+    d = np.maximum(np.asarray(d0, dtype=np.float64).copy(), 0.0)
+    p = d.size
+    cols, piv = [], []
+    F = np.zeros((p, 0))
+    for i in range(t):
+        if not d.sum() >= eps or not np.any(d > 0.0):
+            break
+        u = _philox.rpchol_uniforms(p, b, i, seed, step)          # (p, b)
+        keys = np.full((p, b), np.inf)
+        pos = d > 0.0
+        keys[pos, :] = -np.log(u[pos, :]) / d[pos, None]
+        S = np.unique(np.argmin(keys, axis=0))
+        C = G_cols(S) - F @ F[S, :].T
+        try:
+            L = np.linalg.cholesky(0.5 * (C[S, :] + C[S, :].T))
+        except np.linalg.LinAlgError:
+            break
+        Fn = scipy.linalg.solve_triangular(L, C.T, lower=True).T    # C L^{-T} = C R^{-1}, R = L^T
+        F = np.concatenate([F, Fn], axis=1)
+        piv.extend(int(s) for s in S)
+        d = np.maximum(d - np.sum(Fn * Fn, axis=1), 0.0)
+        d[S] = 0.0
+        if d.sum() < eps:
+            break
+    return F, piv
+
+
+def rpchol_precond_apply(F, mu, v):
+    """P^{-1} v for P = F F^T + mu I by the Woodbury identity with F^T F + mu I = R^T R
+    (Eq. rpchol_precond): mu^{-1} (v - F R^{-1} R^{-T} F^T v)."""
+    r = F.shape[1]
+    if r == 0:
+        return np.asarray(v, dtype=np.float64) / mu
+    R = np.linalg.cholesky(F.T @ F + mu * np.eye(r)).T
+    t = scipy.linalg.solve_triangular(R, scipy.linalg.solve_triangular(R, F.T @ v, trans="T"))
+    return (v - F @ t) / mu
+
+
+def power_lambda1(G_apply, v0, iters: int = 4) -> float:
+    """lambda_1 of G by the power method (Alg. 5): v <- G v / ||G v|| from v0, the estimate the
+    Rayleigh quotient v^T G v of the last step."""
+    v = np.asarray(v0, dtype=np.float64) / np.linalg.norm(v0)
+    lam = 0.0
+    for _ in range(iters):
+        w = G_apply(v)
+        lam = float(v @ w)
+        v = w / np.linalg.norm(w)
+    return lam

@@ -94,3 +94,35 @@ def sampling_uniforms(p: int, seed: int, step: int) -> np.ndarray:
                     np.full_like(j, np.uint64(seed) >> np.uint64(32))], axis=-1)
     x = philox4x32_10(ctr, key)
     return uniform52(x[..., 0], x[..., 1])
+
+
+def rpchol_uniforms(p: int, b: int, rnd: int, seed: int, step: int) -> np.ndarray:
+    """u (p, b) of round rnd of block RPCholesky: counter (j, 2^30 + rnd b + k, step mod 2^32,
+    step >> 32), words (x0, x1) as in sampling_uniforms."""
+    j = np.arange(p, dtype=np.uint64)
+    k = np.arange(b, dtype=np.uint64)
+    jj, kk = np.meshgrid(j, k, indexing="ij")
+    ctr = np.stack([jj, np.uint64(1 << 30) + np.uint64(rnd * b) + kk,
+                    np.full_like(jj, np.uint64(step) & MASK32),
+                    np.full_like(jj, np.uint64(step) >> np.uint64(32))], axis=-1)
+    key = np.stack([np.full_like(jj, np.uint64(seed) & MASK32),
+                    np.full_like(jj, np.uint64(seed) >> np.uint64(32))], axis=-1)
+    x = philox4x32_10(ctr, key)
+    return uniform52(x[..., 0], x[..., 1])
+
+
+def power_start(p: int, seed: int, step: int) -> np.ndarray:
+    """Start vector of the power method: the Gaussian column with counter word 2^32 - 2."""
+    npairs = (p + 1) // 2
+    m = np.arange(npairs, dtype=np.uint64)
+    ctr = np.stack([m, np.full_like(m, np.uint64(0xFFFFFFFE)),
+                    np.full_like(m, np.uint64(step) & MASK32),
+                    np.full_like(m, np.uint64(step) >> np.uint64(32))], axis=-1)
+    key = np.stack([np.full_like(m, np.uint64(seed) & MASK32),
+                    np.full_like(m, np.uint64(seed) >> np.uint64(32))], axis=-1)
+    x = philox4x32_10(ctr, key)
+    z0, z1 = box_muller(uniform52(x[..., 0], x[..., 1]), uniform52(x[..., 2], x[..., 3]))
+    out = np.empty(2 * npairs)
+    out[0::2] = z0
+    out[1::2] = z1
+    return out[:p]

@@ -97,7 +97,7 @@ class StepInfo:
 
 def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gamma=10.0,
              c1=1e-4, rho=0.5, max_trials=30, return_parts=False, mu_loss_coef=0.0, ell_max=0, ell_delta=20,
-             test_matrix="gaussian"):
+             test_matrix="gaussian", precond="nystrom", rpchol_block=20):
     """One Nystrom-preconditioned matrix-free NGD step (Alg. 1 + Alg. 3 + Alg. 4).
 
     mu=None selects mu = gamma eps lambda_hat_1 (Alg. 4), raised to mu_loss_coef L(theta)^2 when
@@ -105,7 +105,14 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
     iterations (for comparisons at a fixed iteration count).  ell_max > 0 applies the rank rule
     of Alg. 4 to the returned info.ell_next (otherwise ell_next = ell).  test_matrix "sampling"
     draws Omega = I[:, S] with S sampled proportionally to diag G (Sec. 3 and Sec. 5).
+    precond "rpchol" builds the RPCholNGD preconditioner instead (Alg. 5): diag G, lambda_1 by four
+    power-method steps, mu, block RPCholesky of rank at most ell (blocks of rpchol_block, stopping
+    when the trace of the residual is below mu p), P^{-1} by Woodbury (Eq. rpchol_precond);
+    info.ell_next is then the rank found.
     """
+    if precond == "rpchol":
+        return _rpchol_step(problem, theta, ell, mu, rtol, maxit, seed, step, gamma, c1, rho, max_trials,
+                            return_parts, mu_loss_coef, rpchol_block)
     g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1: gradient
     J = _mlp.jacobian(problem, theta)                              # 'precompute Jacobian only'
     w = problem.w
@@ -174,3 +181,48 @@ def nystrom_ngd(problem, theta0, steps, ell0, ell_max, ell_delta=20, rtol=1e-6, 
         ells.append(ell)
         ell = info.ell_next
     return theta, infos, ells
+
+
+def _rpchol_step(problem, theta, ell, mu, rtol, maxit, seed, step, gamma, c1, rho, max_trials, return_parts,
+                 mu_loss_coef, b):
+    """One RPCholNGD step (Alg. 1 with Alg. 3 and Alg. 5)."""
+    g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1: gradient
+    J = _mlp.jacobian(problem, theta)
+    w = problem.w
+    p = J.shape[1]
+
+    def G_apply(v):
+        return _gram.gramian_mv(J, w, v)
+
+    def G_cols(S):
+        return J.T @ (w[:, None] * J[:, S])
+
+    d0 = _gram.gramian_diag(J, w)                                   # Alg. 5: diagonal
+    lam1 = _nys.power_lambda1(G_apply, _philox.power_start(p, seed, step), 4)   # Alg. 5: power method
+    if mu is not None:
+        mu_eff = float(mu)
+    elif mu_loss_coef > 0.0:
+        mu_eff = _nys.mu_adaptive(lam1, L0, gamma, mu_loss_coef)
+    else:
+        mu_eff = _nys.mu_from_lambda1(lam1, gamma)
+    F, piv = _nys.rpcholesky_block(G_cols, d0, b, ell // b, mu_eff * p, seed, step)   # Alg. 5: RPCholesky
+
+    def A(v):
+        return _gram.gramian_mv(J, w, v, mu_eff)
+
+    def Pinv(v):
+        return _nys.rpchol_precond_apply(F, mu_eff, v)
+
+    d, iters, relres = pcg(A, g, Pinv, rtol, maxit)                # Alg. 3: direction by pCG
+
+    def loss_fn(th):
+        return _mlp.residual(problem, th)[1]
+
+    alpha, L1, trials = armijo(loss_fn, theta, d, g, L0, c1, rho, max_trials)   # Alg. 1: line search
+    sig2 = np.linalg.svd(F, compute_uv=False) ** 2 if F.shape[1] else np.zeros(0)
+    info = StepInfo(L0, L1, alpha, mu_eff, lam1, float(sig2[-1]) if sig2.size else 0.0, 0.0, iters, relres,
+                    trials, F.shape[1])
+    theta_new = theta - alpha * d                                   # Alg. 1: update
+    if return_parts:
+        return theta_new, info, dict(g=g, r=r, J=J, F=F, piv=piv, d=d, d0=d0)
+    return theta_new, info

@@ -361,3 +361,81 @@ def test_ngd_step_with_sampling_test_matrix_decreases_the_loss():
     th1, info = solve.ngd_step(pr, th, ell=12, mu=None, rtol=1e-10, maxit=400, seed=3, step=1,
                                test_matrix="sampling")
     assert info.loss_after < info.loss_before
+
+
+# ---------------------------------------------------------------------------- RPCholesky (Sec. 3, App. B, Alg. 5)
+def _decaying_psd(p=30, n=60, rate=3.0, seed=0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, p)) * np.exp(-np.arange(p) / rate)[None, :]
+    return A.T @ A / n
+
+
+def test_rpcholesky_is_the_nystrom_approximation_of_its_pivots():
+    """F F^T = G[:, S] G[S, S]^{-1} G[S, :] (RPCholesky equals Nystrom with the pivot columns),
+    and the residual diagonal sums to the trace-norm error tr(G - F F^T)."""
+    G = _decaying_psd()
+    F, piv = nystrom.rpcholesky_block(lambda S: G[:, S], np.diag(G), 5, 3, 0.0, 3, 1)
+    S = np.array(piv)
+    ref = G[:, S] @ np.linalg.solve(G[np.ix_(S, S)], G[S, :])
+    assert np.linalg.norm(F @ F.T - ref) <= 1e-9 * np.linalg.norm(G)
+    d = np.maximum(np.diag(G) - np.sum(F * F, axis=1), 0.0)
+    assert abs(d.sum() - np.trace(G - F @ F.T)) <= 1e-12 * np.trace(G)
+
+
+def test_rpcholesky_is_exact_on_a_low_rank_matrix():
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((25, 6))
+    G = B @ B.T
+    F, piv = nystrom.rpcholesky_block(lambda S: G[:, S], np.diag(G), 4, 10, 1e-10 * np.trace(G), 5, 0)
+    # a round of 4 pivots can overshoot rank 6 by columns of rounding size; it stops right after
+    assert 6 <= F.shape[1] <= 6 + 3
+    assert np.linalg.norm(G - F @ F.T) <= 1e-10 * np.linalg.norm(G)
+    assert np.linalg.matrix_rank(F, tol=1e-6 * np.linalg.norm(F)) == 6
+
+
+def test_rpcholesky_pivots_are_drawn_proportionally_to_the_diagonal():
+    """The first sample of the first round follows d / sum(d) (one race per sample)."""
+    d = np.array([1.0, 2.0, 3.0, 4.0])
+    n = 5000
+    hits = np.zeros(4)
+    for seed in range(n):
+        u = philox.rpchol_uniforms(4, 1, 0, seed, 2)[:, 0]
+        hits[int(np.argmin(-np.log(u) / d))] += 1
+    pr = d / d.sum()
+    assert np.all(np.abs(hits / n - pr) <= 4.5 * np.sqrt(pr * (1 - pr) / n))
+
+
+def test_rpchol_preconditioner_is_the_inverse_of_ffT_plus_mu():
+    rng = np.random.default_rng(6)
+    F = rng.standard_normal((20, 7))
+    mu = 0.3
+    v = rng.standard_normal(20)
+    z = nystrom.rpchol_precond_apply(F, mu, v)
+    assert np.linalg.norm(z - np.linalg.solve(F @ F.T + mu * np.eye(20), v)) <= 1e-12 * np.linalg.norm(z)
+    U, s, _ = np.linalg.svd(F, full_matrices=False)         # Eq. rpchol_svdprecond
+    z2 = (v - U @ (U.T @ v)) / mu + U @ ((U.T @ v) / (s * s + mu))
+    assert np.linalg.norm(z - z2) <= 1e-12 * np.linalg.norm(z)
+    assert np.array_equal(nystrom.rpchol_precond_apply(np.zeros((20, 0)), mu, v), v / mu)
+
+
+def test_power_method_estimate_with_a_spectral_gap():
+    """Four matrix-vector products: the estimate is the Rayleigh quotient of G^3 v0, in closed form
+    sum c_i^2 lambda_i^7 / sum c_i^2 lambda_i^6 (c = Q^T v0), and with lambda_2 / lambda_1 = 0.05
+    it is within ~0.05^6 of lambda_1."""
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    lam = np.concatenate([[10.0, 0.5], np.linspace(0.4, 0.01, 10)])
+    G = (Q * lam) @ Q.T
+    v0 = philox.power_start(12, 3, 0)
+    est = nystrom.power_lambda1(lambda v: G @ v, v0, 4)
+    c2 = (Q.T @ v0) ** 2
+    assert abs(est - np.sum(c2 * lam ** 7) / np.sum(c2 * lam ** 6)) <= 1e-13 * 10.0
+    assert abs(est - 10.0) <= 1e-5 * 10.0
+
+
+def test_rpchol_ngd_step_decreases_the_loss():
+    pr, th = inputs.small_problem(d=2, widths=[2, 6, 5, 1], n_int=30, n_bnd=10, seed=7)
+    th1, info = solve.ngd_step(pr, th, ell=20, mu=None, rtol=1e-10, maxit=400, seed=2, step=0, precond="rpchol",
+                               rpchol_block=5, mu_loss_coef=1e-4)
+    assert info.loss_after < info.loss_before
+    assert 1 <= info.ell_next <= 20
