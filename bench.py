@@ -505,11 +505,16 @@ def run_train(args, rank):
                 float(torch.sqrt((du ** 2).sum() + (dg ** 2).sum())) / norm_h1)
 
     theta = torch.tensor(thetas[0], device="cuda")
-    opts = dict(mu=None, mu_loss_coef=1e-4, ell_max=500, ell_delta=20, rtol=wl.rtol, maxit=20, sketch=args.sketch,
-                seed=0, test_matrix=args.test_matrix)
+    if args.precond == "rpchol":
+        # Alg. 5: rank found by block RPCholesky (20 pivots per round, at most 500), no rank rule
+        opts = dict(mu=None, mu_loss_coef=1e-4, precond="rpchol", rpchol_block=20, rtol=wl.rtol, maxit=20,
+                    sketch=args.sketch, seed=0)
+    else:
+        opts = dict(mu=None, mu_loss_coef=1e-4, ell_max=500, ell_delta=20, rtol=wl.rtol, maxit=20,
+                    sketch=args.sketch, seed=0, test_matrix=args.test_matrix)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
-    ell, total_ms, log, ells = wl.ell, 0.0, [], []
+    ell, total_ms, log, ells = (500 if args.precond == "rpchol" else wl.ell), 0.0, [], []
     l2, h1 = errors(theta)
     log.append({"step": 0, "seconds": 0.0, "ell": ell, "loss": None, "rel_l2": l2, "rel_h1": h1})
     for k in range(args.train_steps):
@@ -518,8 +523,9 @@ def run_train(args, rank):
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
-        ells.append(ell)
-        ell = info["ell_next"]
+        ells.append(info["ell_next"] if args.precond == "rpchol" else ell)
+        if args.precond != "rpchol":
+            ell = info["ell_next"]
         if (k + 1) % 10 == 0 or k + 1 == args.train_steps:
             l2, h1 = errors(theta)
             log.append({"step": k + 1, "seconds": total_ms / 1e3, "ell": ells[-1], "loss": info["loss_after"],
@@ -529,7 +535,8 @@ def run_train(args, rank):
             "steps": args.train_steps, "ms_per_step": total_ms / args.train_steps, "data": "synthetic",
             "config": {"workload": "poisson3d", "N": pr.n, "p": pr.p, "ell0": wl.ell, "ell_max": 500,
                        "ell_delta": 20, "mu": "max(10 eps lambda_1, 1e-4 L^2)", "pcg_maxit": 20,
-                       "sketch": args.sketch, "test_matrix": args.test_matrix, "eval_points": len(xe)},
+                       "sketch": args.sketch, "test_matrix": args.test_matrix, "precond": args.precond,
+                       "eval_points": len(xe)},
             "final": log[-1], "ell_trajectory": ells, "log": log}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -551,6 +558,9 @@ def main():
                     help="a NystromNGD training run (adaptive rank and damping) on the 3-D Poisson PINN, "
                          "--train-steps NGD steps, with L2/H1 errors every 10 steps")
     ap.add_argument("--train-steps", type=int, default=200)
+    ap.add_argument("--precond", default="nystrom", choices=["nystrom", "rpchol"],
+                    help="preconditioner in --train: NystromNGD (Alg. 4) or RPCholNGD (Alg. 5; the rank is the one "
+                         "block RPCholesky finds, at most 500)")
     ap.add_argument("--test-matrix", default="gaussian", choices=["gaussian", "sampling"],
                     help="test matrix of the Nystrom sketch in --train (sampling: columns drawn proportionally "
                          "to diag G)")

@@ -100,6 +100,20 @@ typedef struct {
  *                      ("NystromNGD Sampling", Sec. 5), see ngd_nystrom_sketch_sampled. */
 typedef enum { NGD_TEST_GAUSSIAN = 0, NGD_TEST_SAMPLING = 1 } ngd_test_matrix;
 
+/* Preconditioner of the NGD step:
+ * NGD_PRECOND_NYSTROM  randomized Nystrom (Alg. 4: sketch of rank ell, shift, thin SVD);
+ * NGD_PRECOND_RPCHOL   RPCholesky (Alg. 5): diag G, lambda_1 by four power-method steps
+ *                      (start vector: the Gaussian column with counter word 2^32 - 2), mu, block
+ *                      RPCholesky F of rank at most ell (rounds of rpchol_block pivots drawn i.i.d.
+ *                      proportionally to the residual diagonal, stopping when its sum is below
+ *                      mu p), P = F F^T + mu I.  Pivot k of round i is the winner of the race
+ *                      argmin_j -ln(u_j) / d_j with u_j from Philox at counter
+ *                      (j, 2^30 + i b + k, step); pivots are made unique per round.  P^{-1} is
+ *                      applied in its thin-SVD form (Eq. rpchol_svdprecond), equal to the Woodbury
+ *                      form of Eq. rpchol_precond; info->ell_next returns the rank found and
+ *                      info->lam1 the power-method estimate.  Needs the stored Jacobian. */
+typedef enum { NGD_PRECOND_NYSTROM = 0, NGD_PRECOND_RPCHOL = 1 } ngd_precond;
+
 typedef struct {
   int ell;                /* Nystrom rank (sketch size), 1 <= ell <= min(p, 2048) */
   double mu;              /* damping; mu <= 0 selects mu = gamma eps lambda_hat_1 (Alg. 4) */
@@ -119,6 +133,9 @@ typedef struct {
                              l_max >= 1 of ell_next */
   int ell_delta;          /* rank increase delta_l of Alg. 4 (the paper's runs: 20), >= 0 */
   int test_matrix;        /* ngd_test_matrix of the sketch (default NGD_TEST_GAUSSIAN) */
+  int precond;            /* ngd_precond (default NGD_PRECOND_NYSTROM) */
+  int rpchol_block;       /* RPCholNGD: pivots per round b (the paper: 20), 1 <= b <= ell; ell is the
+                             maximum rank l_max (<= 2047), rounds floor(ell / b) */
 } ngd_step_opts;
 
 typedef struct {
@@ -322,7 +339,7 @@ ngd_status ngd_batch_step(ngd_batch* batch, double* const* thetas, const ngd_ste
 /* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
  * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,
  * c1 1e-4, rho 0.5, 30 trials, mu_loss_coef 0, ell_max 0 (fixed rank), ell_delta 20,
- * Gaussian test matrix. */
+ * Gaussian test matrix, Nystrom preconditioner, rpchol_block 20. */
 void ngd_default_step_opts(ngd_step_opts* opts);
 
 #ifdef __cplusplus

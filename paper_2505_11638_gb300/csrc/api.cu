@@ -75,6 +75,7 @@ struct ngd_ctx {
   double* gdiag = nullptr;
   unsigned long long* samp_keys = nullptr;
   int* samp_idx = nullptr;
+  int* samp_count = nullptr;
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -82,7 +83,7 @@ struct ngd_ctx {
   cudaEvent_t ev[6] = {};
 };
 
-enum { kSLoss = 0, kSFrob2 = 1, kSNu = 2, kSMu = 3, kSDot = 4, kSCount = 8 };
+enum { kSLoss = 0, kSFrob2 = 1, kSNu = 2, kSMu = 3, kSDot = 4, kSLam1 = 5, kSTrace = 6, kSCount = 8 };
 // factor attempts of ngd_step: the shift nu times 1, 8, 64, ... on NOT_SPD
 constexpr int kShiftAttempts = 6;
 
@@ -397,6 +398,7 @@ ngd_status ensure_sampling(ngd_ctx* ctx) {
   TRY(dalloc(ctx, &ctx->gdiag, (size_t)ctx->p * 8));
   TRY(dalloc(ctx, &ctx->samp_keys, (size_t)ctx->p * 8));
   TRY(dalloc(ctx, &ctx->samp_idx, (size_t)2048 * sizeof(int)));
+  TRY(dalloc(ctx, &ctx->samp_count, sizeof(int)));
   // valid indices before the first selection: a failed selection leaves them in place
   CK(cudaMemsetAsync(ctx->samp_idx, 0, (size_t)2048 * sizeof(int), ctx->stream));
   return NGD_OK;
@@ -773,6 +775,151 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   return pcg_result(ctx, h, iters, relres);
 }
 
+// RPCholNGD preconditioner (Alg. 5) at the current linearization (stored J): diag G, lambda_1 by
+// four power-method steps (start: the Gaussian column with word 2^32 - 2), mu (into scal[kSMu]),
+// block RPCholesky (rounds of o->rpchol_block pivots, at most o->ell columns, stopping when the
+// residual trace is below mu p), then the thin SVD F = U Sigma V^T by eig(F^T F) in FP64, so that
+// P^{-1} = U (Sigma^2 + mu I)^{-1} U^T + mu^{-1} (I - U U^T) (Eq. rpchol_svdprecond), which equals
+// the Woodbury form (Eq. rpchol_precond).  It is handed to pCG as a Nystrom-form preconditioner
+// with lambda = Sigma^2 and one appended zero column and eigenvalue, whose scaled form mu times
+// the above: *ell_pc = rank + 1 (0 when no column was found: P = mu I).  Outputs: U (FP64, ld ldP)
+// in *Uout, rank, lambda_1.
+template <typename T>
+ngd_status rpchol_build(ngd_ctx* ctx, const ngd_step_opts* o, int* ell_pc, int* rank, double* lam1_out,
+                        const double** Uout) {
+  const int64_t p = ctx->p, ld = ctx->ldP;
+  const int b = o->rpchol_block, t = o->ell / o->rpchol_block;
+  const bool f32 = std::is_same<T, float>::value;
+  if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "RPCholNGD needs the stored Jacobian%s");
+  TRY(ensure_ell(ctx, o->ell + 1));
+  TRY(ensure_sampling(ctx));
+  TRY(ensure_gpart(ctx, (size_t)o->ell * b));
+  double* F = f32 ? ctx->B64 : (double*)ctx->B;         // p x ell
+  double* Cb = f32 ? ctx->Y64 : (double*)ctx->Y;        // p x b residual block
+  double* Zb = f32 ? ctx->Zw64 : (double*)ctx->Zw;      // N x b: diag(w) J[:, S']
+  double* Uo = f32 ? ctx->U64 : (double*)ctx->U;
+  cudaStream_t st = ctx->stream;
+  TRY(clear_status(ctx));
+  TRY(gram_diag_internal<T>(ctx, ctx->gdiag));
+  // lambda_1: four steps of the power method, v in z, G v in q
+  double* v = ctx->z;
+  double* w = ctx->q;
+  launch_philox_column(v, p, 0xFFFFFFFEu, o->seed, o->step, st);
+  launch_dot(v, v, p, ctx->part, ctx->scal + kSDot, st);
+  launch_scale_rsqrt(v, ctx->scal + kSDot, v, p, st);
+  for (int it = 0; it < 4; ++it) {
+    TRY(gv_current<T>(ctx, v, 0.0, nullptr, w, nullptr));
+    launch_dot(v, w, p, ctx->part, ctx->scal + kSLam1, st);
+    launch_dot(w, w, p, ctx->part, ctx->scal + kSDot, st);
+    launch_scale_rsqrt(w, ctx->scal + kSDot, v, p, st);
+  }
+  launch_set_mu(ctx->scal + kSLam1, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, st);
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double mu = ctx->h_scal[kSMu];
+  *lam1_out = ctx->h_scal[kSLam1];
+  if (!(mu > 0.0) || !std::isfinite(mu)) return set_err(ctx, NGD_ERR_NONFINITE, "RPCholNGD: mu is not positive%s");
+  const double eps = mu * (double)p;
+  double trace = 0.0;
+  {
+    std::vector<double> dh((size_t)p);
+    CK(cudaMemcpyAsync(dh.data(), ctx->gdiag, (size_t)p * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (double x : dh) trace += x > 0.0 ? x : 0.0;
+  }
+  int r = 0;
+  for (int i = 0; i < t && trace >= eps; ++i) {
+    launch_rpchol_pivots(ctx->gdiag, p, b, i, o->seed, o->step, ctx->perm, ctx->samp_idx, ctx->samp_count, st);
+    CK(cudaMemcpyAsync(ctx->h_int, ctx->samp_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int nsel = ctx->h_int[0];
+    if (nsel <= 0) break;
+    // C = G[:, S'] - F F[S', :]^T
+    if (f32) {
+      launch_gather_cols<float, double>((const float*)ctx->J, ctx->ldJ, ctx->N, ctx->samp_idx, nsel, ctx->ps.w, Zb, st);
+      GemmDfArgs<float, double> g;
+      g.M = p; g.N = nsel; g.K = ctx->N;
+      g.A = (const float*)ctx->J; g.sam = 1; g.sak = ctx->ldJ;
+      g.B = Zb; g.sbk = nsel; g.sbn = 1;
+      g.out64 = Cb; g.scm = 1; g.scn = ld;
+      launch_gemm_df<float, double>(g, st);
+    } else {
+      launch_gather_cols<double, double>((const double*)ctx->J, ctx->ldJ, ctx->N, ctx->samp_idx, nsel, ctx->ps.w, Zb,
+                                         st);
+      GemmArgs<double> g;
+      g.M = p; g.N = nsel; g.K = ctx->N;
+      g.A = (const double*)ctx->J; g.sam = 1; g.sak = ctx->ldJ;
+      g.B = Zb; g.sbk = nsel; g.sbn = 1;
+      g.outT = Cb; g.scm = 1; g.scn = ld;
+      launch_gemm<double>(g, st);
+    }
+    if (r > 0) {
+      launch_gather_rows_neg(F, ld, ctx->samp_idx, nsel, r, ctx->gpart, st);
+      GemmDfArgs<double, double> g;
+      g.M = p; g.N = nsel; g.K = r;
+      g.A = F; g.sam = 1; g.sak = ld;
+      g.B = ctx->gpart; g.sbk = 1; g.sbn = r;
+      g.out64 = Cb; g.scm = 1; g.scn = ld;
+      g.accumulate = 1;
+      launch_gemm_df<double, double>(g, st);
+    }
+    // R = chol(C[S', S']); new columns C R^{-1}; a pivot block that is not positive definite ends
+    // the factorization with the columns found so far
+    launch_pivot_block(Cb, ld, ctx->samp_idx, nsel, ctx->M, st);
+    CK(launch_cholesky(ctx->M, nsel, ctx->status, st));
+    CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->h_int[0] & kStatNotSpd) {
+      CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+      break;
+    }
+    double* Fn = F + (int64_t)r * ld;
+    CK(cudaMemcpy2DAsync(Fn, (size_t)ld * 8, Cb, (size_t)ld * 8, (size_t)p * 8, nsel, cudaMemcpyDeviceToDevice, st));
+    launch_trsm_lt<double>(Fn, ld, p, nsel, ctx->M, ctx->A1, st);
+    const int nb = launch_rpchol_diag(ctx->gdiag, Fn, ld, p, nsel, ctx->samp_idx, ctx->part, st);
+    launch_sum_partials(ctx->part, nb, 1.0, ctx->scal + kSTrace, st);
+    CK(cudaMemcpyAsync(ctx->h_scal + kSTrace, ctx->scal + kSTrace, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    trace = ctx->h_scal[kSTrace];
+    r += nsel;
+  }
+  *rank = r;
+  *Uout = Uo;
+  if (r == 0) {
+    *ell_pc = 0;
+    return check_launch(ctx);
+  }
+  // thin SVD of F by eig(F^T F)
+  {
+    GemmDfArgs<double, double> g;
+    g.M = r; g.N = r; g.K = p;
+    g.A = F; g.sam = ld; g.sak = 1;
+    g.B = F; g.sbk = 1; g.sbn = ld;
+    g.nsplit = choose_splits(r, r, p);
+    const int nz = split_count(g.K, g.nsplit);
+    TRY(ensure_gpart(ctx, (size_t)nz * r * r));
+    g.out64 = ctx->gpart; g.split_stride = (int64_t)r * r; g.scm = 1; g.scn = r;
+    launch_gemm_df<double, double>(g, st);
+    launch_sum_splits(ctx->gpart, nz, (int64_t)r * r, (int64_t)r * r, ctx->V, st);
+  }
+  launch_symmetrize(ctx->V, r, st);
+  CK(launch_sym_eig(ctx->V, r, ctx->sig2, ctx->M, ctx->eigws, ctx->status, st));
+  launch_rpchol_lambda(ctx->sig2, r, ctx->lam, ctx->inv_sigma, st);
+  {
+    GemmDfArgs<double, double> g;                                                      // U = F V Sigma^{-1}
+    g.M = p; g.N = r; g.K = r;
+    g.A = F; g.sam = 1; g.sak = ld;
+    g.B = ctx->M; g.sbk = 1; g.sbn = r;
+    g.out64 = Uo; g.scm = 1; g.scn = ld;
+    g.colscale = ctx->inv_sigma;
+    launch_gemm_df<double, double>(g, st);
+  }
+  CK(cudaMemsetAsync(Uo + (int64_t)r * ld, 0, (size_t)ld * 8, st));                  // the appended column
+  *ell_pc = r + 1;
+  TRY(check_launch(ctx));
+  return sync_status(ctx);
+}
+
 template <typename T>
 ngd_status loss_at(ngd_ctx* ctx, const double* theta, double* loss_host) {
   TRY(prep_theta<T>(ctx, theta));
@@ -820,30 +967,46 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   launch_mul(ctx->ps.w, ctx->r, ctx->svec, ctx->N, ctx->stream);
   TRY(vjp_current<T>(ctx, ctx->svec, ctx->g, true));
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-  phase.next("sketch");
-  // Alg. 4, randomized Nystrom (App. A): fresh Omega from (seed, step)
-  TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch, o->test_matrix));
-  CK(cudaEventRecord(ctx->ev[2], ctx->stream));
-  phase.next("factor");
-  double scale = 1.0;
-  ngd_status fs = NGD_OK;
-  for (int attempt = 0; attempt < kShiftAttempts; ++attempt) {
-    fs = factor_internal<T>(ctx, o->ell, o->sketch, scale);
-    if (fs != NGD_ERR_NOT_SPD) break;
-    inf.shift_retries++;
-    scale *= 8.0;
+  const bool rpchol = o->precond == NGD_PRECOND_RPCHOL;
+  int ell_pc = o->ell, rp_rank = 0;
+  double rp_lam1 = 0.0;
+  bool u_f64 = true;
+  const void* Ust = nullptr;               // taken after the factor: the workspace grows on demand
+  if (rpchol) {
+    // Alg. 5: RPCholesky preconditioner (its mu comes from the power-method lambda_1)
+    phase.next("rpchol");
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    const double* Urp = nullptr;
+    TRY(rpchol_build<T>(ctx, o, &ell_pc, &rp_rank, &rp_lam1, &Urp));
+    Ust = Urp;
+    u_f64 = true;
+    CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+  } else {
+    phase.next("sketch");
+    // Alg. 4, randomized Nystrom (App. A): fresh Omega from (seed, step)
+    TRY(sketch_internal<T>(ctx, o->ell, o->seed, o->step, o->sketch, o->test_matrix));
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    phase.next("factor");
+    double scale = 1.0;
+    ngd_status fs = NGD_OK;
+    for (int attempt = 0; attempt < kShiftAttempts; ++attempt) {
+      fs = factor_internal<T>(ctx, o->ell, o->sketch, scale);
+      if (fs != NGD_ERR_NOT_SPD) break;
+      inf.shift_retries++;
+      scale *= 8.0;
+    }
+    if (fs != NGD_OK) return fs;
+    CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+    // Alg. 4, damping: mu fixed, gamma eps lambda_1, or the Sec. 5 maximum with c L^2
+    launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, ctx->stream);
+    u_f64 = !std::is_same<T, float>::value || o->sketch == NGD_SKETCH_F64;
+    Ust = std::is_same<T, float>::value && o->sketch == NGD_SKETCH_F64 ? (const void*)ctx->U64 : ctx->U;
   }
-  if (fs != NGD_OK) return fs;
-  CK(cudaEventRecord(ctx->ev[3], ctx->stream));
   phase.next("pcg");
-  // Alg. 4, damping: mu fixed, gamma eps lambda_1, or the Sec. 5 maximum with c L^2
-  launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, ctx->stream);
-  // Alg. 3, direction: pCG on (G + mu I) d = g with the Nystrom preconditioner of Alg. 4
+  // Alg. 3, direction: pCG on (G + mu I) d = g with the preconditioner of Alg. 4 or Alg. 5
   int iters = 0;
   double relres = 0.0;
-  const bool u_f64 = !std::is_same<T, float>::value || o->sketch == NGD_SKETCH_F64;
-  const void* Ust = std::is_same<T, float>::value && o->sketch == NGD_SKETCH_F64 ? (const void*)ctx->U64 : ctx->U;
-  TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, o->ell, o->rtol, o->maxit,
+  TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, ell_pc, o->rtol, o->maxit,
                       ctx->d, &iters, &relres));
   CK(cudaEventRecord(ctx->ev[4], ctx->stream));
   phase.next("linesearch");
@@ -851,14 +1014,24 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   launch_dot(ctx->g, ctx->d, p, ctx->part, ctx->scal + kSDot, ctx->stream);
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  const double L0 = ctx->h_scal[kSLoss], slope = ctx->h_scal[kSDot], mu = ctx->h_scal[kSMu], nu = ctx->h_scal[kSNu];
-  std::vector<double> lam_all((size_t)o->ell);
-  CK(cudaMemcpyAsync(lam_all.data(), ctx->lam, (size_t)o->ell * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  const double lam_h[2] = {lam_all[0], lam_all[(size_t)o->ell - 1]};
-  // Alg. 4: rank of the next step's sketch
+  const double L0 = ctx->h_scal[kSLoss], slope = ctx->h_scal[kSDot], mu = ctx->h_scal[kSMu];
+  const double nu = rpchol ? 0.0 : ctx->h_scal[kSNu];
+  std::vector<double> lam_all((size_t)std::max(ell_pc, 1), 0.0);
+  if (ell_pc > 0) {
+    CK(cudaMemcpyAsync(lam_all.data(), ctx->lam, (size_t)ell_pc * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  double lam_h[2] = {lam_all[0], lam_all[(size_t)std::max(ell_pc, 1) - 1]};
   int ell_next = o->ell;
-  if (o->ell_max > 0) {
+  if (rpchol) {
+    // lambda_1 from the power method; the smallest kept sigma^2 of F; the rank RPCholesky found
+    lam_h[0] = rp_lam1;
+    lam_h[1] = 0.0;
+    for (int i = 0; i + 1 < ell_pc; ++i)
+      if (lam_all[(size_t)i] > 0.0) lam_h[1] = lam_all[(size_t)i];
+    ell_next = rp_rank;
+  } else if (o->ell_max > 0) {
+    // Alg. 4: rank of the next step's sketch
     if (lam_h[1] > 10.0 * mu) {
       ell_next = std::min(o->ell + o->ell_delta, o->ell_max);
     } else {
@@ -937,6 +1110,8 @@ void ngd_default_step_opts(ngd_step_opts* o) {
   o->ell_max = 0;
   o->ell_delta = 20;
   o->test_matrix = 0;
+  o->precond = 0;
+  o->rpchol_block = 20;
 }
 
 ngd_status ngd_create(const ngd_problem_desc* desc, ngd_ctx** out) {
@@ -1087,7 +1262,7 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
                  ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64, ctx->Uh, ctx->Ul,
                  ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf, ctx->gdiag,
-                 ctx->samp_keys, ctx->samp_idx};
+                 ctx->samp_keys, ctx->samp_idx, ctx->samp_count};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -1350,7 +1525,8 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
   if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
       !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1 ||
       !(o->mu_loss_coef >= 0.0) || o->ell_max < 0 || o->ell_max > std::min<int64_t>(ctx->p, 2048) ||
-      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1)
+      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1 || o->precond < 0 || o->precond > 1 ||
+      (o->precond == NGD_PRECOND_RPCHOL && (o->rpchol_block < 1 || o->rpchol_block > o->ell || o->ell > 2047)))
     return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
   if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");

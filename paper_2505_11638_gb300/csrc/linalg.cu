@@ -845,6 +845,181 @@ template void launch_gather_cols<float, float>(const float*, int64_t, int64_t, c
 template void launch_gather_cols<double, double>(const double*, int64_t, int64_t, const int*, int, const double*,
                                                  double*, cudaStream_t);
 
+// ---------------------------------------------------------------------------- RPCholesky (App. B, Alg. 5)
+// Gaussian vector v (p) from the test-matrix generator with column word `word` (rows 2m, 2m+1 from
+// counter (m, word, step_lo, step_hi)): the power method's start vector uses word 2^32 - 2.
+__global__ void k_philox_column(double* __restrict__ v, int64_t p, uint32_t word, uint64_t seed, uint64_t step) {
+  const int64_t npairs = (p + 1) / 2;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < npairs; m += st) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)m, word, (uint32_t)step, (uint32_t)(step >> 32)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u1 = uniform52(x.x, x.y), u2 = uniform52(x.z, x.w);
+    const double rr = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    v[2 * m] = rr * cs;
+    if (2 * m + 1 < p) v[2 * m + 1] = rr * sn;
+  }
+}
+void launch_philox_column(double* v, int64_t p, uint32_t word, uint64_t seed, uint64_t step, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(((p + 1) / 2 + 255) / 256, 1024);
+  k_philox_column<<<blocks, 256, 0, s>>>(v, p, word, seed, step); note_launch();
+}
+
+// dst = src / sqrt(*ss)
+__global__ void k_scale_rsqrt(const double* __restrict__ src, const double* __restrict__ ss, double* __restrict__ dst,
+                              int64_t n) {
+  const double f = 1.0 / sqrt(*ss);
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) dst[i] = src[i] * f;
+}
+void launch_scale_rsqrt(const double* src, const double* ss, double* dst, int64_t n, cudaStream_t s) {
+  k_scale_rsqrt<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(src, ss, dst, n); note_launch();
+}
+
+// Round rnd of block RPCholesky: sample k (block k) is the winner of the race
+// argmin_j -ln(u_jk) / d_j, u_jk from the counter (j, 2^30 + rnd b + k, step_lo, step_hi); ties to
+// the smaller j.  piv[k] = -1 when every d_j <= 0.
+__global__ void __launch_bounds__(256) k_rpchol_pivots(const double* __restrict__ d, int64_t p, int b, int rnd,
+                                                       uint64_t seed, uint64_t step, int* __restrict__ piv) {
+  __shared__ unsigned long long sk[256];
+  __shared__ long long sj[256];
+  const int k = blockIdx.x;
+  const uint32_t word = (1u << 30) + (uint32_t)(rnd * b + k);
+  unsigned long long best = ~0ull;
+  long long bj = -1;
+  for (int64_t j = threadIdx.x; j < p; j += blockDim.x) {
+    const double dj = d[j];
+    if (!(dj > 0.0) || !isfinite(dj)) continue;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, word, (uint32_t)step, (uint32_t)(step >> 32)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const unsigned long long key = (unsigned long long)__double_as_longlong(-log(uniform52(x.x, x.y)) / dj);
+    if (key < best) {                       // j increases: the first of equal keys is kept
+      best = key;
+      bj = j;
+    }
+  }
+  sk[threadIdx.x] = best;
+  sj[threadIdx.x] = bj;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const unsigned long long k2 = sk[threadIdx.x + o];
+      const long long j2 = sj[threadIdx.x + o];
+      if (j2 >= 0 && (sj[threadIdx.x] < 0 || k2 < sk[threadIdx.x] || (k2 == sk[threadIdx.x] && j2 < sj[threadIdx.x]))) {
+        sk[threadIdx.x] = k2;
+        sj[threadIdx.x] = j2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) piv[k] = (int)sj[0];
+}
+
+// The b pivots of a round made unique and increasing (piv < 0 dropped); count written to *nsel.
+__global__ void k_unique_pivots(const int* __restrict__ piv, int b, int* __restrict__ sel, int* __restrict__ nsel) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int n = 0;
+  for (int k = 0; k < b; ++k) {
+    const int v = piv[k];
+    if (v < 0) continue;
+    int pos = n;
+    bool dup = false;
+    for (int i = 0; i < n; ++i) {
+      if (sel[i] == v) { dup = true; break; }
+      if (sel[i] > v) { pos = i; break; }
+    }
+    if (dup) continue;
+    for (int i = n; i > pos; --i) sel[i] = sel[i - 1];
+    sel[pos] = v;
+    ++n;
+  }
+  *nsel = n;
+}
+
+void launch_rpchol_pivots(const double* d, int64_t p, int b, int rnd, uint64_t seed, uint64_t step, int* piv,
+                          int* sel, int* nsel, cudaStream_t s) {
+  k_rpchol_pivots<<<b, 256, 0, s>>>(d, p, b, rnd, seed, step, piv); note_launch();
+  k_unique_pivots<<<1, 32, 0, s>>>(piv, b, sel, nsel); note_launch();
+}
+
+// Fs[k + n r] = -F[sel_n, k] (r x nsel, column-major): minus the pivot rows of F, transposed
+__global__ void k_gather_rows_neg(const double* __restrict__ F, int64_t ld, const int* __restrict__ sel, int nsel, int r,
+                                  double* __restrict__ Fs) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * nsel) return;
+  const int k = e % r, n = e / r;
+  Fs[e] = -F[(int64_t)sel[n] + (int64_t)k * ld];
+}
+void launch_gather_rows_neg(const double* F, int64_t ld, const int* sel, int nsel, int r, double* Fs, cudaStream_t s) {
+  if (r <= 0 || nsel <= 0) return;
+  k_gather_rows_neg<<<(r * nsel + 255) / 256, 256, 0, s>>>(F, ld, sel, nsel, r, Fs); note_launch();
+}
+
+// M = sym(C[sel, :]) (nsel x nsel, column-major) of the p x nsel residual block C (ld)
+__global__ void k_pivot_block(const double* __restrict__ C, int64_t ld, const int* __restrict__ sel, int nsel,
+                              double* __restrict__ M) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nsel * nsel) return;
+  const int a = e % nsel, c = e / nsel;
+  M[e] = 0.5 * (C[(int64_t)sel[a] + (int64_t)c * ld] + C[(int64_t)sel[c] + (int64_t)a * ld]);
+}
+void launch_pivot_block(const double* C, int64_t ld, const int* sel, int nsel, double* M, cudaStream_t s) {
+  k_pivot_block<<<(nsel * nsel + 255) / 256, 256, 0, s>>>(C, ld, sel, nsel, M); note_launch();
+}
+
+// d_j <- max(0, d_j - sum_k F_new[j, k]^2), 0 on the pivots; block partial sums of the new d in part
+__global__ void k_rpchol_diag(double* __restrict__ d, const double* __restrict__ Fn, int64_t ld, int64_t p, int nsel,
+                              const int* __restrict__ sel, double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += st) {
+    double s2 = 0.0;
+    bool piv = false;
+    for (int k = 0; k < nsel; ++k) {
+      const double f = Fn[j + (int64_t)k * ld];
+      s2 += f * f;
+      piv |= sel[k] == (int)j;
+    }
+    const double v = piv ? 0.0 : fmax(0.0, d[j] - s2);
+    d[j] = v;
+    acc += v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+int launch_rpchol_diag(double* d, const double* Fn, int64_t ld, int64_t p, int nsel, const int* sel, double* part,
+                       cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((p + 255) / 256, 256);
+  k_rpchol_diag<<<blocks, 256, 0, s>>>(d, Fn, ld, p, nsel, sel, part); note_launch();
+  return blocks;
+}
+
+// lam_k = sigma_k^2 of F (descending) where sigma_k^2 > 2^-40 sigma_1^2, else 0 (that direction is
+// left to the mu part of P); inv_sigma_k = 1 / sigma_k for the kept ones, 0 otherwise; lam[r] = 0.
+__global__ void k_rpchol_lambda(const double* __restrict__ sig2, int r, double* __restrict__ lam,
+                                double* __restrict__ inv_sigma) {
+  const double top = r > 0 ? sig2[0] : 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= r; k += gridDim.x * blockDim.x) {
+    const double s2 = k < r ? sig2[k] : 0.0;
+    const bool keep = s2 > 0x1p-40 * top && s2 > 0.0;
+    lam[k] = keep ? s2 : 0.0;
+    inv_sigma[k] = keep ? 1.0 / sqrt(s2) : 0.0;
+  }
+}
+void launch_rpchol_lambda(const double* sig2, int r, double* lam, double* inv_sigma, cudaStream_t s) {
+  k_rpchol_lambda<<<(r + 1 + 255) / 256, 256, 0, s>>>(sig2, r, lam, inv_sigma); note_launch();
+}
+
 // ---------------------------------------------------------------------------- SIMT GEMM
 // C(m, n) = sum_k A(m, k) B(k, n) with element strides; A(m,k) = A[m*sam + k*sak],
 // B(k,n) = B[k*sbk + n*sbn].  64x64 tiles, 16-deep K slices, 4x4 per thread.

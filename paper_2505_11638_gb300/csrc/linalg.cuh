@@ -55,6 +55,16 @@ template <typename T> void launch_selection_omega(T* Om, int64_t ld, const int* 
 template <typename T, typename TO>
 void launch_gather_cols(const T* J, int64_t ldJ, int64_t N, const int* idx, int ell, const double* w, TO* Zw,
                         cudaStream_t s);
+// RPCholesky (block variant) and the power method
+void launch_philox_column(double* v, int64_t p, uint32_t word, uint64_t seed, uint64_t step, cudaStream_t s);
+void launch_scale_rsqrt(const double* src, const double* ss, double* dst, int64_t n, cudaStream_t s);
+void launch_rpchol_pivots(const double* d, int64_t p, int b, int rnd, uint64_t seed, uint64_t step, int* piv,
+                          int* sel, int* nsel, cudaStream_t s);
+void launch_gather_rows_neg(const double* F, int64_t ld, const int* sel, int nsel, int r, double* Fs, cudaStream_t s);
+void launch_pivot_block(const double* C, int64_t ld, const int* sel, int nsel, double* M, cudaStream_t s);
+int launch_rpchol_diag(double* d, const double* Fn, int64_t ld, int64_t p, int nsel, const int* sel, double* part,
+                       cudaStream_t s);
+void launch_rpchol_lambda(const double* sig2, int r, double* lam, double* inv_sigma, cudaStream_t s);
 
 
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);

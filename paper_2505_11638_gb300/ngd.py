@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_SPD", 5:
 DTYPES = {"f64": 0, "f32": 1}
 SKETCH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
 TEST_MATRIX = {"gaussian": 0, "sampling": 1}
+PRECOND = {"nystrom": 0, "rpchol": 1}
 PDES = {"poisson": 0, "heat": 1}
 GV_MODES = {"auto": 0, "stored": 1, "matrix_free": 2}
 
@@ -51,7 +52,8 @@ class StepOpts(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("sketch", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64), ("armijo_c1", ctypes.c_double),
                 ("armijo_rho", ctypes.c_double), ("armijo_max", ctypes.c_int), ("mu_loss_coef", ctypes.c_double),
-                ("ell_max", ctypes.c_int), ("ell_delta", ctypes.c_int), ("test_matrix", ctypes.c_int)]
+                ("ell_max", ctypes.c_int), ("ell_delta", ctypes.c_int), ("test_matrix", ctypes.c_int),
+                ("precond", ctypes.c_int), ("rpchol_block", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -382,6 +384,8 @@ class Context:
                 v = SKETCH[v]
             if k == "test_matrix":
                 v = TEST_MATRIX[v]
+            if k == "precond":
+                v = PRECOND[v]
             if k == "mu" and v is None:
                 v = 0.0
             setattr(o, k, v)

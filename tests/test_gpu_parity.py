@@ -584,3 +584,39 @@ def test_sampling_rejects_too_few_positive_diagonal_entries(ngd):
         ctx.nystrom_sketch_sampled(dev(th), ell, seed=1, step=0)
     assert e.value.name == "INVALID_ARG"
     ctx.close()
+
+
+@pytest.mark.parametrize("mu", [1e-6, None])
+def test_rpchol_step_matches_oracle(ngd, mu):
+    """One RPCholNGD step (Alg. 5): the power-method lambda_1, mu, the rank block RPCholesky finds
+    (same pivot races on the FP64 residual diagonal) and the update agree with the oracle step at
+    the GPU's PCG iteration count."""
+    pr, th = small(SMALL[0], seed=90)
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    kw = dict(ell=24, rpchol_block=6, mu=mu, mu_loss_coef=1e-4 if mu is None else 0.0)
+    info = ctx.step(t, precond="rpchol", rtol=1e-10, maxit=500, seed=4, step=1, sketch="f64", **kw)
+    th1_o, info_o = solve.ngd_step(pr, th, rtol=0.0, maxit=info["pcg_iters"], seed=4, step=1, precond="rpchol", **kw)
+    assert info["loss_after"] < info["loss_before"]
+    assert info["lam1"] == pytest.approx(info_o.lam1, rel=1e-10)
+    assert info["mu"] == pytest.approx(info_o.mu, rel=1e-10)
+    assert info["ell_next"] == info_o.ell_next
+    assert rel(host(t) - th, th1_o - th) <= 1e-6
+    ctx.close()
+
+
+def test_rpchol_step_fp32_context(ngd):
+    """RPCholNGD in an FP32 context (FP64-accurate columns of G and FP64 F): the step solves to the
+    requested tolerance, decreases the loss and finds the oracle's rank within one block."""
+    pr, th = inputs.small_problem(d=3, widths=[3, 24, 24, 1], n_int=600, n_bnd=150, seed=91)
+    ctx = ngd.Context(pr, dtype="f32")
+    t = dev(th)
+    info = ctx.step(t, precond="rpchol", ell=60, rpchol_block=10, mu=1e-6, rtol=1e-7, maxit=2000, seed=2, step=0,
+                    sketch="f64")
+    _, info_o = solve.ngd_step(pr, th, ell=60, rpchol_block=10, mu=1e-6, rtol=1e-7, maxit=2000, seed=2, step=0,
+                               precond="rpchol")
+    assert info["relres"] <= 1e-7
+    assert info["loss_after"] < info["loss_before"]
+    assert info["lam1"] == pytest.approx(info_o.lam1, rel=1e-4)
+    assert abs(info["ell_next"] - info_o.ell_next) <= 10
+    ctx.close()
