@@ -505,7 +505,10 @@ def run_train(args, rank):
                 float(torch.sqrt((du ** 2).sum() + (dg ** 2).sum())) / norm_h1)
 
     theta = torch.tensor(thetas[0], device="cuda")
-    if args.precond == "rpchol":
+    if args.precond == "full":
+        # Alg. 2: the direction by Cholesky of the explicit G + mu I (no preconditioner, no pCG)
+        opts = dict(mu=None, mu_loss_coef=1e-4, precond="full", sketch=args.sketch, seed=0)
+    elif args.precond == "rpchol":
         # Alg. 5: rank found by block RPCholesky (20 pivots per round, at most 500), no rank rule
         opts = dict(mu=None, mu_loss_coef=1e-4, precond="rpchol", rpchol_block=20, rtol=wl.rtol, maxit=20,
                     sketch=args.sketch, seed=0)
@@ -514,7 +517,7 @@ def run_train(args, rank):
                     sketch=args.sketch, seed=0, test_matrix=args.test_matrix)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
-    ell, total_ms, log, ells = (500 if args.precond == "rpchol" else wl.ell), 0.0, [], []
+    ell, total_ms, log, ells = (500 if args.precond == "rpchol" else 1 if args.precond == "full" else wl.ell), 0.0, [], []
     l2, h1 = errors(theta)
     log.append({"step": 0, "seconds": 0.0, "ell": ell, "loss": None, "rel_l2": l2, "rel_h1": h1})
     for k in range(args.train_steps):
@@ -523,8 +526,8 @@ def run_train(args, rank):
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
-        ells.append(info["ell_next"] if args.precond == "rpchol" else ell)
-        if args.precond != "rpchol":
+        ells.append(info["ell_next"] if args.precond == "rpchol" else 0 if args.precond == "full" else ell)
+        if args.precond == "nystrom":
             ell = info["ell_next"]
         if (k + 1) % 10 == 0 or k + 1 == args.train_steps:
             l2, h1 = errors(theta)
@@ -558,9 +561,9 @@ def main():
                     help="a NystromNGD training run (adaptive rank and damping) on the 3-D Poisson PINN, "
                          "--train-steps NGD steps, with L2/H1 errors every 10 steps")
     ap.add_argument("--train-steps", type=int, default=200)
-    ap.add_argument("--precond", default="nystrom", choices=["nystrom", "rpchol"],
-                    help="preconditioner in --train: NystromNGD (Alg. 4) or RPCholNGD (Alg. 5; the rank is the one "
-                         "block RPCholesky finds, at most 500)")
+    ap.add_argument("--precond", default="nystrom", choices=["nystrom", "rpchol", "full"],
+                    help="direction method in --train: NystromNGD (Alg. 4), RPCholNGD (Alg. 5; the rank is the one "
+                         "block RPCholesky finds, at most 500) or NGD full (Alg. 2: Cholesky of the explicit Gramian)")
     ap.add_argument("--test-matrix", default="gaussian", choices=["gaussian", "sampling"],
                     help="test matrix of the Nystrom sketch in --train (sampling: columns drawn proportionally "
                          "to diag G)")

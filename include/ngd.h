@@ -100,7 +100,7 @@ typedef struct {
  *                      ("NystromNGD Sampling", Sec. 5), see ngd_nystrom_sketch_sampled. */
 typedef enum { NGD_TEST_GAUSSIAN = 0, NGD_TEST_SAMPLING = 1 } ngd_test_matrix;
 
-/* Preconditioner of the NGD step:
+/* Direction method of the NGD step:
  * NGD_PRECOND_NYSTROM  randomized Nystrom (Alg. 4: sketch of rank ell, shift, thin SVD);
  * NGD_PRECOND_RPCHOL   RPCholesky (Alg. 5): diag G, lambda_1 by four power-method steps
  *                      (start vector: the Gaussian column with counter word 2^32 - 2), mu, block
@@ -111,8 +111,12 @@ typedef enum { NGD_TEST_GAUSSIAN = 0, NGD_TEST_SAMPLING = 1 } ngd_test_matrix;
  *                      (j, 2^30 + i b + k, step); pivots are made unique per round.  P^{-1} is
  *                      applied in its thin-SVD form (Eq. rpchol_svdprecond), equal to the Woodbury
  *                      form of Eq. rpchol_precond; info->ell_next returns the rank found and
- *                      info->lam1 the power-method estimate.  Needs the stored Jacobian. */
-typedef enum { NGD_PRECOND_NYSTROM = 0, NGD_PRECOND_RPCHOL = 1 } ngd_precond;
+ *                      info->lam1 the power-method estimate.  Needs the stored Jacobian.
+ * NGD_DIRECT_FULL      no preconditioner and no pCG: NGD full (Alg. 2), the explicit Gramian
+ *                      G = J^T (w .* J) (FP64-accurate), lambda_1 by the same power method, mu,
+ *                      the FP64 Cholesky G + mu I = L L^T and d = L^{-T} L^{-1} g.  ell is unused;
+ *                      needs the stored Jacobian and p^2 float64 of device memory. */
+typedef enum { NGD_PRECOND_NYSTROM = 0, NGD_PRECOND_RPCHOL = 1, NGD_DIRECT_FULL = 2 } ngd_precond;
 
 typedef struct {
   int ell;                /* Nystrom rank (sketch size), 1 <= ell <= min(p, 2048) */

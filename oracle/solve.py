@@ -105,6 +105,8 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
     iterations (for comparisons at a fixed iteration count).  ell_max > 0 applies the rank rule
     of Alg. 4 to the returned info.ell_next (otherwise ell_next = ell).  test_matrix "sampling"
     draws Omega = I[:, S] with S sampled proportionally to diag G (Sec. 3 and Sec. 5).
+    precond "full" takes the direction of NGD full instead (Alg. 2): the explicit G, lambda_1 by four
+    power-method steps, mu, Cholesky of G + mu I and two triangular solves (no pCG, ell unused).
     precond "rpchol" builds the RPCholNGD preconditioner instead (Alg. 5): diag G, lambda_1 by four
     power-method steps, mu, block RPCholesky of rank at most ell (blocks of rpchol_block, stopping
     when the trace of the residual is below mu p), P^{-1} by Woodbury (Eq. rpchol_precond);
@@ -113,6 +115,8 @@ def ngd_step(problem, theta, ell, mu, rtol, maxit, seed, step, mant_bits=52, gam
     if precond == "rpchol":
         return _rpchol_step(problem, theta, ell, mu, rtol, maxit, seed, step, gamma, c1, rho, max_trials,
                             return_parts, mu_loss_coef, rpchol_block)
+    if precond == "full":
+        return _full_step(problem, theta, mu, seed, step, gamma, c1, rho, max_trials, return_parts, mu_loss_coef)
     g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1: gradient
     J = _mlp.jacobian(problem, theta)                              # 'precompute Jacobian only'
     w = problem.w
@@ -225,4 +229,29 @@ def _rpchol_step(problem, theta, ell, mu, rtol, maxit, seed, step, gamma, c1, rh
     theta_new = theta - alpha * d                                   # Alg. 1: update
     if return_parts:
         return theta_new, info, dict(g=g, r=r, J=J, F=F, piv=piv, d=d, d0=d0)
+    return theta_new, info
+
+
+def _full_step(problem, theta, mu, seed, step, gamma, c1, rho, max_trials, return_parts, mu_loss_coef):
+    """One step of NGD full (Alg. 1 with Alg. 2): direction d = (G + mu I)^{-1} g by Cholesky."""
+    g, r, L0 = _mlp.gradient(problem, theta)                       # Alg. 1: gradient
+    J = _mlp.jacobian(problem, theta)
+    G = _gram.gramian(J, problem.w)                                 # Alg. 2: full Gramian
+    lam1 = _nys.power_lambda1(lambda v: G @ v, _philox.power_start(G.shape[0], seed, step), 4)
+    if mu is not None:
+        mu_eff = float(mu)
+    elif mu_loss_coef > 0.0:
+        mu_eff = _nys.mu_adaptive(lam1, L0, gamma, mu_loss_coef)
+    else:
+        mu_eff = _nys.mu_from_lambda1(lam1, gamma)
+    d = _gram.direct_direction(G, g, mu_eff)                        # Alg. 2: Cholesky, two solves
+
+    def loss_fn(th):
+        return _mlp.residual(problem, th)[1]
+
+    alpha, L1, trials = armijo(loss_fn, theta, d, g, L0, c1, rho, max_trials)   # Alg. 1: line search
+    info = StepInfo(L0, L1, alpha, mu_eff, lam1, 0.0, 0.0, 0, 0.0, trials, 0)
+    theta_new = theta - alpha * d                                   # Alg. 1: update
+    if return_parts:
+        return theta_new, info, dict(g=g, r=r, J=J, G=G, d=d)
     return theta_new, info

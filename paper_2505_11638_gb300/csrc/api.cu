@@ -76,6 +76,9 @@ struct ngd_ctx {
   unsigned long long* samp_keys = nullptr;
   int* samp_idx = nullptr;
   int* samp_count = nullptr;
+  // NGD full: the explicit Gramian (p x p) and diag(w) J in FP64 (N x ldJ), grown on demand
+  double* Gfull = nullptr;
+  double* Zfull = nullptr;
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -775,6 +778,57 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   return pcg_result(ctx, h, iters, relres);
 }
 
+// lambda_1 of G at the current linearization by four steps of the power method (Alg. 2, Alg. 5):
+// v0 the Gaussian column with counter word 2^32 - 2, v <- G v / ||G v||, the estimate the last
+// Rayleigh quotient, into scal[kSLam1].  Uses z and q as scratch.
+template <typename T>
+ngd_status power_lambda1(ngd_ctx* ctx, uint64_t seed, uint64_t step) {
+  const int64_t p = ctx->p;
+  cudaStream_t st = ctx->stream;
+  double* v = ctx->z;
+  double* w = ctx->q;
+  launch_philox_column(v, p, 0xFFFFFFFEu, seed, step, st);
+  launch_dot(v, v, p, ctx->part, ctx->scal + kSDot, st);
+  launch_scale_rsqrt(v, ctx->scal + kSDot, v, p, st);
+  for (int it = 0; it < 4; ++it) {
+    TRY(gv_current<T>(ctx, v, 0.0, nullptr, w, nullptr));
+    launch_dot(v, w, p, ctx->part, ctx->scal + kSLam1, st);
+    launch_dot(w, w, p, ctx->part, ctx->scal + kSDot, st);
+    launch_scale_rsqrt(w, ctx->scal + kSDot, v, p, st);
+  }
+  return check_launch(ctx);
+}
+
+// NGD full (Alg. 2) direction at the current linearization (stored J) into ctx->d: lambda_1 by the
+// power method, mu (into scal[kSMu]), G = J^T (w .* J) formed explicitly (FP64-accurate: w .* J in
+// FP64, the double-float GEMM), G + mu I = L L^T (FP64 Cholesky), d = L^{-T} L^{-1} g.
+template <typename T>
+ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
+  const int64_t p = ctx->p;
+  cudaStream_t st = ctx->stream;
+  if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "NGD full needs the stored Jacobian%s");
+  if (!ctx->Gfull) {
+    TRY(dalloc(ctx, &ctx->Gfull, (size_t)p * p * 8));
+    TRY(dalloc(ctx, &ctx->Zfull, (size_t)ctx->N * ctx->ldJ * 8));
+  }
+  TRY(clear_status(ctx));
+  TRY(power_lambda1<T>(ctx, o->seed, o->step));
+  launch_set_mu(ctx->scal + kSLam1, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, st);
+  launch_scale_rows_f64<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->ps.w, ctx->Zfull, st);
+  GemmDfArgs<T, double> g;                                      // G = J^T (w .* J)
+  g.M = p; g.N = p; g.K = ctx->N;
+  g.A = (const T*)ctx->J; g.sam = 1; g.sak = ctx->ldJ;
+  g.B = ctx->Zfull; g.sbk = ctx->ldJ; g.sbn = 1;
+  g.out64 = ctx->Gfull; g.scm = 1; g.scn = p;
+  launch_gemm_df<T, double>(g, st);
+  launch_symmetrize(ctx->Gfull, (int)p, st);
+  launch_add_diag_dev(ctx->Gfull, p, ctx->scal + kSMu, st);
+  CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
+  TRY(sync_status(ctx));
+  CK(launch_chol_solve(ctx->Gfull, (int)p, ctx->g, ctx->d, ctx->z, st));
+  return check_launch(ctx);
+}
+
 // RPCholNGD preconditioner (Alg. 5) at the current linearization (stored J): diag G, lambda_1 by
 // four power-method steps (start: the Gaussian column with word 2^32 - 2), mu (into scal[kSMu]),
 // block RPCholesky (rounds of o->rpchol_block pivots, at most o->ell columns, stopping when the
@@ -801,18 +855,7 @@ ngd_status rpchol_build(ngd_ctx* ctx, const ngd_step_opts* o, int* ell_pc, int* 
   cudaStream_t st = ctx->stream;
   TRY(clear_status(ctx));
   TRY(gram_diag_internal<T>(ctx, ctx->gdiag));
-  // lambda_1: four steps of the power method, v in z, G v in q
-  double* v = ctx->z;
-  double* w = ctx->q;
-  launch_philox_column(v, p, 0xFFFFFFFEu, o->seed, o->step, st);
-  launch_dot(v, v, p, ctx->part, ctx->scal + kSDot, st);
-  launch_scale_rsqrt(v, ctx->scal + kSDot, v, p, st);
-  for (int it = 0; it < 4; ++it) {
-    TRY(gv_current<T>(ctx, v, 0.0, nullptr, w, nullptr));
-    launch_dot(v, w, p, ctx->part, ctx->scal + kSLam1, st);
-    launch_dot(w, w, p, ctx->part, ctx->scal + kSDot, st);
-    launch_scale_rsqrt(w, ctx->scal + kSDot, v, p, st);
-  }
+  TRY(power_lambda1<T>(ctx, o->seed, o->step));
   launch_set_mu(ctx->scal + kSLam1, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, st);
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -968,6 +1011,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   TRY(vjp_current<T>(ctx, ctx->svec, ctx->g, true));
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
   const bool rpchol = o->precond == NGD_PRECOND_RPCHOL;
+  const bool full = o->precond == NGD_DIRECT_FULL;
   int ell_pc = o->ell, rp_rank = 0;
   double rp_lam1 = 0.0;
   bool u_f64 = true;
@@ -980,6 +1024,13 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
     TRY(rpchol_build<T>(ctx, o, &ell_pc, &rp_rank, &rp_lam1, &Urp));
     Ust = Urp;
     u_f64 = true;
+    CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+  } else if (full) {
+    // Alg. 2: the direction by Cholesky of the explicit G + mu I (no pCG)
+    phase.next("full");
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    TRY(full_direction<T>(ctx, o));
+    ell_pc = 0;
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
   } else {
     phase.next("sketch");
@@ -1006,8 +1057,9 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   // Alg. 3, direction: pCG on (G + mu I) d = g with the preconditioner of Alg. 4 or Alg. 5
   int iters = 0;
   double relres = 0.0;
-  TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, ell_pc, o->rtol, o->maxit,
-                      ctx->d, &iters, &relres));
+  if (!full)
+    TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, ell_pc, o->rtol,
+                        o->maxit, ctx->d, &iters, &relres));
   CK(cudaEventRecord(ctx->ev[4], ctx->stream));
   phase.next("linesearch");
   // Alg. 1, line search: Armijo backtracking along theta - alpha d
@@ -1015,7 +1067,7 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, kSCount * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   const double L0 = ctx->h_scal[kSLoss], slope = ctx->h_scal[kSDot], mu = ctx->h_scal[kSMu];
-  const double nu = rpchol ? 0.0 : ctx->h_scal[kSNu];
+  const double nu = (rpchol || full) ? 0.0 : ctx->h_scal[kSNu];
   std::vector<double> lam_all((size_t)std::max(ell_pc, 1), 0.0);
   if (ell_pc > 0) {
     CK(cudaMemcpyAsync(lam_all.data(), ctx->lam, (size_t)ell_pc * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1030,6 +1082,9 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
     for (int i = 0; i + 1 < ell_pc; ++i)
       if (lam_all[(size_t)i] > 0.0) lam_h[1] = lam_all[(size_t)i];
     ell_next = rp_rank;
+  } else if (full) {
+    lam_h[0] = ctx->h_scal[kSLam1];          // the power-method estimate
+    lam_h[1] = 0.0;
   } else if (o->ell_max > 0) {
     // Alg. 4: rank of the next step's sketch
     if (lam_h[1] > 10.0 * mu) {
@@ -1262,7 +1317,7 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
                  ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64, ctx->Uh, ctx->Ul,
                  ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf, ctx->gdiag,
-                 ctx->samp_keys, ctx->samp_idx, ctx->samp_count};
+                 ctx->samp_keys, ctx->samp_idx, ctx->samp_count, ctx->Gfull, ctx->Zfull};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -1525,7 +1580,7 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
   if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
       !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1 ||
       !(o->mu_loss_coef >= 0.0) || o->ell_max < 0 || o->ell_max > std::min<int64_t>(ctx->p, 2048) ||
-      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1 || o->precond < 0 || o->precond > 1 ||
+      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1 || o->precond < 0 || o->precond > 2 ||
       (o->precond == NGD_PRECOND_RPCHOL && (o->rpchol_block < 1 || o->rpchol_block > o->ell || o->ell > 2047)))
     return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
   if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)

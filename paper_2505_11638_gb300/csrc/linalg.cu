@@ -1020,6 +1020,107 @@ void launch_rpchol_lambda(const double* sig2, int r, double* lam, double* inv_si
   k_rpchol_lambda<<<(r + 1 + 255) / 256, 256, 0, s>>>(sig2, r, lam, inv_sigma); note_launch();
 }
 
+// ---------------------------------------------------------------------------- NGD full (Alg. 2)
+// Z[n ld + j] = w_n J[n ld + j] in FP64 (N x ld row-major, the padding columns stay zero)
+template <typename T>
+__global__ void k_scale_rows_f64(const T* __restrict__ J, int64_t ld, int64_t N, const double* __restrict__ w,
+                                 double* __restrict__ Z) {
+  const int64_t total = N * ld;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st)
+    Z[e] = w[e / ld] * (double)J[e];
+}
+template <typename T>
+void launch_scale_rows_f64(const T* J, int64_t ld, int64_t N, const double* w, double* Z, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((N * ld + 255) / 256, 8192);
+  k_scale_rows_f64<T><<<blocks, 256, 0, s>>>(J, ld, N, w, Z); note_launch();
+}
+template void launch_scale_rows_f64<float>(const float*, int64_t, int64_t, const double*, double*, cudaStream_t);
+template void launch_scale_rows_f64<double>(const double*, int64_t, int64_t, const double*, double*, cudaStream_t);
+
+// A[i + i n] += *shift
+__global__ void k_add_diag_dev(double* __restrict__ A, int64_t n, const double* __restrict__ shift) {
+  const double sh = *shift;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) A[i + i * n] += sh;
+}
+void launch_add_diag_dev(double* A, int64_t n, const double* shift, cudaStream_t s) {
+  k_add_diag_dev<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, shift); note_launch();
+}
+
+// x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, ld n): forward then
+// backward substitution by blocks of 32 rows in one cooperative launch.  Warp 0 of block 0 solves
+// each diagonal block (its lanes hold the block's entries); the grid then updates the remaining
+// rows: below the block with columns of L (forward), above it with rows of L, i.e. contiguous
+// pieces of its columns (backward).  A row moves between threads from one block of rows to the
+// next, so the vectors are read through L2 (__ldcg).  y: scratch of n.
+__global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L, int n, const double* __restrict__ b,
+                                                    double* __restrict__ x, double* __restrict__ y) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double blk[32];
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t ln = n;
+  for (int64_t i = gtid; i < n; i += gthreads) y[i] = b[i];
+  grid.sync();
+  for (int k0 = 0; k0 < n; k0 += 32) {                      // L y = b
+    const int bs = min(32, n - k0);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+      const int i = threadIdx.x;
+      double yi = i < bs ? __ldcg(y + k0 + i) : 0.0;
+      for (int j = 0; j < bs; ++j) {
+        if (i == j) yi /= L[(k0 + j) * (ln + 1)];
+        const double yj = __shfl_sync(0xffffffffu, yi, j);
+        if (i > j && i < bs) yi -= L[(k0 + i) + (int64_t)(k0 + j) * ln] * yj;
+      }
+      if (i < bs) y[k0 + i] = yi;
+    }
+    grid.sync();
+    if (threadIdx.x < bs) blk[threadIdx.x] = __ldcg(y + k0 + threadIdx.x);
+    __syncthreads();
+    for (int64_t i = k0 + bs + gtid; i < n; i += gthreads) {
+      double s = 0.0;
+      for (int j = 0; j < bs; ++j) s += L[i + (int64_t)(k0 + j) * ln] * blk[j];
+      y[i] = __ldcg(y + i) - s;
+    }
+    grid.sync();
+  }
+  for (int64_t i = gtid; i < n; i += gthreads) x[i] = __ldcg(y + i);
+  grid.sync();
+  for (int k0 = ((n - 1) / 32) * 32; k0 >= 0; k0 -= 32) {  // L^T x = y
+    const int bs = min(32, n - k0);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+      const int i = threadIdx.x;
+      double xi = i < bs ? __ldcg(x + k0 + i) : 0.0;
+      for (int j = bs - 1; j >= 0; --j) {
+        if (i == j) xi /= L[(k0 + j) * (ln + 1)];
+        const double xj = __shfl_sync(0xffffffffu, xi, j);
+        if (i < j) xi -= L[(k0 + j) + (int64_t)(k0 + i) * ln] * xj;
+      }
+      if (i < bs) x[k0 + i] = xi;
+    }
+    grid.sync();
+    if (threadIdx.x < bs) blk[threadIdx.x] = __ldcg(x + k0 + threadIdx.x);
+    __syncthreads();
+    for (int64_t i = gtid; i < k0; i += gthreads) {
+      double s = 0.0;
+      const double* col = L + i * ln + k0;                    // L[k0 .. k0 + bs, i]
+      for (int j = 0; j < bs; ++j) s += col[j] * blk[j];
+      x[i] = __ldcg(x + i) - s;
+    }
+    grid.sync();
+  }
+}
+cudaError_t launch_chol_solve(const double* L, int n, const double* b, double* x, double* y, cudaStream_t s) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_solve, 256, 0);
+  const int blocks = std::max(1, std::min(per, 2)) * nsm;
+  void* args[] = {(void*)&L, &n, (void*)&b, &x, &y};
+  note_launch();
+  return cudaLaunchCooperativeKernel((const void*)k_chol_solve, blocks, 256, args, 0, s);
+}
+
 // ---------------------------------------------------------------------------- SIMT GEMM
 // C(m, n) = sum_k A(m, k) B(k, n) with element strides; A(m,k) = A[m*sam + k*sak],
 // B(k,n) = B[k*sbk + n*sbn].  64x64 tiles, 16-deep K slices, 4x4 per thread.

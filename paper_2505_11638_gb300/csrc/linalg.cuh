@@ -65,6 +65,11 @@ void launch_pivot_block(const double* C, int64_t ld, const int* sel, int nsel, d
 int launch_rpchol_diag(double* d, const double* Fn, int64_t ld, int64_t p, int nsel, const int* sel, double* part,
                        cudaStream_t s);
 void launch_rpchol_lambda(const double* sig2, int r, double* lam, double* inv_sigma, cudaStream_t s);
+// NGD full (Alg. 2): w .* J in FP64, diagonal shift, Cholesky solve
+template <typename T>
+void launch_scale_rows_f64(const T* J, int64_t ld, int64_t N, const double* w, double* Z, cudaStream_t s);
+void launch_add_diag_dev(double* A, int64_t n, const double* shift, cudaStream_t s);
+cudaError_t launch_chol_solve(const double* L, int n, const double* b, double* x, double* y, cudaStream_t s);
 
 
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_SPD", 5:
 DTYPES = {"f64": 0, "f32": 1}
 SKETCH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
 TEST_MATRIX = {"gaussian": 0, "sampling": 1}
-PRECOND = {"nystrom": 0, "rpchol": 1}
+PRECOND = {"nystrom": 0, "rpchol": 1, "full": 2}
 PDES = {"poisson": 0, "heat": 1}
 GV_MODES = {"auto": 0, "stored": 1, "matrix_free": 2}
 

@@ -620,3 +620,37 @@ def test_rpchol_step_fp32_context(ngd):
     assert info["lam1"] == pytest.approx(info_o.lam1, rel=1e-4)
     assert abs(info["ell_next"] - info_o.ell_next) <= 10
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ngd_full_step_matches_oracle(ngd, dtype):
+    """NGD full (Alg. 2): the explicit Gramian, the power-method lambda_1, mu, the FP64 Cholesky and
+    two triangular solves give the oracle's direct direction.  FP64: the direction tolerance 1e-6
+    (the Gramian is formed to ~2^-48 and kappa(G + mu I) ~ 1e8 here), and the GPU direction solves
+    the oracle's system to a backward error of 1e-12; FP32 context: the FP32 rounding of J, 5e-3."""
+    pr, th = inputs.small_problem(d=3, widths=[3, 20, 20, 1], n_int=500, n_bnd=120, seed=95)
+    ctx = ngd.Context(pr, dtype=dtype)
+    t = dev(th)
+    info = ctx.step(t, precond="full", ell=1, mu=1e-6, seed=3, step=0, sketch="f64")
+    th1_o, info_o, parts = solve.ngd_step(pr, th, ell=1, mu=1e-6, rtol=0.0, maxit=1, seed=3, step=0, precond="full",
+                                          return_parts=True)
+    assert info["pcg_iters"] == 0
+    assert info["loss_after"] < info["loss_before"]
+    assert info["lam1"] == pytest.approx(info_o.lam1, rel=1e-10 if dtype == "f64" else 1e-4)
+    assert rel(host(t) - th, th1_o - th) <= (1e-6 if dtype == "f64" else 5e-3)
+    if dtype == "f64" and info["alpha"] > 0:
+        d_gpu = (th - host(t)) / info["alpha"]
+        G, g = parts["G"], parts["g"]
+        res = G @ d_gpu + 1e-6 * d_gpu - g
+        assert np.linalg.norm(res) <= 1e-12 * (np.linalg.norm(G, 2) * np.linalg.norm(d_gpu) + np.linalg.norm(g))
+    ctx.close()
+
+
+def test_ngd_full_step_adaptive_damping(ngd):
+    """NGD full with mu = max(10 eps lambda_1, 1e-4 L^2): mu from the power method and the loss."""
+    pr, th = small(SMALL[0], seed=96)
+    ctx = ngd.Context(pr, dtype="f64")
+    info = ctx.step(dev(th), precond="full", ell=1, mu=None, mu_loss_coef=1e-4, seed=1, step=2, sketch="f64")
+    assert info["mu"] == pytest.approx(max(10 * 2.0 ** -52 * info["lam1"], 1e-4 * info["loss_before"] ** 2),
+                                       rel=1e-14)
+    ctx.close()

@@ -439,3 +439,17 @@ def test_rpchol_ngd_step_decreases_the_loss():
                                rpchol_block=5, mu_loss_coef=1e-4)
     assert info.loss_after < info.loss_before
     assert 1 <= info.ell_next <= 20
+
+
+def test_ngd_full_step_solves_the_damped_system():
+    """NGD full (Alg. 2): the direction solves (G + mu I) d = g to rounding, with mu from the power
+    method, and the step decreases the loss."""
+    pr, th = inputs.small_problem(d=2, widths=[2, 6, 5, 1], n_int=30, n_bnd=10, seed=8)
+    th1, info, parts = solve.ngd_step(pr, th, ell=1, mu=None, rtol=0.0, maxit=1, seed=1, step=0, precond="full",
+                                      return_parts=True)
+    G, g, d = parts["G"], parts["g"], parts["d"]
+    assert info.mu == pytest.approx(10 * 2.0 ** -52 * info.lam1, rel=1e-15)
+    assert info.lam1 <= np.linalg.eigvalsh(G)[-1] * (1 + 1e-12)
+    res = G @ d + info.mu * d - g
+    assert np.linalg.norm(res) <= 1e-6 * np.linalg.norm(g)
+    assert info.loss_after < info.loss_before
