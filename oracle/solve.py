@@ -244,7 +244,14 @@ def _full_step(problem, theta, mu, seed, step, gamma, c1, rho, max_trials, retur
         mu_eff = _nys.mu_adaptive(lam1, L0, gamma, mu_loss_coef)
     else:
         mu_eff = _nys.mu_from_lambda1(lam1, gamma)
-    d = _gram.direct_direction(G, g, mu_eff)                        # Alg. 2: Cholesky, two solves
+    for scale in SHIFT_SCALES:          # a numerically indefinite G + mu I is retried with 8 mu, ...
+        try:
+            d = _gram.direct_direction(G, g, mu_eff)                # Alg. 2: Cholesky, two solves
+            break
+        except np.linalg.LinAlgError:
+            if scale == SHIFT_SCALES[-1]:
+                raise
+            mu_eff *= 8.0
 
     def loss_fn(th):
         return _mlp.residual(problem, th)[1]

@@ -822,8 +822,23 @@ ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
   g.out64 = ctx->Gfull; g.scm = 1; g.scn = p;
   launch_gemm_df<T, double>(g, st);
   launch_symmetrize(ctx->Gfull, (int)p, st);
+  launch_copy_diag(ctx->Gfull, p, ctx->x, st);               // x: scratch for diag(G)
   launch_add_diag_dev(ctx->Gfull, p, ctx->scal + kSMu, st);
-  CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
+  // A mu below the rounding of the formed G (mu = 10 eps lambda_1 late in training) can leave
+  // G + mu I numerically indefinite; the paper is silent on failures, and the factorization is
+  // retried with 8 mu, 64 mu, ..., 8^5 mu (the Cholesky writes only the lower triangle: it is
+  // rebuilt from the upper one and the saved diagonal).
+  for (int attempt = 0;; ++attempt) {
+    CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
+    CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!(ctx->h_int[0] & kStatNotSpd)) break;
+    if (attempt + 1 >= kShiftAttempts)
+      return set_err(ctx, NGD_ERR_NOT_SPD, "NGD full: G + mu I is not positive definite up to 8^5 mu%s");
+    TRY(clear_status(ctx));
+    launch_scale_scalar(ctx->scal + kSMu, 8.0, st);
+    launch_restore_lower(ctx->Gfull, p, ctx->x, ctx->scal + kSMu, st);
+  }
   TRY(sync_status(ctx));
   CK(launch_chol_solve(ctx->Gfull, (int)p, ctx->g, ctx->d, ctx->z, st));
   return check_launch(ctx);

@@ -1048,6 +1048,34 @@ void launch_add_diag_dev(double* A, int64_t n, const double* shift, cudaStream_t
   k_add_diag_dev<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, shift); note_launch();
 }
 
+// dg = diag(A) (before the shift and the in-place Cholesky, which only writes the lower triangle)
+__global__ void k_copy_diag(const double* __restrict__ A, int64_t n, double* __restrict__ dg) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) dg[i] = A[i + i * n];
+}
+void launch_copy_diag(const double* A, int64_t n, double* dg, cudaStream_t s) {
+  k_copy_diag<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, dg); note_launch();
+}
+// A's lower triangle again from its untouched upper triangle, diagonal dg + *shift
+__global__ void k_restore_lower(double* __restrict__ A, int64_t n, const double* __restrict__ dg,
+                                const double* __restrict__ shift) {
+  const double sh = *shift;
+  const int64_t total = n * n;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st) {
+    const int64_t i = e % n, j = e / n;                    // A[i + j n], lower when i >= j
+    if (i > j) A[e] = A[j + i * n];
+    else if (i == j) A[e] = dg[i] + sh;
+  }
+}
+void launch_restore_lower(double* A, int64_t n, const double* dg, const double* shift, cudaStream_t s) {
+  k_restore_lower<<<(int)std::min<int64_t>((n * n + 255) / 256, 8192), 256, 0, s>>>(A, n, dg, shift); note_launch();
+}
+__global__ void k_scale_scalar(double* __restrict__ x, double f) { *x *= f; }
+void launch_scale_scalar(double* x, double f, cudaStream_t s) {
+  k_scale_scalar<<<1, 1, 0, s>>>(x, f); note_launch();
+}
+
 // x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, ld n): forward then
 // backward substitution by blocks of 32 rows in one cooperative launch.  Warp 0 of block 0 solves
 // each diagonal block (its lanes hold the block's entries); the grid then updates the remaining

@@ -70,6 +70,9 @@ template <typename T>
 void launch_scale_rows_f64(const T* J, int64_t ld, int64_t N, const double* w, double* Z, cudaStream_t s);
 void launch_add_diag_dev(double* A, int64_t n, const double* shift, cudaStream_t s);
 cudaError_t launch_chol_solve(const double* L, int n, const double* b, double* x, double* y, cudaStream_t s);
+void launch_copy_diag(const double* A, int64_t n, double* dg, cudaStream_t s);
+void launch_restore_lower(double* A, int64_t n, const double* dg, const double* shift, cudaStream_t s);
+void launch_scale_scalar(double* x, double f, cudaStream_t s);
 
 
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);
