@@ -20,6 +20,7 @@ using namespace ngd;
 
 static std::atomic<unsigned long long> g_launches{0};
 void ngd::note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+static unsigned long long launches_now() { return g_launches.load(std::memory_order_relaxed); }
 
 struct ngd_ctx {
   NetDesc net{};
@@ -76,6 +77,14 @@ struct ngd_ctx {
   unsigned long long* samp_keys = nullptr;
   int* samp_idx = nullptr;
   int* samp_count = nullptr;
+  // multi-kernel PCG: a CUDA graph of `chunk` iterations, reused while its inputs stay the same
+  cudaGraphExec_t pcg_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;     // private stream the graph is captured on
+  struct {
+    const void* U; bool u_f64; int64_t ldU; const double* lam; int ell; double mu_h; const double* mu_d;
+    double* x; int chunk; void* J; void* prep;
+  } pcg_key{};
+  int pcg_graph_kernels = 0;
   // NGD full: the explicit Gramian (p x p) and diag(w) J in FP64 (N x ldJ), grown on demand
   double* Gfull = nullptr;
   double* Zfull = nullptr;
@@ -759,16 +768,75 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   if (pre) precond(ctx, u_f64, U, ldU, ell, lam, mu_h, mu_d, r, z, nullptr);
   launch_pcg_first_dir(r, pre ? z : r, pv, p, ctx->part, ctx->pcg, ctx->stream);
   TRY(check_launch(ctx));
-  const int chunk = 2;
+  auto one_iteration = [&]() -> ngd_status {
+    TRY(gv_current<T>(ctx, pv, mu_h, mu_d, q, done));
+    launch_pcg_alpha(pv, q, p, ctx->part, ctx->pcg, ctx->stream);
+    launch_pcg_update_xr(x, r, pv, q, p, ctx->part, ctx->pcg, ctx->stream);
+    if (pre) precond(ctx, u_f64, U, ldU, ell, lam, mu_h, mu_d, r, z, done);
+    launch_pcg_beta(r, pre ? z : r, p, ctx->part, ctx->pcg, ctx->stream);
+    launch_pcg_update_p(pv, pre ? z : r, p, ctx->pcg, ctx->stream);
+    return NGD_OK;
+  };
+  // The iterations are launch-bound at small sizes: `chunk` of them run as one CUDA graph, captured
+  // once and replayed while U, lambda, mu, x and the linearization buffers stay the same.  The
+  // kernels stop themselves on the device (done flag, maxit), so iterations past convergence in
+  // the last replay return at once; the host reads the flag after each replay.  Matrix-free
+  // matvecs do not check the flag, so that mode replays fewer iterations at a time.
+  const int chunk = ctx->stored_j ? 8 : 2;
+  const auto key_same = [&]() {
+    const auto& k = ctx->pcg_key;
+    return ctx->pcg_exec && k.U == U && k.u_f64 == u_f64 && k.ldU == ldU && k.lam == lam && k.ell == (pre ? ell : 0) &&
+           k.mu_h == mu_h && k.mu_d == mu_d && k.x == x && k.chunk == chunk && k.J == ctx->J && k.prep == ctx->prep;
+  };
   int launched = 0;
-  while (launched < maxit) {
-    for (int k = 0; k < chunk && launched < maxit; ++k, ++launched) {
-      TRY(gv_current<T>(ctx, pv, mu_h, mu_d, q, done));
-      launch_pcg_alpha(pv, q, p, ctx->part, ctx->pcg, ctx->stream);
-      launch_pcg_update_xr(x, r, pv, q, p, ctx->part, ctx->pcg, ctx->stream);
-      if (pre) precond(ctx, u_f64, U, ldU, ell, lam, mu_h, mu_d, r, z, done);
-      launch_pcg_beta(r, pre ? z : r, p, ctx->part, ctx->pcg, ctx->stream);
-      launch_pcg_update_p(pv, pre ? z : r, p, ctx->pcg, ctx->stream);
+  bool converged = false;
+  if (!key_same()) {
+    if (ctx->pcg_exec) {
+      cudaGraphExecDestroy(ctx->pcg_exec);
+      ctx->pcg_exec = nullptr;
+    }
+    // one iteration for real first: it grows any workspace a matvec allocates on first use, which
+    // a capture could not do
+    TRY(one_iteration());
+    ++launched;
+    TRY(check_launch(ctx));
+    CK(cudaMemcpyAsync(h, ctx->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    converged = h->done != 0;
+    // the caller's stream may be the legacy default stream, which cannot be captured: capture on a
+    // private stream (nothing runs during a capture) and replay on the caller's
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      ctx->cap_stream = nullptr;
+    if (ctx->cap_stream) {
+      cudaStream_t caller = ctx->stream;
+      ctx->stream = ctx->cap_stream;
+      const unsigned long long l0 = launches_now();
+      cudaGraph_t graph = nullptr;
+      ngd_status st = NGD_OK;
+      if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        for (int k = 0; k < chunk && st == NGD_OK; ++k) st = one_iteration();
+        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (st == NGD_OK && e == cudaSuccess && graph &&
+            cudaGraphInstantiate(&ctx->pcg_exec, graph, 0) == cudaSuccess) {
+          ctx->pcg_key = {U, u_f64, ldU, lam, pre ? ell : 0, mu_h, mu_d, x, chunk, ctx->J, ctx->prep};
+          ctx->pcg_graph_kernels = (int)(launches_now() - l0);
+        } else {
+          ctx->pcg_exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      ctx->stream = caller;
+      g_launches.fetch_sub(launches_now() - l0, std::memory_order_relaxed);   // captured, not run
+      cudaGetLastError();
+    }
+  }
+  while (!converged && launched < maxit) {
+    if (ctx->pcg_exec) {
+      CK(cudaGraphLaunch(ctx->pcg_exec, ctx->stream));
+      note_launch(ctx->pcg_graph_kernels);
+      launched += chunk;
+    } else {                                // no graph (capture refused): launch the iterations
+      for (int k = 0; k < chunk && launched < maxit; ++k, ++launched) TRY(one_iteration());
     }
     TRY(check_launch(ctx));
     CK(cudaMemcpyAsync(h, ctx->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1341,6 +1409,8 @@ void ngd_destroy(ngd_ctx* ctx) {
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->tc) tc_destroy(ctx->tc);
+  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
