@@ -85,9 +85,14 @@ struct ngd_ctx {
     double* x; int chunk; void* J; void* prep;
   } pcg_key{};
   int pcg_graph_kernels = 0;
-  // NGD full: the explicit Gramian (p x p) and diag(w) J in FP64 (N x ldJ), grown on demand
+  // NGD full: the explicit Gramian (p x p, leading dimension ldG) and diag(w) J in FP64 (N x ldJ),
+  // allocated on first use; for large p the scratch of the blocked Cholesky
   double* Gfull = nullptr;
   double* Zfull = nullptr;
+  int64_t ldG = 0;
+  double* chol_D = nullptr;
+  double* chol_W = nullptr;
+  double* chol_T = nullptr;
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -869,35 +874,50 @@ ngd_status power_lambda1(ngd_ctx* ctx, uint64_t seed, uint64_t step) {
 
 // NGD full (Alg. 2) direction at the current linearization (stored J) into ctx->d: lambda_1 by the
 // power method, mu (into scal[kSMu]), G = J^T (w .* J) formed explicitly (FP64-accurate: w .* J in
-// FP64, the double-float GEMM), G + mu I = L L^T (FP64 Cholesky), d = L^{-T} L^{-1} g.
+// FP64, the double-float GEMM on the lower triangle, mirrored), G + mu I = L L^T (FP64 Cholesky:
+// one cooperative kernel up to kCholBlockedMin - 1 unknowns, the blocked form above),
+// d = L^{-T} L^{-1} g.
+constexpr int64_t kCholBlockedMin = 768;
 template <typename T>
 ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
   const int64_t p = ctx->p;
+  const bool blocked = p >= kCholBlockedMin;
   cudaStream_t st = ctx->stream;
   if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "NGD full needs the stored Jacobian%s");
   if (!ctx->Gfull) {
-    TRY(dalloc(ctx, &ctx->Gfull, (size_t)p * p * 8));
+    ctx->ldG = blocked ? (p + 3) / 4 * 4 : p;                  // even: the blocked GEMMs stay vectorised
+    TRY(dalloc(ctx, &ctx->Gfull, (size_t)ctx->ldG * p * 8));
     TRY(dalloc(ctx, &ctx->Zfull, (size_t)ctx->N * ctx->ldJ * 8));
+    if (blocked) {
+      TRY(dalloc(ctx, &ctx->chol_D, (size_t)256 * 256 * 8));
+      TRY(dalloc(ctx, &ctx->chol_W, (size_t)256 * 256 * 8));
+      TRY(dalloc(ctx, &ctx->chol_T, (size_t)256 * (p - 256) * 8));
+    }
   }
+  const int64_t ldG = ctx->ldG;
   TRY(clear_status(ctx));
   TRY(power_lambda1<T>(ctx, o->seed, o->step));
   launch_set_mu(ctx->scal + kSLam1, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, st);
   launch_scale_rows_f64<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->ps.w, ctx->Zfull, st);
-  GemmDfArgs<T, double> g;                                      // G = J^T (w .* J)
+  GemmDfArgs<T, double> g;                                      // lower(G) = lower(J^T (w .* J))
   g.M = p; g.N = p; g.K = ctx->N;
   g.A = (const T*)ctx->J; g.sam = 1; g.sak = ctx->ldJ;
   g.B = ctx->Zfull; g.sbk = ctx->ldJ; g.sbn = 1;
-  g.out64 = ctx->Gfull; g.scm = 1; g.scn = p;
+  g.out64 = ctx->Gfull; g.scm = 1; g.scn = ldG;
+  g.lower = 1;
   launch_gemm_df<T, double>(g, st);
-  launch_symmetrize(ctx->Gfull, (int)p, st);
-  launch_copy_diag(ctx->Gfull, p, ctx->x, st);               // x: scratch for diag(G)
-  launch_add_diag_dev(ctx->Gfull, p, ctx->scal + kSMu, st);
+  launch_lower_to_upper(ctx->Gfull, p, ldG, st);
+  launch_copy_diag(ctx->Gfull, p, ldG, ctx->x, st);          // x: scratch for diag(G)
+  launch_add_diag_dev(ctx->Gfull, p, ldG, ctx->scal + kSMu, st);
   // A mu below the rounding of the formed G (mu = 10 eps lambda_1 late in training) can leave
   // G + mu I numerically indefinite; the paper is silent on failures, and the factorization is
-  // retried with 8 mu, 64 mu, ..., 8^5 mu (the Cholesky writes only the lower triangle: it is
-  // rebuilt from the upper one and the saved diagonal).
+  // retried with 8 mu, 64 mu, ..., 8^5 mu (both Cholesky forms write only the lower triangle: it
+  // is rebuilt from the upper one and the saved diagonal).
   for (int attempt = 0;; ++attempt) {
-    CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
+    if (blocked)
+      CK(launch_cholesky_blocked(ctx->Gfull, p, ldG, ctx->status, ctx->chol_D, ctx->chol_W, ctx->chol_T, st));
+    else
+      CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
     CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (!(ctx->h_int[0] & kStatNotSpd)) break;
@@ -905,10 +925,10 @@ ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
       return set_err(ctx, NGD_ERR_NOT_SPD, "NGD full: G + mu I is not positive definite up to 8^5 mu%s");
     TRY(clear_status(ctx));
     launch_scale_scalar(ctx->scal + kSMu, 8.0, st);
-    launch_restore_lower(ctx->Gfull, p, ctx->x, ctx->scal + kSMu, st);
+    launch_restore_lower(ctx->Gfull, p, ldG, ctx->x, ctx->scal + kSMu, st);
   }
   TRY(sync_status(ctx));
-  CK(launch_chol_solve(ctx->Gfull, (int)p, ctx->g, ctx->d, ctx->z, st));
+  CK(launch_chol_solve(ctx->Gfull, (int)p, ldG, ctx->g, ctx->d, ctx->z, st));
   return check_launch(ctx);
 }
 
@@ -1400,7 +1420,8 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->A1, ctx->V, ctx->Vs, ctx->sig2, ctx->inv_sigma, ctx->lam, ctx->dinv, ctx->w1, ctx->gpart,
                  ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64, ctx->Uh, ctx->Ul,
                  ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf, ctx->gdiag,
-                 ctx->samp_keys, ctx->samp_idx, ctx->samp_count, ctx->Gfull, ctx->Zfull};
+                 ctx->samp_keys, ctx->samp_idx, ctx->samp_count, ctx->Gfull, ctx->Zfull, ctx->chol_D,
+                 ctx->chol_W, ctx->chol_T};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);

@@ -1038,56 +1038,119 @@ void launch_scale_rows_f64(const T* J, int64_t ld, int64_t N, const double* w, d
 template void launch_scale_rows_f64<float>(const float*, int64_t, int64_t, const double*, double*, cudaStream_t);
 template void launch_scale_rows_f64<double>(const double*, int64_t, int64_t, const double*, double*, cudaStream_t);
 
-// A[i + i n] += *shift
-__global__ void k_add_diag_dev(double* __restrict__ A, int64_t n, const double* __restrict__ shift) {
+// A[i + i ld] += *shift
+__global__ void k_add_diag_dev(double* __restrict__ A, int64_t n, int64_t ld, const double* __restrict__ shift) {
   const double sh = *shift;
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) A[i + i * n] += sh;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) A[i + i * ld] += sh;
 }
-void launch_add_diag_dev(double* A, int64_t n, const double* shift, cudaStream_t s) {
-  k_add_diag_dev<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, shift); note_launch();
+void launch_add_diag_dev(double* A, int64_t n, int64_t ld, const double* shift, cudaStream_t s) {
+  k_add_diag_dev<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, ld, shift); note_launch();
+}
+
+// A's strict upper triangle from its lower one (n x n, column-major, ld)
+__global__ void k_lower_to_upper(double* __restrict__ A, int64_t n, int64_t ld) {
+  const int64_t total = n * n;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st) {
+    const int64_t i = e % n, j = e / n;
+    if (i < j) A[i + j * ld] = A[j + i * ld];
+  }
+}
+void launch_lower_to_upper(double* A, int64_t n, int64_t ld, cudaStream_t s) {
+  k_lower_to_upper<<<(int)std::min<int64_t>((n * n + 255) / 256, 8192), 256, 0, s>>>(A, n, ld); note_launch();
+}
+
+// T[k + j nb] = -X[j + k ld] (nb x m): the negated, transposed panel for the trailing update's GEMM
+__global__ void k_neg_copy(const double* __restrict__ X, int64_t ld, int64_t m, int nb, double* __restrict__ T) {
+  const int64_t total = m * nb;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st) {
+    const int64_t k = e % nb, j = e / nb;
+    T[e] = -X[j + k * ld];
+  }
+}
+
+// Right-looking blocked Cholesky A = L L^T for large n (A n x n, column-major, leading dimension
+// lda; L into the lower triangle, the strict upper triangle left as it was): diagonal blocks of 256
+// by the cooperative k_cholesky (through the contiguous scratch D), the panel below them by
+// launch_trsm_lt, the trailing matrix by the double-float GEMM on its lower triangle
+// (A22 -= P P^T).  A non-positive-definite pivot block sets kStatNotSpd in *status; the later
+// blocks then compute on meaningless but finite-or-NaN values and write nothing outside A.
+// D: 256 x 256 doubles; W: 256 x 256 doubles; T: 256 x (n - 256) doubles.  An even lda keeps
+// the GEMM on its vectorised path.
+cudaError_t launch_cholesky_blocked(double* A, int64_t n, int64_t lda, int* status, double* D, double* W, double* T,
+                                    cudaStream_t s) {
+  constexpr int nb = 256;
+  for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    const int bs = (int)std::min<int64_t>(nb, n - k0);
+    double* Akk = A + k0 + k0 * lda;
+    cudaError_t e = cudaMemcpy2DAsync(D, (size_t)bs * 8, Akk, (size_t)lda * 8, (size_t)bs * 8, bs,
+                                      cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = launch_cholesky(D, bs, status, s);                  // lower triangle of D; its upper one kept
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy2DAsync(Akk, (size_t)lda * 8, D, (size_t)bs * 8, (size_t)bs * 8, bs, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    const int64_t m = n - k0 - bs;
+    if (m <= 0) break;
+    double* P = Akk + bs;                                   // rows k0 + bs .., columns k0 .. k0 + bs
+    launch_trsm_lt<double>(P, lda, m, bs, D, W, s);         // P <- P L_kk^{-T}
+    k_neg_copy<<<(int)std::min<int64_t>((m * bs + 255) / 256, 8192), 256, 0, s>>>(P, lda, m, bs, T); note_launch();
+    GemmDfArgs<double, double> g;                           // lower(A22) += lower(P (-P^T))
+    g.M = m; g.N = m; g.K = bs;
+    g.A = P; g.sam = 1; g.sak = lda;
+    g.B = T; g.sbk = 1; g.sbn = bs;                         // B[k][j] = T[k + j bs] = -P[j, k]
+    g.out64 = Akk + bs + bs * lda; g.scm = 1; g.scn = lda;
+    g.accumulate = 1;
+    g.lower = 1;
+    launch_gemm_df<double, double>(g, s);
+  }
+  return cudaGetLastError();
 }
 
 // dg = diag(A) (before the shift and the in-place Cholesky, which only writes the lower triangle)
-__global__ void k_copy_diag(const double* __restrict__ A, int64_t n, double* __restrict__ dg) {
+__global__ void k_copy_diag(const double* __restrict__ A, int64_t n, int64_t ld, double* __restrict__ dg) {
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) dg[i] = A[i + i * n];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) dg[i] = A[i + i * ld];
 }
-void launch_copy_diag(const double* A, int64_t n, double* dg, cudaStream_t s) {
-  k_copy_diag<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, dg); note_launch();
+void launch_copy_diag(const double* A, int64_t n, int64_t ld, double* dg, cudaStream_t s) {
+  k_copy_diag<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(A, n, ld, dg); note_launch();
 }
-// A's lower triangle again from its untouched upper triangle, diagonal dg + *shift
-__global__ void k_restore_lower(double* __restrict__ A, int64_t n, const double* __restrict__ dg,
+// A's lower triangle again from its untouched strict upper triangle, diagonal dg + *shift
+__global__ void k_restore_lower(double* __restrict__ A, int64_t n, int64_t ld, const double* __restrict__ dg,
                                 const double* __restrict__ shift) {
   const double sh = *shift;
   const int64_t total = n * n;
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st) {
-    const int64_t i = e % n, j = e / n;                    // A[i + j n], lower when i >= j
-    if (i > j) A[e] = A[j + i * n];
-    else if (i == j) A[e] = dg[i] + sh;
+    const int64_t i = e % n, j = e / n;                    // A[i + j ld], lower when i >= j
+    if (i > j) A[i + j * ld] = A[j + i * ld];
+    else if (i == j) A[i + j * ld] = dg[i] + sh;
   }
 }
-void launch_restore_lower(double* A, int64_t n, const double* dg, const double* shift, cudaStream_t s) {
-  k_restore_lower<<<(int)std::min<int64_t>((n * n + 255) / 256, 8192), 256, 0, s>>>(A, n, dg, shift); note_launch();
+void launch_restore_lower(double* A, int64_t n, int64_t ld, const double* dg, const double* shift, cudaStream_t s) {
+  k_restore_lower<<<(int)std::min<int64_t>((n * n + 255) / 256, 8192), 256, 0, s>>>(A, n, ld, dg, shift);
+  note_launch();
 }
 __global__ void k_scale_scalar(double* __restrict__ x, double f) { *x *= f; }
 void launch_scale_scalar(double* x, double f, cudaStream_t s) {
   k_scale_scalar<<<1, 1, 0, s>>>(x, f); note_launch();
 }
 
-// x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, ld n): forward then
+// x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, leading dimension ld): forward then
 // backward substitution by blocks of 32 rows in one cooperative launch.  Warp 0 of block 0 solves
 // each diagonal block (its lanes hold the block's entries); the grid then updates the remaining
 // rows: below the block with columns of L (forward), above it with rows of L, i.e. contiguous
 // pieces of its columns (backward).  A row moves between threads from one block of rows to the
 // next, so the vectors are read through L2 (__ldcg).  y: scratch of n.
-__global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L, int n, const double* __restrict__ b,
+__global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L, int n, int64_t ld,
+                                                    const double* __restrict__ b,
                                                     double* __restrict__ x, double* __restrict__ y) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double blk[32];
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t ln = n;
+  const int64_t ln = ld;
   for (int64_t i = gtid; i < n; i += gthreads) y[i] = b[i];
   grid.sync();
   for (int k0 = 0; k0 < n; k0 += 32) {                      // L y = b
@@ -1138,13 +1201,14 @@ __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L
     grid.sync();
   }
 }
-cudaError_t launch_chol_solve(const double* L, int n, const double* b, double* x, double* y, cudaStream_t s) {
+cudaError_t launch_chol_solve(const double* L, int n, int64_t ld, const double* b, double* x, double* y,
+                              cudaStream_t s) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_solve, 256, 0);
   const int blocks = std::max(1, std::min(per, 2)) * nsm;
-  void* args[] = {(void*)&L, &n, (void*)&b, &x, &y};
+  void* args[] = {(void*)&L, &n, &ld, (void*)&b, &x, &y};
   note_launch();
   return cudaLaunchCooperativeKernel((const void*)k_chol_solve, blocks, 256, args, 0, s);
 }
@@ -1271,7 +1335,7 @@ __global__ void __launch_bounds__(256) k_gemm_df(int64_t M, int64_t N, int64_t K
                                                  int64_t sbn, int64_t k_per_split, double* __restrict__ out64,
                                                  int64_t split_stride, float* __restrict__ out32, int64_t scm,
                                                  int64_t scn, const double* __restrict__ rowscale,
-                                                 const double* __restrict__ colscale, int accumulate) {
+                                                 const double* __restrict__ colscale, int accumulate, int lower) {
   constexpr int BM = 64, BN = 64, BK = 16;
   constexpr bool AL = IsDouble<TA>::v, BL = IsDouble<TB>::v;
   __shared__ float Ah[BK][BM + 1];
@@ -1280,6 +1344,7 @@ __global__ void __launch_bounds__(256) k_gemm_df(int64_t M, int64_t N, int64_t K
   __shared__ float Bl[BL ? BK : 1][BL ? BN + 1 : 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (lower && n0 >= m0 + BM) return;                      // tile wholly above the diagonal
   const int64_t kb = (int64_t)blockIdx.z * k_per_split;
   const int64_t ke = min(K, kb + k_per_split);
   DF acc[4][4];
@@ -1352,7 +1417,7 @@ __global__ void __launch_bounds__(256) k_gemm_df(int64_t M, int64_t N, int64_t K
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t gn = n0 + tx + 16 * j;
-      if (gn >= N) continue;
+      if (gn >= N || (lower && gn > gm)) continue;
       double v = ((double)acc[i][j].hi + (double)acc[i][j].lo) * rs;
       if (colscale) v *= colscale[gn];
       if (out64) {
@@ -1460,7 +1525,8 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
                                                     int64_t sbn, int64_t k_per_split, double* __restrict__ out64,
                                                     int64_t split_stride, float* __restrict__ out32, int64_t scm,
                                                     int64_t scn, const double* __restrict__ rowscale,
-                                                    const double* __restrict__ colscale, int accumulate) {
+                                                    const double* __restrict__ colscale, int accumulate,
+                                                    int lower) {
   constexpr bool AL = IsDouble<TA>::v, BL = IsDouble<TB>::v;
   constexpr int SA = BK * LA, SB = BK * LB;                 // floats per stage and word
   extern __shared__ __align__(16) float sh[];
@@ -1470,6 +1536,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
   float* Bl = Bh + 2 * SB;                                  // [2][BK][LB] when BL
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (lower && n0 >= m0 + BM) return;                      // tile wholly above the diagonal
   const int64_t kb = (int64_t)blockIdx.z * k_per_split;
   const int64_t ke = min(K, kb + k_per_split);
   const bool mn_in = m0 + BM <= M && n0 + BN <= N;
@@ -1543,7 +1610,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int64_t gm = m0 + (i < 2 ? 4 * ty + 2 * i : 64 + 4 * ty + 2 * (i - 2)) + u;
-        if (gm >= M || gn >= N) continue;
+        if (gm >= M || gn >= N || (lower && gn > gm)) continue;
         double v = ((double)(u ? h1 : h0) + (double)(u ? l1 : l0)) * (rowscale ? rowscale[gm] : 1.0);
         if (colscale) v *= colscale[gn];
         if (out64) {
@@ -1574,7 +1641,7 @@ void launch_v(const GemmDfArgs<TA, TB>& g, int64_t kps, int nz, cudaStream_t s) 
   }
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)std::max(nz, 1));
   kern<<<grid, NT, smem, s>>>(g.M, g.N, g.K, g.A, g.sam, g.sak, g.B, g.sbk, g.sbn, kps, g.out64, g.split_stride,
-                              g.out32, g.scm, g.scn, g.rowscale, g.colscale, g.accumulate);
+                              g.out32, g.scm, g.scn, g.rowscale, g.colscale, g.accumulate, g.lower);
   note_launch();
 }
 
@@ -1623,7 +1690,7 @@ void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s) {
   dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)std::max(nz, 1));
   k_gemm_df<TA, TB><<<grid, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.sam, g.sak, g.B, g.sbk, g.sbn, kps, g.out64,
                                          g.split_stride, g.out32, g.scm, g.scn, g.rowscale, g.colscale,
-                                         g.accumulate); note_launch();
+                                         g.accumulate, g.lower); note_launch();
 }
 template void launch_gemm_df<float, float>(const GemmDfArgs<float, float>&, cudaStream_t);
 template void launch_gemm_df<float, double>(const GemmDfArgs<float, double>&, cudaStream_t);

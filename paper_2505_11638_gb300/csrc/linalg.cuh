@@ -40,6 +40,7 @@ template <typename TA, typename TB> struct GemmDfArgs {
   const double* rowscale = nullptr;
   const double* colscale = nullptr;
   int accumulate = 0;
+  int lower = 0;     // write only out[m][n] with n <= m (M x N square output); skip tiles above
 };
 template <typename TA, typename TB> void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s);
 // K slices that fill the GPU's block slots most evenly for an M x N double-float GEMM
@@ -68,11 +69,16 @@ void launch_rpchol_lambda(const double* sig2, int r, double* lam, double* inv_si
 // NGD full (Alg. 2): w .* J in FP64, diagonal shift, Cholesky solve
 template <typename T>
 void launch_scale_rows_f64(const T* J, int64_t ld, int64_t N, const double* w, double* Z, cudaStream_t s);
-void launch_add_diag_dev(double* A, int64_t n, const double* shift, cudaStream_t s);
-cudaError_t launch_chol_solve(const double* L, int n, const double* b, double* x, double* y, cudaStream_t s);
-void launch_copy_diag(const double* A, int64_t n, double* dg, cudaStream_t s);
-void launch_restore_lower(double* A, int64_t n, const double* dg, const double* shift, cudaStream_t s);
+void launch_add_diag_dev(double* A, int64_t n, int64_t ld, const double* shift, cudaStream_t s);
+cudaError_t launch_chol_solve(const double* L, int n, int64_t ld, const double* b, double* x, double* y,
+                              cudaStream_t s);
+void launch_copy_diag(const double* A, int64_t n, int64_t ld, double* dg, cudaStream_t s);
+void launch_restore_lower(double* A, int64_t n, int64_t ld, const double* dg, const double* shift, cudaStream_t s);
 void launch_scale_scalar(double* x, double f, cudaStream_t s);
+void launch_lower_to_upper(double* A, int64_t n, int64_t ld, cudaStream_t s);
+// blocked Cholesky for large n; D, W: 256 x 256 doubles, T: 256 x (n - 256) doubles of scratch
+cudaError_t launch_cholesky_blocked(double* A, int64_t n, int64_t lda, int* status, double* D, double* W, double* T,
+                                    cudaStream_t s);
 
 
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);

@@ -646,6 +646,27 @@ def test_ngd_full_step_matches_oracle(ngd, dtype):
     ctx.close()
 
 
+def test_ngd_full_step_blocked_cholesky(ngd):
+    """NGD full at p = 1217: the blocked Cholesky (diagonal blocks of 256 and a ragged last one of
+    193, panel solves, lower-triangle trailing updates) and an even leading dimension 1220 give the
+    oracle's direction; the GPU direction solves the oracle's system to a backward error of 1e-12."""
+    pr, th = inputs.small_problem(d=3, widths=[3, 32, 32, 1], n_int=1500, n_bnd=300, seed=97)
+    assert th.size == 1217
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    info = ctx.step(t, precond="full", ell=1, mu=1e-6, seed=3, step=0, sketch="f64")
+    th1_o, info_o, parts = solve.ngd_step(pr, th, ell=1, mu=1e-6, rtol=0.0, maxit=1, seed=3, step=0, precond="full",
+                                          return_parts=True)
+    assert info["loss_after"] < info["loss_before"]
+    assert info["alpha"] == info_o.alpha
+    assert rel(host(t) - th, th1_o - th) <= 1e-6
+    d_gpu = (th - host(t)) / info["alpha"]
+    G, g = parts["G"], parts["g"]
+    res = G @ d_gpu + 1e-6 * d_gpu - g
+    assert np.linalg.norm(res) <= 1e-12 * (np.linalg.norm(G, 2) * np.linalg.norm(d_gpu) + np.linalg.norm(g))
+    ctx.close()
+
+
 def test_ngd_full_step_adaptive_damping(ngd):
     """NGD full with mu = max(10 eps lambda_1, 1e-4 L^2): mu from the power method and the loss."""
     pr, th = small(SMALL[0], seed=96)
