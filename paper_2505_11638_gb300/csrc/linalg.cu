@@ -1519,7 +1519,7 @@ struct Stage {
   }
 };
 
-template <typename TA, typename TB, bool AKC, bool BKC>
+template <typename TA, typename TB, bool AKC, bool BKC, int TN>
 __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A,
                                                     int64_t sam, int64_t sak, const TB* __restrict__ B, int64_t sbk,
                                                     int64_t sbn, int64_t k_per_split, double* __restrict__ out64,
@@ -1528,32 +1528,36 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
                                                     const double* __restrict__ colscale, int accumulate,
                                                     int lower) {
   constexpr bool AL = IsDouble<TA>::v, BL = IsDouble<TB>::v;
-  constexpr int SA = BK * LA, SB = BK * LB;                 // floats per stage and word
+  static_assert(TN == BN || TN == BN / 2, "tile width");
+  constexpr int LBt = TN + 4;                               // B row length in shared memory
+  constexpr int TXN = TN / 4;                               // threads along n
+  constexpr int RP = BM / (NT / TXN) / 2;                   // row pairs per thread: 4 (TN 64) or 2 (TN 32)
+  constexpr int SA = BK * LA, SB = BK * LBt;                // floats per stage and word
   extern __shared__ __align__(16) float sh[];
   float* Ah = sh;                                           // [2][BK][LA]
   float* Al = Ah + 2 * SA;                                  // [2][BK][LA] when AL
-  float* Bh = Al + (AL ? 2 * SA : 0);                       // [2][BK][LB]
-  float* Bl = Bh + 2 * SB;                                  // [2][BK][LB] when BL
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  float* Bh = Al + (AL ? 2 * SA : 0);                       // [2][BK][LBt]
+  float* Bl = Bh + 2 * SB;                                  // [2][BK][LBt] when BL
+  const int tx = threadIdx.x % TXN, ty = threadIdx.x / TXN;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * TN;
   if (lower && n0 >= m0 + BM) return;                      // tile wholly above the diagonal
   const int64_t kb = (int64_t)blockIdx.z * k_per_split;
   const int64_t ke = min(K, kb + k_per_split);
-  const bool mn_in = m0 + BM <= M && n0 + BN <= N;
-  DF2 acc[4][4];
+  const bool mn_in = m0 + BM <= M && n0 + TN <= N;
+  DF2 acc[RP][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RP; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = DF2{0ull, 0ull};
   Stage<TA, AKC, BM> sa;
-  Stage<TB, BKC, BN> sb;
+  Stage<TB, BKC, TN> sb;
   const int nk = (int)((ke - kb + BK - 1) / BK);
   if (nk > 0) {
     const bool in0 = mn_in && kb + BK <= ke;
     sa.load(A, AKC ? sam : 0, AKC ? 0 : sak, m0, kb, M, ke, in0);
     sb.load(B, BKC ? sbn : 0, BKC ? 0 : sbk, n0, kb, N, ke, in0);
     sa.template store<LA>(Ah, Al);
-    sb.template store<LB>(Bh, Bl);
+    sb.template store<LBt>(Bh, Bl);
   }
   __syncthreads();
   for (int it = 0; it < nk; ++it) {
@@ -1570,24 +1574,29 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
     const float* bl_s = Bl + cur * SB;
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(ah_s + kk * LA + 4 * ty);
-      const float4 a1 = *reinterpret_cast<const float4*>(ah_s + kk * LA + 64 + 4 * ty);
-      const float4 b0 = *reinterpret_cast<const float4*>(bh_s + kk * LB + 4 * tx);
-      f2x ah[4] = {pk2(a0.x, a0.y), pk2(a0.z, a0.w), pk2(a1.x, a1.y), pk2(a1.z, a1.w)};
-      f2x al[4] = {0ull, 0ull, 0ull, 0ull};
-      if constexpr (AL) {
-        const float4 c0 = *reinterpret_cast<const float4*>(al_s + kk * LA + 4 * ty);
-        const float4 c1 = *reinterpret_cast<const float4*>(al_s + kk * LA + 64 + 4 * ty);
-        al[0] = pk2(c0.x, c0.y); al[1] = pk2(c0.z, c0.w); al[2] = pk2(c1.x, c1.y); al[3] = pk2(c1.z, c1.w);
+      // rows 4 ty .. 4 ty + 3, and for TN 64 also 64 + 4 ty .. 64 + 4 ty + 3
+      f2x ah[RP], al[RP];
+#pragma unroll
+      for (int h = 0; h < RP / 2; ++h) {
+        const float4 a0 = *reinterpret_cast<const float4*>(ah_s + kk * LA + 64 * h + 4 * ty);
+        ah[2 * h] = pk2(a0.x, a0.y);
+        ah[2 * h + 1] = pk2(a0.z, a0.w);
+        al[2 * h] = al[2 * h + 1] = 0ull;
+        if constexpr (AL) {
+          const float4 c0 = *reinterpret_cast<const float4*>(al_s + kk * LA + 64 * h + 4 * ty);
+          al[2 * h] = pk2(c0.x, c0.y);
+          al[2 * h + 1] = pk2(c0.z, c0.w);
+        }
       }
+      const float4 b0 = *reinterpret_cast<const float4*>(bh_s + kk * LBt + 4 * tx);
       const float bhv[4] = {b0.x, b0.y, b0.z, b0.w};
       float blv[4] = {0.f, 0.f, 0.f, 0.f};
       if constexpr (BL) {
-        const float4 d0 = *reinterpret_cast<const float4*>(bl_s + kk * LB + 4 * tx);
+        const float4 d0 = *reinterpret_cast<const float4*>(bl_s + kk * LBt + 4 * tx);
         blv[0] = d0.x; blv[1] = d0.y; blv[2] = d0.z; blv[3] = d0.w;
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < RP; ++i) {
         const f2x nah = ah[i] ^ 0x8000000080000000ull;
 #pragma unroll
         for (int j = 0; j < 4; ++j) mac2<AL, BL>(acc[i][j], ah[i], nah, al[i], pk2(bhv[j], bhv[j]), pk2(blv[j], blv[j]));
@@ -1595,12 +1604,12 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
     }
     if (it + 1 < nk) {
       sa.template store<LA>(Ah + (cur ^ 1) * SA, Al + (cur ^ 1) * SA);
-      sb.template store<LB>(Bh + (cur ^ 1) * SB, Bl + (cur ^ 1) * SB);
+      sb.template store<LBt>(Bh + (cur ^ 1) * SB, Bl + (cur ^ 1) * SB);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RP; ++i) {
     float h0, h1, l0, l1;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1609,7 +1618,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
       const int64_t gn = n0 + 4 * tx + j;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int64_t gm = m0 + (i < 2 ? 4 * ty + 2 * i : 64 + 4 * ty + 2 * (i - 2)) + u;
+        const int64_t gm = m0 + 64 * (i / 2) + 4 * ty + 2 * (i % 2) + u;
         if (gm >= M || gn >= N || (lower && gn > gm)) continue;
         double v = ((double)(u ? h1 : h0) + (double)(u ? l1 : l0)) * (rowscale ? rowscale[gm] : 1.0);
         if (colscale) v *= colscale[gn];
@@ -1625,21 +1634,21 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
   }
 }
 
-template <typename TA, typename TB>
+template <typename TA, typename TB, int TN>
 constexpr size_t smem_bytes() {
-  return sizeof(float) * (2 * BK * LA * (IsDouble<TA>::v ? 2 : 1) + 2 * BK * LB * (IsDouble<TB>::v ? 2 : 1));
+  return sizeof(float) * (2 * BK * LA * (IsDouble<TA>::v ? 2 : 1) + 2 * BK * (TN + 4) * (IsDouble<TB>::v ? 2 : 1));
 }
 
-template <typename TA, typename TB, bool AKC, bool BKC>
+template <typename TA, typename TB, bool AKC, bool BKC, int TN>
 void launch_v(const GemmDfArgs<TA, TB>& g, int64_t kps, int nz, cudaStream_t s) {
-  constexpr size_t smem = smem_bytes<TA, TB>();
-  auto kern = k_gemm_dfv<TA, TB, AKC, BKC>;
+  constexpr size_t smem = smem_bytes<TA, TB, TN>();
+  auto kern = k_gemm_dfv<TA, TB, AKC, BKC, TN>;
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)std::max(nz, 1));
+  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + TN - 1) / TN), (unsigned)std::max(nz, 1));
   kern<<<grid, NT, smem, s>>>(g.M, g.N, g.K, g.A, g.sam, g.sak, g.B, g.sbk, g.sbn, kps, g.out64, g.split_stride,
                               g.out32, g.scm, g.scn, g.rowscale, g.colscale, g.accumulate, g.lower);
   note_launch();
@@ -1655,7 +1664,8 @@ int gemm_df_splits(int64_t M, int64_t N, int64_t K) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t slots = 2 * (int64_t)std::max(sms, 1);
-  const int64_t tiles = ((M + gdf::BM - 1) / gdf::BM) * ((N + gdf::BN - 1) / gdf::BN);
+  const int64_t tn = N <= gdf::BN / 2 ? gdf::BN / 2 : gdf::BN;   // the 32-wide tile of skinny FP64 B
+  const int64_t tiles = ((M + gdf::BM - 1) / gdf::BM) * ((N + tn - 1) / tn);
   int best = 1;
   double best_eff = 0.0;
   for (int ns = 1; ns <= 16 && (ns == 1 || K / ns >= 256); ++ns) {
@@ -1681,10 +1691,20 @@ void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s) {
     const bool a_ok = gdf::aligned16(g.A) && ((akc && g.sam % va == 0) || (amc && g.sak % va == 0));
     const bool b_ok = gdf::aligned16(g.B) && ((bkc && g.sbn % vb == 0) || (bnc && g.sbk % vb == 0));
     if (a_ok && b_ok && g.M > 0 && g.N > 0) {
-      if (akc && bkc) return gdf::launch_v<TA, TB, true, true>(g, kps, nz, s);
-      if (akc && bnc) return gdf::launch_v<TA, TB, true, false>(g, kps, nz, s);
-      if (amc && bkc) return gdf::launch_v<TA, TB, false, true>(g, kps, nz, s);
-      return gdf::launch_v<TA, TB, false, false>(g, kps, nz, s);
+      // outputs at most 32 wide (the column blocks of RPCholesky, early low-rank sketches) on the
+      // 128 x 32 tile when B is FP64 (one 16-byte vector per thread and K step)
+      if constexpr (sizeof(TB) == 8) {
+        if (g.N <= gdf::BN / 2) {
+          if (akc && bkc) return gdf::launch_v<TA, TB, true, true, gdf::BN / 2>(g, kps, nz, s);
+          if (akc && bnc) return gdf::launch_v<TA, TB, true, false, gdf::BN / 2>(g, kps, nz, s);
+          if (amc && bkc) return gdf::launch_v<TA, TB, false, true, gdf::BN / 2>(g, kps, nz, s);
+          return gdf::launch_v<TA, TB, false, false, gdf::BN / 2>(g, kps, nz, s);
+        }
+      }
+      if (akc && bkc) return gdf::launch_v<TA, TB, true, true, gdf::BN>(g, kps, nz, s);
+      if (akc && bnc) return gdf::launch_v<TA, TB, true, false, gdf::BN>(g, kps, nz, s);
+      if (amc && bkc) return gdf::launch_v<TA, TB, false, true, gdf::BN>(g, kps, nz, s);
+      return gdf::launch_v<TA, TB, false, false, gdf::BN>(g, kps, nz, s);
     }
   }
   dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)std::max(nz, 1));
