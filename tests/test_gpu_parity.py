@@ -667,6 +667,30 @@ def test_ngd_full_step_blocked_cholesky(ngd):
     ctx.close()
 
 
+def test_ngd_full_blocked_cholesky_retries(ngd):
+    """NGD full at p = 1217 with N = 600 rows (G of rank <= 600) and mu = 1e-16, far below the
+    rounding of the formed G: the blocked Cholesky meets a non-positive pivot, the lower triangle
+    is rebuilt from the upper one (leading dimension 1220) and the factorization retried with
+    8 mu, 64 mu, ...  The damping used is mu times a power of 8, and the direction solves
+    (G + mu_used I) d = g to a backward error of the Cholesky's precision."""
+    pr, th = inputs.small_problem(d=3, widths=[3, 32, 32, 1], n_int=500, n_bnd=100, seed=98)
+    assert th.size == 1217
+    mu0 = 1e-16
+    ctx = ngd.Context(pr, dtype="f64")
+    t = dev(th)
+    info = ctx.step(t, precond="full", ell=1, mu=mu0, seed=4, step=0, sketch="f64", armijo_max=60)
+    k = np.log(info["mu"] / mu0) / np.log(8.0)
+    assert 1 <= round(k) <= 5 and abs(k - round(k)) < 1e-9
+    _, _, parts = solve.ngd_step(pr, th, ell=1, mu=mu0, rtol=0.0, maxit=1, seed=4, step=0, precond="full",
+                                 return_parts=True)
+    if info["alpha"] > 0:
+        d_gpu = (th - host(t)) / info["alpha"]
+        G, g = parts["G"], parts["g"]
+        res = G @ d_gpu + info["mu"] * d_gpu - g
+        assert np.linalg.norm(res) <= 1e-9 * (np.linalg.norm(G, 2) * np.linalg.norm(d_gpu) + np.linalg.norm(g))
+    ctx.close()
+
+
 def test_ngd_full_step_adaptive_damping(ngd):
     """NGD full with mu = max(10 eps lambda_1, 1e-4 L^2): mu from the power method and the loss."""
     pr, th = small(SMALL[0], seed=96)
