@@ -297,6 +297,38 @@ def test_pcg_matches_oracle_at_fixed_iterations(ngd):
     ctx.close()
 
 
+def test_pcg_matrix_free_matches_oracle_at_fixed_iterations(ngd):
+    """PCG with the matrix-free Gramian (JVP then VJP per product; the iterations replayed from a
+    captured CUDA graph two at a time): at 1, 3 and 6 iterations (stops inside and at the end of a
+    replayed chunk) the iterates are the FP64 oracle's; a second solve with the same inputs (a
+    new output buffer, so a new capture) returns the same direction bit for bit."""
+    wl, pr, th = _workload("poisson2d")
+    J = mlp.jacobian(pr, th)
+    G = gramian.gramian(J, pr.w)
+    g_o, _, _ = mlp.gradient(pr, th)
+    ell, mu = 60, 1e-5
+    Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 6, 0))
+    U_o, lam_o, _ = nystrom.nystrom_factor(Om_o, G @ Om_o)
+    ctx = ngd.Context(pr, dtype="f64", gv_mode="matrix_free")
+    t = dev(th)
+    g, _, _ = ctx.gradient(t)
+    U_d = dev(U_o.T.copy())
+    lam_d = dev(lam_o)
+    for k in [1, 3, 6]:
+        d, it, rr = ctx.pcg_solve(None, g, mu, U_d, lam_d, ell, rtol=0.0, maxit=k)
+        d_o, it_o, rr_o = solve.pcg(lambda v: G @ v + mu * v, g_o, lambda v: nystrom.precond_apply(U_o, lam_o, mu, v),
+                                    0.0, k)
+        assert it == it_o == k
+        assert rel(host(d), d_o) <= 1e-8, k
+    d1, it1, rr1 = ctx.pcg_solve(None, g, mu, U_d, lam_d, ell, rtol=1e-9, maxit=500)
+    d2, it2, rr2 = ctx.pcg_solve(None, g, mu, U_d, lam_d, ell, rtol=1e-9, maxit=500)
+    assert rr1 <= 1e-9 and it1 == it2 and rr1 == rr2
+    assert np.array_equal(host(d1), host(d2))
+    res = (G + mu * np.eye(pr.p)) @ host(d1) - g_o
+    assert np.linalg.norm(res) <= 1e-7 * np.linalg.norm(g_o)
+    ctx.close()
+
+
 def test_fp32_matvec_symmetry_and_linearity(ngd):
     """The FP32-context matvec (one pass over the stored FP32 Jacobian, double-float sums): for
     that J, G = J^T W J is exactly symmetric and linear, so u.(Gv) = v.(Gu) and G(u + 2v) =
