@@ -114,8 +114,13 @@ typedef enum { NGD_TEST_GAUSSIAN = 0, NGD_TEST_SAMPLING = 1 } ngd_test_matrix;
  *                      info->lam1 the power-method estimate.  Needs the stored Jacobian.
  * NGD_DIRECT_FULL      no preconditioner and no pCG: NGD full (Alg. 2), the explicit Gramian
  *                      G = J^T (w .* J) (FP64-accurate), lambda_1 by the same power method, mu,
- *                      the FP64 Cholesky G + mu I = L L^T and d = L^{-T} L^{-1} g.  ell is unused;
- *                      needs the stored Jacobian and p^2 float64 of device memory. */
+ *                      the Cholesky G + mu I = L L^T and d = L^{-T} L^{-1} g.  For p < 768 the
+ *                      Cholesky is FP64 throughout; from p = 768 on it is blocked (FP64 256 x 256
+ *                      diagonal blocks, trailing updates FP64-accurate to ~2^-48, the precision G
+ *                      is formed in).  A numerically indefinite G + mu I is retried with 8 mu,
+ *                      64 mu, ..., 8^5 mu (info->mu returns the damping used), then reported as
+ *                      NGD_ERR_NOT_SPD.  ell is unused; needs the stored Jacobian and about
+ *                      p^2 + 256 p float64 of device memory. */
 typedef enum { NGD_PRECOND_NYSTROM = 0, NGD_PRECOND_RPCHOL = 1, NGD_DIRECT_FULL = 2 } ngd_precond;
 
 typedef struct {
