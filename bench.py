@@ -472,6 +472,73 @@ def run_precision_study(args, rank):
     return 0
 
 
+def run_matvec_study(args, rank):
+    """Gramian matvecs/s: (G + mu I) v through ngd_gramian_mv at the current linearization, in FP32
+    contexts on the 5-D Poisson (p = 8769), 10-D Poisson (p = 51073) and 4-D heat (p = 133121)
+    workloads, with J stored (one fused pass over J when p <= 9216, else a row pass and a column
+    pass) or matrix-free (J v by forward tangents, then J^T (w .* J v) from Jacobian row blocks of
+    about 64 MB recomputed and reduced while they sit in L2).  CUDA events around --steps products
+    after --warmup; the stored form is reported against the measured HBM copy bandwidth with its
+    algorithmic bytes (the passes over the N x ldJ FP32 Jacobian)."""
+    import torch
+    from paper_2505_11638_gb300 import build, inputs, ngd
+
+    if rank != 0:
+        return 0
+    build.build()
+    hbm = measured_peaks().get("hbm_gbs")
+    cases = [("poisson5d", "stored"), ("poisson10d", "stored"), ("poisson10d", "matrix_free"),
+             ("heat4d", "stored"), ("heat4d", "matrix_free")]
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    out = []
+    for name, mode in cases:
+        wl, thetas = inputs.make_workload(name, seed=0)
+        pr = wl.problems[0]
+        mu = float(wl.mu) if isinstance(wl.mu, float) else 1e-6
+        ctx = ngd.Context(pr, dtype="f32", gv_mode=mode)
+        theta = torch.tensor(thetas[0], device="cuda")
+        v = torch.tensor(np.random.default_rng(0).standard_normal(pr.p), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.gramian_mv(theta, v, mu)                       # linearize (J formed, or the tape)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_linearize = e0.elapsed_time(e1)
+        for _ in range(args.warmup):
+            ctx.gramian_mv(None, v, mu)
+        torch.cuda.synchronize()
+        l0 = ngd.ngd_kernel_launches()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.gramian_mv(None, v, mu)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        ldj = (pr.p + 31) // 32 * 32
+        jbytes = pr.n * ldj * 4
+        entry = {"workload": name, "mode": mode, "N": pr.n, "p": pr.p, "ms_per_gv": ms, "gv_per_s": 1e3 / ms,
+                 "ms_first_gv_with_linearization": ms_linearize,
+                 "launches_per_gv": (ngd.ngd_kernel_launches() - l0) / args.steps,
+                 "jacobian_fp32_bytes": jbytes}
+        if mode == "stored":
+            passes = 1 if pr.p <= 9216 else 2
+            gbs = passes * jbytes / (ms * 1e-3) / 1e9
+            entry["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": gbs / hbm if hbm else None, "passes_over_J": passes}
+        out.append(entry)
+        ctx.close()
+        del theta, v
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    line = {"metric": "Gramian matvecs/s ((G + mu I) v, FP32 Jacobian, FP64-accurate accumulation)",
+            "unit": "Gv/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "cases": out, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_train(args, rank):
     """NystromNGD training run on the paper's 3-D Poisson PINN (poisson3d: MLP 3-64-64-64-1,
     p = 8641, 10000 + 1000 points): Alg. 1 with Alg. 3 and Alg. 4, adaptive rank from 20 up to
@@ -567,6 +634,9 @@ def main():
     ap.add_argument("--test-matrix", default="gaussian", choices=["gaussian", "sampling"],
                     help="test matrix of the Nystrom sketch in --train (sampling: columns drawn proportionally "
                          "to diag G)")
+    ap.add_argument("--matvec-study", action="store_true",
+                    help="Gramian matvecs/s on the 5-D Poisson, 10-D Poisson and 4-D heat workloads, J stored "
+                         "or matrix-free, --steps products each")
     ap.add_argument("--precision-study", action="store_true",
                     help="the precision form on poisson10d: all-FP64 GPU path vs FP64-accurate (double-float) "
                          "vs TF32 / BF16 tensor-core sketches, --steps NGD steps each")
@@ -576,6 +646,8 @@ def main():
         return run_reference(args, rank, world)
     if args.precision_study:
         return run_precision_study(args, rank)
+    if args.matvec_study:
+        return run_matvec_study(args, rank)
     if args.train:
         return run_train(args, rank)
     if args.workload == "batch64":
