@@ -222,71 +222,37 @@ __device__ __forceinline__ void df_add4(DF& acc, const float4& a, const float4& 
   df_add_prod(acc, a.w, bh.w, bl.w);
 }
 
-// t_n = J_n . v (FP64-accurate), a block per group of kRowsPerBlock rows: its warps take
-// consecutive eighths of the rows' float4 slots (lanes strided, two accumulators per row), and each
-// v element loaded from L2 serves all the group's rows.  The eight warp sums of a row are added in
-// warp order, so the result does not depend on the launch configuration.
-constexpr int kRowsPerBlock = 4;
 __global__ void __launch_bounds__(256) k_rowdot_df(const float* __restrict__ J, int64_t ldJ, int64_t nrows,
                                                    const float* __restrict__ vh, const float* __restrict__ vl,
                                                    const double* __restrict__ w, double* __restrict__ t_out,
                                                    double* __restrict__ s_out, const int* __restrict__ done) {
-  constexpr int R = kRowsPerBlock, NW = 8;
   if (done && *done) return;
-  __shared__ double red[NW][R];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nv = ldJ / 4;
-  const int64_t per = (nv + NW - 1) / NW;
-  const int64_t kb = min(nv, wid * per), ke = min(nv, kb + per);
-  const int64_t ngroups = (nrows + R - 1) / R;
   const float4* __restrict__ h4 = reinterpret_cast<const float4*>(vh);
   const float4* __restrict__ l4 = reinterpret_cast<const float4*>(vl);
-  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const float4* __restrict__ jr[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q)      // rows past the end read the last row; their sums are dropped
-      jr[q] = reinterpret_cast<const float4*>(J + min(grp * R + q, nrows - 1) * ldJ);
-    DF a0[R], a1[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) a0[q] = a1[q] = DF{0.f, 0.f};
-    int64_t k = kb + lane;
-    for (; k + 32 < ke; k += 64) {
-      const float4 h0 = h4[k], l0 = l4[k], h1 = h4[k + 32], l1 = l4[k + 32];
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        df_add4(a0[q], jr[q][k], h0, l0);
-        df_add4(a1[q], jr[q][k + 32], h1, l1);
-      }
+  for (int64_t row = warp; row < nrows; row += nwarps) {
+    const float4* __restrict__ jr = reinterpret_cast<const float4*>(J + row * ldJ);
+    DF a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+    int64_t k = lane;
+    for (; k + 32 < nv; k += 64) {
+      df_add4(a0, jr[k], h4[k], l4[k]);
+      df_add4(a1, jr[k + 32], h4[k + 32], l4[k + 32]);
     }
-    if (k < ke) {
-      const float4 h0 = h4[k], l0 = l4[k];
-#pragma unroll
-      for (int q = 0; q < R; ++q) df_add4(a0[q], jr[q][k], h0, l0);
+    if (k < nv) df_add4(a0, jr[k], h4[k], l4[k]);
+    const double tsum = wsum(((double)a0.hi + (double)a0.lo) + ((double)a1.hi + (double)a1.lo));
+    if (lane == 0) {
+      if (t_out) t_out[row] = tsum;
+      if (s_out) s_out[row] = w ? w[row] * tsum : tsum;
     }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const double t = wsum(((double)a0[q].hi + (double)a0[q].lo) + ((double)a1[q].hi + (double)a1[q].lo));
-      if (lane == 0) red[wid][q] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < R) {
-      const int64_t row = grp * R + threadIdx.x;
-      double tsum = 0.0;
-#pragma unroll
-      for (int v = 0; v < NW; ++v) tsum += red[v][threadIdx.x];
-      if (row < nrows) {
-        if (t_out) t_out[row] = tsum;
-        if (s_out) s_out[row] = w ? w[row] * tsum : tsum;
-      }
-    }
-    __syncthreads();
   }
 }
 
 void launch_rowdot_df(const float* J, int64_t ldJ, int64_t nrows, const float* vh, const float* vl, const double* w,
                       double* t_out, double* s_out, const int* done, cudaStream_t s) {
-  const int64_t ngroups = (nrows + kRowsPerBlock - 1) / kRowsPerBlock;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, 152 * 8));
+  const int blocks = (int)std::min<int64_t>((nrows * 32 + 255) / 256, 152 * 16);
   k_rowdot_df<<<blocks, 256, 0, s>>>(J, ldJ, nrows, vh, vl, w, t_out, s_out, done); note_launch();
 }
 
