@@ -1,4 +1,4 @@
-// Declarations of the dense kernels in linalg.cu.
+// Declarations of the dense kernels in linalg.cu and the double-float GEMM in gemm_df.cu.
 #pragma once
 
 #include "ngd_internal.cuh"
