@@ -614,7 +614,7 @@ def run_train(args, rank):
     return 0
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -640,7 +640,11 @@ def main():
     ap.add_argument("--precision-study", action="store_true",
                     help="the precision form on poisson10d: all-FP64 GPU path vs FP64-accurate (double-float) "
                          "vs TF32 / BF16 tensor-core sketches, --steps NGD steps each")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     rank, world, local_rank = _env_rank()
     if args.impl == "reference":
         return run_reference(args, rank, world)
