@@ -181,6 +181,14 @@ int64_t ngd_num_params(const ngd_ctx* ctx);
 /* Number of collocation points N. */
 int64_t ngd_num_points(const ngd_ctx* ctx);
 
+/* Clock-cycle limit of every bounded device-side wait of the context's tensor-core kernels
+ * (mbarrier waits for TMA loads, MMAs and accumulators; default 4e9, about 2 s).  A wait that
+ * runs out makes the kernel stop issuing work, wait for the loads and MMAs it already issued
+ * (with the default limit), store nothing, free its tensor memory and return; the call then
+ * reports NGD_ERR_TIMEOUT and the context stays usable.  A caller may shorten the limit for
+ * faster failure detection.  cycles >= 1, else NGD_ERR_INVALID_ARG. */
+ngd_status ngd_set_wait_limit(ngd_ctx* ctx, int64_t cycles);
+
 /* Replace the stream the context enqueues on. */
 ngd_status ngd_set_stream(ngd_ctx* ctx, void* stream);
 
@@ -221,6 +229,18 @@ ngd_status ngd_gradient(ngd_ctx* ctx, const double* theta, double* g, double* r,
 
 /* ---------------------------------------------------------------- Gramian */
 
+/* Caller-supplied Jacobian for the "precompute Jacobian only" strategy (Sec. 4.1.2): replace the
+ * context's stored J by J, so that G = J^T diag(w) J (Thm. 1) is the Gramian of that J in every
+ * following call that reuses the linearization (theta = NULL): ngd_gramian_mv, ngd_gramian_diag,
+ * ngd_nystrom_sketch(_sampled), ngd_pcg_solve and ngd_vjp.  This lets the solver run on a
+ * Jacobian computed elsewhere (another residual, another network) with the context's weights w.
+ * J: device, N x p row-major with leading dimension ldJ >= p, in the context dtype (float64 for
+ * NGD_F64, float32 for NGD_F32); copied (the caller keeps ownership), asynchronous.  A later call
+ * with a non-NULL theta re-linearizes and overwrites it.  The residuals and loss are not changed.
+ * Errors: INVALID_ARG (NULL J, ldJ < p), UNSUPPORTED (the context does not store J: matrix-free
+ * mode), CUDA. */
+ngd_status ngd_set_jacobian(ngd_ctx* ctx, const void* J, int64_t ldJ);
+
 /* y = (G + mu I) v with G = J^T diag(w) J (Thm. 1, Eq. G_matrixfree) by the
  * context's matvec strategy.  theta NULL reuses the last linearization.
  * v, y: device p, must not alias.  mu >= 0. */
@@ -238,6 +258,17 @@ ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, do
  * ell <= min(p, 2048).  TF32/BF16 need an F32 context and the stored Jacobian. */
 ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step,
                               int prec, void* Omega, void* Y);
+
+/* Gramian times a block of vectors, Y = G V = J^T (w .* (J V)) (Thm. 1, Eq. G_matrixfree), by the
+ * same products and in the same arithmetic 'prec' as the sketch step of ngd_nystrom_sketch, for a
+ * test matrix V the caller chooses (Eq. nystrom_approx holds for any V of full column rank; the
+ * factor of ngd_nystrom_factor wants V orthonormal).  theta NULL reuses the linearization.
+ * V: device, p x ell column-major, leading dimension ldV >= p, context dtype.  Y: device, p x ell
+ * column-major, leading dimension ldY >= p, float64 when prec = NGD_SKETCH_F64, else the context
+ * dtype.  1 <= ell <= min(p, 2048).  Synchronises (device status).
+ * Errors: as ngd_nystrom_sketch. */
+ngd_status ngd_gramian_mm(ngd_ctx* ctx, const double* theta, int ell, const void* V, int64_t ldV, int prec, void* Y,
+                          int64_t ldY);
 
 /* Gramian diagonal diag(G) = sum_r w_r (d r_r / d theta)^2 elementwise (Eq. gram_diagonal), at
  * theta (NULL: the current linearization): stored J read once, or J recomputed by point blocks
@@ -316,12 +347,17 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* opts, ngd_
  * Scratch: a fixed array of NGD_NOALLOC_MAX_ELL doubles (8 KB) compiled into the library and
  * held by every GPU that loads it until the process exits; ell > NGD_NOALLOC_MAX_ELL returns
  * NGD_ERR_UNSUPPORTED, other bad arguments NGD_ERR_INVALID_ARG (no message: there is no context).
+ * Devices: the array's address is cached for device ordinals below NGD_NOALLOC_MAX_DEVICES (64);
+ * a call with a higher ordinal current returns NGD_ERR_UNSUPPORTED.
  * The first call on a device looks up the array's device address with that device current;
- * make that first call before any stream capture starts.  All calls share the array and it
- * keeps the last call's contents (every call overwrites the entries it reads, so nothing needs
- * clearing); calls that overlap on the GPU (e.g. on two streams) race on it and must be
- * serialised by the caller. */
+ * make that first call before any stream capture starts.  The address is cached per device
+ * together with the id of the CUDA context it was found in: after a device reset (or when the
+ * primary context is released and created again) the next call looks it up again, so that call
+ * too must come before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every call overwrites the entries it reads, so nothing needs clearing); calls
+ * that overlap on the GPU (e.g. on two streams) race on it and must be serialised by the caller. */
 #define NGD_NOALLOC_MAX_ELL 1024
+#define NGD_NOALLOC_MAX_DEVICES 64
 ngd_status ngd_precond_apply_noalloc(int dtype, int64_t p, int ell, const void* U, int64_t ldU, const double* lam,
                                      double mu, const double* v, double* z, void* stream);
 
@@ -345,10 +381,11 @@ ngd_ctx* ngd_batch_context(ngd_batch* batch, int i);   /* problem i's context (N
 const char* ngd_batch_last_error(const ngd_batch* batch);
 ngd_status ngd_batch_step(ngd_batch* batch, double* const* thetas, const ngd_step_opts* opts, ngd_step_info* infos);
 
-/* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, TF32 sketch
- * for F32 contexts (F64 otherwise chosen by ngd_step), seed 0, step 0,
- * c1 1e-4, rho 0.5, 30 trials, mu_loss_coef 0, ell_max 0 (fixed rank), ell_delta 20,
- * Gaussian test matrix, Nystrom preconditioner, rpchol_block 20. */
+/* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, FP64-accurate sketch
+ * (NGD_SKETCH_F64) in every context (in an F32 context the TF32 / BF16 sketches force a shift of
+ * their own eps that truncates the captured spectrum, so PCG needs many more iterations at small
+ * mu: they are opt-in), seed 0, step 0, c1 1e-4, rho 0.5, 30 trials, mu_loss_coef 0, ell_max 0
+ * (fixed rank), ell_delta 20, Gaussian test matrix, Nystrom preconditioner, rpchol_block 20. */
 void ngd_default_step_opts(ngd_step_opts* opts);
 
 #ifdef __cplusplus

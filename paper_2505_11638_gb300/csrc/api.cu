@@ -38,6 +38,8 @@ struct ngd_ctx {
   bool lin_valid = false;    // prep (and J when stored) match the last linearized theta
   bool tape_valid = false;   // tape matches the current prep
   bool prep_valid = false;   // prep holds the weights of a caller's theta
+  uint64_t j_version = 0;    // bumped whenever the stored J changes (caches derived from J key on it)
+  long long wait_cycles = 4000000000ll;  // limit of each bounded device-side wait (clock cycles)
 
   void* prep = nullptr;      // prepared weights of theta (working dtype)
   void* prep_t = nullptr;    // prepared tangent weights (working dtype)
@@ -156,7 +158,10 @@ ngd_status sync_status(ngd_ctx* ctx) {
   if (st & kStatNotSpd) return set_err(ctx, NGD_ERR_NOT_SPD, "Nystrom core Omega^T Y_nu is not positive definite%s");
   if (st & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
   if (st & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value in a reduction%s");
-  if (st & kStatTimeout) return set_err(ctx, NGD_ERR_TIMEOUT, "device wait timed out%s");
+  if (st & kStatTimeout)
+    return set_err(ctx, NGD_ERR_TIMEOUT, (st & kStatDrain) ? "device wait timed out, and so did the drain of the work "
+                                                              "already issued%s"
+                                                            : "device wait timed out%s");
   if (st & kStatSample)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "fewer positive diagonal entries of G than the sample size ell%s");
   return NGD_OK;
@@ -295,6 +300,7 @@ ngd_status linearize(ngd_ctx* ctx, const double* theta) {
     if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
     // the fused matvec reads the weights as FP32 pairs (the caller owns w: re-split per linearization)
     if (ctx->whf) launch_split_df(ctx->ps.w, ctx->whf, ctx->whf + ctx->N, ctx->N, ctx->N, ctx->stream);
+    ++ctx->j_version;
   } else {
     T* tape = ctx->tape_allowed ? (T*)ctx->tape : nullptr;
     nb = launch_forward<T>(ctx->net, ctx->ps, (const T*)ctx->prep, 0, ctx->N, ctx->r, ctx->lpart, tape, 0,
@@ -480,6 +486,9 @@ ngd_status sketch_second_t(ngd_ctx* ctx, int ell) {
   return check_launch(ctx);
 }
 
+template <typename T>
+ngd_status sketch_product(ngd_ctx* ctx, int ell, int prec);
+
 // test_matrix: 0 Gaussian (Philox, thin QR); 1 columns of the identity sampled with probabilities
 // proportional to diag G (the "sampling" test matrix of Sec. 3), already orthonormal.
 template <typename T>
@@ -510,6 +519,15 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
     launch_philox_omega<T>(Om, ctx->ldP, ctx->p, ell, seed, step, ctx->stream);
     TRY(thin_qr_inplace<T>(ctx, Om, ell));
   }
+  return sketch_product<T>(ctx, ell, prec);
+}
+
+// Y = G Omega for the Omega in ctx->Om (p x ell, ld ldP) in the arithmetic of prec: into ctx->Y64
+// (FP64-accurate sketch of an F32 context) or ctx->Y.
+template <typename T>
+ngd_status sketch_product(ngd_ctx* ctx, int ell, int prec) {
+  T* Om = (T*)ctx->Om;
+  T* Y = (T*)ctx->Y;
   if (prec == NGD_SKETCH_TF32 || prec == NGD_SKETCH_BF16) {
     if (!std::is_same<T, float>::value) return set_err(ctx, NGD_ERR_INVALID_ARG, "TF32/BF16 sketch needs an F32 context%s");
     if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "TF32/BF16 sketch needs the stored Jacobian%s");
@@ -519,7 +537,8 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
     }
     const char* why = nullptr;
     cudaError_t e = tc_sketch(ctx->tc, prec == NGD_SKETCH_BF16, (const float*)ctx->J, ctx->ldJ, ctx->N, ctx->p,
-                              (const float*)Om, ctx->ldP, ell, ctx->ps.w, (float*)Y, &why, ctx->stream, ctx->status);
+                              (const float*)Om, ctx->ldP, ell, ctx->ps.w, (float*)Y, &why, ctx->stream, ctx->status,
+                              ctx->wait_cycles);
     if (why) return set_err(ctx, NGD_ERR_UNSUPPORTED, "tensor-core sketch: %s", why);
     CK(e);
     return check_launch(ctx);
@@ -1258,7 +1277,7 @@ void ngd_default_step_opts(ngd_step_opts* o) {
   o->gamma = 10.0;
   o->rtol = 1e-6;
   o->maxit = 500;
-  o->sketch = NGD_SKETCH_TF32;
+  o->sketch = NGD_SKETCH_F64;
   o->seed = 0;
   o->step = 0;
   o->armijo_c1 = 1e-4;
@@ -1441,6 +1460,13 @@ const char* ngd_last_error(const ngd_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int64_t ngd_num_params(const ngd_ctx* ctx) { return ctx ? ctx->p : -1; }
 int64_t ngd_num_points(const ngd_ctx* ctx) { return ctx ? ctx->N : -1; }
 
+ngd_status ngd_set_wait_limit(ngd_ctx* ctx, int64_t cycles) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (cycles < 1) return set_err(ctx, NGD_ERR_INVALID_ARG, "the wait limit must be >= 1 cycle%s");
+  ctx->wait_cycles = (long long)cycles;
+  return NGD_OK;
+}
+
 ngd_status ngd_set_stream(ngd_ctx* ctx, void* stream) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   ctx->stream = (cudaStream_t)stream;
@@ -1489,7 +1515,7 @@ ngd_status ngd_eval(ngd_ctx* ctx, const double* theta, double* out) {
 ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* out) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!v || !out) return set_err(ctx, NGD_ERR_INVALID_ARG, "v/out is NULL%s");
-  if (!theta && !ctx->prep_valid)
+  if (!theta && !ctx->prep_valid && !(ctx->stored_j && ctx->lin_valid))
     return set_err(ctx, NGD_ERR_INVALID_ARG, "theta is NULL and the context holds no parameters%s");
   return by_dtype(ctx, [&](auto z) -> ngd_status {
     using T = decltype(z);
@@ -1507,7 +1533,7 @@ ngd_status ngd_jvp(ngd_ctx* ctx, const double* theta, const double* v, double* o
 ngd_status ngd_vjp(ngd_ctx* ctx, const double* theta, const double* cot, double* out) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!cot || !out) return set_err(ctx, NGD_ERR_INVALID_ARG, "cot/out is NULL%s");
-  if (!theta && !ctx->prep_valid)
+  if (!theta && !ctx->prep_valid && !(ctx->stored_j && ctx->lin_valid))
     return set_err(ctx, NGD_ERR_INVALID_ARG, "theta is NULL and the context holds no parameters%s");
   return by_dtype(ctx, [&](auto z) -> ngd_status {
     using T = decltype(z);
@@ -1536,6 +1562,21 @@ ngd_status ngd_gradient(ngd_ctx* ctx, const double* theta, double* g, double* r,
     }
     return check_launch(ctx);
   });
+}
+
+ngd_status ngd_set_jacobian(ngd_ctx* ctx, const void* J, int64_t ldJ) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!J || ldJ < ctx->p) return set_err(ctx, NGD_ERR_INVALID_ARG, "J is NULL or ldJ < p%s");
+  if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "the context does not store its Jacobian%s");
+  const size_t row = (size_t)ctx->p * ctx->elt;
+  // the padding columns p .. ldJ-1 of the context's J stay zero (set at creation, never written)
+  CK(cudaMemcpy2DAsync(ctx->J, (size_t)ctx->ldJ * ctx->elt, J, (size_t)ldJ * ctx->elt, row, (size_t)ctx->N,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ctx->whf) launch_split_df(ctx->ps.w, ctx->whf, ctx->whf + ctx->N, ctx->N, ctx->N, ctx->stream);
+  ctx->tape_valid = false;
+  ctx->lin_valid = true;
+  ++ctx->j_version;
+  return check_launch(ctx);
 }
 
 ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, double mu, double* y) {
@@ -1573,6 +1614,36 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
                            cudaMemcpyDeviceToDevice, ctx->stream));
     else
       CK(cudaMemcpy2DAsync(Y, w, ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_gramian_mm(ngd_ctx* ctx, const double* theta, int ell, const void* V, int64_t ldV, int prec, void* Y,
+                          int64_t ldY) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!V || !Y || V == Y) return set_err(ctx, NGD_ERR_INVALID_ARG, "V/Y NULL or aliased%s");
+  if (ell < 1 || ell > std::min<int64_t>(ctx->p, 2048) || ldV < ctx->p || ldY < ctx->p)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "ell out of range or ldV/ldY < p%s");
+  if (!valid_prec(prec)) return set_err(ctx, NGD_ERR_INVALID_ARG, "bad sketch precision%s");
+  if (ctx->dtype == NGD_F64 && prec != NGD_SKETCH_F64)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    TRY(ensure_ell(ctx, ell));
+    const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
+    // rows p .. ldP-1 of the internal copy stay zero: the products read whole padded columns
+    CK(cudaMemsetAsync(ctx->Om, 0, sp * ell, ctx->stream));
+    CK(cudaMemcpy2DAsync(ctx->Om, sp, V, (size_t)ldV * sizeof(T), w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
+    TRY(clear_status(ctx));
+    TRY(sketch_product<T>(ctx, ell, prec));
+    TRY(sync_status(ctx));
+    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+      CK(cudaMemcpy2DAsync(Y, (size_t)ldY * 8, ctx->Y64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(cudaMemcpy2DAsync(Y, (size_t)ldY * sizeof(T), ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
     return check_launch(ctx);
   });
 }

@@ -21,6 +21,7 @@ enum : int {
   kStatNonFinite = 4,
   kStatTimeout = 8,
   kStatSample = 16,      // fewer positive diagonal entries of G than the sample size
+  kStatDrain = 32,       // after a timeout, waiting for work already issued ran out as well
 };
 
 // Network description passed by value to the kernels.

@@ -17,9 +17,10 @@ void tc_destroy(TcSketch* t);
 // core).  Accumulation is FP32 in tensor memory.  On a configuration it cannot serve it
 // sets *why and returns cudaSuccess without work; a device-side wait that ran out sets the
 // status word bit kStatTimeout in *status (nullable).
+// wait_cycles: clock limit of each bounded mbarrier wait (tc_common.cuh).
 cudaError_t tc_sketch(TcSketch* t, bool bf16, const float* J, int64_t ldJ, int64_t N, int64_t p, const float* Omega,
                       int64_t ldY, int ell, const double* w, float* Y, const char** why, cudaStream_t s,
-                      int* status = nullptr);
+                      int* status, long long wait_cycles);
 
 // Plain tcgen05 GEMM D = A B^T (both K-major), exposed for tests: A (M x K, lda), B (Nn x K, ldb),
 // FP32 or BF16 operands, D (M x Nn) written as D[m*ldd_m + n*ldd_n] in FP32.

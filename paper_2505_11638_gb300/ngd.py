@@ -81,12 +81,15 @@ _SIGS = {
     "ngd_num_params": ([_P], ctypes.c_int64),
     "ngd_num_points": ([_P], ctypes.c_int64),
     "ngd_set_stream": ([_P, _P], _I),
+    "ngd_set_wait_limit": ([_P, ctypes.c_int64], _I),
     "ngd_residual": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "ngd_eval": ([_P, _P, _P], _I),
     "ngd_jvp": ([_P, _P, _P, _P], _I),
     "ngd_vjp": ([_P, _P, _P, _P], _I),
     "ngd_gradient": ([_P, _P, _P, _P, ctypes.POINTER(_D)], _I),
     "ngd_gramian_mv": ([_P, _P, _P, _D, _P], _I),
+    "ngd_set_jacobian": ([_P, _P, ctypes.c_int64], _I),
+    "ngd_gramian_mm": ([_P, _P, _I, _P, ctypes.c_int64, _I, _P, ctypes.c_int64], _I),
     "ngd_nystrom_sketch": ([_P, _P, _I, _U64, _U64, _I, _P, _P], _I),
     "ngd_nystrom_sketch_sampled": ([_P, _P, _I, _U64, _U64, _I, _P, _P, _P], _I),
     "ngd_gramian_diag": ([_P, _P, _P], _I),
@@ -154,6 +157,10 @@ def ngd_destroy(h):
     lib().ngd_destroy(h)
 
 
+def ngd_set_wait_limit(h, cycles):
+    _check(h, lib().ngd_set_wait_limit(h, int(cycles)))
+
+
 def ngd_residual(h, theta, r, want_loss=True):
     lib().ngd_set_stream(h, _stream())
     loss = ctypes.c_double(0.0)
@@ -186,6 +193,16 @@ def ngd_gradient(h, theta, g, r=None, want_loss=True):
 def ngd_gramian_mv(h, theta, v, mu, y):
     lib().ngd_set_stream(h, _stream())
     _check(h, lib().ngd_gramian_mv(h, _ptr(theta), _ptr(v), float(mu), _ptr(y)))
+
+
+def ngd_set_jacobian(h, J, ldJ):
+    lib().ngd_set_stream(h, _stream())
+    _check(h, lib().ngd_set_jacobian(h, _ptr(J), int(ldJ)))
+
+
+def ngd_gramian_mm(h, theta, ell, V, ldV, prec, Y, ldY):
+    lib().ngd_set_stream(h, _stream())
+    _check(h, lib().ngd_gramian_mm(h, _ptr(theta), int(ell), _ptr(V), int(ldV), SKETCH[prec], _ptr(Y), int(ldY)))
 
 
 def ngd_nystrom_sketch(h, theta, ell, seed, step, prec, Omega, Y):
@@ -329,6 +346,27 @@ class Context:
         if theta is not None:
             self.version += 1
         return y
+
+    def set_jacobian(self, J):
+        """Replace the stored Jacobian by J, an (N, p) CUDA tensor of the context dtype (row-major)."""
+        if not isinstance(J, torch.Tensor) or not J.is_cuda or J.dtype != self.wdtype or J.dim() != 2 \
+                or J.shape[0] != self.N or J.shape[1] != self.p or J.stride(1) != 1:
+            raise ValueError(f"J: expected an ({self.N}, {self.p}) CUDA {self.wdtype} tensor with unit column stride")
+        ngd_set_jacobian(self.handle, J, J.stride(0))
+        self.version += 1
+
+    def gramian_mm(self, theta, V, prec="f64"):
+        """Y = G V for V an (ell, p) tensor of the context dtype (column-major p x ell); Y likewise,
+        float64 when prec is "f64"."""
+        _need(V, self.wdtype, None, "V")
+        if V.dim() != 2 or V.shape[1] != self.p:
+            raise ValueError(f"V: expected shape (ell, {self.p})")
+        ell = V.shape[0]
+        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
+        ngd_gramian_mm(self.handle, theta, ell, V, self.p, prec, Y, self.p)
+        if theta is not None:
+            self.version += 1
+        return Y
 
     def nystrom_sketch(self, theta, ell, seed=0, step=0, prec="f64"):
         Om = torch.empty((ell, self.p), dtype=self.wdtype, device=self.device)   # column-major p x ell

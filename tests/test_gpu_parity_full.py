@@ -1,0 +1,232 @@
+"""GPU parity at the full sizes the bench and the large workloads run, and on caller-supplied
+Jacobians.
+
+Two kinds of comparison:
+  * the context's own Jacobian (FP32 Taylor-mode recurrences) against the FP64 oracle: bounded by
+    the FP32 rounding of J, so the tolerances are those of the FP32 path (1e-5 for a matvec);
+  * a Jacobian handed to both sides (ngd_set_jacobian): the oracle computes J in FP64, the test
+    rounds it to FP32 (a test-side operation on the oracle's output), and both sides then apply
+    G = J32^T W J32 to the same inputs, so every remaining difference is the arithmetic of the
+    kernels: double-float sums (~2^-48 per operation) against FP64.
+Element-wise checks bound each entry by the magnitude of its own terms, (|J|^T (w |J| |v|))_k, so
+that an error confined to a few entries (a wrong ragged tile, a column-split boundary) cannot hide
+in a norm.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import gramian, mlp, nystrom, philox, solve  # noqa: E402
+from paper_2505_11638_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ngd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_11638_gb300 import build
+    build.build()
+    from paper_2505_11638_gb300 import ngd as _ngd
+    _ngd.lib()
+    return _ngd
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def workload(name, n_int=None, n_bnd=None):
+    wl, ths = inputs.make_workload(name, seed=0)
+    pr = wl.problems[0]
+    if n_int is not None:
+        pr = inputs.subsample(pr, n_int, n_bnd)
+    return wl, pr, ths[0]
+
+
+def termwise_bound(J, w, v, mu):
+    """Entry k of |J|^T (w |J| |v|) + mu |v|: the sum of the magnitudes of the terms of y_k."""
+    A = np.abs(J)
+    return A.T @ (w * (A @ np.abs(v))) + mu * np.abs(v)
+
+
+def round32(J):
+    return J.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name,n_int,n_bnd", [("poisson10d", 1200, 300), ("heat4d", 450, 150)])
+def test_two_pass_matvec_large_p(ngd, name, n_int, n_bnd):
+    """p > 9216 (51073 and 133121 parameters): the stored-J matvec of an F32 context runs the row
+    pass k_rowdot_df and the column pass k_coldot_df.  (i) With its own FP32 Jacobian: against the
+    oracle's FP64 G at 1e-5, and every entry within 2e-5 of its term magnitude.  (ii) With the
+    oracle's Jacobian rounded to FP32 given to both sides: every entry within 1e-12 of its term
+    magnitude (double-float sums against FP64)."""
+    wl, pr, th = workload(name, n_int, n_bnd)
+    J = mlp.jacobian(pr, th)
+    assert pr.p > 9216
+    ctx = ngd.Context(pr, dtype="f32")
+    rng = np.random.default_rng(21)
+    mu = 1e-4
+    v = rng.standard_normal(pr.p)
+    y = host(ctx.gramian_mv(dev(th), dev(v), mu))
+    y_o = gramian.gramian_mv(J, pr.w, v, mu)
+    bound = termwise_bound(J, pr.w, v, mu)
+    assert rel(y, y_o) <= 1e-5
+    assert np.all(np.abs(y - y_o) <= 2e-5 * bound)
+    J32 = round32(J)
+    ctx.set_jacobian(dev(J32, torch.float32))
+    for mu2 in [mu, 0.0]:
+        v = rng.standard_normal(pr.p)
+        y = host(ctx.gramian_mv(None, dev(v), mu2))
+        y_o = gramian.gramian_mv(J32, pr.w, v, mu2)
+        err = np.abs(y - y_o) / termwise_bound(J32, pr.w, v, mu2)
+        assert err.max() <= 1e-12, (mu2, err.max(), int(err.argmax()))
+    ctx.close()
+
+
+def test_gramian_mm_fp64_accurate_exact_jacobian(ngd):
+    """Y = G V through ngd_gramian_mm in the FP64-accurate arithmetic of an F32 context, for V and
+    J given to both sides (5-D Poisson, 1500 points, ell = 130: ragged 128-wide tiles): against
+    FP64 at 1e-12 in norm, each entry within 1e-11 of its term magnitude; the Nystrom core
+    V^T G V symmetric to 1e-12."""
+    wl, pr, th = workload("poisson5d", 1200, 300)
+    J32 = round32(mlp.jacobian(pr, th))
+    ctx = ngd.Context(pr, dtype="f32")
+    ctx.set_jacobian(dev(J32, torch.float32))
+    ell = 130
+    V = round32(nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 9, 2)))
+    Y = host(ctx.gramian_mm(None, dev(V.T, torch.float32), "f64")).T
+    Y_o = J32.T @ (pr.w[:, None] * (J32 @ V))
+    B = np.abs(J32).T @ (pr.w[:, None] * (np.abs(J32) @ np.abs(V)))
+    assert rel(Y, Y_o) <= 1e-12
+    assert (np.abs(Y - Y_o) / B).max() <= 1e-11
+    M = V.T @ Y
+    assert np.linalg.norm(M - M.T) / np.linalg.norm(M) <= 1e-12
+    ctx.close()
+
+
+def test_fused_pcg_headline_size_exact_jacobian(ngd):
+    """The 5-D Poisson workload at its full size (N = 5000, p = 8769) and the bench's rank
+    ell = 500: the whole PCG in one cooperative kernel (U staged through shared memory in chunks,
+    row pass over the stored J), on the oracle's Jacobian rounded to FP32.  The Nystrom factor is
+    formed by both sides from the same Omega and Y; then pCG from the same g at fixed iteration
+    counts.  mu = 1e-13 keeps the spectrum below the captured part wide enough that 30 iterations
+    still make progress (relres ~1e-4)."""
+    wl, pr, th = workload("poisson5d")
+    J32 = round32(mlp.jacobian(pr, th))
+    g_o, _, _ = mlp.gradient(pr, th)
+    G = J32.T @ (pr.w[:, None] * J32)
+    ell = 500
+    Om = round32(nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 0, 0)))
+    Y = G @ Om
+    U_o, lam_o, nu_o = nystrom.nystrom_factor(Om, Y, nystrom.MANTISSA_BITS["df"])
+    ctx = ngd.Context(pr, dtype="f32")
+    ctx.set_jacobian(dev(J32, torch.float32))
+    U, lam, nu = ctx.nystrom_factor(ell, dev(Om.T, torch.float32), dev(Y.T), prec="f64")
+    assert abs(nu - nu_o) <= 1e-12 * nu_o
+    lam_g = host(lam)
+    top = lam_o > 1e-6 * lam_o[0]
+    assert rel(lam_g[top], lam_o[top]) <= 1e-8
+    g = dev(g_o)
+    for mu, ks in [(1e-7, [1, 2, 3]), (1e-13, [3, 10, 30])]:
+        A = lambda v: G @ v + mu * v    # noqa: E731
+        Pinv = lambda v: nystrom.precond_apply(U_o, lam_o, mu, v)    # noqa: E731
+        for k in ks:
+            d, it, rr = ctx.pcg_solve(None, g, mu, U, lam, ell, rtol=0.0, maxit=k)
+            d_o, it_o, rr_o = solve.pcg(A, g_o, Pinv, 0.0, k)
+            assert it == it_o == k
+            assert rel(host(d), d_o) <= 1e-7, (mu, k, rel(host(d), d_o))
+            assert abs(rr - rr_o) <= 1e-5 * rr_o, (mu, k, rr, rr_o)
+    # to tolerance: the true residual of the returned direction under the oracle's operator
+    mu = 1e-13
+    d, it, rr = ctx.pcg_solve(None, g, mu, U, lam, ell, rtol=1e-6, maxit=1000)
+    res = G @ host(d) + mu * host(d) - g_o
+    assert rr <= 1e-6 and np.linalg.norm(res) <= 2e-6 * np.linalg.norm(g_o)
+    ctx.close()
+
+
+def test_ngd_step_headline_size(ngd):
+    """One NGD step of the bench workload as the bench runs it (N = 5000, p = 8769, ell = 500,
+    mu = 1e-7, FP64-accurate sketch, the context's own FP32 Jacobian) at fixed PCG iteration
+    counts, against the oracle's FP64 step with the same Philox test matrix and the same shift
+    format: loss, lambda_1, step length and update agree to the FP32 rounding of J; the direction
+    solves the oracle's FP64 system to that accuracy."""
+    wl, pr, th = workload("poisson5d")
+    J = mlp.jacobian(pr, th)
+    g_o, _, _ = mlp.gradient(pr, th)
+    ctx = ngd.Context(pr, dtype="f32")
+    for k in [2, 5]:
+        t = dev(th)
+        info = ctx.step(t, ell=500, mu=1e-7, rtol=0.0, maxit=k, seed=0, step=0, sketch="f64")
+        th1_o, info_o = solve.ngd_step(pr, th, ell=500, mu=1e-7, rtol=0.0, maxit=k, seed=0, step=0,
+                                       mant_bits=nystrom.MANTISSA_BITS["df"])
+        assert info["pcg_iters"] == info_o.pcg_iters == k
+        assert abs(info["loss_before"] - info_o.loss_before) <= 1e-5 * info_o.loss_before
+        assert abs(info["lam1"] - info_o.lam1) <= 1e-5 * info_o.lam1
+        assert info["alpha"] == info_o.alpha
+        assert info["loss_after"] < info["loss_before"]
+        upd = th - host(t)
+        assert rel(upd, th - th1_o) <= 2e-3, (k, rel(upd, th - th1_o))
+        d = upd / info["alpha"]
+        res = J.T @ (pr.w * (J @ d)) + 1e-7 * d - g_o
+        assert np.linalg.norm(res) <= 1e-3 * np.linalg.norm(g_o)
+    ctx.close()
+
+
+def test_fused_pcg_small_exact_jacobian_tight(ngd):
+    """The fused PCG on a 1120-point subset (ell = 60, mu = 1e-5) with the oracle's Jacobian rounded
+    to FP32 on both sides: the direction agrees with FP64 pCG at fixed iteration counts to 1e-8,
+    three orders below the FP32-Jacobian tolerance the context's own J allows."""
+    wl, pr, th = workload("poisson5d", 900, 220)
+    J32 = round32(mlp.jacobian(pr, th))
+    G = J32.T @ (pr.w[:, None] * J32)
+    g_o, _, _ = mlp.gradient(pr, th)
+    ell, mu = 60, 1e-5
+    Om = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 5, 0))
+    U_o, lam_o, _ = nystrom.nystrom_factor(Om, G @ Om)
+    ctx = ngd.Context(pr, dtype="f32")
+    ctx.set_jacobian(dev(J32, torch.float32))
+    g = dev(g_o)
+    for udt in [torch.float64, torch.float32]:
+        U_d = dev(U_o.T, udt)
+        U_p = host(U_d).T
+        for k in [1, 5, 20, 60]:
+            d, it, rr = ctx.pcg_solve(None, g, mu, U_d, dev(lam_o), ell, rtol=0.0, maxit=k)
+            d_o, it_o, _ = solve.pcg(lambda v: G @ v + mu * v, g_o,
+                                     lambda v: nystrom.precond_apply(U_p, lam_o, mu, v), 0.0, k)
+            assert it == it_o == k
+            assert rel(host(d), d_o) <= 1e-8, (udt, k, rel(host(d), d_o))
+    ctx.close()
+
+
+def test_tensor_core_wait_timeout_recovers(ngd):
+    """Failure detection of the tcgen05 kernels: with a one-cycle wait limit every role's first
+    wait runs out before its TMA loads land; the kernel drains what it issued, stores nothing,
+    frees its tensor memory and the call reports TIMEOUT.  With the default limit restored the
+    same context computes the same sketch as a fresh context."""
+    wl, pr, th = workload("poisson5d", 700, 180)
+    ctx = ngd.Context(pr, dtype="f32")
+    t = dev(th)
+    ngd.ngd_set_wait_limit(ctx.handle, 1)
+    with pytest.raises(ngd.NGDError) as e:
+        ctx.nystrom_sketch(t, 130, seed=3, step=1, prec="tf32")
+    assert e.value.name == "TIMEOUT"
+    ngd.ngd_set_wait_limit(ctx.handle, 4_000_000_000)
+    Om, Y = ctx.nystrom_sketch(t, 130, seed=3, step=1, prec="tf32")
+    ref = ngd.Context(pr, dtype="f32")
+    Om2, Y2 = ref.nystrom_sketch(dev(th), 130, seed=3, step=1, prec="tf32")
+    assert torch.equal(Om, Om2) and torch.equal(Y, Y2)
+    ref.close()
+    ctx.close()

@@ -14,6 +14,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+from oracle import nystrom  # noqa: E402
 from paper_2505_11638_gb300 import inputs  # noqa: E402
 
 
@@ -28,8 +29,9 @@ def ngd():
     return _ngd
 
 
-def _call(ngd, dtype, p, ell, U, lam, mu, v, z):
-    return ngd.lib().ngd_precond_apply_noalloc(ngd.DTYPES[dtype], p, ell, ctypes.c_void_p(U.data_ptr()), p,
+def _call(ngd, dtype, p, ell, U, lam, mu, v, z, ldU=None):
+    return ngd.lib().ngd_precond_apply_noalloc(ngd.DTYPES[dtype], p, ell, ctypes.c_void_p(U.data_ptr()),
+                                               p if ldU is None else ldU,
                                                ctypes.c_void_p(lam.data_ptr()), float(mu),
                                                ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
                                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -71,3 +73,34 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(ngd):
     assert _call(ngd, "f64", p, ell, U, lam, 1e-3, v, z) == 9      # NGD_ERR_UNSUPPORTED
     assert _call(ngd, "f64", p, 0, U, lam, 1e-3, v, z) == 1        # NGD_ERR_INVALID_ARG
     assert _call(ngd, "f64", p, 10, U, lam, 1e-3, v, v) == 1       # aliased v, z
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_noalloc_at_its_maximum_rank_with_padded_columns(ngd, dtype):
+    """ell = NGD_NOALLOC_MAX_ELL (the whole scratch array; the largest dynamic shared memory the
+    apply takes) with a leading dimension ldU = p + 8: against the FP64 oracle of Alg. 4 on the
+    same (rounded) U, and against the context apply on a contiguous copy."""
+    pr, _ = inputs.small_problem(d=3, widths=[3, 32, 32, 1], n_int=40, n_bnd=10, seed=98)
+    p, ell, ldU = pr.p, 1024, pr.p + 8
+    assert p >= ell
+    wd = torch.float64 if dtype == "f64" else torch.float32
+    rng = np.random.default_rng(6)
+    Q = np.linalg.qr(rng.standard_normal((p, ell)))[0]
+    lam = np.sort(rng.uniform(1e-3, 10.0, ell))[::-1].copy()
+    Upad = torch.full((ell, ldU), float("nan"), dtype=wd, device="cuda")   # padding never read
+    Upad[:, :p] = torch.tensor(Q.T, dtype=wd, device="cuda")
+    U_r = Upad[:, :p].double().cpu().numpy().T                                # the rounded U both sides use
+    lam_d = torch.tensor(lam, device="cuda")
+    ctx = ngd.Context(pr, dtype=dtype)
+    for call, mu in enumerate([1e-4, 2e-2]):
+        v_h = rng.standard_normal(p)
+        v = torch.tensor(v_h, device="cuda")
+        z = torch.full((p,), float("nan"), dtype=torch.float64, device="cuda")
+        assert _call(ngd, dtype, p, ell, Upad, lam_d, mu, v, z, ldU=ldU) == 0
+        torch.cuda.synchronize()
+        z_o = nystrom.precond_apply(U_r, lam, mu, v_h)
+        z_h = z.cpu().numpy()
+        assert np.linalg.norm(z_h - z_o) <= 1e-12 * np.linalg.norm(z_o), call
+        z_ref = ctx.precond_apply(ell, Upad[:, :p].contiguous(), lam_d, mu, v)
+        assert float(torch.linalg.norm(z - z_ref) / torch.linalg.norm(z_ref)) <= 1e-12, call
+    ctx.close()
