@@ -5,11 +5,12 @@ points, FP32 activations and Jacobian, FP64 CG reductions, ell = 500, mu = 1e-7,
 synthetic Monte-Carlo points drawn from a fixed seed.  One step = one ngd_step: gradient and
 Jacobian, Gaussian test matrix, sketch, Nystrom factor, preconditioned CG, Armijo, update.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sketch f64|f32|tf32|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sketch f64|df|f32|tf32|bf16]
 
---sketch f64 (default) forms the sketch and the Nystrom factor in FP64-accurate arithmetic
-(double-float on the FP32 pipes for the FP32 Jacobian); f32/tf32/bf16 are the lower-precision
-variants of the precision study (larger shift nu, more PCG iterations).
+--sketch f64 (default) forms the sketch in FP64-accurate arithmetic on the tensor cores (exact
+sums of BF16 digit-plane products of the FP32 Jacobian) and the Nystrom factor in double-float;
+df forms the same FP64-accurate sketch in double-float on the FP32 pipes; f32/tf32/bf16 are the
+lower-precision variants of the precision study (larger shift nu, more PCG iterations).
 
 N > 1 runs under torchrun: every rank steps an independent replica (its own seed), with no
 data-path collective; the barrier and the max-over-ranks timing use the process group.
@@ -644,7 +645,7 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--sketch", default="f64", choices=["f64", "f32", "tf32", "bf16"])
+    ap.add_argument("--sketch", default="f64", choices=["f64", "df", "f32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"],
                     help="batch64: the batching form, 64 problems of uneven size per step (ngd_batch_step)")

@@ -55,14 +55,23 @@ typedef enum {
 typedef enum { NGD_F64 = 0, NGD_F32 = 1 } ngd_dtype;
 
 /* Arithmetic of the sketch GEMMs Z = J Omega and Y = J^T (w .* Z) and of the factor:
- *   F64  FP64-accurate.  In an F64 context: FP64 CUDA cores.  In an F32 context: the FP32
- *        Jacobian and Omega are multiplied with double-float arithmetic on the FP32 pipes
- *        (exact products, TwoSum accumulation), Y is float64 and the factor keeps FP64 accuracy;
- *        only U is rounded to FP32.  Shift nu = eps64(||Y||_F), the paper's algorithm.
+ *   F64  FP64-accurate.  In an F64 context: FP64 CUDA cores.  In an F32 context with the stored
+ *        Jacobian: the tcgen05 tensor cores on an error-free split of the FP32 operands into BF16
+ *        digit planes (J by rows and Omega by columns scaled by powers of two, signed base-256
+ *        digits; Z split likewise); digit products of the leading levels are summed exactly in
+ *        FP32 tensor memory over K-chunks of 256 and the chunk sums in double-float, leaving
+ *        ~2^-46 of the term magnitudes.  Y is float64; the factor runs in double-float (FP64-
+ *        accurate) with shift nu = eps_48(||Y||_F).
  *   F32  FP32 CUDA cores with FP64 cross-tile sums; Y float32; shift eps32(||Y||_F).
  *   TF32 / BF16 tcgen05 tensor cores (operands rounded, FP32 accumulation in TMEM); Y float32;
- *        shift eps_TF32 / eps_BF16 (||Y||_F). */
-typedef enum { NGD_SKETCH_F64 = 0, NGD_SKETCH_F32 = 1, NGD_SKETCH_TF32 = 2, NGD_SKETCH_BF16 = 3 } ngd_sketch_prec;
+ *        shift eps_TF32 / eps_BF16 (||Y||_F).
+ *   DF   FP64-accurate like F64, on the FP32 CUDA cores: exact FP32 products summed in double-float
+ *        (the same accuracy class, without tensor cores).  F32 contexts only.
+ * The sampled sketch (ngd_nystrom_sketch_sampled) and the matrix-free mode form the FP64-accurate
+ * products in double-float for F64 and DF alike. */
+typedef enum {
+  NGD_SKETCH_F64 = 0, NGD_SKETCH_F32 = 1, NGD_SKETCH_TF32 = 2, NGD_SKETCH_BF16 = 3, NGD_SKETCH_DF = 4
+} ngd_sketch_prec;
 
 /* Interior residual: Poisson  r = Delta u + f  (Eq. energy_poisson);
  *                    heat     r = u_t - kappa Delta u - f, coordinate 0 = t.

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "linalg.cuh"
+#include "sketch_oz.cuh"
 #include "sketch_tc.cuh"
 
 using namespace ngd;
@@ -74,6 +75,7 @@ struct ngd_ctx {
   size_t gpart_elems = 0;
   int* perm = nullptr;
   TcSketch* tc = nullptr;
+  OzSketch* oz = nullptr;    // digit planes of the FP64-accurate tensor-core sketch
   // sampling test matrix: diag G, race keys, selected columns (grown on demand)
   double* gdiag = nullptr;
   unsigned long long* samp_keys = nullptr;
@@ -397,12 +399,16 @@ ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* 
 // format (the shift of App. A, read as MATLAB's eps of the sketch's precision).
 int mantissa_bits(int prec) {
   switch (prec) {
+    case NGD_SKETCH_DF: return 48;
     case NGD_SKETCH_TF32: return 10;
     case NGD_SKETCH_BF16: return 7;
     case NGD_SKETCH_F32: return 23;
     default: return 52;
   }
 }
+
+// FP64-accurate sketch (Y in float64): the tensor-core digit-plane form or the double-float form
+bool acc64(int prec) { return prec == NGD_SKETCH_F64 || prec == NGD_SKETCH_DF; }
 
 template <typename T>
 ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell) {
@@ -506,7 +512,7 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
     launch_selection_omega<T>(Om, ctx->ldP, ctx->samp_idx, ell, ctx->stream);
     // G Omega = G[:, S]: the first product is a gather of Jacobian columns
     if (ctx->stored_j && prec != NGD_SKETCH_TF32 && prec != NGD_SKETCH_BF16) {
-      if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64) {
+      if (std::is_same<T, float>::value && acc64(prec)) {
         launch_gather_cols<float, double>((const float*)ctx->J, ctx->ldJ, ctx->N, ctx->samp_idx, ell, ctx->ps.w,
                                           ctx->Zw64, ctx->stream);
         return sketch_second_df(ctx, ell);
@@ -543,10 +549,24 @@ ngd_status sketch_product(ngd_ctx* ctx, int ell, int prec) {
     CK(e);
     return check_launch(ctx);
   }
-  if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64) {
+  if (std::is_same<T, float>::value && acc64(prec)) {
+    if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "the FP64-accurate sketch needs the stored Jacobian%s");
+    if (prec == NGD_SKETCH_F64) {
+      // FP64-accurate sketch on the tensor cores: exact sums of BF16 digit-plane products
+      if (!ctx->oz) {
+        ctx->oz = oz_create();
+        if (!ctx->oz) return set_err(ctx, NGD_ERR_OOM, "tensor-core sketch state%s");
+      }
+      const char* why = nullptr;
+      cudaError_t e = oz_sketch(ctx->oz, (const float*)ctx->J, ctx->ldJ, ctx->N, ctx->p, ctx->j_version, (const float*)Om,
+                                ctx->ldP, ell, ctx->ps.w, ctx->Y64, &why, ctx->stream, ctx->status, ctx->wait_cycles);
+      if (why) return set_err(ctx, NGD_ERR_UNSUPPORTED, "tensor-core sketch: %s", why);
+      if (e == cudaErrorMemoryAllocation) return set_err(ctx, NGD_ERR_OOM, "tensor-core sketch workspace%s");
+      CK(e);
+      return check_launch(ctx);
+    }
     // FP64-accurate sketch of the FP32 Jacobian (double-float arithmetic): Zw (FP64) = diag(w) J Om,
     // Y64 = J^T Zw.  The Nystrom core then resolves G's spectrum down to eps64 ||Y||, as in the paper.
-    if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "the FP64-accurate sketch needs the stored Jacobian%s");
     // K is split where that fills the GPU's block slots more evenly; the slices' FP64 partials
     // are then added in a fixed order
     GemmDfArgs<float, float> g1;
@@ -691,7 +711,7 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
 template <typename T>
 ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) {
   TRY(ensure_ell(ctx, ell));
-  if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64) return factor_df(ctx, ell, shift_scale);
+  if (std::is_same<T, float>::value && acc64(prec)) return factor_df(ctx, ell, shift_scale);
   const T* Om = (const T*)ctx->Om;
   const T* Y = (const T*)ctx->Y;
   T* Bm = (T*)ctx->B;
@@ -1172,8 +1192,8 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
     // Alg. 4, damping: mu fixed, gamma eps lambda_1, or the Sec. 5 maximum with c L^2
     launch_set_mu(ctx->lam, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, ctx->stream);
-    u_f64 = !std::is_same<T, float>::value || o->sketch == NGD_SKETCH_F64;
-    Ust = std::is_same<T, float>::value && o->sketch == NGD_SKETCH_F64 ? (const void*)ctx->U64 : ctx->U;
+    u_f64 = !std::is_same<T, float>::value || acc64(o->sketch);
+    Ust = std::is_same<T, float>::value && acc64(o->sketch) ? (const void*)ctx->U64 : ctx->U;
   }
   phase.next("pcg");
   // Alg. 3, direction: pCG on (G + mu I) d = g with the preconditioner of Alg. 4 or Alg. 5
@@ -1449,6 +1469,7 @@ void ngd_destroy(ngd_ctx* ctx) {
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->tc) tc_destroy(ctx->tc);
+  if (ctx->oz) oz_destroy(ctx->oz);
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
@@ -1591,7 +1612,7 @@ ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, do
   });
 }
 
-static bool valid_prec(int prec) { return prec >= NGD_SKETCH_F64 && prec <= NGD_SKETCH_BF16; }
+static bool valid_prec(int prec) { return prec >= NGD_SKETCH_F64 && prec <= NGD_SKETCH_DF; }
 
 ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step, int prec,
                               void* Omega, void* Y) {
@@ -1609,7 +1630,7 @@ ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64
     TRY(sync_status(ctx));
     const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
     CK(cudaMemcpy2DAsync(Omega, w, ctx->Om, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+    if (std::is_same<T, float>::value && acc64(prec))
       CK(cudaMemcpy2DAsync(Y, (size_t)ctx->p * 8, ctx->Y64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
                            cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -1639,7 +1660,7 @@ ngd_status ngd_gramian_mm(ngd_ctx* ctx, const double* theta, int ell, const void
     TRY(clear_status(ctx));
     TRY(sketch_product<T>(ctx, ell, prec));
     TRY(sync_status(ctx));
-    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+    if (std::is_same<T, float>::value && acc64(prec))
       CK(cudaMemcpy2DAsync(Y, (size_t)ldY * 8, ctx->Y64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
                            cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -1676,7 +1697,7 @@ ngd_status ngd_nystrom_sketch_sampled(ngd_ctx* ctx, const double* theta, int ell
     const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
     CK(cudaMemcpyAsync(idx, ctx->samp_idx, (size_t)ell * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpy2DAsync(Omega, w, ctx->Om, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+    if (std::is_same<T, float>::value && acc64(prec))
       CK(cudaMemcpy2DAsync(Y, (size_t)ctx->p * 8, ctx->Y64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
                            cudaMemcpyDeviceToDevice, ctx->stream));
     else
@@ -1697,13 +1718,13 @@ ngd_status ngd_nystrom_factor(ngd_ctx* ctx, int ell, const void* Omega, const vo
     TRY(ensure_ell(ctx, ell));
     const size_t w = (size_t)ctx->p * sizeof(T), sp = (size_t)ctx->ldP * sizeof(T);
     CK(cudaMemcpy2DAsync(ctx->Om, sp, Omega, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+    if (std::is_same<T, float>::value && acc64(prec))
       CK(cudaMemcpy2DAsync(ctx->Y64, (size_t)ctx->ldP * 8, Y, (size_t)ctx->p * 8, (size_t)ctx->p * 8, ell,
                            cudaMemcpyDeviceToDevice, ctx->stream));
     else
       CK(cudaMemcpy2DAsync(ctx->Y, sp, Y, w, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
     TRY(factor_internal<T>(ctx, ell, prec, shift_scale));
-    if (std::is_same<T, float>::value && prec == NGD_SKETCH_F64)
+    if (std::is_same<T, float>::value && acc64(prec))
       CK(cudaMemcpy2DAsync(U, (size_t)ctx->p * 8, ctx->U64, (size_t)ctx->ldP * 8, (size_t)ctx->p * 8, ell,
                            cudaMemcpyDeviceToDevice, ctx->stream));
     else

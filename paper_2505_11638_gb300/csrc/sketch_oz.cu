@@ -1,0 +1,505 @@
+// FP64-accurate Nystrom sketch Y = G Omega = J^T diag(w) (J Omega) (App. A, the sketch step) on
+// the tcgen05 tensor cores, for an FP32 Jacobian.
+//
+// Method: an error-free split of the operands into BF16 "digit planes" (the splitting idea of
+// Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication and its applications", Numer. Algorithms 59 (2012),
+// here with signed base-256 digits and exact fixed-point accumulation):
+//   * each row n of J is scaled by a power of two 2^-e_n (e_n: max_k |J_nk| < 2^e_n) and written
+//     as J_nk = 2^(e_n - 7) (a_0 + a_1 2^-8 + ... + a_4 2^-32) with integer digits |a_s| <= 128
+//     (round-to-nearest digits: each next digit takes the rounding remainder times 256);
+//   * each column j of Omega likewise with 5 digits (exact for every entry above 2^-16 of its
+//     column's largest; below that, truncated at 2^-41 of it);
+//   * Z'' = diag(w) diag(2^e_n) (J Omega) is split per column with 6 digits;
+//   * digit s is stored as the BF16 number a_s 2^(-8 s) (exact: 8 significant bits), so a product
+//     of digit planes s and t carries its weight 2^(-8 (s + t)) by itself.
+// GEMM1 Z = J Omega and GEMM2 Y = J^T Z'' then become sums over digit-plane products (s, t) with
+// s + t <= 5 ("levels"; the dropped levels weigh <= 2^-48 of the leading one).  Levels 0, 1 and 2
+// are summed exactly: within one level every product is an integer times the level's weight, a
+// K-chunk of 256 keeps every partial sum below 2^24 such units (at most 3 pairs x 256 x 2^14),
+// and the tensor core's FP32 accumulation of such sums is exact (measured on GB300 with integer
+// digit data up to 2^24: no rounding; mixed magnitudes inside one 16-wide group do round, which
+// the split avoids by giving every MMA a single (s, t) pair).  Levels 3..5 (weight <= 2^-24) share
+// one FP32 accumulator whose rounding stays below 2^-46 of the leading level.  Each CTA sums one
+// 128 x 128 output tile over one K-chunk into four TMEM accumulators (512 columns), combines them
+// into a double-float value, and writes it as a split-K partial; a second kernel adds the
+// partials of a tile in a fixed order (deterministic) and applies the power-of-two scales.
+//
+// Kernel structure (k_oz_gemm): warp 0 lane 0 issues TMA loads of 16 KB tiles (128 rows x 64
+// BF16, 128-byte swizzle) into a ring of 12 shared-memory slots; per 64-wide k-block, the B digit
+// tiles (descending digit) and then the A digit tiles (ascending digit).  Warp 1 lane 0 issues
+// tcgen05.mma (kind::f16, M = N = 128, K = 16) pair by pair and releases each tile after its last
+// use.  Warps 2..5 drain the accumulators with tcgen05.ld.  Waits follow the bounded protocol of
+// tc_common.cuh.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+
+#include "df.cuh"
+#include "ngd_internal.cuh"
+#include "sketch_oz.cuh"
+#include "tc_common.cuh"
+
+namespace ngd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kDigJ = 5;       // digits of the row-scaled Jacobian
+constexpr int kDigOm = 5;      // digits of the column-scaled test matrix
+constexpr int kDigZ = 6;       // digits of the column-scaled Z''
+constexpr int kLevels = 5;     // pairs (s, t) with s + t <= kLevels are kept
+constexpr int kChunk = 256;    // K per CTA: exact level sums (3 pairs x 256 x 2^14 < 2^24)
+constexpr int kBM = 128, kBN = 128, kBK = 64;
+constexpr int kTile = kBM * kBK * 2;                        // 16 KB: 128 rows x 128 bytes
+constexpr int kRing = 12;
+constexpr int kSmem = kRing * kTile + 1024 + 512;
+constexpr size_t kPartialCap = size_t(1) << 30;             // bytes of split-K partials per launch
+
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// exponent e with m < 2^e (m >= 0; 0 for m = 0)
+__device__ __forceinline__ int exp_above(float m) {
+  int e = 0;
+  frexpf(m, &e);
+  return m > 0.0f ? e : 0;
+}
+__device__ __forceinline__ int exp_above_d(double m) {
+  int e = 0;
+  frexp(m, &e);
+  return m > 0.0 ? e : 0;
+}
+
+// ---------------------------------------------------------------------------- splits
+// e_n of every row of J (max over the row's p entries; padding columns are zero).  One warp per row.
+__global__ void k_oz_rowexp(const float* __restrict__ J, int64_t ldJ, int64_t N, int* __restrict__ jexp) {
+  const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (n >= N) return;
+  const float4* row = reinterpret_cast<const float4*>(J + n * ldJ);
+  float m = 0.0f;
+  for (int64_t i = lane; i < ldJ / 4; i += 32) {
+    const float4 v = row[i];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) jexp[n] = exp_above(m);
+}
+
+// Digit planes of the row-scaled J in both layouts: JD[s] (N x ldJ, as J) for Z = J Omega and
+// JDT[s] (ldJ x ldN, transposed; rows n >= N zero) for Y = J^T Z''.  32 x 32 tiles.
+__global__ void k_oz_split_rows(const float* __restrict__ J, int64_t ldJ, int64_t N, const int* __restrict__ jexp,
+                                __nv_bfloat16* __restrict__ JD, __nv_bfloat16* __restrict__ JDT, int64_t ldN) {
+  __shared__ __nv_bfloat16 tile[kDigJ][32][34];
+  const int64_t k0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 32; i += blockDim.y) {
+    const int64_t n = n0 + i, k = k0 + tx;
+    float a[kDigJ];
+    if (n < N) {
+      float r = ldexpf(J[n * ldJ + k], 7 - jexp[n]);      // |r| < 128
+#pragma unroll
+      for (int s = 0; s < kDigJ; ++s) {
+        a[s] = rintf(r);
+        r = (r - a[s]) * 256.0f;                            // exact
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < kDigJ; ++s) a[s] = 0.0f;
+    }
+#pragma unroll
+    for (int s = 0; s < kDigJ; ++s) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(ldexpf(a[s], -8 * s));   // exact
+      tile[s][i][tx] = b;
+      if (n < N) JD[(int64_t)s * N * ldJ + n * ldJ + k] = b;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += blockDim.y) {
+    const int64_t k = k0 + i, n = n0 + tx;
+#pragma unroll
+    for (int s = 0; s < kDigJ; ++s) JDT[(int64_t)s * ldJ * ldN + k * ldN + n] = tile[s][tx][i];
+  }
+}
+
+// Column exponents of a column-major matrix V (rows x cols, leading dimension ld): one block per
+// column.
+template <typename T>
+__global__ void k_oz_colexp(const T* __restrict__ V, int64_t ld, int64_t rows, int* __restrict__ cexp) {
+  __shared__ double red[32];
+  const T* col = V + (int64_t)blockIdx.x * ld;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) m = fmax(m, fabs((double)col[i]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) cexp[blockIdx.x] = exp_above_d(m);
+  }
+}
+
+// Digit planes D[t] (cols x ld, the layout of V) of the column-scaled column-major V.
+template <typename T, int S>
+__global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t cols, const int* __restrict__ cexp,
+                                __nv_bfloat16* __restrict__ D) {
+  const int64_t total = ld * cols;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += st) {
+    const int64_t j = idx / ld;
+    const int e = cexp[j];
+    T r = sizeof(T) == 4 ? (T)ldexpf((float)V[idx], 7 - e) : (T)ldexp((double)V[idx], 7 - e);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const T a = sizeof(T) == 4 ? (T)rintf((float)r) : (T)rint((double)r);
+      r = (r - a) * (T)256;                                               // exact
+      D[(int64_t)s * total + idx] = __float2bfloat16_rn((float)ldexp((double)a, -8 * s));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- digit-plane GEMM
+// Accumulator of the level s + t: levels 0, 1, 2 exact, levels 3.. shared (TMEM columns acc*128).
+__host__ __device__ constexpr int acc_of(int level) { return level < 3 ? level : 3; }
+
+// Split-K partial of D = sum over kept (s, t) of A_s B_t^T on one 128 x 128 tile and one K-chunk:
+// A planes (tmA: cols = K, rows = M, planes = SA), B planes (tmB: cols = K, rows = Nout, planes =
+// SB), both K-major.  Grid: (Nout tiles, M tiles, chunks of this launch).  Partial (hi, lo) of
+// output (m, n) of local chunk c at P[(c * ldL + n) * ldM + m].
+template <int SA, int SB>
+__global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                   const __grid_constant__ CUtensorMap tmB, int64_t K, int chunk0,
+                                                   float2* __restrict__ P, int64_t ldL, int64_t ldM, int* status,
+                                                   long long wait_cycles) {
+  static_assert(SB - 1 <= kLevels && SA - 1 <= kLevels, "every digit plane takes part in a kept pair");
+  constexpr int T = SA + SB;   // tiles per k-block: B_{SB-1} .. B_0, then A_0 .. A_{SA-1}
+  // a k-block's tiles fit the ring together: a tile only ever waits for a slot of an earlier
+  // k-block, which the MMA issuer can always finish (no circular wait)
+  static_assert(T <= kRing, "one k-block of digit tiles must fit the ring");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kRing * kTile);
+  uint64_t* empty = full + kRing;
+  uint64_t* accum = empty + kRing;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile uint32_t* started_out = reinterpret_cast<volatile uint32_t*>(tmem_slot + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
+  const int64_t k0 = (int64_t)(chunk0 + (int)blockIdx.z) * kChunk;
+  const int64_t klen = K - k0 < kChunk ? K - k0 : kChunk;
+  const int nkb = (int)((klen + kBK - 1) / kBK);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    *started_out = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  int err = 0;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
+      const int x = (int)(k0 + (int64_t)kb * kBK);
+      for (int q = 0; q < T; ++q) {
+        const int i = kb * T + q, slot = i % kRing, use = i / kRing;
+        if (*abort_flag) break;
+        if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, wait_cycles)) {
+          err |= 1;
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full[slot], kTile);
+        if (q < SB)
+          tma_load_3d(smem + slot * kTile, &tmB, x, n0, SB - 1 - q, &full[slot]);
+        else
+          tma_load_3d(smem + slot * kTile, &tmA, x, m0, q - SB, &full[slot]);
+        issued = i + 1;
+      }
+    }
+    for (int j = issued > kRing ? issued - kRing : 0; j < issued; ++j)
+      if (!mbar_wait(&full[j % kRing], (j / kRing) & 1, kDrainCycles)) err |= 2;
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = make_idesc(1u, kBM, kBN);
+    uint32_t started = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nkb && ok; ++kb) {
+      const int base = kb * T;
+      for (int q = 0; q < SB && ok; ++q) {
+        const int i = base + q;
+        if (*abort_flag || !mbar_wait(&full[i % kRing], (i / kRing) & 1, wait_cycles)) ok = false;
+      }
+      for (int s = 0; s < SA && ok; ++s) {
+        const int i = base + SB + s;
+        if (*abort_flag || !mbar_wait(&full[i % kRing], (i / kRing) & 1, wait_cycles)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint64_t ad = make_desc(smem + (i % kRing) * kTile);
+#pragma unroll
+        for (int t = 0; t < SB; ++t) {
+          if (s + t > kLevels) continue;
+          const int acc = acc_of(s + t);
+          const uint64_t bd = make_desc(smem + ((base + SB - 1 - t) % kRing) * kTile);
+          const uint32_t accf = (started >> acc) & 1u;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16(tmem + (uint32_t)(acc * 128), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
+                     accf | (uint32_t)(k > 0));
+          started |= 1u << acc;
+        }
+        mma_commit(&empty[i % kRing]);                                // A_s is done
+#pragma unroll
+        for (int t = 0; t < SB; ++t)                                  // B_t after its last pair
+          if ((SA - 1 < kLevels - t ? SA - 1 : kLevels - t) == s) mma_commit(&empty[(base + SB - 1 - t) % kRing]);
+      }
+    }
+    if (!ok) {
+      err |= 1;
+      *abort_flag = 1;
+    }
+    *started_out = started;
+    mma_commit(accum);   // arrives once every MMA issued above has completed
+  } else if (warp >= 2 && lane == 0) {
+    if (!mbar_wait(accum, 0, wait_cycles)) {
+      err |= 1;
+      *abort_flag = 1;
+      if (!mbar_wait(accum, 0, kDrainCycles)) err |= 2;
+    }
+  }
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp >= 2 && !*abort_flag) {
+    const int q = warp & 3;                       // TMEM lane quarter of this warp
+    const int64_t row = (int64_t)m0 + q * 32 + lane;
+    const uint32_t started = *started_out;
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    float2* out = P + ((int64_t)blockIdx.z * ldL + n0) * ldM + row;
+    for (int c0 = 0; c0 < kBN; c0 += 16) {
+      uint32_t e0[16], e1[16], e2[16], e3[16];
+      tmem_ld16(lane_addr + 0 * 128 + c0, e0);
+      tmem_ld16(lane_addr + 1 * 128 + c0, e1);
+      tmem_ld16(lane_addr + 2 * 128 + c0, e2);
+      tmem_ld16(lane_addr + 3 * 128 + c0, e3);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        // exact parts: E0 integer, E1 in 2^-8 units, E2 in 2^-16 units, all below 2^24 units;
+        // the pair holds their 40-bit sum exactly, then the rounded levels 3..
+        DF v;
+        v.hi = (started & 1u) ? __uint_as_float(e0[j]) : 0.0f;
+        v.lo = 0.0f;
+        if (started & 2u) v = df_add(v, DF{__uint_as_float(e1[j]), 0.0f});
+        if (started & 4u) v = df_add(v, DF{__uint_as_float(e2[j]), 0.0f});
+        if (started & 8u) v = df_add(v, DF{__uint_as_float(e3[j]), 0.0f});
+        out[(int64_t)(c0 + j) * ldM] = make_float2(v.hi, v.lo);
+      }
+    }
+  }
+  if (err && status) atomicOr(status, (err & 2) ? (kStatTimeout | kStatDrain) : kStatTimeout);
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Sum of the partials of chunks [0, nc) of output (m, j) in chunk order (double-float), added to
+// the running sum acc when !first, stored back to acc when !last; when last, scaled and written as
+// float64: MODE 1 (Z'' = diag(w) diag(2^e) J Omega): out[j * ldOut + m] = w_m 2^(2 e_m + f_j - 14)
+// v; MODE 2 (Y): out[j * ldOut + m] = 2^(f_j - 14) v.  Rows M <= m < ldOut are written as zero.
+template <int MODE>
+__global__ void k_oz_reduce(const float2* __restrict__ P, int nc, int64_t ldL, int64_t ldM, float2* __restrict__ acc,
+                            int first, int last, int64_t M, int64_t ldOut, const int* __restrict__ rexp,
+                            const int* __restrict__ cexp, const double* __restrict__ w, double* __restrict__ out) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (m >= ldOut) return;
+  if (m >= M) {
+    if (last) out[j * ldOut + m] = 0.0;
+    return;
+  }
+  DF v{0.0f, 0.0f};
+  if (!first) {
+    const float2 a = acc[j * ldM + m];
+    v = DF{a.x, a.y};
+  }
+  for (int c = 0; c < nc; ++c) {
+    const float2 x = P[((int64_t)c * ldL + j) * ldM + m];
+    v = df_add(v, DF{x.x, x.y});
+  }
+  if (!last) {
+    acc[j * ldM + m] = make_float2(v.hi, v.lo);
+    return;
+  }
+  const double x = (double)v.hi + (double)v.lo;
+  if (MODE == 1)
+    out[j * ldOut + m] = w[m] * ldexp(x, 2 * rexp[m] + cexp[j] - 14);
+  else
+    out[j * ldOut + m] = ldexp(x, cexp[j] - 14);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- host
+struct OzSketch {
+  __nv_bfloat16 *JD = nullptr, *JDT = nullptr, *OD = nullptr, *ZD = nullptr;
+  size_t JD_b = 0, JDT_b = 0, OD_b = 0, ZD_b = 0;
+  int *jexp = nullptr, *oexp = nullptr, *zexp = nullptr;
+  size_t jexp_b = 0, oexp_b = 0, zexp_b = 0;
+  double* Zs = nullptr;   size_t Zs_b = 0;     // Z'' transposed: ell x ldN
+  float2* part = nullptr; size_t part_b = 0;   // split-K partials of one launch
+  float2* acc = nullptr;  size_t acc_b = 0;    // running sums across launches
+  // the Jacobian the digit planes were made from
+  const float* J = nullptr;
+  int64_t N = 0, ldJ = 0, ldN = 0;
+  uint64_t j_version = ~0ull;
+};
+
+namespace {
+
+template <typename P>
+cudaError_t grow(P** p, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) *cap = bytes;
+  return e;
+}
+
+// D[m, n] = sum over kept digit pairs for an M x Nout output and K columns, into out (float64,
+// MODE as k_oz_reduce).  Split-K over chunks of kChunk; launches of at most kPartialCap bytes of
+// partials, their sums carried in the running double-float sums.
+template <int SA, int SB, int MODE>
+cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMap& tmB, int64_t M, int64_t Nout,
+                           int64_t K, const int* rexp, const int* cexp, const double* w, double* out, int64_t ldOut,
+                           int* status, cudaStream_t s, long long wait_cycles) {
+  const int64_t ldL = rup(Nout, kBN), ldM = rup(M, kBM);
+  const int64_t nchunks = (K + kChunk - 1) / kChunk;
+  const size_t chunk_bytes = (size_t)ldL * ldM * sizeof(float2);
+  const int64_t per_launch = std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)(kPartialCap / chunk_bytes)));
+  cudaError_t e;
+  if ((e = grow(&o->part, &o->part_b, chunk_bytes * per_launch)) != cudaSuccess) return e;
+  if (per_launch < nchunks && (e = grow(&o->acc, &o->acc_b, chunk_bytes)) != cudaSuccess) return e;
+  auto kern = k_oz_gemm<SA, SB>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)) != cudaSuccess) return e;
+  for (int64_t c0 = 0; c0 < nchunks; c0 += per_launch) {
+    const int nc = (int)std::min<int64_t>(per_launch, nchunks - c0);
+    dim3 grid((unsigned)(ldL / kBN), (unsigned)(ldM / kBM), (unsigned)nc);
+    kern<<<grid, 192, kSmem, s>>>(tmA, tmB, K, (int)c0, o->part, ldL, ldM, status, wait_cycles);
+    note_launch();
+    dim3 rg((unsigned)((ldOut + 255) / 256), (unsigned)Nout);
+    k_oz_reduce<MODE><<<rg, 256, 0, s>>>(o->part, nc, ldL, ldM, o->acc, c0 == 0, c0 + nc >= nchunks, M, ldOut, rexp,
+                                         cexp, w, out);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+OzSketch* oz_create() { return new (std::nothrow) OzSketch(); }
+
+void oz_destroy(OzSketch* o) {
+  if (!o) return;
+  void* bufs[] = {o->JD, o->JDT, o->OD, o->ZD, o->jexp, o->oexp, o->zexp, o->Zs, o->part, o->acc};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete o;
+}
+
+cudaError_t oz_sketch(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64_t p, uint64_t j_version,
+                      const float* Omega, int64_t ldY, int ell, const double* w, double* Y64, const char** why,
+                      cudaStream_t s, int* status, long long wait_cycles) {
+  *why = nullptr;
+  if (!tensor_map_encoder()) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  if ((ldJ % 32) || (ldY % 32) || ldY != ldJ || N < 1 || ell < 1) {
+    *why = "leading dimensions must be equal multiples of 32";
+    return cudaSuccess;
+  }
+  const int64_t ldN = rup(N, 32);
+  cudaError_t e;
+  // digit planes of J, once per Jacobian
+  if (o->J != J || o->j_version != j_version || o->N != N || o->ldJ != ldJ) {
+    if ((e = grow(&o->JD, &o->JD_b, (size_t)kDigJ * N * ldJ * 2)) != cudaSuccess) return e;
+    if ((e = grow(&o->JDT, &o->JDT_b, (size_t)kDigJ * ldJ * ldN * 2)) != cudaSuccess) return e;
+    if ((e = grow(&o->jexp, &o->jexp_b, (size_t)N * sizeof(int))) != cudaSuccess) return e;
+    k_oz_rowexp<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(J, ldJ, N, o->jexp);
+    note_launch();
+    dim3 blk(32, 8), grd((unsigned)(ldJ / 32), (unsigned)(ldN / 32));
+    k_oz_split_rows<<<grd, blk, 0, s>>>(J, ldJ, N, o->jexp, o->JD, o->JDT, ldN);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    o->J = J;
+    o->j_version = j_version;
+    o->N = N;
+    o->ldJ = ldJ;
+    o->ldN = ldN;
+  }
+  // digit planes of Omega
+  if ((e = grow(&o->OD, &o->OD_b, (size_t)kDigOm * ell * ldY * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->oexp, &o->oexp_b, (size_t)ell * sizeof(int))) != cudaSuccess) return e;
+  if ((e = grow(&o->zexp, &o->zexp_b, (size_t)ell * sizeof(int))) != cudaSuccess) return e;
+  if ((e = grow(&o->Zs, &o->Zs_b, (size_t)ell * ldN * sizeof(double))) != cudaSuccess) return e;
+  if ((e = grow(&o->ZD, &o->ZD_b, (size_t)kDigZ * ell * ldN * 2)) != cudaSuccess) return e;
+  k_oz_colexp<float><<<(unsigned)ell, 256, 0, s>>>(Omega, ldY, p, o->oexp);
+  note_launch();
+  {
+    const int64_t tot = ldY * ell;
+    k_oz_split_cols<float, kDigOm><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, s>>>(
+        Omega, ldY, ell, o->oexp, o->OD);
+    note_launch();
+  }
+  CUtensorMap mA1, mB1, mA2, mB2;
+  if (!make_tile_map(&mA1, o->JD, 2, N, ldJ, ldJ, kDigJ, N * ldJ) ||
+      !make_tile_map(&mB1, o->OD, 2, ell, ldY, ldY, kDigOm, (int64_t)ell * ldY) ||
+      !make_tile_map(&mA2, o->JDT, 2, ldJ, ldN, ldN, kDigJ, ldJ * ldN) ||
+      !make_tile_map(&mB2, o->ZD, 2, ell, ldN, ldN, kDigZ, (int64_t)ell * ldN)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  // GEMM1: Z'' (ell x ldN, transposed) = diag(w) diag(2^e) J Omega
+  if ((e = run_digit_gemm<kDigJ, kDigOm, 1>(o, mA1, mB1, N, ell, ldJ, o->jexp, o->oexp, w, o->Zs, ldN, status, s,
+                                            wait_cycles)) != cudaSuccess)
+    return e;
+  k_oz_colexp<double><<<(unsigned)ell, 256, 0, s>>>(o->Zs, ldN, N, o->zexp);
+  note_launch();
+  {
+    const int64_t tot = ldN * ell;
+    k_oz_split_cols<double, kDigZ><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, s>>>(
+        o->Zs, ldN, ell, o->zexp, o->ZD);
+    note_launch();
+  }
+  // GEMM2: Y = J^T Z''
+  return run_digit_gemm<kDigJ, kDigZ, 2>(o, mA2, mB2, p, ell, ldN, nullptr, o->zexp, nullptr, Y64, ldY, status, s,
+                                         wait_cycles);
+}
+
+}  // namespace ngd

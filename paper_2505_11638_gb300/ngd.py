@@ -25,7 +25,7 @@ NGD_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_SPD", 5: "BREAKDOWN", 6: "MAXIT",
                 7: "NONFINITE", 8: "TIMEOUT", 9: "UNSUPPORTED"}
 DTYPES = {"f64": 0, "f32": 1}
-SKETCH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+SKETCH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "df": 4}
 TEST_MATRIX = {"gaussian": 0, "sampling": 1}
 PRECOND = {"nystrom": 0, "rpchol": 1, "full": 2}
 PDES = {"poisson": 0, "heat": 1}
@@ -362,7 +362,8 @@ class Context:
         if V.dim() != 2 or V.shape[1] != self.p:
             raise ValueError(f"V: expected shape (ell, {self.p})")
         ell = V.shape[0]
-        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
+        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec in ("f64", "df") else self.wdtype,
+                        device=self.device)
         ngd_gramian_mm(self.handle, theta, ell, V, self.p, prec, Y, self.p)
         if theta is not None:
             self.version += 1
@@ -370,7 +371,7 @@ class Context:
 
     def nystrom_sketch(self, theta, ell, seed=0, step=0, prec="f64"):
         Om = torch.empty((ell, self.p), dtype=self.wdtype, device=self.device)   # column-major p x ell
-        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
+        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec in ("f64", "df") else self.wdtype, device=self.device)
         ngd_nystrom_sketch(self.handle, theta, ell, seed, step, prec, Om, Y)
         if theta is not None:
             self.version += 1
@@ -380,7 +381,7 @@ class Context:
         """The sampling test matrix: returns (idx, Omega, Y), idx the sampled parameter indices."""
         idx = torch.empty(ell, dtype=torch.int32, device=self.device)
         Om = torch.empty((ell, self.p), dtype=self.wdtype, device=self.device)
-        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
+        Y = torch.empty((ell, self.p), dtype=torch.float64 if prec in ("f64", "df") else self.wdtype, device=self.device)
         ngd_nystrom_sketch_sampled(self.handle, theta, ell, seed, step, prec, idx, Om, Y)
         if theta is not None:
             self.version += 1
@@ -395,8 +396,8 @@ class Context:
 
     def nystrom_factor(self, ell, Omega, Y, prec="f64", shift_scale=1.0):
         _need(Omega, self.wdtype, self.p * ell, "Omega")
-        _need(Y, torch.float64 if prec == "f64" else self.wdtype, self.p * ell, "Y")
-        U = torch.empty((ell, self.p), dtype=torch.float64 if prec == "f64" else self.wdtype, device=self.device)
+        _need(Y, torch.float64 if prec in ("f64", "df") else self.wdtype, self.p * ell, "Y")
+        U = torch.empty((ell, self.p), dtype=torch.float64 if prec in ("f64", "df") else self.wdtype, device=self.device)
         lam = self._vec(ell)
         nu = ngd_nystrom_factor(self.handle, ell, Omega, Y, prec, shift_scale, U, lam)
         return U, lam, nu

@@ -438,13 +438,13 @@ def test_ngd_step_fp32_paths(ngd):
     J = mlp.jacobian(pr, th)
     g_o = mlp.vjp(pr, th, pr.w * mlp.residual(pr, th)[0])
     iters = {}
-    for sketch in ["f64", "f32", "tf32", "bf16"]:
+    for sketch in ["f64", "df", "f32", "tf32", "bf16"]:
         ctx = ngd.Context(pr, dtype="f32")
         t = dev(th)
         info = ctx.step(t, ell=200, mu=1e-7, rtol=1e-6, maxit=600, seed=1, step=0, sketch=sketch)
         iters[sketch] = info["pcg_iters"]
         assert info["loss_after"] < info["loss_before"], sketch
-        if sketch in ("f32", "f64"):
+        if sketch in ("f32", "f64", "df"):
             assert info["relres"] <= 1e-6
             # the direction solves the oracle's FP64 system to the accuracy of the FP32 operator
             d = (th - host(t)) / info["alpha"]
@@ -452,6 +452,8 @@ def test_ngd_step_fp32_paths(ngd):
             assert np.linalg.norm(res) <= 1e-3 * np.linalg.norm(g_o)
         ctx.close()
     assert iters["f64"] <= iters["f32"] <= iters["tf32"] and iters["f32"] <= iters["bf16"], iters
+    # the two FP64-accurate forms (tensor-core digit planes, double-float) need the same iterations
+    assert abs(iters["f64"] - iters["df"]) <= max(1, 0.02 * iters["df"]), iters
 
 
 def test_heuristic_mu(ngd):

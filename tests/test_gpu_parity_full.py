@@ -96,18 +96,20 @@ def test_two_pass_matvec_large_p(ngd, name, n_int, n_bnd):
     ctx.close()
 
 
-def test_gramian_mm_fp64_accurate_exact_jacobian(ngd):
-    """Y = G V through ngd_gramian_mm in the FP64-accurate arithmetic of an F32 context, for V and
-    J given to both sides (5-D Poisson, 1500 points, ell = 130: ragged 128-wide tiles): against
-    FP64 at 1e-12 in norm, each entry within 1e-11 of its term magnitude; the Nystrom core
-    V^T G V symmetric to 1e-12."""
+@pytest.mark.parametrize("prec", ["f64", "df"])
+def test_gramian_mm_fp64_accurate_exact_jacobian(ngd, prec):
+    """Y = G V through ngd_gramian_mm in the FP64-accurate arithmetic of an F32 context (f64: the
+    tensor-core digit-plane products; df: double-float on the FP32 pipes), for V and J given to
+    both sides (5-D Poisson, 1500 points, ell = 130: ragged 128-wide tiles, N and p not multiples
+    of the 128-row tiles or of the 256-long K-chunks): against FP64 at 1e-12 in norm, each entry
+    within 1e-11 of its term magnitude; the Nystrom core V^T G V symmetric to 1e-12."""
     wl, pr, th = workload("poisson5d", 1200, 300)
     J32 = round32(mlp.jacobian(pr, th))
     ctx = ngd.Context(pr, dtype="f32")
     ctx.set_jacobian(dev(J32, torch.float32))
     ell = 130
     V = round32(nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 9, 2)))
-    Y = host(ctx.gramian_mm(None, dev(V.T, torch.float32), "f64")).T
+    Y = host(ctx.gramian_mm(None, dev(V.T, torch.float32), prec)).T
     Y_o = J32.T @ (pr.w[:, None] * (J32 @ V))
     B = np.abs(J32).T @ (pr.w[:, None] * (np.abs(J32) @ np.abs(V)))
     assert rel(Y, Y_o) <= 1e-12
@@ -220,22 +222,24 @@ def test_fused_pcg_small_exact_jacobian_tight(ngd):
     ctx.close()
 
 
-def test_tensor_core_wait_timeout_recovers(ngd):
-    """Failure detection of the tcgen05 kernels: with a one-cycle wait limit every role's first
-    wait runs out before its TMA loads land; the kernel drains what it issued, stores nothing,
-    frees its tensor memory and the call reports TIMEOUT.  With the default limit restored the
-    same context computes the same sketch as a fresh context."""
+@pytest.mark.parametrize("prec", ["tf32", "f64"])
+def test_tensor_core_wait_timeout_recovers(ngd, prec):
+    """Failure detection of the tcgen05 kernels (tf32: the rounded-operand GEMM; f64: the
+    digit-plane GEMM): with a one-cycle wait limit every role's first wait runs out before its
+    TMA loads land; the kernel drains what it issued, stores nothing, frees its tensor memory and
+    the call reports TIMEOUT.  With the default limit restored the same context computes the same
+    sketch as a fresh context."""
     wl, pr, th = workload("poisson5d", 700, 180)
     ctx = ngd.Context(pr, dtype="f32")
     t = dev(th)
     ngd.ngd_set_wait_limit(ctx.handle, 1)
     with pytest.raises(ngd.NGDError) as e:
-        ctx.nystrom_sketch(t, 130, seed=3, step=1, prec="tf32")
+        ctx.nystrom_sketch(t, 130, seed=3, step=1, prec=prec)
     assert e.value.name == "TIMEOUT"
     ngd.ngd_set_wait_limit(ctx.handle, 4_000_000_000)
-    Om, Y = ctx.nystrom_sketch(t, 130, seed=3, step=1, prec="tf32")
+    Om, Y = ctx.nystrom_sketch(t, 130, seed=3, step=1, prec=prec)
     ref = ngd.Context(pr, dtype="f32")
-    Om2, Y2 = ref.nystrom_sketch(dev(th), 130, seed=3, step=1, prec="tf32")
+    Om2, Y2 = ref.nystrom_sketch(dev(th), 130, seed=3, step=1, prec=prec)
     assert torch.equal(Om, Om2) and torch.equal(Y, Y2)
     ref.close()
     ctx.close()
