@@ -14,21 +14,24 @@
 //   * digit s is stored as the BF16 number a_s 2^(-8 s) (exact: 8 significant bits), so a product
 //     of digit planes s and t carries its weight 2^(-8 (s + t)) by itself.
 // GEMM1 Z = J Omega and GEMM2 Y = J^T Z'' then become sums over digit-plane products (s, t) with
-// s + t <= 5 ("levels"; the dropped levels weigh <= 2^-48 of the leading one).  Levels 0, 1 and 2
-// are summed exactly: within one level every product is an integer times the level's weight, a
-// K-chunk of 256 keeps every partial sum below 2^24 such units (at most 3 pairs x 256 x 2^14),
-// and the tensor core's FP32 accumulation of such sums is exact (measured on GB300 with integer
-// digit data up to 2^24: no rounding; mixed magnitudes inside one 16-wide group do round, which
-// the split avoids by giving every MMA a single (s, t) pair).  Levels 3..5 (weight <= 2^-24) share
-// one FP32 accumulator whose rounding stays below 2^-46 of the leading level.  Each CTA sums one
-// 128 x 128 output tile over one K-chunk into four TMEM accumulators (512 columns), combines them
-// into a double-float value, and writes it as a split-K partial; a second kernel adds the
-// partials of a tile in a fixed order (deterministic) and applies the power-of-two scales.
+// s + t <= 5 ("levels"; the dropped levels weigh <= 2^-48 of the leading one).  Levels 0 to 3
+// are summed exactly, each in its own accumulator: within one level every product is an integer
+// times the level's weight, a K-chunk of 256 keeps every partial sum within 2^24 such units (at
+// most 4 pairs x 256 x 2^14), and the tensor core's FP32 accumulation of such sums is exact
+// (measured on GB300 with integer digit data up to 2^24: no rounding; mixed magnitudes inside one
+// 16-wide group, or an accumulator of a larger magnitude than its addends, do round, which the
+// split avoids by giving every MMA a single (s, t) pair and every exact level its own
+// accumulator).  Levels 4 and 5 (weight <= 2^-32) share a fifth FP32 accumulator, whose rounding
+// (half a level-4 unit per addition) stays below 2^-52 of the leading level.  Each CTA sums one
+// 128 x 96 output tile over one K-chunk into the five TMEM accumulators (480 of 512 columns),
+// combines them into a double-float value, and writes it as a split-K partial; a second kernel
+// adds the partials of a tile in a fixed order (deterministic) and applies the power-of-two scales.
 //
-// Kernel structure (k_oz_gemm): warp 0 lane 0 issues TMA loads of 16 KB tiles (128 rows x 64
-// BF16, 128-byte swizzle) into a ring of 12 shared-memory slots; per 64-wide k-block, the B digit
-// tiles (descending digit) and then the A digit tiles (ascending digit).  Warp 1 lane 0 issues
-// tcgen05.mma (kind::f16, M = N = 128, K = 16) pair by pair and releases each tile after its last
+// Kernel structure (k_oz_gemm): warp 0 lane 0 issues TMA loads of digit tiles (A: 128 rows, B: 96
+// rows, 64 BF16 = 128 bytes each, 128-byte swizzle) into a ring of 12 16-KB shared-memory slots;
+// per 64-wide k-block, the B digit tiles (descending digit) and then the A digit tiles (ascending
+// digit).  Warp 1 lane 0 issues tcgen05.mma (kind::f16, M = 128, N = 96, K = 16) pair by pair and
+// releases each tile after its last
 // use.  Warps 2..5 drain the accumulators with tcgen05.ld.  Waits follow the bounded protocol of
 // tc_common.cuh.
 #include <cuda.h>
@@ -53,9 +56,11 @@ constexpr int kDigJ = 5;       // digits of the row-scaled Jacobian
 constexpr int kDigOm = 5;      // digits of the column-scaled test matrix
 constexpr int kDigZ = 6;       // digits of the column-scaled Z''
 constexpr int kLevels = 5;     // pairs (s, t) with s + t <= kLevels are kept
-constexpr int kChunk = 256;    // K per CTA: exact level sums (3 pairs x 256 x 2^14 < 2^24)
-constexpr int kBM = 128, kBN = 128, kBK = 64;
-constexpr int kTile = kBM * kBK * 2;                        // 16 KB: 128 rows x 128 bytes
+constexpr int kChunk = 256;    // K per CTA: exact level sums (4 pairs x 256 x 2^14 = 2^24)
+constexpr int kBM = 128, kBN = 96, kBK = 64;
+constexpr int kTile = kBM * kBK * 2;                        // 16 KB slot: 128 rows x 128 bytes
+constexpr int kTileB = kBN * kBK * 2;                       // 12 KB of a B tile
+constexpr int kAcc = 5;                                     // TMEM accumulators of kBN columns
 constexpr int kRing = 12;
 constexpr int kSmem = kRing * kTile + 1024 + 512;
 constexpr size_t kPartialCap = size_t(1) << 30;             // bytes of split-K partials per launch
@@ -167,10 +172,10 @@ __global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t col
 }
 
 // ---------------------------------------------------------------------------- digit-plane GEMM
-// Accumulator of the level s + t: levels 0, 1, 2 exact, levels 3.. shared (TMEM columns acc*128).
-__host__ __device__ constexpr int acc_of(int level) { return level < 3 ? level : 3; }
+// Accumulator of the level s + t: levels 0..3 exact, levels 4.. shared (TMEM columns acc * kBN).
+__host__ __device__ constexpr int acc_of(int level) { return level < 4 ? level : 4; }
 
-// Split-K partial of D = sum over kept (s, t) of A_s B_t^T on one 128 x 128 tile and one K-chunk:
+// Split-K partial of D = sum over kept (s, t) of A_s B_t^T on one 128 x 96 tile and one K-chunk:
 // A planes (tmA: cols = K, rows = M, planes = SA), B planes (tmB: cols = K, rows = Nout, planes =
 // SB), both K-major.  Grid: (Nout tiles, M tiles, chunks of this launch).  Partial (hi, lo) of
 // output (m, n) of local chunk c at P[(c * ldL + n) * ldM + m].
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
           *abort_flag = 1;
           break;
         }
-        mbar_expect_tx(&full[slot], kTile);
+        mbar_expect_tx(&full[slot], q < SB ? kTileB : kTile);
         if (q < SB)
           tma_load_3d(smem + slot * kTile, &tmB, x, n0, SB - 1 - q, &full[slot]);
         else
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
           const uint32_t accf = (started >> acc) & 1u;
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
-            mma_bf16(tmem + (uint32_t)(acc * 128), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
+            mma_bf16(tmem + (uint32_t)(acc * kBN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
                      accf | (uint32_t)(k > 0));
           started |= 1u << acc;
         }
@@ -297,22 +302,18 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     float2* out = P + ((int64_t)blockIdx.z * ldL + n0) * ldM + row;
     for (int c0 = 0; c0 < kBN; c0 += 16) {
-      uint32_t e0[16], e1[16], e2[16], e3[16];
-      tmem_ld16(lane_addr + 0 * 128 + c0, e0);
-      tmem_ld16(lane_addr + 1 * 128 + c0, e1);
-      tmem_ld16(lane_addr + 2 * 128 + c0, e2);
-      tmem_ld16(lane_addr + 3 * 128 + c0, e3);
+      uint32_t e[kAcc][16];
+#pragma unroll
+      for (int a = 0; a < kAcc; ++a) tmem_ld16(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
       tmem_wait_ld();
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        // exact parts: E0 integer, E1 in 2^-8 units, E2 in 2^-16 units, all below 2^24 units;
-        // the pair holds their 40-bit sum exactly, then the rounded levels 3..
-        DF v;
-        v.hi = (started & 1u) ? __uint_as_float(e0[j]) : 0.0f;
-        v.lo = 0.0f;
-        if (started & 2u) v = df_add(v, DF{__uint_as_float(e1[j]), 0.0f});
-        if (started & 4u) v = df_add(v, DF{__uint_as_float(e2[j]), 0.0f});
-        if (started & 8u) v = df_add(v, DF{__uint_as_float(e3[j]), 0.0f});
+        // exact parts: E0 integer, E1..E3 in 2^-8, 2^-16, 2^-24 units, each within 2^24 units;
+        // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded levels 4..
+        DF v{0.0f, 0.0f};
+#pragma unroll
+        for (int a = kAcc - 1; a >= 0; --a)
+          if (started & (1u << a)) v = df_add(v, DF{__uint_as_float(e[a][j]), 0.0f});
         out[(int64_t)(c0 + j) * ldM] = make_float2(v.hi, v.lo);
       }
     }
@@ -478,10 +479,10 @@ cudaError_t oz_sketch(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64
     note_launch();
   }
   CUtensorMap mA1, mB1, mA2, mB2;
-  if (!make_tile_map(&mA1, o->JD, 2, N, ldJ, ldJ, kDigJ, N * ldJ) ||
-      !make_tile_map(&mB1, o->OD, 2, ell, ldY, ldY, kDigOm, (int64_t)ell * ldY) ||
-      !make_tile_map(&mA2, o->JDT, 2, ldJ, ldN, ldN, kDigJ, ldJ * ldN) ||
-      !make_tile_map(&mB2, o->ZD, 2, ell, ldN, ldN, kDigZ, (int64_t)ell * ldN)) {
+  if (!make_tile_map(&mA1, o->JD, 2, N, ldJ, ldJ, kDigJ, N * ldJ, kBM) ||
+      !make_tile_map(&mB1, o->OD, 2, ell, ldY, ldY, kDigOm, (int64_t)ell * ldY, kBN) ||
+      !make_tile_map(&mA2, o->JDT, 2, ldJ, ldN, ldN, kDigJ, ldJ * ldN, kBM) ||
+      !make_tile_map(&mB2, o->ZD, 2, ell, ldN, ldN, kDigZ, (int64_t)ell * ldN, kBN)) {
     *why = "tensor map encoding failed";
     return cudaSuccess;
   }

@@ -41,16 +41,16 @@ EncodeFn tensor_map_encoder() {
 }
 
 bool make_tile_map(CUtensorMap* m, const void* base, int elem_bytes, int64_t rows, int64_t cols, int64_t ld,
-                   int64_t planes, int64_t plane_ld) {
+                   int64_t planes, int64_t plane_ld, int box_rows) {
   EncodeFn enc = tensor_map_encoder();
-  if (!enc || (elem_bytes != 2 && elem_bytes != 4)) return false;
+  if (!enc || (elem_bytes != 2 && elem_bytes != 4) || box_rows < 8 || box_rows > 256) return false;
   const size_t es = (size_t)elem_bytes;
   if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * es) & 15) || (planes > 1 && ((plane_ld * es) & 15)))
     return false;
   const CUtensorMapDataType dt = es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(plane_ld * es)};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / es), 128u, 1u};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   const cuuint32_t rank = planes > 1 ? 3 : 2;
   const CUresult r = enc(m, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -132,12 +132,12 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
 EncodeFn tensor_map_encoder();
 
 // Tiled map of a row-major matrix, or of 'planes' such matrices stacked with a plane stride:
-// rows x cols (cols contiguous, row stride ld elements, plane stride plane_ld elements), box 128
-// rows x 128 bytes, 128-byte swizzle, zero fill outside.  Element size 2 (BF16) or 4 (FP32/TF32).
+// rows x cols (cols contiguous, row stride ld elements, plane stride plane_ld elements), box
+// box_rows rows x 128 bytes, 128-byte swizzle, zero fill outside.  Element size 2 (BF16) or 4 (FP32/TF32).
 // Returns false when the encoder is unavailable or the layout breaks a TMA rule (16-byte aligned
 // base and strides).
 bool make_tile_map(CUtensorMap* m, const void* base, int elem_bytes, int64_t rows, int64_t cols, int64_t ld,
-                   int64_t planes = 1, int64_t plane_ld = 0);
+                   int64_t planes = 1, int64_t plane_ld = 0, int box_rows = 128);
 
 }  // namespace tc
 }  // namespace ngd
