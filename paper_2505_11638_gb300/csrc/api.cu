@@ -412,8 +412,12 @@ bool acc64(int prec) { return prec == NGD_SKETCH_F64 || prec == NGD_SKETCH_DF; }
 
 template <typename T>
 ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell) {
-  // CholeskyQR2: Om <- Om R^{-1} twice, R = chol(Om^T Om)^T (positive diagonal)
-  for (int pass = 0; pass < 2; ++pass) {
+  // CholeskyQR: Om <- Om R^{-1}, R = chol(Om^T Om)^T (positive diagonal).  A Gaussian p x ell
+  // matrix has condition number about (1 + sqrt(ell / p)) / (1 - sqrt(ell / p)) (<= 5/3 for
+  // ell <= p / 16), so one pass leaves Q^T Q - I at a few units of the working precision; wider
+  // test matrices take a second pass (CholeskyQR2).
+  const int passes = 16 * (int64_t)ell <= ctx->p ? 1 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
     TRY(gram_atb<T>(ctx, Om, Om, ctx->p, ctx->ldP, ell, ctx->M));
     launch_symmetrize(ctx->M, ell, ctx->stream);
     CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));

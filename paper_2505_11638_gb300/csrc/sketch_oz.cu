@@ -61,8 +61,6 @@ constexpr int kBM = 128, kBN = 96, kBK = 64;
 constexpr int kTile = kBM * kBK * 2;                        // 16 KB slot: 128 rows x 128 bytes
 constexpr int kTileB = kBN * kBK * 2;                       // 12 KB of a B tile
 constexpr int kAcc = 5;                                     // TMEM accumulators of kBN columns
-constexpr int kRing = 12;
-constexpr int kSmem = kRing * kTile + 1024 + 512;
 constexpr size_t kPartialCap = size_t(1) << 30;             // bytes of split-K partials per launch
 
 int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -175,42 +173,69 @@ __global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t col
 // Accumulator of the level s + t: levels 0..3 exact, levels 4.. shared (TMEM columns acc * kBN).
 __host__ __device__ constexpr int acc_of(int level) { return level < 4 ? level : 4; }
 
-// Split-K partial of D = sum over kept (s, t) of A_s B_t^T on one 128 x 96 tile and one K-chunk:
-// A planes (tmA: cols = K, rows = M, planes = SA), B planes (tmB: cols = K, rows = Nout, planes =
-// SB), both K-major.  Grid: (Nout tiles, M tiles, chunks of this launch).  Partial (hi, lo) of
-// output (m, n) of local chunk c at P[(c * ldL + n) * ldM + m].
+// Shared-memory plan of the digit-plane GEMM: a ring of RB = 2 SB B-tile slots (two k-blocks of B
+// digit tiles) and a ring of RA A-tile slots, as many as fit.
+template <int SB>
+struct OzSmem {
+  static constexpr int RB = 2 * SB;
+  static constexpr int kLimit = 232448;                                    // 227 KB per block
+  static constexpr int kFixed = 1024 + 1024;                               // alignment, barriers
+  static constexpr int RA0 = (kLimit - kFixed - RB * kTileB) / kTile;
+  static constexpr int RA = RA0 > 8 ? 8 : RA0;
+  static constexpr int bytes = RA * kTile + RB * kTileB + kFixed;
+};
+
+constexpr int kEpiWarps = 8;                       // two warps per TMEM lane quarter
+constexpr int kOzThreads = 32 * (2 + kEpiWarps);
+
+// Split-K partials of D = sum over kept (s, t) of A_s B_t^T.  A planes (tmA: cols = K, rows = M,
+// planes = SA), B planes (tmB: cols = K, rows = Nout, planes = SB), both K-major.  Work item =
+// (Nout tile, M tile, chunk of this launch), item = nt + n_tiles (mt + m_tiles c); the persistent
+// CTAs take items blockIdx.x, blockIdx.x + gridDim.x, ...  Partial (hi, lo) of output (m, n) of
+// local chunk c at P[(c * ldL + n) * ldM + m].  While the epilogue warps drain one item's
+// accumulators, the producer already loads the next item's tiles; the MMA issuer waits for the
+// drain (accumulator-empty barrier) before it writes the accumulators again.
 template <int SA, int SB>
-__global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                   const __grid_constant__ CUtensorMap tmB, int64_t K, int chunk0,
-                                                   float2* __restrict__ P, int64_t ldL, int64_t ldM, int* status,
-                                                   long long wait_cycles) {
+__global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB, int64_t K,
+                                                          int chunk0, int n_tiles, int m_tiles, int nchunk,
+                                                          float2* __restrict__ P, int64_t ldL, int64_t ldM,
+                                                          int* status, long long wait_cycles) {
   static_assert(SB - 1 <= kLevels && SA - 1 <= kLevels, "every digit plane takes part in a kept pair");
-  constexpr int T = SA + SB;   // tiles per k-block: B_{SB-1} .. B_0, then A_0 .. A_{SA-1}
-  // a k-block's tiles fit the ring together: a tile only ever waits for a slot of an earlier
-  // k-block, which the MMA issuer can always finish (no circular wait)
-  static_assert(T <= kRing, "one k-block of digit tiles must fit the ring");
+  using SP = OzSmem<SB>;
+  constexpr int RA = SP::RA, RB = SP::RB;
+  // a k-block's tiles fit the rings together: a tile only waits for a slot of an earlier k-block,
+  // which the MMA issuer can always finish (no circular wait)
+  static_assert(RA >= SA && RB >= SB, "one k-block of digit tiles must fit the rings");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kRing * kTile);
-  uint64_t* empty = full + kRing;
-  uint64_t* accum = empty + kRing;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint8_t* ringA = smem;
+  uint8_t* ringB = smem + RA * kTile;
+  uint64_t* fullA = reinterpret_cast<uint64_t*>(ringB + RB * kTileB);
+  uint64_t* emptyA = fullA + RA;
+  uint64_t* fullB = emptyA + RA;
+  uint64_t* emptyB = fullB + RB;
+  uint64_t* acc_full = emptyB + RB;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* mma_done = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile uint32_t* started_out = reinterpret_cast<volatile uint32_t*>(tmem_slot + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
-  const int64_t k0 = (int64_t)(chunk0 + (int)blockIdx.z) * kChunk;
-  const int64_t klen = K - k0 < kChunk ? K - k0 : kChunk;
-  const int nkb = (int)((klen + kBK - 1) / kBK);
+  const int items = n_tiles * m_tiles * nchunk;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kRing; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+    for (int i = 0; i < RA; ++i) {
+      mbar_init(&fullA[i], 1);
+      mbar_init(&emptyA[i], 1);
     }
-    mbar_init(accum, 1);
+    for (int i = 0; i < RB; ++i) {
+      mbar_init(&fullB[i], 1);
+      mbar_init(&emptyB[i], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
-    *started_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, 512);
@@ -221,103 +246,158 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
   int err = 0;
 
   if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
-      const int x = (int)(k0 + (int64_t)kb * kBK);
-      for (int q = 0; q < T; ++q) {
-        const int i = kb * T + q, slot = i % kRing, use = i / kRing;
-        if (*abort_flag) break;
-        if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, wait_cycles)) {
-          err |= 1;
-          *abort_flag = 1;
-          break;
+    // ---------------------------------------------------------------- TMA producer
+    int iA = 0, iB = 0;
+    for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
+      const int nt = item % n_tiles, mt = (item / n_tiles) % m_tiles, c = item / (n_tiles * m_tiles);
+      const int64_t k0 = (int64_t)(chunk0 + c) * kChunk;
+      const int nkb = (int)(((K - k0 < kChunk ? K - k0 : kChunk) + kBK - 1) / kBK);
+      for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
+        const int x = (int)(k0 + (int64_t)kb * kBK);
+        for (int q = 0; q < SA + SB; ++q) {
+          const bool isB = q < SB;
+          const int i = isB ? iB : iA, R = isB ? RB : RA;
+          uint64_t* fb = isB ? &fullB[i % R] : &fullA[i % R];
+          uint64_t* eb = isB ? &emptyB[i % R] : &emptyA[i % R];
+          if (i >= R && !mbar_wait(eb, ((i / R) - 1) & 1, wait_cycles)) {
+            err |= 1;
+            *abort_flag = 1;
+            break;
+          }
+          if (isB) {
+            mbar_expect_tx(fb, kTileB);
+            tma_load_3d(ringB + (i % RB) * kTileB, &tmB, x, nt * kBN, SB - 1 - q, fb);
+            ++iB;
+          } else {
+            mbar_expect_tx(fb, kTile);
+            tma_load_3d(ringA + (i % RA) * kTile, &tmA, x, mt * kBM, q - SB, fb);
+            ++iA;
+          }
         }
-        mbar_expect_tx(&full[slot], q < SB ? kTileB : kTile);
-        if (q < SB)
-          tma_load_3d(smem + slot * kTile, &tmB, x, n0, SB - 1 - q, &full[slot]);
-        else
-          tma_load_3d(smem + slot * kTile, &tmA, x, m0, q - SB, &full[slot]);
-        issued = i + 1;
       }
     }
-    for (int j = issued > kRing ? issued - kRing : 0; j < issued; ++j)
-      if (!mbar_wait(&full[j % kRing], (j / kRing) & 1, kDrainCycles)) err |= 2;
+    // every load still unconsumed must land before the CTA may exit
+    for (int j = iA > RA ? iA - RA : 0; j < iA; ++j)
+      if (!mbar_wait(&fullA[j % RA], (j / RA) & 1, kDrainCycles)) err |= 2;
+    for (int j = iB > RB ? iB - RB : 0; j < iB; ++j)
+      if (!mbar_wait(&fullB[j % RB], (j / RB) & 1, kDrainCycles)) err |= 2;
   } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = make_idesc(1u, kBM, kBN);
-    uint32_t started = 0;
-    bool ok = true;
-    for (int kb = 0; kb < nkb && ok; ++kb) {
-      const int base = kb * T;
-      for (int q = 0; q < SB && ok; ++q) {
-        const int i = base + q;
-        if (*abort_flag || !mbar_wait(&full[i % kRing], (i / kRing) & 1, wait_cycles)) ok = false;
+    int iA = 0, iB = 0, nitem = 0;
+    bool ok = true, pending = false;   // pending: MMAs of the current item not yet committed
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++nitem) {
+      const int c = item / (n_tiles * m_tiles);
+      const int64_t k0 = (int64_t)(chunk0 + c) * kChunk;
+      const int nkb = (int)(((K - k0 < kChunk ? K - k0 : kChunk) + kBK - 1) / kBK);
+      // the epilogue has read the previous item's accumulators
+      if (nitem > 0 && (*abort_flag || !mbar_wait(acc_empty, (nitem - 1) & 1, wait_cycles))) {
+        ok = false;
+        break;
       }
-      for (int s = 0; s < SA && ok; ++s) {
-        const int i = base + SB + s;
-        if (*abort_flag || !mbar_wait(&full[i % kRing], (i / kRing) & 1, wait_cycles)) {
-          ok = false;
-          break;
+      fence_after();
+      uint32_t started = 0;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int b0 = iB;                       // B tile of digit t sits at counter b0 + SB - 1 - t
+        for (int q = 0; q < SB && ok; ++q, ++iB)
+          if (*abort_flag || !mbar_wait(&fullB[iB % RB], (iB / RB) & 1, wait_cycles)) ok = false;
+        for (int s = 0; s < SA && ok; ++s, ++iA) {
+          if (*abort_flag || !mbar_wait(&fullA[iA % RA], (iA / RA) & 1, wait_cycles)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint64_t ad = make_desc(ringA + (iA % RA) * kTile);
+#pragma unroll
+          for (int t = 0; t < SB; ++t) {
+            if (s + t > kLevels) continue;
+            const int acc = acc_of(s + t);
+            const uint64_t bd = make_desc(ringB + ((b0 + SB - 1 - t) % RB) * kTileB);
+            const uint32_t accf = (started >> acc) & 1u;
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+              mma_bf16(tmem + (uint32_t)(acc * kBN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
+                       accf | (uint32_t)(k > 0));
+            started |= 1u << acc;
+            pending = true;
+          }
+          mma_commit(&emptyA[iA % RA]);                                 // A_s is done
+#pragma unroll
+          for (int t = 0; t < SB; ++t)                                  // B_t after its last pair
+            if ((SA - 1 < kLevels - t ? SA - 1 : kLevels - t) == s) mma_commit(&emptyB[(b0 + SB - 1 - t) % RB]);
         }
-        fence_after();
-        const uint64_t ad = make_desc(smem + (i % kRing) * kTile);
-#pragma unroll
-        for (int t = 0; t < SB; ++t) {
-          if (s + t > kLevels) continue;
-          const int acc = acc_of(s + t);
-          const uint64_t bd = make_desc(smem + ((base + SB - 1 - t) % kRing) * kTile);
-          const uint32_t accf = (started >> acc) & 1u;
-#pragma unroll
-          for (int k = 0; k < kBK / 16; ++k)
-            mma_bf16(tmem + (uint32_t)(acc * kBN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
-                     accf | (uint32_t)(k > 0));
-          started |= 1u << acc;
-        }
-        mma_commit(&empty[i % kRing]);                                // A_s is done
-#pragma unroll
-        for (int t = 0; t < SB; ++t)                                  // B_t after its last pair
-          if ((SA - 1 < kLevels - t ? SA - 1 : kLevels - t) == s) mma_commit(&empty[(base + SB - 1 - t) % kRing]);
       }
+      if (!ok) break;
+      mma_commit(acc_full);          // arrives once this item's MMAs have completed
+      pending = false;
     }
     if (!ok) {
       err |= 1;
       *abort_flag = 1;
+      if (pending) mma_commit(acc_full);   // the phase an epilogue warp may be waiting on
     }
-    *started_out = started;
-    mma_commit(accum);   // arrives once every MMA issued above has completed
-  } else if (warp >= 2 && lane == 0) {
-    if (!mbar_wait(accum, 0, wait_cycles)) {
-      err |= 1;
-      *abort_flag = 1;
-      if (!mbar_wait(accum, 0, kDrainCycles)) err |= 2;
+    // every MMA this thread issued has completed before the tensor memory is freed
+    mma_commit(mma_done);
+    if (!mbar_wait(mma_done, 0, kDrainCycles)) err |= 2;
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue
+    const int ew = warp - 2;
+    const int q = warp & 3;                       // TMEM lane quarter this warp may access
+    const int half = ew >> 2;                     // which half of the kBN columns
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    // accumulators some kept pair writes (the MMA issuer's first write to each clears it)
+    uint32_t started = 0;
+#pragma unroll
+    for (int s = 0; s < SA; ++s)
+#pragma unroll
+      for (int t = 0; t < SB; ++t)
+        if (s + t <= kLevels) started |= 1u << acc_of(s + t);
+    int nitem = 0;
+    for (int item = blockIdx.x; item < items; item += gridDim.x, ++nitem) {
+      // wait for the item's accumulators; give up when another role aborted (the MMA issuer then
+      // waits for its own MMAs before the tensor memory is freed)
+      int got = 0;
+      if (lane == 0) {
+        const long long t0 = clock64();
+        while (true) {
+          if (mbar_try_wait(acc_full, nitem & 1)) { got = 1; break; }
+          if (*abort_flag) break;
+          if (clock64() - t0 > wait_cycles) {
+            err |= 1;
+            *abort_flag = 1;
+            break;
+          }
+        }
+      }
+      got = __shfl_sync(0xffffffffu, got, 0);
+      __syncwarp();
+      fence_after();
+      if (!got || *abort_flag) break;
+      const int nt = item % n_tiles, mt = (item / n_tiles) % m_tiles, c = item / (n_tiles * m_tiles);
+      const int64_t row = (int64_t)mt * kBM + q * 32 + lane;
+      float2* out = P + ((int64_t)c * ldL + (int64_t)nt * kBN) * ldM + row;
+      for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 16) {
+        uint32_t e[kAcc][16];
+#pragma unroll
+        for (int a = 0; a < kAcc; ++a) tmem_ld16(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          // exact parts: E0 integer, E1..E3 in 2^-8, 2^-16, 2^-24 units, each within 2^24 units;
+          // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded levels 4..
+          DF v{0.0f, 0.0f};
+#pragma unroll
+          for (int a = kAcc - 1; a >= 0; --a)
+            if (started & (1u << a)) v = df_add(v, DF{__uint_as_float(e[a][j]), 0.0f});
+          out[(int64_t)(c0 + j) * ldM] = make_float2(v.hi, v.lo);
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
     }
   }
   __syncwarp();
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (warp >= 2 && !*abort_flag) {
-    const int q = warp & 3;                       // TMEM lane quarter of this warp
-    const int64_t row = (int64_t)m0 + q * 32 + lane;
-    const uint32_t started = *started_out;
-    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    float2* out = P + ((int64_t)blockIdx.z * ldL + n0) * ldM + row;
-    for (int c0 = 0; c0 < kBN; c0 += 16) {
-      uint32_t e[kAcc][16];
-#pragma unroll
-      for (int a = 0; a < kAcc; ++a) tmem_ld16(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
-      tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        // exact parts: E0 integer, E1..E3 in 2^-8, 2^-16, 2^-24 units, each within 2^24 units;
-        // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded levels 4..
-        DF v{0.0f, 0.0f};
-#pragma unroll
-        for (int a = kAcc - 1; a >= 0; --a)
-          if (started & (1u << a)) v = df_add(v, DF{__uint_as_float(e[a][j]), 0.0f});
-        out[(int64_t)(c0 + j) * ldM] = make_float2(v.hi, v.lo);
-      }
-    }
-  }
   if (err && status) atomicOr(status, (err & 2) ? (kStatTimeout | kStatDrain) : kStatTimeout);
   fence_before();
   __syncthreads();
@@ -407,11 +487,18 @@ cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMa
   if ((e = grow(&o->part, &o->part_b, chunk_bytes * per_launch)) != cudaSuccess) return e;
   if (per_launch < nchunks && (e = grow(&o->acc, &o->acc_b, chunk_bytes)) != cudaSuccess) return e;
   auto kern = k_oz_gemm<SA, SB>;
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)) != cudaSuccess) return e;
+  constexpr int smem = OzSmem<SB>::bytes;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int n_tiles = (int)(ldL / kBN), m_tiles = (int)(ldM / kBM);
   for (int64_t c0 = 0; c0 < nchunks; c0 += per_launch) {
     const int nc = (int)std::min<int64_t>(per_launch, nchunks - c0);
-    dim3 grid((unsigned)(ldL / kBN), (unsigned)(ldM / kBM), (unsigned)nc);
-    kern<<<grid, 192, kSmem, s>>>(tmA, tmB, K, (int)c0, o->part, ldL, ldM, status, wait_cycles);
+    const int64_t items = (int64_t)n_tiles * m_tiles * nc;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, nsm);
+    kern<<<grid, kOzThreads, smem, s>>>(tmA, tmB, K, (int)c0, n_tiles, m_tiles, nc, o->part, ldL, ldM, status,
+                                         wait_cycles);
     note_launch();
     dim3 rg((unsigned)((ldOut + 255) / 256), (unsigned)Nout);
     k_oz_reduce<MODE><<<rg, 256, 0, s>>>(o->part, nc, ldL, ldM, o->acc, c0 == 0, c0 + nc >= nchunks, M, ldOut, rexp,

@@ -252,3 +252,18 @@ def test_tensor_core_wait_timeout_recovers(ngd, prec):
     assert torch.equal(Om, Om2) and torch.equal(Y, Y2)
     ref.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_test_matrix_single_cholesky_qr_pass(ngd, dtype, tol):
+    """ell <= p / 16 (here 500 of 8769): one CholeskyQR pass orthonormalizes the Gaussian test
+    matrix (condition number <= 5/3); the result is the thin QR factor of the oracle's Philox
+    matrix to the working precision, and orthonormal to a few units of it."""
+    wl, pr, th = workload("poisson5d", 300, 80)
+    ctx = ngd.Context(pr, dtype=dtype)
+    Om, Y = ctx.nystrom_sketch(dev(th), 500, seed=17, step=4, prec="f64")
+    O = host(Om).T
+    Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, 500, 17, 4))
+    assert rel(O, Om_o) <= tol
+    assert np.abs(O.T @ O - np.eye(500)).max() <= 5 * tol
+    ctx.close()
