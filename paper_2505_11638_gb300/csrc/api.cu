@@ -86,7 +86,7 @@ struct ngd_ctx {
   cudaStream_t cap_stream = nullptr;     // private stream the graph is captured on
   struct {
     const void* U; bool u_f64; int64_t ldU; const double* lam; int ell; double mu_h; const double* mu_d;
-    double* x; int chunk; void* J; void* prep;
+    double* x; int chunk; void* J; void* prep; bool tape;
   } pcg_key{};
   int pcg_graph_kernels = 0;
   // NGD full: the explicit Gramian (p x p, leading dimension ldG) and diag(w) J in FP64 (N x ldJ),
@@ -97,6 +97,11 @@ struct ngd_ctx {
   double* chol_D = nullptr;
   double* chol_W = nullptr;
   double* chol_T = nullptr;
+
+  // matrix-free VJP by layers: [pt * C + c][max_width] buffers for a chunk of rev_rows points, a
+  // chunk tape when the Taylor coefficients are not stored, K-slice partials, a ones vector
+  int64_t rev_rows = 0;
+  void *rev_A = nullptr, *rev_X = nullptr, *rev_Xb = nullptr, *rev_tape = nullptr, *rev_ones = nullptr;
 
   double* h_scal = nullptr;  // pinned host scalars
   int* h_int = nullptr;
@@ -315,8 +320,101 @@ ngd_status linearize(ngd_ctx* ctx, const double* theta) {
   return check_launch(ctx);
 }
 
-// y = J^T c for the current prep: stored J (when valid), else by point blocks whose Jacobian
-// rows are recomputed (or rebuilt from the stored tape).
+// Workspace of the matrix-free VJP (allocated on first use).
+template <typename T>
+ngd_status ensure_rev(ngd_ctx* ctx) {
+  if (ctx->rev_A) return NGD_OK;
+  const NetDesc& net = ctx->net;
+  const size_t per_row = ((size_t)3 * net.C * net.max_width + (size_t)net.tape_per_point + 1) * sizeof(T);
+  ctx->rev_rows = std::max<int64_t>(32, std::min<int64_t>(ctx->N, (int64_t)((256ull << 20) / per_row)));
+  const size_t buf = (size_t)ctx->rev_rows * net.C * net.max_width * sizeof(T);
+  TRY(dalloc(ctx, &ctx->rev_A, buf));
+  TRY(dalloc(ctx, &ctx->rev_X, buf));
+  TRY(dalloc(ctx, &ctx->rev_Xb, buf));
+  TRY(dalloc(ctx, &ctx->rev_tape, (size_t)ctx->rev_rows * net.tape_per_point * sizeof(T)));
+  TRY(dalloc(ctx, &ctx->rev_ones, (size_t)ctx->rev_rows * sizeof(T)));
+  std::vector<T> ones((size_t)ctx->rev_rows, T(1));
+  CK(cudaMemcpy(ctx->rev_ones, ones.data(), ones.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return NGD_OK;
+}
+
+// K slices of a reduction GEMM with a tiles x K shape: enough blocks to fill the GPU, at least
+// 256 terms per slice.  Returns the slice count launch_gemm will use.
+template <typename T>
+int rev_splits(GemmArgs<T>& g) {
+  const int64_t tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  g.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((600 + tiles - 1) / tiles, g.K / 256));
+  const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : std::max<int64_t>(g.K, 1);
+  return (int)std::max<int64_t>(1, (g.K + kps - 1) / kps);
+}
+
+// y = J^T c with J rows never formed: the reverse of the Taylor-mode forward by layers over chunks
+// of points (Thm. 1; Sec. 4.1.2), the weight adjoint of each layer one GEMM over the chunk's
+// points and channels, the input adjoint another.  The forward coefficients come from the stored
+// tape when it is valid, else the chunk's forward is recomputed.
+template <typename T>
+ngd_status vjp_reverse(ngd_ctx* ctx, const double* cot, double* out) {
+  TRY(ensure_rev<T>(ctx));
+  const NetDesc& net = ctx->net;
+  const int C = net.C, ldb = net.max_width, L = net.n_layers;
+  const int64_t tpp = net.tape_per_point;
+  int64_t toffs[kMaxLayers] = {};
+  for (int l = 1; l < L - 1; ++l) toffs[l] = toffs[l - 1] + (int64_t)C * net.width[l];
+  T* A = (T*)ctx->rev_A;
+  T* X = (T*)ctx->rev_X;
+  T* Xb = (T*)ctx->rev_Xb;
+  const T* prep = (const T*)ctx->prep;
+  for (int64_t r0 = 0; r0 < ctx->N; r0 += ctx->rev_rows) {
+    const int64_t nr = std::min(ctx->rev_rows, ctx->N - r0);
+    const T* tape = (const T*)ctx->tape;
+    if (!ctx->tape_valid) {
+      T* tb = (T*)ctx->rev_tape - r0 * tpp;        // the forward writes the tape of row r at tb + r * tpp
+      if (launch_forward<T>(net, ctx->ps, prep, r0, nr, nullptr, nullptr, tb, 0, ctx->stream) <= 0)
+        return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the forward kernel%s");
+      tape = tb;
+    }
+    launch_rev_seed<T>(net, ctx->ps, r0, nr, cot, A, ldb, ctx->stream);
+    for (int l = L - 1; l >= 0; --l) {
+      const int n_in = net.width[l], n_out = net.width[l + 1];
+      const int64_t nW = (int64_t)n_out * n_in;
+      launch_rev_input<T>(net, ctx->ps, l, tape, l >= 1 ? toffs[l - 1] : 0, r0, nr, X, ldb, ctx->stream);
+      // W_bar_l = sum over (point, channel) rows of abar_l (outer) x_{l-1}
+      GemmArgs<T> g;
+      g.M = n_out; g.N = n_in; g.K = nr * C;
+      g.A = A; g.sam = 1; g.sak = ldb;
+      g.B = X; g.sbk = ldb; g.sbn = 1;
+      g.scm = n_in; g.scn = 1;
+      const int nz = rev_splits(g);
+      TRY(ensure_gpart(ctx, (size_t)nz * nW));
+      g.out64 = ctx->gpart; g.split_stride = nW;
+      launch_gemm<T>(g, ctx->stream);
+      launch_rev_sum(ctx->gpart, nz, nW, nW, out + net.theta_off[l], r0 > 0 ? 1 : 0, ctx->stream);
+      // b_bar_l = sum over points of the value channel of abar_l
+      GemmArgs<T> gb;
+      gb.M = n_out; gb.N = 1; gb.K = nr;
+      gb.A = A; gb.sam = 1; gb.sak = (int64_t)C * ldb;
+      gb.B = (const T*)ctx->rev_ones; gb.sbk = 1; gb.sbn = 0;
+      gb.scm = 1; gb.scn = 0;
+      const int nzb = rev_splits(gb);
+      TRY(ensure_gpart(ctx, (size_t)nzb * n_out));
+      gb.out64 = ctx->gpart; gb.split_stride = n_out;
+      launch_gemm<T>(gb, ctx->stream);
+      launch_rev_sum(ctx->gpart, nzb, n_out, n_out, out + net.theta_off[l] + nW, r0 > 0 ? 1 : 0, ctx->stream);
+      if (l == 0) break;
+      // xbar_{l-1} = W_l^T abar_l for every (point, channel) row, then the adjoint through tanh
+      GemmArgs<T> gx;
+      gx.M = nr * C; gx.N = n_in; gx.K = n_out;
+      gx.A = A; gx.sam = ldb; gx.sak = 1;
+      gx.B = prep + net.wr_off[l]; gx.sbk = n_in; gx.sbn = 1;
+      gx.outT = Xb; gx.scm = ldb; gx.scn = 1;
+      launch_gemm<T>(gx, ctx->stream);
+      launch_rev_tanh<T>(net, l - 1, tape, toffs[l - 1], r0, nr, Xb, A, ldb, ctx->stream);
+    }
+  }
+  return check_launch(ctx);
+}
+
+// y = J^T c for the current prep: stored J (when valid), else the reverse pass by layers.
 template <typename T>
 ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_stored) {
   if (use_stored && ctx->stored_j && ctx->lin_valid) {
@@ -328,22 +426,7 @@ ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_st
                          ctx->stream);
     return check_launch(ctx);
   }
-  const int64_t B = ctx->jrows;
-  const T* tape = ctx->tape_valid ? (const T*)ctx->tape : nullptr;
-  for (int64_t r0 = 0; r0 < ctx->N; r0 += B) {
-    const int64_t nr = std::min(B, ctx->N - r0);
-    const int nb = launch_jacobian<T>(ctx->net, ctx->ps, (const T*)ctx->prep, r0, nr, (T*)ctx->J, ctx->ldJ, nullptr,
-                                      nullptr, tape, 0, ctx->stream);
-    if (nb <= 0) return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the Jacobian kernel%s");
-    const int ns = coldot_nsplit(nr, ctx->ldJ, sizeof(T) == 4 ? 4 : 2);
-    if (std::is_same<T, float>::value)
-      launch_coldot_df((const float*)ctx->J, ctx->ldJ, nr, cot + r0, ctx->colpart, ns, nullptr, ctx->stream);
-    else
-      launch_coldot<T>((const T*)ctx->J, ctx->ldJ, nr, cot + r0, ctx->colpart, ns, nullptr, ctx->stream);
-    launch_coldot_finish(ctx->colpart, ns, ctx->p, ctx->ldJ, nullptr, 0.0, nullptr, out, r0 > 0 ? 1 : 0, nullptr,
-                         ctx->stream);
-  }
-  return check_launch(ctx);
+  return vjp_reverse<T>(ctx, cot, out);
 }
 
 // y = (G + mu I) v at the current linearization.
@@ -834,7 +917,8 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   const auto key_same = [&]() {
     const auto& k = ctx->pcg_key;
     return ctx->pcg_exec && k.U == U && k.u_f64 == u_f64 && k.ldU == ldU && k.lam == lam && k.ell == (pre ? ell : 0) &&
-           k.mu_h == mu_h && k.mu_d == mu_d && k.x == x && k.chunk == chunk && k.J == ctx->J && k.prep == ctx->prep;
+           k.mu_h == mu_h && k.mu_d == mu_d && k.x == x && k.chunk == chunk && k.J == ctx->J && k.prep == ctx->prep &&
+           k.tape == ctx->tape_valid;
   };
   int launched = 0;
   bool converged = false;
@@ -866,7 +950,7 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
         const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
         if (st == NGD_OK && e == cudaSuccess && graph &&
             cudaGraphInstantiate(&ctx->pcg_exec, graph, 0) == cudaSuccess) {
-          ctx->pcg_key = {U, u_f64, ldU, lam, pre ? ell : 0, mu_h, mu_d, x, chunk, ctx->J, ctx->prep};
+          ctx->pcg_key = {U, u_f64, ldU, lam, pre ? ell : 0, mu_h, mu_d, x, chunk, ctx->J, ctx->prep, ctx->tape_valid};
           ctx->pcg_graph_kernels = (int)(launches_now() - l0);
         } else {
           ctx->pcg_exec = nullptr;
@@ -1464,7 +1548,7 @@ void ngd_destroy(ngd_ctx* ctx) {
                  ctx->perm, ctx->eigws, ctx->Y64, ctx->B64, ctx->Zw64, ctx->U64, ctx->Uh, ctx->Ul,
                  ctx->yph, ctx->ypl, ctx->fred, ctx->w1p, ctx->w2f, ctx->vhf, ctx->whf, ctx->gdiag,
                  ctx->samp_keys, ctx->samp_idx, ctx->samp_count, ctx->Gfull, ctx->Zfull, ctx->chol_D,
-                 ctx->chol_W, ctx->chol_T};
+                 ctx->chol_W, ctx->chol_T, ctx->rev_A, ctx->rev_X, ctx->rev_Xb, ctx->rev_tape, ctx->rev_ones};
   for (void* pp : dev)
     if (pp) cudaFree(pp);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);

@@ -84,4 +84,19 @@ template <typename T>
 int launch_jvp(const NetDesc& net, const PointSet& ps, const T* prep, const T* prep_t, double* out,
                int tp, cudaStream_t s);
 
+// ---------------------------------------------------------------- vjp_rev.cu
+// Reverse pass by layers over the points [row0, row0 + npts) (buffers [pt * C + c][ldb]); tape
+// row-indexed (tape + row * tape_per_point), toff the hidden layer's offset in a point's tape.
+template <typename T>
+void launch_rev_seed(const NetDesc& net, const PointSet& ps, int64_t row0, int64_t npts, const double* cot, T* A,
+                     int ldb, cudaStream_t s);
+template <typename T>
+void launch_rev_input(const NetDesc& net, const PointSet& ps, int l, const T* tape, int64_t toff, int64_t row0,
+                      int64_t npts, T* X, int ldb, cudaStream_t s);
+template <typename T>
+void launch_rev_tanh(const NetDesc& net, int lh, const T* tape, int64_t toff, int64_t row0, int64_t npts,
+                     const T* Xb, T* A, int ldb, cudaStream_t s);
+void launch_rev_sum(const double* part, int nz, int64_t stride, int64_t n, double* out, int accumulate,
+                    cudaStream_t s);
+
 }  // namespace ngd

@@ -267,3 +267,30 @@ def test_test_matrix_single_cholesky_qr_pass(ngd, dtype, tol):
     assert rel(O, Om_o) <= tol
     assert np.abs(O.T @ O - np.eye(500)).max() <= 5 * tol
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 5e-5)])
+def test_matrix_free_vjp_heat_width_256(ngd, dtype, tol):
+    """The matrix-free VJP (reverse of the Taylor-mode forward by layers: per-layer weight adjoints
+    as GEMMs over points and channels, no Jacobian rows) on the 4-D heat network (widths 256, p =
+    133121) at 300 interior + 100 boundary/initial points, with the stored Taylor coefficients
+    (budget 0) and with a one-byte budget (the forward recomputed per chunk of points), through the
+    autograd function and through ngd_vjp, against the oracle's VJP; the matrix-free Gramian matvec
+    (JVP then this VJP) against the oracle's explicit Jacobian."""
+    wl, pr, th = workload("heat4d", 300, 100)
+    J = mlp.jacobian(pr, th)
+    rng = np.random.default_rng(31)
+    c = rng.standard_normal(pr.n)
+    g_o = mlp.vjp(pr, th, c)
+    v = rng.standard_normal(pr.p)
+    y_o = gramian.gramian_mv(J, pr.w, v, 1e-3)
+    for budget in [0, 1]:
+        ctx = ngd.Context(pr, dtype=dtype, gv_mode="matrix_free", mem_budget=budget)
+        t = dev(th).requires_grad_(True)
+        r = ngd.PinnResidual.apply(t, ctx)
+        (r * dev(c)).sum().backward()
+        assert rel(host(t.grad), g_o) <= tol, (budget, rel(host(t.grad), g_o))
+        assert rel(host(ctx.vjp(dev(th), dev(c))), g_o) <= tol
+        y = host(ctx.gramian_mv(dev(th), dev(v), 1e-3))
+        assert rel(y, y_o) <= (1e-10 if dtype == "f64" else 1e-5), (budget, rel(y, y_o))
+        ctx.close()
