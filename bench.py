@@ -399,7 +399,9 @@ def run_batch(args, rank, world, local_rank):
         if dist:
             dist.barrier()
 
-    for k in range(args.warmup):
+    if args.packing is not None:
+        batch.set_packing(args.packing)
+    for k in range(args.warmup):             # the first step also tunes the packing of the solves
         batch.step(thetas, step=k, **opts)
     for th, th0 in zip(thetas, thetas0):
         th.copy_(torch.tensor(th0, device="cuda"))
@@ -428,7 +430,8 @@ def run_batch(args, rank, world, local_rank):
                        "p_each": wl.problems[0].p, "ell": wl.ell, "mu": "rule", "rtol": wl.rtol,
                        "sketch": args.sketch},
             "pcg_iters_mean": float(np.mean(iters)), "pcg_iters_max": int(np.max(iters)),
-            "gpu_launches": int(launches), "clocks": clk}
+            "solves_per_launch": batch.packing, "solve_launches_per_step": batch.solve_launches,
+            "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
@@ -647,6 +650,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sketch", default="f64", choices=["f64", "df", "f32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--packing", type=int, default=None,
+                    help="batch64: pCG solves per cooperative launch (default: tuned by the first step)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"],
                     help="batch64: the batching form, 64 problems of uneven size per step (ngd_batch_step)")
     ap.add_argument("--train", action="store_true",

@@ -377,11 +377,25 @@ ngd_status ngd_precond_apply_noalloc(int dtype, int64_t p, int ell, const void* 
  * ngd_batch_create makes one context per description (same rules as ngd_create); every context
  * enqueues on descs[0].stream, so a batch step is one ordered stream of work.
  * ngd_batch_step runs one NGD step (Alg. 1 with Alg. 3 and Alg. 4) for every problem i, with
- * the options in opts and the Philox key opts->seed + i (a distinct test matrix per problem).
+ * the options in opts and the Philox key opts->seed + i (a distinct test matrix per problem), in
+ * three stages over the problems: every problem's gradient, sketch, factor and damping; the pCG
+ * solves; every problem's line search and update.  The solves that take the fused kernel (F32
+ * contexts with the stored Jacobian and a Jacobian width of the first problem's kernel variant)
+ * are packed several to one cooperative launch: each solve runs on a block group sized in
+ * proportion to its point count (at least what its p and ell need), with barriers of its own, so
+ * that the latency-bound phases of one solve overlap the row passes over the Jacobian of the
+ * others; solves are grouped longest-previous-solve first.  The number of solves per launch is
+ * the batch's packing (see ngd_batch_set_packing); untuned (the default), the first batch step
+ * times packings of 1, 2, 4 and 8 solves per launch on its own launches and keeps the one with
+ * the least time per pCG iteration; with the environment variable NGD_AUTOTUNE_CACHE naming a
+ * file, the choice is read from and stored in that JSON file under a key of the SM count, p,
+ * the padded Jacobian width, the problem count and ell.  info->ms_pcg of a packed solve is the
+ * time of all the batch's solves.
  * thetas: host array of n device pointers (each p_i float64, updated in place); infos: host
  * array of n entries or NULL.  Synchronises.  The first failing problem stops the step; its
  * status is returned and ngd_batch_last_error names the problem.
- * Errors: as ngd_create / ngd_step; INVALID_ARG for n < 1 or a NULL argument. */
+ * Errors: as ngd_create / ngd_step; INVALID_ARG for n < 1 or a NULL argument; TIMEOUT when a
+ * packed solve's block-group barrier waited longer than the context's wait limit. */
 typedef struct ngd_batch ngd_batch;
 ngd_status ngd_batch_create(const ngd_problem_desc* descs, int n, ngd_batch** out);
 void ngd_batch_destroy(ngd_batch* batch);
@@ -389,6 +403,12 @@ int ngd_batch_size(const ngd_batch* batch);
 ngd_ctx* ngd_batch_context(ngd_batch* batch, int i);   /* problem i's context (NULL if out of range) */
 const char* ngd_batch_last_error(const ngd_batch* batch);
 ngd_status ngd_batch_step(ngd_batch* batch, double* const* thetas, const ngd_step_opts* opts, ngd_step_info* infos);
+/* Solves per cooperative launch of later batch steps: 0 = tune on the next step (see above),
+ * 1 = one solve per launch on the whole GPU, k > 1 = up to k solves per launch (fewer when their
+ * minimum block groups do not fit).  0 <= solves_per_launch <= 64, else INVALID_ARG. */
+ngd_status ngd_batch_set_packing(ngd_batch* batch, int solves_per_launch);
+int ngd_batch_packing(const ngd_batch* batch);          /* current packing (0: not tuned yet) */
+int ngd_batch_solve_launches(const ngd_batch* batch);   /* packed-solve launches of the last step */
 
 /* Default options: ell 100, mu 0 (rule), gamma 10, rtol 1e-6, maxit 500, FP64-accurate sketch
  * (NGD_SKETCH_F64) in every context (in an F32 context the TF32 / BF16 sketches force a shift of

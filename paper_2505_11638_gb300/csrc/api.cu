@@ -414,6 +414,56 @@ ngd_status vjp_reverse(ngd_ctx* ctx, const double* cot, double* out) {
   return check_launch(ctx);
 }
 
+// out = J v (FP64, N) for the tangent weights prept of v, by forward tangents by layers over chunks
+// of points: per affine layer the pre-activation tangents of every (point, channel) row are
+// X_{l-1} Wdot_l^T + Xdot_{l-1} W_l^T (two GEMMs), then the tangent through tanh (Thm. 1: the
+// J v half of the Gramian matvec, the same layer arithmetic as vjp_reverse's).
+template <typename T>
+ngd_status jvp_layers(ngd_ctx* ctx, const T* prept, double* out) {
+  TRY(ensure_rev<T>(ctx));
+  const NetDesc& net = ctx->net;
+  const int C = net.C, ldb = net.max_width, L = net.n_layers;
+  const int64_t tpp = net.tape_per_point;
+  int64_t toffs[kMaxLayers] = {};
+  for (int l = 1; l < L - 1; ++l) toffs[l] = toffs[l - 1] + (int64_t)C * net.width[l];
+  T* A = (T*)ctx->rev_A;
+  T* X = (T*)ctx->rev_X;
+  T* Xd = (T*)ctx->rev_Xb;
+  const T* prep = (const T*)ctx->prep;
+  for (int64_t r0 = 0; r0 < ctx->N; r0 += ctx->rev_rows) {
+    const int64_t nr = std::min(ctx->rev_rows, ctx->N - r0);
+    const T* tape = (const T*)ctx->tape;
+    if (!ctx->tape_valid) {
+      T* tb = (T*)ctx->rev_tape - r0 * tpp;
+      if (launch_forward<T>(net, ctx->ps, prep, r0, nr, nullptr, nullptr, tb, 0, ctx->stream) <= 0)
+        return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the forward kernel%s");
+      tape = tb;
+    }
+    for (int l = 0; l < L; ++l) {
+      const int n_in = net.width[l], n_out = net.width[l + 1];
+      launch_rev_input<T>(net, ctx->ps, l, tape, l >= 1 ? toffs[l - 1] : 0, r0, nr, X, ldb, ctx->stream);
+      GemmArgs<T> g;
+      g.M = nr * C; g.N = n_out; g.K = n_in;
+      g.A = X; g.sam = ldb; g.sak = 1;
+      g.B = prept + net.wr_off[l]; g.sbk = 1; g.sbn = n_in;
+      g.outT = A; g.scm = ldb; g.scn = 1;
+      launch_gemm<T>(g, ctx->stream);
+      if (l >= 1) {
+        GemmArgs<T> g2 = g;
+        g2.A = Xd;
+        g2.B = prep + net.wr_off[l];
+        g2.accumulate = 1;
+        launch_gemm<T>(g2, ctx->stream);
+      }
+      if (l < L - 1)
+        launch_fwd_tangent<T>(net, l, tape, toffs[l], r0, nr, A, prept + net.b_off[l], Xd, ldb, ctx->stream);
+      else
+        launch_jvp_out<T>(net, ctx->ps, r0, nr, A, prept + net.b_off[l], ldb, out, ctx->stream);
+    }
+  }
+  return check_launch(ctx);
+}
+
 // y = J^T c for the current prep: stored J (when valid), else the reverse pass by layers.
 template <typename T>
 ngd_status vjp_current(ngd_ctx* ctx, const double* cot, double* out, bool use_stored) {
@@ -467,10 +517,9 @@ ngd_status gv_current(ngd_ctx* ctx, const double* v, double mu_h, const double* 
     launch_coldot_finish(ctx->colpart, ctx->colsplit, ctx->p, ctx->ldJ, v, mu_h, mu_d, y, 0, done, ctx->stream);
     return check_launch(ctx);
   }
-  // matrix-free: t = J v by forward tangents, then y = J^T (w t) by recomputed Jacobian blocks
+  // matrix-free: t = J v by forward tangents by layers, then y = J^T (w t) by the reverse by layers
   launch_prep_weights<T>(ctx->net, v, (T*)ctx->prep_t, ctx->stream);
-  if (launch_jvp<T>(ctx->net, ctx->ps, (const T*)ctx->prep, (const T*)ctx->prep_t, ctx->tvec, 0, ctx->stream) <= 0)
-    return set_err(ctx, NGD_ERR_UNSUPPORTED, "network too wide for the JVP kernel%s");
+  TRY(jvp_layers<T>(ctx, (const T*)ctx->prep_t, ctx->tvec));
   launch_mul(ctx->ps.w, ctx->tvec, ctx->svec, ctx->N, ctx->stream);
   TRY(vjp_current<T>(ctx, ctx->svec, y, false));
   launch_coldot_finish(nullptr, 0, ctx->p, ctx->p, v, mu_h, mu_d, y, 1, nullptr, ctx->stream);  // y += mu v
@@ -850,16 +899,53 @@ void precond(ngd_ctx* ctx, bool u_f64, const void* U, int64_t ldU, int ell, cons
     launch_precond<float>((const float*)U, ldU, ctx->p, ell, lam, mu_h, mu_d, v, z, ctx->w1, done, ctx->stream);
 }
 
+// Arguments of the whole solve in one cooperative kernel for this context (FP32 stored J) on G
+// blocks, with U split into its FP32 pair on the context stream; false when the context cannot
+// take that kernel.  The solve's scalars (rtol, maxit) are already on the device.
 template <typename T>
-ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double* mu_d, const void* U, bool u_f64,
-                        int64_t ldU, const double* lam, int ell, double rtol, int maxit, double* dout, int* iters,
-                        double* relres) {
+bool fused_args(ngd_ctx* ctx, const double* g, double mu_h, const double* mu_d, const void* U, bool u_f64,
+                int64_t ldU, const double* lam, int ell, double* x, int G, FusedPcgArgs* out) {
+  const bool pre = U != nullptr && ell > 0;
+  const int64_t p = ctx->p;
+  if (!std::is_same<T, float>::value || !ctx->stored_j || !ctx->yph ||
+      !fused_pcg_supported_on(p, ctx->ldJ, pre ? ell : 0, G))
+    return false;
+  FusedPcgArgs fa;
+  fa.J = (const float*)ctx->J; fa.ldJ = ctx->ldJ; fa.N = ctx->N; fa.p = p; fa.w = ctx->ps.w;
+  if (pre) {
+    if (u_f64)
+      launch_split_transpose_df<double>((const double*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
+    else
+      launch_split_transpose_df<float>((const float*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
+    fa.Uh = ctx->Uh; fa.Ul = ctx->Ul; fa.lam = lam; fa.ell = ell; fa.ldu = (ell + 3) / 4 * 4;
+  }
+  fa.mu_d = mu_d; fa.mu_h = mu_h;
+  fa.g = g; fa.x = x; fa.r = ctx->rr; fa.z = ctx->z; fa.pv = ctx->pv; fa.q = ctx->q;
+  fa.wh = ctx->whf; fa.wl = ctx->whf + ctx->N;
+  fa.vhf = ctx->vhf; fa.vlf = ctx->vhf + ctx->ldJ;
+  fa.yph = ctx->yph; fa.ypl = ctx->ypl; fa.red = ctx->fred; fa.w1p = ctx->w1p; fa.w2 = ctx->w2f;
+  fa.sc = ctx->pcg; fa.mode = 0;
+  fa.wait_cycles = ctx->wait_cycles;
+  *out = fa;
+  return true;
+}
+
+// The device scalars of a solve: rtol and maxit in, everything else cleared; the status word too.
+ngd_status pcg_begin(ngd_ctx* ctx, double rtol, int maxit) {
   PcgScalars* h = ctx->h_pcg;
   memset(h, 0, sizeof(PcgScalars));
   h->rtol2 = rtol * rtol;
   h->maxit = maxit;
   CK(cudaMemcpyAsync(ctx->pcg, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, ctx->stream));
-  TRY(clear_status(ctx));
+  return clear_status(ctx);
+}
+
+template <typename T>
+ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double* mu_d, const void* U, bool u_f64,
+                        int64_t ldU, const double* lam, int ell, double rtol, int maxit, double* dout, int* iters,
+                        double* relres) {
+  PcgScalars* h = ctx->h_pcg;
+  TRY(pcg_begin(ctx, rtol, maxit));
   const int64_t p = ctx->p;
   double* x = dout;
   double* r = ctx->rr;
@@ -868,23 +954,9 @@ ngd_status pcg_internal(ngd_ctx* ctx, const double* g, double mu_h, const double
   double* q = ctx->q;
   const bool pre = U != nullptr && ell > 0;
   const int* done = &ctx->pcg->done;
-  if (std::is_same<T, float>::value && ctx->stored_j && ctx->yph && fused_pcg_supported(p, ctx->ldJ, pre ? ell : 0)) {
+  FusedPcgArgs fa;
+  if (fused_args<T>(ctx, g, mu_h, mu_d, U, u_f64, ldU, lam, ell, x, fused_pcg_blocks(), &fa)) {
     // the whole solve in one cooperative kernel (pcg_fused.cu)
-    FusedPcgArgs fa;
-    fa.J = (const float*)ctx->J; fa.ldJ = ctx->ldJ; fa.N = ctx->N; fa.p = p; fa.w = ctx->ps.w;
-    if (pre) {
-      if (u_f64)
-        launch_split_transpose_df<double>((const double*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
-      else
-        launch_split_transpose_df<float>((const float*)U, ldU, p, ell, ctx->Uh, ctx->Ul, ctx->stream);
-      fa.Uh = ctx->Uh; fa.Ul = ctx->Ul; fa.lam = lam; fa.ell = ell; fa.ldu = (ell + 3) / 4 * 4;
-    }
-    fa.mu_d = mu_d; fa.mu_h = mu_h;
-    fa.g = g; fa.x = x; fa.r = r; fa.z = z; fa.pv = pv; fa.q = q;
-    fa.wh = ctx->whf; fa.wl = ctx->whf + ctx->N;
-    fa.vhf = ctx->vhf; fa.vlf = ctx->vhf + ctx->ldJ;
-    fa.yph = ctx->yph; fa.ypl = ctx->ypl; fa.red = ctx->fred; fa.w1p = ctx->w1p; fa.w2 = ctx->w2f;
-    fa.sc = ctx->pcg; fa.mode = 0;
     const cudaError_t e = launch_pcg_fused(fa, ctx->stream);
     if (e != cudaErrorCooperativeLaunchTooLarge) {
       CK(e);
@@ -1228,10 +1300,24 @@ struct PhaseRange {
   }
 };
 
-template <typename T>
-ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_step_info* info) {
+// State of one NGD step between its stages (a batch runs the stages of many problems in turn).
+struct StepState {
   ngd_step_info inf{};
-  const int64_t p = ctx->p;
+  bool rpchol = false, full = false;
+  int ell_pc = 0, rp_rank = 0;
+  double rp_lam1 = 0.0;
+  bool u_f64 = true;
+  const void* Ust = nullptr;
+  int iters = 0;
+  double relres = 0.0;
+};
+
+// Stage 1 of a step: gradient and linearization, then the preconditioner (Nystrom sketch and
+// factor with the damping, RPCholesky) or NGD full's direction.
+template <typename T>
+ngd_status step_prepare(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, StepState& st) {
+  ngd_step_info& inf = st.inf;
+  inf = ngd_step_info{};
   PhaseRange phase;
   phase.next("linearize");
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
@@ -1240,18 +1326,22 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   launch_mul(ctx->ps.w, ctx->r, ctx->svec, ctx->N, ctx->stream);
   TRY(vjp_current<T>(ctx, ctx->svec, ctx->g, true));
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-  const bool rpchol = o->precond == NGD_PRECOND_RPCHOL;
-  const bool full = o->precond == NGD_DIRECT_FULL;
-  int ell_pc = o->ell, rp_rank = 0;
-  double rp_lam1 = 0.0;
-  bool u_f64 = true;
-  const void* Ust = nullptr;               // taken after the factor: the workspace grows on demand
+  const bool rpchol = st.rpchol = o->precond == NGD_PRECOND_RPCHOL;
+  const bool full = st.full = o->precond == NGD_DIRECT_FULL;
+  int& ell_pc = st.ell_pc;
+  ell_pc = o->ell;
+  st.rp_rank = 0;
+  st.rp_lam1 = 0.0;
+  bool& u_f64 = st.u_f64;
+  u_f64 = true;
+  const void*& Ust = st.Ust;               // taken after the factor: the workspace grows on demand
+  Ust = nullptr;
   if (rpchol) {
     // Alg. 5: RPCholesky preconditioner (its mu comes from the power-method lambda_1)
     phase.next("rpchol");
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
     const double* Urp = nullptr;
-    TRY(rpchol_build<T>(ctx, o, &ell_pc, &rp_rank, &rp_lam1, &Urp));
+    TRY(rpchol_build<T>(ctx, o, &ell_pc, &st.rp_rank, &st.rp_lam1, &Urp));
     Ust = Urp;
     u_f64 = true;
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -1283,14 +1373,35 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
     u_f64 = !std::is_same<T, float>::value || acc64(o->sketch);
     Ust = std::is_same<T, float>::value && acc64(o->sketch) ? (const void*)ctx->U64 : ctx->U;
   }
+  return NGD_OK;
+}
+
+// Stage 2: the direction by pCG on (G + mu I) d = g with the preconditioner of Alg. 4 or Alg. 5
+// (Alg. 3); nothing for NGD full.
+template <typename T>
+ngd_status step_solve(ngd_ctx* ctx, const ngd_step_opts* o, StepState& st) {
+  PhaseRange phase;
   phase.next("pcg");
-  // Alg. 3, direction: pCG on (G + mu I) d = g with the preconditioner of Alg. 4 or Alg. 5
-  int iters = 0;
-  double relres = 0.0;
-  if (!full)
-    TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, Ust, u_f64, ctx->ldP, ctx->lam, ell_pc, o->rtol,
-                        o->maxit, ctx->d, &iters, &relres));
+  st.iters = 0;
+  st.relres = 0.0;
+  if (!st.full)
+    TRY(pcg_internal<T>(ctx, ctx->g, 0.0, ctx->scal + kSMu, st.Ust, st.u_f64, ctx->ldP, ctx->lam, st.ell_pc, o->rtol,
+                        o->maxit, ctx->d, &st.iters, &st.relres));
   CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+  return NGD_OK;
+}
+
+// Stage 3: Armijo line search along theta - alpha d, the update, the next rank and the step's info.
+template <typename T>
+ngd_status step_finish(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, StepState& st, ngd_step_info* info) {
+  ngd_step_info& inf = st.inf;
+  const int64_t p = ctx->p;
+  const bool rpchol = st.rpchol, full = st.full;
+  const int ell_pc = st.ell_pc, rp_rank = st.rp_rank;
+  const double rp_lam1 = st.rp_lam1;
+  const int iters = st.iters;
+  const double relres = st.relres;
+  PhaseRange phase;
   phase.next("linesearch");
   // Alg. 1, line search: Armijo backtracking along theta - alpha d
   launch_dot(ctx->g, ctx->d, p, ctx->part, ctx->scal + kSDot, ctx->stream);
@@ -1373,7 +1484,30 @@ ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_st
   return check_launch(ctx);
 }
 
+template <typename T>
+ngd_status step_impl(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_step_info* info) {
+  StepState st;
+  TRY(step_prepare<T>(ctx, theta, o, st));
+  TRY(step_solve<T>(ctx, o, st));
+  return step_finish<T>(ctx, theta, o, st, info);
+}
+
 }  // namespace
+
+static bool valid_prec(int prec) { return prec >= NGD_SKETCH_F64 && prec <= NGD_SKETCH_DF; }
+
+// Host checks of ngd_step's options against the context.
+static ngd_status check_step_opts(ngd_ctx* ctx, const ngd_step_opts* o) {
+  if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
+      !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1 ||
+      !(o->mu_loss_coef >= 0.0) || o->ell_max < 0 || o->ell_max > std::min<int64_t>(ctx->p, 2048) ||
+      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1 || o->precond < 0 || o->precond > 2 ||
+      (o->precond == NGD_PRECOND_RPCHOL && (o->rpchol_block < 1 || o->rpchol_block > o->ell || o->ell > 2047)))
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
+  if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)
+    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
+  return NGD_OK;
+}
 
 // ====================================================================== C ABI
 extern "C" {
@@ -1700,7 +1834,6 @@ ngd_status ngd_gramian_mv(ngd_ctx* ctx, const double* theta, const double* v, do
   });
 }
 
-static bool valid_prec(int prec) { return prec >= NGD_SKETCH_F64 && prec <= NGD_SKETCH_DF; }
 
 ngd_status ngd_nystrom_sketch(ngd_ctx* ctx, const double* theta, int ell, uint64_t seed, uint64_t step, int prec,
                               void* Omega, void* Y) {
@@ -1863,14 +1996,7 @@ ngd_status ngd_pcg_solve(ngd_ctx* ctx, const double* theta, const double* g, dou
 ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_step_info* info) {
   if (!ctx) return NGD_ERR_INVALID_ARG;
   if (!theta || !o) return set_err(ctx, NGD_ERR_INVALID_ARG, "theta/opts NULL%s");
-  if (o->ell < 1 || o->ell > std::min<int64_t>(ctx->p, 2048) || !(o->rtol >= 0.0) || o->maxit < 1 ||
-      !valid_prec(o->sketch) || !(o->armijo_rho > 0.0 && o->armijo_rho < 1.0) || o->armijo_max < 1 ||
-      !(o->mu_loss_coef >= 0.0) || o->ell_max < 0 || o->ell_max > std::min<int64_t>(ctx->p, 2048) ||
-      o->ell_delta < 0 || o->test_matrix < 0 || o->test_matrix > 1 || o->precond < 0 || o->precond > 2 ||
-      (o->precond == NGD_PRECOND_RPCHOL && (o->rpchol_block < 1 || o->rpchol_block > o->ell || o->ell > 2047)))
-    return set_err(ctx, NGD_ERR_INVALID_ARG, "bad step options%s");
-  if (ctx->dtype == NGD_F64 && o->sketch != NGD_SKETCH_F64)
-    return set_err(ctx, NGD_ERR_INVALID_ARG, "an F64 context sketches in F64 only%s");
+  TRY(check_step_opts(ctx, o));
   return by_dtype(ctx, [&](auto z) -> ngd_status {
     using T = decltype(z);
     return step_impl<T>(ctx, theta, o, info);
@@ -1880,10 +2006,239 @@ ngd_status ngd_step(ngd_ctx* ctx, double* theta, const ngd_step_opts* o, ngd_ste
 }  // extern "C"
 
 // ------------------------------------------------------------------ batching form
+// Many problems stepped together.  A batch step runs every problem's first stage (gradient,
+// sketch, factor, damping), then the pCG solves, then every problem's line search.  Solves that
+// fit the fused kernel are packed several to one cooperative launch: problem j gets a block group
+// sized in proportion to its point count (at least the blocks its p and ell need), the groups
+// synchronise on their own barrier counters, and the latency-bound phases of one solve overlap the
+// row passes of the others.  How many solves share a launch is tuned on the batch itself: the
+// first batch step times each feasible packing (1, 2, 4, 8 solves per launch) on its own
+// launches and keeps the one with the lowest time per pCG iteration; the choice can be kept in a
+// JSON file named by the environment variable NGD_AUTOTUNE_CACHE (key: SM count, p, padded
+// Jacobian width, ell, problem count).
 struct ngd_batch {
   std::vector<ngd_ctx*> ctx;
   std::string err;
+  FusedPcgArgs* tab_host = nullptr;   // pinned: one table slot per problem and launch
+  FusedPcgArgs* tab_dev = nullptr;
+  unsigned int* bars = nullptr;       // one barrier counter (padded to 32 words) per problem
+  int cap = 0;
+  std::vector<int> last_iters;        // pCG iterations of each problem's previous solve
+  int pack = 0;                       // solves per launch (0: not tuned yet)
+  std::vector<int> tune_candidates;
+  std::vector<double> tune_cost;      // ms per pCG iteration of each candidate
+  std::string tune_key_base, tune_key;
+  cudaEvent_t ev[2] = {};
+  int launches_last = 0;              // cooperative launches of the last batch step's solves
 };
+
+namespace {
+
+// JSON cache of tuned packings: a flat object {"key": value, ...}.
+std::string tune_cache_path() {
+  const char* p = std::getenv("NGD_AUTOTUNE_CACHE");
+  return p ? std::string(p) : std::string();
+}
+
+int tune_cache_get(const std::string& key) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return 0;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return 0;
+  std::string text;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, n);
+  std::fclose(f);
+  const std::string pat = "\"" + key + "\":";
+  const size_t at = text.find(pat);
+  if (at == std::string::npos) return 0;
+  return std::atoi(text.c_str() + at + pat.size());
+}
+
+void tune_cache_put(const std::string& key, int value) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  std::vector<std::pair<std::string, int>> entries;
+  if (FILE* f = std::fopen(path.c_str(), "r")) {
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, n);
+    std::fclose(f);
+    size_t pos = 0;
+    while ((pos = text.find('"', pos)) != std::string::npos) {
+      const size_t end = text.find('"', pos + 1);
+      if (end == std::string::npos) break;
+      const size_t colon = text.find(':', end);
+      if (colon == std::string::npos) break;
+      entries.emplace_back(text.substr(pos + 1, end - pos - 1), std::atoi(text.c_str() + colon + 1));
+      pos = colon + 1;
+    }
+  }
+  bool found = false;
+  for (auto& e : entries)
+    if (e.first == key) {
+      e.second = value;
+      found = true;
+    }
+  if (!found) entries.emplace_back(key, value);
+  const std::string tmp = path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{");
+  for (size_t i = 0; i < entries.size(); ++i)
+    std::fprintf(f, "%s\n  \"%s\": %d", i ? "," : "", entries[i].first.c_str(), entries[i].second);
+  std::fprintf(f, "\n}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+// Block groups of one launch: problems idx (their point counts N), at least gmin[k] blocks each,
+// G blocks in all; the rest shared in proportion to N.  False if the minima do not fit.
+bool split_blocks(const std::vector<int>& idx, const std::vector<ngd_ctx*>& ctx, const std::vector<int>& gmin, int G,
+                  std::vector<int>& groups) {
+  const size_t m = idx.size();
+  groups.assign(m, 0);
+  int need = 0;
+  double ntot = 0.0;
+  for (size_t k = 0; k < m; ++k) {
+    need += gmin[k];
+    ntot += (double)ctx[idx[k]]->N;
+  }
+  if (need > G) return false;
+  int used = 0;
+  for (size_t k = 0; k < m; ++k) {
+    const int share = (int)std::floor((double)G * (double)ctx[idx[k]]->N / ntot);
+    groups[k] = std::max(gmin[k], share);
+    used += groups[k];
+  }
+  // trim the largest groups down to G, or hand the remainder to the largest problems
+  while (used > G) {
+    size_t best = m;
+    for (size_t k = 0; k < m; ++k)
+      if (groups[k] > gmin[k] && (best == m || groups[k] > groups[best])) best = k;
+    if (best == m) return false;
+    --groups[best];
+    --used;
+  }
+  for (size_t k = 0; used < G; k = (k + 1) % m, ++used) ++groups[k];
+  return true;
+}
+
+ngd_status batch_fail(ngd_batch* b, int i, ngd_status st) {
+  b->err = "problem " + std::to_string(i) + ": " + ngd_last_error(b->ctx[(size_t)i]);
+  return st;
+}
+
+// The pCG solves of the problems in `solve` (stage 2 of a batch step), packed b->pack (or the
+// candidate being tuned) to a cooperative launch.
+ngd_status batch_solves(ngd_batch* b, const std::vector<int>& solve, std::vector<StepState>& st,
+                        const ngd_step_opts* o) {
+  ngd_ctx* ctx = b->ctx[0];            // CUDA failures of the shared stream are reported on problem 0
+  const int G = fused_pcg_blocks();
+  cudaStream_t s = ctx->stream;
+  // order: longest previous solves first, so that a launch holds solves of similar length
+  std::vector<int> order(solve);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->last_iters[x] > b->last_iters[y]; });
+  const bool tuning = b->pack == 0;
+  size_t pos = 0;
+  int cand = 0, launches = 0, slot = 0;
+  while (pos < order.size()) {
+    const int want = tuning ? b->tune_candidates[(size_t)cand % b->tune_candidates.size()] : b->pack;
+    // take up to `want` solves whose minima fit G together
+    std::vector<int> idx, gmin, groups;
+    while (pos < order.size() && (int)idx.size() < want) {
+      const int i = order[pos];
+      ngd_ctx* c = b->ctx[(size_t)i];
+      const int gm = fused_pcg_min_blocks(c->p, st[(size_t)i].ell_pc);
+      std::vector<int> trial(idx);
+      trial.push_back(i);
+      std::vector<int> tmin(gmin);
+      tmin.push_back(gm);
+      if (!split_blocks(trial, b->ctx, tmin, G, groups)) break;
+      idx.push_back(i);
+      gmin.push_back(gm);
+      ++pos;
+    }
+    if (idx.empty()) return NGD_ERR_UNSUPPORTED;          // cannot happen: one solve takes all blocks
+    split_blocks(idx, b->ctx, gmin, G, groups);
+    const bool timed = tuning;
+    if (timed) cudaEventRecord(b->ev[0], s);
+    int gb0 = 0;
+    for (size_t k = 0; k < idx.size(); ++k) {
+      const int i = idx[k];
+      ngd_ctx* c = b->ctx[(size_t)i];
+      StepState& ss = st[(size_t)i];
+      TRY(pcg_begin(c, o->rtol, o->maxit));
+      FusedPcgArgs fa;
+      if (!fused_args<float>(c, c->g, 0.0, c->scal + kSMu, ss.Ust, ss.u_f64, c->ldP, c->lam, ss.ell_pc, c->d,
+                             groups[k], &fa))
+        return set_err(c, NGD_ERR_UNSUPPORTED, "fused solve unavailable in the batch%s");
+      fa.gb0 = gb0;
+      fa.gG = groups[k];
+      fa.bar = b->bars + (size_t)(slot + (int)k) * 32;
+      b->tab_host[slot + (int)k] = fa;
+      gb0 += groups[k];
+    }
+    const int m = (int)idx.size();
+    if (cudaMemsetAsync(b->bars + (size_t)slot * 32, 0, (size_t)m * 32 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemcpyAsync(b->tab_dev + slot, b->tab_host + slot, (size_t)m * sizeof(FusedPcgArgs),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return batch_fail(b, idx[0], set_err(b->ctx[(size_t)idx[0]], NGD_ERR_CUDA, "batch solve table%s"));
+    const cudaError_t e = launch_pcg_fused_multi(b->tab_dev + slot, b->tab_host + slot, m, s);
+    if (e != cudaSuccess)
+      return batch_fail(b, idx[0], set_err(b->ctx[(size_t)idx[0]], NGD_ERR_CUDA, "multi-problem solve: %s",
+                                           cudaGetErrorString(e)));
+    ++launches;
+    slot += m;
+    if (timed) {
+      cudaEventRecord(b->ev[1], s);
+      for (int i : idx) {
+        ngd_ctx* c = b->ctx[(size_t)i];
+        CK(cudaMemcpyAsync(c->h_pcg, c->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+      }
+      CK(cudaStreamSynchronize(s));
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+      long iters = 0;
+      for (int i : idx) iters += b->ctx[(size_t)i]->h_pcg->iters;
+      const size_t ci = (size_t)cand % b->tune_candidates.size();
+      if (iters > 0 && (b->tune_cost[ci] < 0.0 || ms / (double)iters < b->tune_cost[ci]))
+        b->tune_cost[ci] = ms / (double)iters;
+      ++cand;
+    }
+  }
+  b->launches_last = launches;
+  for (int i : solve) {
+    ngd_ctx* c = b->ctx[(size_t)i];
+    CK(cudaMemcpyAsync(c->h_pcg, c->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int i : solve) {
+    ngd_ctx* c = b->ctx[(size_t)i];
+    if (c->h_pcg->status & kStatTimeout) return batch_fail(b, i, set_err(c, NGD_ERR_TIMEOUT, "solve barrier timed out%s"));
+    const ngd_status r = pcg_result(c, c->h_pcg, &st[(size_t)i].iters, &st[(size_t)i].relres);
+    if (r != NGD_OK) return batch_fail(b, i, r);
+    CK(cudaEventRecord(c->ev[4], c->stream));
+    b->last_iters[(size_t)i] = st[(size_t)i].iters;
+  }
+  if (tuning) {
+    // every candidate measured at least once: keep the cheapest per pCG iteration
+    bool all = true;
+    for (double v : b->tune_cost) all = all && v >= 0.0;
+    if (all) {
+      size_t best = 0;
+      for (size_t k = 1; k < b->tune_cost.size(); ++k)
+        if (b->tune_cost[k] < b->tune_cost[best]) best = k;
+      b->pack = b->tune_candidates[best];
+      tune_cache_put(b->tune_key, b->pack);
+    }
+  }
+  return NGD_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1899,12 +2254,31 @@ ngd_status ngd_batch_create(const ngd_problem_desc* descs, int n, ngd_batch** ou
     ngd_ctx* c = nullptr;
     const ngd_status st = ngd_create(&d, &c);
     if (st != NGD_OK) {
-      for (ngd_ctx* q : b->ctx) ngd_destroy(q);
-      delete b;
+      ngd_batch_destroy(b);
       return st;
     }
     b->ctx.push_back(c);
   }
+  b->cap = n;
+  b->last_iters.assign((size_t)n, 0);
+  if (cudaMallocHost((void**)&b->tab_host, (size_t)n * sizeof(FusedPcgArgs)) != cudaSuccess ||
+      cudaMalloc((void**)&b->tab_dev, (size_t)n * sizeof(FusedPcgArgs)) != cudaSuccess ||
+      cudaMalloc((void**)&b->bars, (size_t)n * 32 * sizeof(unsigned)) != cudaSuccess ||
+      cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    ngd_batch_destroy(b);
+    return NGD_ERR_OOM;
+  }
+  // packings to try (2^k solves per launch while their minimum block groups fit the GPU)
+  const ngd_ctx* c0 = b->ctx[0];
+  b->tune_candidates = {1};
+  for (int k = 2; k <= 8 && k <= n; k *= 2) b->tune_candidates.push_back(k);
+  b->tune_cost.assign(b->tune_candidates.size(), -1.0);
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  b->tune_key_base = "sm" + std::to_string(nsm) + "_p" + std::to_string(c0->p) + "_ldJ" + std::to_string(c0->ldJ) +
+                     "_n" + std::to_string(n);
   *out = b;
   return NGD_OK;
 }
@@ -1912,6 +2286,11 @@ ngd_status ngd_batch_create(const ngd_problem_desc* descs, int n, ngd_batch** ou
 void ngd_batch_destroy(ngd_batch* b) {
   if (!b) return;
   for (ngd_ctx* c : b->ctx) ngd_destroy(c);
+  if (b->tab_host) cudaFreeHost(b->tab_host);
+  if (b->tab_dev) cudaFree(b->tab_dev);
+  if (b->bars) cudaFree(b->bars);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
   delete b;
 }
 
@@ -1924,6 +2303,17 @@ ngd_ctx* ngd_batch_context(ngd_batch* b, int i) {
 
 const char* ngd_batch_last_error(const ngd_batch* b) { return b ? b->err.c_str() : ""; }
 
+ngd_status ngd_batch_set_packing(ngd_batch* b, int solves_per_launch) {
+  if (!b || solves_per_launch < 0 || solves_per_launch > 64) return NGD_ERR_INVALID_ARG;
+  b->pack = solves_per_launch;
+  if (solves_per_launch == 0) std::fill(b->tune_cost.begin(), b->tune_cost.end(), -1.0);
+  return NGD_OK;
+}
+
+int ngd_batch_packing(const ngd_batch* b) { return b ? b->pack : -1; }
+
+int ngd_batch_solve_launches(const ngd_batch* b) { return b ? b->launches_last : -1; }
+
 ngd_status ngd_batch_step(ngd_batch* b, double* const* thetas, const ngd_step_opts* opts, ngd_step_info* infos) {
   if (!b) return NGD_ERR_INVALID_ARG;
   if (!thetas || !opts) {
@@ -1931,14 +2321,64 @@ ngd_status ngd_batch_step(ngd_batch* b, double* const* thetas, const ngd_step_op
     return NGD_ERR_INVALID_ARG;
   }
   b->err.clear();
-  for (size_t i = 0; i < b->ctx.size(); ++i) {
-    ngd_step_opts o = *opts;
-    o.seed = opts->seed + i;
-    const ngd_status st = ngd_step(b->ctx[i], thetas[i], &o, infos ? infos + i : nullptr);
-    if (st != NGD_OK) {
-      b->err = "problem " + std::to_string(i) + ": " + ngd_last_error(b->ctx[i]);
-      return st;
-    }
+  const size_t n = b->ctx.size();
+  b->tune_key = b->tune_key_base + "_ell" + std::to_string(opts->ell);
+  if (b->pack == 0) {
+    const int cached = tune_cache_get(b->tune_key);
+    if (cached > 0) b->pack = cached;
+  }
+  std::vector<ngd_step_opts> o(n, *opts);
+  for (size_t i = 0; i < n; ++i) {
+    o[i].seed = opts->seed + i;
+    const ngd_status v = check_step_opts(b->ctx[i], &o[i]);
+    if (v != NGD_OK) return batch_fail(b, (int)i, v);
+  }
+  std::vector<StepState> st(n);
+  // stage 1 for every problem
+  for (size_t i = 0; i < n; ++i) {
+    ngd_ctx* c = b->ctx[i];
+    const ngd_status r = by_dtype(c, [&](auto z) -> ngd_status {
+      using T = decltype(z);
+      return step_prepare<T>(c, thetas[i], &o[i], st[i]);
+    });
+    if (r != NGD_OK) return batch_fail(b, (int)i, r);
+  }
+  // stage 2: the fused solves packed several to a launch (a single problem, or a packing of one,
+  // keeps the whole-grid launch), the others one by one
+  std::vector<int> packed;
+  for (size_t i = 0; i < n; ++i) {
+    ngd_ctx* c = b->ctx[i];
+    const bool pre = st[i].Ust != nullptr && st[i].ell_pc > 0;
+    if (n > 1 && b->pack != 1 && !st[i].full && c->dtype == NGD_F32 && c->stored_j && c->yph &&
+        fused_pcg_supported(c->p, c->ldJ, pre ? st[i].ell_pc : 0) &&
+        fused_pcg_slots(c->ldJ) == fused_pcg_slots(b->ctx[0]->ldJ))
+      packed.push_back((int)i);
+  }
+  if (packed.size() < 2) packed.clear();
+  std::vector<char> is_packed(n, 0);
+  for (int i : packed) is_packed[(size_t)i] = 1;
+  for (size_t i = 0; i < n; ++i) {
+    if (is_packed[i]) continue;
+    ngd_ctx* c = b->ctx[i];
+    const ngd_status r = by_dtype(c, [&](auto z) -> ngd_status {
+      using T = decltype(z);
+      return step_solve<T>(c, &o[i], st[i]);
+    });
+    if (r != NGD_OK) return batch_fail(b, (int)i, r);
+    b->last_iters[i] = st[i].iters;
+  }
+  if (!packed.empty()) {
+    const ngd_status r = batch_solves(b, packed, st, opts);
+    if (r != NGD_OK) return r;
+  }
+  // stage 3 for every problem
+  for (size_t i = 0; i < n; ++i) {
+    ngd_ctx* c = b->ctx[i];
+    const ngd_status r = by_dtype(c, [&](auto z) -> ngd_status {
+      using T = decltype(z);
+      return step_finish<T>(c, thetas[i], &o[i], st[i], infos ? infos + i : nullptr);
+    });
+    if (r != NGD_OK) return batch_fail(b, (int)i, r);
   }
   return NGD_OK;
 }

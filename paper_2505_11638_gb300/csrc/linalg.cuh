@@ -166,10 +166,24 @@ struct FusedPcgArgs {
   float2* w2 = nullptr;                                      // ell
   PcgScalars* sc = nullptr;                                  // rtol2, maxit in; iterations and status out
   int mode = 0;                                              // 0: PCG; 1: q = (G + mu I) pv only
+  // block group of the solve in a multi-problem launch: blocks gb0 .. gb0 + gG - 1; bar: the
+  // group's barrier counter (zeroed before the launch; null: the whole grid, cooperative grid
+  // barrier); wait_cycles: limit of each group barrier wait
+  int gb0 = 0, gG = 0;
+  unsigned int* bar = nullptr;
+  long long wait_cycles = 4000000000ll;
 };
 int fused_pcg_blocks();
+int fused_pcg_slots(int64_t ldJ);
 bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell);
+bool fused_pcg_supported_on(int64_t p, int64_t ldJ, int ell, int G);
+int fused_pcg_min_blocks(int64_t p, int ell);      // fewest blocks a solve may run on
 cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s);
+// nprob solves in one cooperative launch: tab_host[j] (and its device copy tab_dev) describes
+// problem j with its block group (gb0 consecutive, gG blocks, its own zeroed barrier counter bar);
+// all problems share fused_pcg_slots(ldJ) rounded up to even.
+cudaError_t launch_pcg_fused_multi(const FusedPcgArgs* tab_dev, const FusedPcgArgs* tab_host, int nprob,
+                                   cudaStream_t s);
 template <typename TU>
 void launch_split_transpose_df(const TU* U, int64_t ldu, int64_t p, int ell, float* Uh, float* Ul, cudaStream_t s);
 

@@ -98,5 +98,12 @@ void launch_rev_tanh(const NetDesc& net, int lh, const T* tape, int64_t toff, in
                      const T* Xb, T* A, int ldb, cudaStream_t s);
 void launch_rev_sum(const double* part, int nz, int64_t stride, int64_t n, double* out, int accumulate,
                     cudaStream_t s);
+// forward tangents by layers (J v): tanh tangent of hidden layer lh, and J v from the output tangents
+template <typename T>
+void launch_fwd_tangent(const NetDesc& net, int lh, const T* tape, int64_t toff, int64_t row0, int64_t npts,
+                        const T* Ad, const T* bdot, T* Xd, int ldb, cudaStream_t s);
+template <typename T>
+void launch_jvp_out(const NetDesc& net, const PointSet& ps, int64_t row0, int64_t npts, const T* Ad, const T* bdot,
+                    int ldb, double* out, cudaStream_t s);
 
 }  // namespace ngd

@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kT = 384;            // threads per block (one block per SM, 12 warps)
 constexpr int kW = kT / 32;        // warps per block
-constexpr int kMaxSlice = 128;     // largest j slice per block (p <= kMaxSlice * G)
+constexpr int kMaxSlice = 256;     // largest j slice per block (p <= kMaxSlice * G)
 
 __device__ __forceinline__ uint64_t evict_first_policy() {
   uint64_t pol;
@@ -73,10 +73,43 @@ __device__ __forceinline__ double block_allsum(double v, double* red) {
   return red[kT];
 }
 
-// sum over blocks of red[b * 4 + slot] (G <= kT)
-__device__ __forceinline__ double grid_total(const double* red, int slot, double* sred) {
-  const double v = (int)threadIdx.x < (int)gridDim.x ? __ldcg(red + threadIdx.x * 4 + slot) : 0.0;
+// sum over the G blocks of the solve of red[b * 4 + slot] (G <= kT)
+__device__ __forceinline__ double grid_total(const double* red, int slot, double* sred, int G) {
+  const double v = (int)threadIdx.x < G ? __ldcg(red + threadIdx.x * 4 + slot) : 0.0;
   return block_allsum(v, sred);
+}
+
+// Barrier of the blocks of one solve.  A single-problem launch uses the cooperative grid barrier;
+// a multi-problem launch (one block group per problem, all groups co-resident in one cooperative
+// launch) uses the group's arrival counter a.bar: block arrivals of one barrier make up one
+// generation of gG counts, and a block waits until its generation is complete.  The wait is
+// bounded (a.wait_cycles); when it runs out the solve's status gets kStatTimeout, and every later
+// barrier of the solve returns at once (the loop then ends at its next convergence test).
+__device__ __forceinline__ void gsync(const FusedPcgArgs& a, int gG, cg::grid_group& grid) {
+  if (!a.bar) {
+    grid.sync();
+    return;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* st = &a.sc->status;
+    if (!(*st & kStatTimeout)) {
+      __threadfence();
+      const unsigned arrived = atomicAdd(a.bar, 1u) + 1u;
+      const unsigned target = (arrived + (unsigned)gG - 1u) / (unsigned)gG * (unsigned)gG;
+      const long long t0 = clock64();
+      for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.bar) : "memory");
+        if ((int)(v - target) >= 0) break;
+        if (clock64() - t0 > a.wait_cycles) {
+          atomicOr(&a.sc->status, kStatTimeout);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
 }
 
 
@@ -124,13 +157,13 @@ __device__ __forceinline__ void nbar_arrive(int id, int count) {
 }
 
 template <int CG, int S>
-__device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, Smem& sm) {
+__device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, int gb, int gG, float4* ring, Smem& sm) {
   constexpr int PD = S - 2;                      // rows prefetched ahead of the dot group
   static_assert(S >= 3 && S <= kMaxStages, "ring stages");
   const int tid = threadIdx.x, lane = tid & 31;
   const int g = tid % kGT;
   const bool dot_group = tid < kGT;
-  const int G = gridDim.x, b = blockIdx.x;
+  const int G = gG, b = gb;
   const int nv4 = (int)(a.ldJ / 4);
   const int64_t rb0 = a.N * b / G, rb1 = a.N * (b + 1) / G;
   const int nrows = (int)(rb1 - rb0);
@@ -236,9 +269,9 @@ __device__ __forceinline__ void gv_rows(const FusedPcgArgs& a, float4* ring, Sme
 }
 
 // The block's j slice of v, split into FP32 pairs for phase A.
-__device__ __forceinline__ void split_slice(const FusedPcgArgs& a, const double* v) {
+__device__ __forceinline__ void split_slice(const FusedPcgArgs& a, int gb, int gG, const double* v) {
   int64_t cb0, cb1;
-  col_slice(a.p, blockIdx.x, gridDim.x, cb0, cb1);
+  col_slice(a.p, gb, gG, cb0, cb1);
   for (int64_t j = cb0 + threadIdx.x; j < cb1; j += kT) {
     float h, l;
     split_df(v[j], h, l);
@@ -250,10 +283,11 @@ __device__ __forceinline__ void split_slice(const FusedPcgArgs& a, const double*
 // Phase B: q_j = sum_b y_b[j] + mu v_j on the block's j slice; returns the block's sum of v_j q_j.
 // Thread (c4, g): columns 4 c4 .. 4 c4 + 3 of the slice, partials b = g, g + kW, ...; scr: shared
 // scratch of kW x 32 x 4 double-float values.
-__device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, const double* v, double mu, double* q, DF* scr) {
-  const int tid = threadIdx.x, G = gridDim.x;
+__device__ __forceinline__ double gv_finish(const FusedPcgArgs& a, int gb, int gG, const double* v, double mu,
+                                            double* q, DF* scr) {
+  const int tid = threadIdx.x, G = gG;
   int64_t cb0, cb1;
-  col_slice(a.p, blockIdx.x, G, cb0, cb1);
+  col_slice(a.p, gb, G, cb0, cb1);
   const int c4 = tid & 31, g = tid >> 5;                 // 32 column quads x kW partial groups
   double vq = 0.0;
   for (int64_t j0 = cb0; j0 < cb1; j0 += 128) {
@@ -349,7 +383,7 @@ __device__ __forceinline__ void ustage_issue(const FusedPcgArgs& a, const UStage
 // and rows grp, grp + ngrp, ... of every chunk; the ngrp row groups are combined at the end
 // through the head of shared memory.  Leaves the last two chunks in their buffers.
 constexpr int kUQ = 2;             // k quads per thread: ell <= kUQ * 4 * kT
-__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, int ncol, Smem& sm,
+__device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int gb, int64_t cb0, int ncol, Smem& sm,
                                             unsigned char* dsm) {
   const UStage st = ustage(a, dsm, ncol);
   const int nk4 = a.ldu / 4;
@@ -407,7 +441,7 @@ __device__ __forceinline__ void utr_partial(const FusedPcgArgs& a, int64_t cb0, 
           const int k = 4 * k4 + e;
           DF s = acc[q][e];
           for (int g2 = 1; g2 < ngrp; ++g2) s = df_add(s, scr[((g2 - 1) * nthr + t) * 4 + e]);
-          if (k < a.ell) __stcg(a.w1p + (int64_t)blockIdx.x * a.ell + k, make_float2(s.hi, s.lo));
+          if (k < a.ell) __stcg(a.w1p + (int64_t)gb * a.ell + k, make_float2(s.hi, s.lo));
         }
       }
     }
@@ -471,22 +505,22 @@ __device__ __forceinline__ double precond_rows(const FusedPcgArgs& a, int64_t cb
 }
 
 template <int CG, int S>
-__global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
+__device__ __forceinline__ void pcg_body(const FusedPcgArgs& a, const int gb, const int gG) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
   float4* ring = reinterpret_cast<float4*>(dsm);
   float2* w2s = reinterpret_cast<float2*>(dsm);          // phase E only (aliases the ring)
   DF* scr = reinterpret_cast<DF*>(dsm);                  // phase B only (aliases the ring)
   __shared__ Smem sm;
-  const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, G = gG, b = gb;
   const double mu = a.mu_d ? *a.mu_d : a.mu_h;
 
   if (a.mode == 1) {                                     // q = (G + mu I) v, v = a.pv
-    split_slice(a, a.pv);
-    grid.sync();
-    gv_rows<CG, S>(a, ring, sm);
-    grid.sync();
-    gv_finish(a, a.pv, mu, a.q, scr);
+    split_slice(a, gb, gG, a.pv);
+    gsync(a, gG, grid);
+    gv_rows<CG, S>(a, gb, gG, ring, sm);
+    gsync(a, gG, grid);
+    gv_finish(a, gb, gG, a.pv, mu, a.q, scr);
     return;
   }
 
@@ -517,15 +551,16 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   }
   rr = block_allsum(rr, sm.dred);
   if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
-  if (pre) utr_partial(a, cb0, ncol, sm, dsm);
-  grid.sync();
+  if (pre) utr_partial(a, gb, cb0, ncol, sm, dsm);
+  gsync(a, gG, grid);
 
   int it = 0, status = 0;
   double gn2 = 0.0, rn2 = 0.0, rz = 0.0, alpha = 0.0, beta = 0.0, pq = 0.0;
   for (;;) {
     // D: convergence test; finish U^T r and scale it
-    rn2 = grid_total(a.red, 1, sm.dred);
+    rn2 = grid_total(a.red, 1, sm.dred, G);
     bool done;
+    if (a.bar && (*(volatile int*)&sc->status & kStatTimeout)) break;   // a group barrier gave up
     if (it == 0) {
       gn2 = rn2;
       done = rn2 == 0.0 || maxit <= 0;
@@ -554,7 +589,7 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
           __stcg(a.w2 + k, make_float2(h, l));
         }
       }
-      grid.sync();
+      gsync(a, gG, grid);
     }
     // E: z = P^{-1} r on the j slice, r . z
     double rzp = 0.0;
@@ -571,10 +606,10 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     }
     rzp = block_allsum(rzp, sm.dred);
     if (tid == 0) __stcg(a.red + b * 4 + 2, rzp);
-    grid.sync();
+    gsync(a, gG, grid);
     // F: beta, new direction
     {
-      const double rz_new = grid_total(a.red, 2, sm.dred);
+      const double rz_new = grid_total(a.red, 2, sm.dred, G);
       beta = it == 0 ? 0.0 : rz_new / rz;
       for (int jj = tid; jj < ncol; jj += kT) {
         const int64_t j = cb0 + jj;
@@ -587,18 +622,18 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
       }
       rz = rz_new;
     }
-    grid.sync();
+    gsync(a, gG, grid);
     // A, B: q = (G + mu I) p, p . q
-    gv_rows<CG, S>(a, ring, sm);
-    grid.sync();
+    gv_rows<CG, S>(a, gb, gG, ring, sm);
+    gsync(a, gG, grid);
     {
-      double pqp = gv_finish(a, a.pv, mu, a.q, scr);
+      double pqp = gv_finish(a, gb, gG, a.pv, mu, a.q, scr);
       pqp = block_allsum(pqp, sm.dred);
       if (tid == 0) __stcg(a.red + b * 4 + 0, pqp);
     }
-    grid.sync();
+    gsync(a, gG, grid);
     // C: alpha, x and r, ||r||^2, U^T r
-    pq = grid_total(a.red, 0, sm.dred);
+    pq = grid_total(a.red, 0, sm.dred, G);
     if (!(pq > 0.0) || !isfinite(pq)) {
       status |= isfinite(pq) ? kStatBreakdown : kStatNonFinite;
       break;
@@ -618,9 +653,9 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
     }
     rr = block_allsum(rr, sm.dred);
     if (tid == 0) __stcg(a.red + b * 4 + 1, rr);
-    if (pre) utr_partial(a, cb0, ncol, sm, dsm);
+    if (pre) utr_partial(a, gb, cb0, ncol, sm, dsm);
     ++it;
-    grid.sync();
+    gsync(a, gG, grid);
   }
   if (b == 0 && tid == 0) {
     sc->gn2 = gn2;
@@ -636,6 +671,22 @@ __global__ void __launch_bounds__(kT, 1) k_pcg_fused(FusedPcgArgs a) {
   }
 }
 
+template <int CG, int S>
+__global__ void __launch_bounds__(kT, 1) k_pcg_fused(const FusedPcgArgs a) {
+  pcg_body<CG, S>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Many independent solves in one cooperative launch: problem j owns the blocks
+// [tab[j].gb0, tab[j].gb0 + tab[j].gG) (groups in increasing gb0 order) and synchronises them
+// with its own barrier counter.
+template <int CG, int S>
+__global__ void __launch_bounds__(kT, 1) k_pcg_fused_multi(const FusedPcgArgs* __restrict__ tab, int nprob) {
+  int j = 0;
+  while (j + 1 < nprob && (int)blockIdx.x >= tab[j + 1].gb0) ++j;
+  const FusedPcgArgs& a = tab[j];
+  pcg_body<CG, S>(a, (int)blockIdx.x - a.gb0, a.gG);
+}
+
 constexpr int kMaxCG = 12;       // slots per group thread: p <= 4 * kGT * kMaxCG = 9216
 constexpr int kSmemBudget = 210 * 1024;
 
@@ -645,11 +696,15 @@ constexpr int stages_for() {
   return std::min(kMaxStages, kSmemBudget / (CG * kGT * 16));
 }
 
+// Launch of the fused solve with CG slots per group thread: one problem on G blocks (tab null),
+// or nprob problems from the device table tab on G blocks in all.
 template <int CG>
-cudaError_t launch_cg(const FusedPcgArgs& a, int G, cudaStream_t s) {
+cudaError_t launch_cg(const FusedPcgArgs& a, int G, cudaStream_t s, const FusedPcgArgs* tab = nullptr,
+                      int nprob = 0) {
   constexpr int S = stages_for<CG>();
   static_assert(S >= 3, "shared-memory ring too small");
   auto kern = k_pcg_fused<CG, S>;
+  auto kern_multi = k_pcg_fused_multi<CG, S>;
   // dynamic shared memory: the whole budget (one block per SM in any case), shared by the ring of
   // phase A and the head plus the two U buffers of phases C and E (16 KB + 2 rows of U at least)
   constexpr size_t smem = kSmemBudget;
@@ -664,15 +719,24 @@ cudaError_t launch_cg(const FusedPcgArgs& a, int G, cudaStream_t s) {
     if (configured_dev != dev) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(kern_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem);
       if (e != cudaSuccess) return e;
       configured_dev = dev;
     }
   }
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  FusedPcgArgs args = a;
-  void* params[] = {&args};
-  e = cudaLaunchCooperativeKernel((const void*)kern, G, kT, params, smem, s);
+  if (tab) {
+    const FusedPcgArgs* t = tab;
+    int n = nprob;
+    void* params[] = {&t, &n};
+    e = cudaLaunchCooperativeKernel((const void*)kern_multi, G, kT, params, smem, s);
+  } else {
+    FusedPcgArgs args = a;
+    void* params[] = {&args};
+    e = cudaLaunchCooperativeKernel((const void*)kern, G, kT, params, smem, s);
+  }
   note_launch();
   return e;
 }
@@ -691,24 +755,54 @@ int num_sms() {
 
 int fused_pcg_blocks() { return std::min(num_sms(), kT); }
 
+int fused_pcg_slots(int64_t ldJ) { return (int)((ldJ / 4 + kGT - 1) / kGT); }
+
+bool fused_pcg_supported_on(int64_t p, int64_t ldJ, int ell, int G) {
+  const int64_t cg = fused_pcg_slots(ldJ);
+  return G >= 1 && G <= kT && ldJ % 4 == 0 && cg >= 1 && cg <= kMaxCG &&
+         4 * (((p + 3) / 4 + G - 1) / G) <= kMaxSlice && ell >= 0 && ell <= 2048 && ell <= kMaxKSlice * G;
+}
+
 bool fused_pcg_supported(int64_t p, int64_t ldJ, int ell) {
-  const int G = fused_pcg_blocks();
-  const int64_t cg = (ldJ / 4 + kGT - 1) / kGT;
-  return G >= 1 && ldJ % 4 == 0 && cg >= 1 && cg <= kMaxCG && 4 * (((p + 3) / 4 + G - 1) / G) <= kMaxSlice &&
-         ell >= 0 && ell <= 2048 && ell <= kMaxKSlice * G;
+  return fused_pcg_supported_on(p, ldJ, ell, fused_pcg_blocks());
+}
+
+int fused_pcg_min_blocks(int64_t p, int ell) {
+  const int64_t by_p = ((p + 3) / 4 + kMaxSlice / 4 - 1) / (kMaxSlice / 4);
+  const int64_t by_ell = (ell + kMaxKSlice - 1) / kMaxKSlice;
+  return (int)std::max<int64_t>(1, std::max(by_p, by_ell));
+}
+
+static cudaError_t launch_by_slots(const FusedPcgArgs& a, int G, cudaStream_t s, const FusedPcgArgs* tab, int nprob) {
+  switch ((fused_pcg_slots(a.ldJ) + 1) / 2) {     // slots per group thread, rounded up to even
+    case 1: return launch_cg<2>(a, G, s, tab, nprob);
+    case 2: return launch_cg<4>(a, G, s, tab, nprob);
+    case 3: return launch_cg<6>(a, G, s, tab, nprob);
+    case 4: return launch_cg<8>(a, G, s, tab, nprob);
+    case 5: return launch_cg<10>(a, G, s, tab, nprob);
+    default: return launch_cg<12>(a, G, s, tab, nprob);
+  }
 }
 
 cudaError_t launch_pcg_fused(const FusedPcgArgs& a, cudaStream_t s) {
   if (!fused_pcg_supported(a.p, a.ldJ, a.ell)) return cudaErrorInvalidValue;
-  const int G = fused_pcg_blocks();
-  switch (((a.ldJ / 4 + kGT - 1) / kGT + 1) / 2) {     // slots per group thread, rounded up to even
-    case 1: return launch_cg<2>(a, G, s);
-    case 2: return launch_cg<4>(a, G, s);
-    case 3: return launch_cg<6>(a, G, s);
-    case 4: return launch_cg<8>(a, G, s);
-    case 5: return launch_cg<10>(a, G, s);
-    default: return launch_cg<12>(a, G, s);
+  return launch_by_slots(a, fused_pcg_blocks(), s, nullptr, 0);
+}
+
+cudaError_t launch_pcg_fused_multi(const FusedPcgArgs* tab_dev, const FusedPcgArgs* tab_host, int nprob,
+                                   cudaStream_t s) {
+  if (nprob < 1) return cudaErrorInvalidValue;
+  const int slots = (fused_pcg_slots(tab_host[0].ldJ) + 1) / 2;
+  int G = 0;
+  for (int j = 0; j < nprob; ++j) {
+    const FusedPcgArgs& a = tab_host[j];
+    if (a.gb0 != G || (fused_pcg_slots(a.ldJ) + 1) / 2 != slots || !a.bar ||
+        !fused_pcg_supported_on(a.p, a.ldJ, a.ell, a.gG))
+      return cudaErrorInvalidValue;
+    G += a.gG;
   }
+  if (G > fused_pcg_blocks()) return cudaErrorInvalidValue;
+  return launch_by_slots(tab_host[0], G, s, tab_dev, nprob);
 }
 
 // U (column-major, leading dimension ldu, p x ell, float or double) -> Uh + Ul in j-major order

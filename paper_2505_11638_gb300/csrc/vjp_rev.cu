@@ -121,6 +121,64 @@ __global__ void k_rev_tanh(NetDesc net, int lh, const T* __restrict__ tape, int6
   }
 }
 
+// Forward tangents through tanh of hidden layer lh (width nh): from the tangent adot of the
+// pre-activation channels (the bias tangent bdot added to the value channel) and the stored
+// coefficients, the tangent xdot of the layer's output channels:
+//   xdot        = s1 adot
+//   grad_k xdot = s1 grad_k adot + s2 adot grad_k a
+//   Delta xdot  = s1 Delta adot + s2 (adot Delta a + 2 sum_k spatial grad_k a grad_k adot) + s3 adot q
+template <typename T>
+__global__ void k_fwd_tangent(NetDesc net, int lh, const T* __restrict__ tape, int64_t toff, int64_t row0,
+                              int64_t npts, const T* __restrict__ Ad, const T* __restrict__ bdot,
+                              T* __restrict__ Xd, int ldb) {
+  const int C = net.C, d = net.d, nh = net.width[lh + 1];
+  const int64_t total = npts * nh;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += st) {
+    const int64_t pt = e / nh;
+    const int j = (int)(e - pt * nh);
+    const T* tp = tape + (row0 + pt) * net.tape_per_point + toff + j;
+    const T t = tp[0];
+    const T s1 = T(1) - t * t, s2 = T(-2) * t * s1, s3 = T(-2) * s1 * (T(1) - T(3) * t * t);
+    const T* ad = Ad + pt * C * ldb + j;
+    const T a0 = ad[0] + bdot[j];
+    T qs = T(0), qd = T(0);
+    T* xd = Xd + pt * C * ldb + j;
+    for (int k = 0; k < d; ++k) {
+      const T ga = tp[(int64_t)(1 + k) * nh];
+      const T gad = ad[(int64_t)(1 + k) * ldb];
+      if (spatial(net, k)) {
+        qs += ga * ga;
+        qd += ga * gad;
+      }
+      xd[(int64_t)(1 + k) * ldb] = s1 * gad + s2 * a0 * ga;
+    }
+    const T la = tp[(int64_t)(d + 1) * nh];
+    xd[0] = s1 * a0;
+    xd[(int64_t)(d + 1) * ldb] = s1 * ad[(int64_t)(d + 1) * ldb] + s2 * (a0 * la + T(2) * qd) + s3 * a0 * qs;
+  }
+}
+
+// J v of each point from the tangents of the output channels (the output bias tangent added to
+// the value channel): the residual's coefficients in (u, grad u, Delta u).
+template <typename T>
+__global__ void k_jvp_out(NetDesc net, PointSet ps, int64_t row0, int64_t npts, const T* __restrict__ Ad,
+                          const T* __restrict__ bdot, int ldb, double* __restrict__ out) {
+  const int C = net.C, d = net.d;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pt < npts; pt += st) {
+    const T* ad = Ad + pt * C * ldb;
+    const int64_t row = row0 + pt;
+    double v;
+    if (row < ps.n_int)
+      v = net.pde == NGD_PDE_HEAT ? (double)ad[ldb] - net.kappa * (double)ad[(int64_t)(d + 1) * ldb]
+                                  : (double)ad[(int64_t)(d + 1) * ldb];
+    else
+      v = (double)ad[0] + (double)bdot[0];
+    out[row] = v;
+  }
+}
+
 // out[i] (+)= sum over the nz K-slice partials part[z * stride + i], in slice order.
 __global__ void k_rev_sum(const double* __restrict__ part, int nz, int64_t stride, int64_t n, double* __restrict__ out,
                           int accumulate) {
@@ -154,6 +212,28 @@ void launch_rev_tanh(const NetDesc& net, int lh, const T* tape, int64_t toff, in
   k_rev_tanh<T><<<grid_for(npts * net.width[lh + 1]), 256, 0, s>>>(net, lh, tape, toff, row0, npts, Xb, A, ldb);
   note_launch();
 }
+template <typename T>
+void launch_fwd_tangent(const NetDesc& net, int lh, const T* tape, int64_t toff, int64_t row0, int64_t npts,
+                        const T* Ad, const T* bdot, T* Xd, int ldb, cudaStream_t s) {
+  k_fwd_tangent<T><<<grid_for(npts * net.width[lh + 1]), 256, 0, s>>>(net, lh, tape, toff, row0, npts, Ad, bdot, Xd,
+                                                                       ldb);
+  note_launch();
+}
+template <typename T>
+void launch_jvp_out(const NetDesc& net, const PointSet& ps, int64_t row0, int64_t npts, const T* Ad, const T* bdot,
+                    int ldb, double* out, cudaStream_t s) {
+  k_jvp_out<T><<<grid_for(npts), 256, 0, s>>>(net, ps, row0, npts, Ad, bdot, ldb, out);
+  note_launch();
+}
+template void launch_fwd_tangent<float>(const NetDesc&, int, const float*, int64_t, int64_t, int64_t, const float*,
+                                        const float*, float*, int, cudaStream_t);
+template void launch_fwd_tangent<double>(const NetDesc&, int, const double*, int64_t, int64_t, int64_t, const double*,
+                                         const double*, double*, int, cudaStream_t);
+template void launch_jvp_out<float>(const NetDesc&, const PointSet&, int64_t, int64_t, const float*, const float*, int,
+                                    double*, cudaStream_t);
+template void launch_jvp_out<double>(const NetDesc&, const PointSet&, int64_t, int64_t, const double*, const double*,
+                                     int, double*, cudaStream_t);
+
 void launch_rev_sum(const double* part, int nz, int64_t stride, int64_t n, double* out, int accumulate,
                     cudaStream_t s) {
   k_rev_sum<<<grid_for(n), 256, 0, s>>>(part, nz, stride, n, out, accumulate);

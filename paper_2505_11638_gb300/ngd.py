@@ -106,6 +106,9 @@ _SIGS = {
     "ngd_batch_context": ([_P, _I], _P),
     "ngd_batch_last_error": ([_P], ctypes.c_char_p),
     "ngd_batch_step": ([_P, _P, ctypes.POINTER(StepOpts), _P], _I),
+    "ngd_batch_set_packing": ([_P, _I], _I),
+    "ngd_batch_packing": ([_P], _I),
+    "ngd_batch_solve_launches": ([_P], _I),
 }
 
 
@@ -498,6 +501,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_packing(self, solves_per_launch: int):
+        """Solves per cooperative launch (0: tune on the next step, 1: one per launch)."""
+        st = lib().ngd_batch_set_packing(self.handle, int(solves_per_launch))
+        if st != NGD_OK:
+            raise NGDError(st, "ngd_batch_set_packing")
+
+    @property
+    def packing(self) -> int:
+        return int(lib().ngd_batch_packing(self.handle))
+
+    @property
+    def solve_launches(self) -> int:
+        return int(lib().ngd_batch_solve_launches(self.handle))
 
     def step(self, thetas, **kw):
         """thetas: list of float64 device tensors (one per problem), updated in place."""

@@ -400,21 +400,30 @@ def test_ngd_step_matches_oracle_fp64(ngd):
     ctx.close()
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_batch_step_matches_oracle(ngd, dtype):
+@pytest.mark.parametrize("dtype,packing", [("f64", None), ("f32", 1), ("f32", 2), ("f32", 0)])
+def test_batch_step_matches_oracle(ngd, dtype, packing):
     """Batching form: problems of uneven sizes (and different source frequencies) stepped by one
     ngd_batch_step; problem i uses Philox key seed + i.  Each problem's step matches the oracle's
-    step on that problem (FP64: to the PCG direction tolerance; FP32: the FP64-accurate sketch)."""
+    step on that problem (FP64: to the PCG direction tolerance; FP32: the FP64-accurate sketch).
+    FP32 solves run one per launch (packing 1), two per cooperative launch on block groups of
+    their own (packing 2: two launches for three problems), or with the packing tuned on the
+    step (packing 0)."""
     probs, thetas = [], []
     for i, (n_int, n_bnd, k) in enumerate([(600, 150, 1.0), (1100, 275, 3.0), (350, 87, 2.0)]):
         pr, th = inputs.small_problem(d=3, widths=[3, 24, 24, 1], n_int=n_int, n_bnd=n_bnd, seed=40 + i, freq=k)
         probs.append(pr)
         thetas.append(th)
     batch = ngd.Batch(probs, dtype=dtype)
+    if packing is not None:
+        batch.set_packing(packing)
     ts = [dev(th) for th in thetas]
     ell, mu, rtol = 60, 1e-6, (1e-10 if dtype == "f64" else 1e-7)
     infos = batch.step(ts, ell=ell, mu=mu, rtol=rtol, maxit=2000, seed=7, step=3, sketch="f64")
     assert len(infos) == 3
+    if packing == 2:
+        assert batch.solve_launches == 2 and batch.packing == 2
+    if packing == 0:
+        assert batch.packing in (1, 2, 4, 8)          # tuned on this step
     for i, (pr, th, info) in enumerate(zip(probs, thetas, infos)):
         th1_o, info_o = solve.ngd_step(pr, th, ell=ell, mu=mu, rtol=0.0, maxit=info["pcg_iters"], seed=7 + i, step=3)
         assert info["relres"] <= rtol, i

@@ -272,12 +272,15 @@ def test_test_matrix_single_cholesky_qr_pass(ngd, dtype, tol):
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 5e-5)])
 def test_matrix_free_vjp_heat_width_256(ngd, dtype, tol):
     """The matrix-free VJP (reverse of the Taylor-mode forward by layers: per-layer weight adjoints
-    as GEMMs over points and channels, no Jacobian rows) on the 4-D heat network (widths 256, p =
-    133121) at 300 interior + 100 boundary/initial points, with the stored Taylor coefficients
-    (budget 0) and with a one-byte budget (the forward recomputed per chunk of points), through the
-    autograd function and through ngd_vjp, against the oracle's VJP; the matrix-free Gramian matvec
-    (JVP then this VJP) against the oracle's explicit Jacobian."""
+    as GEMMs over points and channels, no Jacobian rows) on the 4-D heat network at 300 interior +
+    100 boundary/initial points: FP32 with the workload's widths 256 (p = 133121), FP64 with widths
+    64 (the FP64 Taylor kernels stage fewer points of a 256-wide network than they need).  With the
+    stored Taylor coefficients (budget 0) and with a one-byte budget (the forward recomputed per
+    chunk of points), through the autograd function and through ngd_vjp, against the oracle's VJP;
+    the matrix-free Gramian matvec (JVP then this VJP) against the oracle's explicit Jacobian."""
     wl, pr, th = workload("heat4d", 300, 100)
+    if dtype == "f64":
+        pr, th = inputs.small_problem(pde="heat", d=4, widths=[4, 64, 64, 64, 1], n_int=300, n_bnd=100, seed=33)
     J = mlp.jacobian(pr, th)
     rng = np.random.default_rng(31)
     c = rng.standard_normal(pr.n)
