@@ -351,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2: the FP32 Jacobian streamed by every matvec is 176 MB"},
             "gramian_mv_per_s": 1e3 / gv_ms * world,
             "pcg_iters_mean": float(np.mean([i["pcg_iters"] for i in infos])),
+            "shift_retries_total": int(sum(i["shift_retries"] for i in infos)),
             "loss_first_last": [infos[0]["loss_before"], infos[-1]["loss_after"]],
             "phases_ms": phases,
             "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": pr.p * 8,
@@ -431,6 +432,7 @@ def run_batch(args, rank, world, local_rank):
                        "sketch": args.sketch},
             "pcg_iters_mean": float(np.mean(iters)), "pcg_iters_max": int(np.max(iters)),
             "solves_per_launch": batch.packing, "solve_launches_per_step": batch.solve_launches,
+            "shift_retries_total": int(sum(i["shift_retries"] for step in infos for i in step)),
             "gpu_launches": int(launches), "gpu_launches_per_step": int(launches) / args.steps, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -441,10 +443,14 @@ def run_batch(args, rank, world, local_rank):
 
 
 def run_precision_study(args, rank):
-    """Precision form (10-D Poisson, p = 51073, N = 20480, ell = 1000): the same NGD steps from
-    the same theta0 with the sketch and factor in FP64 (FP64 context), FP64-accurate double-float
-    (FP32 context), TF32 and BF16 (tcgen05, FP32 accumulation); PCG iterations, time per step,
-    loss and relative L2 error of u_theta on 4096 independent points."""
+    """Precision form (10-D Poisson, p = 51073, N = 20480, ell = 1000): the same NGD steps from the
+    same theta0 with the sketch in FP64 (FP64 context), FP64-accurate on the tensor cores (digit
+    planes of the FP32 Jacobian), FP64-accurate double-float (FP32 pipes), TF32 and BF16 (tcgen05,
+    rounded operands, FP32 accumulation).  Damping of Sec. 5, mu = max(gamma eps lambda_1,
+    1e-4 L^2), so that every form can reach the common PCG tolerance rtol = 1e-6 (maxit 3000).
+    Reported per form: time per step and per phase, PCG iterations and final residuals, loss,
+    relative L2 error of u_theta on 4096 independent points, and the sketch product Y = G V alone
+    (ngd_gramian_mm on a fixed V at the final theta, CUDA events): its time and rate."""
     import torch
     from paper_2505_11638_gb300 import build, inputs, ngd
 
@@ -459,8 +465,10 @@ def run_precision_study(args, rank):
                         target=ue, n_int=0, n_bnd=len(xe), freq=pr.freq)
     peaks = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops", 1881.0)
-    sketch_flop = 4.0 * pr.n * pr.p * wl.ell
-    forms = [("fp64", "f64", "f64"), ("double-float", "f32", "f64"), ("tf32", "f32", "tf32"), ("bf16", "f32", "bf16")]
+    prod_flop = 4.0 * pr.n * pr.p * wl.ell           # the two products of the sketch, as FP64-accurate work
+    forms = [("fp64", "f64", "f64"), ("fp64-accurate tensor cores", "f32", "f64"), ("double-float", "f32", "df"),
+             ("tf32", "f32", "tf32"), ("bf16", "f32", "bf16")]
+    stream = torch.cuda.current_stream()
     out = {}
     for name, dtype, sketch in forms:
         ctx = ngd.Context(pr, dtype=dtype)
@@ -469,34 +477,97 @@ def run_precision_study(args, rank):
         infos = []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        e0.record()
+        e0.record(stream)
         for k in range(args.steps):
-            infos.append(ctx.step(theta, ell=wl.ell, mu=None, rtol=wl.rtol, maxit=500, seed=0, step=k, sketch=sketch))
-        e1.record()
+            infos.append(ctx.step(theta, ell=wl.ell, mu=None, mu_loss_coef=1e-4, rtol=1e-6, maxit=3000, seed=0,
+                                  step=k, sketch=sketch))
+        e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         r, _ = ectx.residual(theta)
         l2 = float(torch.linalg.norm(r).item() / np.linalg.norm(ue))
-        ms_sketch = float(np.mean([i["ms_sketch"] for i in infos]))
+        # the sketch product alone on a fixed V
+        wd = torch.float64 if dtype == "f64" else torch.float32
+        V = torch.randn(wl.ell, pr.p, generator=torch.Generator(device="cuda").manual_seed(5), device="cuda",
+                        dtype=torch.float64).to(wd)
+        ctx.gramian_mm(theta, V, sketch)               # linearize; digit planes of J made
+        reps = 1 if dtype == "f64" else 3
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.gramian_mm(None, V, sketch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_prod = e0.elapsed_time(e1) / reps
         entry = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "pcg_iters": [i["pcg_iters"] for i in infos],
-                 "relres": [i["relres"] for i in infos], "loss": infos[-1]["loss_after"], "rel_l2_error": l2,
-                 "ms_sketch": ms_sketch, "ms_factor": float(np.mean([i["ms_factor"] for i in infos])),
+                 "relres": [i["relres"] for i in infos], "shift_retries": [i["shift_retries"] for i in infos],
+                 "mu": [i["mu"] for i in infos], "loss": infos[-1]["loss_after"], "rel_l2_error": l2,
+                 "ms_sketch": float(np.mean([i["ms_sketch"] for i in infos])),
+                 "ms_factor": float(np.mean([i["ms_factor"] for i in infos])),
                  "ms_pcg": float(np.mean([i["ms_pcg"] for i in infos])),
-                 "sketch_tflops": sketch_flop / (ms_sketch * 1e-3) / 1e12}
+                 "ms_product": ms_prod, "product_tflops": prod_flop / (ms_prod * 1e-3) / 1e12}
         if sketch in ("tf32", "bf16"):
             peak = bf16_peak * (0.5 if sketch == "tf32" else 1.0)
-            entry["sketch_roofline"] = {"bound": "tensor", "achieved": entry["sketch_tflops"], "peak": peak,
-                                        "unit": "TFLOP/s", "frac": entry["sketch_tflops"] / peak,
-                                        "note": "time includes the test matrix and its CholeskyQR2"}
+            entry["product_roofline"] = {"bound": "tensor", "achieved": entry["product_tflops"], "peak": peak,
+                                         "unit": "TFLOP/s", "frac": entry["product_tflops"] / peak,
+                                         "peak_source": "measured BF16 (x 1/2 for TF32, nominal ratio)",
+                                         "note": "includes the operand copies (transpose, BF16 rounding)"}
         out[name] = entry
         ctx.close()
         ectx.close()
-        del theta
+        del theta, V
         torch.cuda.empty_cache()
     line = {"metric": "precision form: NGD steps/s, PCG iterations and L2 error per sketch precision",
-            "config": {"workload": "poisson10d", "N": pr.n, "p": pr.p, "ell": wl.ell, "mu": "rule",
-                       "rtol": wl.rtol, "steps": args.steps}, "data": "synthetic", "forms": out}
+            "config": {"workload": "poisson10d", "N": pr.n, "p": pr.p, "ell": wl.ell,
+                       "mu": "max(10 eps lambda_1, 1e-4 L^2) (Sec. 5)", "rtol": 1e-6, "maxit": 3000,
+                       "steps": args.steps}, "data": "synthetic", "forms": out}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sketch_product(args, rank):
+    """The sketch product Y = G V (ngd_gramian_mm) alone on the 5-D Poisson workload (N = 5000,
+    p = 8769, ell = 500, FP32 Jacobian) in the precision --sketch: --warmup products, then --steps
+    timed with CUDA events.  Rates: FP64-accurate work 4 N p ell flop per product, and for the
+    digit-plane form the BF16 tensor-core flops it issues (the kept digit-plane pairs of both
+    GEMMs on the padded tiles)."""
+    import torch
+    from paper_2505_11638_gb300 import build, ngd
+
+    if rank != 0:
+        return 0
+    build.build()
+    wl, pr, theta0 = make_problem()
+    ctx = ngd.Context(pr, dtype="f32")
+    theta = torch.tensor(theta0, device="cuda")
+    V = torch.randn(wl.ell, pr.p, generator=torch.Generator(device="cuda").manual_seed(5), device="cuda",
+                    dtype=torch.float32)
+    ctx.gramian_mm(theta, V, args.sketch)
+    for _ in range(args.warmup):
+        ctx.gramian_mm(None, V, args.sketch)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.gramian_mm(None, V, args.sketch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    flop = 4.0 * pr.n * pr.p * wl.ell
+    line = {"metric": "sketch product Y = G V per second", "value": 1e3 / ms, "unit": "products/s", "ms": ms,
+            "sketch": args.sketch, "fp64_accurate_tflops": flop / (ms * 1e-3) / 1e12,
+            "config": {"workload": WORKLOAD, "N": pr.n, "p": pr.p, "ell": wl.ell}}
+    if args.sketch == "f64":
+        ldj = (pr.p + 31) // 32 * 32
+        pairs1, pairs2 = 19, 20                          # kept digit-plane pairs of Z = J V and Y = J^T Z
+        m1, n1, k1 = -(-pr.n // 128) * 128, -(-wl.ell // 96) * 96, -(-ldj // 256) * 256
+        m2, k2 = -(-pr.p // 128) * 128, -(-(-(-pr.n // 32) * 32) // 256) * 256
+        issued = 2.0 * (pairs1 * m1 * n1 * k1 + pairs2 * m2 * n1 * k2)
+        line["tensor_tflops_issued"] = issued / (ms * 1e-3) / 1e12
+        line["tensor_peak_tflops"] = measured_peaks().get("bf16_tflops", 1881.0)
+    print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 
@@ -664,6 +735,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--test-matrix", default="gaussian", choices=["gaussian", "sampling"],
                     help="test matrix of the Nystrom sketch in --train (sampling: columns drawn proportionally "
                          "to diag G)")
+    ap.add_argument("--sketch-product", action="store_true",
+                    help="time the sketch product Y = G V alone on the bench workload (--sketch precision)")
     ap.add_argument("--matvec-study", action="store_true",
                     help="Gramian matvecs/s on the 5-D Poisson, 10-D Poisson and 4-D heat workloads, J stored "
                          "or matrix-free, --steps products each")
@@ -682,6 +755,8 @@ def main():
         return run_precision_study(args, rank)
     if args.matvec_study:
         return run_matvec_study(args, rank)
+    if args.sketch_product:
+        return run_sketch_product(args, rank)
     if args.train:
         return run_train(args, rank)
     if args.workload == "batch64":

@@ -2131,30 +2131,23 @@ ngd_status batch_fail(ngd_batch* b, int i, ngd_status st) {
   return st;
 }
 
-// The pCG solves of the problems in `solve` (stage 2 of a batch step), packed b->pack (or the
-// candidate being tuned) to a cooperative launch.
-ngd_status batch_solves(ngd_batch* b, const std::vector<int>& solve, std::vector<StepState>& st,
-                        const ngd_step_opts* o) {
+// Packed launches for the solves `idxs` (in order), up to `want` solves per launch; table slots
+// and barrier counters from *slot on.
+ngd_status batch_launch(ngd_batch* b, const std::vector<int>& idxs, int want, std::vector<StepState>& st,
+                        const ngd_step_opts* o, int* slot, int* launches) {
   ngd_ctx* ctx = b->ctx[0];            // CUDA failures of the shared stream are reported on problem 0
   const int G = fused_pcg_blocks();
   cudaStream_t s = ctx->stream;
-  // order: longest previous solves first, so that a launch holds solves of similar length
-  std::vector<int> order(solve);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->last_iters[x] > b->last_iters[y]; });
-  const bool tuning = b->pack == 0;
   size_t pos = 0;
-  int cand = 0, launches = 0, slot = 0;
-  while (pos < order.size()) {
-    const int want = tuning ? b->tune_candidates[(size_t)cand % b->tune_candidates.size()] : b->pack;
-    // take up to `want` solves whose minima fit G together
+  while (pos < idxs.size()) {
+    // take up to `want` solves whose minimum block groups fit the GPU together
     std::vector<int> idx, gmin, groups;
-    while (pos < order.size() && (int)idx.size() < want) {
-      const int i = order[pos];
+    while (pos < idxs.size() && (int)idx.size() < want) {
+      const int i = idxs[pos];
       ngd_ctx* c = b->ctx[(size_t)i];
       const int gm = fused_pcg_min_blocks(c->p, st[(size_t)i].ell_pc);
-      std::vector<int> trial(idx);
+      std::vector<int> trial(idx), tmin(gmin);
       trial.push_back(i);
-      std::vector<int> tmin(gmin);
       tmin.push_back(gm);
       if (!split_blocks(trial, b->ctx, tmin, G, groups)) break;
       idx.push_back(i);
@@ -2163,8 +2156,6 @@ ngd_status batch_solves(ngd_batch* b, const std::vector<int>& solve, std::vector
     }
     if (idx.empty()) return NGD_ERR_UNSUPPORTED;          // cannot happen: one solve takes all blocks
     split_blocks(idx, b->ctx, gmin, G, groups);
-    const bool timed = tuning;
-    if (timed) cudaEventRecord(b->ev[0], s);
     int gb0 = 0;
     for (size_t k = 0; k < idx.size(); ++k) {
       const int i = idx[k];
@@ -2177,38 +2168,65 @@ ngd_status batch_solves(ngd_batch* b, const std::vector<int>& solve, std::vector
         return set_err(c, NGD_ERR_UNSUPPORTED, "fused solve unavailable in the batch%s");
       fa.gb0 = gb0;
       fa.gG = groups[k];
-      fa.bar = b->bars + (size_t)(slot + (int)k) * 32;
-      b->tab_host[slot + (int)k] = fa;
+      fa.bar = b->bars + (size_t)(*slot + (int)k) * 32;
+      b->tab_host[*slot + (int)k] = fa;
       gb0 += groups[k];
     }
     const int m = (int)idx.size();
-    if (cudaMemsetAsync(b->bars + (size_t)slot * 32, 0, (size_t)m * 32 * sizeof(unsigned), s) != cudaSuccess ||
-        cudaMemcpyAsync(b->tab_dev + slot, b->tab_host + slot, (size_t)m * sizeof(FusedPcgArgs),
+    if (cudaMemsetAsync(b->bars + (size_t)*slot * 32, 0, (size_t)m * 32 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemcpyAsync(b->tab_dev + *slot, b->tab_host + *slot, (size_t)m * sizeof(FusedPcgArgs),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
       return batch_fail(b, idx[0], set_err(b->ctx[(size_t)idx[0]], NGD_ERR_CUDA, "batch solve table%s"));
-    const cudaError_t e = launch_pcg_fused_multi(b->tab_dev + slot, b->tab_host + slot, m, s);
+    const cudaError_t e = launch_pcg_fused_multi(b->tab_dev + *slot, b->tab_host + *slot, m, s);
     if (e != cudaSuccess)
       return batch_fail(b, idx[0], set_err(b->ctx[(size_t)idx[0]], NGD_ERR_CUDA, "multi-problem solve: %s",
                                            cudaGetErrorString(e)));
-    ++launches;
-    slot += m;
-    if (timed) {
-      cudaEventRecord(b->ev[1], s);
-      for (int i : idx) {
-        ngd_ctx* c = b->ctx[(size_t)i];
-        CK(cudaMemcpyAsync(c->h_pcg, c->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    ++*launches;
+    *slot += m;
+  }
+  return NGD_OK;
+}
+
+// The pCG solves of the problems in `solve` (stage 2 of a batch step), packed b->pack to a
+// cooperative launch.  Untuned, the step first gives every candidate packing the same number of
+// solves (consecutive ones in the order below), times them as a whole, and keeps the candidate with
+// the least time per pCG iteration for the remaining solves and the later steps.
+ngd_status batch_solves(ngd_batch* b, const std::vector<int>& solve, std::vector<StepState>& st,
+                        const ngd_step_opts* o) {
+  ngd_ctx* ctx = b->ctx[0];
+  cudaStream_t s = ctx->stream;
+  // order: longest previous solves first, so that a launch holds solves of similar length
+  std::vector<int> order(solve);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->last_iters[x] > b->last_iters[y]; });
+  int slot = 0, launches = 0;
+  size_t pos = 0;
+  if (b->pack == 0) {
+    const size_t nc = b->tune_candidates.size();
+    const size_t span = std::max<size_t>(1, std::min<size_t>(8, order.size() / nc));
+    for (size_t c = 0; c < nc && pos + span <= order.size(); ++c, pos += span) {
+      std::vector<int> seg(order.begin() + (long)pos, order.begin() + (long)(pos + span));
+      CK(cudaEventRecord(b->ev[0], s));
+      TRY(batch_launch(b, seg, b->tune_candidates[c], st, o, &slot, &launches));
+      CK(cudaEventRecord(b->ev[1], s));
+      for (int i : seg) {
+        ngd_ctx* c2 = b->ctx[(size_t)i];
+        CK(cudaMemcpyAsync(c2->h_pcg, c2->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
       }
       CK(cudaStreamSynchronize(s));
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
       long iters = 0;
-      for (int i : idx) iters += b->ctx[(size_t)i]->h_pcg->iters;
-      const size_t ci = (size_t)cand % b->tune_candidates.size();
-      if (iters > 0 && (b->tune_cost[ci] < 0.0 || ms / (double)iters < b->tune_cost[ci]))
-        b->tune_cost[ci] = ms / (double)iters;
-      ++cand;
+      for (int i : seg) iters += b->ctx[(size_t)i]->h_pcg->iters;
+      b->tune_cost[c] = iters > 0 ? ms / (double)iters : 1e30;
     }
+    size_t best = 0;
+    for (size_t k = 1; k < b->tune_cost.size(); ++k)
+      if (b->tune_cost[k] >= 0.0 && (b->tune_cost[best] < 0.0 || b->tune_cost[k] < b->tune_cost[best])) best = k;
+    b->pack = b->tune_candidates[best];
+    if (b->tune_cost[best] >= 0.0) tune_cache_put(b->tune_key, b->pack);
   }
+  std::vector<int> rest(order.begin() + (long)pos, order.end());
+  TRY(batch_launch(b, rest, b->pack, st, o, &slot, &launches));
   b->launches_last = launches;
   for (int i : solve) {
     ngd_ctx* c = b->ctx[(size_t)i];
@@ -2222,18 +2240,6 @@ ngd_status batch_solves(ngd_batch* b, const std::vector<int>& solve, std::vector
     if (r != NGD_OK) return batch_fail(b, i, r);
     CK(cudaEventRecord(c->ev[4], c->stream));
     b->last_iters[(size_t)i] = st[(size_t)i].iters;
-  }
-  if (tuning) {
-    // every candidate measured at least once: keep the cheapest per pCG iteration
-    bool all = true;
-    for (double v : b->tune_cost) all = all && v >= 0.0;
-    if (all) {
-      size_t best = 0;
-      for (size_t k = 1; k < b->tune_cost.size(); ++k)
-        if (b->tune_cost[k] < b->tune_cost[best]) best = k;
-      b->pack = b->tune_candidates[best];
-      tune_cache_put(b->tune_key, b->pack);
-    }
   }
   return NGD_OK;
 }
