@@ -348,6 +348,35 @@ int rev_splits(GemmArgs<T>& g) {
   return (int)std::max<int64_t>(1, (g.K + kps - 1) / kps);
 }
 
+// One layer product of the matrix-free J v / J^T c: FP32 contexts take the FP32 layer GEMM (K-slices
+// of FP32 sums, FP64 slice partials), FP64 contexts the FP64 SIMT GEMM.  With g.out64 requested
+// (reductions over points) the K-slice partials go to ctx->gpart and the slice count is returned;
+// otherwise the product goes to g.outT in one slice.
+template <typename T>
+ngd_status layer_gemm(ngd_ctx* ctx, GemmArgs<T> g, bool reduce, int* nz_out) {
+  int nz = 1;
+  if (std::is_same<T, float>::value) {
+    nz = reduce ? sgemm_layer_slices(g.M, g.N, g.K) : 1;
+    if (reduce) {
+      TRY(ensure_gpart(ctx, (size_t)nz * g.M * g.N));
+      g.out64 = ctx->gpart;
+      g.split_stride = g.M * g.N;
+      g.outT = nullptr;
+    }
+    launch_sgemm_layer(reinterpret_cast<const GemmArgs<float>&>(g), nz, ctx->stream);
+  } else {
+    if (reduce) {
+      nz = rev_splits(g);
+      TRY(ensure_gpart(ctx, (size_t)nz * g.M * g.N));
+      g.out64 = ctx->gpart;
+      g.split_stride = g.M * g.N;
+    }
+    launch_gemm<T>(g, ctx->stream);
+  }
+  if (nz_out) *nz_out = nz;
+  return NGD_OK;
+}
+
 // y = J^T c with J rows never formed: the reverse of the Taylor-mode forward by layers over chunks
 // of points (Thm. 1; Sec. 4.1.2), the weight adjoint of each layer one GEMM over the chunk's
 // points and channels, the input adjoint another.  The forward coefficients come from the stored
@@ -384,10 +413,8 @@ ngd_status vjp_reverse(ngd_ctx* ctx, const double* cot, double* out) {
       g.A = A; g.sam = 1; g.sak = ldb;
       g.B = X; g.sbk = ldb; g.sbn = 1;
       g.scm = n_in; g.scn = 1;
-      const int nz = rev_splits(g);
-      TRY(ensure_gpart(ctx, (size_t)nz * nW));
-      g.out64 = ctx->gpart; g.split_stride = nW;
-      launch_gemm<T>(g, ctx->stream);
+      int nz = 1;
+      TRY(layer_gemm<T>(ctx, g, true, &nz));
       launch_rev_sum(ctx->gpart, nz, nW, nW, out + net.theta_off[l], r0 > 0 ? 1 : 0, ctx->stream);
       // b_bar_l = sum over points of the value channel of abar_l
       GemmArgs<T> gb;
@@ -407,7 +434,7 @@ ngd_status vjp_reverse(ngd_ctx* ctx, const double* cot, double* out) {
       gx.A = A; gx.sam = ldb; gx.sak = 1;
       gx.B = prep + net.wr_off[l]; gx.sbk = n_in; gx.sbn = 1;
       gx.outT = Xb; gx.scm = ldb; gx.scn = 1;
-      launch_gemm<T>(gx, ctx->stream);
+      TRY(layer_gemm<T>(ctx, gx, false, nullptr));
       launch_rev_tanh<T>(net, l - 1, tape, toffs[l - 1], r0, nr, Xb, A, ldb, ctx->stream);
     }
   }
@@ -447,13 +474,13 @@ ngd_status jvp_layers(ngd_ctx* ctx, const T* prept, double* out) {
       g.A = X; g.sam = ldb; g.sak = 1;
       g.B = prept + net.wr_off[l]; g.sbk = 1; g.sbn = n_in;
       g.outT = A; g.scm = ldb; g.scn = 1;
-      launch_gemm<T>(g, ctx->stream);
+      TRY(layer_gemm<T>(ctx, g, false, nullptr));
       if (l >= 1) {
         GemmArgs<T> g2 = g;
         g2.A = Xd;
         g2.B = prep + net.wr_off[l];
         g2.accumulate = 1;
-        launch_gemm<T>(g2, ctx->stream);
+        TRY(layer_gemm<T>(ctx, g2, false, nullptr));
       }
       if (l < L - 1)
         launch_fwd_tangent<T>(net, l, tape, toffs[l], r0, nr, A, prept + net.b_off[l], Xd, ldb, ctx->stream);

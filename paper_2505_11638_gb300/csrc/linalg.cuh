@@ -119,6 +119,10 @@ template <typename T>
 void launch_philox_omega(T* Om, int64_t ld, int64_t p, int ell, uint64_t seed, uint64_t step, cudaStream_t s);
 
 template <typename T> void launch_gemm(const GemmArgs<T>& g, cudaStream_t s);
+// FP32 GEMM of the layer products (sgemm.cu): K-slices of FP32 accumulation, FP64 slice partials
+// (out64, split_stride) or one slice into outT (accumulate honoured); rowscale/colscale unused.
+int sgemm_layer_slices(int64_t M, int64_t N, int64_t K);
+void launch_sgemm_layer(const GemmArgs<float>& g, int nslices, cudaStream_t s);
 void launch_sum_splits(const double* part, int nz, int64_t stride, int64_t n, double* out, cudaStream_t s);
 template <typename T>
 void launch_sum_splits_t(const double* part, int nz, int64_t stride, int64_t rows, int64_t cols, int64_t ldp, T* out,
