@@ -836,10 +836,11 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
     const int nz = (int)((g.K + kps - 1) / kps);
     TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));
     g.out64 = ctx->gpart; g.split_stride = (int64_t)ell * ell; g.scm = 1; g.scn = ell;
+    g.lower = 1;                                        // symmetric: the lower triangle, mirrored
     launch_gemm_df<float, double>(g, ctx->stream);
     launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, ctx->M, ctx->stream);
   }
-  launch_symmetrize(ctx->M, ell, ctx->stream);
+  launch_mirror_lower(ctx->M, ell, ctx->stream);
   CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));                                // = L L^T
   launch_trsm_lt<double>(Bm, ld, p, ell, ctx->M, (double*)ctx->eigws, ctx->stream);  // B = Y_nu L^{-T}
   {
@@ -852,11 +853,12 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
     const int nz = (int)((g.K + kps - 1) / kps);
     TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));
     g.out64 = ctx->gpart; g.split_stride = (int64_t)ell * ell; g.scm = 1; g.scn = ell;
+    g.lower = 1;
     launch_gemm_df<double, double>(g, ctx->stream);
     launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, ctx->V, ctx->stream);
   }
-  launch_symmetrize(ctx->V, ell, ctx->stream);
-  CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream));
+  launch_mirror_lower(ctx->V, ell, ctx->stream);
+  CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream, ctx->dtype == NGD_F32));
   launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
   {
     GemmDfArgs<double, double> g;                                                          // U = B V Sigma^{-1}
@@ -889,7 +891,7 @@ ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) 
   TRY(gram_atb<T>(ctx, Bm, Bm, ctx->p, ctx->ldP, ell, ctx->V));                          // S = B^T B
   launch_symmetrize(ctx->V, ell, ctx->stream);
   // S = V Sigma^2 V^T in FP64; sorted eigenvectors into M (free again after the triangular solve)
-  CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream));
+  CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream, ctx->dtype == NGD_F32));
   launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
   // U = B V_sorted diag(1/sigma)
   {
@@ -1275,7 +1277,7 @@ ngd_status rpchol_build(ngd_ctx* ctx, const ngd_step_opts* o, int* ell_pc, int* 
     launch_sum_splits(ctx->gpart, nz, (int64_t)r * r, (int64_t)r * r, ctx->V, st);
   }
   launch_symmetrize(ctx->V, r, st);
-  CK(launch_sym_eig(ctx->V, r, ctx->sig2, ctx->M, ctx->eigws, ctx->status, st));
+  CK(launch_sym_eig(ctx->V, r, ctx->sig2, ctx->M, ctx->eigws, ctx->status, st, ctx->dtype == NGD_F32));
   launch_rpchol_lambda(ctx->sig2, r, ctx->lam, ctx->inv_sigma, st);
   {
     GemmDfArgs<double, double> g;                                                      // U = F V Sigma^{-1}

@@ -59,12 +59,51 @@ __device__ __forceinline__ DF df_mul(DF t, float wh, float wl) {
   return DF{hi, pe - (hi - p)};
 }
 
-__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
+// FP64 <-> FP32 conversions by integer operations on the bit patterns.  GB300 executes the
+// hardware conversions on its FP64 pipe (about two per cycle and SM, measured), so bulk splits
+// and recombinations do them in the integer pipes instead; the results are the same bits as the
+// hardware's round-to-nearest-even conversions.  Zeros stay in the integer path; other values
+// outside FP32's normal range (subnormal, overflow, inf, NaN) take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < -126 || e > 127) {
+    if ((b << 1) == 0ull) return __uint_as_float((unsigned)(b >> 32));       // +-0
+    return __double2float_rn(x);
+  }
+  const unsigned long long m = b & 0xfffffffffffffull;                 // 52-bit fraction
+  const unsigned t = (unsigned)((m + 0xfffffffull + ((m >> 29) & 1ull)) >> 29);   // 23 bits, half to even
+  // a rounding carry (t == 2^23) moves into the exponent field; 2^128 becomes inf as it should
+  const unsigned bits = ((unsigned)(b >> 32) & 0x80000000u) | (((unsigned)(e + 127) << 23) + t);
+  return __uint_as_float(bits);
 }
 
-__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0u || ef == 255u) {
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // +-0
+    return (double)f;                                                  // subnormal, inf, NaN
+  }
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ef + (1023u - 127u)) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+double f32_to_f64(double) = delete;     // a double argument would be narrowed first
+
+// widening of a templated accumulator: FP32 by the integer path, FP64 unchanged
+__device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
+// x = hi + lo: hi = x rounded to FP32, lo = the rest rounded to FP32 (one FP64 subtraction)
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = f64_to_f32_rn(x);
+  lo = f64_to_f32_rn(x - f32_to_f64(hi));
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 
 // warp-wide sum by an XOR butterfly: every lane ends with the same value
 __device__ __forceinline__ DF warp_sum_df(DF a) {

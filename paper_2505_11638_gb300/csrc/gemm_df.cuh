@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) k_gemm_df(int64_t M, int64_t N, int64_t K
     for (int j = 0; j < 4; ++j) {
       const int64_t gn = n0 + tx + 16 * j;
       if (gn >= N || (lower && gn > gm)) continue;
-      double v = ((double)acc[i][j].hi + (double)acc[i][j].lo) * rs;
+      double v = (f32_to_f64(acc[i][j].hi) + f32_to_f64(acc[i][j].lo)) * rs;
       if (colscale) v *= colscale[gn];
       if (out64) {
         double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
@@ -314,14 +314,15 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_dfv(int64_t M, int64_t N, int64_
       for (int u = 0; u < 2; ++u) {
         const int64_t gm = m0 + 64 * (i / 2) + 4 * ty + 2 * (i % 2) + u;
         if (gm >= M || gn >= N || (lower && gn > gm)) continue;
-        double v = ((double)(u ? h1 : h0) + (double)(u ? l1 : l0)) * (rowscale ? rowscale[gm] : 1.0);
+        double v = f32_to_f64(u ? h1 : h0) + f32_to_f64(u ? l1 : l0);
+        if (rowscale) v *= rowscale[gm];
         if (colscale) v *= colscale[gn];
         if (out64) {
           double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
           *o = accumulate ? *o + v : v;
         } else {
           float* o = out32 + gm * scm + gn * scn;
-          *o = accumulate ? (float)((double)*o + v) : (float)v;
+          *o = accumulate ? f64_to_f32_rn(f32_to_f64(*o) + v) : f64_to_f32_rn(v);
         }
       }
     }

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_coldot(const T* __restrict__ J, int64_t
   }
   double* pp = part + (int64_t)blockIdx.y * ldJ + col;
 #pragma unroll
-  for (int e = 0; e < VN; ++e) pp[e] = (double)acc[e];
+  for (int e = 0; e < VN; ++e) pp[e] = to_f64(acc[e]);
 }
 
 int coldot_nsplit(int64_t nrows, int64_t ldJ, int vn) {
@@ -211,6 +211,14 @@ __global__ void k_split_df(const double* __restrict__ x, float* __restrict__ hi,
     lo[i] = l;
   }
 }
+__global__ void k_f64_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) y[i] = f64_to_f32_rn(x[i]);
+}
+void launch_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
+  k_f64_to_f32<<<(int)std::min<int64_t>((n + 255) / 256, 2048), 256, 0, s>>>(x, y, n); note_launch();
+}
+
 void launch_split_df(const double* x, float* hi, float* lo, int64_t n, int64_t npad, cudaStream_t s) {
   k_split_df<<<(int)std::min<int64_t>((npad + 255) / 256, 2048), 256, 0, s>>>(x, hi, lo, n, npad); note_launch();
 }
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(256) k_coldot_df(const float* __restrict__ J, 
   if (!active) return;
   double* pp = part + (int64_t)blockIdx.y * ldJ + col;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) pp[e] = (double)acc[e].hi + (double)acc[e].lo;
+  for (int e = 0; e < 4; ++e) pp[e] = f32_to_f64(acc[e].hi) + f32_to_f64(acc[e].lo);
 }
 
 void launch_coldot_df(const float* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(256) k_utv_f(const float* __restrict__ U, int6
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double sv = wsum((double)acc[c].hi + (double)acc[c].lo);
+    const double sv = wsum(f32_to_f64(acc[c].hi) + f32_to_f64(acc[c].lo));
     if (lane == 0) red[c][warp] = sv;
   }
   __syncthreads();
@@ -581,7 +589,7 @@ __global__ void __launch_bounds__(256) k_precond_apply_f(const float* __restrict
       const float2 ww = w2[j];
       df_add_prod(acc, U[i + (int64_t)j * ld], ww.x, ww.y);
     }
-    z[i] = v[i] + ((double)acc.hi + (double)acc.lo);
+    z[i] = v[i] + (f32_to_f64(acc.hi) + f32_to_f64(acc.lo));
   }
 }
 
@@ -1295,7 +1303,7 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, c
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          acc64[i][j] += (double)acc[i][j];
+          acc64[i][j] += to_f64(acc[i][j]);
           acc[i][j] = T(0);
         }
     }
@@ -1309,7 +1317,7 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, c
     for (int j = 0; j < 4; ++j) {
       const int64_t gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      double v = (acc64[i][j] + (double)acc[i][j]) * rs;
+      double v = (acc64[i][j] + to_f64(acc[i][j])) * rs;
       if (colscale) v *= colscale[gn];
       if (out64) {
         double* o = out64 + (int64_t)blockIdx.z * split_stride + gm * scm + gn * scn;
@@ -1474,6 +1482,20 @@ void launch_symmetrize(double* M, int n, cudaStream_t s) {
   k_symmetrize<<<blocks, 256, 0, s>>>(M, n); note_launch();
 }
 
+// M[i][j] = M[j][i] for i < j: the upper triangle from the lower one (n x n column-major)
+__global__ void k_mirror_lower(double* M, int n) {
+  const int64_t total = (int64_t)n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) M[e] = M[j + (int64_t)i * n];
+  }
+}
+void launch_mirror_lower(double* M, int n, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
+  k_mirror_lower<<<blocks, 256, 0, s>>>(M, n); note_launch();
+}
+
 // ---------------------------------------------------------------------------- triangular solve
 // X (p x n, column-major, leading dimension ld) <- X L^{-T}, L lower (FP64, column-major n x n):
 // blocked by 32-column panels, right-looking.  Per panel the rows are solved by forward
@@ -1521,9 +1543,224 @@ __global__ void __launch_bounds__(128) k_trsm_panel(T* __restrict__ X, int64_t l
   }
 }
 
+// Row-block form for double X: each CTA solves R whole rows in one launch (rows are independent),
+// the rows held in shared memory as double-float pairs, column-major by column index.  Per
+// 32-column block J: (1) x_J -= z_{<J} L_{J,<J}^T, double-float multiply-adds on packed f32x2
+// lanes (two columns per instruction), L streamed in 32 x 32 chunks; (2) forward substitution in
+// the 32 x 32 diagonal block in double-float (z_j = x_j / L_jj as a product with the FP64
+// reciprocal's pair, then x_c -= L_cj z_j for c > j), one warp per row, lane = column.  The
+// arithmetic carries ~2^-48 relative error per operation like the blocked form's GEMMs; the
+// solve is one launch instead of two per 32-column panel.
+constexpr int kTrsmThreads = 256;
+
+// For FP32 X (the test matrix's CholeskyQR) the off-diagonal products run in plain FP32 on packed
+// lanes with the high words of L, each 32-term chunk's sum added to a double-float accumulator
+// (FP32 rounding over 32 terms, not over n), the diagonal blocks as for FP64 X.
+template <int R, typename TX>
+__global__ void __launch_bounds__(kTrsmThreads) k_trsm_rows(TX* __restrict__ X, int64_t ld, int64_t p,
+                                                         const double* __restrict__ L, const float* __restrict__ LH,
+                                                         const float* __restrict__ LL, int n) {
+  constexpr bool F32 = sizeof(TX) == 4;
+  static_assert(R == 16 || R == 32, "row block");
+  constexpr int RP = R + 1;                            // padded column stride: no bank conflicts
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Zh = reinterpret_cast<float*>(smem_raw);      // [n][RP]
+  float* Zl = Zh + (size_t)n * RP;                     // [n][RP]
+  __shared__ float Lh[32][33], Ll[32][33];             // chunk of L: [j - j0][t - tc]
+  __shared__ float Dh[32][33], Dl[32][33];             // diagonal block: [c][j]
+  __shared__ float Rh[32], Rl[32];                     // 1 / L_jj as a pair
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  for (int64_t e = tid; e < (int64_t)n * R; e += kTrsmThreads) {
+    const int r = (int)(e % R);
+    const int64_t t = e / R;
+    if constexpr (F32) {
+      Zh[t * RP + r] = r0 + r < p ? X[r0 + r + t * ld] : 0.f;
+      Zl[t * RP + r] = 0.f;
+    } else {
+      const double x = r0 + r < p ? X[r0 + r + t * ld] : 0.0;
+      split_df(x, Zh[t * RP + r], Zl[t * RP + r]);
+    }
+  }
+  const int tj = tid & 15, tr = tid >> 4;              // update: columns tj, tj + 16; rows tr (+16)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int bw = min(32, n - j0);
+    // diagonal block and reciprocals for step (2)
+    for (int e = tid; e < 32 * 32; e += kTrsmThreads) {
+      const int c = e & 31, j = e >> 5;
+      const bool in = c < bw && j < c;
+      const int64_t o = (j0 + c) + (int64_t)(j0 + j) * n;
+      Dh[c][j] = in ? LH[o] : 0.f;
+      Dl[c][j] = in && !F32 ? LL[o] : 0.f;            // FP32 X: L's high words only
+    }
+    if (tid < 32) {
+      const double rv = tid < bw ? 1.0 / L[(int64_t)(j0 + tid) * (n + 1)] : 0.0;
+      split_df(rv, Rh[tid], Rl[tid]);
+    }
+    // (1) x_J -= sum_{t < j0} z_t L_{J,t}; the next chunk of L is fetched into registers while
+    // the current one is used
+    DF2 acc[R / 16];
+#pragma unroll
+    for (int q = 0; q < R / 16; ++q) acc[q] = DF2{0ull, 0ull};
+    float preh[4], prel[4];
+    auto fetch = [&](int tc) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + kTrsmThreads * u, jj = e & 31, tt = e >> 5;
+        const int64_t o = (j0 + jj) + (int64_t)(tc + tt) * n;
+        preh[u] = jj < bw ? LH[o] : 0.f;
+        prel[u] = jj < bw ? LL[o] : 0.f;
+      }
+    };
+    if (j0 > 0) fetch(0);
+    for (int tc = 0; tc < j0; tc += 32) {
+      __syncthreads();                                  // previous chunk consumed
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + kTrsmThreads * u, jj = e & 31, tt = e >> 5;
+        Lh[jj][tt] = preh[u];
+        Ll[jj][tt] = prel[u];
+      }
+      __syncthreads();
+      if (tc + 32 < j0) fetch(tc + 32);
+      if constexpr (F32) {
+        f2x cs[R / 16];
+#pragma unroll
+        for (int q = 0; q < R / 16; ++q) cs[q] = 0ull;
+#pragma unroll 8
+        for (int tt = 0; tt < 32; ++tt) {
+          const f2x bh = pk2(Lh[tj][tt], Lh[tj + 16][tt]);
+#pragma unroll
+          for (int q = 0; q < R / 16; ++q) {
+            const float zh = Zh[(size_t)(tc + tt) * RP + tr + 16 * q];
+            cs[q] = fma2(pk2(zh, zh), bh, cs[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < R / 16; ++q) {       // acc += chunk sum (TwoSum into the high word)
+          const f2x t = add2(acc[q].hi, cs[q]);
+          const f2x z = sub2(t, acc[q].hi);
+          const f2x er = add2(sub2(acc[q].hi, sub2(t, z)), sub2(cs[q], z));
+          acc[q].hi = t;
+          acc[q].lo = add2(acc[q].lo, er);
+        }
+      } else {
+#pragma unroll 4
+      for (int tt = 0; tt < 32; ++tt) {
+        const f2x bh = pk2(Lh[tj][tt], Lh[tj + 16][tt]);
+        const f2x bl = pk2(Ll[tj][tt], Ll[tj + 16][tt]);
+#pragma unroll
+        for (int q = 0; q < R / 16; ++q) {
+          const int r = tr + 16 * q;
+          const float zh = Zh[(size_t)(tc + tt) * RP + r], zl = Zl[(size_t)(tc + tt) * RP + r];
+          // acc += (zh + zl)(bh + bl): the product of the high words exactly, cross terms in lo
+          const f2x ah = pk2(zh, zh), al = pk2(zl, zl);
+          const f2x pn = mul2(ah ^ 0x8000000080000000ull, bh);
+          f2x pe = fma2(ah, bh, pn);
+          pe = fma2(ah, bl, pe);
+          pe = fma2(al, bh, pe);
+          const f2x t = sub2(acc[q].hi, pn);
+          const f2x z = sub2(t, acc[q].hi);
+          const f2x er = sub2(sub2(acc[q].hi, sub2(t, z)), add2(pn, z));
+          acc[q].hi = t;
+          acc[q].lo = add2(add2(acc[q].lo, pe), er);
+        }
+      }
+      }
+    }
+    __syncthreads();                                    // diagonal block loaded, chunks done
+    if (j0 > 0) {
+#pragma unroll
+      for (int q = 0; q < R / 16; ++q) {
+        const int r = tr + 16 * q;
+        DF a0, a1;
+        df2_split(acc[q], a0, a1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = tj + 16 * h;
+          if (c < bw) {
+            const size_t o = (size_t)(j0 + c) * RP + r;
+            const DF a = h ? a1 : a0;
+            const DF x = df_add(DF{Zh[o], Zl[o]}, DF{-a.hi, -a.lo});
+            Zh[o] = x.hi;
+            Zl[o] = x.lo;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // (2) substitution in the diagonal block: lane = column, the warp's rows interleaved
+    {
+      constexpr int NR = R / (kTrsmThreads / 32);
+      DF x[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const size_t o = (size_t)(j0 + lane) * RP + warp + 8 * q;
+        x[q] = lane < bw ? DF{Zh[o], Zl[o]} : DF{0.f, 0.f};
+      }
+      for (int j = 0; j < bw; ++j) {
+        const float rh = Rh[j], rl = Rl[j], nlh = -Dh[lane][j], nll = -Dl[lane][j];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const DF xj{__shfl_sync(0xffffffffu, x[q].hi, j), __shfl_sync(0xffffffffu, x[q].lo, j)};
+          const DF zj = df_mul(xj, rh, rl);
+          if (lane == j) {
+            x[q] = zj;
+          } else if (lane > j) {
+            df_add_prod2(x[q], nlh, nll, zj.hi, zj.lo);   // x -= L_cj z_j
+          }
+        }
+      }
+      if (lane < bw) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const size_t o = (size_t)(j0 + lane) * RP + warp + 8 * q;
+          Zh[o] = x[q].hi;
+          Zl[o] = x[q].lo;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)n * R; e += kTrsmThreads) {
+    const int r = (int)(e % R);
+    const int64_t t = e / R;
+    if (r0 + r < p) {
+      if constexpr (F32) X[r0 + r + t * ld] = Zh[t * RP + r] + Zl[t * RP + r];
+      else X[r0 + r + t * ld] = f32_to_f64(Zh[t * RP + r]) + f32_to_f64(Zl[t * RP + r]);
+    }
+  }
+}
+
+size_t trsm_rows_smem(int n, int R) { return (size_t)2 * n * (R + 1) * sizeof(float); }
+
 // W: n x n scratch of T.
 template <typename T>
 void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* W, cudaStream_t s) {
+  {
+    // one launch over row blocks while 16 rows of the solve fit in shared memory (two CTAs, 16
+    // warps, per SM to hide the double-float chains' latency)
+    constexpr int R = 16;
+    const size_t smem = trsm_rows_smem(n, R);
+    if (n >= 64 && smem <= 200 * 1024) {
+      // L as double-float pairs once (W: n x n elements of T, at least n^2 floats; for FP32 X the
+      // low words are not needed), so that no CTA converts FP64 in its inner loop
+      float* LH = reinterpret_cast<float*>(W);
+      float* LL = sizeof(T) == 8 ? LH + (int64_t)n * n : LH;
+      if (sizeof(T) == 8) launch_split_df(L, LH, LL, (int64_t)n * n, (int64_t)n * n, s);
+      else launch_f64_to_f32(L, LH, (int64_t)n * n, s);
+      const unsigned grid = (unsigned)((p + R - 1) / R);
+      static bool cfg = false;
+      if (!cfg) {
+        cudaFuncSetAttribute((const void*)k_trsm_rows<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cfg = true;
+      }
+      k_trsm_rows<R, T><<<grid, kTrsmThreads, smem, s>>>(X, ld, p, L, LH, LL, n);
+      note_launch();
+      return;
+    }
+  }
   const int blocks0 = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
   k_neg_transpose<T><<<blocks0, 256, 0, s>>>(L, n, W); note_launch();
   static int nsm = 0;

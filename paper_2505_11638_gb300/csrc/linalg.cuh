@@ -93,6 +93,8 @@ void launch_coldot(const T* J, int64_t ldJ, int64_t nrows, const double* s_vec, 
                    const int* done, cudaStream_t st);
 // FP32 Jacobian, FP64-accurate sums (exact FP32 products, double-float accumulation)
 void launch_split_df(const double* x, float* hi, float* lo, int64_t n, int64_t npad, cudaStream_t s);
+// y = x rounded to FP32 (integer conversion), n elements
+void launch_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 void launch_rowdot_df(const float* J, int64_t ldJ, int64_t nrows, const float* vh, const float* vl, const double* w,
                       double* t_out, double* s_out, const int* done, cudaStream_t s);
 void launch_coldot_df(const float* J, int64_t ldJ, int64_t nrows, const double* s_vec, double* part, int nsplit,
@@ -135,6 +137,8 @@ template <typename T>
 void launch_shift_add(const T* src, const T* Om, const double* nu, T* dst, int64_t ld, int64_t p, int ell,
                       cudaStream_t s);
 void launch_symmetrize(double* M, int n, cudaStream_t s);
+// upper triangle = transpose of the lower one
+void launch_mirror_lower(double* M, int n, cudaStream_t s);
 void launch_shift_add_mixed(const double* Y, const float* Om, const double* nu, double* dst, int64_t ld, int64_t p,
                             int ell, cudaStream_t s);
 
@@ -142,10 +146,12 @@ template <typename T>
 void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* W, cudaStream_t s);
 cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s);
 // eigen.cu: FP64 symmetric eigen-decomposition (tridiagonal reduction, multisection, twisted
-// factorization, back-transform, CholeskyQR), eigenvalues decreasing.
+// factorization, back-transform, re-orthonormalization), eigenvalues decreasing.  df_recurrences:
+// the twisted factorization in double-float arithmetic (~2^-48 per operation, for FP32 contexts
+// whose Nystrom core carries that precision) instead of FP64.
 size_t sym_eig_workspace_doubles(int n);
 cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, double* ws, int* status,
-                           cudaStream_t s);
+                           cudaStream_t s, bool df_recurrences = false);
 void launch_nystrom_lambda(const double* sig2, const double* nu, int n, double* lam, double* inv_sigma,
                            cudaStream_t s);
 void launch_set_mu(const double* lam, double fixed_mu, double gamma, const double* loss, double c, double* mu,

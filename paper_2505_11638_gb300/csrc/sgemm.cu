@@ -13,6 +13,7 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "linalg.cuh"
 
 namespace ngd {
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256) k_sgemm(int64_t M, int64_t N, int64_t K, 
       const int64_t gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
       if (gn >= N) continue;
       if (out64) {
-        out64[(int64_t)blockIdx.z * split_stride + gm * scm + gn * scn] = (double)acc[i][j];
+        out64[(int64_t)blockIdx.z * split_stride + gm * scm + gn * scn] = f32_to_f64(acc[i][j]);
       } else {
         float* o = outT + gm * scm + gn * scn;
         *o = accumulate ? *o + acc[i][j] : acc[i][j];

@@ -164,7 +164,9 @@ __global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t col
     for (int s = 0; s < S; ++s) {
       const T a = sizeof(T) == 4 ? (T)rintf((float)r) : (T)rint((double)r);
       r = (r - a) * (T)256;                                               // exact
-      D[(int64_t)s * total + idx] = __float2bfloat16_rn((float)ldexp((double)a, -8 * s));
+      // a is an integer of magnitude <= 128: exact in FP32, and so is its scaling by 2^-8s
+      const float af = sizeof(T) == 4 ? (float)a : f64_to_f32_rn((double)a);
+      D[(int64_t)s * total + idx] = __float2bfloat16_rn(af * __int_as_float((127 - 8 * s) << 23));
     }
   }
 }
@@ -435,7 +437,7 @@ __global__ void k_oz_reduce(const float2* __restrict__ P, int nc, int64_t ldL, i
     acc[j * ldM + m] = make_float2(v.hi, v.lo);
     return;
   }
-  const double x = (double)v.hi + (double)v.lo;
+  const double x = f32_to_f64(v.hi) + f32_to_f64(v.lo);
   if (MODE == 1)
     out[j * ldOut + m] = w[m] * ldexp(x, 2 * rexp[m] + cexp[j] - 14);
   else
