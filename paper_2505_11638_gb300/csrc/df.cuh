@@ -49,6 +49,8 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   return DF{hi, e - (hi - s)};
 }
 
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
 // (t.hi + t.lo) * (wh + wl), renormalised
 __device__ __forceinline__ DF df_mul(DF t, float wh, float wl) {
   const float p = t.hi * wh;

@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256) k_tridiag_dist(const double* __restrict__
   }
 }
 
+
 // ---------------------------------------------------------------------------- 2. eigenvalues
 // lam_asc[i] (ascending), one half-warp per eigenvalue: 16 Sturm counts per step shrink the
 // bracket 17-fold, down to a relative width 2 eps (so that eigenvalues far below eps ||T|| stay
@@ -493,6 +494,119 @@ __global__ void __launch_bounds__(kSectThreads) k_multisect(const double* __rest
   if (sl == 0) lam_asc[i] = 0.5 * (a + b);
 }
 
+// Double-float multisection (FP32 contexts): the count of eigenvalues below x as the number of
+// negative pivots of T - x I = L D L^T, q_j = (d_j - x) - e_{j-1}^2 / q_{j-1} with |q_j| kept
+// above FP32's safe minimum times max(1, max e^2) (LAPACK's pivmin rule, so e^2 / q stays
+// finite), each division an FP32 reciprocal refined by one double-float step.  No rescaling is
+// needed, the chain is tens of FP32-pipe cycles per step instead of the FP64 pipe's issue-bound
+// three operations, and each lane evaluates four points (128 per eigenvalue and step).
+namespace {
+
+__device__ __forceinline__ float rcp_approx(float x) {   // one MUFU operation, ~1 ulp
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// a / b: q0 = a_hi / b_hi from the approximate reciprocal, then q = q0 + (a - q0 b) / b_hi; the
+// correction brings ~2^-22 to ~2^-44
+__device__ __forceinline__ DF df_divq(DF a, DF b) {
+  const float rb = rcp_approx(b.hi);
+  const float q0 = a.hi * rb;
+  const float p = q0 * b.hi;
+  const float pe = fmaf(q0, b.hi, -p);
+  float r = (a.hi - p) - pe;
+  r = fmaf(-q0, b.lo, r + a.lo);
+  const float q1 = r * rb;
+  const float hi = q0 + q1;
+  return DF{hi, q1 - (hi - q0)};
+}
+
+__device__ __forceinline__ void pivot_step(DF dj, DF e2, DF x, DF& q, int& c, float pivmin) {
+  DF t = df_add(dj, DF{-x.hi, -x.lo});
+  t = df_add(t, df_neg(df_divq(e2, q)));
+  if (fabsf(t.hi) < pivmin) t = DF{-pivmin, 0.f};
+  c += t.hi < 0.f;
+  q = t;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(32) k_multisect_df(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                                     double* __restrict__ lam_asc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF* ds = reinterpret_cast<DF*>(smem_raw);           // [n], scaled
+  DF* e2 = ds + n;                                    // [n], scaled squares
+  double lo = DBL_MAX, hi = -DBL_MAX;
+  for (int j = threadIdx.x; j < n; j += 32) {
+    const double dj = d[j];
+    const double ej = j + 1 < n ? fabs(e[j]) : 0.0, ejm = j > 0 ? fabs(e[j - 1]) : 0.0;
+    lo = fmin(lo, dj - ej - ejm);
+    hi = fmax(hi, dj + ej + ejm);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const double tn = fmax(fmax(fabs(lo), fabs(hi)), DBL_MIN);
+  const double tsc = __longlong_as_double((long long)(2046 - (int)((__double_as_longlong(tn) >> 52) & 0x7ff)) << 52);
+  float e2max = 0.f;
+  for (int j = threadIdx.x; j < n; j += 32) {           // scaled copy, ||T|| in [1, 2)
+    DF a, b;
+    split_df(d[j] * tsc, a.hi, a.lo);
+    const double ej = j + 1 < n ? e[j] * tsc : 0.0;
+    split_df(ej * ej, b.hi, b.lo);
+    ds[j] = a;
+    e2[j] = b;
+    e2max = fmaxf(e2max, b.hi);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e2max = fmaxf(e2max, __shfl_xor_sync(0xffffffffu, e2max, o));
+  __syncwarp();
+  const float pivmin = FLT_MIN * fmaxf(1.f, e2max);
+  const int i = blockIdx.x;                           // one eigenvalue per warp
+  const int lane = threadIdx.x;
+  const double span = fmax(hi - lo, fmax(fabs(hi), fabs(lo)));
+  const double atol = 2.0 * DBL_EPSILON * span + DBL_MIN;
+  const double wfloor = DBL_EPSILON * DBL_EPSILON * span + 4.0 * DBL_MIN;
+  double a = lo - atol, b = hi + atol;
+  constexpr int P = 4;                                // points per lane, 128 per eigenvalue and step
+  for (int it = 0; it < 160; ++it) {
+    if (b - a <= fmax(2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)), wfloor)) break;
+    const double h = (b - a) * (1.0 / (32 * P + 1));
+    DF x[P], q[P];
+    int cnt[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {                     // point u * 32 + lane (ascending in the warp's order)
+      split_df((a + h * (u * 32 + lane + 1)) * tsc, x[u].hi, x[u].lo);
+      q[u] = df_add(ds[0], df_neg(x[u]));
+      if (fabsf(q[u].hi) < pivmin) q[u] = DF{-pivmin, 0.f};
+      cnt[u] = q[u].hi < 0.f;
+    }
+    for (int j = 1; j < n; ++j) {
+      const DF dj = ds[j], ej = e2[j - 1];
+#pragma unroll
+      for (int u = 0; u < P; ++u) pivot_step(dj, ej, x[u], q[u], cnt[u], pivmin);
+    }
+    // first of the points (ascending) whose count exceeds i
+    int pt = 32 * P;
+#pragma unroll
+    for (int u = P - 1; u >= 0; --u) {
+      const unsigned m = __ballot_sync(0xffffffffu, cnt[u] > i);
+      if (m) pt = u * 32 + __ffs(m) - 1;
+    }
+    if (pt == 32 * P) {
+      a = a + h * (32 * P);
+    } else {
+      const double nb = a + h * (pt + 1);
+      a = pt == 0 ? a : a + h * pt;
+      b = nb;
+    }
+  }
+  if (lane == 0) lam_asc[i] = 0.5 * (a + b);
+}
+
 // ---------------------------------------------------------------------------- 3. eigenvectors of T
 // Z[:, i] = unit eigenvector of T for lam_asc[i] by the twisted factorization, one thread per
 // eigenvalue.  The recurrences are chains of dependent FP64 divisions and products, so their
@@ -581,13 +695,11 @@ size_t twisted_smem(int n) { return (size_t)(2 + 3 * kTwThreads) * n * sizeof(do
 // Per-thread arrays in shared memory as pairs: [j][kTwThreads] of (hi, lo).
 namespace {
 
-__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
-
 __device__ __forceinline__ DF df_mul2(DF a, DF b) { return df_mul(a, b.hi, b.lo); }
 
 // a / b: q0 = a_hi / b_hi in FP32, then q = q0 + (a - q0 b) / b_hi
 __device__ __forceinline__ DF df_div(DF a, DF b) {
-  const float rb = __frcp_rn(b.hi);
+  const float rb = rcp_approx(b.hi);
   const float q0 = a.hi * rb;
   const float p = q0 * b.hi;
   const float pe = fmaf(q0, b.hi, -p);                 // q0 b_hi = p + pe exactly
@@ -1001,7 +1113,12 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
     err = cudaLaunchCooperativeKernel((const void*)k_tridiag, blocks, 256, args, smem, s);
     if (err != cudaSuccess) return err;
   }
-  {
+  if (df_recurrences) {
+    const size_t smem = 2 * (size_t)n * sizeof(DF);
+    cudaFuncSetAttribute((const void*)k_multisect_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_multisect_df<<<n, 32, smem, s>>>(d, e, n, lam_asc);
+    note_launch();
+  } else {
     const size_t smem = 2 * (size_t)n * sizeof(double);
     cudaFuncSetAttribute((const void*)k_multisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_multisect<<<(n * kSectLanes + kSectThreads - 1) / kSectThreads, kSectThreads, smem, s>>>(d, e, n, lam_asc);
