@@ -13,8 +13,8 @@
 //      recurrences' operands in shared memory):
 //      T - lambda I = L+ D+ L+^T = U- D- U-^T, twist index r = argmin |gamma_r|,
 //      gamma_r = D+_r + D-_r - (d_r - lambda), z_r = 1 and the two bidiagonal recurrences.
-//   4. V = Q Z by applying the reflectors to the columns of Z (one warp per two columns in
-//      double-float on packed f32x2 lanes, no barrier).
+//   4. V = Q Z by applying the reflectors to the columns of Z (one warp per column in FP64; in
+//      FP32 contexts one warp per two columns in double-float on packed f32x2 lanes).
 //   5. V is re-orthonormalised.  Twisted vectors of well-separated eigenvalues are already
 //      orthogonal to eps ||T|| / gap (measured on the 5-D Poisson trajectory at ell = 500:
 //      max |V^T V - I| ~ 1e-12), and then Newton-Schulz steps V <- V (3 I - V^T V) / 2 (one or
@@ -1140,7 +1140,7 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
     }
     note_launch();
   }
-  if (n <= 32 * 32 + 1) {           // the longest reflector, n - 1 entries, within 32 NQ lanes
+  if (df_recurrences && n <= 32 * 32 + 1) {   // the longest reflector, n - 1 entries, within 32 NQ lanes
     // the reflectors as double-float pairs once (into the free L+ / U- scratch), so that no warp
     // converts FP64 in its loop
     float* VH = reinterpret_cast<float*>(A);

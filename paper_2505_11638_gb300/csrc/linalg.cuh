@@ -147,8 +147,8 @@ void launch_trsm_lt(T* X, int64_t ld, int64_t p, int n, const double* L, T* W, c
 cudaError_t launch_cholesky(double* A, int n, int* status, cudaStream_t s);
 // eigen.cu: FP64 symmetric eigen-decomposition (tridiagonal reduction, multisection, twisted
 // factorization, back-transform, re-orthonormalization), eigenvalues decreasing.  df_recurrences:
-// the twisted factorization in double-float arithmetic (~2^-48 per operation, for FP32 contexts
-// whose Nystrom core carries that precision) instead of FP64.
+// multisection, twisted factorization and back-transform in double-float arithmetic (~2^-48 per
+// operation, for FP32 contexts whose Nystrom core carries that precision) instead of FP64.
 size_t sym_eig_workspace_doubles(int n);
 cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, double* ws, int* status,
                            cudaStream_t s, bool df_recurrences = false);
