@@ -831,7 +831,7 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
     g.M = ell; g.N = ell; g.K = p;
     g.A = Om; g.sam = ld; g.sak = 1;
     g.B = Bm; g.sbk = 1; g.sbn = ld;
-    g.nsplit = choose_splits(ell, ell, p);
+    g.nsplit = gemm_df_splits(ell, ell, p, true);
     const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : g.K;
     const int nz = (int)((g.K + kps - 1) / kps);
     TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));
@@ -848,7 +848,7 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
     g.M = ell; g.N = ell; g.K = p;
     g.A = Bm; g.sam = ld; g.sak = 1;
     g.B = Bm; g.sbk = 1; g.sbn = ld;
-    g.nsplit = choose_splits(ell, ell, p);
+    g.nsplit = gemm_df_splits(ell, ell, p, true);
     const int64_t kps = g.nsplit > 1 ? ((g.K + g.nsplit - 1) / g.nsplit + 15) / 16 * 16 : g.K;
     const int nz = (int)((g.K + kps - 1) / kps);
     TRY(ensure_gpart(ctx, (size_t)nz * ell * ell));

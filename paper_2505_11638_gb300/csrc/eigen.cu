@@ -895,12 +895,13 @@ __global__ void __launch_bounds__(32) k_backtransform_df(const double* __restric
     const double tk = ntk;
     if (k > 0) fetch(k - 1);
     if (tk == 0.0) continue;                           // uniform over the warp
-    DF2 acc{0ull, 0ull};
+    DF2 a4[4] = {{0ull, 0ull}, {0ull, 0ull}, {0ull, 0ull}, {0ull, 0ull}};   // four independent chains
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int i = lane + 32 * q;
-      if (i < m) df2_mac4(acc, xh[k + 1 + i], xl[k + 1 + i], pk2(vh[q], vh[q]), pk2(vl[q], vl[q]));
+      if (i < m) df2_mac4(a4[q & 3], xh[k + 1 + i], xl[k + 1 + i], pk2(vh[q], vh[q]), pk2(vl[q], vl[q]));
     }
+    DF2 acc = df2_add(df2_add(a4[0], a4[1]), df2_add(a4[2], a4[3]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
       acc = df2_add(acc, DF2{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});

@@ -1566,7 +1566,8 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_rows(TX* __restrict__ X, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Zh = reinterpret_cast<float*>(smem_raw);      // [n][RP]
   float* Zl = Zh + (size_t)n * RP;                     // [n][RP]
-  __shared__ float Lh[32][33], Ll[32][33];             // chunk of L: [j - j0][t - tc]
+  // chunk of L as column pairs (j0 + c, j0 + c + 16), c < 16, of high and low words: [t - tc][c]
+  __shared__ __align__(16) f2x LPh[32][16], LPl[32][16];
   __shared__ float Dh[32][33], Dl[32][33];             // diagonal block: [c][j]
   __shared__ float Rh[32], Rl[32];                     // 1 / L_jj as a pair
   const int tid = threadIdx.x;
@@ -1619,8 +1620,8 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_rows(TX* __restrict__ X, 
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = tid + kTrsmThreads * u, jj = e & 31, tt = e >> 5;
-        Lh[jj][tt] = preh[u];
-        Ll[jj][tt] = prel[u];
+        reinterpret_cast<float*>(&LPh[tt][jj & 15])[jj >> 4] = preh[u];
+        reinterpret_cast<float*>(&LPl[tt][jj & 15])[jj >> 4] = prel[u];
       }
       __syncthreads();
       if (tc + 32 < j0) fetch(tc + 32);
@@ -1630,7 +1631,7 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_rows(TX* __restrict__ X, 
         for (int q = 0; q < R / 16; ++q) cs[q] = 0ull;
 #pragma unroll 8
         for (int tt = 0; tt < 32; ++tt) {
-          const f2x bh = pk2(Lh[tj][tt], Lh[tj + 16][tt]);
+          const f2x bh = LPh[tt][tj];
 #pragma unroll
           for (int q = 0; q < R / 16; ++q) {
             const float zh = Zh[(size_t)(tc + tt) * RP + tr + 16 * q];
@@ -1648,8 +1649,8 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_rows(TX* __restrict__ X, 
       } else {
 #pragma unroll 4
       for (int tt = 0; tt < 32; ++tt) {
-        const f2x bh = pk2(Lh[tj][tt], Lh[tj + 16][tt]);
-        const f2x bl = pk2(Ll[tj][tt], Ll[tj + 16][tt]);
+        const f2x bh = LPh[tt][tj];
+        const f2x bl = LPl[tt][tj];
 #pragma unroll
         for (int q = 0; q < R / 16; ++q) {
           const int r = tr + 16 * q;

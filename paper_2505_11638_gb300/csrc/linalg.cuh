@@ -43,8 +43,9 @@ template <typename TA, typename TB> struct GemmDfArgs {
   int lower = 0;     // write only out[m][n] with n <= m (M x N square output); skip tiles above
 };
 template <typename TA, typename TB> void launch_gemm_df(const GemmDfArgs<TA, TB>& g, cudaStream_t s);
-// K slices that fill the GPU's block slots most evenly for an M x N double-float GEMM
-int gemm_df_splits(int64_t M, int64_t N, int64_t K);
+// K slices that fill the GPU's block slots most evenly for an M x N double-float GEMM (lower:
+// only the lower-triangle tiles of a square output run)
+int gemm_df_splits(int64_t M, int64_t N, int64_t K, bool lower = false);
 
 // sampling test matrix (column selection with probabilities proportional to diag G)
 template <typename T>
