@@ -285,6 +285,19 @@ ngd_status ngd_gramian_mm(ngd_ctx* ctx, const double* theta, int ell, const void
  * d: device p float64, caller-owned.  Asynchronous.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 ngd_status ngd_gramian_diag(ngd_ctx* ctx, const double* theta, double* d);
 
+/* The explicit Gramian G = J^T diag(w) J (Thm. 1; the matrix NGD full, Alg. 2, factors) at the
+ * linearization (theta NULL reuses the last one; stored-J contexts only).  G: device, p x p
+ * column-major with leading dimension ldG >= p, float64, every entry written (symmetric: the
+ * lower triangle mirrored).  FP64-accurate in both dtypes: an FP32 context forms it on the tensor
+ * cores from six-digit BF16 planes of the column-scaled J^T and (diag(w) J)^T (pairs of digit
+ * weight sum <= 5 kept, each pair's 256-long K chunks summed exactly, ~2^-46 of the term
+ * magnitudes); an FP64 context by the double-float GEMM on the lower triangle.  Workspace of the
+ * FP32 form: 12 p N bytes of digit planes and up to 8 GB of split-K partials (p^2 8 bytes per 256
+ * points), kept by the context.
+ * Errors: INVALID_ARG (NULL G, ldG < p, no linearization), UNSUPPORTED (matrix-free context), OOM,
+ * TIMEOUT (a bounded tensor-core wait ran out), CUDA. */
+ngd_status ngd_gramian_full(ngd_ctx* ctx, const double* theta, double* G, int64_t ldG);
+
 /* Randomized Nystrom sketch with the sampling test matrix (NGD_TEST_SAMPLING): diag G, then ell
  * distinct parameter indices S by an exponential race (Efraimidis & Spirakis, 2006): the ell
  * smallest keys E_j = -ln(u_j) / (diag G)_j, ties to the smaller index, u_j the 52-bit uniform of

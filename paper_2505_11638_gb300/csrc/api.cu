@@ -1100,9 +1100,42 @@ ngd_status power_lambda1(ngd_ctx* ctx, uint64_t seed, uint64_t step) {
   return check_launch(ctx);
 }
 
+// Lower triangle of G = J^T diag(w) J (p x p, column-major, ldG) at the current linearization
+// (stored J), FP64-accurate: for an FP32 Jacobian by the digit-plane tensor-core GEMM (which writes
+// every entry), otherwise w .* J in FP64 (ctx->Zfull) and the double-float GEMM on the lower
+// triangle.
+template <typename T>
+ngd_status form_gramian(ngd_ctx* ctx, double* G, int64_t ldG) {
+  const int64_t p = ctx->p;
+  cudaStream_t st = ctx->stream;
+  if (std::is_same<T, float>::value) {
+    if (!ctx->oz) {
+      ctx->oz = oz_create();
+      if (!ctx->oz) return set_err(ctx, NGD_ERR_OOM, "tensor-core Gramian state%s");
+    }
+    const char* why = nullptr;
+    const cudaError_t e = oz_gram(ctx->oz, (const float*)ctx->J, ctx->ldJ, ctx->N, p, ctx->ps.w, G, ldG, &why, st,
+                                  ctx->status, ctx->wait_cycles);
+    if (e == cudaErrorMemoryAllocation) return set_err(ctx, NGD_ERR_OOM, "tensor-core Gramian workspace%s");
+    CK(e);
+    if (!why) return check_launch(ctx);
+  }
+  if (!ctx->Zfull) TRY(dalloc(ctx, &ctx->Zfull, (size_t)ctx->N * ctx->ldJ * 8));
+  launch_scale_rows_f64<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->ps.w, ctx->Zfull, st);
+  GemmDfArgs<T, double> g;                                      // lower(G) = lower(J^T (w .* J))
+  g.M = p; g.N = p; g.K = ctx->N;
+  g.A = (const T*)ctx->J; g.sam = 1; g.sak = ctx->ldJ;
+  g.B = ctx->Zfull; g.sbk = ctx->ldJ; g.sbn = 1;
+  g.out64 = G; g.scm = 1; g.scn = ldG;
+  g.lower = 1;
+  launch_gemm_df<T, double>(g, st);
+  return check_launch(ctx);
+}
+
 // NGD full (Alg. 2) direction at the current linearization (stored J) into ctx->d: lambda_1 by the
-// power method, mu (into scal[kSMu]), G = J^T (w .* J) formed explicitly (FP64-accurate: w .* J in
-// FP64, the double-float GEMM on the lower triangle, mirrored), G + mu I = L L^T (FP64 Cholesky:
+// power method, mu (into scal[kSMu]), G = J^T (w .* J) formed explicitly (FP64-accurate: for an
+// FP32 Jacobian by the digit-plane tensor-core GEMM, otherwise w .* J in FP64 and the double-float
+// GEMM on the lower triangle; mirrored from the lower one), G + mu I = L L^T (FP64 Cholesky:
 // one cooperative kernel up to kCholBlockedMin - 1 unknowns, the blocked form above),
 // d = L^{-T} L^{-1} g.
 constexpr int64_t kCholBlockedMin = 768;
@@ -1115,7 +1148,6 @@ ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
   if (!ctx->Gfull) {
     ctx->ldG = blocked ? (p + 3) / 4 * 4 : p;                  // even: the blocked GEMMs stay vectorised
     TRY(dalloc(ctx, &ctx->Gfull, (size_t)ctx->ldG * p * 8));
-    TRY(dalloc(ctx, &ctx->Zfull, (size_t)ctx->N * ctx->ldJ * 8));
     if (blocked) {
       TRY(dalloc(ctx, &ctx->chol_D, (size_t)256 * 256 * 8));
       TRY(dalloc(ctx, &ctx->chol_W, (size_t)256 * 256 * 8));
@@ -1126,14 +1158,7 @@ ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
   TRY(clear_status(ctx));
   TRY(power_lambda1<T>(ctx, o->seed, o->step));
   launch_set_mu(ctx->scal + kSLam1, o->mu, o->gamma, ctx->scal + kSLoss, o->mu_loss_coef, ctx->scal + kSMu, st);
-  launch_scale_rows_f64<T>((const T*)ctx->J, ctx->ldJ, ctx->N, ctx->ps.w, ctx->Zfull, st);
-  GemmDfArgs<T, double> g;                                      // lower(G) = lower(J^T (w .* J))
-  g.M = p; g.N = p; g.K = ctx->N;
-  g.A = (const T*)ctx->J; g.sam = 1; g.sak = ctx->ldJ;
-  g.B = ctx->Zfull; g.sbk = ctx->ldJ; g.sbn = 1;
-  g.out64 = ctx->Gfull; g.scm = 1; g.scn = ldG;
-  g.lower = 1;
-  launch_gemm_df<T, double>(g, st);
+  TRY(form_gramian<T>(ctx, ctx->Gfull, ldG));
   launch_lower_to_upper(ctx->Gfull, p, ldG, st);
   launch_copy_diag(ctx->Gfull, p, ldG, ctx->x, st);          // x: scratch for diag(G)
   launch_add_diag_dev(ctx->Gfull, p, ldG, ctx->scal + kSMu, st);
@@ -1916,6 +1941,22 @@ ngd_status ngd_gramian_mm(ngd_ctx* ctx, const double* theta, int ell, const void
     else
       CK(cudaMemcpy2DAsync(Y, (size_t)ldY * sizeof(T), ctx->Y, sp, w, ell, cudaMemcpyDeviceToDevice, ctx->stream));
     return check_launch(ctx);
+  });
+}
+
+ngd_status ngd_gramian_full(ngd_ctx* ctx, const double* theta, double* G, int64_t ldG) {
+  if (!ctx) return NGD_ERR_INVALID_ARG;
+  if (!G || ldG < ctx->p) return set_err(ctx, NGD_ERR_INVALID_ARG, "G is NULL or ldG < p%s");
+  if (!ctx->stored_j) return set_err(ctx, NGD_ERR_UNSUPPORTED, "the explicit Gramian needs the stored Jacobian%s");
+  return by_dtype(ctx, [&](auto z) -> ngd_status {
+    using T = decltype(z);
+    if (theta) TRY(linearize<T>(ctx, theta));
+    if (!ctx->lin_valid) return set_err(ctx, NGD_ERR_INVALID_ARG, "no linearization: pass theta%s");
+    TRY(clear_status(ctx));
+    TRY(form_gramian<T>(ctx, G, ldG));
+    launch_lower_to_upper(G, ctx->p, ldG, ctx->stream);
+    TRY(check_launch(ctx));
+    return sync_status(ctx);
   });
 }
 

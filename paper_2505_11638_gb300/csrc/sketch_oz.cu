@@ -171,18 +171,98 @@ __global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t col
   }
 }
 
+// ---------------------------------------------------------------------------- Gramian operands
+// For G = J^T diag(w) J: column maxima of |J| and of |w_n J_nj| over the points (row blocks of J
+// in blockIdx.y, combined by atomicMax on the bit patterns of non-negative doubles, which order as
+// the values do).  The second maximum is formed in FP32 with w rounded to FP32 and enlarged by
+// 2^-20 of itself, an upper bound of the exact one.
+__global__ void k_oz_gram_colmax(const float* __restrict__ J, int64_t ldJ, int64_t N, const double* __restrict__ w,
+                                 int64_t rows_per, unsigned long long* __restrict__ mj,
+                                 unsigned long long* __restrict__ mw) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ldJ) return;
+  const int64_t n0 = (int64_t)blockIdx.y * rows_per, n1 = min(N, n0 + rows_per);
+  float a = 0.f, b = 0.f;
+  for (int64_t n = n0; n < n1; ++n) {
+    const float x = fabsf(J[n * ldJ + j]);
+    a = fmaxf(a, x);
+    b = fmaxf(b, x * fabsf(f64_to_f32_rn(w[n])));
+  }
+  atomicMax(mj + j, (unsigned long long)__double_as_longlong((double)a));
+  atomicMax(mw + j, (unsigned long long)__double_as_longlong((double)b * (1.0 + 0x1p-20)));
+}
+
+__global__ void k_oz_gram_exp(const unsigned long long* __restrict__ mj, const unsigned long long* __restrict__ mw,
+                              int64_t n, int* __restrict__ ej, int* __restrict__ ew) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  ej[j] = exp_above_d(__longlong_as_double((long long)mj[j]));
+  ew[j] = exp_above_d(__longlong_as_double((long long)mw[j]));
+}
+
+// Digit planes of the column-scaled J^T and (diag(w) J)^T, both p-major with the points
+// contiguous (AT[s] and BT[s]: ldJ x ldN, columns n >= N zero), kDigG digits each: A from the FP32
+// J (exact steps in FP32), B from the FP64 products w_n J_nj (steps in FP64).  32 x 32 tiles,
+// transposed through shared memory.
+constexpr int kDigG = 6;
+
+__global__ void k_oz_split_gram(const float* __restrict__ J, int64_t ldJ, int64_t N, const double* __restrict__ w,
+                                const int* __restrict__ ej, const int* __restrict__ ew,
+                                __nv_bfloat16* __restrict__ AT, __nv_bfloat16* __restrict__ BT, int64_t ldN) {
+  __shared__ __nv_bfloat16 ta[kDigG][32][34], tb[kDigG][32][34];
+  const int64_t j0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t j = j0 + tx;
+  const int ea = ej[j], eb = ew[j];
+  for (int i = ty; i < 32; i += blockDim.y) {
+    const int64_t n = n0 + i;
+    float ra = 0.f;
+    double rb = 0.0;
+    if (n < N) {
+      const float x = J[n * ldJ + j];
+      ra = x * __int_as_float((127 + 7 - ea) << 23);      // |ra| < 128, exact
+      rb = (w[n] * (double)x) * __longlong_as_double((long long)(1023 + 7 - eb) << 52);   // |rb| < 128
+    }
+#pragma unroll
+    for (int s = 0; s < kDigG; ++s) {
+      const float a = rintf(ra);
+      ra = (ra - a) * 256.0f;                             // exact
+      const double b = rint(rb);
+      rb = (rb - b) * 256.0;                              // exact
+      const float sc = __int_as_float((127 - 8 * s) << 23);
+      ta[s][i][tx] = __float2bfloat16_rn(a * sc);         // integers of magnitude <= 128: exact
+      tb[s][i][tx] = __float2bfloat16_rn(f64_to_f32_rn(b) * sc);
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += blockDim.y) {
+    const int64_t jj = j0 + i, n = n0 + tx;
+#pragma unroll
+    for (int s = 0; s < kDigG; ++s) {
+      AT[(int64_t)s * ldJ * ldN + jj * ldN + n] = ta[s][tx][i];
+      BT[(int64_t)s * ldJ * ldN + jj * ldN + n] = tb[s][tx][i];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------- digit-plane GEMM
 // Accumulator of the level s + t: levels 0..3 exact, levels 4.. shared (TMEM columns acc * kBN).
 __host__ __device__ constexpr int acc_of(int level) { return level < 4 ? level : 4; }
 
 // Shared-memory plan of the digit-plane GEMM: a ring of RB = 2 SB B-tile slots (two k-blocks of B
-// digit tiles) and a ring of RA A-tile slots, as many as fit.
-template <int SB>
+// digit tiles) and a ring of RA A-tile slots, as many as fit (at most 8).  When one k-block of A
+// tiles does not fit beside two of B (SA = SB = 6), A gets one k-block and B every slot left
+// (RB >= SB): the MMA issuer frees B tiles highest digit first, the order in which the producer
+// refills them, so the next k-block's B tiles land in slots freed before the current one ends.
+template <int SA, int SB>
 struct OzSmem {
-  static constexpr int RB = 2 * SB;
   static constexpr int kLimit = 232448;                                    // 227 KB per block
   static constexpr int kFixed = 1024 + 1024;                               // alignment, barriers
-  static constexpr int RA0 = (kLimit - kFixed - RB * kTileB) / kTile;
+  static constexpr int kAvail = kLimit - kFixed;
+  static constexpr bool kTwoB = kAvail - 2 * SB * kTileB >= SA * kTile;
+  static constexpr int RB0 = (kAvail - SA * kTile) / kTileB;
+  static constexpr int RB = kTwoB ? 2 * SB : (RB0 > 2 * SB ? 2 * SB : RB0);
+  static constexpr int RA0 = (kAvail - RB * kTileB) / kTile;
   static constexpr int RA = RA0 > 8 ? 8 : RA0;
   static constexpr int bytes = RA * kTile + RB * kTileB + kFixed;
 };
@@ -204,7 +284,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
                                                           float2* __restrict__ P, int64_t ldL, int64_t ldM,
                                                           int* status, long long wait_cycles) {
   static_assert(SB - 1 <= kLevels && SA - 1 <= kLevels, "every digit plane takes part in a kept pair");
-  using SP = OzSmem<SB>;
+  using SP = OzSmem<SA, SB>;
   constexpr int RA = SP::RA, RB = SP::RB;
   // a k-block's tiles fit the rings together: a tile only waits for a slot of an earlier k-block,
   // which the MMA issuer can always finish (no circular wait)
@@ -412,7 +492,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
 // Sum of the partials of chunks [0, nc) of output (m, j) in chunk order (double-float), added to
 // the running sum acc when !first, stored back to acc when !last; when last, scaled and written as
 // float64: MODE 1 (Z'' = diag(w) diag(2^e) J Omega): out[j * ldOut + m] = w_m 2^(2 e_m + f_j - 14)
-// v; MODE 2 (Y): out[j * ldOut + m] = 2^(f_j - 14) v.  Rows M <= m < ldOut are written as zero.
+// v; MODE 2 (Y): out[j * ldOut + m] = 2^(f_j - 14) v; MODE 3 (a product of a row-scaled and a
+// column-scaled operand): out[j * ldOut + m] = 2^(e_m + f_j - 14) v.  Rows M <= m < ldOut are
+// written as zero.
 template <int MODE>
 __global__ void k_oz_reduce(const float2* __restrict__ P, int nc, int64_t ldL, int64_t ldM, float2* __restrict__ acc,
                             int first, int last, int64_t M, int64_t ldOut, const int* __restrict__ rexp,
@@ -440,8 +522,10 @@ __global__ void k_oz_reduce(const float2* __restrict__ P, int nc, int64_t ldL, i
   const double x = f32_to_f64(v.hi) + f32_to_f64(v.lo);
   if (MODE == 1)
     out[j * ldOut + m] = w[m] * ldexp(x, 2 * rexp[m] + cexp[j] - 14);
-  else
+  else if (MODE == 2)
     out[j * ldOut + m] = ldexp(x, cexp[j] - 14);
+  else
+    out[j * ldOut + m] = ldexp(x, rexp[m] + cexp[j] - 14);
 }
 
 }  // namespace
@@ -453,6 +537,11 @@ struct OzSketch {
   int *jexp = nullptr, *oexp = nullptr, *zexp = nullptr;
   size_t jexp_b = 0, oexp_b = 0, zexp_b = 0;
   double* Zs = nullptr;   size_t Zs_b = 0;     // Z'' transposed: ell x ldN
+  // the Gramian's operands (column-scaled J^T and (diag(w) J)^T digit planes) and exponents
+  __nv_bfloat16 *GA = nullptr, *GB = nullptr;
+  size_t GA_b = 0, GB_b = 0;
+  int* gexp = nullptr;    size_t gexp_b = 0;   // 2 ldJ: exponents of J's and of diag(w) J's columns
+  unsigned long long* gmax = nullptr; size_t gmax_b = 0;
   float2* part = nullptr; size_t part_b = 0;   // split-K partials of one launch
   float2* acc = nullptr;  size_t acc_b = 0;    // running sums across launches
   // the Jacobian the digit planes were made from
@@ -475,21 +564,21 @@ cudaError_t grow(P** p, size_t* cap, size_t bytes) {
 }
 
 // D[m, n] = sum over kept digit pairs for an M x Nout output and K columns, into out (float64,
-// MODE as k_oz_reduce).  Split-K over chunks of kChunk; launches of at most kPartialCap bytes of
+// MODE as k_oz_reduce).  Split-K over chunks of kChunk; launches of at most partial_cap bytes of
 // partials, their sums carried in the running double-float sums.
 template <int SA, int SB, int MODE>
 cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMap& tmB, int64_t M, int64_t Nout,
                            int64_t K, const int* rexp, const int* cexp, const double* w, double* out, int64_t ldOut,
-                           int* status, cudaStream_t s, long long wait_cycles) {
+                           int* status, cudaStream_t s, long long wait_cycles, size_t partial_cap = kPartialCap) {
   const int64_t ldL = rup(Nout, kBN), ldM = rup(M, kBM);
   const int64_t nchunks = (K + kChunk - 1) / kChunk;
   const size_t chunk_bytes = (size_t)ldL * ldM * sizeof(float2);
-  const int64_t per_launch = std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)(kPartialCap / chunk_bytes)));
+  const int64_t per_launch = std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)(partial_cap / chunk_bytes)));
   cudaError_t e;
   if ((e = grow(&o->part, &o->part_b, chunk_bytes * per_launch)) != cudaSuccess) return e;
   if (per_launch < nchunks && (e = grow(&o->acc, &o->acc_b, chunk_bytes)) != cudaSuccess) return e;
   auto kern = k_oz_gemm<SA, SB>;
-  constexpr int smem = OzSmem<SB>::bytes;
+  constexpr int smem = OzSmem<SA, SB>::bytes;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   int dev = 0, nsm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -516,7 +605,8 @@ OzSketch* oz_create() { return new (std::nothrow) OzSketch(); }
 
 void oz_destroy(OzSketch* o) {
   if (!o) return;
-  void* bufs[] = {o->JD, o->JDT, o->OD, o->ZD, o->jexp, o->oexp, o->zexp, o->Zs, o->part, o->acc};
+  void* bufs[] = {o->JD, o->JDT, o->OD, o->ZD, o->jexp, o->oexp, o->zexp, o->Zs, o->part, o->acc,
+                  o->GA, o->GB, o->gexp, o->gmax};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete o;
@@ -590,6 +680,51 @@ cudaError_t oz_sketch(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64
   // GEMM2: Y = J^T Z''
   return run_digit_gemm<kDigJ, kDigZ, 2>(o, mA2, mB2, p, ell, ldN, nullptr, o->zexp, nullptr, Y64, ldY, status, s,
                                          wait_cycles);
+}
+
+cudaError_t oz_gram(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64_t p, const double* w, double* G,
+                    int64_t ldG, const char** why, cudaStream_t s, int* status, long long wait_cycles) {
+  *why = nullptr;
+  if (!tensor_map_encoder()) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  if ((ldJ % 32) || N < 1 || p < 1 || ldG < p) {
+    *why = "the Jacobian's leading dimension must be a multiple of 32";
+    return cudaSuccess;
+  }
+  const int64_t ldN = rup(N, 32);
+  cudaError_t e;
+  if ((e = grow(&o->GA, &o->GA_b, (size_t)kDigG * ldJ * ldN * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->GB, &o->GB_b, (size_t)kDigG * ldJ * ldN * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->gexp, &o->gexp_b, (size_t)2 * ldJ * sizeof(int))) != cudaSuccess) return e;
+  if ((e = grow(&o->gmax, &o->gmax_b, (size_t)2 * ldJ * sizeof(unsigned long long))) != cudaSuccess) return e;
+  int* ej = o->gexp;
+  int* ew = o->gexp + ldJ;
+  if ((e = cudaMemsetAsync(o->gmax, 0, (size_t)2 * ldJ * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  {
+    const int64_t rows_per = 256;
+    dim3 g((unsigned)((ldJ + 255) / 256), (unsigned)((N + rows_per - 1) / rows_per));
+    k_oz_gram_colmax<<<g, 256, 0, s>>>(J, ldJ, N, w, rows_per, o->gmax, o->gmax + ldJ);
+    note_launch();
+    k_oz_gram_exp<<<(unsigned)((ldJ + 255) / 256), 256, 0, s>>>(o->gmax, o->gmax + ldJ, ldJ, ej, ew);
+    note_launch();
+    dim3 blk(32, 8), grd((unsigned)(ldJ / 32), (unsigned)(ldN / 32));
+    k_oz_split_gram<<<grd, blk, 0, s>>>(J, ldJ, N, w, ej, ew, o->GA, o->GB, ldN);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  CUtensorMap mA, mB;
+  if (!make_tile_map(&mA, o->GA, 2, ldJ, ldN, ldN, kDigG, ldJ * ldN, kBM) ||
+      !make_tile_map(&mB, o->GB, 2, ldJ, ldN, ldN, kDigG, ldJ * ldN, kBN)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  // G[j', j] = 2^(e_j' + f_j - 14) sum over kept pairs of AT_s BT_t^T (all p x p entries)
+  // a p x p output: up to 8 GB of split-K partials per launch, so that the reduction passes over
+  // the output a few times rather than once per K chunk
+  return run_digit_gemm<kDigG, kDigG, 3>(o, mA, mB, p, p, ldN, ej, ew, nullptr, G, ldG, status, s, wait_cycles,
+                                         size_t(8) << 30);
 }
 
 }  // namespace ngd

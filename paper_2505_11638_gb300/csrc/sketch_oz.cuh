@@ -23,4 +23,12 @@ cudaError_t oz_sketch(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64
                       const float* Omega, int64_t ldY, int ell, const double* w, double* Y64, const char** why,
                       cudaStream_t s, int* status, long long wait_cycles);
 
+// G (p x p, column-major, leading dimension ldG >= p, float64) = J^T diag(w) J for the FP32
+// Jacobian J (N x ldJ row-major, zero columns p..ldJ-1): NGD full's Gramian by the same digit-plane
+// tensor-core GEMM, with J^T and (diag(w) J)^T split per column of J into six digits each (pairs
+// with s + t <= 5 kept; ~2^-46 of the term magnitudes).  Every entry of G is written (the upper
+// triangle is the transposed product, equal up to rounding).  *why / status as oz_sketch.
+cudaError_t oz_gram(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64_t p, const double* w, double* G,
+                    int64_t ldG, const char** why, cudaStream_t s, int* status, long long wait_cycles);
+
 }  // namespace ngd

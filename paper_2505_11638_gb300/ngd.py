@@ -93,6 +93,7 @@ _SIGS = {
     "ngd_nystrom_sketch": ([_P, _P, _I, _U64, _U64, _I, _P, _P], _I),
     "ngd_nystrom_sketch_sampled": ([_P, _P, _I, _U64, _U64, _I, _P, _P, _P], _I),
     "ngd_gramian_diag": ([_P, _P, _P], _I),
+    "ngd_gramian_full": ([_P, _P, _P, ctypes.c_int64], _I),
     "ngd_nystrom_factor": ([_P, _I, _P, _P, _I, _D, _P, _P, ctypes.POINTER(_D)], _I),
     "ngd_precond_apply": ([_P, _I, _P, _I, _P, _D, _P, _P], _I),
     "ngd_pcg_solve": ([_P, _P, _P, _D, _P, _I, _P, _I, _D, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
@@ -218,6 +219,11 @@ def ngd_nystrom_sketch_sampled(h, theta, ell, seed, step, prec, idx, Omega, Y):
     lib().ngd_set_stream(h, _stream())
     _check(h, lib().ngd_nystrom_sketch_sampled(h, _ptr(theta), int(ell), int(seed), int(step), SKETCH[prec],
                                                _ptr(idx), _ptr(Omega), _ptr(Y)))
+
+
+def ngd_gramian_full(h, theta, G, ldG):
+    """G (p x p column-major, ldG) = J^T diag(w) J at the linearization."""
+    _check(h, lib().ngd_gramian_full(h, _ptr(theta), _ptr(G), int(ldG)))
 
 
 def ngd_gramian_diag(h, theta, d):
@@ -389,6 +395,14 @@ class Context:
         if theta is not None:
             self.version += 1
         return idx, Om, Y
+
+    def gramian_full(self, theta):
+        """The explicit Gramian as a (p, p) float64 CUDA tensor (symmetric)."""
+        G = torch.empty((self.p, self.p), dtype=torch.float64, device=self.device)
+        ngd_gramian_full(self.handle, theta, G, self.p)
+        if theta is not None:
+            self.version += 1
+        return G
 
     def gramian_diag(self, theta):
         d = self._vec(self.p)

@@ -297,3 +297,31 @@ def test_matrix_free_vjp_heat_width_256(ngd, dtype, tol):
         y = host(ctx.gramian_mv(dev(th), dev(v), 1e-3))
         assert rel(y, y_o) <= (1e-10 if dtype == "f64" else 1e-5), (budget, rel(y, y_o))
         ctx.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-11), ("f64", 2e-11)])
+def test_gramian_full_matches_oracle(ngd, dtype, tol):
+    """The explicit Gramian NGD full factors (ngd_gramian_full) on a Jacobian handed to both sides:
+    the FP32 context forms it on the tensor cores from six-digit BF16 planes of the column-scaled
+    J^T and (diag(w) J)^T, the FP64 context by the double-float GEMM on the lower triangle; the
+    oracle computes J^T diag(w) J of the same J in FP64.  p = 1217 (10 x 13 output tiles, the last
+    ragged), N = 1800 (eight K chunks of 256, the last ragged).  Each entry is bounded against
+    sqrt(G_jj G_kk) (Cauchy-Schwarz: the scale of the entry's terms), the whole matrix in norm, and
+    the result must be symmetric.  Bounds: the digit planes keep ~2^-46 of a column's largest
+    term; the double-float GEMM holds FP64 operands as FP32 pairs (48 bits), ~2^-44 per product,
+    so 1800 terms of random sign leave a few 1e-12 in the largest of 1.5e6 entries."""
+    pr, th = inputs.small_problem(d=3, widths=[3, 32, 32, 1], n_int=1500, n_bnd=300, seed=97)
+    assert th.size == 1217 and pr.n == 1800
+    J = mlp.jacobian(pr, th)
+    Jd = round32(J) if dtype == "f32" else J
+    ctx = ngd.Context(pr, dtype=dtype)
+    ctx.residual(dev(th))
+    ctx.set_jacobian(dev(Jd, torch.float32 if dtype == "f32" else torch.float64))
+    G = host(ctx.gramian_full(None))
+    G_o = Jd.T @ (pr.w[:, None] * Jd)
+    dg = np.sqrt(np.diag(G_o))
+    err = np.abs(G - G_o) / np.maximum(np.outer(dg, dg), 1e-300)
+    assert err.max() <= tol, (err.max(), np.unravel_index(int(err.argmax()), err.shape))
+    assert rel(G, G_o) <= tol / 20
+    assert np.array_equal(G, G.T)
+    ctx.close()
