@@ -162,13 +162,14 @@ ngd_status sync_status(ngd_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   const int st = ctx->h_int[0];
-  if (st & kStatNotSpd) return set_err(ctx, NGD_ERR_NOT_SPD, "Nystrom core Omega^T Y_nu is not positive definite%s");
-  if (st & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
-  if (st & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value in a reduction%s");
+  // a timed-out kernel leaves its outputs unwritten: what later kernels report follows from that
   if (st & kStatTimeout)
     return set_err(ctx, NGD_ERR_TIMEOUT, (st & kStatDrain) ? "device wait timed out, and so did the drain of the work "
                                                               "already issued%s"
                                                             : "device wait timed out%s");
+  if (st & kStatNotSpd) return set_err(ctx, NGD_ERR_NOT_SPD, "Nystrom core Omega^T Y_nu is not positive definite%s");
+  if (st & kStatBreakdown) return set_err(ctx, NGD_ERR_BREAKDOWN, "CG breakdown: p^T (G + mu I) p <= 0%s");
+  if (st & kStatNonFinite) return set_err(ctx, NGD_ERR_NONFINITE, "non-finite value in a reduction%s");
   if (st & kStatSample)
     return set_err(ctx, NGD_ERR_INVALID_ARG, "fewer positive diagonal entries of G than the sample size ell%s");
   return NGD_OK;
@@ -570,15 +571,34 @@ int mantissa_bits(int prec) {
 bool acc64(int prec) { return prec == NGD_SKETCH_F64 || prec == NGD_SKETCH_DF; }
 
 template <typename T>
-ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell) {
+ngd_status thin_qr_inplace(ngd_ctx* ctx, T* Om, int ell, bool tc) {
   // CholeskyQR: Om <- Om R^{-1}, R = chol(Om^T Om)^T (positive diagonal).  A Gaussian p x ell
   // matrix has condition number about (1 + sqrt(ell / p)) / (1 - sqrt(ell / p)) (<= 5/3 for
   // ell <= p / 16), so one pass leaves Q^T Q - I at a few units of the working precision; wider
-  // test matrices take a second pass (CholeskyQR2).
+  // test matrices take a second pass (CholeskyQR2).  With tc (FP32 Omega) the Gram matrix comes
+  // FP64-accurate from the digit-plane tensor-core GEMM (its lower triangle, mirrored).
   const int passes = 16 * (int64_t)ell <= ctx->p ? 1 : 2;
   for (int pass = 0; pass < passes; ++pass) {
-    TRY(gram_atb<T>(ctx, Om, Om, ctx->p, ctx->ldP, ell, ctx->M));
-    launch_symmetrize(ctx->M, ell, ctx->stream);
+    bool done = false;
+    if (tc && std::is_same<T, float>::value) {
+      if (!ctx->oz) {
+        ctx->oz = oz_create();
+        if (!ctx->oz) return set_err(ctx, NGD_ERR_OOM, "tensor-core sketch state%s");
+      }
+      const char* why = nullptr;
+      const cudaError_t e = oz_gram_self32(ctx->oz, (const float*)Om, ctx->p, ctx->ldP, ell, ctx->M, ell, &why,
+                                           ctx->stream, ctx->status, ctx->wait_cycles);
+      if (e == cudaErrorMemoryAllocation) return set_err(ctx, NGD_ERR_OOM, "tensor-core sketch workspace%s");
+      CK(e);
+      if (!why) {
+        launch_mirror_lower(ctx->M, ell, ctx->stream);
+        done = true;
+      }
+    }
+    if (!done) {
+      TRY(gram_atb<T>(ctx, Om, Om, ctx->p, ctx->ldP, ell, ctx->M));
+      launch_symmetrize(ctx->M, ell, ctx->stream);
+    }
     CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));
     launch_trsm_lt<T>(Om, ctx->ldP, ctx->p, ell, ctx->M, (T*)ctx->Lr, ctx->stream);
   }
@@ -686,7 +706,7 @@ ngd_status sketch_internal(ngd_ctx* ctx, int ell, uint64_t seed, uint64_t step, 
     }
   } else {
     launch_philox_omega<T>(Om, ctx->ldP, ctx->p, ell, seed, step, ctx->stream);
-    TRY(thin_qr_inplace<T>(ctx, Om, ell));
+    TRY(thin_qr_inplace<T>(ctx, Om, ell, prec == NGD_SKETCH_F64));
   }
   return sketch_product<T>(ctx, ell, prec);
 }
@@ -814,10 +834,36 @@ ngd_status sketch_product(ngd_ctx* ctx, int ell, int prec) {
 }
 
 // Factor of an FP64-accurate sketch in an FP32 context: Omega FP32 (exact values), Y, B and U in
-// FP64, products by the double-float GEMM.  U stays FP64: the apply of Alg. 4 scales the top
+// FP64.  The products Omega^T Y_nu, B^T B and U = B V Sigma^{-1} by the digit-plane tensor-core
+// GEMM with the tensor-core sketch (prec NGD_SKETCH_F64), by the double-float GEMM otherwise.  U stays FP64: the apply of Alg. 4 scales the top
 // directions by (lam_ell + mu) / (lam_1 + mu), ~1e-7 at later steps of the 5-D Poisson problem, a
 // value formed by cancellation in I - U U^T that an FP32-rounded U perturbs by its own rounding.
-ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
+// Lower triangle of C (ell x ell) = A^T B for the p x ell column-major operands (A = Omega in
+// FP32, or A = B when Om is null) on the tensor cores; false when that path cannot serve.
+bool oz_factor_gram(ngd_ctx* ctx, const float* Om, const double* B, int ell, double* C, ngd_status* st) {
+  *st = NGD_OK;
+  if (!ctx->oz) {
+    ctx->oz = oz_create();
+    if (!ctx->oz) {
+      *st = set_err(ctx, NGD_ERR_OOM, "tensor-core sketch state%s");
+      return true;
+    }
+  }
+  const char* why = nullptr;
+  const cudaError_t e = oz_gram_cols(ctx->oz, Om, B, ctx->p, ctx->ldP, ell, C, ell, &why, ctx->stream, ctx->status,
+                                     ctx->wait_cycles);
+  if (e == cudaErrorMemoryAllocation) {
+    *st = set_err(ctx, NGD_ERR_OOM, "tensor-core factor workspace%s");
+    return true;
+  }
+  if (e != cudaSuccess) {
+    *st = set_err(ctx, NGD_ERR_CUDA, "CUDA: %s", cudaGetErrorString(e));
+    return true;
+  }
+  return why == nullptr;
+}
+
+ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale, int prec) {
   const float* Om = (const float*)ctx->Om;
   double* Bm = ctx->B64;
   const int64_t p = ctx->p, ld = ctx->ldP;
@@ -826,7 +872,9 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
   // the double-float format carries 48 significant bits: nu = eps_48(||Y||_F)
   launch_compute_nu(ctx->scal + kSFrob2, 48, shift_scale, ctx->scal + kSNu, ctx->stream);
   launch_shift_add_mixed(ctx->Y64, Om, ctx->scal + kSNu, Bm, ld, p, ell, ctx->stream);      // Y_nu
-  {
+  const bool tc = prec == NGD_SKETCH_F64;
+  ngd_status st = NGD_OK;
+  if (!(tc && oz_factor_gram(ctx, Om, Bm, ell, ctx->M, &st))) {
     GemmDfArgs<float, double> g;                                                           // Omega^T Y_nu
     g.M = ell; g.N = ell; g.K = p;
     g.A = Om; g.sam = ld; g.sak = 1;
@@ -840,10 +888,11 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
     launch_gemm_df<float, double>(g, ctx->stream);
     launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, ctx->M, ctx->stream);
   }
+  TRY(st);
   launch_mirror_lower(ctx->M, ell, ctx->stream);
   CK(launch_cholesky(ctx->M, ell, ctx->status, ctx->stream));                                // = L L^T
   launch_trsm_lt<double>(Bm, ld, p, ell, ctx->M, (double*)ctx->eigws, ctx->stream);  // B = Y_nu L^{-T}
-  {
+  if (!(tc && oz_factor_gram(ctx, nullptr, Bm, ell, ctx->V, &st))) {
     GemmDfArgs<double, double> g;                                                          // S = B^T B
     g.M = ell; g.N = ell; g.K = p;
     g.A = Bm; g.sam = ld; g.sak = 1;
@@ -857,10 +906,20 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
     launch_gemm_df<double, double>(g, ctx->stream);
     launch_sum_splits(ctx->gpart, nz, (int64_t)ell * ell, (int64_t)ell * ell, ctx->V, ctx->stream);
   }
+  TRY(st);
   launch_mirror_lower(ctx->V, ell, ctx->stream);
   CK(launch_sym_eig(ctx->V, ell, ctx->sig2, ctx->M, ctx->eigws, ctx->status, ctx->stream, ctx->dtype == NGD_F32));
   launch_nystrom_lambda(ctx->sig2, ctx->scal + kSNu, ell, ctx->lam, ctx->inv_sigma, ctx->stream);
-  {
+  bool u_done = false;
+  if (tc) {                                                                                // U = B V Sigma^{-1}
+    const char* why = nullptr;
+    const cudaError_t e = oz_gemm_bw(ctx->oz, Bm, ld, p, ell, ctx->M, ell, ctx->inv_sigma, ctx->U64, ld, &why,
+                                     ctx->stream, ctx->status, ctx->wait_cycles);
+    if (e == cudaErrorMemoryAllocation) return set_err(ctx, NGD_ERR_OOM, "tensor-core factor workspace%s");
+    CK(e);
+    u_done = why == nullptr;
+  }
+  if (!u_done) {
     GemmDfArgs<double, double> g;                                                          // U = B V Sigma^{-1}
     g.M = p; g.N = ell; g.K = ell;
     g.A = Bm; g.sam = 1; g.sak = ld;
@@ -876,7 +935,7 @@ ngd_status factor_df(ngd_ctx* ctx, int ell, double shift_scale) {
 template <typename T>
 ngd_status factor_internal(ngd_ctx* ctx, int ell, int prec, double shift_scale) {
   TRY(ensure_ell(ctx, ell));
-  if (std::is_same<T, float>::value && acc64(prec)) return factor_df(ctx, ell, shift_scale);
+  if (std::is_same<T, float>::value && acc64(prec)) return factor_df(ctx, ell, shift_scale, prec);
   const T* Om = (const T*)ctx->Om;
   const T* Y = (const T*)ctx->Y;
   T* Bm = (T*)ctx->B;
@@ -1101,9 +1160,9 @@ ngd_status power_lambda1(ngd_ctx* ctx, uint64_t seed, uint64_t step) {
 }
 
 // Lower triangle of G = J^T diag(w) J (p x p, column-major, ldG) at the current linearization
-// (stored J), FP64-accurate: for an FP32 Jacobian by the digit-plane tensor-core GEMM (which writes
-// every entry), otherwise w .* J in FP64 (ctx->Zfull) and the double-float GEMM on the lower
-// triangle.
+// (stored J), FP64-accurate: for an FP32 Jacobian by the digit-plane tensor-core GEMM on the tiles
+// of the lower triangle, otherwise w .* J in FP64 (ctx->Zfull) and the double-float GEMM on the
+// lower triangle.
 template <typename T>
 ngd_status form_gramian(ngd_ctx* ctx, double* G, int64_t ldG) {
   const int64_t p = ctx->p;
@@ -1173,7 +1232,7 @@ ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
       CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
     CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (!(ctx->h_int[0] & kStatNotSpd)) break;
+    if (!(ctx->h_int[0] & kStatNotSpd) || (ctx->h_int[0] & kStatTimeout)) break;
     if (attempt + 1 >= kShiftAttempts)
       return set_err(ctx, NGD_ERR_NOT_SPD, "NGD full: G + mu I is not positive definite up to 8^5 mu%s");
     TRY(clear_status(ctx));
@@ -1268,6 +1327,7 @@ ngd_status rpchol_build(ngd_ctx* ctx, const ngd_step_opts* o, int* ell_pc, int* 
     CK(launch_cholesky(ctx->M, nsel, ctx->status, st));
     CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (ctx->h_int[0] & kStatTimeout) return sync_status(ctx);
     if (ctx->h_int[0] & kStatNotSpd) {
       CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
       break;

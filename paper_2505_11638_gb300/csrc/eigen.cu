@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kSectThreads) k_multisect(const double* __rest
 // above FP32's safe minimum times max(1, max e^2) (LAPACK's pivmin rule, so e^2 / q stays
 // finite), each division an FP32 reciprocal refined by one double-float step.  No rescaling is
 // needed, the chain is tens of FP32-pipe cycles per step instead of the FP64 pipe's issue-bound
-// three operations, and each lane evaluates four points (128 per eigenvalue and step).
+// three operations, and each lane evaluates two points (64 per eigenvalue and step).
 namespace {
 
 __device__ __forceinline__ float rcp_approx(float x) {   // one MUFU operation, ~1 ulp
@@ -570,16 +570,40 @@ __global__ void __launch_bounds__(32) k_multisect_df(const double* __restrict__ 
   const double span = fmax(hi - lo, fmax(fabs(hi), fabs(lo)));
   const double atol = 2.0 * DBL_EPSILON * span + DBL_MIN;
   const double wfloor = DBL_EPSILON * DBL_EPSILON * span + 4.0 * DBL_MIN;
+  // Points per step: 32 P, two per lane (a warp's step then issues about as many instructions as
+  // the dependent chain of one point takes cycles).  While the bracket spans more than a factor of
+  // 4 (or holds zero) the points are spaced evenly in s(x) = sign(x) log2(1 + |x| / wfloor), i.e.
+  // geometrically above wfloor: a small eigenvalue of a wide spectrum is then located to a factor
+  // of ~3 in one step instead of shrinking the bracket by 32 P per step from ||T|| down.  Any
+  // increasing points refine the bracket (the counts are monotone in x); FP32 placement suffices
+  // while the bracket is that wide.
+  constexpr int P = 2;
+  constexpr int M = 32 * P;
+  const double inv_wf = 1.0 / wfloor;
   double a = lo - atol, b = hi + atol;
-  constexpr int P = 4;                                // points per lane, 128 per eigenvalue and step
   for (int it = 0; it < 160; ++it) {
     if (b - a <= fmax(2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)), wfloor)) break;
-    const double h = (b - a) * (1.0 / (32 * P + 1));
+    const bool wide = (a <= 0.0 && b >= 0.0) || (b - a > 4.0 * fmin(fabs(a), fabs(b)));
+    float sa = 0.f, ds_ = 0.f;
+    if (wide) {
+      sa = copysignf(log2f(1.f + (float)(fabs(a) * inv_wf)), (float)a);
+      const float sb = copysignf(log2f(1.f + (float)(fabs(b) * inv_wf)), (float)b);
+      ds_ = (sb - sa) * (1.f / (M + 1));
+    }
+    const double h = (b - a) * (1.0 / (M + 1));
+    double xv[P];
     DF x[P], q[P];
     int cnt[P];
 #pragma unroll
     for (int u = 0; u < P; ++u) {                     // point u * 32 + lane (ascending in the warp's order)
-      split_df((a + h * (u * 32 + lane + 1)) * tsc, x[u].hi, x[u].lo);
+      const int k = u * 32 + lane + 1;
+      if (wide) {
+        const float sk = sa + ds_ * k;
+        xv[u] = copysign(wfloor * (double)(exp2f(fabsf(sk)) - 1.f), (double)sk);
+      } else {
+        xv[u] = a + h * k;
+      }
+      split_df(xv[u] * tsc, x[u].hi, x[u].lo);
       q[u] = df_add(ds[0], df_neg(x[u]));
       if (fabsf(q[u].hi) < pivmin) q[u] = DF{-pivmin, 0.f};
       cnt[u] = q[u].hi < 0.f;
@@ -589,19 +613,29 @@ __global__ void __launch_bounds__(32) k_multisect_df(const double* __restrict__ 
 #pragma unroll
       for (int u = 0; u < P; ++u) pivot_step(dj, ej, x[u], q[u], cnt[u], pivmin);
     }
-    // first of the points (ascending) whose count exceeds i
-    int pt = 32 * P;
+    // first of the points (ascending) whose count exceeds i: lambda_i lies between it and the point
+    // before it (or a); none: above the last point
+    int pt = M;
 #pragma unroll
     for (int u = P - 1; u >= 0; --u) {
       const unsigned m = __ballot_sync(0xffffffffu, cnt[u] > i);
       if (m) pt = u * 32 + __ffs(m) - 1;
     }
-    if (pt == 32 * P) {
-      a = a + h * (32 * P);
+    const double x_last = __shfl_sync(0xffffffffu, xv[P - 1], 31);
+    if (pt == M) {
+      a = fmax(a, x_last);
     } else {
-      const double nb = a + h * (pt + 1);
-      a = pt == 0 ? a : a + h * pt;
-      b = nb;
+      const int u = pt >> 5, l = pt & 31;
+      double xb = xv[0], xa = xv[0];
+#pragma unroll
+      for (int w = 0; w < P; ++w) {
+        const double vb = __shfl_sync(0xffffffffu, xv[w], l);
+        const double va = __shfl_sync(0xffffffffu, xv[w], (l + 31) & 31);
+        if (w == u) xb = vb;
+        if (w == (l == 0 ? u - 1 : u)) xa = va;
+      }
+      if (pt > 0) a = fmax(a, xa);
+      b = fmin(b, xb);
     }
   }
   if (lane == 0) lam_asc[i] = 0.5 * (a + b);
@@ -941,6 +975,230 @@ __global__ void __launch_bounds__(32) k_backtransform_df(const double* __restric
   }
 }
 
+// Blocked form of the double-float back-transform: the reflectors in blocks of kWy (block b:
+// k = kWy b .. min(kWy b + kWy - 1, n - 3)), each block's product H_k0 H_k0+1 ... H_k1 written in
+// the compact WY form I - Y T Y^T (Schreiber and Van Loan, "A storage-efficient WY representation
+// for products of Householder transformations", SIAM J. Sci. Stat. Comput. 10 (1989)): column j
+// of Y is the reflector vector of H_k0+j (zero above row k0 + j + 1), T is upper triangular with
+// T_jj = tau_j and T[0:j, j] = -tau_j T[0:j, 0:j] (Y[:, 0:j]^T y_j).  A block then acts on a set of
+// columns X as X -= Y (T (Y^T X)): two small matrix products per kWy reflectors, where the
+// one-reflector form runs kWy dependent warp-wide dot products and updates.
+constexpr int kWy = 32;
+constexpr int kWyCols = 4;          // eigenvector columns per CTA of the apply kernel
+constexpr int kWyThreads = 512;
+constexpr int kWyTRows = 256;       // rows of Y per shared-memory chunk in k_wy_t
+
+// Rows [r0, r0 + rows) of block b's Y into Yc[rr][0..kWy) (row stride kWy + 1): entry (r, j) =
+// v_{k0+j}[r - k0 - j - 1] for r > k0 + j and j < nbk, else zero (so that the products need no
+// masks).  Consecutive threads read consecutive entries of one reflector; each thread issues eight
+// loads before it stores any (the L2 latency once per eight entries, not per entry).
+__device__ __forceinline__ void wy_load_rows(const float* __restrict__ VH, const float* __restrict__ VL, int n, int k0,
+                                             int nbk, int r0, int rows, DF* __restrict__ Yc, int tid, int nthr) {
+  constexpr int U = 8;
+  const int total = rows * kWy;
+  for (int base = tid; base < total; base += U * nthr) {
+    float h[U], l[U];
+    int dst[U];
+#pragma unroll
+    for (int t = 0; t < U; ++t) {
+      const int idx = base + t * nthr;
+      h[t] = 0.f;
+      l[t] = 0.f;
+      dst[t] = -1;
+      if (idx < total) {
+        const int j = idx / rows, rr = idx - j * rows, r = r0 + rr;
+        dst[t] = rr * (kWy + 1) + j;
+        if (j < nbk && r > k0 + j) {
+          const int64_t o = (int64_t)(k0 + j) * n + (r - k0 - j - 1);
+          h[t] = VH[o];
+          l[t] = VL[o];
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < U; ++t)
+      if (dst[t] >= 0) Yc[dst[t]] = DF{h[t], l[t]};
+  }
+}
+
+// T of every block: TH / TL [b][kWy][kWy] row-major (zero below the diagonal and past the block's
+// last reflector).  One CTA per block: S = Y^T Y (strict upper triangle, a thread per entry over
+// shared-memory chunks of Y's rows), then the recurrence for T by one warp (lane = row of T).
+__global__ void __launch_bounds__(512) k_wy_t(int n, const double* __restrict__ tau, const float* __restrict__ VH,
+                                              const float* __restrict__ VL, float* __restrict__ TH,
+                                              float* __restrict__ TL) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF* Yc = reinterpret_cast<DF*>(smem_raw);                 // [kWyTRows][kWy + 1]
+  __shared__ DF S[kWy][kWy + 1];
+  __shared__ DF T[kWy][kWy + 1];
+  const int b = blockIdx.x, k0 = b * kWy;
+  const int nbk = min(kWy, n - 2 - k0);
+  const int tid = threadIdx.x, lane = tid & 31;
+  // entry pi = j (j - 1) / 2 + i of the strict upper triangle (i < j): consecutive threads share j
+  const int npair = nbk * (nbk - 1) / 2;
+  int pj = 1, pii = tid;
+  while (pii >= pj) {
+    pii -= pj;
+    ++pj;
+  }
+  const bool has = tid < npair;
+  DF a0{0.f, 0.f}, a1{0.f, 0.f};
+  for (int r0 = k0 + 1; r0 < n; r0 += kWyTRows) {
+    const int rows = min(kWyTRows, n - r0);
+    __syncthreads();
+    wy_load_rows(VH, VL, n, k0, nbk, r0, rows, Yc, tid, blockDim.x);
+    __syncthreads();
+    if (has) {
+      int rr = 0;
+      for (; rr + 1 < rows; rr += 2) {
+        const DF x0 = Yc[rr * (kWy + 1) + pii], y0 = Yc[rr * (kWy + 1) + pj];
+        const DF x1 = Yc[(rr + 1) * (kWy + 1) + pii], y1 = Yc[(rr + 1) * (kWy + 1) + pj];
+        df_add_prod2(a0, x0.hi, x0.lo, y0.hi, y0.lo);
+        df_add_prod2(a1, x1.hi, x1.lo, y1.hi, y1.lo);
+      }
+      if (rr < rows) {
+        const DF x0 = Yc[rr * (kWy + 1) + pii], y0 = Yc[rr * (kWy + 1) + pj];
+        df_add_prod2(a0, x0.hi, x0.lo, y0.hi, y0.lo);
+      }
+    }
+  }
+  if (has) S[pii][pj] = df_add(a0, a1);
+  __syncthreads();
+  if (tid < 32) {
+    for (int c = 0; c < kWy; ++c) T[lane][c] = DF{0.f, 0.f};
+    __syncwarp();
+    for (int j = 0; j < nbk; ++j) {
+      float th, tl;
+      split_df(tau[k0 + j], th, tl);
+      DF v{th, tl};
+      if (lane < j) {
+        // -tau_j sum over l in [lane, j) of T[lane][l] S[l][j], four chains
+        DF c4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int l = lane; l < j; ++l) df_add_prod2(c4[(l - lane) & 3], T[lane][l].hi, T[lane][l].lo, S[l][j].hi, S[l][j].lo);
+        v = df_mul(df_add(df_add(c4[0], c4[1]), df_add(c4[2], c4[3])), -th, -tl);
+      }
+      __syncwarp();
+      if (lane <= j) T[lane][j] = v;
+      __syncwarp();
+    }
+    float* th_b = TH + (int64_t)b * kWy * kWy;
+    float* tl_b = TL + (int64_t)b * kWy * kWy;
+    for (int r = 0; r < kWy; ++r) {
+      th_b[r * kWy + lane] = T[r][lane].hi;
+      tl_b[r * kWy + lane] = T[r][lane].lo;
+    }
+  }
+}
+
+// Rows of Y a k_wy_apply chunk holds for n (shared memory: X, the chunk, the static arrays).
+__host__ __device__ inline int wy_apply_rows(int n) {
+  const int avail = (200 * 1024 - n * kWyCols * 8 - 11 * 1024) / ((kWy + 1) * 8);
+  return avail < n ? avail : n;
+}
+
+// V[:, c] = H_0 H_1 ... H_{n-3} Z[:, n-1-c] for the CTA's kWyCols columns c (X in shared memory as
+// double-float, row-major [n][kWyCols]), the blocks applied from the last to the first.  Per
+// block, over shared-memory chunks of Y's rows: W = Y^T X (four threads per entry of W, each over
+// every fourth row of the chunk), W2 = T W, X -= Y W2 (a thread per row); a chunk holding all the
+// block's rows serves both products.
+__global__ void __launch_bounds__(kWyThreads) k_wy_apply(const double* __restrict__ Z, int n,
+                                                         const float* __restrict__ VH, const float* __restrict__ VL,
+                                                         const float* __restrict__ TH, const float* __restrict__ TL,
+                                                         double* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF* X = reinterpret_cast<DF*>(smem_raw);                  // [n][kWyCols]
+  DF* Yc = X + (int64_t)n * kWyCols;                        // [RC][kWy + 1]
+  __shared__ DF W[kWy][kWyCols], W2[kWy][kWyCols];
+  __shared__ DF Ts[kWy][kWy + 1];
+  const int RC = wy_apply_rows(n);
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * kWyCols;
+  for (int idx = tid; idx < n * kWyCols; idx += kWyThreads) {
+    const int q = idx / n, r = idx - q * n;
+    float h = 0.f, l = 0.f;
+    if (c0 + q < n) split_df(Z[(int64_t)(n - 1 - c0 - q) * n + r], h, l);
+    X[r * kWyCols + q] = DF{h, l};
+  }
+  const int nblk = n >= 3 ? (n - 2 + kWy - 1) / kWy : 0;
+  // W entry (j, q) of this thread and its row residue
+  const int wo = tid >> 2, wj = wo / kWyCols, wq = wo % kWyCols, ws = tid & 3;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int k0 = b * kWy, nbk = min(kWy, n - 2 - k0);
+    const int rbeg = k0 + 1, nrow = n - rbeg;
+    const bool one_chunk = nrow <= RC;
+    __syncthreads();                                          // X of the previous block, Yc free
+    for (int idx = tid; idx < kWy * kWy; idx += kWyThreads)
+      Ts[idx / kWy][idx % kWy] = DF{TH[(int64_t)b * kWy * kWy + idx], TL[(int64_t)b * kWy * kWy + idx]};
+    DF acc{0.f, 0.f}, acc2{0.f, 0.f};
+    for (int r0 = rbeg; r0 < n; r0 += RC) {
+      const int rows = min(RC, n - r0);
+      if (r0 > rbeg) __syncthreads();
+      wy_load_rows(VH, VL, n, k0, nbk, r0, rows, Yc, tid, kWyThreads);
+      __syncthreads();
+      if (wo < kWy * kWyCols) {
+        int rr = ws;
+        for (; rr + 4 < rows; rr += 8) {
+          const DF y0 = Yc[rr * (kWy + 1) + wj], x0 = X[(r0 + rr) * kWyCols + wq];
+          const DF y1 = Yc[(rr + 4) * (kWy + 1) + wj], x1 = X[(r0 + rr + 4) * kWyCols + wq];
+          df_add_prod2(acc, y0.hi, y0.lo, x0.hi, x0.lo);
+          df_add_prod2(acc2, y1.hi, y1.lo, x1.hi, x1.lo);
+        }
+        if (rr < rows) {
+          const DF y0 = Yc[rr * (kWy + 1) + wj], x0 = X[(r0 + rr) * kWyCols + wq];
+          df_add_prod2(acc, y0.hi, y0.lo, x0.hi, x0.lo);
+        }
+      }
+    }
+    // the four threads of an entry are lanes 4o .. 4o + 3 of one warp
+    acc = df_add(acc, acc2);
+    acc = df_add(acc, shfl_xor_df(acc, 1));
+    acc = df_add(acc, shfl_xor_df(acc, 2));
+    if (ws == 0 && wo < kWy * kWyCols) W[wj][wq] = acc;
+    __syncthreads();
+    // W2 = T W (T upper triangular)
+    if (tid < kWy * kWyCols) {
+      const int j = tid / kWyCols, q = tid % kWyCols;
+      DF a0{0.f, 0.f}, a1{0.f, 0.f};
+      int i = j;
+      for (; i + 1 < nbk; i += 2) {
+        df_add_prod2(a0, Ts[j][i].hi, Ts[j][i].lo, W[i][q].hi, W[i][q].lo);
+        df_add_prod2(a1, Ts[j][i + 1].hi, Ts[j][i + 1].lo, W[i + 1][q].hi, W[i + 1][q].lo);
+      }
+      if (i < nbk) df_add_prod2(a0, Ts[j][i].hi, Ts[j][i].lo, W[i][q].hi, W[i][q].lo);
+      W2[j][q] = j < nbk ? df_add(a0, a1) : DF{0.f, 0.f};
+    }
+    __syncthreads();
+    // X[r] -= Y[r] W2 (Y's zeros above each reflector's start make the row's sum run over all kWy)
+    for (int r0 = rbeg; r0 < n; r0 += RC) {
+      const int rows = min(RC, n - r0);
+      if (!one_chunk) {
+        __syncthreads();
+        wy_load_rows(VH, VL, n, k0, nbk, r0, rows, Yc, tid, kWyThreads);
+        __syncthreads();
+      }
+      for (int rr = tid; rr < rows; rr += kWyThreads) {
+        DF s4[kWyCols];
+#pragma unroll
+        for (int q = 0; q < kWyCols; ++q) s4[q] = DF{0.f, 0.f};
+        const DF* yr = Yc + rr * (kWy + 1);
+        for (int j = 0; j < nbk; ++j) {
+          const DF y = yr[j];
+#pragma unroll
+          for (int q = 0; q < kWyCols; ++q) df_add_prod2(s4[q], y.hi, y.lo, W2[j][q].hi, W2[j][q].lo);
+        }
+        DF* xr = X + (int64_t)(r0 + rr) * kWyCols;
+#pragma unroll
+        for (int q = 0; q < kWyCols; ++q) xr[q] = df_add(xr[q], df_neg(s4[q]));
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * kWyCols; idx += kWyThreads) {
+    const int q = idx / n, r = idx - q * n;
+    if (c0 + q < n) V[(int64_t)(c0 + q) * n + r] = df_to_double(X[r * kWyCols + q]);
+  }
+}
+
 __global__ void k_add_diag(double* __restrict__ G, int n, double sh) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) G[i + (int64_t)i * n] += sh;
@@ -1141,7 +1399,24 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
     }
     note_launch();
   }
-  if (df_recurrences && n <= 32 * 32 + 1) {   // the longest reflector, n - 1 entries, within 32 NQ lanes
+  if (df_recurrences && n >= 64 && wy_apply_rows(n) >= 64) {
+    // blocked (compact WY) form: the reflectors as double-float pairs once (into the free L+ / U-
+    // scratch A), the blocks' T factors into the free LU scratch (nblk kWy^2 pairs <= n^2 doubles)
+    float* VH = reinterpret_cast<float*>(A);
+    float* VL = VH + nn;
+    launch_split_df(Vh, VH, VL, (int64_t)nn, (int64_t)nn, s);
+    const int nblk = (n - 2 + kWy - 1) / kWy;
+    float* TH = reinterpret_cast<float*>(LU);
+    float* TL = TH + (size_t)nblk * kWy * kWy;
+    const int tsm = kWyTRows * (kWy + 1) * (int)sizeof(DF);
+    cudaFuncSetAttribute((const void*)k_wy_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm);
+    k_wy_t<<<nblk, 512, tsm, s>>>(n, tau, VH, VL, TH, TL);
+    note_launch();
+    const size_t smem = ((size_t)n * kWyCols + (size_t)wy_apply_rows(n) * (kWy + 1)) * sizeof(DF);
+    cudaFuncSetAttribute((const void*)k_wy_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_wy_apply<<<(n + kWyCols - 1) / kWyCols, kWyThreads, smem, s>>>(Z, n, VH, VL, TH, TL, V);
+    note_launch();
+  } else if (df_recurrences && n <= 32 * 32 + 1) {   // the longest reflector, n - 1 entries, within 32 NQ lanes
     // the reflectors as double-float pairs once (into the free L+ / U- scratch), so that no warp
     // converts FP64 in its loop
     float* VH = reinterpret_cast<float*>(A);

@@ -655,9 +655,57 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-__device__ __forceinline__ double uniform52(uint32_t a, uint32_t b) {
-  const uint64_t m = ((((uint64_t)a) << 20) ^ (uint64_t)(b >> 12)) & ((1ull << 52) - 1ull);
-  return ((double)m + 0.5) * 0x1p-52;
+__device__ __forceinline__ uint64_t bits52(uint32_t a, uint32_t b) {
+  return ((((uint64_t)a) << 20) ^ (uint64_t)(b >> 12)) & ((1ull << 52) - 1ull);
+}
+
+__device__ __forceinline__ double uniform52(uint32_t a, uint32_t b) { return ((double)bits52(a, b) + 0.5) * 0x1p-52; }
+
+// N 2^e rounded to FP32 (nearest, ties to even) for 0 < N < 2^62, by integer operations (GB300
+// runs integer-to-float conversions of 64-bit values through its narrow FP64 pipe).
+__device__ __forceinline__ float u64_scaled_to_f32(uint64_t N, int e) {
+  const int top = 63 - __clzll((long long)N);              // N in [2^top, 2^(top+1))
+  uint32_t mant;
+  if (top > 23) {
+    const int sh = top - 23;
+    const uint64_t q = N >> sh, rem = N & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mant = (uint32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
+  } else {
+    mant = (uint32_t)(N << (23 - top));
+  }
+  int ex = top + e;
+  if (mant >> 24) {                                        // rounded up to 2^24
+    mant >>= 1;
+    ++ex;
+  }
+  return __uint_as_float((uint32_t)(ex + 127) << 23 | (mant & 0x7fffffu));
+}
+
+// One Box-Muller pair in FP32 arithmetic for an FP32 test matrix: u1 = (m1 + 1/2) 2^-52 and
+// u2 = (m2 + 1/2) 2^-52 as above; log u1 from the exact complement for u1 >= 1/2 (log1p of -(1 - u1),
+// so that u1 near 1 keeps its low bits), 2 pi u2 reduced exactly to a quadrant (the top two bits
+// of m2) plus (pi / 2) f, f in (0, 1), and f above 1/2 to its exact complement (sine and cosine
+// swapped), with FP32 sinpi / cospi of an argument in (0, 1/4].  Each value is within a few units
+// of FP32 rounding, relative to the pair's radius, of the FP64 pair.
+__device__ __forceinline__ void box_muller_f32(uint64_t m1, uint64_t m2, float& g0, float& g1) {
+  float L;
+  if (m1 >> 51) L = log1pf(-u64_scaled_to_f32(2ull * ((1ull << 52) - 1ull - m1) + 1ull, -53));
+  else L = logf(u64_scaled_to_f32(2ull * m1 + 1ull, -53));
+  const float rr = sqrtf(-2.f * L);
+  const int q = (int)(m2 >> 50);
+  const uint64_t F = 2ull * (m2 & ((1ull << 50) - 1ull)) + 1ull;   // f = F 2^-51
+  float sn, cs;                                            // sin, cos of (pi / 2) f
+  if (F >> 50) {                                           // f > 1/2: from the exact complement 1 - f
+    sincospif(0.5f * u64_scaled_to_f32((1ull << 51) - F, -51), &cs, &sn);
+  } else {
+    sincospif(0.5f * u64_scaled_to_f32(F, -51), &sn, &cs);
+  }
+  float c = cs, s = sn;                                    // cos, sin of q pi / 2 + (pi / 2) f
+  if (q == 1) { c = -sn; s = cs; }
+  else if (q == 2) { c = -cs; s = -sn; }
+  else if (q == 3) { c = sn; s = -cs; }
+  g0 = rr * c;
+  g1 = rr * s;
 }
 
 // Omega[i + j*ld] for i < p (rows 2m, 2m+1 from counter (m, j, step_lo, step_hi), key (seed_lo, seed_hi)).
@@ -671,13 +719,20 @@ __global__ void k_philox_omega(T* __restrict__ Om, int64_t ld, int64_t p, int el
     const int64_t m = t - (int64_t)j * npairs;
     const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)j, (uint32_t)step, (uint32_t)(step >> 32)),
                                   (uint32_t)seed, (uint32_t)(seed >> 32));
-    const double u1 = uniform52(x.x, x.y), u2 = uniform52(x.z, x.w);
-    const double rr = sqrt(-2.0 * log(u1));
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);
     T* col = Om + (int64_t)j * ld;
-    col[2 * m] = (T)(rr * cs);
-    if (2 * m + 1 < p) col[2 * m + 1] = (T)(rr * sn);
+    if constexpr (sizeof(T) == 4) {
+      float g0, g1;
+      box_muller_f32(bits52(x.x, x.y), bits52(x.z, x.w), g0, g1);
+      col[2 * m] = g0;
+      if (2 * m + 1 < p) col[2 * m + 1] = g1;
+    } else {
+      const double u1 = uniform52(x.x, x.y), u2 = uniform52(x.z, x.w);
+      const double rr = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      col[2 * m] = (T)(rr * cs);
+      if (2 * m + 1 < p) col[2 * m + 1] = (T)(rr * sn);
+    }
   }
 }
 

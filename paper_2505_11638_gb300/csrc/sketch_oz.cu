@@ -39,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <new>
 
 #include "df.cuh"
@@ -131,26 +132,81 @@ __global__ void k_oz_split_rows(const float* __restrict__ J, int64_t ldJ, int64_
 }
 
 // Column exponents of a column-major matrix V (rows x cols, leading dimension ld): one block per
-// column.
+// column; the maximum taken on the magnitudes' bit patterns (non-negative floats order as their
+// bits) in the integer pipes.
 template <typename T>
 __global__ void k_oz_colexp(const T* __restrict__ V, int64_t ld, int64_t rows, int* __restrict__ cexp) {
-  __shared__ double red[32];
-  const T* col = V + (int64_t)blockIdx.x * ld;
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) m = fmax(m, fabs((double)col[i]));
+  using U = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
+  constexpr U kAbs = sizeof(T) == 4 ? (U)0x7fffffffu : (U)0x7fffffffffffffffull;
+  __shared__ U red[32];
+  const U* col = reinterpret_cast<const U*>(V + (int64_t)blockIdx.x * ld);
+  U m = 0;
+#pragma unroll 4
+  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+    const U b = col[i] & kAbs;
+    m = b > m ? b : m;
+  }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o; o >>= 1) {
+    const U x = __shfl_xor_sync(0xffffffffu, m, o);
+    m = x > m ? x : m;
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x < 32) {
-    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (U)0;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) cexp[blockIdx.x] = exp_above_d(m);
+    for (int o = 16; o; o >>= 1) {
+      const U x = __shfl_xor_sync(0xffffffffu, m, o);
+      m = x > m ? x : m;
+    }
+    if (threadIdx.x == 0) {
+      if constexpr (sizeof(T) == 4) cexp[blockIdx.x] = exp_above(__uint_as_float(m));
+      else cexp[blockIdx.x] = exp_above_d(__longlong_as_double((long long)m));
+    }
   }
 }
 
-// Digit planes D[t] (cols x ld, the layout of V) of the column-scaled column-major V.
+// S digits of an FP64 value, on the integer pipes (GB300's FP64 pipe runs ~2 operations per cycle
+// and SM): r = x 2^(7 - e) (|r| <= 128) is rounded to the unit of the last digit, R = round(r
+// 2^(8 (S - 1))) (nearest, ties to even), straight from x's bit pattern, and R is written in
+// balanced base 256 from the lowest digit: a_s in [-128, 127] for s >= 1, |a_0| <= 128, and
+// sum a_s 2^(-8 s) = R 2^(-8 (S - 1)); the digits come back as floats (exact).  Zeros and
+// subnormal x give zero digits (a subnormal lies below 2^-1022, far under the last digit of any
+// column whose largest entry is normal); a non-finite x, or one at or above 2^e (not possible for
+// e from the column's maximum of finite entries), gives NaN digits, which the products carry on.
+template <int S>
+__device__ __forceinline__ void oz_digits_f64(double x, int e, float* af) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7ff);
+  const int k = 1075 - E - 7 + e - 8 * (S - 1);                            // R = m 2^-k
+  if (E == 0x7ff || (E != 0 && k < 1)) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) af[s] = __int_as_float(0x7fc00000);
+    return;
+  }
+  long long R = 0;
+  if (E != 0) {
+    const long long m = (bits & 0xfffffffffffffll) | 0x10000000000000ll;     // x = +-m 2^(E - 1075)
+    if (k < 63) {
+      R = m >> k;
+      const long long rem = m & ((1ll << k) - 1), half = 1ll << (k - 1);
+      if (rem > half || (rem == half && (R & 1))) ++R;
+    }
+    if (bits < 0) R = -R;
+  }
+#pragma unroll
+  for (int s = S - 1; s >= 1; --s) {
+    const int d = (int)((R + 128) & 255) - 128;
+    af[s] = (float)d;
+    R = (R - d) >> 8;                                                      // exact: R - d = 0 mod 256
+  }
+  af[0] = (float)R;
+}
+
+// Digit planes D[t] (cols x ld, the layout of V) of the column-scaled column-major V: for FP32 V
+// by FP32 steps (each digit the rounded remainder, the next the remainder times 256, exact), for
+// FP64 V on the integer pipes (oz_digits_f64).
 template <typename T, int S>
 __global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t cols, const int* __restrict__ cexp,
                                 __nv_bfloat16* __restrict__ D) {
@@ -159,15 +215,20 @@ __global__ void k_oz_split_cols(const T* __restrict__ V, int64_t ld, int64_t col
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += st) {
     const int64_t j = idx / ld;
     const int e = cexp[j];
-    T r = sizeof(T) == 4 ? (T)ldexpf((float)V[idx], 7 - e) : (T)ldexp((double)V[idx], 7 - e);
+    float af[S];
+    if constexpr (sizeof(T) == 4) {
+      float r = ldexpf((float)V[idx], 7 - e);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const T a = sizeof(T) == 4 ? (T)rintf((float)r) : (T)rint((double)r);
-      r = (r - a) * (T)256;                                               // exact
-      // a is an integer of magnitude <= 128: exact in FP32, and so is its scaling by 2^-8s
-      const float af = sizeof(T) == 4 ? (float)a : f64_to_f32_rn((double)a);
-      D[(int64_t)s * total + idx] = __float2bfloat16_rn(af * __int_as_float((127 - 8 * s) << 23));
+      for (int s = 0; s < S; ++s) {
+        af[s] = rintf(r);
+        r = (r - af[s]) * 256.0f;                                         // exact
+      }
+    } else {
+      oz_digits_f64<S>((double)V[idx], e, af);
     }
+#pragma unroll
+    for (int s = 0; s < S; ++s)   // an integer of magnitude <= 128 times 2^-8s: exact in BF16
+      D[(int64_t)s * total + idx] = __float2bfloat16_rn(af[s] * __int_as_float((127 - 8 * s) << 23));
   }
 }
 
@@ -202,8 +263,8 @@ __global__ void k_oz_gram_exp(const unsigned long long* __restrict__ mj, const u
 
 // Digit planes of the column-scaled J^T and (diag(w) J)^T, both p-major with the points
 // contiguous (AT[s] and BT[s]: ldJ x ldN, columns n >= N zero), kDigG digits each: A from the FP32
-// J (exact steps in FP32), B from the FP64 products w_n J_nj (steps in FP64).  32 x 32 tiles,
-// transposed through shared memory.
+// J (exact steps in FP32), B from the FP64 products w_n J_nj (digits on the integer pipes).
+// 32 x 32 tiles, transposed through shared memory.
 constexpr int kDigG = 6;
 
 __global__ void k_oz_split_gram(const float* __restrict__ J, int64_t ldJ, int64_t N, const double* __restrict__ w,
@@ -217,21 +278,22 @@ __global__ void k_oz_split_gram(const float* __restrict__ J, int64_t ldJ, int64_
   for (int i = ty; i < 32; i += blockDim.y) {
     const int64_t n = n0 + i;
     float ra = 0.f;
-    double rb = 0.0;
+    float b[kDigG];
     if (n < N) {
       const float x = J[n * ldJ + j];
       ra = x * __int_as_float((127 + 7 - ea) << 23);      // |ra| < 128, exact
-      rb = (w[n] * (double)x) * __longlong_as_double((long long)(1023 + 7 - eb) << 52);   // |rb| < 128
+      oz_digits_f64<kDigG>(w[n] * f32_to_f64(x), eb, b);  // |w_n J_nj 2^(7 - eb)| < 128
+    } else {
+#pragma unroll
+      for (int s = 0; s < kDigG; ++s) b[s] = 0.f;
     }
 #pragma unroll
     for (int s = 0; s < kDigG; ++s) {
       const float a = rintf(ra);
       ra = (ra - a) * 256.0f;                             // exact
-      const double b = rint(rb);
-      rb = (rb - b) * 256.0;                              // exact
       const float sc = __int_as_float((127 - 8 * s) << 23);
       ta[s][i][tx] = __float2bfloat16_rn(a * sc);         // integers of magnitude <= 128: exact
-      tb[s][i][tx] = __float2bfloat16_rn(f64_to_f32_rn(b) * sc);
+      tb[s][i][tx] = __float2bfloat16_rn(b[s] * sc);
     }
   }
   __syncthreads();
@@ -243,6 +305,74 @@ __global__ void k_oz_split_gram(const float* __restrict__ J, int64_t ldJ, int64_
       BT[(int64_t)s * ldJ * ldN + jj * ldN + n] = tb[s][tx][i];
     }
   }
+}
+
+// ---------------------------------------------------------------------------- row-scaled FP64 operand
+// For U = B W (B: p x ell column-major FP64, contracted over its columns): e_m of every row of B
+// (max over the row's ell entries).  Block (32, 8): 32 rows (coalesced), eight column residues,
+// the maximum taken on the magnitudes' bit patterns (non-negative doubles order as their bits) in
+// the integer pipes.
+__global__ void k_oz_rowexp_cm(const double* __restrict__ B, int64_t ldB, int64_t rows, int cols,
+                               int* __restrict__ rexp) {
+  __shared__ unsigned long long red[8][33];
+  const int64_t m = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  unsigned long long mx = 0;
+  if (m < rows) {
+#pragma unroll 4
+    for (int k = threadIdx.y; k < cols; k += 8) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(B[m + (int64_t)k * ldB]) & 0x7fffffffffffffffull;
+      mx = b > mx ? b : mx;
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && m < rows) {
+#pragma unroll
+    for (int y = 1; y < 8; ++y) mx = red[y][threadIdx.x] > mx ? red[y][threadIdx.x] : mx;
+    rexp[m] = exp_above_d(__longlong_as_double((long long)mx));
+  }
+}
+
+// Digit planes BT[s] (rows x ldK, K-major: row m's ell entries contiguous, k >= cols zero) of the
+// row-scaled B, kDigZ digits per entry on the integer pipes; 32 x 32 tiles transposed through
+// shared memory.
+__global__ void k_oz_split_rows_cm(const double* __restrict__ B, int64_t ldB, int64_t rows, int cols,
+                                   const int* __restrict__ rexp, __nv_bfloat16* __restrict__ BT, int64_t ldK) {
+  __shared__ __nv_bfloat16 tile[kDigZ][32][34];
+  const int64_t m0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 32; i += blockDim.y) {            // column k0 + i, rows m0 + tx (coalesced)
+    const int64_t m = m0 + tx;
+    const int k = k0 + i;
+    float a[kDigZ];
+    if (m < rows && k < cols) {
+      oz_digits_f64<kDigZ>(B[m + (int64_t)k * ldB], rexp[m], a);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kDigZ; ++q) a[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kDigZ; ++q)
+      tile[q][tx][i] = __float2bfloat16_rn(a[q] * __int_as_float((127 - 8 * q) << 23));
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += blockDim.y) {            // row m0 + i, entries k0 + tx (coalesced)
+    const int64_t m = m0 + i;
+    if (m >= rows) continue;
+#pragma unroll
+    for (int q = 0; q < kDigZ; ++q) BT[(int64_t)q * rows * ldK + m * ldK + k0 + tx] = tile[q][i][tx];
+  }
+}
+
+// Ws (cols x ldK, column j at Ws + j ldK) = W[:, j] * colscale[j] (W: rows x cols column-major,
+// leading dimension ldW), rows rows..ldK-1 zero.
+__global__ void k_oz_scale_pad(const double* __restrict__ W, int64_t ldW, int rows, int cols,
+                               const double* __restrict__ colscale, double* __restrict__ Ws, int64_t ldK) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)cols * ldK) return;
+  const int64_t j = idx / ldK, k = idx - j * ldK;
+  Ws[idx] = k < rows ? W[k + j * ldW] * colscale[j] : 0.0;
 }
 
 // ---------------------------------------------------------------------------- digit-plane GEMM
@@ -270,18 +400,78 @@ struct OzSmem {
 constexpr int kEpiWarps = 8;                       // two warps per TMEM lane quarter
 constexpr int kOzThreads = 32 * (2 + kEpiWarps);
 
-// Split-K partials of D = sum over kept (s, t) of A_s B_t^T.  A planes (tmA: cols = K, rows = M,
-// planes = SA), B planes (tmB: cols = K, rows = Nout, planes = SB), both K-major.  Work item =
-// (Nout tile, M tile, chunk of this launch), item = nt + n_tiles (mt + m_tiles c); the persistent
-// CTAs take items blockIdx.x, blockIdx.x + gridDim.x, ...  Partial (hi, lo) of output (m, n) of
-// local chunk c at P[(c * ldL + n) * ldM + m].  While the epilogue warps drain one item's
-// accumulators, the producer already loads the next item's tiles; the MMA issuer waits for the
-// drain (accumulator-empty barrier) before it writes the accumulators again.
+// Work items of the digit-plane GEMM: output tiles of kBM x kBN (all of them, or for a symmetric
+// product only the tiles that hold an entry on or below the diagonal, m >= n) times K slices of
+// cps chunks, item = tile + tiles * slice.  Tiles are enumerated M-tile-major with the N tile
+// fastest, so that consecutive items (taken by neighbouring CTAs) share their A digit tiles.
+struct OzItems {
+  int n_tiles, m_tiles, tiles;   // tiles: number of enumerated tiles
+  int lower;                     // enumerate only tiles with an entry m >= n
+  int nks, cps;                  // K slices of this launch; chunks per slice
+  int chunk0, chunk_end;         // chunks [chunk0, chunk_end) of this launch
+};
+
+// Tiles of M-tile row mt that hold an entry m >= n.
+__host__ __device__ __forceinline__ int oz_lower_count(int mt, int n_tiles) {
+  const int c = ((mt + 1) * kBM - 1) / kBN + 1;
+  return c < n_tiles ? c : n_tiles;
+}
+
+__device__ __forceinline__ void oz_item(const OzItems& it, int item, int& mt, int& nt, int& ks, int& c_lo,
+                                        int& c_hi) {
+  int tile = item % it.tiles;
+  ks = item / it.tiles;
+  if (!it.lower) {
+    nt = tile % it.n_tiles;
+    mt = tile / it.n_tiles;
+  } else {
+    // item < tiles * nks, so the walk ends within the m_tiles rows
+    mt = 0;
+    for (int cnt = oz_lower_count(0, it.n_tiles); tile >= cnt; cnt = oz_lower_count(mt, it.n_tiles)) {
+      tile -= cnt;
+      ++mt;
+    }
+    nt = tile;
+  }
+  c_lo = it.chunk0 + ks * it.cps;
+  c_hi = c_lo + it.cps < it.chunk_end ? c_lo + it.cps : it.chunk_end;
+}
+
+// Final scaled output written by the epilogue itself (one K slice covering all of K):
+// out[n * ldOut + m] = 2^(rexp[m] + cexp[n] - 14) v for m < M, n < Nout (and m >= n when lower).
+struct OzDirect {
+  const int* rexp;
+  const int* cexp;
+  double* out;
+  int64_t ldOut, M, Nout;
+  int on;
+};
+
+// x 2^E for a double x built from an FP32 value (normal range), by integer exponent arithmetic
+// (GB300's FP64 pipe is narrow); ldexp where the result would leave the normal range.
+__device__ __forceinline__ double oz_scale(double x, int E) {
+  if (x == 0.0) return 0.0;
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff) + E;
+  if (ex < 1 || ex > 2046) return ldexp(x, E);
+  return __longlong_as_double(b + ((long long)E << 52));
+}
+
+// D = sum over kept (s, t) of A_s B_t^T.  A planes (tmA: cols = K, rows = M, planes = SA), B
+// planes (tmB: cols = K, rows = Nout, planes = SB), both K-major.  The persistent CTAs take items
+// blockIdx.x, blockIdx.x + gridDim.x, ...; an item runs the chunks of its K slice one after the
+// other through the TMEM accumulators, and the epilogue adds each chunk's double-float value to a
+// running sum (run: per CTA and epilogue thread, 48 float2, L2-resident) in chunk order.  At the
+// slice's last chunk the epilogue writes the slice's partial (hi, lo) of output (m, n) at
+// P[(slice * ldL + n) * ldM + m], or with d.on the scaled float64 output itself.  While the
+// epilogue warps drain one chunk's accumulators, the producer already loads the next chunk's
+// tiles; the MMA issuer waits for the drain (accumulator-empty barrier) before it writes the
+// accumulators again.
 template <int SA, int SB>
 __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB, int64_t K,
-                                                          int chunk0, int n_tiles, int m_tiles, int nchunk,
-                                                          float2* __restrict__ P, int64_t ldL, int64_t ldM,
+                                                          const OzItems it, float2* __restrict__ P, int64_t ldL,
+                                                          int64_t ldM, float2* __restrict__ run, const OzDirect d,
                                                           int* status, long long wait_cycles) {
   static_assert(SB - 1 <= kLevels && SA - 1 <= kLevels, "every digit plane takes part in a kept pair");
   using SP = OzSmem<SA, SB>;
@@ -303,7 +493,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = n_tiles * m_tiles * nchunk;
+  const int items = it.tiles * it.nks;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < RA; ++i) {
@@ -331,11 +521,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
     // ---------------------------------------------------------------- TMA producer
     int iA = 0, iB = 0;
     for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
-      const int nt = item % n_tiles, mt = (item / n_tiles) % m_tiles, c = item / (n_tiles * m_tiles);
-      const int64_t k0 = (int64_t)(chunk0 + c) * kChunk;
-      const int nkb = (int)(((K - k0 < kChunk ? K - k0 : kChunk) + kBK - 1) / kBK);
-      for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
-        const int x = (int)(k0 + (int64_t)kb * kBK);
+      int mt, nt, ks, c_lo, c_hi;
+      oz_item(it, item, mt, nt, ks, c_lo, c_hi);
+      // the k-blocks of the slice's chunks (every chunk but the last of K is kChunk long)
+      const int64_t k_end = (int64_t)c_hi * kChunk < K ? (int64_t)c_hi * kChunk : K;
+      for (int64_t x0 = (int64_t)c_lo * kChunk; x0 < k_end && !*abort_flag; x0 += kBK) {
+        const int x = (int)x0;
         for (int q = 0; q < SA + SB; ++q) {
           const bool isB = q < SB;
           const int i = isB ? iB : iA, R = isB ? RB : RA;
@@ -366,52 +557,55 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = make_idesc(1u, kBM, kBN);
-    int iA = 0, iB = 0, nitem = 0;
-    bool ok = true, pending = false;   // pending: MMAs of the current item not yet committed
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++nitem) {
-      const int c = item / (n_tiles * m_tiles);
-      const int64_t k0 = (int64_t)(chunk0 + c) * kChunk;
-      const int nkb = (int)(((K - k0 < kChunk ? K - k0 : kChunk) + kBK - 1) / kBK);
-      // the epilogue has read the previous item's accumulators
-      if (nitem > 0 && (*abort_flag || !mbar_wait(acc_empty, (nitem - 1) & 1, wait_cycles))) {
-        ok = false;
-        break;
-      }
-      fence_after();
-      uint32_t started = 0;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int b0 = iB;                       // B tile of digit t sits at counter b0 + SB - 1 - t
-        for (int q = 0; q < SB && ok; ++q, ++iB)
-          if (*abort_flag || !mbar_wait(&fullB[iB % RB], (iB / RB) & 1, wait_cycles)) ok = false;
-        for (int s = 0; s < SA && ok; ++s, ++iA) {
-          if (*abort_flag || !mbar_wait(&fullA[iA % RA], (iA / RA) & 1, wait_cycles)) {
-            ok = false;
-            break;
-          }
-          fence_after();
-          const uint64_t ad = make_desc(ringA + (iA % RA) * kTile);
-#pragma unroll
-          for (int t = 0; t < SB; ++t) {
-            if (s + t > kLevels) continue;
-            const int acc = acc_of(s + t);
-            const uint64_t bd = make_desc(ringB + ((b0 + SB - 1 - t) % RB) * kTileB);
-            const uint32_t accf = (started >> acc) & 1u;
-#pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-              mma_bf16(tmem + (uint32_t)(acc * kBN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
-                       accf | (uint32_t)(k > 0));
-            started |= 1u << acc;
-            pending = true;
-          }
-          mma_commit(&emptyA[iA % RA]);                                 // A_s is done
-#pragma unroll
-          for (int t = 0; t < SB; ++t)                                  // B_t after its last pair
-            if ((SA - 1 < kLevels - t ? SA - 1 : kLevels - t) == s) mma_commit(&emptyB[(b0 + SB - 1 - t) % RB]);
+    int iA = 0, iB = 0, nsub = 0;        // nsub: chunks run through the accumulators so far
+    bool ok = true, pending = false;   // pending: MMAs of the current chunk not yet committed
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      int mt, nt, ks, c_lo, c_hi;
+      oz_item(it, item, mt, nt, ks, c_lo, c_hi);
+      for (int c = c_lo; c < c_hi && ok; ++c, ++nsub) {
+        const int64_t k0 = (int64_t)c * kChunk;
+        const int nkb = (int)(((K - k0 < kChunk ? K - k0 : kChunk) + kBK - 1) / kBK);
+        // the epilogue has read the previous chunk's accumulators
+        if (nsub > 0 && (*abort_flag || !mbar_wait(acc_empty, (nsub - 1) & 1, wait_cycles))) {
+          ok = false;
+          break;
         }
+        fence_after();
+        uint32_t started = 0;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          const int b0 = iB;                       // B tile of digit t sits at counter b0 + SB - 1 - t
+          for (int q = 0; q < SB && ok; ++q, ++iB)
+            if (*abort_flag || !mbar_wait(&fullB[iB % RB], (iB / RB) & 1, wait_cycles)) ok = false;
+          for (int s = 0; s < SA && ok; ++s, ++iA) {
+            if (*abort_flag || !mbar_wait(&fullA[iA % RA], (iA / RA) & 1, wait_cycles)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint64_t ad = make_desc(ringA + (iA % RA) * kTile);
+#pragma unroll
+            for (int t = 0; t < SB; ++t) {
+              if (s + t > kLevels) continue;
+              const int acc = acc_of(s + t);
+              const uint64_t bd = make_desc(ringB + ((b0 + SB - 1 - t) % RB) * kTileB);
+              const uint32_t accf = (started >> acc) & 1u;
+#pragma unroll
+              for (int k = 0; k < kBK / 16; ++k)
+                mma_bf16(tmem + (uint32_t)(acc * kBN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
+                         accf | (uint32_t)(k > 0));
+              started |= 1u << acc;
+              pending = true;
+            }
+            mma_commit(&emptyA[iA % RA]);                                 // A_s is done
+#pragma unroll
+            for (int t = 0; t < SB; ++t)                                  // B_t after its last pair
+              if ((SA - 1 < kLevels - t ? SA - 1 : kLevels - t) == s) mma_commit(&emptyB[(b0 + SB - 1 - t) % RB]);
+          }
+        }
+        if (!ok) break;
+        mma_commit(acc_full);          // arrives once this chunk's MMAs have completed
+        pending = false;
       }
-      if (!ok) break;
-      mma_commit(acc_full);          // arrives once this item's MMAs have completed
-      pending = false;
     }
     if (!ok) {
       err |= 1;
@@ -434,49 +628,75 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
 #pragma unroll
       for (int t = 0; t < SB; ++t)
         if (s + t <= kLevels) started |= 1u << acc_of(s + t);
-    int nitem = 0;
-    for (int item = blockIdx.x; item < items; item += gridDim.x, ++nitem) {
-      // wait for the item's accumulators; give up when another role aborted (the MMA issuer then
-      // waits for its own MMAs before the tensor memory is freed)
-      int got = 0;
-      if (lane == 0) {
-        const long long t0 = clock64();
-        while (true) {
-          if (mbar_try_wait(acc_full, nitem & 1)) { got = 1; break; }
-          if (*abort_flag) break;
-          if (clock64() - t0 > wait_cycles) {
-            err |= 1;
-            *abort_flag = 1;
-            break;
+    // running sums of this thread's 48 outputs: element e at my_run[e * 256] (coalesced per warp)
+    constexpr int kEpiT = kEpiWarps * 32;
+    float2* my_run = run ? run + (int64_t)blockIdx.x * (kEpiT * (kBN / 2)) + (ew * 32 + lane) : nullptr;
+    int nsub = 0;
+    bool stop = false;
+    for (int item = blockIdx.x; item < items && !stop; item += gridDim.x) {
+      int mt, nt, ks, c_lo, c_hi;
+      oz_item(it, item, mt, nt, ks, c_lo, c_hi);
+      const int64_t row = (int64_t)mt * kBM + q * 32 + lane;
+      for (int c = c_lo; c < c_hi; ++c, ++nsub) {
+        // wait for the chunk's accumulators; give up when another role aborted (the MMA issuer
+        // then waits for its own MMAs before the tensor memory is freed)
+        int got = 0;
+        if (lane == 0) {
+          const long long t0 = clock64();
+          while (true) {
+            if (mbar_try_wait(acc_full, nsub & 1)) { got = 1; break; }
+            if (*abort_flag) break;
+            if (clock64() - t0 > wait_cycles) {
+              err |= 1;
+              *abort_flag = 1;
+              break;
+            }
           }
         }
-      }
-      got = __shfl_sync(0xffffffffu, got, 0);
-      __syncwarp();
-      fence_after();
-      if (!got || *abort_flag) break;
-      const int nt = item % n_tiles, mt = (item / n_tiles) % m_tiles, c = item / (n_tiles * m_tiles);
-      const int64_t row = (int64_t)mt * kBM + q * 32 + lane;
-      float2* out = P + ((int64_t)c * ldL + (int64_t)nt * kBN) * ldM + row;
-      for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 16) {
-        uint32_t e[kAcc][16];
-#pragma unroll
-        for (int a = 0; a < kAcc; ++a) tmem_ld16(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          // exact parts: E0 integer, E1..E3 in 2^-8, 2^-16, 2^-24 units, each within 2^24 units;
-          // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded levels 4..
-          DF v{0.0f, 0.0f};
-#pragma unroll
-          for (int a = kAcc - 1; a >= 0; --a)
-            if (started & (1u << a)) v = df_add(v, DF{__uint_as_float(e[a][j]), 0.0f});
-          out[(int64_t)(c0 + j) * ldM] = make_float2(v.hi, v.lo);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        fence_after();
+        if (!got || *abort_flag) {
+          stop = true;
+          break;
         }
+        const bool first = c == c_lo, last = c + 1 == c_hi;
+        for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 16) {
+          uint32_t e[kAcc][16];
+#pragma unroll
+          for (int a = 0; a < kAcc; ++a) tmem_ld16(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            // exact parts: E0 integer, E1..E3 in 2^-8, 2^-16, 2^-24 units, each within 2^24 units;
+            // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded
+            // levels 4..
+            DF v{0.0f, 0.0f};
+#pragma unroll
+            for (int a = kAcc - 1; a >= 0; --a)
+              if (started & (1u << a)) v = df_add(v, DF{__uint_as_float(e[a][j]), 0.0f});
+            float2* rp = my_run + (int64_t)(c0 - half * (kBN / 2) + j) * kEpiT;
+            if (!first) {
+              const float2 r = *rp;
+              v = df_add(DF{r.x, r.y}, v);
+            }
+            if (!last) {
+              *rp = make_float2(v.hi, v.lo);
+              continue;
+            }
+            const int64_t n = (int64_t)nt * kBN + c0 + j;
+            if (!d.on) {
+              P[((int64_t)ks * ldL + n) * ldM + row] = make_float2(v.hi, v.lo);
+            } else if (row < d.M && n < d.Nout && (!it.lower || row >= n)) {
+              d.out[n * d.ldOut + row] =
+                  oz_scale(f32_to_f64(v.hi) + f32_to_f64(v.lo), d.rexp[row] + d.cexp[n] - 14);
+            }
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
     }
   }
   __syncwarp();
@@ -494,11 +714,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
 // float64: MODE 1 (Z'' = diag(w) diag(2^e) J Omega): out[j * ldOut + m] = w_m 2^(2 e_m + f_j - 14)
 // v; MODE 2 (Y): out[j * ldOut + m] = 2^(f_j - 14) v; MODE 3 (a product of a row-scaled and a
 // column-scaled operand): out[j * ldOut + m] = 2^(e_m + f_j - 14) v.  Rows M <= m < ldOut are
-// written as zero.
+// written as zero.  With lower, entries m < j (whose partials a lower-tile GEMM may not have
+// written) are left untouched.
 template <int MODE>
 __global__ void k_oz_reduce(const float2* __restrict__ P, int nc, int64_t ldL, int64_t ldM, float2* __restrict__ acc,
                             int first, int last, int64_t M, int64_t ldOut, const int* __restrict__ rexp,
-                            const int* __restrict__ cexp, const double* __restrict__ w, double* __restrict__ out) {
+                            const int* __restrict__ cexp, const double* __restrict__ w, double* __restrict__ out,
+                            int lower) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = blockIdx.y;
   if (m >= ldOut) return;
@@ -506,6 +728,7 @@ __global__ void k_oz_reduce(const float2* __restrict__ P, int nc, int64_t ldL, i
     if (last) out[j * ldOut + m] = 0.0;
     return;
   }
+  if (lower && m < j) return;
   DF v{0.0f, 0.0f};
   if (!first) {
     const float2 a = acc[j * ldM + m];
@@ -544,6 +767,16 @@ struct OzSketch {
   unsigned long long* gmax = nullptr; size_t gmax_b = 0;
   float2* part = nullptr; size_t part_b = 0;   // split-K partials of one launch
   float2* acc = nullptr;  size_t acc_b = 0;    // running sums across launches
+  float2* run = nullptr;  size_t run_b = 0;    // per-CTA running sums of the chunks of a K slice
+  // the factor's Gram products: digit planes of an FP64 p x ell operand and its column exponents
+  __nv_bfloat16* FD = nullptr; size_t FD_b = 0;
+  int* fexp = nullptr;    size_t fexp_b = 0;
+  // U = B W: digit planes of the row-scaled B (K-major) and of the column-scaled W, exponents
+  __nv_bfloat16 *UA = nullptr, *UB = nullptr;
+  size_t UA_b = 0, UB_b = 0;
+  int *uexp = nullptr, *wexp = nullptr;
+  size_t uexp_b = 0, wexp_b = 0;
+  double* Ws = nullptr;   size_t Ws_b = 0;
   // the Jacobian the digit planes were made from
   const float* J = nullptr;
   int64_t N = 0, ldJ = 0, ldN = 0;
@@ -563,37 +796,66 @@ cudaError_t grow(P** p, size_t* cap, size_t bytes) {
   return e;
 }
 
+// Tiles a lower-triangle digit-plane GEMM enumerates.
+int64_t oz_lower_tiles(int m_tiles, int n_tiles) {
+  int64_t t = 0;
+  for (int m = 0; m < m_tiles; ++m) t += oz_lower_count(m, n_tiles);
+  return t;
+}
+
 // D[m, n] = sum over kept digit pairs for an M x Nout output and K columns, into out (float64,
-// MODE as k_oz_reduce).  Split-K over chunks of kChunk; launches of at most partial_cap bytes of
-// partials, their sums carried in the running double-float sums.
+// MODE as k_oz_reduce; with lower only the entries m >= n, of tiles that hold one).  K is cut into
+// slices of up to max_cps chunks of kChunk, as few as keep four items per SM; each item sums its
+// slice's chunks in order.  With MODE 3 and one slice the GEMM's epilogue writes out itself;
+// otherwise the slices' partials go to launches of at most partial_cap bytes, each followed by the
+// fixed-order reduction, their sums carried in the running double-float sums.
 template <int SA, int SB, int MODE>
 cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMap& tmB, int64_t M, int64_t Nout,
                            int64_t K, const int* rexp, const int* cexp, const double* w, double* out, int64_t ldOut,
-                           int* status, cudaStream_t s, long long wait_cycles, size_t partial_cap = kPartialCap) {
+                           int* status, cudaStream_t s, long long wait_cycles, bool lower = false, int max_cps = 1,
+                           size_t partial_cap = kPartialCap) {
   const int64_t ldL = rup(Nout, kBN), ldM = rup(M, kBM);
   const int64_t nchunks = (K + kChunk - 1) / kChunk;
   const size_t chunk_bytes = (size_t)ldL * ldM * sizeof(float2);
-  const int64_t per_launch = std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)(partial_cap / chunk_bytes)));
-  cudaError_t e;
-  if ((e = grow(&o->part, &o->part_b, chunk_bytes * per_launch)) != cudaSuccess) return e;
-  if (per_launch < nchunks && (e = grow(&o->acc, &o->acc_b, chunk_bytes)) != cudaSuccess) return e;
   auto kern = k_oz_gemm<SA, SB>;
   constexpr int smem = OzSmem<SA, SB>::bytes;
+  cudaError_t e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   int dev = 0, nsm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int n_tiles = (int)(ldL / kBN), m_tiles = (int)(ldM / kBM);
-  for (int64_t c0 = 0; c0 < nchunks; c0 += per_launch) {
-    const int nc = (int)std::min<int64_t>(per_launch, nchunks - c0);
-    const int64_t items = (int64_t)n_tiles * m_tiles * nc;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, nsm);
-    kern<<<grid, kOzThreads, smem, s>>>(tmA, tmB, K, (int)c0, n_tiles, m_tiles, nc, o->part, ldL, ldM, status,
-                                         wait_cycles);
+  const int64_t tiles = lower ? oz_lower_tiles(m_tiles, n_tiles) : (int64_t)n_tiles * m_tiles;
+  int64_t nks = std::min<int64_t>(nchunks, std::max<int64_t>(1, (4 * (int64_t)nsm + tiles - 1) / tiles));
+  const int64_t cps = std::min<int64_t>(std::max(1, max_cps), (nchunks + nks - 1) / nks);
+  nks = (nchunks + cps - 1) / cps;
+  if (cps > 1) {
+    const size_t run_bytes = (size_t)std::min<int64_t>(tiles * nks, nsm) * (kEpiWarps * 32) * (kBN / 2) * sizeof(float2);
+    if ((e = grow(&o->run, &o->run_b, run_bytes)) != cudaSuccess) return e;
+  }
+  OzDirect d{rexp, cexp, out, ldOut, M, Nout, 0};
+  if (MODE == 3 && nks == 1) {
+    d.on = 1;
+    const OzItems it{n_tiles, m_tiles, (int)tiles, lower ? 1 : 0, 1, (int)cps, 0, (int)nchunks};
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
+    kern<<<grid, kOzThreads, smem, s>>>(tmA, tmB, K, it, nullptr, ldL, ldM, o->run, d, status, wait_cycles);
+    note_launch();
+    return cudaGetLastError();
+  }
+  const int64_t slice_bytes = (int64_t)chunk_bytes;
+  const int64_t per_launch = std::max<int64_t>(1, std::min<int64_t>(nks, (int64_t)(partial_cap / slice_bytes)));
+  if ((e = grow(&o->part, &o->part_b, chunk_bytes * per_launch)) != cudaSuccess) return e;
+  if (per_launch < nks && (e = grow(&o->acc, &o->acc_b, chunk_bytes)) != cudaSuccess) return e;
+  for (int64_t s0 = 0; s0 < nks; s0 += per_launch) {
+    const int ns = (int)std::min<int64_t>(per_launch, nks - s0);
+    const OzItems it{n_tiles, m_tiles, (int)tiles, lower ? 1 : 0, ns, (int)cps, (int)(s0 * cps),
+                     (int)std::min<int64_t>(nchunks, (s0 + ns) * cps)};
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles * ns, nsm);
+    kern<<<grid, kOzThreads, smem, s>>>(tmA, tmB, K, it, o->part, ldL, ldM, o->run, d, status, wait_cycles);
     note_launch();
     dim3 rg((unsigned)((ldOut + 255) / 256), (unsigned)Nout);
-    k_oz_reduce<MODE><<<rg, 256, 0, s>>>(o->part, nc, ldL, ldM, o->acc, c0 == 0, c0 + nc >= nchunks, M, ldOut, rexp,
-                                         cexp, w, out);
+    k_oz_reduce<MODE><<<rg, 256, 0, s>>>(o->part, ns, ldL, ldM, o->acc, s0 == 0, s0 + ns >= nks, M, ldOut, rexp,
+                                         cexp, w, out, lower ? 1 : 0);
     note_launch();
   }
   return cudaGetLastError();
@@ -606,7 +868,8 @@ OzSketch* oz_create() { return new (std::nothrow) OzSketch(); }
 void oz_destroy(OzSketch* o) {
   if (!o) return;
   void* bufs[] = {o->JD, o->JDT, o->OD, o->ZD, o->jexp, o->oexp, o->zexp, o->Zs, o->part, o->acc,
-                  o->GA, o->GB, o->gexp, o->gmax};
+                  o->GA, o->GB, o->gexp, o->gmax, o->run, o->FD, o->fexp, o->UA, o->UB, o->uexp, o->wexp,
+                  o->Ws};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete o;
@@ -720,11 +983,136 @@ cudaError_t oz_gram(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64_t
     *why = "tensor map encoding failed";
     return cudaSuccess;
   }
-  // G[j', j] = 2^(e_j' + f_j - 14) sum over kept pairs of AT_s BT_t^T (all p x p entries)
-  // a p x p output: up to 8 GB of split-K partials per launch, so that the reduction passes over
-  // the output a few times rather than once per K chunk
+  // G[j', j] = 2^(e_j' + f_j - 14) sum over kept pairs of AT_s BT_t^T for j' >= j: the tiles of the
+  // lower triangle, each summed over all of K by one CTA and written by the GEMM's epilogue
   return run_digit_gemm<kDigG, kDigG, 3>(o, mA, mB, p, p, ldN, ej, ew, nullptr, G, ldG, status, s, wait_cycles,
-                                         size_t(8) << 30);
+                                         true, 1 << 30);
+}
+
+cudaError_t oz_gram_cols(OzSketch* o, const float* A32, const double* B, int64_t K, int64_t ld, int ell, double* C,
+                         int64_t ldC, const char** why, cudaStream_t s, int* status, long long wait_cycles) {
+  *why = nullptr;
+  if (!tensor_map_encoder()) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  if ((ld % 32) || K < 1 || K > ld || ell < 1 || ldC < ell) {
+    *why = "the operands' leading dimension must be a multiple of 32";
+    return cudaSuccess;
+  }
+  cudaError_t e;
+  const int64_t tot = ld * ell;
+  const unsigned sg = (unsigned)std::min<int64_t>((tot + 255) / 256, 8192);
+  if ((e = grow(&o->FD, &o->FD_b, (size_t)kDigZ * ell * ld * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->fexp, &o->fexp_b, (size_t)ell * sizeof(int))) != cudaSuccess) return e;
+  k_oz_colexp<double><<<(unsigned)ell, 256, 0, s>>>(B, ld, K, o->fexp);
+  note_launch();
+  k_oz_split_cols<double, kDigZ><<<sg, 256, 0, s>>>(B, ld, ell, o->fexp, o->FD);
+  note_launch();
+  CUtensorMap mA, mB;
+  // the maps' K extent is K itself: rows K..ld-1 of the operands are read as zeros
+  if (!make_tile_map(&mB, o->FD, 2, ell, K, ld, kDigZ, (int64_t)ell * ld, kBN)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  if (!A32) {
+    // B^T B: both operands are B's planes
+    if (!make_tile_map(&mA, o->FD, 2, ell, K, ld, kDigZ, (int64_t)ell * ld, kBM)) {
+      *why = "tensor map encoding failed";
+      return cudaSuccess;
+    }
+    return run_digit_gemm<kDigZ, kDigZ, 3>(o, mA, mB, ell, ell, K, o->fexp, o->fexp, nullptr, C, ldC, status, s,
+                                           wait_cycles, true, 1 << 30);
+  }
+  if ((e = grow(&o->OD, &o->OD_b, (size_t)kDigOm * ell * ld * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->oexp, &o->oexp_b, (size_t)ell * sizeof(int))) != cudaSuccess) return e;
+  k_oz_colexp<float><<<(unsigned)ell, 256, 0, s>>>(A32, ld, K, o->oexp);
+  note_launch();
+  k_oz_split_cols<float, kDigOm><<<sg, 256, 0, s>>>(A32, ld, ell, o->oexp, o->OD);
+  note_launch();
+  if (!make_tile_map(&mA, o->OD, 2, ell, K, ld, kDigOm, (int64_t)ell * ld, kBM)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  return run_digit_gemm<kDigOm, kDigZ, 3>(o, mA, mB, ell, ell, K, o->oexp, o->fexp, nullptr, C, ldC, status, s,
+                                          wait_cycles, true, 1 << 30);
+}
+
+cudaError_t oz_gemm_bw(OzSketch* o, const double* B, int64_t ldB, int64_t p, int ell, const double* W, int64_t ldW,
+                       const double* colscale, double* U, int64_t ldU, const char** why, cudaStream_t s, int* status,
+                       long long wait_cycles) {
+  *why = nullptr;
+  if (!tensor_map_encoder()) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  if (p < 1 || ell < 1 || ldU < p) {
+    *why = "empty operands";
+    return cudaSuccess;
+  }
+  const int64_t ldK = rup(ell, 32);
+  cudaError_t e;
+  if ((e = grow(&o->UA, &o->UA_b, (size_t)kDigZ * p * ldK * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->UB, &o->UB_b, (size_t)kDigZ * ell * ldK * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->uexp, &o->uexp_b, (size_t)p * sizeof(int))) != cudaSuccess) return e;
+  if ((e = grow(&o->wexp, &o->wexp_b, (size_t)ell * sizeof(int))) != cudaSuccess) return e;
+  if ((e = grow(&o->Ws, &o->Ws_b, (size_t)ell * ldK * sizeof(double))) != cudaSuccess) return e;
+  k_oz_rowexp_cm<<<(unsigned)((p + 31) / 32), dim3(32, 8), 0, s>>>(B, ldB, p, ell, o->uexp);
+  note_launch();
+  {
+    dim3 blk(32, 8), grd((unsigned)((p + 31) / 32), (unsigned)(ldK / 32));
+    k_oz_split_rows_cm<<<grd, blk, 0, s>>>(B, ldB, p, ell, o->uexp, o->UA, ldK);
+    note_launch();
+  }
+  {
+    const int64_t tot = (int64_t)ell * ldK;
+    k_oz_scale_pad<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W, ldW, ell, ell, colscale, o->Ws, ldK);
+    note_launch();
+    k_oz_colexp<double><<<(unsigned)ell, 256, 0, s>>>(o->Ws, ldK, ell, o->wexp);
+    note_launch();
+    k_oz_split_cols<double, kDigZ><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, s>>>(
+        o->Ws, ldK, ell, o->wexp, o->UB);
+    note_launch();
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  if (!make_tile_map(&mA, o->UA, 2, p, ldK, ldK, kDigZ, p * ldK, kBM) ||
+      !make_tile_map(&mB, o->UB, 2, ell, ldK, ldK, kDigZ, (int64_t)ell * ldK, kBN)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  return run_digit_gemm<kDigZ, kDigZ, 3>(o, mA, mB, p, ell, ldK, o->uexp, o->wexp, nullptr, U, ldU, status, s,
+                                         wait_cycles, false, 1 << 30);
+}
+
+cudaError_t oz_gram_self32(OzSketch* o, const float* A, int64_t K, int64_t ld, int ell, double* C, int64_t ldC,
+                           const char** why, cudaStream_t s, int* status, long long wait_cycles) {
+  *why = nullptr;
+  if (!tensor_map_encoder()) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  if ((ld % 32) || K < 1 || K > ld || ell < 1 || ldC < ell) {
+    *why = "the operand's leading dimension must be a multiple of 32";
+    return cudaSuccess;
+  }
+  cudaError_t e;
+  const int64_t tot = ld * ell;
+  if ((e = grow(&o->OD, &o->OD_b, (size_t)kDigOm * ell * ld * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->oexp, &o->oexp_b, (size_t)ell * sizeof(int))) != cudaSuccess) return e;
+  k_oz_colexp<float><<<(unsigned)ell, 256, 0, s>>>(A, ld, K, o->oexp);
+  note_launch();
+  k_oz_split_cols<float, kDigOm><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, s>>>(A, ld, ell,
+                                                                                                    o->oexp, o->OD);
+  note_launch();
+  CUtensorMap mA, mB;
+  if (!make_tile_map(&mA, o->OD, 2, ell, K, ld, kDigOm, (int64_t)ell * ld, kBM) ||
+      !make_tile_map(&mB, o->OD, 2, ell, K, ld, kDigOm, (int64_t)ell * ld, kBN)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  return run_digit_gemm<kDigOm, kDigOm, 3>(o, mA, mB, ell, ell, K, o->oexp, o->oexp, nullptr, C, ldC, status, s,
+                                           wait_cycles, true, 1 << 30);
 }
 
 }  // namespace ngd

@@ -325,3 +325,30 @@ def test_gramian_full_matches_oracle(ngd, dtype, tol):
     assert rel(G, G_o) <= tol / 20
     assert np.array_equal(G, G.T)
     ctx.close()
+
+
+@pytest.mark.parametrize("widths,n_int,n_bnd", [
+    ([3, 32, 32, 1], 8000, 1800),    # p = 1217, 39 K chunks: 8 slices of 5 chunks (the last of 4)
+    ([3, 60, 60, 1], 2400, 600),     # p = 3961, 12 K chunks: one slice, written by the GEMM itself
+])
+def test_gramian_full_tensor_core_layouts(ngd, widths, n_int, n_bnd):
+    """The tensor-core Gramian's other two work layouts against the oracle's J^T diag(w) J of the
+    same FP32-rounded J.  The GEMM runs only the output tiles that hold an entry on or below the
+    diagonal and cuts K into as few slices as keep four items per SM; each CTA sums the chunks of
+    its slice in order (double-float running sums).  p = 1217 with N = 9800: 76 of 130 tiles, 8
+    slices of 5 chunks, partials added by the reduction; p = 3961 with N = 3000: 672 of 1302 tiles,
+    one slice of all 12 chunks, scaled and written by the GEMM's epilogue (no partials).  Bounds as
+    in test_gramian_full_matches_oracle for the FP32 context."""
+    pr, th = inputs.small_problem(d=3, widths=widths, n_int=n_int, n_bnd=n_bnd, seed=53)
+    J = round32(mlp.jacobian(pr, th))
+    ctx = ngd.Context(pr, dtype="f32")
+    ctx.residual(dev(th))
+    ctx.set_jacobian(dev(J, torch.float32))
+    G = host(ctx.gramian_full(None))
+    G_o = J.T @ (pr.w[:, None] * J)
+    dg = np.sqrt(np.diag(G_o))
+    err = np.abs(G - G_o) / np.maximum(np.outer(dg, dg), 1e-300)
+    assert err.max() <= 1e-11, (err.max(), np.unravel_index(int(err.argmax()), err.shape))
+    assert rel(G, G_o) <= 5e-13
+    assert np.array_equal(G, G.T)
+    ctx.close()
