@@ -376,6 +376,220 @@ __global__ void __launch_bounds__(256) k_tridiag_dist(const double* __restrict__
 }
 
 
+// Double-float form of k_tridiag_dist for FP32 contexts (the Nystrom core FP64-accurate to
+// ~2^-48): the columns, v, p and w as FP32 pairs, the matrix-vector products and rank-2 updates on
+// the FP32 pipes.  With one block per SM each block owns ~n / 152 columns, and in FP64 their
+// products and updates cost ~1.5 us per column of GB300's narrow FP64 pipe.  The reflector's
+// scalars (norm, sigma, tau) and the cross-block sum K stay FP64; the outputs (d, e, tau, Vh) are
+// FP64.  Same protocol, buffers and bounded waits as k_tridiag_dist (vbuf and pbuf hold pairs).
+namespace {
+
+__device__ __forceinline__ DF ld_df(const DF* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return DF{v.x, v.y};
+}
+__device__ __forceinline__ void st_df(DF* p, DF v) { __stcg(reinterpret_cast<float2*>(p), make_float2(v.hi, v.lo)); }
+
+__device__ __forceinline__ DF dsplit(double x) {
+  DF r;
+  split_df(x, r.hi, r.lo);
+  return r;
+}
+
+// hi + lo renormalised (|lo| <= half an FP32 unit of hi): a stored pair that later enters a
+// product whose lo x lo term is dropped must not carry a low word grown by cancellations
+__device__ __forceinline__ DF df_norm(DF a) {
+  float s, e;
+  two_sum(a.hi, a.lo, s, e);
+  return DF{s, e};
+}
+
+__device__ void house_from_col_df(const DF* __restrict__ col, int n, int k, double* __restrict__ d,
+                                  double* __restrict__ e, double* __restrict__ tau, double* __restrict__ Vh,
+                                  DF* __restrict__ vout, DF* red8, double* s_bc) {
+  const int m = n - k - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DF s2{0.f, 0.f};
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const DF x = col[k + 1 + i];
+    df_add_prod2(s2, x.hi, x.lo, x.hi, x.lo);
+  }
+  s2 = warp_sum_df(s2);
+  if (lane == 0) red8[warp] = s2;
+  __syncthreads();
+  if (warp == 0) {
+    DF t = lane < (int)(blockDim.x >> 5) ? red8[lane] : DF{0.f, 0.f};
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) t = df_add(t, shfl_xor_df(t, o));
+    if (lane == 0) {
+      const double tsum = df_to_double(t);
+      const double x0 = df_to_double(col[k + 1]);
+      const double sig = sqrt(tsum);
+      double alpha, tu, v0;
+      if (tsum - x0 * x0 <= 0.0) {      // nothing below the subdiagonal: H = I
+        alpha = x0;
+        tu = 0.0;
+        v0 = 0.0;
+      } else {
+        alpha = x0 >= 0.0 ? -sig : sig;
+        v0 = x0 - alpha;
+        tu = 1.0 / (tsum + fabs(x0) * sig);
+      }
+      d[k] = df_to_double(col[k]);
+      e[k] = alpha;
+      __stcg(tau + k, tu);
+      s_bc[0] = v0;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const DF vi = i == 0 ? dsplit(s_bc[0]) : col[k + 1 + i];
+    st_df(vout + i, vi);
+    Vh[(int64_t)k * n + i] = i == 0 ? s_bc[0] : df_to_double(vi);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_tridiag_dist_df(const double* __restrict__ A, int n, double* __restrict__ d,
+                                                         double* __restrict__ e, double* __restrict__ tau,
+                                                         double* __restrict__ Vh, double* __restrict__ vbuf_,
+                                                         double* __restrict__ pbuf_, double* __restrict__ red,
+                                                         unsigned* __restrict__ flags, int* __restrict__ status) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int ncl = (n + G - 1) / G;
+  DF* cols = reinterpret_cast<DF*>(smem_raw);            // [ncl][n]
+  DF* vs = cols + (int64_t)ncl * n;                       // [n]
+  DF* ws = vs + n;                                        // [n]
+  DF* vbuf = reinterpret_cast<DF*>(vbuf_);                // [2][n]
+  DF* pbuf = reinterpret_cast<DF*>(pbuf_);                // [2][n]
+  __shared__ DF red8[8];
+  __shared__ double s_bc[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int s = 0; s < ncl; ++s) {
+    const int j = b + s * G;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      cols[(int64_t)s * n + i] = j < n ? dsplit(A[i + (int64_t)j * n]) : DF{0.f, 0.f};
+  }
+  __syncthreads();
+  if (n >= 3 && b == 0) {
+    house_from_col_df(cols, n, 0, d, e, tau, Vh, vbuf, red8, s_bc);
+    publish_flag(flags);
+  }
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    const int par = k & 1;
+    const DF* vk = vbuf + (int64_t)par * n;
+    DF* pk = pbuf + (int64_t)par * n;
+    double* rk = red + (int64_t)par * G;
+    if (k % G != b) wait_flag(flags + k, status);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) vs[i] = ld_df(vk + i);   // with tau: one round trip
+    const double tk = __ldcg(tau + k);
+    const int s_first = (k + 1 - b + G - 1) / G;          // first local slot with column j > k
+    __syncthreads();
+    if (tk != 0.0) {                                      // uniform: every block reads the same tau
+      const DF tkd = dsplit(tk);
+      // p_j = tau A[k+1:, j] . v for owned columns j > k, one warp per column
+      DF part{0.f, 0.f};
+      for (int s = s_first + warp; s < ncl; s += (int)(blockDim.x >> 5)) {
+        const int j = b + s * G;
+        if (j >= n) break;
+        const DF* col = cols + (int64_t)s * n + k + 1;
+        DF a0{0.f, 0.f}, a1{0.f, 0.f};
+        int i = lane;
+        for (; i + 32 < m; i += 64) {
+          df_add_prod2(a0, col[i].hi, col[i].lo, vs[i].hi, vs[i].lo);
+          df_add_prod2(a1, col[i + 32].hi, col[i + 32].lo, vs[i + 32].hi, vs[i + 32].lo);
+        }
+        if (i < m) df_add_prod2(a0, col[i].hi, col[i].lo, vs[i].hi, vs[i].lo);
+        const DF dot = warp_sum_df(df_add(a0, a1));
+        const DF pj = df_mul(dot, tkd.hi, tkd.lo);
+        if (lane == 0) {
+          st_df(pk + (j - k - 1), pj);
+          const DF vj = vs[j - k - 1];
+          df_add_prod2(part, vj.hi, vj.lo, pj.hi, pj.lo);
+        }
+      }
+      if (lane == 0) red8[warp] = part;
+      __syncthreads();
+      if (warp == 0) {
+        DF sb = lane < (int)(blockDim.x >> 5) ? red8[lane] : DF{0.f, 0.f};
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) sb = df_add(sb, shfl_xor_df(sb, o));
+        if (lane == 0) __stcg(rk + b, df_to_double(sb));
+      }
+    }
+    grid.sync();
+    const bool next = k + 3 < n;
+    const int own_next = next && (k + 1) % G == b;
+    if (tk != 0.0) {
+      // K = tau/2 v . p (summed over blocks in block order, FP64), w = p - K v
+      if (warp == 0) {
+        double sv = 0.0;
+        for (int q = lane; q < G; q += 32) sv += __ldcg(rk + q);
+        sv = wsum_d(sv);
+        if (lane == 0) s_bc[1] = 0.5 * tk * sv;
+      }
+      for (int i = threadIdx.x; i < m; i += blockDim.x) ws[i] = ld_df(pk + i);
+      __syncthreads();
+      const DF nK = dsplit(-s_bc[1]);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        DF w = ws[i];
+        df_add_prod2(w, nK.hi, nK.lo, vs[i].hi, vs[i].lo);
+        ws[i] = df_norm(w);
+      }
+      __syncthreads();
+      if (own_next) {                                     // look-ahead: column k + 1 first
+        DF* col = cols + (int64_t)((k + 1) / G) * n + k + 1;
+        const DF wj = ws[0], vj = vs[0];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          DF c = col[i];
+          df_add_prod2(c, -vs[i].hi, -vs[i].lo, wj.hi, wj.lo);
+          df_add_prod2(c, -ws[i].hi, -ws[i].lo, vj.hi, vj.lo);
+          col[i] = df_norm(c);
+        }
+        __syncthreads();
+      }
+    }
+    if (own_next) {
+      house_from_col_df(cols + (int64_t)((k + 1) / G) * n, n, k + 1, d, e, tau, Vh, vbuf + (int64_t)(par ^ 1) * n,
+                        red8, s_bc);
+      publish_flag(flags + k + 1);
+    }
+    if (tk != 0.0) {
+      for (int s = s_first; s < ncl; ++s) {
+        const int j = b + s * G;
+        if (j >= n) break;
+        if (own_next && j == k + 1) continue;
+        DF* col = cols + (int64_t)s * n + k + 1;
+        const DF wj = ws[j - k - 1], vj = vs[j - k - 1];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          DF c = col[i];
+          df_add_prod2(c, -vs[i].hi, -vs[i].lo, wj.hi, wj.lo);
+          df_add_prod2(c, -ws[i].hi, -ws[i].lo, vj.hi, vj.lo);
+          col[i] = df_norm(c);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // the last 2 x 2 block
+  if (threadIdx.x == 0) {
+    if (n >= 2) {
+      if ((n - 2) % G == b) {
+        const DF* c = cols + (int64_t)((n - 2) / G) * n;
+        d[n - 2] = df_to_double(c[n - 2]);
+        e[n - 2] = df_to_double(c[n - 1]);
+      }
+      if ((n - 1) % G == b) d[n - 1] = df_to_double(cols[(int64_t)((n - 1) / G) * n + n - 1]);
+    } else if (b == 0) {
+      d[0] = df_to_double(cols[0]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------- 2. eigenvalues
 // lam_asc[i] (ascending), one half-warp per eigenvalue: 16 Sturm counts per step shrink the
 // bracket 17-fold, down to a relative width 2 eps (so that eigenvalues far below eps ||T|| stay
@@ -1351,16 +1565,18 @@ cudaError_t launch_sym_eig(const double* S, int n, double* lam_desc, double* V, 
   const size_t dist_smem = (size_t)((n + gdist - 1) / gdist + 2) * n * sizeof(double);
   if (dist_smem <= 200 * 1024) {
     // A stays in shared memory across the grid, one block per SM
-    cudaFuncSetAttribute((const void*)k_tridiag_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dist_smem);
+    // double-float columns (8 bytes per entry, as FP64) in FP32 contexts
+    const void* kern = df_recurrences ? (const void*)k_tridiag_dist_df : (const void*)k_tridiag_dist;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dist_smem);
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_tridiag_dist, 256, dist_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, dist_smem);
     if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
     int nn_ = n;
     const double* Ac = A;
     cudaMemsetAsync(flags, 0, (size_t)n * sizeof(unsigned), s);
     void* args[] = {&Ac, &nn_, &d, &e, &tau, &Vh, &vbuf, &pbuf, &redb, &flags, &status};
     note_launch();
-    err = cudaLaunchCooperativeKernel((const void*)k_tridiag_dist, gdist, 256, args, dist_smem, s);
+    err = cudaLaunchCooperativeKernel(kern, gdist, 256, args, dist_smem, s);
     if (err != cudaSuccess) return err;
   } else {
     const size_t smem = (size_t)n * sizeof(double);
