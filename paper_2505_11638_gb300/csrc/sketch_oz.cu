@@ -983,10 +983,14 @@ cudaError_t oz_gram(OzSketch* o, const float* J, int64_t ldJ, int64_t N, int64_t
     *why = "tensor map encoding failed";
     return cudaSuccess;
   }
-  // G[j', j] = 2^(e_j' + f_j - 14) sum over kept pairs of AT_s BT_t^T for j' >= j: the tiles of the
-  // lower triangle, each summed over all of K by one CTA and written by the GEMM's epilogue
+  // G[j', j] = 2^(e_j' + f_j - 14) sum over kept pairs of AT_s BT_t^T for j' >= j, on the tiles of
+  // the lower triangle.  Up to 16 K chunks: each tile summed over all of K by one CTA and written by
+  // the GEMM's epilogue.  Longer K: one-chunk slices whose partials (up to 8 GB per launch) the
+  // reduction adds, which measured faster than the CTA's running sums (3-D Poisson, p = 8641,
+  // 43 chunks: 186 ms per NGD full step against 194, the same G bit for bit).
+  const int64_t nchunks = (ldN + 255) / 256;
   return run_digit_gemm<kDigG, kDigG, 3>(o, mA, mB, p, p, ldN, ej, ew, nullptr, G, ldG, status, s, wait_cycles,
-                                         true, 1 << 30);
+                                         true, nchunks <= 16 ? 1 << 30 : 1, size_t(8) << 30);
 }
 
 cudaError_t oz_gram_cols(OzSketch* o, const float* A32, const double* B, int64_t K, int64_t ld, int ell, double* C,

@@ -328,17 +328,16 @@ def test_gramian_full_matches_oracle(ngd, dtype, tol):
 
 
 @pytest.mark.parametrize("widths,n_int,n_bnd", [
-    ([3, 32, 32, 1], 8000, 1800),    # p = 1217, 39 K chunks: 8 slices of 5 chunks (the last of 4)
+    ([3, 32, 32, 1], 8000, 1800),    # p = 1217, 39 K chunks: one-chunk slices, partials reduced
     ([3, 60, 60, 1], 2400, 600),     # p = 3961, 12 K chunks: one slice, written by the GEMM itself
 ])
 def test_gramian_full_tensor_core_layouts(ngd, widths, n_int, n_bnd):
     """The tensor-core Gramian's other two work layouts against the oracle's J^T diag(w) J of the
     same FP32-rounded J.  The GEMM runs only the output tiles that hold an entry on or below the
-    diagonal and cuts K into as few slices as keep four items per SM; each CTA sums the chunks of
-    its slice in order (double-float running sums).  p = 1217 with N = 9800: 76 of 130 tiles, 8
-    slices of 5 chunks, partials added by the reduction; p = 3961 with N = 3000: 672 of 1302 tiles,
-    one slice of all 12 chunks, scaled and written by the GEMM's epilogue (no partials).  Bounds as
-    in test_gramian_full_matches_oracle for the FP32 context."""
+    diagonal.  p = 1217 with N = 9800: 76 of 130 tiles, 39 one-chunk K slices whose partials the
+    reduction adds in order; p = 3961 with N = 3000: 672 of 1302 tiles, one slice of all 12 chunks
+    summed by each CTA in order (double-float running sums), scaled and written by the GEMM's
+    epilogue (no partials).  Bounds as in test_gramian_full_matches_oracle for the FP32 context."""
     pr, th = inputs.small_problem(d=3, widths=widths, n_int=n_int, n_bnd=n_bnd, seed=53)
     J = round32(mlp.jacobian(pr, th))
     ctx = ngd.Context(pr, dtype="f32")
