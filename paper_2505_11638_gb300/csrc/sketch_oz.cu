@@ -376,6 +376,15 @@ __global__ void k_oz_scale_pad(const double* __restrict__ W, int64_t ldW, int ro
 }
 
 // ---------------------------------------------------------------------------- digit-plane GEMM
+// (a.hi + a.lo) + b for an FP32 b, renormalised (df_add with b's low word zero, one add fewer)
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  e += a.lo;
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+
 // Accumulator of the level s + t: levels 0..3 exact, levels 4.. shared (TMEM columns acc * kBN).
 __host__ __device__ constexpr int acc_of(int level) { return level < 4 ? level : 4; }
 
@@ -694,9 +703,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
             // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded
             // levels 4..
             DF v{0.0f, 0.0f};
+            bool init = false;                                  // resolved at compile time
 #pragma unroll
             for (int a = kAcc - 1; a >= 0; --a)
-              if (started & (1u << a)) v = df_add(v, DF{__uint_as_float(e[a][j]), 0.0f});
+              if (started & (1u << a)) {
+                const float x = __uint_as_float(e[a][j]);
+                if (!init) v = DF{x, 0.0f};
+                else v = df_add_f(v, x);
+                init = true;
+              }
             float2* rp = my_run + (int64_t)(c0 - half * (kBN / 2) + j) * kEpiT;
             if (!first) {
               const float2 r = *rp;
