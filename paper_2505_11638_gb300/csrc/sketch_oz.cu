@@ -27,13 +27,13 @@
 // combines them into a double-float value, and writes it as a split-K partial; a second kernel
 // adds the partials of a tile in a fixed order (deterministic) and applies the power-of-two scales.
 //
-// Kernel structure (k_oz_gemm): warp 0 lane 0 issues TMA loads of digit tiles (A: 128 rows, B: 96
-// rows, 64 BF16 = 128 bytes each, 128-byte swizzle) into a ring of 12 16-KB shared-memory slots;
-// per 64-wide k-block, the B digit tiles (descending digit) and then the A digit tiles (ascending
-// digit).  Warp 1 lane 0 issues tcgen05.mma (kind::f16, M = 128, N = 96, K = 16) pair by pair and
-// releases each tile after its last
-// use.  Warps 2..5 drain the accumulators with tcgen05.ld.  Waits follow the bounded protocol of
-// tc_common.cuh.
+// Kernel structure (k_oz_gemm): warp 0 lane 0 issues TMA loads of digit tiles (A: 128 rows, 16 KB;
+// B: 96 rows, 12 KB; 64 BF16 = 128 bytes per row, 128-byte swizzle) into two shared-memory rings
+// (OzSmem); per 64-wide k-block, the B digit tiles (descending digit) and then the A digit tiles
+// (ascending digit).  Warp 1 lane 0 issues tcgen05.mma (kind::f16, M = 128, N = 96, K = 16) pair
+// by pair, each k-block in straight-line code, and releases each tile after its last use.  Warps
+// 2..17 (four per TMEM lane quarter) drain the accumulators with tcgen05.ld.  Waits follow the
+// bounded protocol of tc_common.cuh.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -406,8 +406,11 @@ struct OzSmem {
   static constexpr int bytes = RA * kTile + RB * kTileB + kFixed;
 };
 
-constexpr int kEpiWarps = 8;                       // two warps per TMEM lane quarter
+constexpr int kEpiWarps = 16;                      // four warps per TMEM lane quarter
 constexpr int kOzThreads = 32 * (2 + kEpiWarps);
+constexpr int kEpiT = kEpiWarps * 32;              // epilogue threads
+constexpr int kColW = kBN / (kEpiWarps / 4);       // accumulator columns each epilogue thread drains
+constexpr int kEpiG = 8;                           // columns per tcgen05.ld
 
 // Work items of the digit-plane GEMM: output tiles of kBM x kBN (all of them, or for a symmetric
 // product only the tiles that hold an entry on or below the diagonal, m >= n) times K slices of
@@ -650,7 +653,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
     // ---------------------------------------------------------------- epilogue
     const int ew = warp - 2;
     const int q = warp & 3;                       // TMEM lane quarter this warp may access
-    const int half = ew >> 2;                     // which half of the kBN columns
+    const int part = ew >> 2;                     // which kColW-wide part of the kBN columns
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     // accumulators some kept pair writes (the MMA issuer's first write to each clears it)
     uint32_t started = 0;
@@ -659,9 +662,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
 #pragma unroll
       for (int t = 0; t < SB; ++t)
         if (s + t <= kLevels) started |= 1u << acc_of(s + t);
-    // running sums of this thread's 48 outputs: element e at my_run[e * 256] (coalesced per warp)
-    constexpr int kEpiT = kEpiWarps * 32;
-    float2* my_run = run ? run + (int64_t)blockIdx.x * (kEpiT * (kBN / 2)) + (ew * 32 + lane) : nullptr;
+    // running sums of this thread's kColW outputs: element e at my_run[e * kEpiT] (coalesced per warp)
+    float2* my_run = run ? run + (int64_t)blockIdx.x * (kEpiT * kColW) + (ew * 32 + lane) : nullptr;
     int nsub = 0;
     bool stop = false;
     for (int item = blockIdx.x; item < items && !stop; item += gridDim.x) {
@@ -692,13 +694,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
           break;
         }
         const bool first = c == c_lo, last = c + 1 == c_hi;
-        for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 16) {
-          uint32_t e[kAcc][16];
+        for (int c0 = part * kColW; c0 < (part + 1) * kColW; c0 += kEpiG) {
+          uint32_t e[kAcc][kEpiG];
 #pragma unroll
-          for (int a = 0; a < kAcc; ++a) tmem_ld16(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
+          for (int a = 0; a < kAcc; ++a) tmem_ld8(lane_addr + (uint32_t)(a * kBN + c0), e[a]);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < kEpiG; ++j) {
             // exact parts: E0 integer, E1..E3 in 2^-8, 2^-16, 2^-24 units, each within 2^24 units;
             // added from the smallest: the pair keeps ~48 bits of their sum, then the rounded
             // levels 4..
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
                 else v = df_add_f(v, x);
                 init = true;
               }
-            float2* rp = my_run + (int64_t)(c0 - half * (kBN / 2) + j) * kEpiT;
+            float2* rp = my_run + (int64_t)(c0 - part * kColW + j) * kEpiT;
             if (!first) {
               const float2 r = *rp;
               v = df_add(DF{r.x, r.y}, v);
@@ -867,7 +869,7 @@ cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMa
   const int64_t cps = std::min<int64_t>(std::max(1, max_cps), (nchunks + nks - 1) / nks);
   nks = (nchunks + cps - 1) / cps;
   if (cps > 1) {
-    const size_t run_bytes = (size_t)std::min<int64_t>(tiles * nks, nsm) * (kEpiWarps * 32) * (kBN / 2) * sizeof(float2);
+    const size_t run_bytes = (size_t)std::min<int64_t>(tiles * nks, nsm) * kEpiT * kColW * sizeof(float2);
     if ((e = grow(&o->run, &o->run_b, run_bytes)) != cudaSuccess) return e;
   }
   OzDirect d{rexp, cexp, out, ldOut, M, Nout, 0};
