@@ -351,3 +351,37 @@ def test_gramian_full_tensor_core_layouts(ngd, widths, n_int, n_bnd):
     assert rel(G, G_o) <= 5e-13
     assert np.array_equal(G, G.T)
     ctx.close()
+
+
+def test_factor_wide_core_matches_oracle(ngd):
+    """The FP64-accurate factor of an FP32 context at l = 700: its core is wide enough that the
+    compact-WY back-transform passes the rows of each block of reflectors through shared memory in
+    two chunks (the l = 500 core of the bench fits in one), the double-float tridiagonalization
+    holds five columns of B^T B per block, and the tensor-core products cut K = p into 35 chunks
+    over 8 x 8 lower tiles.  Eigenvalues and the preconditioner apply against the oracle's factor of
+    the same FP32-rounded Omega and FP64 Y (double-float shift), as in
+    test_factor_and_preconditioner_match_oracle[f32-f64]."""
+    wl, pr, th = workload("poisson5d", 600, 150)
+    ell = 700
+    J = mlp.jacobian(pr, th)
+    Om_o = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 11, 0))
+    ctx = ngd.Context(pr, dtype="f32")
+    Om_d = torch.tensor(Om_o.T.copy(), dtype=torch.float32, device="cuda")
+    Om_r = host(Om_d).T
+    Y_r = J.T @ (pr.w[:, None] * (J @ Om_r))
+    Y_d = torch.tensor(Y_r.T.copy(), dtype=torch.float64, device="cuda")
+    U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec="f64")
+    U_o, lam_o, nu_o = nystrom.nystrom_factor(Om_r, host(Y_d).T, nystrom.MANTISSA_BITS["df"])
+    assert abs(nu - nu_o) <= 1e-12 * nu_o
+    lam_g = host(lam)
+    top = lam_o > 1e-6 * lam_o[0]
+    assert np.all(np.diff(lam_g) <= 0)
+    assert rel(lam_g[top], lam_o[top]) <= 1e-8
+    mu = 1e-4
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        v = rng.standard_normal(pr.p)
+        z = host(ctx.precond_apply(ell, U, lam, mu, dev(v)))
+        z_o = nystrom.precond_apply(U_o, lam_o, mu, v)
+        assert rel(z, z_o) <= 1e-8
+    ctx.close()
