@@ -1195,8 +1195,8 @@ ngd_status form_gramian(ngd_ctx* ctx, double* G, int64_t ldG) {
 // power method, mu (into scal[kSMu]), G = J^T (w .* J) formed explicitly (FP64-accurate: for an
 // FP32 Jacobian by the digit-plane tensor-core GEMM, otherwise w .* J in FP64 and the double-float
 // GEMM on the lower triangle; mirrored from the lower one), G + mu I = L L^T (FP64 Cholesky:
-// one cooperative kernel up to kCholBlockedMin - 1 unknowns, the blocked form above),
-// d = L^{-T} L^{-1} g.
+// one cooperative kernel up to kCholBlockedMin - 1 unknowns, the blocked form above, its trailing
+// updates on the digit-plane tensor-core GEMM for an FP32 Jacobian), d = L^{-T} L^{-1} g.
 constexpr int64_t kCholBlockedMin = 768;
 template <typename T>
 ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
@@ -1227,7 +1227,8 @@ ngd_status full_direction(ngd_ctx* ctx, const ngd_step_opts* o) {
   // is rebuilt from the upper one and the saved diagonal).
   for (int attempt = 0;; ++attempt) {
     if (blocked)
-      CK(launch_cholesky_blocked(ctx->Gfull, p, ldG, ctx->status, ctx->chol_D, ctx->chol_W, ctx->chol_T, st));
+      CK(launch_cholesky_blocked(ctx->Gfull, p, ldG, ctx->status, ctx->chol_D, ctx->chol_W, ctx->chol_T, st,
+                                 std::is_same<T, float>::value ? ctx->oz : nullptr, ctx->wait_cycles));
     else
       CK(launch_cholesky(ctx->Gfull, (int)p, ctx->status, st));
     CK(cudaMemcpyAsync(ctx->h_int, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));

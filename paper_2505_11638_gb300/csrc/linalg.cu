@@ -10,6 +10,7 @@
 
 #include "df.cuh"
 #include "linalg.cuh"
+#include "sketch_oz.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1161,7 +1162,7 @@ __global__ void k_neg_copy(const double* __restrict__ X, int64_t ld, int64_t m, 
 // D: 256 x 256 doubles; W: 256 x 256 doubles; T: 256 x (n - 256) doubles.  An even lda keeps
 // the GEMM on its vectorised path.
 cudaError_t launch_cholesky_blocked(double* A, int64_t n, int64_t lda, int* status, double* D, double* W, double* T,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, OzSketch* oz, long long wait_cycles) {
   constexpr int nb = 256;
   for (int64_t k0 = 0; k0 < n; k0 += nb) {
     const int bs = (int)std::min<int64_t>(nb, n - k0);
@@ -1177,6 +1178,12 @@ cudaError_t launch_cholesky_blocked(double* A, int64_t n, int64_t lda, int* stat
     if (m <= 0) break;
     double* P = Akk + bs;                                   // rows k0 + bs .., columns k0 .. k0 + bs
     launch_trsm_lt<double>(P, lda, m, bs, D, W, s);         // P <- P L_kk^{-T}
+    if (oz) {                                               // lower(A22) -= P P^T on the tensor cores
+      const char* why = nullptr;
+      e = oz_syrk_sub(oz, P, lda, m, bs, Akk + bs + bs * lda, lda, &why, s, status, wait_cycles);
+      if (e != cudaSuccess) return e;
+      if (!why) continue;
+    }
     k_neg_copy<<<(int)std::min<int64_t>((m * bs + 255) / 256, 8192), 256, 0, s>>>(P, lda, m, bs, T); note_launch();
     GemmDfArgs<double, double> g;                           // lower(A22) += lower(P (-P^T))
     g.M = m; g.N = m; g.K = bs;

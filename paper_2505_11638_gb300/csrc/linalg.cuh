@@ -77,9 +77,12 @@ void launch_copy_diag(const double* A, int64_t n, int64_t ld, double* dg, cudaSt
 void launch_restore_lower(double* A, int64_t n, int64_t ld, const double* dg, const double* shift, cudaStream_t s);
 void launch_scale_scalar(double* x, double f, cudaStream_t s);
 void launch_lower_to_upper(double* A, int64_t n, int64_t ld, cudaStream_t s);
-// blocked Cholesky for large n; D, W: 256 x 256 doubles, T: 256 x (n - 256) doubles of scratch
+// blocked Cholesky for large n; D, W: 256 x 256 doubles, T: 256 x (n - 256) doubles of scratch.
+// With oz, the trailing updates run on the digit-plane tensor-core GEMM (oz_syrk_sub), otherwise
+// (or where that path cannot serve) on the double-float GEMM.
+struct OzSketch;
 cudaError_t launch_cholesky_blocked(double* A, int64_t n, int64_t lda, int* status, double* D, double* W, double* T,
-                                    cudaStream_t s);
+                                    cudaStream_t s, OzSketch* oz = nullptr, long long wait_cycles = 0);
 
 
 void launch_sum_partials(const double* part, int n, double scale, double* out, cudaStream_t s);

@@ -457,6 +457,7 @@ struct OzDirect {
   double* out;
   int64_t ldOut, M, Nout;
   int on;
+  int sub;                          // subtract from out instead of writing it
 };
 
 // x 2^E for a double x built from an FP32 value (normal range), by integer exponent arithmetic
@@ -727,8 +728,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __grid_constant
             if (!d.on) {
               P[((int64_t)ks * ldL + n) * ldM + row] = make_float2(v.hi, v.lo);
             } else if (row < d.M && n < d.Nout && (!it.lower || row >= n)) {
-              d.out[n * d.ldOut + row] =
-                  oz_scale(f32_to_f64(v.hi) + f32_to_f64(v.lo), d.rexp[row] + d.cexp[n] - 14);
+              double* o = d.out + n * d.ldOut + row;
+              const double val = oz_scale(f32_to_f64(v.hi) + f32_to_f64(v.lo), d.rexp[row] + d.cexp[n] - 14);
+              *o = d.sub ? *o - val : val;
             }
           }
         }
@@ -852,7 +854,7 @@ template <int SA, int SB, int MODE>
 cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMap& tmB, int64_t M, int64_t Nout,
                            int64_t K, const int* rexp, const int* cexp, const double* w, double* out, int64_t ldOut,
                            int* status, cudaStream_t s, long long wait_cycles, bool lower = false, int max_cps = 1,
-                           size_t partial_cap = kPartialCap) {
+                           size_t partial_cap = kPartialCap, bool sub = false) {
   const int64_t ldL = rup(Nout, kBN), ldM = rup(M, kBM);
   const int64_t nchunks = (K + kChunk - 1) / kChunk;
   const size_t chunk_bytes = (size_t)ldL * ldM * sizeof(float2);
@@ -872,7 +874,8 @@ cudaError_t run_digit_gemm(OzSketch* o, const CUtensorMap& tmA, const CUtensorMa
     const size_t run_bytes = (size_t)std::min<int64_t>(tiles * nks, nsm) * kEpiT * kColW * sizeof(float2);
     if ((e = grow(&o->run, &o->run_b, run_bytes)) != cudaSuccess) return e;
   }
-  OzDirect d{rexp, cexp, out, ldOut, M, Nout, 0};
+  OzDirect d{rexp, cexp, out, ldOut, M, Nout, 0, sub ? 1 : 0};
+  if (sub && !(MODE == 3 && nks == 1)) return cudaErrorInvalidValue;   // subtraction: one slice only
   if (MODE == 3 && nks == 1) {
     d.on = 1;
     const OzItems it{n_tiles, m_tiles, (int)tiles, lower ? 1 : 0, 1, (int)cps, 0, (int)nchunks};
@@ -1156,6 +1159,40 @@ cudaError_t oz_gram_self32(OzSketch* o, const float* A, int64_t K, int64_t ld, i
   }
   return run_digit_gemm<kDigOm, kDigOm, 3>(o, mA, mB, ell, ell, K, o->oexp, o->oexp, nullptr, C, ldC, status, s,
                                            wait_cycles, true, 1 << 30);
+}
+
+cudaError_t oz_syrk_sub(OzSketch* o, const double* P, int64_t ldP, int64_t m, int bs, double* C, int64_t ldC,
+                        const char** why, cudaStream_t s, int* status, long long wait_cycles) {
+  *why = nullptr;
+  if (!tensor_map_encoder()) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  if (m < 1 || bs < 1 || bs > kChunk) {
+    *why = "the panel must be 1 to 256 columns wide";
+    return cudaSuccess;
+  }
+  const int64_t ldK = rup(bs, 32);
+  cudaError_t e;
+  if ((e = grow(&o->UA, &o->UA_b, (size_t)kDigZ * m * ldK * 2)) != cudaSuccess) return e;
+  if ((e = grow(&o->uexp, &o->uexp_b, (size_t)m * sizeof(int))) != cudaSuccess) return e;
+  k_oz_rowexp_cm<<<(unsigned)((m + 31) / 32), dim3(32, 8), 0, s>>>(P, ldP, m, bs, o->uexp);
+  note_launch();
+  {
+    dim3 blk(32, 8), grd((unsigned)((m + 31) / 32), (unsigned)(ldK / 32));
+    k_oz_split_rows_cm<<<grd, blk, 0, s>>>(P, ldP, m, bs, o->uexp, o->UA, ldK);
+    note_launch();
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  if (!make_tile_map(&mA, o->UA, 2, m, ldK, ldK, kDigZ, m * ldK, kBM) ||
+      !make_tile_map(&mB, o->UA, 2, m, ldK, ldK, kDigZ, m * ldK, kBN)) {
+    *why = "tensor map encoding failed";
+    return cudaSuccess;
+  }
+  // one K chunk: each lower tile summed by one CTA and subtracted from C by the epilogue
+  return run_digit_gemm<kDigZ, kDigZ, 3>(o, mA, mB, m, m, ldK, o->uexp, o->uexp, nullptr, C, ldC, status, s,
+                                         wait_cycles, true, 1 << 30, kPartialCap, true);
 }
 
 }  // namespace ngd

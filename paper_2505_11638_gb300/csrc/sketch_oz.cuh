@@ -53,6 +53,15 @@ cudaError_t oz_gram_cols(OzSketch* o, const float* A32, const double* B, int64_t
 cudaError_t oz_gram_self32(OzSketch* o, const float* A, int64_t K, int64_t ld, int ell, double* C, int64_t ldC,
                            const char** why, cudaStream_t s, int* status, long long wait_cycles);
 
+// Lower triangle (entries m >= n) of C (m x m, column-major, leading dimension ldC, float64) -=
+// P P^T for the FP64 panel P (m x bs, column-major, leading dimension ldP, bs <= 256): the trailing
+// update of a blocked Cholesky on the digit-plane tensor-core GEMM, P split per row into six
+// digits (~2^-46 of the products of two rows' largest entries per term), one K chunk, the scaled
+// product subtracted by the GEMM's epilogue.  Entries m < n are left untouched.  *why / status as
+// oz_sketch.
+cudaError_t oz_syrk_sub(OzSketch* o, const double* P, int64_t ldP, int64_t m, int bs, double* C, int64_t ldC,
+                        const char** why, cudaStream_t s, int* status, long long wait_cycles);
+
 cudaError_t oz_gemm_bw(OzSketch* o, const double* B, int64_t ldB, int64_t p, int ell, const double* W, int64_t ldW,
                        const double* colscale, double* U, int64_t ldU, const char** why, cudaStream_t s, int* status,
                        long long wait_cycles);

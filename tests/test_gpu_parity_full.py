@@ -385,3 +385,25 @@ def test_factor_wide_core_matches_oracle(ngd):
         z_o = nystrom.precond_apply(U_o, lam_o, mu, v)
         assert rel(z, z_o) <= 1e-8
     ctx.close()
+
+
+def test_ngd_full_step_fp32_tensor_core_cholesky(ngd):
+    """NGD full in an FP32 context at p = 1217: the blocked Cholesky of G + mu I (256-column
+    diagonal blocks, a ragged last one of 193) with its trailing updates on the digit-plane
+    tensor-core GEMM (panel rows split into six digits, lower tiles, the product subtracted by the
+    GEMM's epilogue).  The step's direction solves (G + mu I) d = g, with the context's own G at
+    theta (ngd_gramian_full, pinned against the oracle by the test_gramian_full tests) and its own
+    gradient, to a backward error of 1e-10, and the step decreases the loss."""
+    pr, th = inputs.small_problem(d=3, widths=[3, 32, 32, 1], n_int=1500, n_bnd=300, seed=97)
+    assert th.size == 1217
+    ctx = ngd.Context(pr, dtype="f32")
+    t = dev(th)
+    G = host(ctx.gramian_full(t))
+    g, _, _ = ctx.gradient(t)
+    g = host(g)
+    info = ctx.step(t, precond="full", ell=1, mu=1e-6, seed=3, step=0, sketch="f64")
+    assert info["loss_after"] < info["loss_before"] and info["alpha"] > 0
+    d = (th - host(t)) / info["alpha"]
+    res = G @ d + info["mu"] * d - g
+    assert np.linalg.norm(res) <= 1e-10 * (np.linalg.norm(G, 2) * np.linalg.norm(d) + np.linalg.norm(g))
+    ctx.close()
