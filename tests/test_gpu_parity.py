@@ -227,32 +227,45 @@ def test_factor_and_preconditioner_match_oracle(ngd, dtype, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_factor_eigen_edge_sizes(ngd, dtype):
+@pytest.mark.parametrize("dtype,prec", [("f64", "f64"), ("f32", "f32"), ("f32", "f64")])
+def test_factor_eigen_edge_sizes(ngd, dtype, prec):
     """The l x l eigen-solver at sizes that hit its edge cases: l = 1, 2 (no Householder step),
-    3, and around the 32-wide tiles of the tridiagonal reduction."""
+    3, around the 32-wide tiles of the tridiagonal reduction and, for FP32 contexts, around
+    multiples of 16; an FP32 context's FP64-accurate factor (double-float reduction) to 1e-8."""
     pr, th = small(SMALL[3], seed=31)          # heat, p = 4*12+12+12*9+9+9+1 = 187
     J = mlp.jacobian(pr, th)
     G = J.T @ (pr.w[:, None] * J)
     ctx = ngd.Context(pr, dtype=dtype)
     wd = torch.float64 if dtype == "f64" else torch.float32
-    mb = nystrom.MANTISSA_BITS[dtype]
+    yd = torch.float64 if prec == "f64" else wd
+    # an FP64-accurate factor in an FP32 context runs in double-float (48-bit spacing)
+    mb = nystrom.MANTISSA_BITS["df" if (prec == "f64" and dtype == "f32") else prec]
+    tight = prec == "f64"
     rng = np.random.default_rng(8)
-    for ell in [1, 2, 3, 31, 32, 33, 64, 65, 97]:
+    sizes = [1, 2, 3, 31, 32, 33, 64, 65, 97] if dtype == "f64" else [1, 2, 3, 15, 16, 17, 31, 32, 33, 47, 64, 65, 97]
+    for ell in sizes:
         Om = nystrom.thin_qr(philox.gaussian_test_matrix(pr.p, ell, 17, ell))
         Om_d = torch.tensor(np.ascontiguousarray(Om.T), dtype=wd, device="cuda")
-        Y_d = torch.tensor(np.ascontiguousarray((G @ Om).T), dtype=wd, device="cuda")
-        U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=dtype)
-        U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, mb)
+        Y_d = torch.tensor(np.ascontiguousarray((G @ host(Om_d).T).T), dtype=yd, device="cuda")
+        # G has rank 42 here (42 residual rows), so for l > 42 the core's smallest eigenvalues
+        # are the shift itself; as in the step, a core that the shifted Cholesky finds
+        # indefinite is retried with 8x the shift (the oracle then factors with the same shift)
+        for scale in [1.0, 8.0, 64.0, 512.0]:
+            try:
+                U, lam, nu = ctx.nystrom_factor(ell, Om_d, Y_d, prec=prec, shift_scale=scale)
+                break
+            except ngd.NGDError as err:
+                assert "NOT_SPD" in str(err) and scale < 512.0, (ell, scale)
+        U_o, lam_o, nu_o = nystrom.nystrom_factor(host(Om_d).T, host(Y_d).T, mb, shift_scale=scale)
         lam_g = host(lam)
         top = lam_o > 1e-6 * lam_o[0]
-        assert rel(lam_g[top], lam_o[top]) <= (1e-9 if dtype == "f64" else 1e-4), ell
+        assert rel(lam_g[top], lam_o[top]) <= (1e-8 if tight else 1e-4), ell
         Ug = host(U).T[:, top]     # columns below the core's noise floor are only an orthonormal completion
-        assert np.abs(Ug.T @ Ug - np.eye(int(top.sum()))).max() <= (1e-10 if dtype == "f64" else 2e-5), ell
+        assert np.abs(Ug.T @ Ug - np.eye(int(top.sum()))).max() <= (1e-10 if tight else 2e-5), ell
         v = rng.standard_normal(pr.p)
         mu = 1e-5
         z = host(ctx.precond_apply(ell, U, lam, mu, dev(v)))
-        assert rel(z, nystrom.precond_apply(U_o, lam_o, mu, v)) <= (1e-8 if dtype == "f64" else 2e-3), ell
+        assert rel(z, nystrom.precond_apply(U_o, lam_o, mu, v)) <= (1e-8 if tight else 2e-3), ell
     ctx.close()
 
 
