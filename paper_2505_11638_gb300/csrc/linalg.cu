@@ -1226,67 +1226,133 @@ void launch_scale_scalar(double* x, double f, cudaStream_t s) {
   k_scale_scalar<<<1, 1, 0, s>>>(x, f); note_launch();
 }
 
-// x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, leading dimension ld): forward then
-// backward substitution by blocks of 32 rows in one cooperative launch.  Warp 0 of block 0 solves
-// each diagonal block (its lanes hold the block's entries); the grid then updates the remaining
-// rows: below the block with columns of L (forward), above it with rows of L, i.e. contiguous
-// pieces of its columns (backward).  A row moves between threads from one block of rows to the
-// next, so the vectors are read through L2 (__ldcg).  y: scratch of n.
+// x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, leading dimension ld):
+// forward then backward substitution by blocks of kCsB rows in one cooperative launch, one grid
+// barrier per block.  Block 0 owns the sequential part: its warp 0 solves each diagonal block from
+// shared memory (the block staged there, with the reciprocals of its diagonal, while the other
+// blocks wait at the previous barrier; lanes hold two rows each).  After the barrier every block
+// reads the solved piece, and the rows it still touches are updated: the next diagonal block's
+// rows by block 0 itself (look-ahead), so that block 0 can solve it at once, and the rest by the
+// other blocks.  A row's earlier updates by other blocks lie at least one barrier back.  Forward:
+// one thread per row, columns of L (coalesced).  Backward: one warp per row i < k0, the contiguous
+// piece L[k0 .. k0 + bs, i] of column i.  All arithmetic FP64.  y: scratch of n; gridDim.x >= 2.
+constexpr int kCsB = 64;           // rows per diagonal block
+constexpr int kCsLd = kCsB + 1;    // padded leading dimension of the staged diagonal block
+
+// block 0: diagonal block of L at (k0, k0), bs x bs, into Ls (column-major, ld kCsLd; zeros past
+// bs) and 1 / L_jj into rd
+__device__ __forceinline__ void cs_stage_diag(const double* __restrict__ L, int64_t ld, int k0, int bs,
+                                              double* __restrict__ Ls, double* __restrict__ rd) {
+  for (int e = threadIdx.x; e < kCsB * kCsB; e += blockDim.x) {
+    const int r = e % kCsB, c = e / kCsB;
+    Ls[c * kCsLd + r] = (r < bs && c < bs) ? L[(int64_t)(k0 + r) + (int64_t)(k0 + c) * ld] : 0.0;
+  }
+  if ((int)threadIdx.x < bs) rd[threadIdx.x] = 1.0 / L[(int64_t)(k0 + threadIdx.x) * (ld + 1)];
+}
+
 __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L, int n, int64_t ld,
                                                     const double* __restrict__ b,
                                                     double* __restrict__ x, double* __restrict__ y) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double blk[32];
+  __shared__ double Ls[kCsB * kCsLd];
+  __shared__ double rd[kCsB];
+  __shared__ double blk[kCsB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t ln = ld;
+  const int64_t ot = gtid - blockDim.x, othreads = gthreads - blockDim.x;        // blocks 1 ..
+  const int64_t ow = (int64_t)(blockIdx.x - 1) * nwarp + warp, owarps = (int64_t)(gridDim.x - 1) * nwarp;
+  const bool b0 = blockIdx.x == 0;
   for (int64_t i = gtid; i < n; i += gthreads) y[i] = b[i];
+  if (b0 && n > 0) cs_stage_diag(L, ld, 0, min(kCsB, n), Ls, rd);
   grid.sync();
-  for (int k0 = 0; k0 < n; k0 += 32) {                      // L y = b
-    const int bs = min(32, n - k0);
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-      const int i = threadIdx.x;
-      double yi = i < bs ? __ldcg(y + k0 + i) : 0.0;
-      for (int j = 0; j < bs; ++j) {
-        if (i == j) yi /= L[(k0 + j) * (ln + 1)];
-        const double yj = __shfl_sync(0xffffffffu, yi, j);
-        if (i > j && i < bs) yi -= L[(k0 + i) + (int64_t)(k0 + j) * ln] * yj;
+  for (int k0 = 0; k0 < n; k0 += kCsB) {                    // L y = b
+    const int bs = min(kCsB, n - k0);
+    if (b0) {
+      __syncthreads();                                      // look-ahead rows and the staged block
+      if (warp == 0) {
+        double ya = lane < bs ? __ldcg(y + k0 + lane) : 0.0;
+        double yb = lane + 32 < bs ? __ldcg(y + k0 + 32 + lane) : 0.0;
+        for (int j = 0; j < bs; ++j) {
+          double xj;
+          if (j < 32) {
+            if (lane == j) ya *= rd[j];
+            xj = __shfl_sync(0xffffffffu, ya, j);
+          } else {
+            if (lane == j - 32) yb *= rd[j];
+            xj = __shfl_sync(0xffffffffu, yb, j - 32);
+          }
+          if (lane > j) ya = fma(-Ls[j * kCsLd + lane], xj, ya);
+          if (lane + 32 > j) yb = fma(-Ls[j * kCsLd + lane + 32], xj, yb);
+        }
+        if (lane < bs) y[k0 + lane] = ya;
+        if (lane + 32 < bs) y[k0 + 32 + lane] = yb;
       }
-      if (i < bs) y[k0 + i] = yi;
+      __syncthreads();
+      if (k0 + kCsB < n) cs_stage_diag(L, ld, k0 + kCsB, min(kCsB, n - k0 - kCsB), Ls, rd);
     }
     grid.sync();
-    if (threadIdx.x < bs) blk[threadIdx.x] = __ldcg(y + k0 + threadIdx.x);
+    if (k0 + kCsB >= n) break;                              // the same in every block
+    if ((int)threadIdx.x < kCsB) blk[threadIdx.x] = __ldcg(y + k0 + threadIdx.x);
     __syncthreads();
-    for (int64_t i = k0 + bs + gtid; i < n; i += gthreads) {
-      double s = 0.0;
-      for (int j = 0; j < bs; ++j) s += L[i + (int64_t)(k0 + j) * ln] * blk[j];
-      y[i] = __ldcg(y + i) - s;
+    const int64_t i0 = b0 ? k0 + kCsB + threadIdx.x : k0 + 2 * kCsB + ot;
+    const int64_t i1 = b0 ? min(n, k0 + 2 * kCsB) : n;
+    for (int64_t i = i0; i < i1; i += b0 ? (int64_t)blockDim.x : othreads) {
+      const double* Lr = L + i + (int64_t)k0 * ld;           // L[i, k0 + j] at Lr[j ld]
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+      for (int j = 0; j < kCsB; j += 4) {
+        s0 = fma(Lr[(int64_t)j * ld], blk[j], s0);
+        s1 = fma(Lr[(int64_t)(j + 1) * ld], blk[j + 1], s1);
+        s2 = fma(Lr[(int64_t)(j + 2) * ld], blk[j + 2], s2);
+        s3 = fma(Lr[(int64_t)(j + 3) * ld], blk[j + 3], s3);
+      }
+      y[i] = __ldcg(y + i) - ((s0 + s1) + (s2 + s3));
     }
-    grid.sync();
   }
   for (int64_t i = gtid; i < n; i += gthreads) x[i] = __ldcg(y + i);
+  const int klast = n > 0 ? ((n - 1) / kCsB) * kCsB : 0;
+  if (b0 && n > 0) cs_stage_diag(L, ld, klast, n - klast, Ls, rd);
   grid.sync();
-  for (int k0 = ((n - 1) / 32) * 32; k0 >= 0; k0 -= 32) {  // L^T x = y
-    const int bs = min(32, n - k0);
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-      const int i = threadIdx.x;
-      double xi = i < bs ? __ldcg(x + k0 + i) : 0.0;
-      for (int j = bs - 1; j >= 0; --j) {
-        if (i == j) xi /= L[(k0 + j) * (ln + 1)];
-        const double xj = __shfl_sync(0xffffffffu, xi, j);
-        if (i < j) xi -= L[(k0 + j) + (int64_t)(k0 + i) * ln] * xj;
+  for (int k0 = klast; k0 >= 0 && n > 0; k0 -= kCsB) {      // L^T x = y
+    const int bs = min(kCsB, n - k0);
+    if (b0) {
+      __syncthreads();
+      if (warp == 0) {
+        double xa = lane < bs ? __ldcg(x + k0 + lane) : 0.0;
+        double xb = lane + 32 < bs ? __ldcg(x + k0 + 32 + lane) : 0.0;
+        for (int j = bs - 1; j >= 0; --j) {
+          double xj;
+          if (j < 32) {
+            if (lane == j) xa *= rd[j];
+            xj = __shfl_sync(0xffffffffu, xa, j);
+          } else {
+            if (lane == j - 32) xb *= rd[j];
+            xj = __shfl_sync(0xffffffffu, xb, j - 32);
+          }
+          if (lane < j) xa = fma(-Ls[lane * kCsLd + j], xj, xa);            // L[k0 + j, k0 + lane]
+          if (lane + 32 < j) xb = fma(-Ls[(lane + 32) * kCsLd + j], xj, xb);
+        }
+        if (lane < bs) x[k0 + lane] = xa;
+        if (lane + 32 < bs) x[k0 + 32 + lane] = xb;
       }
-      if (i < bs) x[k0 + i] = xi;
+      __syncthreads();
+      if (k0 > 0) cs_stage_diag(L, ld, k0 - kCsB, kCsB, Ls, rd);
     }
     grid.sync();
-    if (threadIdx.x < bs) blk[threadIdx.x] = __ldcg(x + k0 + threadIdx.x);
+    if (k0 == 0) break;
+    if ((int)threadIdx.x < bs) blk[threadIdx.x] = __ldcg(x + k0 + threadIdx.x);
     __syncthreads();
-    for (int64_t i = gtid; i < k0; i += gthreads) {
-      double s = 0.0;
-      const double* col = L + i * ln + k0;                    // L[k0 .. k0 + bs, i]
-      for (int j = 0; j < bs; ++j) s += col[j] * blk[j];
-      x[i] = __ldcg(x + i) - s;
+    // rows k0 - kCsB .. k0 - 1 by block 0, the rows below them by the others; one warp per row
+    const int64_t r0 = b0 ? warp : kCsB + ow;
+    const int64_t r1 = b0 ? kCsB : k0;
+    for (int64_t r = r0; r < r1; r += b0 ? nwarp : owarps) {
+      const int64_t i = k0 - 1 - r;
+      const double* c = L + i * ld + k0;                     // L[k0 + j, i] at c[j]
+      double s = lane < bs ? c[lane] * blk[lane] : 0.0;
+      if (lane + 32 < bs) s = fma(c[lane + 32], blk[lane + 32], s);
+      s = wsum(s);
+      if (lane == 0) x[i] = __ldcg(x + i) - s;
     }
-    grid.sync();
   }
 }
 cudaError_t launch_chol_solve(const double* L, int n, int64_t ld, const double* b, double* x, double* y,
@@ -1295,7 +1361,7 @@ cudaError_t launch_chol_solve(const double* L, int n, int64_t ld, const double* 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_solve, 256, 0);
-  const int blocks = std::max(1, std::min(per, 2)) * nsm;
+  const int blocks = std::max(2, std::max(1, std::min(per, 2)) * nsm);   // block 0 and at least one more
   void* args[] = {(void*)&L, &n, &ld, (void*)&b, &x, &y};
   note_launch();
   return cudaLaunchCooperativeKernel((const void*)k_chol_solve, blocks, 256, args, 0, s);
