@@ -1229,41 +1229,81 @@ void launch_scale_scalar(double* x, double f, cudaStream_t s) {
 // x = (L L^T)^{-1} b for the lower Cholesky factor L (n x n, column-major, leading dimension ld):
 // forward then backward substitution by blocks of kCsB rows in one cooperative launch, one grid
 // barrier per block.  Block 0 owns the sequential part: its warp 0 solves each diagonal block from
-// shared memory (the block staged there, with the reciprocals of its diagonal, while the other
-// blocks wait at the previous barrier; lanes hold two rows each).  After the barrier every block
-// reads the solved piece, and the rows it still touches are updated: the next diagonal block's
-// rows by block 0 itself (look-ahead), so that block 0 can solve it at once, and the rest by the
-// other blocks.  A row's earlier updates by other blocks lie at least one barrier back.  Forward:
-// one thread per row, columns of L (coalesced).  Backward: one warp per row i < k0, the contiguous
-// piece L[k0 .. k0 + bs, i] of column i.  All arithmetic FP64.  y: scratch of n; gridDim.x >= 2.
+// shared memory (lanes hold two rows each), the block staged there while the other blocks wait at
+// the previous barrier, its strictly lower entries already divided by the pivot that multiplies
+// them (column pivots forward, row pivots backward), so that the dependent chain is one shuffle
+// and the FMAs of the rows still open per column, and the solved piece is scaled by the
+// reciprocal pivots at the end.  After the barrier every block reads the solved piece, and the
+// rows still to be updated are: the next diagonal block's rows by block 0 itself (look-ahead), so
+// that block 0 can solve it at once, and the rest by the other blocks.  A row's earlier updates by
+// other blocks lie at least one barrier back.  Each row's kCsB-term update is split over four
+// threads (a quarter of the columns each) and combined in shared memory, so that every warp-wide
+// FP64 instruction carries 32 rows: GB300's FP64 pipe retires about two FMAs per clock and SM.
+// All arithmetic FP64.  y: scratch of n; gridDim.x >= 2, blockDim.x = kCsT.
 constexpr int kCsB = 64;           // rows per diagonal block
 constexpr int kCsLd = kCsB + 1;    // padded leading dimension of the staged diagonal block
+constexpr int kCsT = 256;          // threads per block: kCsB rows x 4 quarters of the columns
+static_assert(kCsT == 4 * kCsB, "one row per four threads");
 
-// block 0: diagonal block of L at (k0, k0), bs x bs, into Ls (column-major, ld kCsLd; zeros past
-// bs) and 1 / L_jj into rd
-__device__ __forceinline__ void cs_stage_diag(const double* __restrict__ L, int64_t ld, int k0, int bs,
+// block 0: diagonal block of L at (k0, k0), bs x bs, into Ls (column-major, ld kCsLd) with only its
+// strictly lower entries kept, each divided by its column's pivot (fwd) or its row's pivot (bwd);
+// 1 / L_jj into rd.
+__device__ __forceinline__ void cs_stage_diag(const double* __restrict__ L, int64_t ld, int k0, int bs, bool fwd,
                                               double* __restrict__ Ls, double* __restrict__ rd) {
+  if ((int)threadIdx.x < bs) rd[threadIdx.x] = 1.0 / L[(int64_t)(k0 + threadIdx.x) * (ld + 1)];
+  __syncthreads();
   for (int e = threadIdx.x; e < kCsB * kCsB; e += blockDim.x) {
     const int r = e % kCsB, c = e / kCsB;
-    Ls[c * kCsLd + r] = (r < bs && c < bs) ? L[(int64_t)(k0 + r) + (int64_t)(k0 + c) * ld] : 0.0;
+    Ls[c * kCsLd + r] = (r < bs && c < r) ? L[(int64_t)(k0 + r) + (int64_t)(k0 + c) * ld] * rd[fwd ? c : r] : 0.0;
   }
-  if ((int)threadIdx.x < bs) rd[threadIdx.x] = 1.0 / L[(int64_t)(k0 + threadIdx.x) * (ld + 1)];
 }
 
-__global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L, int n, int64_t ld,
+// y[i] -= sum_{j < bs} L(i, j) blk[j] for the rows i = row(r), r = r0 + (tid mod kCsB),
+// r0 + kCsB G', ... < r1, where L(i, j) = L[i + (k0 + j) ld] (fwd) or L[k0 + j + i ld] (bwd):
+// four threads per row, a quarter of the j each.  Every thread of the block calls it.
+__device__ __forceinline__ void cs_update_rows(const double* __restrict__ L, int64_t ld, int k0, int bs, bool fwd,
+                                               int64_t r0, int64_t r1, int64_t rstride, int64_t base, int64_t dir,
+                                               const double* __restrict__ blk, double* __restrict__ red,
+                                               double* __restrict__ v) {
+  const int rr = threadIdx.x % kCsB, q = threadIdx.x / kCsB;
+  constexpr int kQ = kCsB / 4;
+  for (int64_t r = r0; r < r1; r += rstride) {              // r0, r1, rstride the same in the whole block
+    const int64_t rt = r + rr;
+    const bool on = rt < r1;
+    const int64_t i = base + dir * rt;
+    double s0 = 0.0, s1 = 0.0;
+    if (on) {
+#pragma unroll
+      for (int t = 0; t < kQ; t += 2) {
+        const int j = q * kQ + t;
+        const double l0 = j < bs ? (fwd ? L[i + (int64_t)(k0 + j) * ld] : L[k0 + j + i * ld]) : 0.0;
+        const double l1 = j + 1 < bs ? (fwd ? L[i + (int64_t)(k0 + j + 1) * ld] : L[k0 + j + 1 + i * ld]) : 0.0;
+        s0 = fma(l0, blk[j], s0);
+        s1 = fma(l1, blk[j + 1], s1);
+      }
+    }
+    red[q * kCsB + rr] = s0 + s1;
+    __syncthreads();
+    if (q == 0 && on) v[i] = __ldcg(v + i) - ((red[rr] + red[kCsB + rr]) + (red[2 * kCsB + rr] + red[3 * kCsB + rr]));
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kCsT) k_chol_solve(const double* __restrict__ L, int n, int64_t ld,
                                                     const double* __restrict__ b,
                                                     double* __restrict__ x, double* __restrict__ y) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double Ls[kCsB * kCsLd];
   __shared__ double rd[kCsB];
   __shared__ double blk[kCsB];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ double red[4 * kCsB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t ot = gtid - blockDim.x, othreads = gthreads - blockDim.x;        // blocks 1 ..
-  const int64_t ow = (int64_t)(blockIdx.x - 1) * nwarp + warp, owarps = (int64_t)(gridDim.x - 1) * nwarp;
   const bool b0 = blockIdx.x == 0;
+  // rows of the other blocks: kCsB per block and pass, passes over the G - 1 blocks
+  const int64_t orow0 = (int64_t)(blockIdx.x - 1) * kCsB, ostride = (int64_t)(gridDim.x - 1) * kCsB;
   for (int64_t i = gtid; i < n; i += gthreads) y[i] = b[i];
-  if (b0 && n > 0) cs_stage_diag(L, ld, 0, min(kCsB, n), Ls, rd);
+  if (b0 && n > 0) cs_stage_diag(L, ld, 0, min(kCsB, n), true, Ls, rd);
   grid.sync();
   for (int k0 = 0; k0 < n; k0 += kCsB) {                    // L y = b
     const int bs = min(kCsB, n - k0);
@@ -1272,46 +1312,28 @@ __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L
       if (warp == 0) {
         double ya = lane < bs ? __ldcg(y + k0 + lane) : 0.0;
         double yb = lane + 32 < bs ? __ldcg(y + k0 + 32 + lane) : 0.0;
-        for (int j = 0; j < bs; ++j) {
-          double xj;
-          if (j < 32) {
-            if (lane == j) ya *= rd[j];
-            xj = __shfl_sync(0xffffffffu, ya, j);
-          } else {
-            if (lane == j - 32) yb *= rd[j];
-            xj = __shfl_sync(0xffffffffu, yb, j - 32);
-          }
-          if (lane > j) ya = fma(-Ls[j * kCsLd + lane], xj, ya);
-          if (lane + 32 > j) yb = fma(-Ls[j * kCsLd + lane + 32], xj, yb);
+        for (int j = 0; j < bs; ++j) {                      // unscaled: pivots applied at the end
+          const double yj = __shfl_sync(0xffffffffu, j < 32 ? ya : yb, j & 31);
+          if (j < 31) ya = fma(-Ls[j * kCsLd + lane], yj, ya);
+          yb = fma(-Ls[j * kCsLd + lane + 32], yj, yb);
         }
-        if (lane < bs) y[k0 + lane] = ya;
-        if (lane + 32 < bs) y[k0 + 32 + lane] = yb;
+        if (lane < bs) y[k0 + lane] = ya * rd[lane];
+        if (lane + 32 < bs) y[k0 + 32 + lane] = yb * rd[lane + 32];
       }
       __syncthreads();
-      if (k0 + kCsB < n) cs_stage_diag(L, ld, k0 + kCsB, min(kCsB, n - k0 - kCsB), Ls, rd);
+      if (k0 + kCsB < n) cs_stage_diag(L, ld, k0 + kCsB, min(kCsB, n - k0 - kCsB), true, Ls, rd);
     }
     grid.sync();
     if (k0 + kCsB >= n) break;                              // the same in every block
     if ((int)threadIdx.x < kCsB) blk[threadIdx.x] = __ldcg(y + k0 + threadIdx.x);
     __syncthreads();
-    const int64_t i0 = b0 ? k0 + kCsB + threadIdx.x : k0 + 2 * kCsB + ot;
-    const int64_t i1 = b0 ? min(n, k0 + 2 * kCsB) : n;
-    for (int64_t i = i0; i < i1; i += b0 ? (int64_t)blockDim.x : othreads) {
-      const double* Lr = L + i + (int64_t)k0 * ld;           // L[i, k0 + j] at Lr[j ld]
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll 4
-      for (int j = 0; j < kCsB; j += 4) {
-        s0 = fma(Lr[(int64_t)j * ld], blk[j], s0);
-        s1 = fma(Lr[(int64_t)(j + 1) * ld], blk[j + 1], s1);
-        s2 = fma(Lr[(int64_t)(j + 2) * ld], blk[j + 2], s2);
-        s3 = fma(Lr[(int64_t)(j + 3) * ld], blk[j + 3], s3);
-      }
-      y[i] = __ldcg(y + i) - ((s0 + s1) + (s2 + s3));
-    }
+    const int64_t nrest = n - (k0 + kCsB);                  // rows below the solved block
+    if (b0) cs_update_rows(L, ld, k0, kCsB, true, 0, nrest < kCsB ? nrest : kCsB, kCsB, k0 + kCsB, 1, blk, red, y);
+    else cs_update_rows(L, ld, k0, kCsB, true, kCsB + orow0, nrest, ostride, k0 + kCsB, 1, blk, red, y);
   }
   for (int64_t i = gtid; i < n; i += gthreads) x[i] = __ldcg(y + i);
   const int klast = n > 0 ? ((n - 1) / kCsB) * kCsB : 0;
-  if (b0 && n > 0) cs_stage_diag(L, ld, klast, n - klast, Ls, rd);
+  if (b0 && n > 0) cs_stage_diag(L, ld, klast, n - klast, false, Ls, rd);
   grid.sync();
   for (int k0 = klast; k0 >= 0 && n > 0; k0 -= kCsB) {      // L^T x = y
     const int bs = min(kCsB, n - k0);
@@ -1320,39 +1342,24 @@ __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ L
       if (warp == 0) {
         double xa = lane < bs ? __ldcg(x + k0 + lane) : 0.0;
         double xb = lane + 32 < bs ? __ldcg(x + k0 + 32 + lane) : 0.0;
-        for (int j = bs - 1; j >= 0; --j) {
-          double xj;
-          if (j < 32) {
-            if (lane == j) xa *= rd[j];
-            xj = __shfl_sync(0xffffffffu, xa, j);
-          } else {
-            if (lane == j - 32) xb *= rd[j];
-            xj = __shfl_sync(0xffffffffu, xb, j - 32);
-          }
-          if (lane < j) xa = fma(-Ls[lane * kCsLd + j], xj, xa);            // L[k0 + j, k0 + lane]
-          if (lane + 32 < j) xb = fma(-Ls[(lane + 32) * kCsLd + j], xj, xb);
+        for (int j = bs - 1; j >= 0; --j) {                 // x_r -= (L[k0 + j, k0 + r] / L_jj) x_j
+          const double xj = __shfl_sync(0xffffffffu, j < 32 ? xa : xb, j & 31);
+          xa = fma(-Ls[lane * kCsLd + j], xj, xa);
+          if (j > 32) xb = fma(-Ls[(lane + 32) * kCsLd + j], xj, xb);
         }
-        if (lane < bs) x[k0 + lane] = xa;
-        if (lane + 32 < bs) x[k0 + 32 + lane] = xb;
+        if (lane < bs) x[k0 + lane] = xa * rd[lane];
+        if (lane + 32 < bs) x[k0 + 32 + lane] = xb * rd[lane + 32];
       }
       __syncthreads();
-      if (k0 > 0) cs_stage_diag(L, ld, k0 - kCsB, kCsB, Ls, rd);
+      if (k0 > 0) cs_stage_diag(L, ld, k0 - kCsB, kCsB, false, Ls, rd);
     }
     grid.sync();
     if (k0 == 0) break;
-    if ((int)threadIdx.x < bs) blk[threadIdx.x] = __ldcg(x + k0 + threadIdx.x);
+    if ((int)threadIdx.x < kCsB) blk[threadIdx.x] = (int)threadIdx.x < bs ? __ldcg(x + k0 + threadIdx.x) : 0.0;
     __syncthreads();
-    // rows k0 - kCsB .. k0 - 1 by block 0, the rows below them by the others; one warp per row
-    const int64_t r0 = b0 ? warp : kCsB + ow;
-    const int64_t r1 = b0 ? kCsB : k0;
-    for (int64_t r = r0; r < r1; r += b0 ? nwarp : owarps) {
-      const int64_t i = k0 - 1 - r;
-      const double* c = L + i * ld + k0;                     // L[k0 + j, i] at c[j]
-      double s = lane < bs ? c[lane] * blk[lane] : 0.0;
-      if (lane + 32 < bs) s = fma(c[lane + 32], blk[lane + 32], s);
-      s = wsum(s);
-      if (lane == 0) x[i] = __ldcg(x + i) - s;
-    }
+    // row i = k0 - 1 - r: r < kCsB by block 0, the rest by the others
+    if (b0) cs_update_rows(L, ld, k0, bs, false, 0, kCsB, kCsB, k0 - 1, -1, blk, red, x);
+    else cs_update_rows(L, ld, k0, bs, false, kCsB + orow0, k0, ostride, k0 - 1, -1, blk, red, x);
   }
 }
 cudaError_t launch_chol_solve(const double* L, int n, int64_t ld, const double* b, double* x, double* y,
@@ -1360,11 +1367,11 @@ cudaError_t launch_chol_solve(const double* L, int n, int64_t ld, const double* 
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_solve, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_solve, kCsT, 0);
   const int blocks = std::max(2, std::max(1, std::min(per, 2)) * nsm);   // block 0 and at least one more
   void* args[] = {(void*)&L, &n, &ld, (void*)&b, &x, &y};
   note_launch();
-  return cudaLaunchCooperativeKernel((const void*)k_chol_solve, blocks, 256, args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_chol_solve, blocks, kCsT, args, 0, s);
 }
 
 // ---------------------------------------------------------------------------- SIMT GEMM
